@@ -1,0 +1,510 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a printed
+value of the paper (tests/golden), a published test vector, a closed form,
+brute force on tiny inputs, or an invariant. All run on the CPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# config-1 parameters: N=2^12, Q = 60/40/40, P = 3 x 60 (reading R2), dnum = 1, Delta = 2^40
+P1 = dict(log_n=12, q_bits=[60, 40, 40], p_bits=[60, 60, 60], dnum=1, scale_bits=40)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return oracle.Ctx(**P1)
+
+
+@pytest.fixture(scope="module")
+def k1(c1):
+    return c1.keygen(0xC0FFEE01)
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                key, val = line.split(None, 1)
+                vals[key] = val.strip()
+    return vals
+
+
+def brev(x, bits):
+    return int(format(x, f"0{bits}b")[::-1], 2)
+
+
+def rhaz(x):
+    """round half away from zero"""
+    return np.sign(x) * np.floor(np.abs(x) + 0.5)
+
+
+# ---------------------------------------------------------------------------
+# generator of randomness: ChaCha20 (RFC 8439)
+# ---------------------------------------------------------------------------
+def test_chacha20_rfc8439_vector():
+    g = read_golden("chacha20_rfc8439_block.txt")
+    key = bytes.fromhex(g["key"])
+    nonce = bytes.fromhex(g["nonce"])
+    kw = np.frombuffer(key, dtype="<u4").astype(np.uint32)
+    nw = np.frombuffer(nonce, dtype="<u4").astype(np.uint32)
+    out = oracle.chacha20_block(kw, int(g["counter"]), nw)
+    assert out.tobytes().hex() == g["block"]
+
+
+def test_chacha20_matches_independent_library():
+    crypt = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        key = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
+        nonce = rng.integers(0, 256, 12, dtype=np.uint8).tobytes()
+        ctr = int(rng.integers(0, 2**31))
+        enc = crypt.Cipher(crypt.algorithms.ChaCha20(key, ctr.to_bytes(4, "little") + nonce), mode=None).encryptor()
+        ref = enc.update(bytes(64))
+        out = oracle.chacha20_block(np.frombuffer(key, "<u4").astype(np.uint32), ctr,
+                                    np.frombuffer(nonce, "<u4").astype(np.uint32))
+        assert out.tobytes() == ref
+
+
+def test_samplers_distributions():
+    n = 1 << 15
+    t = oracle.sample_ternary(11, 1, n)
+    assert set(np.unique(t)) <= {-1, 0, 1}
+    frac = [(t == v).mean() for v in (-1, 0, 1)]
+    assert max(abs(f - 1 / 3) for f in frac) < 0.02
+    e = oracle.sample_cbd(11, 3, n)
+    assert np.abs(e).max() <= 21 and abs(e.mean()) < 0.1 and abs(e.var() - 10.5) < 0.6
+    q = (1 << 50) - 1234567
+    u = oracle.sample_uniform(11, 2, 4, q, n)
+    assert u.max() < q and abs(u.astype(np.float64).mean() / q - 0.5) < 0.02
+    # distinct objects / limbs give distinct streams
+    assert not np.array_equal(u, oracle.sample_uniform(11, 2, 5, q, n))
+
+
+# ---------------------------------------------------------------------------
+# primes and roots (reading R1)
+# ---------------------------------------------------------------------------
+def test_primes_config1_and_config2():
+    sympy = pytest.importorskip("sympy")
+    for log_n, qb, pb in [(12, [60, 40, 40], [60, 60, 60]), (16, [60] + [50] * 24, [60] * 4)]:
+        ps = oracle.gen_primes(log_n, qb + pb)
+        M = 2 << log_n
+        assert len(set(ps)) == len(ps)
+        for p, b in zip(ps, qb + pb):
+            assert sympy.isprime(p) and p % M == 1 and p.bit_length() == b
+        # "largest-first per bit size": every prime = 1 mod 2N of that size above the
+        # smallest chosen one is chosen, and they appear in descending order
+        for b in set(qb + pb):
+            chosen = [p for p, bb in zip(ps, qb + pb) if bb == b]
+            assert chosen == sorted(chosen, reverse=True)
+            c = ((1 << b) - 1) // M * M + 1
+            above = []
+            while c >= min(chosen):
+                if sympy.isprime(c):
+                    above.append(c)
+                c -= M
+            assert above == chosen
+
+
+def test_psi_is_primitive_root_from_smallest_generator(c1):
+    sympy = pytest.importorskip("sympy")
+    N = c1.N
+    for i, q in enumerate(c1.primes):
+        psi = c1.psi(i)
+        g = int(sympy.primitive_root(q))
+        assert psi == pow(g, (q - 1) // (2 * N), q)
+        assert pow(psi, N, q) == q - 1
+
+
+# ---------------------------------------------------------------------------
+# NTT: evaluation at psi^(2 brev(k) + 1), pinned by O(N^2) evaluation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("log_n", [3, 4, 6])
+def test_ntt_is_evaluation_at_odd_powers(log_n):
+    c = oracle.Ctx(log_n, [30], [31], 1, 20)
+    N, q, psi = c.N, c.primes[0], c.psi(0)
+    rng = np.random.default_rng(log_n)
+    a = [int(x) for x in rng.integers(0, q, N)]
+    A = c.ntt_fwd(0, np.array(a, dtype=np.uint64))
+    for k in range(N):
+        e = 2 * brev(k, log_n) + 1
+        ref = sum(a[j] * pow(psi, e * j, q) for j in range(N)) % q
+        assert int(A[k]) == ref
+    assert [int(x) for x in c.ntt_inv(0, A)] == a
+
+
+def test_ntt_negacyclic_convolution_schoolbook():
+    log_n = 8
+    c = oracle.Ctx(log_n, [40], [41], 1, 20)
+    N, q = c.N, c.primes[0]
+    rng = np.random.default_rng(3)
+    a = [int(x) for x in rng.integers(0, q, N)]
+    b = [int(x) for x in rng.integers(0, q, N)]
+    ref = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                ref[k] = (ref[k] + a[i] * b[j]) % q
+            else:
+                ref[k - N] = (ref[k - N] - a[i] * b[j]) % q
+    A = c.ntt_fwd(0, np.array(a, dtype=np.uint64))
+    B = c.ntt_fwd(0, np.array(b, dtype=np.uint64))
+    C = np.array([(int(x) * int(y)) % q for x, y in zip(A, B)], dtype=np.uint64)
+    assert [int(x) for x in c.ntt_inv(0, C)] == ref
+
+
+def test_automorphism_coef_and_eval_agree(c1):
+    rng = np.random.default_rng(2)
+    q = c1.primes[1]
+    N = c1.N
+    a = rng.integers(0, q, N).astype(np.uint64)
+    for k in (1, 3, 17, -5):
+        g = c1.galois(k)
+        assert g == pow(5, k % (N // 2), 2 * N)
+        # plain restatement of a(X) -> a(X^g)
+        ref = np.zeros(N, dtype=object)
+        for j in range(N):
+            e = (j * g) % (2 * N)
+            if e < N:
+                ref[e] = int(a[j])
+            else:
+                ref[e - N] = (q - int(a[j])) % q
+        got = c1.automorph_coef(g, 1, a)
+        assert [int(x) for x in got] == list(ref)
+        assert np.array_equal(c1.ntt_fwd(1, got), c1.automorph_eval(g, c1.ntt_fwd(1, a)))
+
+
+# ---------------------------------------------------------------------------
+# Encoding: inverse canonical embedding over the 5^j slot order (reading R5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("log_n", [5, 8, 10])
+def test_encode_matches_quadratic_definition(log_n):
+    c = oracle.Ctx(log_n, [50], [51], 1, 40)
+    N, n, M = c.N, c.N // 2, 2 * c.N
+    rng = np.random.default_rng(log_n)
+    z = rng.uniform(-1, 1, n)
+    g = np.array([pow(5, j, M) for j in range(n)], dtype=np.int64)
+    cc = np.arange(N, dtype=np.int64)
+    ang = 2 * np.pi * ((g[:, None] * cc[None, :]) % M) / M
+    m_def = (z[:, None] * np.cos(ang)).sum(axis=0) / n * 2.0 ** 40
+    ref = rhaz(m_def)
+    got = c.encode_coeffs(z).astype(np.float64)
+    bad = np.nonzero(got != ref)[0]
+    near_tie = np.abs(np.abs(m_def - np.trunc(m_def)) - 0.5) < 1e-2
+    assert np.all(near_tie[bad]) and np.all(np.abs(got - ref) <= 1)
+    assert len(bad) <= max(2, N // 256)
+
+
+def test_encode_decode_round_trip(c1):
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-1, 1, c1.n)
+    m = c1.encode_coeffs(z)
+    assert np.abs(c1.decode_coeffs(m, 2.0 ** 40) - z).max() < 1e-9
+
+
+def test_galois_5k_is_left_rotation_of_slots(c1):
+    """decode(sigma_{5^k}(encode(z))) = z rotated left by k (Eq. equ:diag's Rot_i direction)."""
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, c1.n)
+    m = c1.encode_coeffs(z)
+    N = c1.N
+    for k in (1, 2, 7, 100):
+        g = pow(5, k, 2 * N)
+        out = np.zeros(N, dtype=np.int64)
+        for j in range(N):
+            e = (j * g) % (2 * N)
+            if e < N:
+                out[e] = m[j]
+            else:
+                out[e - N] = -m[j]
+        assert np.abs(c1.decode_coeffs(out, 2.0 ** 40) - np.roll(z, -k)).max() < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Keys, encryption, key switching, rescale, products
+# ---------------------------------------------------------------------------
+def test_encrypt_decrypt(c1, k1):
+    rng = np.random.default_rng(6)
+    z = rng.uniform(-1, 1, c1.n)
+    ct = k1.encrypt(z, 0xE0C00001)
+    assert ct.shape == (2, 3, c1.N) and all(int(ct[:, i].max()) < c1.primes[i] for i in range(3))
+    assert np.abs(k1.decrypt(ct, 2) - z).max() < 1e-6
+    # same seed -> same ciphertext; other seed -> other ciphertext
+    assert np.array_equal(ct, k1.encrypt(z, 0xE0C00001))
+    assert not np.array_equal(ct, k1.encrypt(z, 0xE0C00002))
+
+
+def _small_centered(v, q):
+    v = int(v) % q
+    return v - q if v > q // 2 else v
+
+
+def test_evk_structure(c1, k1):
+    """evk_d0 + evk_d1 * s = e_d + [P]_{q_i} s' on the digit's limbs (hybrid key switching key)."""
+    s = k1.secret().astype(np.int64)
+    N = c1.N
+    g = c1.galois(3)
+    evk = k1.make_evk(0, g)
+    T = c1.nq + c1.np_
+    P = 1
+    for p in c1.primes[c1.nq:]:
+        P *= p
+    for d in range(c1.ndig):
+        lo, hi = c1.dstart[d], c1.dstart[d + 1]
+        for i in range(T):
+            q = c1.primes[i]
+            se = c1.ntt_fwd(i, (s % q).astype(np.uint64))
+            sp = c1.automorph_eval(g, se)
+            b = evk[d, 0, i].astype(object)
+            a = evk[d, 1, i].astype(object)
+            val = (b + a * se.astype(object)) % q
+            if lo <= i < hi:
+                val = (val - (P % q) * sp.astype(object)) % q
+            e = c1.ntt_inv(i, np.array(val, dtype=np.uint64))
+            ec = np.array([_small_centered(x, q) for x in e])
+            assert np.abs(ec).max() <= 21
+
+
+def test_rotation_decrypts_to_left_rotation(c1, k1):
+    rng = np.random.default_rng(7)
+    z = rng.uniform(-1, 1, c1.n)
+    ct = k1.encrypt(z, 99)
+    for k in (1, 5, 64, c1.n - 1):
+        r = k1.rotate(ct, 2, k)
+        assert np.abs(k1.decrypt(r, 2) - np.roll(z, -k)).max() < 1e-6
+    ct1 = c1.drop(ct, 2, 1)
+    assert np.abs(k1.decrypt(k1.rotate(ct1, 1, 9), 1) - np.roll(z, -9)).max() < 1e-6
+
+
+def test_hoisted_equals_individual_rotations(c1, k1):
+    rng = np.random.default_rng(8)
+    ct = k1.encrypt(rng.uniform(-1, 1, c1.n), 5)
+    ks = [0, 1, 2, 7]
+    H = k1.hoisted_rotate(ct, 2, ks)
+    for i, k in enumerate(ks):
+        assert np.array_equal(H[i], k1.rotate(ct, 2, k))
+
+
+def test_rescale_is_rounded_division_by_last_prime(c1):
+    """Exact CRT check: output = (x - v) / q_l with v the centered residue mod q_l."""
+    rng = np.random.default_rng(9)
+    qs = c1.primes[:3]
+    Q = qs[0] * qs[1] * qs[2]
+    N = 64
+    ct = np.zeros((2, 3, c1.N), dtype=np.uint64)
+    xs = [int(v) for v in rng.integers(0, 2 ** 62, N)]
+    xs = [(x * 977 + 12345) % Q for x in xs]
+    for j, x in enumerate(xs):
+        for i in range(3):
+            ct[0, i, j] = x % qs[i]
+            ct[1, i, j] = (x * 3) % qs[i]
+    out = c1.rescale(ct, 2)
+    ql = qs[2]
+    for t, mult in ((0, 1), (1, 3)):
+        for j, x0 in enumerate(xs):
+            x = (x0 * mult) % Q
+            v = x % ql
+            v = v - ql if v > (ql - 1) // 2 else v
+            y = (x - v) // ql
+            assert (x - v) % ql == 0
+            for i in range(2):
+                assert int(out[t, i, j]) == y % qs[i]
+
+
+def test_mul_relin_rescale(c1, k1):
+    rng = np.random.default_rng(10)
+    z1, z2 = rng.uniform(-1, 1, c1.n), rng.uniform(-1, 1, c1.n)
+    a, b = k1.encrypt(z1, 1), k1.encrypt(z2, 2)
+    m = c1.rescale(k1.mul_relin(a, b, 2), 2)
+    assert np.abs(k1.decrypt(m, 1) - z1 * z2).max() < 1e-6
+
+
+def test_rotate_sum_gives_total_in_every_slot(c1, k1):
+    rng = np.random.default_rng(11)
+    z = rng.uniform(-1, 1, c1.n) / c1.n
+    ct = k1.encrypt(z, 3)
+    steps = int(np.log2(c1.n))
+    r = k1.rotate_sum(ct, 2, steps)
+    assert np.abs(k1.decrypt(r, 2) - z.sum()).max() < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Matrix-vector product: diagonal method and BSGS (Eq. equ:diag, Eq. equ:diagbsgs-grouped,
+# Eq. eq:prerotation), checked against the FP64 matvec and against each other
+# ---------------------------------------------------------------------------
+def _templates(K, ell, seed):
+    rng = np.random.default_rng(seed)
+    T = rng.standard_normal((K, ell))
+    T /= np.linalg.norm(T, axis=1, keepdims=True)
+    return T.astype(np.float32)
+
+
+def test_diag_slots_is_hydia_packing():
+    ell, slots = 8, 32
+    T = _templates(50, ell, 1)
+    for k, d, shift in [(0, 0, 0), (0, 3, 0), (1, 5, 16), (0, 7, 8)]:
+        z = oracle.diag_slots(T, ell, slots, k, d, shift)
+        for x in range(slots):
+            y = (x - shift) % slots
+            b, r = divmod(y, ell)
+            row = (k * (slots // ell) + b) * ell + r
+            ref = T[row, (r + d) % ell] if row < len(T) else 0.0
+            assert z[x] == np.float64(ref)
+
+
+def test_bsgs_and_diagonal_match_plain_matvec(c1, k1):
+    K, ell = 64, 64
+    T = _templates(K, ell, 0xF00D0001)
+    rng = np.random.default_rng(12)
+    q = T[0].astype(np.float64) + 0.1 * rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k1.encrypt(np.tile(q, c1.n // ell), 13)
+    ref = T.astype(np.float64) @ q
+    for n1 in (8, 5, 64):
+        S = k1.bsgs_scores(qct, T, ell, n1)
+        got = k1.decrypt(S[0], 1)
+        assert np.abs(got[:K] - ref).max() < 1e-4
+        assert np.abs(got[K:]).max() < 1e-4        # padding rows score 0
+    D = k1.diag_scores(qct, T, ell)
+    assert np.abs(k1.decrypt(D[0], 1)[:K] - ref).max() < 1e-4
+    # n1 = l is HyDia-DG (no giant steps): the same computation as the naive diagonal method
+    assert np.array_equal(k1.bsgs_scores(qct, T, ell, ell), D)
+
+
+def test_bsgs_special_cases(c1, k1):
+    ell = 32
+    T = _templates(200, ell, 3)
+    # one-hot query picks column c of the templates
+    for col in (0, 5, 31):
+        q = np.zeros(ell)
+        q[col] = 1.0
+        qct = k1.encrypt(np.tile(q, c1.n // ell), 40 + col)
+        got = k1.decrypt(k1.bsgs_scores(qct, T, ell, 4)[0], 1)
+        assert np.abs(got[:200] - T[:, col]).max() < 1e-4
+    # K = l: one square, the textbook diagonal method of Eq. equ:diag
+    Tsq = _templates(ell, ell, 4)
+    q = np.linalg.norm(Tsq[1]) * Tsq[1].astype(np.float64)
+    qct = k1.encrypt(np.tile(q, c1.n // ell), 7)
+    got = k1.decrypt(k1.bsgs_scores(qct, Tsq, ell, 8)[0], 1)
+    assert np.abs(got[:ell] - Tsq.astype(np.float64) @ q).max() < 1e-4
+
+
+def test_multi_group_packing():
+    """K > numSlots: G = ceil(K / numSlots) groups (Fig. 1), score of row t in slot t mod numSlots of group t div numSlots."""
+    c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
+    k = c.keygen(77)
+    ell = 16
+    K = 2 * c.n + 100
+    T = _templates(K, ell, 5)
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k.encrypt(np.tile(q, c.n // ell), 2)
+    S = k.bsgs_scores(qct, T, ell, 4)
+    assert S.shape[0] == 3
+    ref = T.astype(np.float64) @ q
+    got = np.concatenate([k.decrypt(S[g], 1) for g in range(3)])
+    assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev threshold (Eq. eq:cheb-sign, Paterson-Stockmeyer paragraph)
+# ---------------------------------------------------------------------------
+def test_ps_split_printed_values():
+    g = read_golden("paper_counts.txt")
+    assert oracle.ps_split(13) == (int(g["ps_d1_n13"]), int(g["ps_d2_n13"]))
+    assert oracle.ps_split(59) == (2, 6)
+    assert oracle.ps_split(27) == (2, 5)
+    # rule itself: minimal d1 + d2 with d1 * 2^(d2-1) >= n, ties to larger d1
+    for n in range(2, 130):
+        d1, d2 = oracle.ps_split(n)
+        assert d1 * 2 ** (d2 - 1) >= n
+        for a in range(1, n + 2):
+            for b in range(1, 12):
+                if a * 2 ** (b - 1) >= n:
+                    assert a + b > d1 + d2 or (a + b == d1 + d2 and a <= d1)
+
+
+@pytest.mark.parametrize("n", [13, 27, 59])
+def test_chebyshev_coefficients_interpolate_step(n):
+    tau = 0.5
+    cf = oracle.cheb_coeffs(n, tau)
+    theta = np.pi * (np.arange(n + 1) + 0.5) / (n + 1)
+    xj = np.cos(theta)
+    fj = (xj >= tau).astype(np.float64)
+    # interpolation property: p(x_j) = f(x_j) at the n+1 Chebyshev nodes
+    V = np.cos(np.outer(np.arange(n + 1) * 1.0, theta)).T
+    assert np.abs(V @ cf - fj).max() < 1e-12
+    # PS recursion (Chebyshev division) == closed form == Clenshaw on a grid
+    d1, d2 = oracle.ps_split(n)
+    pad = np.zeros(d1 * 2 ** (d2 - 1))
+    pad[: n + 1] = cf
+    xs = np.linspace(-1, 1, 41)
+    closed = np.array([np.sum(cf * np.cos(np.arange(n + 1) * np.arccos(x))) for x in xs])
+    clen = np.polynomial.chebyshev.chebval(xs, cf)
+    ps = np.array([oracle.cheb_ps_eval_fp64(pad, x) for x in xs])
+    assert np.abs(closed - clen).max() < 1e-12 and np.abs(ps - clen).max() < 1e-12
+
+
+def test_chebyshev_decision_margin():
+    """(p(s) >= 0.5) == (s >= 0.5) for |s - 0.5| > 0.02 at degree 59 (reading R12)."""
+    cf = oracle.cheb_coeffs(59, 0.5)
+    xs = np.linspace(-1, 1, 200001)
+    p = np.polynomial.chebyshev.chebval(xs, cf)
+    far = np.abs(xs - 0.5) > 0.02
+    assert np.all((p[far] >= 0.5) == (xs[far] >= 0.5))
+
+
+def test_homomorphic_chebyshev_matches_fp64():
+    c = oracle.Ctx(11, [60] + [40] * 8, [60, 60, 60], 3, 40)
+    k = c.keygen(21)
+    rng = np.random.default_rng(13)
+    z = rng.uniform(-1, 1, c.n)
+    ct = k.encrypt(z, 4)
+    for n in (13, 59):
+        d1, d2 = oracle.ps_split(n)
+        out = k.cheb_eval(ct, c.top, n, 0.5)
+        got = k.decrypt(out, c.top - d2)
+        ref = np.polynomial.chebyshev.chebval(z, oracle.cheb_coeffs(n, 0.5))
+        assert np.abs(got - ref).max() < 1e-3, n
+
+
+# ---------------------------------------------------------------------------
+# Full pipeline, small: identification and membership (Algorithms 5 and 6)
+# ---------------------------------------------------------------------------
+def test_match_modes_small():
+    c = oracle.Ctx(11, [60] + [40] * 8, [60, 60, 60], 3, 40)
+    k = c.keygen(31)
+    ell = 32
+    K = 700
+    T = _templates(K, ell, 7)
+    q = T[3].astype(np.float64)
+    # plant near-duplicates at cosine 0.8
+    rng = np.random.default_rng(14)
+    for idx in (10, 200, 650):
+        u = rng.standard_normal(ell)
+        u -= (u @ q) * q
+        u /= np.linalg.norm(u)
+        T[idx] = (0.8 * q + 0.6 * u).astype(np.float32)
+    qct = k.encrypt(np.tile(q, c.n // ell), 9)
+    s = T.astype(np.float64) @ q
+    cf = oracle.cheb_coeffs(59, 0.5)
+    p = np.polynomial.chebyshev.chebval(np.concatenate([s, np.zeros(c.n - K)]), cf)
+    ident, lvl = k.match(qct, T, ell, 4, oracle.MODE_IDENTIFY, 59, 0.5)
+    assert lvl == c.top - 1 - 6
+    got = k.decrypt(ident[0], lvl)
+    assert np.abs(got - p).max() < 1e-2
+    far = np.abs(s - 0.5) > 0.02
+    assert np.array_equal((got[:K] >= 0.5)[far], (s >= 0.5)[far])
+    memb, lvl2 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5)
+    m = k.decrypt(memb[0], lvl2)
+    assert abs(m[0] - p.sum()) < 1e-2 and np.abs(m - p.sum()).max() < 1e-2
