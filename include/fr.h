@@ -1,0 +1,193 @@
+/*
+ * fr.h -- C ABI of the GB300 encrypted 1:N face-matching library.
+ *
+ * The library computes, on one GPU, the server side of the encrypted
+ * similarity search of "Lightweight, Practical Encrypted Face Recognition with
+ * GPU Support" (arXiv 2604.00546): a CKKS plaintext-template-matrix times
+ * encrypted-query product by BSGS with hoisted baby steps and pre-rotated
+ * diagonals (Section "BSGS with pre-rotated diagonals on GPU", Eq.
+ * eq:prerotation, Algorithms 5 and 6), the Chebyshev threshold of Eq.
+ * eq:cheb-sign (Paterson-Stockmeyer paragraph) and the membership slot sum
+ * (Algorithm 5, aggregation step). The client side (key generation,
+ * encryption, decryption; Fig. "HyDia protocol", Section "HyDia") runs on the
+ * host.
+ *
+ * Conventions
+ *  - Every call returns fr_status. On error the out-pointers are untouched and
+ *    fr_last_error() (thread-local) describes the failure.
+ *  - Inputs are copied; the caller keeps ownership. Outputs are library-owned
+ *    handles released with the matching fr_free_* call.
+ *  - A ciphertext in the exported format is coefficient form, limb-major
+ *    uint64 [2][level+1][N], each word in [0, q_i), component 0 first; it
+ *    decrypts as c0 + c1 * s.
+ *  - Slots: n = N/2 real slots; slot j is the evaluation at zeta^(5^j mod 2N).
+ *    A rotation by k moves slot j+k to slot j (left rotation).
+ *  - Device work runs on the context stream (fr_params.cuda_stream, or a
+ *    stream the context creates). Calls that return device handles enqueue
+ *    work and return; calls that read results (fr_ct_export, fr_decrypt,
+ *    fr_sync) wait for the stream.
+ *  - There is no CPU fallback: without a usable CUDA device fr_setup fails
+ *    with FR_ERR_CUDA.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fr_ctx fr_ctx;
+typedef struct fr_keys fr_keys;
+typedef struct fr_db fr_db;
+typedef struct fr_ct fr_ct;
+
+typedef enum {
+    FR_OK = 0,
+    FR_ERR_INVALID_ARG = 1,
+    FR_ERR_HBM_BUDGET = 2,   /* resident + working set would exceed fr_params.hbm_budget_bytes */
+    FR_ERR_CUDA = 3,         /* CUDA runtime error (no device, launch failure, out of memory) */
+    FR_ERR_TIMEOUT = 4,      /* a bounded wait ran out */
+    FR_ERR_LEVEL = 5,        /* ciphertext level too low / mismatched for the operation */
+    FR_ERR_FORMAT = 6,       /* malformed ciphertext words (a residue >= q_i) */
+    FR_ERR_INTERNAL = 7,
+    FR_ERR_UNSUPPORTED = 8   /* valid but unsupported request (e.g. a Chebyshev degree with d1 != 2) */
+} fr_status;
+
+typedef enum {
+    FR_MODE_SCORES = 0,      /* G ciphertexts of encrypted cosine scores (level L-1) */
+    FR_MODE_IDENTIFY = 1,    /* G ciphertexts of p(score), p = Chebyshev step (Algorithm 6) */
+    FR_MODE_MEMBERSHIP = 2   /* 1 ciphertext: sum over all slots of p(score) (Algorithm 5) */
+} fr_mode;
+
+/* Rotation-index sets for fr_rotation_set (paper: client-side key counts,
+ * Section "Complexity analysis and memory consumption"; GPU complexity table). */
+typedef enum {
+    FR_KEYS_ONDEMAND = 0,    /* this library: baby {1..n1-1}, giant {j n1}, + powers of two if membership */
+    FR_KEYS_CPU_BSGS = 1,    /* BSGS-Diagonal on CPU: baby + giant */
+    FR_KEYS_HYDIA_DG = 2,    /* HyDia diagonal method: 1..ell-1 and EvalSum powers of two */
+    FR_KEYS_TBS_ONLINE = 3,  /* server pre-rotation, keys resident online: giant + powers of two */
+    FR_KEYS_TBS_TOTAL = 4,   /* server pre-rotation, all client keys: baby + giant + negative giant + powers */
+    FR_KEYS_TBE_TOTAL = 5    /* enroller pre-rotation: baby + giant + powers */
+} fr_keyset;
+
+typedef struct {
+    uint32_t log_n;            /* ring degree N = 2^log_n, 10 <= log_n <= 16 */
+    uint32_t n_q;              /* number of ciphertext primes (top level L = n_q - 1) */
+    const uint32_t* q_bits;    /* bit size of each Q prime, q_0 first (primes = 1 mod 2N, largest first) */
+    uint32_t n_p;              /* number of special primes P */
+    const uint32_t* p_bits;
+    uint32_t dnum;             /* key-switching digits (capped at n_q); remainder limbs go to the last digits */
+    uint32_t scale_bits;       /* Delta = 2^scale_bits */
+    uint32_t ell;              /* template dimension (divides N/2) */
+    uint32_t n1;               /* BSGS baby steps; n2 = ceil(ell / n1) */
+    uint32_t schedule;         /* 0: on-demand BSGS with pre-rotated diagonals (only schedule implemented) */
+    uint32_t cheb_degree;      /* Chebyshev degree n of the threshold (PS split must give d1 = 2) */
+    double threshold;          /* tau in step(x - tau) */
+    uint64_t hbm_budget_bytes; /* 0: no budget beyond the device */
+    int device;                /* CUDA device ordinal */
+    void* cuda_stream;         /* optional cudaStream_t to run on (not owned); NULL: the context creates one */
+} fr_params;
+
+/* Set up primes, NTT / base-conversion tables and device state.
+ * Errors: FR_ERR_INVALID_ARG (parameters), FR_ERR_CUDA (no device). */
+fr_status fr_setup(const fr_params* params, fr_ctx** out);
+
+/* Rotation indices this context needs for `mode` (sorted ascending). Writes at most
+ * `cap` entries to `out` and the full count to *n. */
+fr_status fr_required_rotations(const fr_ctx* ctx, fr_mode mode, int32_t* out, size_t cap, size_t* n);
+
+/* Rotation-index set of one of the compared schemes (pure host function, no context). */
+fr_status fr_rotation_set(uint32_t ell, uint32_t n1, uint32_t slots, fr_keyset which, int membership, int32_t* out,
+                          size_t cap, size_t* n);
+
+/* Number of ciphertext rotations a query performs (Section "Complexity analysis of our
+ * BSGS-Diagonal"): schedule 0 (grouped, on demand): (n1-1) + G (n2-1); schedule 1
+ * (full table, Algorithm 1): ell - 1 (reading: only the ell-1 nontrivial rotations count). */
+uint64_t fr_rotation_count(uint32_t ell, uint32_t n1, uint64_t groups, uint32_t schedule);
+
+/* Client-side key generation from a seed (ChaCha20 streams): secret key, public key,
+ * relinearisation key and one hybrid key-switching key per rotation index. The secret
+ * stays in host memory. */
+fr_status fr_keygen(fr_ctx* ctx, const int32_t* rotations, size_t n_rot, uint64_t seed, fr_keys** out);
+
+/* Upload the evaluation keys of `keys` to HBM (resident until fr_free). */
+fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
+
+/* Load a plaintext template database: row-major K x ell float32 (host pointer),
+ * L2-normalised by the caller. Templates are packed per Section "Diagonal method
+ * for rectangular matrices" (G = ceil(K / (N/2)) groups) and every pre-rotated
+ * diagonal (Eq. eq:prerotation) is encoded on the device and kept in HBM. */
+fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
+
+/* Client-side encryption of one query q (ell values) replicated across the N/2 slots
+ * (numSlots/ell copies, Section "Packed matrices and batched multiplications"). */
+fr_status fr_encrypt(const fr_ctx* ctx, const fr_keys* keys, const double* q, size_t ell, uint64_t seed,
+                     fr_ct** out);
+
+/* Encrypt an arbitrary slot vector (n = N/2 values) at the top level. */
+fr_status fr_encrypt_slots(const fr_ctx* ctx, const fr_keys* keys, const double* z, size_t n, uint64_t seed,
+                           fr_ct** out);
+
+/* Encrypted 1:N match of one query (Algorithms 5 and 6). The query must be at the top
+ * level; host-resident queries are uploaded (one H2D copy). Returns *n_out library-owned
+ * device ciphertexts in *out (array freed with fr_free_cts). */
+fr_status fr_match(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out);
+
+/* Client-side decryption + decoding of up to n_slots slot values (divided by the nominal scale). */
+fr_status fr_decrypt(const fr_ctx* ctx, const fr_keys* keys, const fr_ct* ct, double* slots, size_t n_slots);
+
+/* Export / import ciphertext words (format above). `words` must be >= 2 (level+1) N. */
+fr_status fr_ct_export(const fr_ct* ct, uint64_t* buf, size_t words, uint32_t* level, double* scale);
+fr_status fr_ct_import(const fr_ctx* ctx, const uint64_t* buf, uint32_t level, double scale, fr_ct** out);
+fr_status fr_ct_info(const fr_ct* ct, uint32_t* level, int* on_device);
+/* Move a host ciphertext into HBM (NTT form); no-op if already there. */
+fr_status fr_ct_upload(fr_ctx* ctx, fr_ct* ct);
+
+/* Homomorphic primitives on device ciphertexts (paper: GPU primitives mult, add,
+ * rotate, rescale; Section "GPU-accelerated encrypted search"). Outputs are new handles. */
+fr_status fr_rotate(fr_ctx* ctx, const fr_ct* ct, int32_t k, fr_ct** out);
+/* hoisted rotations of one ciphertext by ks[0..n) (one shared ModUp) */
+fr_status fr_rotate_hoisted(fr_ctx* ctx, const fr_ct* ct, const int32_t* ks, size_t n, fr_ct** out);
+fr_status fr_rescale(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
+/* ct x ct product with relinearisation (no rescale); both at the same level */
+fr_status fr_mul_relin(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
+fr_status fr_add(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
+/* Chebyshev threshold p(x) of the context's degree and threshold */
+fr_status fr_chebyshev(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
+/* RotateAndSum over all N/2 slots */
+fr_status fr_rotate_sum(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
+
+/* Wait for all work enqueued on the context stream. */
+fr_status fr_sync(fr_ctx* ctx);
+
+/* Per-region device timing (CUDA events on the context stream). enable=1 starts
+ * accumulating, 0 stops; fr_profile_read returns the summed milliseconds and the
+ * number of timed launches of a region ("ntt", "modup", "ip", "moddown", "rescale",
+ * "tensor", "mac", "encode", "misc"). */
+fr_status fr_profile(fr_ctx* ctx, int enable);
+fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches);
+/* Number of kernel launches issued by the library so far. */
+uint64_t fr_launch_count(const fr_ctx* ctx);
+
+/* Context facts: primes (Q then P), digit boundaries, resident HBM bytes. */
+fr_status fr_ctx_primes(const fr_ctx* ctx, uint64_t* out, size_t cap, size_t* n);
+fr_status fr_ctx_info(const fr_ctx* ctx, uint32_t* n_slots, uint32_t* top_level, uint32_t* n_digits,
+                      uint64_t* resident_bytes);
+
+/* Chebyshev coefficients c_0..c_n of the step interpolant (host, no context). */
+fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out);
+
+void fr_free_ct(fr_ct* ct);
+void fr_free_cts(fr_ct** cts, size_t n);
+void fr_free_keys(fr_keys* keys);
+void fr_free_db(fr_db* db);
+void fr_free(fr_ctx* ctx);
+const char* fr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FR_H */

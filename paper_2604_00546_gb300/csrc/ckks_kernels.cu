@@ -1,0 +1,541 @@
+// CKKS device kernels: base conversion (ModUp / ModDown), key-switch inner
+// product with the slot automorphism fused into its gather, rescale, tensor
+// product, the diagonal plaintext x ciphertext multiply-accumulate, Chebyshev
+// scalar steps and the on-device slot encoder for template diagonals.
+#include <cstdio>
+
+#include "ckks_kernels.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void fold(Acc128& a, u64 q) {
+    if (a.hi >= q) a.hi -= q;
+}
+
+// ---------------------------------------------------------------------------
+// ModUp: per digit, copy the digit's own limbs and fast-convert them to every
+// other position of Q_l u P. Coefficient form in and out.
+// in: [J] jobs, job j at in + j * in_job, limb i at + i * N
+// ext: [J][beta][npos][N]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, long long in_job,
+                                                    u64* __restrict__ ext, const ModUpTab* __restrict__ tabs,
+                                                    int beta, int npos, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    const int j = blockIdx.z;
+    if (k >= N) return;
+    const ModUpTab& T = tabs[d];
+    const u64* x = in + (long long)j * in_job;
+    u64* out = ext + (((long long)j * beta + d) * npos) * N;
+    u64 xs[FR_MAX_DIGIT_LIMBS], ys[FR_MAX_DIGIT_LIMBS];
+    for (int i = 0; i < T.ns; ++i) {
+        xs[i] = x[(long long)(T.lo + i) * N + k];
+        ys[i] = mul_shoup(xs[i], T.inv_hat[i], T.inv_hat_s[i], T.src_q[i]);
+    }
+    for (int pos = 0; pos < npos; ++pos) {
+        u64 v;
+        if (pos >= T.lo && pos < T.lo + T.ns) {
+            v = xs[pos - T.lo];
+        } else {
+            const u64 t = T.tq[pos];
+            v = 0;
+            for (int i = 0; i < T.ns; ++i) v = add_mod(v, mul_shoup(ys[i], T.hat[i][pos], T.hat_s[i][pos], t), t);
+        }
+        out[(long long)pos * N + k] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Key-switch inner product: acc_t[pos] = sum_d sigma_g(ext_d[pos]) * key_d[t][limb(pos)]
+// Keys are stored in Montgomery form, so one REDC of the 128-bit sum gives
+// the canonical residue. The automorphism is a gather on the ext index.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, int npos, int level, int nq, int T,
+                                                 const DevPrime* __restrict__ primes, const PrimeMap pos_prime,
+                                                 int logN) {
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y;
+    const IPJob& J = jobs.j[blockIdx.z];
+    if (k >= N) return;
+    const int pi = pos_prime.idx[pos];
+    const u64 q = primes[pi].q, qinv = primes[pi].qinv;
+    const int klimb = pos <= level ? pos : nq + (pos - (level + 1));
+    const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
+    Acc128 a0{0, 0}, a1{0, 0};
+    for (int d = 0; d < beta; ++d) {
+        const u64 e = J.ext[((long long)d * npos + pos) * N + src];
+        const u64 k0 = J.key[(((long long)d * 2 + 0) * T + klimb) * N + k];
+        const u64 k1 = J.key[(((long long)d * 2 + 1) * T + klimb) * N + k];
+        mac128(a0, e, k0);
+        mac128(a1, e, k1);
+        if ((d & 7) == 7) { fold(a0, q); fold(a1, q); }
+    }
+    fold(a0, q);
+    fold(a1, q);
+    J.out[(long long)pos * N + k] = redc(a0.hi, a0.lo, q, qinv);
+    J.out[((long long)npos + pos) * N + k] = redc(a1.hi, a1.lo, q, qinv);
+}
+
+// ---------------------------------------------------------------------------
+// ModDown base conversion P -> Q_l of the (coefficient-form) P limbs of acc.
+// acc: job j at acc + j * acc_job, poly t at + t * npos * N, P limb jj at position level+1+jj
+// conv: [J][2][level+1][N]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_p2q(const u64* __restrict__ acc, long long acc_job, int npos,
+                                                  int level, u64* __restrict__ conv, const P2QTab* __restrict__ tab,
+                                                  int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    const int j = blockIdx.z;
+    if (k >= N) return;
+    const u64* x = acc + (long long)j * acc_job + (long long)t * npos * N;
+    u64 ys[FR_MAX_DIGIT_LIMBS];
+    for (int i = 0; i < tab->np; ++i) {
+        u64 xv = x[(long long)(level + 1 + i) * N + k];
+        ys[i] = mul_shoup(xv, tab->inv_hat[i], tab->inv_hat_s[i], tab->pq[i]);
+    }
+    u64* o = conv + ((long long)j * 2 + t) * (level + 1) * N;
+    for (int i = 0; i <= level; ++i) {
+        const u64 q = tab->qq[i];
+        u64 v = 0;
+        for (int jj = 0; jj < tab->np; ++jj) v = add_mod(v, mul_shoup(ys[jj], tab->hat[jj][i], tab->hat_s[jj][i], q), q);
+        o[(long long)i * N + k] = v;
+    }
+}
+
+// out[t][i] = (acc[t][i] - conv[t][i]) * P^-1 + addend   (evaluation form)
+// addend modes: 0 none, 1 rotation (t=0 gets sigma_g(add c0)), 2 plain ct add (both polys)
+__global__ void __launch_bounds__(kThreads) k_moddown_combine(const MDJobs jobs, int npos, int level,
+                                                              const u64* __restrict__ pinv,
+                                                              const u64* __restrict__ pinv_s,
+                                                              const DevPrime* __restrict__ primes, int logN) {
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % (level + 1);
+    const int t = blockIdx.y / (level + 1);
+    const MDJob& J = jobs.j[blockIdx.z];
+    if (k >= N) return;
+    const u64 q = primes[i].q;
+    const u64 a = J.acc[((long long)t * npos + i) * N + k];
+    const u64 c = J.conv[((long long)t * (level + 1) + i) * N + k];
+    u64 v = mul_shoup(sub_mod(a, c, q), pinv[i], pinv_s[i], q);
+    if (J.mode == 1) {
+        if (t == 0) {
+            const u32 src = galois_src_index((u32)k, J.galois, logN);
+            v = add_mod(v, J.add[(long long)i * N + src], q);
+        }
+    } else if (J.mode == 2) {
+        v = add_mod(v, J.add[((long long)t * J.add_cap + i) * N + k], q);
+    }
+    J.out[((long long)t * J.out_cap + i) * N + k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Rescale. lift: centered last limb (coefficient form) to each q_i, i < l.
+// last: [B][2][N] ; lifted: [B][2][l][N]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_rescale_lift(const u64* __restrict__ last, u64* __restrict__ lifted,
+                                                           const RescaleTab* __restrict__ tab, int l, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bt = blockIdx.y;
+    if (k >= N) return;
+    const u64 x = last[(long long)bt * N + k];
+    const bool neg = x > tab->half;
+    u64* o = lifted + (long long)bt * l * N;
+    for (int i = 0; i < l; ++i) {
+        const u64 q = tab->q[i];
+        u64 r = x % q;  // x < 2^61, one reduction per coefficient and limb
+        if (neg) r = sub_mod(r, tab->ql_mod[i], q);
+        o[(long long)i * N + k] = r;
+    }
+}
+
+// out[b][t][i] = (x[b][t][i] - lifted[b][t][i]) * q_l^-1
+__global__ void __launch_bounds__(kThreads) k_rescale_combine(const u64* __restrict__ x, int x_cap,
+                                                              const u64* __restrict__ lifted, u64* __restrict__ out,
+                                                              int out_cap, const RescaleTab* __restrict__ tab, int l,
+                                                              int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % l;
+    const int bt = blockIdx.y / l;
+    if (k >= N) return;
+    const u64 q = tab->q[i];
+    const u64 a = x[((long long)bt * x_cap + i) * N + k];
+    const u64 c = lifted[((long long)bt * l + i) * N + k];
+    out[((long long)bt * out_cap + i) * N + k] = mul_shoup(sub_mod(a, c, q), tab->qlinv[i], tab->qlinv_s[i], q);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor product of ciphertext pairs (evaluation form):
+// d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1.  out: [B][3][level+1][N]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int level,
+                                                     const DevPrime* __restrict__ primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    const TensorJob& J = jobs.j[blockIdx.z];
+    if (k >= N) return;
+    const DevPrime P = primes[i];
+    const u64 a0 = J.a[(long long)i * N + k], a1 = J.a[((long long)J.a_cap + i) * N + k];
+    const u64 b0 = J.b[(long long)i * N + k], b1 = J.b[((long long)J.b_cap + i) * N + k];
+    const long long ps = (long long)(level + 1) * N;
+    J.out[(long long)i * N + k] = mul_mod(a0, b0, P);
+    J.out[ps + (long long)i * N + k] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+    J.out[2 * ps + (long long)i * N + k] = mul_mod(a1, b1, P);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal MAC (on-demand BSGS, Eq. eq:prerotation): for every giant step j
+//   P_j[t][i][k] = sum_{b < n1, j n1 + b < ell} baby_b[t][i][k] * D'_{j n1 + b}[i][k]
+// One thread per evaluation point; its n1 baby values (both polys) are staged
+// in shared memory once and reused by all n2 giant steps, so the babies are
+// read once and every plaintext diagonal word exactly once.
+// ---------------------------------------------------------------------------
+template <int TP>
+__global__ void __launch_bounds__(TP) k_mac(const u64* __restrict__ babies, int cap_b, const u64* __restrict__ diags,
+                                            u64* __restrict__ out, int cap_o, int nl, int n1, int n2, int ell,
+                                            const DevPrime* __restrict__ primes, int N) {
+    extern __shared__ u64 sb[];  // [n1][2][TP]
+    const int k = blockIdx.x * TP + threadIdx.x;
+    const int i = blockIdx.y;
+    const u64 q = primes[i].q, qinv = primes[i].qinv;
+    for (int b = 0; b < n1; ++b) {
+        const u64* B = babies + (long long)b * 2 * cap_b * N;
+        sb[(b * 2 + 0) * TP + threadIdx.x] = B[(long long)i * N + k];
+        sb[(b * 2 + 1) * TP + threadIdx.x] = B[((long long)cap_b + i) * N + k];
+    }
+    const long long dstride = (long long)nl * N;
+    for (int j = 0; j < n2; ++j) {
+        const int cnt = min(n1, ell - j * n1);
+        Acc128 a0{0, 0}, a1{0, 0};
+        const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
+#pragma unroll 8
+        for (int b = 0; b < cnt; ++b) {
+            const u64 d = __ldcs(D + (long long)b * dstride);
+            mac128(a0, sb[(b * 2 + 0) * TP + threadIdx.x], d);
+            mac128(a1, sb[(b * 2 + 1) * TP + threadIdx.x], d);
+            if ((b & 7) == 7) { fold(a0, q); fold(a1, q); }
+        }
+        fold(a0, q);
+        fold(a1, q);
+        u64* O = out + (long long)j * 2 * cap_o * N;
+        O[(long long)i * N + k] = redc(a0.hi, a0.lo, q, qinv);
+        O[((long long)cap_o + i) * N + k] = redc(a1.hi, a1.lo, q, qinv);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers on ciphertext batches [B][2][cap][N] (evaluation form).
+// ---------------------------------------------------------------------------
+// out = a + b over limbs 0..level of both polys
+__global__ void k_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
+                      int o_cap, long long o_bs, int level, const DevPrime* primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % (level + 1);
+    const int t = blockIdx.y / (level + 1);
+    const int bb = blockIdx.z;
+    if (k >= N) return;
+    const u64 q = primes[i].q;
+    const u64 x = a[bb * a_bs + ((long long)t * a_cap + i) * N + k];
+    const u64 y = b[bb * b_bs + ((long long)t * b_cap + i) * N + k];
+    out[bb * o_bs + ((long long)t * o_cap + i) * N + k] = add_mod(x, y, q);
+}
+
+// sum of J ciphertexts (stride js) into out
+__global__ void k_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level,
+                      const DevPrime* primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % (level + 1);
+    const int t = blockIdx.y / (level + 1);
+    if (k >= N) return;
+    const u64 q = primes[i].q;
+    u64 v = 0;
+    for (int j = 0; j < J; ++j) v = add_mod(v, a[j * js + ((long long)t * cap + i) * N + k], q);
+    out[((long long)t * o_cap + i) * N + k] = v;
+}
+
+// Chebyshev leaves: out[leaf] = x * cb[leaf] + (c0 += ca[leaf])   (before rescale)
+__global__ void k_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, const u64* cb,
+                              const u64* cb_s, const u64* ca, const DevPrime* primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % (level + 1);
+    const int t = blockIdx.y / (level + 1);
+    const int leaf = blockIdx.z;
+    if (k >= N) return;
+    const u64 q = primes[i].q;
+    const int L1 = level + 1;
+    u64 v = mul_shoup(x[((long long)t * x_cap + i) * N + k], cb[leaf * L1 + i], cb_s[leaf * L1 + i], q);
+    if (t == 0) v = add_mod(v, ca[leaf * L1 + i], q);
+    out[(long long)leaf * 2 * o_cap * N + ((long long)t * o_cap + i) * N + k] = v;
+}
+
+// x <- 2 x - c (c added to the constant term: every evaluation point of c0)
+__global__ void k_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y % (level + 1);
+    const int t = blockIdx.y / (level + 1);
+    if (k >= N) return;
+    const u64 q = primes[i].q;
+    u64* p = x + ((long long)t * cap + i) * N + k;
+    u64 v = add_mod(*p, *p, q);
+    if (t == 0) v = sub_mod(v, cres[i], q);
+    *p = v;
+}
+
+__global__ void k_to_mont(u64* x, long long n_per_poly, PrimeMap pm, const DevPrime* primes, long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / n_per_poly);
+        const DevPrime P = primes[pm.idx[p % pm.period]];
+        x[e] = to_mont(x[e], P);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device slot encoder for template diagonals (reading R5, same operations and
+// order as the host encoder: inverse special FFT stages len = n..2, bit
+// reversal, times 1/n and Delta, rounded half away from zero).
+// Stage arithmetic uses explicitly rounded intrinsics (no contraction).
+// ---------------------------------------------------------------------------
+struct cplx {
+    double r, i;
+};
+
+__device__ __forceinline__ void fft_inv_bfly(cplx& a, cplx& b, double wr, double wi) {
+    const double sr = __dadd_rn(a.r, b.r), si = __dadd_rn(a.i, b.i);
+    const double dr = __dsub_rn(a.r, b.r), di = __dsub_rn(a.i, b.i);
+    a.r = sr;
+    a.i = si;
+    b.r = __dsub_rn(__dmul_rn(dr, wr), __dmul_rn(di, wi));
+    b.i = __dadd_rn(__dmul_rn(dr, wi), __dmul_rn(di, wr));
+}
+
+// Gather of the pre-rotated diagonals into slot vectors:
+// z[x] = diag_d(M_k)[(x - shift) mod n], diag_d(M_k)[b ell + r] = T[(k B + b) ell + r][(r + d) mod ell]
+__global__ void k_diag_gather(const float* __restrict__ T, long long K, int ell, int n, long long grp, int d0, int nd,
+                              int n1, cplx* __restrict__ z) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int di = blockIdx.y;
+    if (x >= n || di >= nd) return;
+    const int d = d0 + di;
+    const long long shift = (long long)(d / n1) * n1;
+    long long y = ((long long)x - shift) % n;
+    if (y < 0) y += n;
+    const long long B = n / ell;
+    const long long b = y / ell, r = y % ell;
+    const long long row = (grp * B + b) * ell + r;
+    const double v = row < K ? (double)T[row * ell + (r + d) % ell] : 0.0;
+    z[(long long)di * n + x] = cplx{v, 0.0};
+}
+
+// first log2(R) stages (len = n .. 2n/R): columns of stride n/R; one tile of 16 columns
+__global__ void __launch_bounds__(256) k_fft_col(cplx* z, int logn, int logR, const unsigned* rot, const double* zr,
+                                                 const double* zi) {
+    extern __shared__ cplx sc[];
+    const int n = 1 << logn, Rr = 1 << logR, C = n >> logR;
+    const int TC = 16;
+    const long long M = 4ll * n;
+    cplx* x = z + (long long)blockIdx.y * n;
+    const int col0 = blockIdx.x * TC;
+    for (int e = threadIdx.x; e < Rr * TC; e += blockDim.x) {
+        int r = e / TC, c = e % TC;
+        sc[e] = x[(long long)r * C + col0 + c];
+    }
+    __syncthreads();
+    for (int len = n; len >= 2 * C; len >>= 1) {
+        const int hrow = (len >> 1) / C;  // half block in rows
+        const long long lq = (long long)len << 2, gap = M / lq;
+        for (int bf = threadIdx.x; bf < (Rr >> 1) * TC; bf += blockDim.x) {
+            int c = bf % TC, pr = bf / TC;
+            int blk = pr / hrow, u = pr - blk * hrow;
+            int ra = blk * 2 * hrow + u, rb = ra + hrow;
+            const int j = (col0 + c) + u * C;  // position inside the len-block
+            const long long idx = (lq - (long long)(rot[j] % lq)) * gap;
+            fft_inv_bfly(sc[ra * TC + c], sc[rb * TC + c], zr[idx], zi[idx]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < Rr * TC; e += blockDim.x) {
+        int r = e / TC, c = e % TC;
+        x[(long long)r * C + col0 + c] = sc[e];
+    }
+}
+
+// remaining stages (len = C .. 2) inside contiguous blocks of C
+__global__ void __launch_bounds__(256) k_fft_row(cplx* z, int logn, int logR, int bpc, const unsigned* rot,
+                                                 const double* zr, const double* zi) {
+    extern __shared__ cplx sc[];
+    const int n = 1 << logn, C = n >> logR;
+    const long long M = 4ll * n;
+    cplx* x = z + (long long)blockIdx.y * n + (long long)blockIdx.x * bpc * C;
+    const int tile = bpc * C;
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) sc[e] = x[e];
+    __syncthreads();
+    for (int len = C; len >= 2; len >>= 1) {
+        const int h = len >> 1;
+        const long long lq = (long long)len << 2, gap = M / lq;
+        for (int bf = threadIdx.x; bf < tile / 2; bf += blockDim.x) {
+            int blk = bf / h, u = bf - blk * h;
+            int a = blk * len + u, b = a + h;
+            const long long idx = (lq - (long long)(rot[u] % lq)) * gap;
+            fft_inv_bfly(sc[a], sc[b], zr[idx], zi[idx]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) x[e] = sc[e];
+}
+
+// bit reversal, scaling, rounding and residues: out [nd][nl][N] (coefficient form)
+__global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* __restrict__ out, int nl,
+                             const DevPrime* __restrict__ primes, int scale_bits) {
+    const int n = 1 << logn;
+    const int N = 2 * n;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int di = blockIdx.y;
+    if (c >= N || di >= nd) return;
+    const int cc = c < n ? c : c - n;
+    const int src = __brev(cc) >> (32 - logn);
+    const cplx w = z[(long long)di * n + src];
+    const double v = c < n ? w.r : w.i;
+    const double inv_n = 1.0 / (double)n;
+    const double delta = ldexp(1.0, scale_bits);
+    const long long m = llround(__dmul_rn(__dmul_rn(v, inv_n), delta));
+    u64* o = out + (long long)di * nl * N;
+    for (int i = 0; i < nl; ++i) {
+        const u64 q = primes[i].q;
+        u64 r;
+        if (m >= 0) {
+            r = (u64)m % q;
+        } else {
+            u64 a = (u64)(-(m + 1)) % q;
+            r = q - 1 - a;
+        }
+        o[(long long)i * N + c] = r;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+static inline dim3 g1(int N) { return dim3((N + kThreads - 1) / kThreads); }
+
+void launch_modup(const u64* in, long long in_job, u64* ext, const ModUpTab* tabs, int beta, int npos, int N, int J,
+                  cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, beta, J);
+    k_modup<<<g, kThreads, 0, s>>>(in, in_job, ext, tabs, beta, npos, N);
+}
+
+void launch_ip(const IPJobs& jobs, int J, int beta, int npos, int level, int nq, int T, const DevPrime* primes,
+               const PrimeMap& pos_prime, int logN, cudaStream_t s) {
+    const int N = 1 << logN;
+    dim3 g((N + kThreads - 1) / kThreads, npos, J);
+    k_ip<<<g, kThreads, 0, s>>>(jobs, beta, npos, level, nq, T, primes, pos_prime, logN);
+}
+
+void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
+                cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2, J);
+    k_p2q<<<g, kThreads, 0, s>>>(acc, acc_job, npos, level, conv, tab, N);
+}
+
+void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,
+                            const DevPrime* primes, int logN, cudaStream_t s) {
+    const int N = 1 << logN;
+    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), J);
+    k_moddown_combine<<<g, kThreads, 0, s>>>(jobs, npos, level, pinv, pinv_s, primes, logN);
+}
+
+void launch_rescale_lift(const u64* last, u64* lifted, const RescaleTab* tab, int l, int N, int BT, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, BT);
+    k_rescale_lift<<<g, kThreads, 0, s>>>(last, lifted, tab, l, N);
+}
+
+void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out, int out_cap, const RescaleTab* tab,
+                            int l, int N, int BT, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, BT * l);
+    k_rescale_combine<<<g, kThreads, 0, s>>>(x, x_cap, lifted, out, out_cap, tab, l, N);
+}
+
+void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, level + 1, J);
+    k_tensor<<<g, kThreads, 0, s>>>(jobs, level, primes, N);
+}
+
+void launch_mac(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
+                const DevPrime* primes, int N, cudaStream_t s) {
+    constexpr int TP = 128;
+    const size_t sm = (size_t)n1 * 2 * TP * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mac<TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 g(N / TP, nl);
+    k_mac<TP><<<g, TP, sm, s>>>(babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, primes, N);
+}
+
+void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,
+                long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), B);
+    k_add<<<g, kThreads, 0, s>>>(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, primes, N);
+}
+
+void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,
+                int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1));
+    k_sum<<<g, kThreads, 0, s>>>(a, cap, js, J, out, o_cap, level, primes, N);
+}
+
+void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
+                        const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), nleaves);
+    k_cheb_leaves<<<g, kThreads, 0, s>>>(x, x_cap, out, o_cap, level, cb, cb_s, ca, primes, N);
+}
+
+void launch_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1));
+    k_double_sub<<<g, kThreads, 0, s>>>(x, cap, level, cres, primes, N);
+}
+
+void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,
+                    cudaStream_t s) {
+    long long blocks = (total + kThreads - 1) / kThreads;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_to_mont<<<(unsigned)blocks, kThreads, 0, s>>>(x, n_per_poly, pm, primes, total);
+}
+
+void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                         void* zbuf, u64* out_coeff, int nl, const DevPrime* primes, int scale_bits,
+                         const unsigned* rot, const double* zr, const double* zi, cudaStream_t s) {
+    const int n = 1 << logn;
+    cplx* z = (cplx*)zbuf;
+    {
+        dim3 g((n + kThreads - 1) / kThreads, nd);
+        k_diag_gather<<<g, kThreads, 0, s>>>(T, K, ell, n, grp, d0, nd, n1, z);
+    }
+    const int logR = logn / 2;
+    const int Rr = 1 << logR, C = n >> logR;
+    {
+        dim3 g(C / 16, nd);
+        const size_t sm = (size_t)Rr * 16 * sizeof(cplx);
+        k_fft_col<<<g, 256, sm, s>>>(z, logn, logR, rot, zr, zi);
+    }
+    {
+        int bpc = 1024 / C;
+        if (bpc < 1) bpc = 1;
+        if (bpc > Rr) bpc = Rr;
+        dim3 g(Rr / bpc, nd);
+        const size_t sm = (size_t)bpc * C * sizeof(cplx);
+        k_fft_row<<<g, 256, sm, s>>>(z, logn, logR, bpc, rot, zr, zi);
+    }
+    {
+        dim3 g((2 * n + kThreads - 1) / kThreads, nd);
+        k_fft_finish<<<g, kThreads, 0, s>>>(z, logn, nd, out_coeff, nl, primes, scale_bits);
+    }
+}

@@ -1,0 +1,93 @@
+// Tables and launchers of the CKKS device kernels.
+#pragma once
+#include "kernels.h"
+
+#define FR_MAX_DIGIT_LIMBS 16
+
+// ModUp constants of one digit at one level: sources are the digit's Q limbs
+// [lo, lo + ns); targets are every position of Q_l u P.
+struct ModUpTab {
+    int ns, lo;
+    u64 src_q[FR_MAX_DIGIT_LIMBS];
+    u64 inv_hat[FR_MAX_DIGIT_LIMBS], inv_hat_s[FR_MAX_DIGIT_LIMBS];
+    u64 tq[FR_MAX_PRIMES];
+    u64 hat[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+    u64 hat_s[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+};
+
+// ModDown constants: sources are the P limbs, targets Q limbs 0..l
+struct P2QTab {
+    int np;
+    u64 pq[FR_MAX_DIGIT_LIMBS];
+    u64 inv_hat[FR_MAX_DIGIT_LIMBS], inv_hat_s[FR_MAX_DIGIT_LIMBS];
+    u64 qq[FR_MAX_PRIMES];
+    u64 hat[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+    u64 hat_s[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+};
+
+// Rescale constants at level l (divide by q_l)
+struct RescaleTab {
+    u64 half;  // (q_l - 1) / 2
+    u64 q[FR_MAX_PRIMES];
+    u64 ql_mod[FR_MAX_PRIMES];
+    u64 qlinv[FR_MAX_PRIMES], qlinv_s[FR_MAX_PRIMES];
+};
+
+struct IPJob {
+    const u64* ext;  // [beta][npos][N]
+    const u64* key;  // [ndig][2][T][N], Montgomery form
+    u64* out;        // [2][npos][N]
+    u32 galois;      // 1: no automorphism
+    u32 pad;
+};
+
+struct MDJob {
+    const u64* acc;   // [2][npos][N]
+    const u64* conv;  // [2][level+1][N]
+    const u64* add;   // mode 1: c0 limbs (stride N); mode 2: ct with add_cap
+    u64* out;         // ct with out_cap
+    int out_cap;
+    int add_cap;
+    int mode;         // 0 none, 1 rotation addend sigma_g(c0), 2 ct addend
+    u32 galois;
+};
+
+struct TensorJob {
+    const u64* a;
+    const u64* b;
+    u64* out;  // [3][level+1][N]
+    int a_cap, b_cap;
+};
+
+// job lists travel as kernel parameters (no descriptor copies, capturable in graphs)
+#define FR_MAX_JOBS 64
+struct IPJobs { IPJob j[FR_MAX_JOBS]; };
+struct MDJobs { MDJob j[FR_MAX_JOBS]; };
+struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
+
+void launch_modup(const u64* in, long long in_job, u64* ext, const ModUpTab* tabs, int beta, int npos, int N, int J,
+                  cudaStream_t s);
+void launch_ip(const IPJobs& jobs, int J, int beta, int npos, int level, int nq, int T, const DevPrime* primes,
+               const PrimeMap& pos_prime, int logN, cudaStream_t s);
+void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
+                cudaStream_t s);
+void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,
+                            const DevPrime* primes, int logN, cudaStream_t s);
+void launch_rescale_lift(const u64* last, u64* lifted, const RescaleTab* tab, int l, int N, int BT, cudaStream_t s);
+void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out, int out_cap, const RescaleTab* tab,
+                            int l, int N, int BT, cudaStream_t s);
+void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s);
+void launch_mac(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
+                const DevPrime* primes, int N, cudaStream_t s);
+void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,
+                long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s);
+void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,
+                int N, cudaStream_t s);
+void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
+                        const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s);
+void launch_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N, cudaStream_t s);
+void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,
+                    cudaStream_t s);
+void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                         void* zbuf, u64* out_coeff, int nl, const DevPrime* primes, int scale_bits,
+                         const unsigned* rot, const double* zr, const double* zi, cudaStream_t s);

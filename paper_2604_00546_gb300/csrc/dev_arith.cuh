@@ -1,0 +1,71 @@
+// Device-side 64-bit RNS arithmetic for sm_103a.
+//
+// Residues are kept canonical ([0, q)) between kernels. Products by constants
+// use Shoup's precomputed quotient (w' = floor(w * 2^64 / q)); products of two
+// variable residues and multiply-accumulate chains use Montgomery reduction
+// with R = 2^64 (one operand stored pre-multiplied by R, or a second
+// reduction by R^2 mod q). All primes are below 2^61, which the lazy
+// accumulation bounds below rely on.
+#pragma once
+#include <cstdint>
+
+typedef uint64_t u64;
+typedef unsigned int u32;
+
+struct DevPrime {
+    u64 q;       // modulus
+    u64 qinv;    // q^-1 mod 2^64 (Montgomery)
+    u64 r2;      // 2^128 mod q
+    u64 ninv;    // N^-1 mod q
+    u64 ninv_s;  // Shoup quotient of ninv
+};
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// x * w mod q for a constant w with Shoup quotient ws; any 64-bit x.
+__device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 ws, u64 q) {
+    u64 hi = __umul64hi(x, ws);
+    u64 r = x * w - hi * q;
+    return r >= q ? r - q : r;
+}
+
+// Montgomery reduction of T = hi * 2^64 + lo with hi < q: returns T * 2^-64 mod q in [0, q).
+__device__ __forceinline__ u64 redc(u64 hi, u64 lo, u64 q, u64 qinv) {
+    u64 m = lo * qinv;
+    u64 t = __umul64hi(m, q);
+    return hi >= t ? hi - t : hi - t + q;
+}
+
+struct Acc128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128& a, u64 x, u64 y) {
+    u64 l = x * y;
+    u64 h = __umul64hi(x, y);
+    a.lo += l;
+    a.hi += h + (a.lo < l ? 1ull : 0ull);
+}
+
+// a * b mod q for two variable residues: REDC(REDC(a b) * R^2)
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const DevPrime& P) {
+    u64 t = redc(__umul64hi(a, b), a * b, P.q, P.qinv);
+    return redc(__umul64hi(t, P.r2), t * P.r2, P.q, P.qinv);
+}
+
+// x * R mod q (Montgomery form)
+__device__ __forceinline__ u64 to_mont(u64 x, const DevPrime& P) {
+    return redc(__umul64hi(x, P.r2), x * P.r2, P.q, P.qinv);
+}
+
+// Automorphism sigma_g in evaluation form: position k holds the value at
+// psi^(2 brev(k) + 1); sigma_g(a) at that point is a at psi^((2 brev(k)+1) g).
+__device__ __forceinline__ u32 galois_src_index(u32 k, u32 g, int logN) {
+    u32 e = 2u * (__brev(k) >> (32 - logN)) + 1u;
+    u32 M = 2u << logN;
+    u32 e2 = (u32)(((u64)e * g) & (M - 1));
+    return __brev((e2 - 1u) >> 1) >> (32 - logN);
+}

@@ -1,0 +1,1341 @@
+// Engine: device-resident CKKS state, batched homomorphic operations and the
+// encrypted 1:N matcher behind the C ABI declared in include/fr.h.
+//
+// Data layout in HBM
+//   ciphertext batch : [B][2][cap][N] u64, evaluation (NTT) form, limbs 0..level
+//                      valid (cap >= level+1, dropping a level keeps the buffer)
+//   key-switching key: [ndig][2][nq+np][N] u64, Montgomery form (x * 2^64 mod q)
+//   template database: [G][ell][nq][N] u64, pre-rotated diagonals (Eq.
+//                      eq:prerotation), evaluation + Montgomery form
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/fr.h"
+#include "ckks_kernels.h"
+#include "fr_host.h"
+
+using frh::u128;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct FrError {
+    fr_status s;
+    std::string msg;
+};
+
+[[noreturn]] void raise(fr_status s, const std::string& m) { throw FrError{s, m}; }
+
+void cuda_check(cudaError_t e, const char* what, int line) {
+    if (e != cudaSuccess)
+        raise(FR_ERR_CUDA, std::string(what) + " (line " + std::to_string(line) + "): " + cudaGetErrorString(e));
+}
+#define CU(x) cuda_check((x), #x, __LINE__)
+
+template <class F>
+fr_status guard(F f) {
+    try {
+        f();
+        return FR_OK;
+    } catch (const FrError& e) {
+        g_last_error = e.msg;
+        return e.s;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return FR_ERR_INTERNAL;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return FR_ERR_INTERNAL;
+    }
+}
+
+struct Region {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0;
+    uint64_t launches = 0;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct fr_ctx {
+    frh::Ring R;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    RingDev rd{};
+    DevPrime* d_primes = nullptr;
+    u64 *d_tw = nullptr, *d_tws = nullptr, *d_itw = nullptr, *d_itws = nullptr;
+    unsigned* d_rot = nullptr;
+    double *d_zr = nullptr, *d_zi = nullptr;
+    uint32_t ell = 0, n1 = 0, schedule = 0, cheb_n = 0;
+    double tau = 0.5;
+    uint64_t budget = 0;
+    int d1 = 0, d2 = 0;
+    std::vector<ModUpTab*> d_modup;      // per level: digits_at(level) tables
+    P2QTab* d_p2q = nullptr;
+    std::vector<RescaleTab*> d_rescale;  // per level (index level), level >= 1
+    u64 *d_pinv = nullptr, *d_pinv_s = nullptr;
+    u64* d_delta = nullptr;              // Delta mod q_i
+    std::map<int, u64*> d_cheb;          // per input level: leaf constants [3][nleaves][level+1]
+    std::vector<std::pair<double, double>> leaves;  // Chebyshev leaves (c0, c1), BFS order
+    std::map<u64, u64*> rotkeys;         // galois element -> key
+    u64* relin = nullptr;
+    size_t key_words = 0;
+    size_t resident = 0;
+    std::vector<void*> owned;            // persistent device allocations
+    bool prof = false;
+    std::map<std::string, Region> regions;
+    uint64_t launches = 0;
+    int host_threads = 1;
+};
+
+struct fr_keys {
+    frh::KeySet ks;
+    int logN = 0, nq = 0, np = 0;
+};
+
+struct DevBlock {
+    fr_ctx* ctx;
+    u64* p;
+    DevBlock(fr_ctx* c, u64* ptr) : ctx(c), p(ptr) {}
+    ~DevBlock();
+};
+
+struct fr_ct {
+    const fr_ctx* ctx = nullptr;
+    int level = 0;
+    int cap = 0;
+    double scale = 1.0;
+    bool on_dev = false;
+    std::vector<u64> host;             // coefficient form [2][level+1][N]
+    std::shared_ptr<DevBlock> block;   // device storage (shared by a batch)
+    u64* dev = nullptr;                // evaluation form [2][cap][N]
+};
+
+struct fr_db {
+    fr_ctx* ctx = nullptr;
+    long long K = 0;
+    int ell = 0;
+    long long G = 0;
+    u64* diags = nullptr;
+    size_t bytes = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// device memory (stream-ordered pool)
+// ---------------------------------------------------------------------------
+u64* dalloc(fr_ctx* c, size_t words) {
+    if (words == 0) words = 1;
+    void* p = nullptr;
+    CU(cudaMallocAsync(&p, words * sizeof(u64), c->stream));
+    return (u64*)p;
+}
+void dfree(fr_ctx* c, void* p) {
+    if (p) cudaFreeAsync(p, c->stream);
+}
+struct Tmp {
+    fr_ctx* c;
+    u64* p;
+    Tmp(fr_ctx* cc, size_t words) : c(cc), p(dalloc(cc, words)) {}
+    ~Tmp() { dfree(c, p); }
+    Tmp(const Tmp&) = delete;
+    Tmp& operator=(const Tmp&) = delete;
+};
+template <class T>
+T* upload_persistent(fr_ctx* c, const T* h, size_t count) {
+    void* p = nullptr;
+    CU(cudaMalloc(&p, sizeof(T) * (count ? count : 1)));
+    CU(cudaMemcpy(p, h, sizeof(T) * count, cudaMemcpyHostToDevice));
+    c->owned.push_back(p);
+    return (T*)p;
+}
+
+// profiling regions
+struct Prof {
+    fr_ctx* c;
+    Region* r = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Prof(fr_ctx* cc, const char* name) : c(cc) {
+        if (!c->prof) return;
+        r = &c->regions[name];
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, c->stream);
+    }
+    ~Prof() {
+        if (!r) return;
+        cudaEventRecord(b, c->stream);
+        r->pending.emplace_back(a, b);
+        r->launches++;
+    }
+};
+
+PrimeMap pm_level(int level) {
+    PrimeMap m{};
+    m.period = level + 1;
+    for (int i = 0; i <= level; ++i) m.idx[i] = (unsigned char)i;
+    return m;
+}
+PrimeMap pm_ext(const fr_ctx* c, int level) {
+    PrimeMap m{};
+    const int npos = level + 1 + c->R.np;
+    m.period = npos;
+    for (int pos = 0; pos < npos; ++pos) m.idx[pos] = (unsigned char)(pos <= level ? pos : c->R.nq + pos - level - 1);
+    return m;
+}
+
+void ntt(fr_ctx* c, u64* base, long long outer, int inner, int npolys, const PrimeMap& pm, bool inv) {
+    Prof p(c, "ntt");
+    PolyBatch b{base, outer, inner, npolys, pm};
+    launch_ntt(c->rd, b, inv, c->stream);
+    c->launches += 2;
+}
+// all limbs 0..level of a ciphertext batch [B][2][cap][N]
+void ntt_cts(fr_ctx* c, u64* p, int B, int level, int cap, bool inv) {
+    ntt(c, p, (long long)cap * c->R.N, level + 1, 2 * B * (level + 1), pm_level(level), inv);
+}
+
+long long ctw(const fr_ctx* c, int cap) { return 2ll * cap * c->R.N; }
+
+void copy_d2d(fr_ctx* c, u64* dst, const u64* src, size_t words) {
+    CU(cudaMemcpyAsync(dst, src, words * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream));
+}
+// copy limbs 0..level of B cts from cap_s to cap_d layout
+void copy_cts(fr_ctx* c, u64* dst, int cap_d, const u64* src, int cap_s, int B, int level) {
+    const size_t N = c->R.N;
+    CU(cudaMemcpy2DAsync(dst, cap_d * N * 8, src, cap_s * N * 8, (level + 1) * N * 8, 2 * (size_t)B,
+                         cudaMemcpyDeviceToDevice, c->stream));
+}
+
+// ---------------------------------------------------------------------------
+// hybrid key switching (ModUp -> automorphism -> inner product -> ModDown)
+// ---------------------------------------------------------------------------
+struct KSReq {
+    const u64* c;      // polynomial to switch, evaluation form, limbs 0..level stride N
+    const u64* key;
+    u32 galois;
+    int mode;          // MDJob mode
+    const u64* add;
+    int add_cap;
+    u64* out;
+    int out_cap;
+};
+
+void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, bool shared) {
+    const int N = c->R.N, np = c->R.np, nq = c->R.nq;
+    const int npos = level + 1 + np, beta = c->R.digits_at(level);
+    Tmp acc(c, (size_t)nj * 2 * npos * N);
+    Tmp conv(c, (size_t)nj * 2 * (level + 1) * N);
+    IPJobs ij;
+    for (int j = 0; j < nj; ++j) {
+        ij.j[j].ext = shared ? ext : ext + (size_t)j * beta * npos * N;
+        ij.j[j].key = reqs[j].key;
+        ij.j[j].out = acc.p + (size_t)j * 2 * npos * N;
+        ij.j[j].galois = reqs[j].galois;
+        ij.j[j].pad = 0;
+    }
+    {
+        Prof p(c, "ip");
+        launch_ip(ij, nj, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level), c->R.logN, c->stream);
+        c->launches++;
+    }
+    PrimeMap pmP{};
+    pmP.period = np;
+    for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
+    ntt(c, acc.p + (size_t)(level + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, true);
+    {
+        Prof p(c, "moddown");
+        launch_p2q(acc.p, 2ll * npos * N, npos, level, conv.p, c->d_p2q, N, nj, c->stream);
+        c->launches++;
+    }
+    ntt(c, conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level), false);
+    MDJobs md;
+    for (int j = 0; j < nj; ++j) {
+        MDJob& m = md.j[j];
+        m.acc = acc.p + (size_t)j * 2 * npos * N;
+        m.conv = conv.p + (size_t)j * 2 * (level + 1) * N;
+        m.add = reqs[j].add;
+        m.add_cap = reqs[j].add_cap;
+        m.out = reqs[j].out;
+        m.out_cap = reqs[j].out_cap;
+        m.mode = reqs[j].mode;
+        m.galois = reqs[j].galois;
+    }
+    Prof p(c, "moddown");
+    launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->stream);
+    c->launches++;
+}
+
+void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoisted) {
+    if (reqs.empty()) return;
+    const int N = c->R.N;
+    const int npos = level + 1 + c->R.np, beta = c->R.digits_at(level);
+    const PrimeMap pe = pm_ext(c, level);
+    if (hoisted) {
+        Tmp in(c, (size_t)(level + 1) * N);
+        copy_d2d(c, in.p, reqs[0].c, (size_t)(level + 1) * N);
+        ntt(c, in.p, (long long)(level + 1) * N, level + 1, level + 1, pm_level(level), true);
+        Tmp ext(c, (size_t)beta * npos * N);
+        {
+            Prof p(c, "modup");
+            launch_modup(in.p, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->stream);
+            c->launches++;
+        }
+        ntt(c, ext.p, (long long)npos * N, npos, beta * npos, pe, false);
+        const int chunk = 32;
+        for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
+            int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
+            ks_finish(c, level, &reqs[j0], nj, ext.p, true);
+        }
+        return;
+    }
+    const int chunk = 16;
+    for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
+        int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
+        Tmp in(c, (size_t)nj * (level + 1) * N);
+        for (int j = 0; j < nj; ++j)
+            copy_d2d(c, in.p + (size_t)j * (level + 1) * N, reqs[j0 + j].c, (size_t)(level + 1) * N);
+        ntt(c, in.p, (long long)(level + 1) * N, level + 1, nj * (level + 1), pm_level(level), true);
+        Tmp ext(c, (size_t)nj * beta * npos * N);
+        {
+            Prof p(c, "modup");
+            launch_modup(in.p, (long long)(level + 1) * N, ext.p, c->d_modup[level], beta, npos, N, nj, c->stream);
+            c->launches++;
+        }
+        ntt(c, ext.p, (long long)npos * N, npos, nj * beta * npos, pe, false);
+        ks_finish(c, level, &reqs[j0], nj, ext.p, false);
+    }
+}
+
+const u64* rot_key(fr_ctx* c, u64 g) {
+    auto it = c->rotkeys.find(g);
+    if (it == c->rotkeys.end()) raise(FR_ERR_INVALID_ARG, "rotation key not loaded (galois element " + std::to_string(g) + ")");
+    return it->second;
+}
+const u64* relin_key(fr_ctx* c) {
+    if (!c->relin) raise(FR_ERR_INVALID_ARG, "relinearisation key not loaded");
+    return c->relin;
+}
+
+// rotations of B cts (or of one ct by several indices when hoisted)
+void rotate_cts(fr_ctx* c, int level, const std::vector<const u64*>& in, int in_cap, const std::vector<long>& ks,
+                const std::vector<u64*>& out, int out_cap, bool hoisted) {
+    std::vector<KSReq> reqs;
+    const int N = c->R.N;
+    for (size_t j = 0; j < ks.size(); ++j) {
+        const u64* src = hoisted ? in[0] : in[j];
+        const u64 g = frh::galois_of_rotation(c->R, ks[j]);
+        if (g == 1) {
+            copy_cts(c, out[j], out_cap, src, in_cap, 1, level);
+            continue;
+        }
+        reqs.push_back(KSReq{src + (size_t)in_cap * N, rot_key(c, g), (u32)g, 1, src, in_cap, out[j], out_cap});
+    }
+    keyswitch(c, level, reqs, hoisted);
+}
+
+// ---------------------------------------------------------------------------
+// rescale of B cts at `level` (divide by q_level)
+// ---------------------------------------------------------------------------
+void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, int out_cap) {
+    if (level < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
+    const int N = c->R.N, l = level;
+    Tmp last(c, (size_t)2 * B * N);
+    CU(cudaMemcpy2DAsync(last.p, (size_t)N * 8, in + (size_t)l * N, (size_t)in_cap * N * 8, (size_t)N * 8,
+                         2 * (size_t)B, cudaMemcpyDeviceToDevice, c->stream));
+    PrimeMap one{};
+    one.period = 1;
+    one.idx[0] = (unsigned char)l;
+    ntt(c, last.p, N, 1, 2 * B, one, true);
+    Tmp lifted(c, (size_t)2 * B * l * N);
+    {
+        Prof p(c, "rescale");
+        launch_rescale_lift(last.p, lifted.p, c->d_rescale[l], l, N, 2 * B, c->stream);
+        c->launches++;
+    }
+    ntt(c, lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1), false);
+    Prof p(c, "rescale");
+    launch_rescale_combine(in, in_cap, lifted.p, out, out_cap, c->d_rescale[l], l, N, 2 * B, c->stream);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------
+// ct x ct with relinearisation (no rescale): out_j = relin(a_j (x) b_j)
+// ---------------------------------------------------------------------------
+void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap, const std::vector<const u64*>& Bv,
+               int b_cap, const std::vector<u64*>& out, int out_cap) {
+    const int N = c->R.N;
+    const size_t J = A.size();
+    const size_t dw = (size_t)3 * (level + 1) * N;
+    const size_t chunk = 16;
+    for (size_t j0 = 0; j0 < J; j0 += chunk) {
+        const int nj = (int)std::min(chunk, J - j0);
+        Tmp d(c, nj * dw);
+        TensorJobs tj;
+        for (int j = 0; j < nj; ++j) tj.j[j] = TensorJob{A[j0 + j], Bv[j0 + j], d.p + j * dw, a_cap, b_cap};
+        {
+            Prof p(c, "tensor");
+            launch_tensor(tj, nj, level, c->d_primes, N, c->stream);
+            c->launches++;
+        }
+        std::vector<KSReq> reqs;
+        for (int j = 0; j < nj; ++j)
+            reqs.push_back(KSReq{d.p + j * dw + (size_t)2 * (level + 1) * N, relin_key(c), 1u, 2, d.p + j * dw,
+                                 level + 1, out[j0 + j], out_cap});
+        keyswitch(c, level, reqs, false);
+    }
+}
+
+void add_cts(fr_ctx* c, const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
+             int o_cap, long long o_bs, int level, int B) {
+    Prof p(c, "misc");
+    launch_add(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, B, c->d_primes, c->R.N, c->stream);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev threshold (Paterson-Stockmeyer, d1 = 2): B cts at level ls -> level ls - d2
+// ---------------------------------------------------------------------------
+const u64* cheb_consts(fr_ctx* c, int ls) {
+    auto it = c->d_cheb.find(ls);
+    if (it != c->d_cheb.end()) return it->second;
+    const int nl = (int)c->leaves.size(), L1 = ls + 1;
+    std::vector<u64> h((size_t)3 * nl * L1);
+    const double delta = std::ldexp(1.0, c->R.scale_bits);
+    for (int leaf = 0; leaf < nl; ++leaf) {
+        const int64_t b = std::llround(c->leaves[leaf].second * delta);
+        const int64_t a = std::llround(c->leaves[leaf].first * delta);
+        for (int i = 0; i < L1; ++i) {
+            const u64 q = c->R.primes[i];
+            const u64 bres = frh::resid(b, q);
+            h[(size_t)leaf * L1 + i] = bres;
+            h[(size_t)nl * L1 + (size_t)leaf * L1 + i] = frh::shoup_quot(bres, q);
+            const u64 dm = frh::powm(2, (u64)c->R.scale_bits, q);
+            h[(size_t)2 * nl * L1 + (size_t)leaf * L1 + i] = frh::mulm(frh::resid(a, q), dm, q);
+        }
+    }
+    u64* d = upload_persistent(c, h.data(), h.size());
+    c->d_cheb[ls] = d;
+    return d;
+}
+
+void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int out_cap) {
+    const int N = c->R.N, d2 = c->d2;
+    if (ls - d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the Chebyshev evaluation");
+    const int nleaves = (int)c->leaves.size();
+    // giant powers T_{2^m}, m = 1..d2-1, T_{2^m} at level ls - m
+    std::vector<std::unique_ptr<Tmp>> pw(d2);
+    std::vector<int> pw_cap(d2, 0);
+    const u64* prev = x;
+    int prev_cap = x_cap;
+    for (int m = 1; m < d2; ++m) {
+        const int lv = ls - (m - 1);
+        Tmp sq(c, (size_t)B * ctw(c, lv + 1));
+        std::vector<const u64*> A;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b) {
+            A.push_back(prev + (size_t)b * ctw(c, prev_cap));
+            O.push_back(sq.p + (size_t)b * ctw(c, lv + 1));
+        }
+        mul_relin(c, lv, A, prev_cap, A, prev_cap, O, lv + 1);
+        pw[m].reset(new Tmp(c, (size_t)B * ctw(c, lv)));
+        pw_cap[m] = lv;
+        rescale(c, sq.p, B, lv, lv + 1, pw[m]->p, lv);
+        for (int b = 0; b < B; ++b) {
+            Prof p(c, "misc");
+            launch_double_sub(pw[m]->p + (size_t)b * ctw(c, lv), lv, lv - 1, c->d_delta, c->d_primes, N, c->stream);
+            c->launches++;
+        }
+        prev = pw[m]->p;
+        prev_cap = lv;
+    }
+    // leaves: Rescale(T_1 round(c1 Delta) + round(c0 Delta) Delta)
+    const u64* cc = cheb_consts(c, ls);
+    const int L1 = ls + 1;
+    std::unique_ptr<Tmp> v(new Tmp(c, (size_t)B * nleaves * ctw(c, ls)));
+    {
+        Tmp pre(c, (size_t)B * nleaves * ctw(c, ls + 1));
+        for (int b = 0; b < B; ++b) {
+            Prof p(c, "misc");
+            launch_cheb_leaves(x + (size_t)b * ctw(c, x_cap), x_cap, pre.p + (size_t)b * nleaves * ctw(c, ls + 1),
+                               ls + 1, ls, nleaves, cc, cc + (size_t)nleaves * L1, cc + (size_t)2 * nleaves * L1,
+                               c->d_primes, N, c->stream);
+            c->launches++;
+        }
+        rescale(c, pre.p, B * nleaves, ls, ls + 1, v->p, ls);
+    }
+    int vcap = ls;
+    // tree: parents i = child(2i) * T_{2^s} + child(2i+1)
+    for (int s = 1; s < d2; ++s) {
+        const int P = nleaves >> s;
+        const int lc = ls - s;
+        Tmp prod(c, (size_t)B * P * ctw(c, lc + 1));
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b)
+            for (int i = 0; i < P; ++i) {
+                A.push_back(v->p + ((size_t)b * 2 * P + 2 * i) * ctw(c, vcap));
+                Bv.push_back(pw[s]->p + (size_t)b * ctw(c, pw_cap[s]));
+                O.push_back(prod.p + ((size_t)b * P + i) * ctw(c, lc + 1));
+            }
+        mul_relin(c, lc, A, vcap, Bv, pw_cap[s], O, lc + 1);
+        std::unique_ptr<Tmp> w(new Tmp(c, (size_t)B * P * ctw(c, lc)));
+        rescale(c, prod.p, B * P, lc, lc + 1, w->p, lc);
+        add_cts(c, w->p, lc, ctw(c, lc), v->p + ctw(c, vcap), vcap, 2 * ctw(c, vcap), w->p, lc, ctw(c, lc), lc - 1,
+                B * P);
+        v = std::move(w);
+        vcap = lc;
+    }
+    copy_cts(c, out, out_cap, v->p, vcap, B, ls - d2);
+}
+
+void rotate_sum(fr_ctx* c, u64* ct, int cap, int level) {
+    const int n = c->R.N / 2;
+    Tmp r(c, (size_t)ctw(c, cap));
+    for (long t = 1; t < n; t <<= 1) {
+        rotate_cts(c, level, {ct}, cap, {t}, {r.p}, cap, false);
+        add_cts(c, ct, cap, 0, r.p, cap, 0, ct, cap, 0, level, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// helpers for handles
+// ---------------------------------------------------------------------------
+fr_ct* new_dev_ct(fr_ctx* c, std::shared_ptr<DevBlock> blk, u64* p, int level, int cap) {
+    fr_ct* ct = new fr_ct();
+    ct->ctx = c;
+    ct->level = level;
+    ct->cap = cap;
+    ct->scale = std::ldexp(1.0, c->R.scale_bits);
+    ct->on_dev = true;
+    ct->block = std::move(blk);
+    ct->dev = p;
+    return ct;
+}
+std::shared_ptr<DevBlock> new_block(fr_ctx* c, size_t words) { return std::make_shared<DevBlock>(c, dalloc(c, words)); }
+
+// device copy of a ciphertext (evaluation form); host cts are uploaded
+void to_device(fr_ctx* c, const fr_ct* ct, u64* dst, int cap) {
+    const int N = c->R.N;
+    if (ct->on_dev) {
+        copy_cts(c, dst, cap, ct->dev, ct->cap, 1, ct->level);
+        return;
+    }
+    const size_t L1 = ct->level + 1;
+    CU(cudaMemcpy2DAsync(dst, (size_t)cap * N * 8, ct->host.data(), L1 * N * 8, L1 * N * 8, 2,
+                         cudaMemcpyHostToDevice, c->stream));
+    ntt_cts(c, dst, 1, ct->level, cap, false);
+}
+
+void export_words(fr_ctx* c, const fr_ct* ct, u64* buf) {
+    const int N = c->R.N;
+    const size_t L1 = ct->level + 1;
+    if (!ct->on_dev) {
+        std::memcpy(buf, ct->host.data(), 2 * L1 * N * 8);
+        return;
+    }
+    Tmp t(c, 2 * L1 * N);
+    copy_cts(c, t.p, (int)L1, ct->dev, ct->cap, 1, ct->level);
+    ntt_cts(c, t.p, 1, ct->level, (int)L1, true);
+    CU(cudaMemcpyAsync(buf, t.p, 2 * L1 * N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+}
+
+void need_device(const fr_ctx* c) {
+    if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+    if (c->device < 0) raise(FR_ERR_CUDA, "client-only context (device -1) has no GPU state");
+}
+
+void check_ct(const fr_ctx* c, const fr_ct* ct) {
+    if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+    if (!ct) raise(FR_ERR_INVALID_ARG, "null ciphertext");
+    if (ct->ctx && ct->ctx != c) raise(FR_ERR_INVALID_ARG, "ciphertext belongs to another context");
+    if (ct->level < 0 || ct->level >= c->R.nq) raise(FR_ERR_LEVEL, "ciphertext level out of range");
+}
+
+void build_tables(fr_ctx* c) {
+    const frh::Ring& R = c->R;
+    const int N = R.N, T = R.total();
+    // primes
+    std::vector<DevPrime> dp(T);
+    for (int i = 0; i < T; ++i) {
+        const u64 q = R.primes[i];
+        u64 inv = 1;  // Newton iteration for q^-1 mod 2^64
+        for (int k = 0; k < 7; ++k) inv *= 2 - q * inv;
+        dp[i].q = q;
+        dp[i].qinv = inv;
+        const u64 r1 = (u64)(((u128)1 << 64) % q);
+        dp[i].r2 = frh::mulm(r1, r1, q);
+        dp[i].ninv = R.tabs[i].ninv;
+        dp[i].ninv_s = frh::shoup_quot(R.tabs[i].ninv, q);
+    }
+    c->d_primes = upload_persistent(c, dp.data(), T);
+    std::vector<u64> tw((size_t)T * N), tws((size_t)T * N), itw((size_t)T * N), itws((size_t)T * N);
+    for (int i = 0; i < T; ++i) {
+        std::copy(R.tabs[i].tw.begin(), R.tabs[i].tw.end(), tw.begin() + (size_t)i * N);
+        std::copy(R.tabs[i].tws.begin(), R.tabs[i].tws.end(), tws.begin() + (size_t)i * N);
+        std::copy(R.tabs[i].itw.begin(), R.tabs[i].itw.end(), itw.begin() + (size_t)i * N);
+        std::copy(R.tabs[i].itws.begin(), R.tabs[i].itws.end(), itws.begin() + (size_t)i * N);
+    }
+    c->d_tw = upload_persistent(c, tw.data(), tw.size());
+    c->d_tws = upload_persistent(c, tws.data(), tws.size());
+    c->d_itw = upload_persistent(c, itw.data(), itw.size());
+    c->d_itws = upload_persistent(c, itws.data(), itws.size());
+    c->rd = RingDev{R.logN, N, T, c->d_primes, c->d_tw, c->d_tws, c->d_itw, c->d_itws};
+    c->d_rot = upload_persistent(c, R.rot_group.data(), R.rot_group.size());
+    c->d_zr = upload_persistent(c, R.zr.data(), R.zr.size());
+    c->d_zi = upload_persistent(c, R.zi.data(), R.zi.size());
+    // ModUp tables per level
+    c->d_modup.assign(R.nq, nullptr);
+    for (int l = 0; l < R.nq; ++l) {
+        const int beta = R.digits_at(l), npos = l + 1 + R.np;
+        std::vector<ModUpTab> tabs(beta);
+        for (int d = 0; d < beta; ++d) {
+            ModUpTab& t = tabs[d];
+            std::memset(&t, 0, sizeof(t));
+            int lo, hi;
+            R.digit_range(l, d, &lo, &hi);
+            t.lo = lo;
+            t.ns = hi - lo;
+            if (t.ns > FR_MAX_DIGIT_LIMBS) raise(FR_ERR_UNSUPPORTED, "digit wider than 16 limbs");
+            std::vector<int> src;
+            for (int i = lo; i < hi; ++i) src.push_back(i);
+            for (int i = 0; i < t.ns; ++i) t.src_q[i] = R.primes[lo + i];
+            for (int pos = 0; pos < npos; ++pos) {
+                const int pi = pos <= l ? pos : R.nq + pos - l - 1;
+                t.tq[pos] = R.primes[pi];
+                std::vector<u64> ih, ht;
+                frh::bconv_consts(R, src, pi, ih, ht);
+                for (int i = 0; i < t.ns; ++i) {
+                    t.inv_hat[i] = ih[i];
+                    t.inv_hat_s[i] = frh::shoup_quot(ih[i], R.primes[lo + i]);
+                    t.hat[i][pos] = ht[i];
+                    t.hat_s[i][pos] = frh::shoup_quot(ht[i], R.primes[pi]);
+                }
+            }
+        }
+        c->d_modup[l] = upload_persistent(c, tabs.data(), tabs.size());
+    }
+    // ModDown: P -> Q
+    {
+        P2QTab t;
+        std::memset(&t, 0, sizeof(t));
+        t.np = R.np;
+        if (R.np > FR_MAX_DIGIT_LIMBS) raise(FR_ERR_UNSUPPORTED, "more than 16 special primes");
+        std::vector<int> src;
+        for (int j = 0; j < R.np; ++j) src.push_back(R.nq + j);
+        for (int j = 0; j < R.np; ++j) t.pq[j] = R.primes[R.nq + j];
+        std::vector<u64> pinv(R.nq), pinv_s(R.nq);
+        for (int i = 0; i < R.nq; ++i) {
+            t.qq[i] = R.primes[i];
+            std::vector<u64> ih, ht;
+            frh::bconv_consts(R, src, i, ih, ht);
+            for (int j = 0; j < R.np; ++j) {
+                t.inv_hat[j] = ih[j];
+                t.inv_hat_s[j] = frh::shoup_quot(ih[j], t.pq[j]);
+                t.hat[j][i] = ht[j];
+                t.hat_s[j][i] = frh::shoup_quot(ht[j], R.primes[i]);
+            }
+            u64 P = 1;
+            for (int j = 0; j < R.np; ++j) P = frh::mulm(P, t.pq[j] % R.primes[i], R.primes[i]);
+            pinv[i] = frh::invm(P, R.primes[i]);
+            pinv_s[i] = frh::shoup_quot(pinv[i], R.primes[i]);
+        }
+        c->d_p2q = upload_persistent(c, &t, 1);
+        c->d_pinv = upload_persistent(c, pinv.data(), pinv.size());
+        c->d_pinv_s = upload_persistent(c, pinv_s.data(), pinv_s.size());
+    }
+    // rescale tables
+    c->d_rescale.assign(R.nq, nullptr);
+    for (int l = 1; l < R.nq; ++l) {
+        RescaleTab t;
+        std::memset(&t, 0, sizeof(t));
+        const u64 ql = R.primes[l];
+        t.half = (ql - 1) / 2;
+        for (int i = 0; i < l; ++i) {
+            const u64 q = R.primes[i];
+            t.q[i] = q;
+            t.ql_mod[i] = ql % q;
+            t.qlinv[i] = frh::invm(ql % q, q);
+            t.qlinv_s[i] = frh::shoup_quot(t.qlinv[i], q);
+        }
+        c->d_rescale[l] = upload_persistent(c, &t, 1);
+    }
+    std::vector<u64> delta(R.nq);
+    for (int i = 0; i < R.nq; ++i) delta[i] = frh::powm(2, (u64)R.scale_bits, R.primes[i]);
+    c->d_delta = upload_persistent(c, delta.data(), delta.size());
+}
+
+void build_leaves(fr_ctx* c) {
+    std::vector<double> cf;
+    frh::cheb_coeffs((int)c->cheb_n, c->tau, cf);
+    const size_t len = (size_t)1 << c->d2;
+    cf.resize(len, 0.0);
+    std::vector<std::vector<double>> level{cf};
+    while (level[0].size() > 2) {
+        std::vector<std::vector<double>> nxt;
+        for (auto& v : level) {
+            std::vector<double> q, r;
+            frh::cheb_split(v, q, r);
+            nxt.push_back(q);
+            nxt.push_back(r);
+        }
+        level.swap(nxt);
+    }
+    c->leaves.clear();
+    for (auto& v : level) c->leaves.emplace_back(v[0], v[1]);
+}
+
+}  // namespace
+
+DevBlock::~DevBlock() { dfree(ctx, p); }
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* fr_last_error(void) { return g_last_error.c_str(); }
+
+fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
+    return guard([&] {
+        if (!prm || !out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (!prm->q_bits || !prm->p_bits || prm->n_q < 2 || prm->n_p < 1)
+            raise(FR_ERR_INVALID_ARG, "need at least 2 Q primes and 1 P prime");
+        if (prm->n_q + prm->n_p > FR_MAX_PRIMES) raise(FR_ERR_INVALID_ARG, "too many primes");
+        std::unique_ptr<fr_ctx> c(new fr_ctx());
+        std::string err;
+        std::vector<int> qb(prm->q_bits, prm->q_bits + prm->n_q), pb(prm->p_bits, prm->p_bits + prm->n_p);
+        if (!frh::ring_init(c->R, (int)prm->log_n, qb, pb, (int)prm->dnum, (int)prm->scale_bits, err))
+            raise(FR_ERR_INVALID_ARG, err);
+        const uint32_t n = (uint32_t)c->R.N / 2;
+        if (prm->ell == 0 || n % prm->ell != 0) raise(FR_ERR_INVALID_ARG, "ell must divide N/2");
+        if (prm->n1 == 0 || prm->n1 > prm->ell) raise(FR_ERR_INVALID_ARG, "need 1 <= n1 <= ell");
+        if (prm->schedule != 0) raise(FR_ERR_UNSUPPORTED, "only the on-demand BSGS schedule (0) is implemented");
+        c->ell = prm->ell;
+        c->n1 = prm->n1;
+        c->schedule = prm->schedule;
+        c->cheb_n = prm->cheb_degree;
+        c->tau = prm->threshold;
+        c->budget = prm->hbm_budget_bytes;
+        if (c->cheb_n > 0) {
+            frh::ps_split((int)c->cheb_n, &c->d1, &c->d2);
+            if (c->d1 != 2) raise(FR_ERR_UNSUPPORTED, "Chebyshev degree whose PS split has d1 != 2");
+            build_leaves(c.get());
+        }
+        c->host_threads = std::max(1u, std::thread::hardware_concurrency());
+        if (prm->device < 0) {
+            // client-only context: key generation, encryption and decryption on
+            // the host; every device operation fails with FR_ERR_CUDA
+            c->device = -1;
+            *out = c.release();
+            return;
+        }
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) raise(FR_ERR_CUDA, "no CUDA device available");
+        if (prm->device < 0 || prm->device >= ndev) raise(FR_ERR_INVALID_ARG, "device ordinal out of range");
+        c->device = prm->device;
+        CU(cudaSetDevice(c->device));
+        if (prm->cuda_stream) {
+            c->stream = (cudaStream_t)prm->cuda_stream;
+        } else {
+            CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        cudaMemPool_t pool;
+        CU(cudaDeviceGetDefaultMemPool(&pool, c->device));
+        uint64_t thr = ~0ull;
+        CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        build_tables(c.get());
+        CU(cudaStreamSynchronize(c->stream));
+        *out = c.release();
+    });
+}
+
+void fr_free(fr_ctx* c) {
+    if (!c) return;
+    if (c->device < 0) {
+        delete c;
+        return;
+    }
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->rotkeys) cudaFree(kv.second);
+    if (c->relin) cudaFree(c->relin);
+    for (void* p : c->owned) cudaFree(p);
+    for (auto& r : c->regions)
+        for (auto& e : r.second.pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+fr_status fr_rotation_set(uint32_t ell, uint32_t n1, uint32_t slots, fr_keyset which, int membership, int32_t* out,
+                          size_t cap, size_t* n) {
+    return guard([&] {
+        if (!n) raise(FR_ERR_INVALID_ARG, "null count pointer");
+        std::vector<long> v;
+        if (!frh::rotation_set(ell, n1, slots, (int)which, membership != 0, v))
+            raise(FR_ERR_INVALID_ARG, "bad rotation-set arguments");
+        *n = v.size();
+        for (size_t i = 0; i < v.size() && i < cap && out; ++i) out[i] = (int32_t)v[i];
+    });
+}
+
+uint64_t fr_rotation_count(uint32_t ell, uint32_t n1, uint64_t groups, uint32_t schedule) {
+    if (ell == 0 || n1 == 0) return 0;
+    const uint64_t n2 = (ell + n1 - 1) / n1;
+    if (schedule == 1) return ell - 1;
+    return (n1 - 1) + groups * (n2 - 1);
+}
+
+fr_status fr_required_rotations(const fr_ctx* c, fr_mode mode, int32_t* out, size_t cap, size_t* n) {
+    return guard([&] {
+        if (!c || !n) raise(FR_ERR_INVALID_ARG, "null argument");
+        std::vector<long> v;
+        frh::rotation_set(c->ell, c->n1, (uint32_t)c->R.N / 2, frh::RV_ONDEMAND, mode == FR_MODE_MEMBERSHIP, v);
+        *n = v.size();
+        for (size_t i = 0; i < v.size() && i < cap && out; ++i) out[i] = (int32_t)v[i];
+    });
+}
+
+fr_status fr_keygen(fr_ctx* c, const int32_t* rotations, size_t n_rot, uint64_t seed, fr_keys** out) {
+    return guard([&] {
+        if (!c || !out || (n_rot && !rotations)) raise(FR_ERR_INVALID_ARG, "null argument");
+        std::unique_ptr<fr_keys> k(new fr_keys());
+        std::vector<u64> gal;
+        for (size_t i = 0; i < n_rot; ++i) gal.push_back(frh::galois_of_rotation(c->R, rotations[i]));
+        frh::keygen(c->R, seed, gal, k->ks, c->host_threads);
+        k->logN = c->R.logN;
+        k->nq = c->R.nq;
+        k->np = c->R.np;
+        *out = k.release();
+    });
+}
+
+void fr_free_keys(fr_keys* k) { delete k; }
+
+fr_status fr_load_keys(fr_ctx* c, const fr_keys* k) {
+    return guard([&] {
+        need_device(c);
+        if (!c || !k) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (k->logN != c->R.logN || k->nq != c->R.nq || k->np != c->R.np)
+            raise(FR_ERR_INVALID_ARG, "keys were generated for other parameters");
+        CU(cudaSetDevice(c->device));
+        const int T = c->R.total();
+        const size_t words = (size_t)c->R.ndig * 2 * T * c->R.N;
+        c->key_words = words;
+        size_t need = words * 8 * (1 + k->ks.rot.size());
+        if (c->budget && c->resident + need > c->budget)
+            raise(FR_ERR_HBM_BUDGET, "evaluation keys exceed the HBM budget");
+        PrimeMap pm{};
+        pm.period = T;
+        for (int i = 0; i < T; ++i) pm.idx[i] = (unsigned char)i;
+        auto up = [&](const std::vector<u64>& h) {
+            u64* d = nullptr;
+            CU(cudaMalloc(&d, words * 8));
+            CU(cudaMemcpyAsync(d, h.data(), words * 8, cudaMemcpyHostToDevice, c->stream));
+            launch_to_mont(d, c->R.N, pm, c->d_primes, (long long)words, c->stream);
+            CU(cudaStreamSynchronize(c->stream));
+            return d;
+        };
+        if (!c->relin) {
+            c->relin = up(k->ks.relin);
+            c->resident += words * 8;
+        }
+        for (auto& kv : k->ks.rot) {
+            if (c->rotkeys.count(kv.first)) continue;
+            c->rotkeys[kv.first] = up(kv.second);
+            c->resident += words * 8;
+        }
+    });
+}
+
+fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr_db** out) {
+    return guard([&] {
+        need_device(c);
+        if (!c || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
+        if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
+        CU(cudaSetDevice(c->device));
+        const int N = c->R.N, n = N / 2, nl = c->R.nq;
+        std::unique_ptr<fr_db> db(new fr_db());
+        db->ctx = c;
+        db->K = (long long)K;
+        db->ell = (int)ell;
+        db->G = ((long long)K + n - 1) / n;
+        const size_t words = (size_t)db->G * ell * nl * N;
+        db->bytes = words * 8;
+        if (c->budget && c->resident + db->bytes > c->budget)
+            raise(FR_ERR_HBM_BUDGET, "database diagonals exceed the HBM budget");
+        CU(cudaMalloc(&db->diags, db->bytes));
+        float* dT = nullptr;
+        CU(cudaMalloc(&dT, K * ell * sizeof(float)));
+        CU(cudaMemcpyAsync(dT, templates, K * ell * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        const int chunk = 64;
+        Tmp z(c, (size_t)chunk * n * 2);
+        PrimeMap pm = pm_level(nl - 1);
+        for (long long g = 0; g < db->G; ++g) {
+            for (int d0 = 0; d0 < (int)ell; d0 += chunk) {
+                const int nd = std::min(chunk, (int)ell - d0);
+                u64* dst = db->diags + ((size_t)g * ell + d0) * nl * N;
+                {
+                    Prof p(c, "encode");
+                    launch_encode_diags(dT, (long long)K, (int)ell, c->R.logN - 1, g, d0, nd, (int)c->n1, z.p, dst,
+                                        nl, c->d_primes, c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->stream);
+                    c->launches += 4;
+                }
+                ntt(c, dst, (long long)nl * N, nl, nd * nl, pm, false);
+                launch_to_mont(dst, N, pm, c->d_primes, (long long)nd * nl * N, c->stream);
+                c->launches++;
+            }
+        }
+        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaFree(dT));
+        c->resident += db->bytes;
+        *out = db.release();
+    });
+}
+
+void fr_free_db(fr_db* db) {
+    if (!db) return;
+    if (db->ctx) {
+        cudaStreamSynchronize(db->ctx->stream);
+        db->ctx->resident -= db->bytes;
+    }
+    cudaFree(db->diags);
+    delete db;
+}
+
+static fr_status encrypt_slots(const fr_ctx* c, const fr_keys* k, const std::vector<double>& z, uint64_t seed,
+                               fr_ct** out) {
+    return guard([&] {
+        std::unique_ptr<fr_ct> ct(new fr_ct());
+        ct->ctx = c;
+        ct->level = c->R.nq - 1;
+        ct->cap = c->R.nq;
+        ct->scale = std::ldexp(1.0, c->R.scale_bits);
+        ct->host.resize((size_t)2 * c->R.nq * c->R.N);
+        frh::encrypt(c->R, k->ks, z.data(), seed, ct->host.data());
+        *out = ct.release();
+    });
+}
+
+fr_status fr_encrypt(const fr_ctx* c, const fr_keys* k, const double* q, size_t ell, uint64_t seed, fr_ct** out) {
+    if (!c || !k || !q || !out) {
+        g_last_error = "null argument";
+        return FR_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)c->R.N / 2;
+    if (ell == 0 || n % ell != 0) {
+        g_last_error = "ell must divide N/2";
+        return FR_ERR_INVALID_ARG;
+    }
+    std::vector<double> z(n);
+    for (size_t i = 0; i < n; ++i) z[i] = q[i % ell];
+    return encrypt_slots(c, k, z, seed, out);
+}
+
+fr_status fr_encrypt_slots(const fr_ctx* c, const fr_keys* k, const double* zin, size_t n, uint64_t seed,
+                           fr_ct** out) {
+    if (!c || !k || !zin || !out || n != (size_t)c->R.N / 2) {
+        g_last_error = "bad arguments (need N/2 slot values)";
+        return FR_ERR_INVALID_ARG;
+    }
+    std::vector<double> z(zin, zin + n);
+    return encrypt_slots(c, k, z, seed, out);
+}
+
+fr_status fr_ct_import(const fr_ctx* c, const uint64_t* buf, uint32_t level, double scale, fr_ct** out) {
+    return guard([&] {
+        if (!c || !buf || !out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
+        const size_t N = c->R.N, L1 = level + 1;
+        for (int t = 0; t < 2; ++t)
+            for (size_t i = 0; i < L1; ++i) {
+                const u64 q = c->R.primes[i];
+                const uint64_t* p = buf + (t * L1 + i) * N;
+                for (size_t k = 0; k < N; ++k)
+                    if (p[k] >= q) raise(FR_ERR_FORMAT, "residue not below its prime");
+            }
+        std::unique_ptr<fr_ct> ct(new fr_ct());
+        ct->ctx = c;
+        ct->level = (int)level;
+        ct->cap = (int)L1;
+        ct->scale = scale;
+        ct->host.assign(buf, buf + 2 * L1 * N);
+        *out = ct.release();
+    });
+}
+
+fr_status fr_ct_export(const fr_ct* ct, uint64_t* buf, size_t words, uint32_t* level, double* scale) {
+    return guard([&] {
+        if (!ct || !buf) raise(FR_ERR_INVALID_ARG, "null argument");
+        fr_ctx* c = const_cast<fr_ctx*>(ct->ctx);
+        if (!c) raise(FR_ERR_INVALID_ARG, "ciphertext without context");
+        const size_t need = (size_t)2 * (ct->level + 1) * c->R.N;
+        if (words < need) raise(FR_ERR_INVALID_ARG, "export buffer too small");
+        export_words(c, ct, buf);
+        if (level) *level = (uint32_t)ct->level;
+        if (scale) *scale = ct->scale;
+    });
+}
+
+fr_status fr_ct_info(const fr_ct* ct, uint32_t* level, int* on_device) {
+    if (!ct) return FR_ERR_INVALID_ARG;
+    if (level) *level = (uint32_t)ct->level;
+    if (on_device) *on_device = ct->on_dev ? 1 : 0;
+    return FR_OK;
+}
+
+fr_status fr_ct_upload(fr_ctx* c, fr_ct* ct) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (ct->on_dev) return;
+        const int cap = ct->level + 1;
+        auto blk = new_block(c, ctw(c, cap));
+        to_device(c, ct, blk->p, cap);
+        CU(cudaStreamSynchronize(c->stream));
+        ct->block = blk;
+        ct->dev = blk->p;
+        ct->cap = cap;
+        ct->on_dev = true;
+        ct->host.clear();
+        ct->host.shrink_to_fit();
+    });
+}
+
+void fr_free_ct(fr_ct* ct) { delete ct; }
+void fr_free_cts(fr_ct** cts, size_t n) {
+    if (!cts) return;
+    for (size_t i = 0; i < n; ++i) delete cts[i];
+    delete[] cts;
+}
+
+fr_status fr_decrypt(const fr_ctx* c, const fr_keys* k, const fr_ct* ct, double* slots, size_t n_slots) {
+    return guard([&] {
+        if (!c || !k || !ct || !slots) raise(FR_ERR_INVALID_ARG, "null argument");
+        check_ct(c, ct);
+        const int N = c->R.N;
+        std::vector<u64> w((size_t)2 * (ct->level + 1) * N);
+        export_words(const_cast<fr_ctx*>(c), ct, w.data());
+        std::vector<int64_t> x(N);
+        frh::decrypt_coeffs(c->R, k->ks, w.data(), ct->level, x.data());
+        std::vector<double> z(N / 2);
+        frh::decode_coeffs(c->R, x.data(), ct->scale, z.data());
+        for (size_t i = 0; i < n_slots && i < z.size(); ++i) slots[i] = z[i];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// primitives on device ciphertexts
+// ---------------------------------------------------------------------------
+static const u64* dev_view(fr_ctx* c, const fr_ct* ct, std::unique_ptr<Tmp>& hold, int* cap) {
+    if (ct->on_dev) {
+        *cap = ct->cap;
+        return ct->dev;
+    }
+    hold.reset(new Tmp(c, ctw(c, ct->level + 1)));
+    to_device(c, ct, hold->p, ct->level + 1);
+    *cap = ct->level + 1;
+    return hold->p;
+}
+
+fr_status fr_rotate_hoisted(fr_ctx* c, const fr_ct* ct, const int32_t* ks, size_t n, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (!ks || !out || n == 0) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> hold;
+        int cap;
+        const u64* src = dev_view(c, ct, hold, &cap);
+        const int l = ct->level, L1 = l + 1;
+        auto blk = new_block(c, n * ctw(c, L1));
+        std::vector<long> kv(ks, ks + n);
+        std::vector<u64*> outs;
+        for (size_t i = 0; i < n; ++i) outs.push_back(blk->p + i * ctw(c, L1));
+        rotate_cts(c, l, {src}, cap, kv, outs, L1, true);
+        for (size_t i = 0; i < n; ++i) out[i] = new_dev_ct(c, blk, outs[i], l, L1);
+    });
+}
+
+fr_status fr_rotate(fr_ctx* c, const fr_ct* ct, int32_t k, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> hold;
+        int cap;
+        const u64* src = dev_view(c, ct, hold, &cap);
+        const int l = ct->level, L1 = l + 1;
+        auto blk = new_block(c, ctw(c, L1));
+        rotate_cts(c, l, {src}, cap, {(long)k}, {blk->p}, L1, false);
+        *out = new_dev_ct(c, blk, blk->p, l, L1);
+    });
+}
+
+fr_status fr_rescale(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (ct->level < 1) raise(FR_ERR_LEVEL, "cannot rescale at level 0");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> hold;
+        int cap;
+        const u64* src = dev_view(c, ct, hold, &cap);
+        const int l = ct->level;
+        auto blk = new_block(c, ctw(c, l));
+        rescale(c, src, 1, l, cap, blk->p, l);
+        *out = new_dev_ct(c, blk, blk->p, l - 1, l);
+    });
+}
+
+fr_status fr_mul_relin(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, a);
+        check_ct(c, b);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (a->level != b->level) raise(FR_ERR_LEVEL, "operands at different levels");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> ha, hb;
+        int ca, cb;
+        const u64* pa = dev_view(c, a, ha, &ca);
+        const u64* pb = dev_view(c, b, hb, &cb);
+        const int l = a->level, L1 = l + 1;
+        auto blk = new_block(c, ctw(c, L1));
+        mul_relin(c, l, {pa}, ca, {pb}, cb, {blk->p}, L1);
+        *out = new_dev_ct(c, blk, blk->p, l, L1);
+    });
+}
+
+fr_status fr_add(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, a);
+        check_ct(c, b);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> ha, hb;
+        int ca, cb;
+        const u64* pa = dev_view(c, a, ha, &ca);
+        const u64* pb = dev_view(c, b, hb, &cb);
+        const int l = std::min(a->level, b->level), L1 = l + 1;
+        auto blk = new_block(c, ctw(c, L1));
+        add_cts(c, pa, ca, 0, pb, cb, 0, blk->p, L1, 0, l, 1);
+        *out = new_dev_ct(c, blk, blk->p, l, L1);
+    });
+}
+
+fr_status fr_chebyshev(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<Tmp> hold;
+        int cap;
+        const u64* src = dev_view(c, ct, hold, &cap);
+        const int lo = ct->level - c->d2;
+        if (lo < 0) raise(FR_ERR_LEVEL, "not enough levels for the Chebyshev evaluation");
+        auto blk = new_block(c, ctw(c, lo + 1));
+        chebyshev(c, src, 1, ct->level, cap, blk->p, lo + 1);
+        *out = new_dev_ct(c, blk, blk->p, lo, lo + 1);
+    });
+}
+
+fr_status fr_rotate_sum(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        check_ct(c, ct);
+        if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaSetDevice(c->device));
+        const int l = ct->level, L1 = l + 1;
+        auto blk = new_block(c, ctw(c, L1));
+        to_device(c, ct, blk->p, L1);
+        rotate_sum(c, blk->p, L1, l);
+        *out = new_dev_ct(c, blk, blk->p, l, L1);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// The encrypted 1:N match: on-demand BSGS with hoisted baby steps and
+// pre-rotated diagonals (Algorithms 5 and 6; Eq. eq:prerotation), then the
+// Chebyshev threshold and, for membership, the group sum and RotateAndSum.
+// ---------------------------------------------------------------------------
+fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out) {
+    return guard([&] {
+        need_device(c);
+        if (!c || !db || !query || !out || !n_out) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
+        check_ct(c, query);
+        const int L = c->R.nq - 1;
+        if (query->level != L) raise(FR_ERR_LEVEL, "the query must be at the top level");
+        if ((size_t)c->n1 * 2 * 128 * 8 > 200 * 1024)
+            raise(FR_ERR_UNSUPPORTED, "n1 > 100: the MAC stages 2 n1 baby words per point in shared memory");
+        if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
+        if (mode != FR_MODE_SCORES && L - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+        CU(cudaSetDevice(c->device));
+        const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
+        const int n2 = (ell + n1 - 1) / n1;
+        const long long G = db->G;
+        const int L1 = L + 1;
+        // S1: query ingest (one H2D if host-resident) and baby steps B_i = Rot_i(q), hoisted (S2)
+        Tmp babies(c, (size_t)n1 * ctw(c, L1));
+        to_device(c, query, babies.p, L1);
+        if (n1 > 1) {
+            std::vector<long> ks;
+            std::vector<u64*> outs;
+            for (int i = 1; i < n1; ++i) {
+                ks.push_back(i);
+                outs.push_back(babies.p + (size_t)i * ctw(c, L1));
+            }
+            rotate_cts(c, L, {babies.p}, L1, ks, outs, L1, true);
+        }
+        // S3-S5 per group: MAC with pre-rotated diagonals, rescale, giant rotations, sum
+        auto sblk = new_block(c, (size_t)G * ctw(c, L));
+        for (long long g = 0; g < G; ++g) {
+            Tmp Pj(c, (size_t)n2 * ctw(c, L1));
+            {
+                Prof p(c, "mac");
+                launch_mac(babies.p, L1, db->diags + (size_t)g * ell * L1 * N, Pj.p, L1, L1, n1, n2, ell,
+                           c->d_primes, N, c->stream);
+                c->launches++;
+            }
+            Tmp Gs(c, (size_t)n2 * ctw(c, L));
+            rescale(c, Pj.p, n2, L, L1, Gs.p, L);
+            if (n2 > 1) {
+                Tmp Pr(c, (size_t)(n2 - 1) * ctw(c, L));
+                copy_d2d(c, Pr.p, Gs.p + ctw(c, L), (size_t)(n2 - 1) * ctw(c, L));
+                std::vector<const u64*> in;
+                std::vector<long> ks;
+                std::vector<u64*> outs;
+                for (int j = 1; j < n2; ++j) {
+                    in.push_back(Pr.p + (size_t)(j - 1) * ctw(c, L));
+                    ks.push_back((long)j * n1);
+                    outs.push_back(Gs.p + (size_t)j * ctw(c, L));
+                }
+                rotate_cts(c, L - 1, in, L, ks, outs, L, false);
+            }
+            Prof p(c, "misc");
+            launch_sum(Gs.p, L, ctw(c, L), n2, sblk->p + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->stream);
+            c->launches++;
+        }
+        std::vector<fr_ct*> res;
+        if (mode == FR_MODE_SCORES) {
+            for (long long g = 0; g < G; ++g) res.push_back(new_dev_ct(c, sblk, sblk->p + (size_t)g * ctw(c, L), L - 1, L));
+        } else {
+            // S6: Chebyshev threshold on every group's scores (batched)
+            const int lo = L - 1 - c->d2;
+            auto cblk = new_block(c, (size_t)G * ctw(c, lo + 1));
+            chebyshev(c, sblk->p, (int)G, L - 1, L, cblk->p, lo + 1);
+            sblk.reset();
+            if (mode == FR_MODE_IDENTIFY) {
+                for (long long g = 0; g < G; ++g)
+                    res.push_back(new_dev_ct(c, cblk, cblk->p + (size_t)g * ctw(c, lo + 1), lo, lo + 1));
+            } else {
+                // S7: sum over groups, then RotateAndSum over all slots
+                auto mblk = new_block(c, ctw(c, lo + 1));
+                {
+                    Prof p(c, "misc");
+                    launch_sum(cblk->p, lo + 1, ctw(c, lo + 1), (int)G, mblk->p, lo + 1, lo, c->d_primes, N,
+                               c->stream);
+                    c->launches++;
+                }
+                cblk.reset();
+                rotate_sum(c, mblk->p, lo + 1, lo);
+                res.push_back(new_dev_ct(c, mblk, mblk->p, lo, lo + 1));
+            }
+        }
+        fr_ct** arr = new fr_ct*[res.size()];
+        for (size_t i = 0; i < res.size(); ++i) arr[i] = res[i];
+        *out = arr;
+        *n_out = res.size();
+    });
+}
+
+fr_status fr_sync(fr_ctx* c) {
+    return guard([&] {
+        need_device(c);
+        CU(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fr_status fr_profile(fr_ctx* c, int enable) {
+    return guard([&] {
+        if (!c) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaStreamSynchronize(c->stream));
+        for (auto& r : c->regions) {
+            for (auto& e : r.second.pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+            r.second.pending.clear();
+            r.second.ms = 0;
+            r.second.launches = 0;
+        }
+        c->prof = enable != 0;
+    });
+}
+
+fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* launches) {
+    return guard([&] {
+        if (!c || !region) raise(FR_ERR_INVALID_ARG, "null argument");
+        CU(cudaStreamSynchronize(c->stream));
+        Region& r = c->regions[region];
+        for (auto& e : r.pending) {
+            float t = 0;
+            CU(cudaEventElapsedTime(&t, e.first, e.second));
+            r.ms += t;
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        r.pending.clear();
+        if (ms) *ms = r.ms;
+        if (launches) *launches = r.launches;
+    });
+}
+
+uint64_t fr_launch_count(const fr_ctx* c) { return c ? c->launches : 0; }
+
+fr_status fr_ctx_primes(const fr_ctx* c, uint64_t* out, size_t cap, size_t* n) {
+    if (!c || !n) return FR_ERR_INVALID_ARG;
+    *n = c->R.primes.size();
+    for (size_t i = 0; i < c->R.primes.size() && i < cap && out; ++i) out[i] = c->R.primes[i];
+    return FR_OK;
+}
+
+fr_status fr_ctx_info(const fr_ctx* c, uint32_t* n_slots, uint32_t* top_level, uint32_t* n_digits,
+                      uint64_t* resident_bytes) {
+    if (!c) return FR_ERR_INVALID_ARG;
+    if (n_slots) *n_slots = (uint32_t)c->R.N / 2;
+    if (top_level) *top_level = (uint32_t)c->R.nq - 1;
+    if (n_digits) *n_digits = (uint32_t)c->R.ndig;
+    if (resident_bytes) *resident_bytes = c->resident;
+    return FR_OK;
+}
+
+fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
+    if (!out) return FR_ERR_INVALID_ARG;
+    std::vector<double> c;
+    frh::cheb_coeffs((int)n, tau, c);
+    std::copy(c.begin(), c.end(), out);
+    return FR_OK;
+}
+
+}  // extern "C"

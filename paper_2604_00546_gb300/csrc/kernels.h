@@ -1,0 +1,52 @@
+// Kernel launchers shared by the engine (host-callable, device pointers only).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "dev_arith.cuh"
+
+#define FR_MAX_PRIMES 64
+#define FR_MAX_DIGITS 16
+
+// Periodic prime assignment of a batch of polynomials: poly p uses prime idx[p % period].
+struct PrimeMap {
+    int period;
+    unsigned char idx[FR_MAX_PRIMES];
+};
+
+// A batch of N-point polynomials: poly p lives at base + (p / inner) * outer + (p % inner) * N.
+struct PolyBatch {
+    u64* base;
+    long long outer;
+    int inner;
+    int npolys;
+    PrimeMap pm;
+};
+
+// Ring tables resident on the device for one parameter set.
+struct RingDev {
+    int logN;
+    int N;
+    int nprimes;
+    const DevPrime* primes;  // [nprimes]
+    const u64* tw;           // [nprimes][N] psi^brev(k)
+    const u64* tws;          // Shoup quotients
+    const u64* itw;          // [nprimes][N] psi^-brev(k)
+    const u64* itws;
+};
+
+// Batched negacyclic NTT (evaluation order: position k = value at psi^(2 brev(k)+1)).
+void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s);
+
+// Fast base conversion tables for one (source set, target list).
+struct BconvTab {
+    int ns;                          // source limbs
+    int nt;                          // target limbs
+    int src_prime[FR_MAX_DIGITS];    // prime indices of the sources
+    int src_pos[FR_MAX_DIGITS];      // positions of the sources in the input layout
+    u64 inv_hat[FR_MAX_DIGITS];      // [(B/b_i)^-1]_{b_i}
+    u64 inv_hat_s[FR_MAX_DIGITS];
+    int tgt_prime[FR_MAX_PRIMES];    // prime index of target t
+    int tgt_pos[FR_MAX_PRIMES];      // position of target t in the output layout
+};
+// hat[i][t] = [B/b_i]_{q_t}, with Shoup quotients; stored on the device as [ns][nt] pairs

@@ -1,0 +1,364 @@
+"""Python binding of the C ABI in include/fr.h (argument marshalling only).
+
+Every computation runs in libfr.so (CUDA kernels for sm_103a and the host
+client code). If the library is missing or fails to load, importing the
+binding raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FR_OK = 0
+FR_ERR_INVALID_ARG = 1
+FR_ERR_HBM_BUDGET = 2
+FR_ERR_CUDA = 3
+FR_ERR_TIMEOUT = 4
+FR_ERR_LEVEL = 5
+FR_ERR_FORMAT = 6
+FR_ERR_INTERNAL = 7
+FR_ERR_UNSUPPORTED = 8
+
+FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
+(FR_KEYS_ONDEMAND, FR_KEYS_CPU_BSGS, FR_KEYS_HYDIA_DG, FR_KEYS_TBS_ONLINE, FR_KEYS_TBS_TOTAL,
+ FR_KEYS_TBE_TOTAL) = range(6)
+
+EXPORTED = [
+    "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
+    "fr_load_db", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
+    "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rescale", "fr_mul_relin", "fr_add",
+    "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
+    "fr_ctx_primes", "fr_ctx_info", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
+    "fr_free", "fr_last_error",
+]
+
+
+class FrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fr status {status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("log_n", C.c_uint32), ("n_q", C.c_uint32), ("q_bits", C.POINTER(C.c_uint32)), ("n_p", C.c_uint32),
+        ("p_bits", C.POINTER(C.c_uint32)), ("dnum", C.c_uint32), ("scale_bits", C.c_uint32), ("ell", C.c_uint32),
+        ("n1", C.c_uint32), ("schedule", C.c_uint32), ("cheb_degree", C.c_uint32), ("threshold", C.c_double),
+        ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfr.so (building it first if needed); raise if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libfr.so is not built; run paper_2604_00546_gb300.build.build()")
+    L = C.CDLL(_build.LIB)
+    vp, st = C.c_void_p, C.c_int
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    sig = {
+        "fr_setup": (st, [C.POINTER(Params), C.POINTER(vp)]),
+        "fr_required_rotations": (st, [vp, C.c_int, i32p, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "fr_rotation_set": (st, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int, i32p, C.c_size_t,
+                                 C.POINTER(C.c_size_t)]),
+        "fr_rotation_count": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32]),
+        "fr_keygen": (st, [vp, i32p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
+        "fr_load_keys": (st, [vp, vp]),
+        "fr_load_db": (st, [vp, f32p, C.c_size_t, C.c_size_t, C.POINTER(vp)]),
+        "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
+        "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
+        "fr_match": (st, [vp, vp, vp, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t)]),
+        "fr_decrypt": (st, [vp, vp, vp, f64p, C.c_size_t]),
+        "fr_ct_export": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_uint32), C.POINTER(C.c_double)]),
+        "fr_ct_import": (st, [vp, u64p, C.c_uint32, C.c_double, C.POINTER(vp)]),
+        "fr_ct_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
+        "fr_ct_upload": (st, [vp, vp]),
+        "fr_rotate": (st, [vp, vp, C.c_int32, C.POINTER(vp)]),
+        "fr_rotate_hoisted": (st, [vp, vp, i32p, C.c_size_t, C.POINTER(vp)]),
+        "fr_rescale": (st, [vp, vp, C.POINTER(vp)]),
+        "fr_mul_relin": (st, [vp, vp, vp, C.POINTER(vp)]),
+        "fr_add": (st, [vp, vp, vp, C.POINTER(vp)]),
+        "fr_chebyshev": (st, [vp, vp, C.POINTER(vp)]),
+        "fr_rotate_sum": (st, [vp, vp, C.POINTER(vp)]),
+        "fr_sync": (st, [vp]),
+        "fr_profile": (st, [vp, C.c_int]),
+        "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+        "fr_launch_count": (C.c_uint64, [vp]),
+        "fr_ctx_primes": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "fr_ctx_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                             C.POINTER(C.c_uint64)]),
+        "fr_cheb_coeffs": (st, [C.c_uint32, C.c_double, f64p]),
+        "fr_free_ct": (None, [vp]),
+        "fr_free_cts": (None, [C.POINTER(vp), C.c_size_t]),
+        "fr_free_keys": (None, [vp]),
+        "fr_free_db": (None, [vp]),
+        "fr_free": (None, [vp]),
+        "fr_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != FR_OK:
+        raise FrError(status, (_lib.fr_last_error() or b"").decode())
+
+
+# ---------------------------------------------------------------------------
+# object layer
+# ---------------------------------------------------------------------------
+class Ciphertext:
+    """Library-owned ciphertext handle."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle
+
+    def __del__(self):
+        try:
+            if self.h and self.h.value and _lib is not None:
+                _lib.fr_free_ct(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def info(self):
+        lvl, dev = C.c_uint32(), C.c_int()
+        _check(_lib.fr_ct_info(self.h, C.byref(lvl), C.byref(dev)))
+        return lvl.value, bool(dev.value)
+
+    @property
+    def level(self):
+        return self.info()[0]
+
+    def export(self):
+        lvl = self.level
+        buf = np.empty((2, lvl + 1, self.ctx.N), dtype=np.uint64)
+        out_l, sc = C.c_uint32(), C.c_double()
+        _check(_lib.fr_ct_export(self.h, buf, buf.size, C.byref(out_l), C.byref(sc)))
+        return buf
+
+    def upload(self):
+        _check(_lib.fr_ct_upload(self.ctx.h, self.h))
+        return self
+
+
+class Context:
+    """fr_ctx: parameters, primes, device tables."""
+
+    def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
+                 hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0):
+        L = load()
+        self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
+        self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
+        self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
+                             schedule, cheb_degree, threshold, hbm_budget_bytes, device,
+                             C.c_void_p(cuda_stream) if cuda_stream else None)
+        h = C.c_void_p()
+        _check(L.fr_setup(C.byref(self.params), C.byref(h)))
+        self.h = h
+        self.N = 1 << log_n
+        self.n = self.N // 2
+        self.ell = ell
+        self.n1 = n1
+        self.nq = len(q_bits)
+        self.top = self.nq - 1
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _lib.fr_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def primes(self):
+        out = np.zeros(64, dtype=np.uint64)
+        n = C.c_size_t()
+        _check(_lib.fr_ctx_primes(self.h, out, 64, C.byref(n)))
+        return [int(x) for x in out[: n.value]]
+
+    def info(self):
+        a, b, d, r = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint64()
+        _check(_lib.fr_ctx_info(self.h, C.byref(a), C.byref(b), C.byref(d), C.byref(r)))
+        return dict(n_slots=a.value, top_level=b.value, n_digits=d.value, resident_bytes=r.value)
+
+    def required_rotations(self, mode):
+        out = np.zeros(4096, dtype=np.int32)
+        n = C.c_size_t()
+        _check(_lib.fr_required_rotations(self.h, int(mode), out, out.size, C.byref(n)))
+        return [int(x) for x in out[: n.value]]
+
+    def keygen(self, rotations, seed):
+        r = np.ascontiguousarray(rotations, dtype=np.int32)
+        h = C.c_void_p()
+        _check(_lib.fr_keygen(self.h, r, len(r), int(seed), C.byref(h)))
+        return Keys(self, h)
+
+    def load_keys(self, keys):
+        _check(_lib.fr_load_keys(self.h, keys.h))
+
+    def load_db(self, templates):
+        T = np.ascontiguousarray(templates, dtype=np.float32)
+        h = C.c_void_p()
+        _check(_lib.fr_load_db(self.h, T, T.shape[0], T.shape[1], C.byref(h)))
+        return Database(self, h, T.shape[0])
+
+    def encrypt(self, keys, q, seed):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        h = C.c_void_p()
+        _check(_lib.fr_encrypt(self.h, keys.h, q, q.size, int(seed), C.byref(h)))
+        return Ciphertext(self, h)
+
+    def encrypt_slots(self, keys, z, seed):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        h = C.c_void_p()
+        _check(_lib.fr_encrypt_slots(self.h, keys.h, z, z.size, int(seed), C.byref(h)))
+        return Ciphertext(self, h)
+
+    def import_ct(self, words, level, scale=None):
+        w = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1)
+        h = C.c_void_p()
+        sc = float(scale) if scale is not None else float(2.0 ** self.params.scale_bits)
+        _check(_lib.fr_ct_import(self.h, w, int(level), sc, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def decrypt(self, keys, ct, n=None):
+        n = self.n if n is None else n
+        out = np.empty(n, dtype=np.float64)
+        _check(_lib.fr_decrypt(self.h, keys.h, ct.h, out, n))
+        return out
+
+    def match(self, db, query, mode):
+        arr = C.POINTER(C.c_void_p)()
+        n = C.c_size_t()
+        _check(_lib.fr_match(self.h, db.h, query.h, int(mode), C.byref(arr), C.byref(n)))
+        cts = [Ciphertext(self, C.c_void_p(arr[i])) for i in range(n.value)]
+        # release only the array (the handles are owned by the Ciphertext objects)
+        _lib.fr_free_cts(arr, 0)
+        return cts
+
+    def _unary(self, fn, ct):
+        h = C.c_void_p()
+        _check(fn(self.h, ct.h, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def rotate(self, ct, k):
+        h = C.c_void_p()
+        _check(_lib.fr_rotate(self.h, ct.h, int(k), C.byref(h)))
+        return Ciphertext(self, h)
+
+    def rotate_hoisted(self, ct, ks):
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        hs = (C.c_void_p * len(ks))()
+        _check(_lib.fr_rotate_hoisted(self.h, ct.h, ks, len(ks), C.cast(hs, C.POINTER(C.c_void_p))))
+        return [Ciphertext(self, C.c_void_p(hs[i])) for i in range(len(ks))]
+
+    def rescale(self, ct):
+        return self._unary(_lib.fr_rescale, ct)
+
+    def chebyshev(self, ct):
+        return self._unary(_lib.fr_chebyshev, ct)
+
+    def rotate_sum(self, ct):
+        return self._unary(_lib.fr_rotate_sum, ct)
+
+    def mul_relin(self, a, b):
+        h = C.c_void_p()
+        _check(_lib.fr_mul_relin(self.h, a.h, b.h, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def add(self, a, b):
+        h = C.c_void_p()
+        _check(_lib.fr_add(self.h, a.h, b.h, C.byref(h)))
+        return Ciphertext(self, h)
+
+    def sync(self):
+        _check(_lib.fr_sync(self.h))
+
+    def profile(self, enable):
+        _check(_lib.fr_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, region):
+        ms, n = C.c_double(), C.c_uint64()
+        _check(_lib.fr_profile_read(self.h, region.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self):
+        return int(_lib.fr_launch_count(self.h))
+
+
+class Keys:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h and self.h.value and _lib is not None:
+                _lib.fr_free_keys(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Database:
+    def __init__(self, ctx, h, K):
+        self.ctx = ctx
+        self.h = h
+        self.K = K
+
+    def __del__(self):
+        try:
+            if self.h and self.h.value and _lib is not None:
+                _lib.fr_free_db(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# host-only functions
+# ---------------------------------------------------------------------------
+def rotation_set(ell, n1, slots, which, membership=False):
+    L = load()
+    out = np.zeros(1 << 16, dtype=np.int32)
+    n = C.c_size_t()
+    _check(L.fr_rotation_set(int(ell), int(n1), int(slots), int(which), 1 if membership else 0, out, out.size,
+                             C.byref(n)))
+    return [int(x) for x in out[: n.value]]
+
+
+def rotation_count(ell, n1, groups, schedule=0):
+    return int(load().fr_rotation_count(int(ell), int(n1), int(groups), int(schedule)))
+
+
+def cheb_coeffs(n, tau):
+    out = np.empty(n + 1, dtype=np.float64)
+    _check(load().fr_cheb_coeffs(int(n), float(tau), out))
+    return out

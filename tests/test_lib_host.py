@@ -1,0 +1,130 @@
+"""CPU tests of libfr.so: exported symbols, host client code (bit-exact with the
+oracle on the same seeds), rotation-set and rotation-count bookkeeping against
+the values printed in the paper. No GPU is needed."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_00546_gb300 import fr
+from paper_2604_00546_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split(None, 1)
+                vals[k] = int(v)
+    return vals
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "fr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = fr.load()
+    names = header_functions()
+    assert len(names) >= 30
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(fr.EXPORTED) == names
+
+
+def test_setup_without_gpu_fails_loudly():
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    with pytest.raises(fr.FrError) as e:
+        fr.Context(device=0, **W.ctx_params("tiny"))
+    assert e.value.status == fr.FR_ERR_CUDA
+
+
+@pytest.mark.parametrize("cfg", ["tiny", "mid"])
+def test_client_primes_keys_and_encryption_match_oracle(cfg):
+    c = W.CONFIGS[cfg]
+    ctx = fr.Context(device=-1, **W.ctx_params(cfg))
+    oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
+    assert ctx.primes() == oc.primes
+    assert ctx.info()["n_digits"] == oc.ndig
+    keys = ctx.keygen([1, 2], W.key_seed(cfg))
+    ok = oc.keygen(W.key_seed(cfg))
+    T, q, _ = W.workload(cfg)
+    ct = ctx.encrypt(keys, q, W.enc_seed(cfg))
+    ref = ok.encrypt(np.tile(q, oc.n // c["ell"]), W.enc_seed(cfg))
+    assert np.array_equal(ct.export(), ref)
+    # decryption by the library of the oracle's ciphertext
+    imp = ctx.import_ct(ref, oc.top)
+    z = ctx.decrypt(keys, imp)
+    assert np.abs(z - np.tile(q, oc.n // c["ell"])).max() < 1e-6
+
+
+def test_import_rejects_unreduced_words():
+    c = W.CONFIGS["tiny"]
+    ctx = fr.Context(device=-1, **W.ctx_params("tiny"))
+    w = np.zeros((2, 3, 1 << c["log_n"]), dtype=np.uint64)
+    w[1, 2, 7] = np.uint64(ctx.primes()[2])
+    with pytest.raises(fr.FrError) as e:
+        ctx.import_ct(w, 2)
+    assert e.value.status == fr.FR_ERR_FORMAT
+
+
+def test_device_calls_on_client_context_fail():
+    ctx = fr.Context(device=-1, **W.ctx_params("tiny"))
+    keys = ctx.keygen([1], 5)
+    ct = ctx.encrypt(keys, np.ones(64) / 8, 9)
+    with pytest.raises(fr.FrError) as e:
+        ctx.rotate(ct, 1)
+    assert e.value.status == fr.FR_ERR_CUDA
+
+
+@pytest.mark.parametrize("n", [13, 27, 59])
+def test_chebyshev_coefficients_bit_identical_to_oracle(n):
+    a = fr.cheb_coeffs(n, 0.5)
+    b = oracle.cheb_coeffs(n, 0.5)
+    assert a.tobytes() == b.tobytes()
+
+
+def test_rotation_sets_reproduce_paper_key_counts():
+    g = read_golden("paper_counts.txt")
+    ell, n1, slots = 512, 23, 1 << 14
+    assert len(fr.rotation_set(ell, n1, slots, fr.FR_KEYS_CPU_BSGS)) == g["keys_cpu_bsgs_l512_n1_23"]
+    hydia = fr.rotation_set(ell, n1, slots, fr.FR_KEYS_HYDIA_DG)
+    assert len(hydia) == g["keys_dg_total"]
+    assert len([k for k in hydia if k < ell]) == g["keys_hydia_l512"]
+    assert len(fr.rotation_set(ell, n1, slots, fr.FR_KEYS_TBS_ONLINE)) == g["keys_tbs_online"]
+    assert len(fr.rotation_set(ell, n1, slots, fr.FR_KEYS_TBS_TOTAL)) == g["keys_tbs_total"]
+    assert len(fr.rotation_set(ell, n1, slots, fr.FR_KEYS_TBE_TOTAL)) == g["keys_tbe_total"]
+    # this library's on-demand set at the headline parameters: 31 baby + 15 giant (+ 6 extra powers of two)
+    assert len(fr.rotation_set(512, 32, 1 << 15, fr.FR_KEYS_ONDEMAND, False)) == 46
+    assert len(fr.rotation_set(512, 32, 1 << 15, fr.FR_KEYS_ONDEMAND, True)) == 52
+
+
+def test_rotation_counts_reproduce_paper_table():
+    g = read_golden("paper_counts.txt")
+    for G, key in [(1, "rot_textbook_G1"), (4, "rot_textbook_G4"), (16, "rot_textbook_G16"),
+                   (32, "rot_textbook_G32"), (64, "rot_textbook_G64")]:
+        assert fr.rotation_count(512, 23, G, 0) == g[key]
+    assert fr.rotation_count(512, 23, 64, 1) == g["rot_bsgs_diagonal"]
+
+
+def test_required_rotations_of_context():
+    ctx = fr.Context(device=-1, **W.ctx_params("membership"))
+    s = ctx.required_rotations(fr.FR_MODE_SCORES)
+    assert s == list(range(1, 32)) + [32 * j for j in range(1, 16)]
+    m = ctx.required_rotations(fr.FR_MODE_MEMBERSHIP)
+    assert set(m) == set(s) | {1 << t for t in range(15)}
