@@ -163,12 +163,13 @@ fr_status fr_rotate_sum(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 /* Wait for all work enqueued on the context stream. */
 fr_status fr_sync(fr_ctx* ctx);
 
-/* Per-region device timing (CUDA events on the context stream). enable=1 starts
- * accumulating, 0 stops; fr_profile_read returns the summed milliseconds and the
- * number of timed launches of a region ("ntt", "modup", "ip", "moddown", "rescale",
- * "tensor", "mac", "encode", "misc"). */
+/* Per-region device timing (CUDA events on the context stream). enable=1 clears and
+ * starts accumulating, 0 clears and stops; fr_profile_read returns the summed
+ * milliseconds, the number of timed launches and their algorithmic bytes (the
+ * minimum DRAM reads + writes the launches must make) for a region: "ntt", "modup",
+ * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc". */
 fr_status fr_profile(fr_ctx* ctx, int enable);
-fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches);
+fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
 /* Number of kernel launches issued by the library so far. */
 uint64_t fr_launch_count(const fr_ctx* ctx);
 

@@ -111,6 +111,10 @@ def _declare(L):
     L.or_diag_slots.argtypes = [f32p, C.c_long, C.c_int, C.c_int, C.c_long, C.c_int, C.c_long, f64p]
     L.or_bsgs_scores.restype = C.c_int
     L.or_bsgs_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, C.c_int, u64p]
+    L.or_bsgs_scores_range.restype = C.c_int
+    L.or_bsgs_scores_range.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, u64p]
+    L.or_giant_step.restype = C.c_int
+    L.or_giant_step.argtypes = [vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_long, C.c_int, u64p]
     L.or_diag_scores.restype = C.c_int
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
@@ -321,6 +325,30 @@ class Keys:
             raise ValueError("bad BSGS parameters")
         return out
 
+    def bsgs_scores_range(self, qct, T, ell, n1, j0, j1):
+        """Scores restricted to giant steps j0 <= j < j1 (a bounded sample of the BSGS work)."""
+        c = self.ctx
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        K = T.shape[0]
+        G = (K + c.n - 1) // c.n
+        out = np.empty((G, 2, c.top, c.N), dtype=np.uint64)
+        r = self.L.or_bsgs_scores_range(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), T, K, ell, n1,
+                                        int(j0), int(j1), out)
+        if r < 0:
+            raise ValueError("bad BSGS parameters")
+        return out
+
+    def giant_step(self, babies_eval, n1, T, ell, g, j):
+        """One giant step (diagonal encodes, MAC, rescale) on evaluation-form babies [n1][2][L+1][N]."""
+        c = self.ctx
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        P = np.empty((2, c.top, c.N), dtype=np.uint64)
+        r = self.L.or_giant_step(c.h, np.ascontiguousarray(babies_eval, dtype=np.uint64), int(n1), T, T.shape[0],
+                                 int(ell), int(g), int(j), P)
+        if r < 0:
+            raise ValueError("bad giant step")
+        return P
+
     def diag_scores(self, qct, T, ell):
         c = self.ctx
         T = np.ascontiguousarray(T, dtype=np.float32)
@@ -338,16 +366,15 @@ class Keys:
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
         cnt = 1 if mode == MODE_MEMBERSHIP else G
-        out = np.zeros((cnt, 2, c.top, c.N), dtype=np.uint64)   # large enough for any output level
+        out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), T, K, ell, n1, mode,
                             int(cheb_n), float(tau), out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value
-        w = 2 * (level + 1) * c.N
-        flat = out.reshape(cnt, -1)[:, :w].reshape(cnt, 2, level + 1, c.N).copy()
-        return flat, level
+        w = 2 * (level + 1) * c.N          # output ciphertexts are packed back to back
+        return out[: cnt * w].reshape(cnt, 2, level + 1, c.N).copy(), level
 
 
 # ---------------------------------------------------------------------------

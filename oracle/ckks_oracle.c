@@ -1198,11 +1198,48 @@ static void ct_to_eval(const or_ctx* c, const u64* ct, int l, u64* out) {
 /*                      S_k += (j > 0 ? Rot_{j n1}(P) : P)                   */
 /* scores: out [G][2][L][N] at level L-1 (L = top level).                    */
 /* ------------------------------------------------------------------------ */
-int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell,
-                   int n1, u64* out) {
+/* One giant step j of group g (Algorithm 5, inner loop): babies B_i in evaluation
+ * form [n1][2][L+1][N]; P = Rescale(sum_{i < n1, j n1 + i < ell} B_i (.) D'_{g, j n1 + i}),
+ * written at level L-1 ([2][L][N], coefficient form). */
+int or_giant_step(const or_ctx* c, const u64* babies, int n1, const float* T, long K, int ell, long g, int j,
+                  u64* P) {
+    int N = c->n, L = c->nq - 1;
+    size_t cw = ct_words(c, L);
+    int cnt = (j * n1 + n1 <= ell) ? n1 : ell - j * n1;
+    if (cnt <= 0) return -1;
+    u64* pts = (u64*)malloc(sizeof(u64) * (size_t)cnt * (L + 1) * N);
+    u64* acc = (u64*)malloc(sizeof(u64) * cw);
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < cnt; i++)
+        diag_pt_eval(c, T, K, ell, g, j * n1 + i, (long)j * n1, L, pts + (size_t)i * (L + 1) * N);
+#pragma omp parallel for schedule(dynamic)
+    for (int li = 0; li <= L; li++) {
+        u64 q = c->p[li];
+        for (int t = 0; t < 2; t++) {
+            u64* a = acc + ((size_t)t * (L + 1) + li) * N;
+            memset(a, 0, sizeof(u64) * N);
+            for (int i = 0; i < cnt; i++) {
+                const u64* b = babies + (size_t)i * cw + ((size_t)t * (L + 1) + li) * N;
+                const u64* d = pts + ((size_t)i * (L + 1) + li) * N;
+                for (int x = 0; x < N; x++) a[x] = madd(a[x], mmul(b[x], d[x], q), q);
+            }
+            ntt_inv(c, li, a);
+        }
+    }
+    or_rescale(c, acc, L, P);
+    free(pts);
+    free(acc);
+    return 0;
+}
+
+/* On-demand BSGS over giant steps j_begin <= j < j_end (all steps: 0..n2) */
+int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell,
+                         int n1, int j_begin, int j_end, u64* out) {
     int N = c->n, L = c->nq - 1, n = N / 2;
     if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
     int n2 = (ell + n1 - 1) / n1;
+    if (j_begin < 0) j_begin = 0;
+    if (j_end > n2) j_end = n2;
     long G = (K + n - 1) / n;
     size_t cw = ct_words(c, L), cw1 = ct_words(c, L - 1);
     long* rots = (long*)malloc(sizeof(long) * n1);
@@ -1210,33 +1247,14 @@ int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, const floa
     u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
     or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
     for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
-    u64* pts = (u64*)malloc(sizeof(u64) * (size_t)n1 * (L + 1) * N);
-    u64* acc = (u64*)malloc(sizeof(u64) * cw);
     u64* P = (u64*)malloc(sizeof(u64) * cw1);
     u64* R = (u64*)malloc(sizeof(u64) * cw1);
+    (void)N;
     for (long g = 0; g < G; g++) {
         u64* S = out + (size_t)g * cw1;
         memset(S, 0, sizeof(u64) * cw1);
-        for (int j = 0; j < n2; j++) {
-            int cnt = (j * n1 + n1 <= ell) ? n1 : ell - j * n1;
-#pragma omp parallel for schedule(dynamic)
-            for (int i = 0; i < cnt; i++)
-                diag_pt_eval(c, T, K, ell, g, j * n1 + i, (long)j * n1, L, pts + (size_t)i * (L + 1) * N);
-#pragma omp parallel for schedule(dynamic)
-            for (int li = 0; li <= L; li++) {
-                u64 q = c->p[li];
-                for (int t = 0; t < 2; t++) {
-                    u64* a = acc + ((size_t)t * (L + 1) + li) * N;
-                    memset(a, 0, sizeof(u64) * N);
-                    for (int i = 0; i < cnt; i++) {
-                        const u64* b = babies + (size_t)i * cw + ((size_t)t * (L + 1) + li) * N;
-                        const u64* d = pts + ((size_t)i * (L + 1) + li) * N;
-                        for (int x = 0; x < N; x++) a[x] = madd(a[x], mmul(b[x], d[x], q), q);
-                    }
-                    ntt_inv(c, li, a);
-                }
-            }
-            or_rescale(c, acc, L, P);
+        for (int j = j_begin; j < j_end; j++) {
+            or_giant_step(c, babies, n1, T, K, ell, g, j, P);
             if (j > 0) {
                 or_rotate(c, k, P, L - 1, (long)j * n1, R);
                 or_add(c, S, R, L - 1, S);
@@ -1245,8 +1263,13 @@ int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, const floa
             }
         }
     }
-    free(rots); free(babies); free(pts); free(acc); free(P); free(R);
+    free(rots); free(babies); free(P); free(R);
     return (int)G;
+}
+
+int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell,
+                   int n1, u64* out) {
+    return or_bsgs_scores_range(c, k, qct, T, K, ell, n1, 0, ell, out);
 }
 
 /* Naive diagonal method (Eq. equ:diag), one hoisted rotation per diagonal and a

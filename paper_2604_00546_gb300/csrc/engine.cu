@@ -63,6 +63,7 @@ struct Region {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     double ms = 0;
     uint64_t launches = 0;
+    uint64_t bytes = 0;  // algorithmic bytes (minimum DRAM reads + writes) of the timed launches
 };
 
 }  // namespace
@@ -170,9 +171,10 @@ struct Prof {
     fr_ctx* c;
     Region* r = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
-    Prof(fr_ctx* cc, const char* name) : c(cc) {
+    Prof(fr_ctx* cc, const char* name, double bytes = 0) : c(cc) {
         if (!c->prof) return;
         r = &c->regions[name];
+        r->bytes += (uint64_t)bytes;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
         cudaEventRecord(a, c->stream);
@@ -200,7 +202,7 @@ PrimeMap pm_ext(const fr_ctx* c, int level) {
 }
 
 void ntt(fr_ctx* c, u64* base, long long outer, int inner, int npolys, const PrimeMap& pm, bool inv) {
-    Prof p(c, "ntt");
+    Prof p(c, "ntt", 16.0 * npolys * c->R.N);
     PolyBatch b{base, outer, inner, npolys, pm};
     launch_ntt(c->rd, b, inv, c->stream);
     c->launches += 2;
@@ -250,7 +252,8 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
         ij.j[j].pad = 0;
     }
     {
-        Prof p(c, "ip");
+        const double W = 8.0 * N;
+        Prof p(c, "ip", W * (nj * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos + nj * 2.0 * npos));
         launch_ip(ij, nj, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level), c->R.logN, c->stream);
         c->launches++;
     }
@@ -259,7 +262,7 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
     for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
     ntt(c, acc.p + (size_t)(level + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, true);
     {
-        Prof p(c, "moddown");
+        Prof p(c, "moddown", 8.0 * N * nj * 2.0 * (np + level + 1));
         launch_p2q(acc.p, 2ll * npos * N, npos, level, conv.p, c->d_p2q, N, nj, c->stream);
         c->launches++;
     }
@@ -276,7 +279,9 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
         m.mode = reqs[j].mode;
         m.galois = reqs[j].galois;
     }
-    Prof p(c, "moddown");
+    double addw = 0;
+    for (int j = 0; j < nj; ++j) addw += reqs[j].mode == 1 ? (level + 1) : reqs[j].mode == 2 ? 2.0 * (level + 1) : 0;
+    Prof p(c, "moddown", 8.0 * N * (nj * 6.0 * (level + 1) + addw));
     launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->stream);
     c->launches++;
 }
@@ -292,7 +297,7 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
         ntt(c, in.p, (long long)(level + 1) * N, level + 1, level + 1, pm_level(level), true);
         Tmp ext(c, (size_t)beta * npos * N);
         {
-            Prof p(c, "modup");
+            Prof p(c, "modup", 8.0 * N * ((level + 1) + (double)beta * npos));
             launch_modup(in.p, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->stream);
             c->launches++;
         }
@@ -313,7 +318,7 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
         ntt(c, in.p, (long long)(level + 1) * N, level + 1, nj * (level + 1), pm_level(level), true);
         Tmp ext(c, (size_t)nj * beta * npos * N);
         {
-            Prof p(c, "modup");
+            Prof p(c, "modup", 8.0 * N * nj * ((level + 1) + (double)beta * npos));
             launch_modup(in.p, (long long)(level + 1) * N, ext.p, c->d_modup[level], beta, npos, N, nj, c->stream);
             c->launches++;
         }
@@ -364,12 +369,12 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     ntt(c, last.p, N, 1, 2 * B, one, true);
     Tmp lifted(c, (size_t)2 * B * l * N);
     {
-        Prof p(c, "rescale");
+        Prof p(c, "rescale", 8.0 * N * 2 * B * (1.0 + l));
         launch_rescale_lift(last.p, lifted.p, c->d_rescale[l], l, N, 2 * B, c->stream);
         c->launches++;
     }
     ntt(c, lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1), false);
-    Prof p(c, "rescale");
+    Prof p(c, "rescale", 8.0 * N * 2 * B * 3.0 * l);
     launch_rescale_combine(in, in_cap, lifted.p, out, out_cap, c->d_rescale[l], l, N, 2 * B, c->stream);
     c->launches++;
 }
@@ -389,7 +394,7 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
         TensorJobs tj;
         for (int j = 0; j < nj; ++j) tj.j[j] = TensorJob{A[j0 + j], Bv[j0 + j], d.p + j * dw, a_cap, b_cap};
         {
-            Prof p(c, "tensor");
+            Prof p(c, "tensor", 8.0 * N * nj * 7.0 * (level + 1));
             launch_tensor(tj, nj, level, c->d_primes, N, c->stream);
             c->launches++;
         }
@@ -403,7 +408,7 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
 
 void add_cts(fr_ctx* c, const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
              int o_cap, long long o_bs, int level, int B) {
-    Prof p(c, "misc");
+    Prof p(c, "misc", 8.0 * c->R.N * B * 6.0 * (level + 1));
     launch_add(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, B, c->d_primes, c->R.N, c->stream);
     c->launches++;
 }
@@ -1215,7 +1220,7 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
         for (long long g = 0; g < G; ++g) {
             Tmp Pj(c, (size_t)n2 * ctw(c, L1));
             {
-                Prof p(c, "mac");
+                Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
                 launch_mac(babies.p, L1, db->diags + (size_t)g * ell * L1 * N, Pj.p, L1, L1, n1, n2, ell,
                            c->d_primes, N, c->stream);
                 c->launches++;
@@ -1288,12 +1293,13 @@ fr_status fr_profile(fr_ctx* c, int enable) {
             r.second.pending.clear();
             r.second.ms = 0;
             r.second.launches = 0;
+            r.second.bytes = 0;
         }
         c->prof = enable != 0;
     });
 }
 
-fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* launches) {
+fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* launches, uint64_t* bytes) {
     return guard([&] {
         if (!c || !region) raise(FR_ERR_INVALID_ARG, "null argument");
         CU(cudaStreamSynchronize(c->stream));
@@ -1308,6 +1314,7 @@ fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* l
         r.pending.clear();
         if (ms) *ms = r.ms;
         if (launches) *launches = r.launches;
+        if (bytes) *bytes = r.bytes;
     });
 }
 

@@ -100,7 +100,8 @@ def load(build_if_missing: bool = True):
         "fr_rotate_sum": (st, [vp, vp, C.POINTER(vp)]),
         "fr_sync": (st, [vp]),
         "fr_profile": (st, [vp, C.c_int]),
-        "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+        "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
+                                 C.POINTER(C.c_uint64)]),
         "fr_launch_count": (C.c_uint64, [vp]),
         "fr_ctx_primes": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
         "fr_ctx_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -305,9 +306,9 @@ class Context:
         _check(_lib.fr_profile(self.h, 1 if enable else 0))
 
     def profile_read(self, region):
-        ms, n = C.c_double(), C.c_uint64()
-        _check(_lib.fr_profile_read(self.h, region.encode(), C.byref(ms), C.byref(n)))
-        return ms.value, n.value
+        ms, n, b = C.c_double(), C.c_uint64(), C.c_uint64()
+        _check(_lib.fr_profile_read(self.h, region.encode(), C.byref(ms), C.byref(n), C.byref(b)))
+        return ms.value, n.value, b.value
 
     def launch_count(self):
         return int(_lib.fr_launch_count(self.h))
