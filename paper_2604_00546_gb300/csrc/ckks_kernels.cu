@@ -15,63 +15,74 @@ __device__ __forceinline__ void fold(Acc128& a, u64 q) {
 }
 
 // ---------------------------------------------------------------------------
-// ModUp: per digit, copy the digit's own limbs and fast-convert them to every
-// other position of Q_l u P. Coefficient form in and out.
-// in: [J] jobs, job j at in + j * in_job, limb i at + i * N
+// ModUp: per digit, fast-convert the digit's limbs to every other position of
+// Q_l u P (coefficient form); the digit's own positions are copied from the
+// evaluation-form input so they need no forward NTT afterwards.
+// in: coefficient form, job j at in + j * in_job; in_eval: evaluation form (same layout)
 // ext: [J][beta][npos][N]
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, long long in_job,
-                                                    u64* __restrict__ ext, const ModUpTab* __restrict__ tabs,
-                                                    int beta, int npos, int N) {
+template <int NS>
+__device__ __forceinline__ void modup_body(const ModUpTab& T, const u64* __restrict__ x,
+                                           const u64* __restrict__ xe, u64* __restrict__ out, int npos, int N,
+                                           int k) {
+    u64 ys[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+        ys[i] = mul_shoup(x[(long long)(T.lo + i) * N + k], T.inv_hat[i], T.inv_hat_s[i], T.src_q[i]);
+    for (int pos = 0; pos < npos; ++pos) {
+        u64 v;
+        if (pos >= T.lo && pos < T.lo + NS) {
+            v = xe[(long long)pos * N + k];
+        } else {
+            const u64 t = T.tq[pos];
+            v = 0;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) v = add_mod(v, mul_shoup(ys[i], T.hat[i][pos], T.hat_s[i][pos], t), t);
+        }
+        out[(long long)pos * N + k] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, const u64* __restrict__ in_eval,
+                                                    long long in_job, u64* __restrict__ ext,
+                                                    const ModUpTab* __restrict__ tabs, int beta, int npos, int N) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int d = blockIdx.y;
     const int j = blockIdx.z;
     if (k >= N) return;
     const ModUpTab& T = tabs[d];
     const u64* x = in + (long long)j * in_job;
+    const u64* xe = in_eval + (long long)j * in_job;
     u64* out = ext + (((long long)j * beta + d) * npos) * N;
-    u64 xs[FR_MAX_DIGIT_LIMBS], ys[FR_MAX_DIGIT_LIMBS];
-    for (int i = 0; i < T.ns; ++i) {
-        xs[i] = x[(long long)(T.lo + i) * N + k];
-        ys[i] = mul_shoup(xs[i], T.inv_hat[i], T.inv_hat_s[i], T.src_q[i]);
-    }
-    for (int pos = 0; pos < npos; ++pos) {
-        u64 v;
-        if (pos >= T.lo && pos < T.lo + T.ns) {
-            v = xs[pos - T.lo];
-        } else {
-            const u64 t = T.tq[pos];
-            v = 0;
-            for (int i = 0; i < T.ns; ++i) v = add_mod(v, mul_shoup(ys[i], T.hat[i][pos], T.hat_s[i][pos], t), t);
-        }
-        out[(long long)pos * N + k] = v;
+    switch (T.ns) {
+        case 1: modup_body<1>(T, x, xe, out, npos, N, k); break;
+        case 2: modup_body<2>(T, x, xe, out, npos, N, k); break;
+        case 3: modup_body<3>(T, x, xe, out, npos, N, k); break;
+        case 4: modup_body<4>(T, x, xe, out, npos, N, k); break;
+        case 5: modup_body<5>(T, x, xe, out, npos, N, k); break;
+        case 6: modup_body<6>(T, x, xe, out, npos, N, k); break;
+        case 7: modup_body<7>(T, x, xe, out, npos, N, k); break;
+        default: modup_body<8>(T, x, xe, out, npos, N, k); break;  // ns <= 8, checked on the host
     }
 }
 
 // ---------------------------------------------------------------------------
 // Key-switch inner product: acc_t[pos] = sum_d sigma_g(ext_d[pos]) * key_d[t][limb(pos)]
 // Keys are stored in Montgomery form, so one REDC of the 128-bit sum gives
-// the canonical residue. The automorphism is a gather on the ext index.
+// the canonical residue. The automorphism is a gather on the ext index. When
+// all jobs of a launch use the same key (batched relinearisation), a thread
+// reads its key words once and applies them to every job.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, int npos, int level, int nq, int T,
-                                                 const DevPrime* __restrict__ primes, const PrimeMap pos_prime,
-                                                 int logN) {
-    const int N = 1 << logN;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pos = blockIdx.y;
-    const IPJob& J = jobs.j[blockIdx.z];
-    if (k >= N) return;
-    const int pi = pos_prime.idx[pos];
-    const u64 q = primes[pi].q, qinv = primes[pi].qinv;
-    const int klimb = pos <= level ? pos : nq + (pos - (level + 1));
+template <int BETA>
+__device__ __forceinline__ void ip_job(const IPJob& J, const u64 (&k0)[BETA], const u64 (&k1)[BETA], int npos, int pos,
+                                       int k, u64 q, u64 qinv, int logN, int N) {
     const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
     Acc128 a0{0, 0}, a1{0, 0};
-    for (int d = 0; d < beta; ++d) {
+#pragma unroll
+    for (int d = 0; d < BETA; ++d) {
         const u64 e = J.ext[((long long)d * npos + pos) * N + src];
-        const u64 k0 = J.key[(((long long)d * 2 + 0) * T + klimb) * N + k];
-        const u64 k1 = J.key[(((long long)d * 2 + 1) * T + klimb) * N + k];
-        mac128(a0, e, k0);
-        mac128(a1, e, k1);
+        mac128(a0, e, k0[d]);
+        mac128(a1, e, k1[d]);
         if ((d & 7) == 7) { fold(a0, q); fold(a1, q); }
     }
     fold(a0, q);
@@ -80,11 +91,73 @@ __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, in
     J.out[((long long)npos + pos) * N + k] = redc(a1.hi, a1.lo, q, qinv);
 }
 
+template <int BETA>
+__device__ __forceinline__ void ip_body(const IPJobs& jobs, int nj, bool shared_key, int npos, int pos, int klimb,
+                                        int T, int k, u64 q, u64 qinv, int logN, int N) {
+    u64 k0[BETA], k1[BETA];
+    if (shared_key) {
+        const u64* key = jobs.j[0].key;
+#pragma unroll
+        for (int d = 0; d < BETA; ++d) {
+            k0[d] = key[(((long long)d * 2 + 0) * T + klimb) * N + k];
+            k1[d] = key[(((long long)d * 2 + 1) * T + klimb) * N + k];
+        }
+        for (int j = 0; j < nj; ++j) ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N);
+    } else {
+        const IPJob& J = jobs.j[blockIdx.z];
+#pragma unroll
+        for (int d = 0; d < BETA; ++d) {
+            k0[d] = J.key[(((long long)d * 2 + 0) * T + klimb) * N + k];
+            k1[d] = J.key[(((long long)d * 2 + 1) * T + klimb) * N + k];
+        }
+        ip_job<BETA>(J, k0, k1, npos, pos, k, q, qinv, logN, N);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int nj, int shared_key, int beta, int npos,
+                                                 int level, int nq, int T, const DevPrime* __restrict__ primes,
+                                                 const PrimeMap pos_prime, int logN) {
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y;
+    if (k >= N) return;
+    const int pi = pos_prime.idx[pos];
+    const u64 q = primes[pi].q, qinv = primes[pi].qinv;
+    const int klimb = pos <= level ? pos : nq + (pos - (level + 1));
+    const bool sh = shared_key != 0;
+    switch (beta) {
+        case 1: ip_body<1>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 2: ip_body<2>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 3: ip_body<3>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 4: ip_body<4>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 5: ip_body<5>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 6: ip_body<6>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 7: ip_body<7>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        default: ip_body<8>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;  // beta <= 8
+    }
+}
+
 // ---------------------------------------------------------------------------
 // ModDown base conversion P -> Q_l of the (coefficient-form) P limbs of acc.
 // acc: job j at acc + j * acc_job, poly t at + t * npos * N, P limb jj at position level+1+jj
 // conv: [J][2][level+1][N]
 // ---------------------------------------------------------------------------
+template <int NP>
+__device__ __forceinline__ void p2q_body(const u64* __restrict__ x, u64* __restrict__ o, const P2QTab* __restrict__ tab,
+                                         int level, int N, int k) {
+    u64 ys[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+        ys[i] = mul_shoup(x[(long long)(level + 1 + i) * N + k], tab->inv_hat[i], tab->inv_hat_s[i], tab->pq[i]);
+    for (int i = 0; i <= level; ++i) {
+        const u64 q = tab->qq[i];
+        u64 v = 0;
+#pragma unroll
+        for (int jj = 0; jj < NP; ++jj) v = add_mod(v, mul_shoup(ys[jj], tab->hat[jj][i], tab->hat_s[jj][i], q), q);
+        o[(long long)i * N + k] = v;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_p2q(const u64* __restrict__ acc, long long acc_job, int npos,
                                                   int level, u64* __restrict__ conv, const P2QTab* __restrict__ tab,
                                                   int N) {
@@ -93,17 +166,16 @@ __global__ void __launch_bounds__(kThreads) k_p2q(const u64* __restrict__ acc, l
     const int j = blockIdx.z;
     if (k >= N) return;
     const u64* x = acc + (long long)j * acc_job + (long long)t * npos * N;
-    u64 ys[FR_MAX_DIGIT_LIMBS];
-    for (int i = 0; i < tab->np; ++i) {
-        u64 xv = x[(long long)(level + 1 + i) * N + k];
-        ys[i] = mul_shoup(xv, tab->inv_hat[i], tab->inv_hat_s[i], tab->pq[i]);
-    }
     u64* o = conv + ((long long)j * 2 + t) * (level + 1) * N;
-    for (int i = 0; i <= level; ++i) {
-        const u64 q = tab->qq[i];
-        u64 v = 0;
-        for (int jj = 0; jj < tab->np; ++jj) v = add_mod(v, mul_shoup(ys[jj], tab->hat[jj][i], tab->hat_s[jj][i], q), q);
-        o[(long long)i * N + k] = v;
+    switch (tab->np) {
+        case 1: p2q_body<1>(x, o, tab, level, N, k); break;
+        case 2: p2q_body<2>(x, o, tab, level, N, k); break;
+        case 3: p2q_body<3>(x, o, tab, level, N, k); break;
+        case 4: p2q_body<4>(x, o, tab, level, N, k); break;
+        case 5: p2q_body<5>(x, o, tab, level, N, k); break;
+        case 6: p2q_body<6>(x, o, tab, level, N, k); break;
+        case 7: p2q_body<7>(x, o, tab, level, N, k); break;
+        default: p2q_body<8>(x, o, tab, level, N, k); break;  // np <= 8, checked on the host
     }
 }
 
@@ -148,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_rescale_lift(const u64* __restrict
     u64* o = lifted + (long long)bt * l * N;
     for (int i = 0; i < l; ++i) {
         const u64 q = tab->q[i];
-        u64 r = x % q;  // x < 2^61, one reduction per coefficient and limb
+        u64 r = mul_shoup(x, 1, tab->one_s[i], q);  // x mod q
         if (neg) r = sub_mod(r, tab->ql_mod[i], q);
         o[(long long)i * N + k] = r;
     }
@@ -191,40 +263,60 @@ __global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int 
 // ---------------------------------------------------------------------------
 // Diagonal MAC (on-demand BSGS, Eq. eq:prerotation): for every giant step j
 //   P_j[t][i][k] = sum_{b < n1, j n1 + b < ell} baby_b[t][i][k] * D'_{j n1 + b}[i][k]
-// One thread per evaluation point; its n1 baby values (both polys) are staged
-// in shared memory once and reused by all n2 giant steps, so the babies are
-// read once and every plaintext diagonal word exactly once.
+// A CTA owns TP evaluation points of one limb. Their n1 baby words (both
+// polys) are staged in shared memory once; JG thread groups then split the
+// n2 giant steps among themselves, so every plaintext diagonal word is read
+// exactly once and the babies once per query. Two accumulator pairs (even /
+// odd b) keep two independent multiply-add chains in flight.
 // ---------------------------------------------------------------------------
-template <int TP>
-__global__ void __launch_bounds__(TP) k_mac(const u64* __restrict__ babies, int cap_b, const u64* __restrict__ diags,
-                                            u64* __restrict__ out, int cap_o, int nl, int n1, int n2, int ell,
-                                            const DevPrime* __restrict__ primes, int N) {
+template <int TP, int JG>
+__global__ void __launch_bounds__(TP * JG) k_mac(const u64* __restrict__ babies, int cap_b,
+                                                 const u64* __restrict__ diags, u64* __restrict__ out, int cap_o,
+                                                 int nl, int n1, int n2, int ell, const DevPrime* __restrict__ primes,
+                                                 int N) {
     extern __shared__ u64 sb[];  // [n1][2][TP]
-    const int k = blockIdx.x * TP + threadIdx.x;
+    const int pl = threadIdx.x % TP;
+    const int jg = threadIdx.x / TP;
+    const int k = blockIdx.x * TP + pl;
     const int i = blockIdx.y;
     const u64 q = primes[i].q, qinv = primes[i].qinv;
-    for (int b = 0; b < n1; ++b) {
-        const u64* B = babies + (long long)b * 2 * cap_b * N;
-        sb[(b * 2 + 0) * TP + threadIdx.x] = B[(long long)i * N + k];
-        sb[(b * 2 + 1) * TP + threadIdx.x] = B[((long long)cap_b + i) * N + k];
+    for (int e = threadIdx.x; e < n1 * 2 * TP; e += TP * JG) {
+        const int b = e / (2 * TP), t = (e / TP) & 1, pp = e % TP;
+        sb[e] = babies[((long long)b * 2 + t) * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp];
     }
+    __syncthreads();
     const long long dstride = (long long)nl * N;
-    for (int j = 0; j < n2; ++j) {
+    for (int j = jg; j < n2; j += JG) {
         const int cnt = min(n1, ell - j * n1);
-        Acc128 a0{0, 0}, a1{0, 0};
+        Acc128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
         const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
-#pragma unroll 8
-        for (int b = 0; b < cnt; ++b) {
-            const u64 d = __ldcs(D + (long long)b * dstride);
-            mac128(a0, sb[(b * 2 + 0) * TP + threadIdx.x], d);
-            mac128(a1, sb[(b * 2 + 1) * TP + threadIdx.x], d);
-            if ((b & 7) == 7) { fold(a0, q); fold(a1, q); }
+        int b = 0;
+#pragma unroll 4
+        for (; b + 1 < cnt; b += 2) {
+            const u64 d0 = __ldcs(D + (long long)b * dstride);
+            const u64 d1 = __ldcs(D + (long long)(b + 1) * dstride);
+            mac128(a0, sb[(b * 2 + 0) * TP + pl], d0);
+            mac128(a1, sb[(b * 2 + 1) * TP + pl], d0);
+            mac128(b0, sb[(b * 2 + 2) * TP + pl], d1);
+            mac128(b1, sb[(b * 2 + 3) * TP + pl], d1);
+            if ((b & 7) == 6) { fold(a0, q); fold(a1, q); fold(b0, q); fold(b1, q); }
         }
-        fold(a0, q);
-        fold(a1, q);
+        if (b < cnt) {
+            const u64 d0 = __ldcs(D + (long long)b * dstride);
+            mac128(a0, sb[(b * 2 + 0) * TP + pl], d0);
+            mac128(a1, sb[(b * 2 + 1) * TP + pl], d0);
+        }
+        fold(a0, q); fold(a1, q); fold(b0, q); fold(b1, q);
+        // a + b: both halves below q, sum of highs below 2q + 1
+        u64 lo0 = a0.lo + b0.lo, hi0 = a0.hi + b0.hi + (lo0 < a0.lo ? 1ull : 0ull);
+        u64 lo1 = a1.lo + b1.lo, hi1 = a1.hi + b1.hi + (lo1 < a1.lo ? 1ull : 0ull);
+        hi0 = hi0 >= q ? hi0 - q : hi0;
+        hi0 = hi0 >= q ? hi0 - q : hi0;
+        hi1 = hi1 >= q ? hi1 - q : hi1;
+        hi1 = hi1 >= q ? hi1 - q : hi1;
         u64* O = out + (long long)j * 2 * cap_o * N;
-        O[(long long)i * N + k] = redc(a0.hi, a0.lo, q, qinv);
-        O[((long long)cap_o + i) * N + k] = redc(a1.hi, a1.lo, q, qinv);
+        O[(long long)i * N + k] = redc(hi0, lo0, q, qinv);
+        O[((long long)cap_o + i) * N + k] = redc(hi1, lo1, q, qinv);
     }
 }
 
@@ -425,17 +517,17 @@ __global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* 
 // ===========================================================================
 static inline dim3 g1(int N) { return dim3((N + kThreads - 1) / kThreads); }
 
-void launch_modup(const u64* in, long long in_job, u64* ext, const ModUpTab* tabs, int beta, int npos, int N, int J,
-                  cudaStream_t s) {
+void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
+                  int npos, int N, int J, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, beta, J);
-    k_modup<<<g, kThreads, 0, s>>>(in, in_job, ext, tabs, beta, npos, N);
+    k_modup<<<g, kThreads, 0, s>>>(in, in_eval, in_job, ext, tabs, beta, npos, N);
 }
 
-void launch_ip(const IPJobs& jobs, int J, int beta, int npos, int level, int nq, int T, const DevPrime* primes,
-               const PrimeMap& pos_prime, int logN, cudaStream_t s) {
+void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int nq, int T,
+               const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s) {
     const int N = 1 << logN;
-    dim3 g((N + kThreads - 1) / kThreads, npos, J);
-    k_ip<<<g, kThreads, 0, s>>>(jobs, beta, npos, level, nq, T, primes, pos_prime, logN);
+    dim3 g((N + kThreads - 1) / kThreads, npos, shared_key ? 1 : J);
+    k_ip<<<g, kThreads, 0, s>>>(jobs, J, shared_key ? 1 : 0, beta, npos, level, nq, T, primes, pos_prime, logN);
 }
 
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
@@ -469,15 +561,15 @@ void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* pri
 
 void launch_mac(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
                 const DevPrime* primes, int N, cudaStream_t s) {
-    constexpr int TP = 128;
+    constexpr int TP = 128, JG = 4;
     const size_t sm = (size_t)n1 * 2 * TP * sizeof(u64);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mac<TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_mac<TP, JG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     dim3 g(N / TP, nl);
-    k_mac<TP><<<g, TP, sm, s>>>(babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, primes, N);
+    k_mac<TP, JG><<<g, TP * JG, sm, s>>>(babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, primes, N);
 }
 
 void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,

@@ -29,6 +29,7 @@ struct P2QTab {
 struct RescaleTab {
     u64 half;  // (q_l - 1) / 2
     u64 q[FR_MAX_PRIMES];
+    u64 one_s[FR_MAX_PRIMES];  // floor(2^64 / q_i): Shoup quotient of 1, for x mod q_i
     u64 ql_mod[FR_MAX_PRIMES];
     u64 qlinv[FR_MAX_PRIMES], qlinv_s[FR_MAX_PRIMES];
 };
@@ -65,10 +66,10 @@ struct IPJobs { IPJob j[FR_MAX_JOBS]; };
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
-void launch_modup(const u64* in, long long in_job, u64* ext, const ModUpTab* tabs, int beta, int npos, int N, int J,
-                  cudaStream_t s);
-void launch_ip(const IPJobs& jobs, int J, int beta, int npos, int level, int nq, int T, const DevPrime* primes,
-               const PrimeMap& pos_prime, int logN, cudaStream_t s);
+void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
+                  int npos, int N, int J, cudaStream_t s);
+void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int nq, int T,
+               const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s);
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
                 cudaStream_t s);
 void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,

@@ -86,6 +86,8 @@ struct fr_ctx {
     uint64_t budget = 0;
     int d1 = 0, d2 = 0;
     std::vector<ModUpTab*> d_modup;      // per level: digits_at(level) tables
+    std::vector<int*> d_modup_ntt;       // per level: (offset, prime) of the ext positions to transform
+    std::vector<int> modup_ntt_n;
     P2QTab* d_p2q = nullptr;
     std::vector<RescaleTab*> d_rescale;  // per level (index level), level >= 1
     u64 *d_pinv = nullptr, *d_pinv_s = nullptr;
@@ -207,6 +209,15 @@ void ntt(fr_ctx* c, u64* base, long long outer, int inner, int npolys, const Pri
     launch_ntt(c->rd, b, inv, c->stream);
     c->launches += 2;
 }
+// forward NTT of the non-own positions of nj ModUp outputs [nj][beta][npos][N]
+void ntt_modup(fr_ctx* c, u64* ext, int nj, int level) {
+    const int beta = c->R.digits_at(level), npos = level + 1 + c->R.np;
+    const int cnt = c->modup_ntt_n[level];
+    Prof p(c, "ntt", 16.0 * nj * cnt * c->R.N);
+    PolyBatch b{ext, (long long)beta * npos * c->R.N, 1, nj * cnt, PrimeMap{}, c->d_modup_ntt[level], cnt};
+    launch_ntt(c->rd, b, false, c->stream);
+    c->launches += 2;
+}
 // all limbs 0..level of a ciphertext batch [B][2][cap][N]
 void ntt_cts(fr_ctx* c, u64* p, int B, int level, int cap, bool inv) {
     ntt(c, p, (long long)cap * c->R.N, level + 1, 2 * B * (level + 1), pm_level(level), inv);
@@ -251,10 +262,14 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
         ij.j[j].galois = reqs[j].galois;
         ij.j[j].pad = 0;
     }
+    bool same_key = true;
+    for (int j = 1; j < nj; ++j) same_key &= reqs[j].key == reqs[0].key;
     {
         const double W = 8.0 * N;
-        Prof p(c, "ip", W * (nj * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos + nj * 2.0 * npos));
-        launch_ip(ij, nj, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level), c->R.logN, c->stream);
+        Prof p(c, "ip", W * ((same_key ? 1.0 : nj) * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos +
+                             nj * 2.0 * npos));
+        launch_ip(ij, nj, same_key && nj > 1, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level),
+                  c->R.logN, c->stream);
         c->launches++;
     }
     PrimeMap pmP{};
@@ -290,18 +305,20 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
     if (reqs.empty()) return;
     const int N = c->R.N;
     const int npos = level + 1 + c->R.np, beta = c->R.digits_at(level);
-    const PrimeMap pe = pm_ext(c, level);
+    const size_t L1N = (size_t)(level + 1) * N;
     if (hoisted) {
-        Tmp in(c, (size_t)(level + 1) * N);
-        copy_d2d(c, in.p, reqs[0].c, (size_t)(level + 1) * N);
-        ntt(c, in.p, (long long)(level + 1) * N, level + 1, level + 1, pm_level(level), true);
+        // one ModUp shared by every rotation of the same ciphertext (Algorithm 1, step 1)
+        Tmp in(c, 2 * L1N);
+        copy_d2d(c, in.p + L1N, reqs[0].c, L1N);
+        copy_d2d(c, in.p, reqs[0].c, L1N);
+        ntt(c, in.p, (long long)L1N, level + 1, level + 1, pm_level(level), true);
         Tmp ext(c, (size_t)beta * npos * N);
         {
-            Prof p(c, "modup", 8.0 * N * ((level + 1) + (double)beta * npos));
-            launch_modup(in.p, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->stream);
+            Prof p(c, "modup", 8.0 * N * (2.0 * (level + 1) + (double)beta * npos));
+            launch_modup(in.p, in.p + L1N, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->stream);
             c->launches++;
         }
-        ntt(c, ext.p, (long long)npos * N, npos, beta * npos, pe, false);
+        ntt_modup(c, ext.p, 1, level);
         const int chunk = 32;
         for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
             int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
@@ -312,17 +329,18 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
     const int chunk = 16;
     for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
         int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
-        Tmp in(c, (size_t)nj * (level + 1) * N);
-        for (int j = 0; j < nj; ++j)
-            copy_d2d(c, in.p + (size_t)j * (level + 1) * N, reqs[j0 + j].c, (size_t)(level + 1) * N);
-        ntt(c, in.p, (long long)(level + 1) * N, level + 1, nj * (level + 1), pm_level(level), true);
+        Tmp in(c, (size_t)2 * nj * L1N);  // [nj] coefficient-form copies, then [nj] evaluation-form copies
+        u64* in_e = in.p + (size_t)nj * L1N;
+        for (int j = 0; j < nj; ++j) copy_d2d(c, in_e + (size_t)j * L1N, reqs[j0 + j].c, L1N);
+        copy_d2d(c, in.p, in_e, (size_t)nj * L1N);
+        ntt(c, in.p, (long long)L1N, level + 1, nj * (level + 1), pm_level(level), true);
         Tmp ext(c, (size_t)nj * beta * npos * N);
         {
-            Prof p(c, "modup", 8.0 * N * nj * ((level + 1) + (double)beta * npos));
-            launch_modup(in.p, (long long)(level + 1) * N, ext.p, c->d_modup[level], beta, npos, N, nj, c->stream);
+            Prof p(c, "modup", 8.0 * N * nj * (2.0 * (level + 1) + (double)beta * npos));
+            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nj, c->stream);
             c->launches++;
         }
-        ntt(c, ext.p, (long long)npos * N, npos, nj * beta * npos, pe, false);
+        ntt_modup(c, ext.p, nj, level);
         ks_finish(c, level, &reqs[j0], nj, ext.p, false);
     }
 }
@@ -605,8 +623,11 @@ void build_tables(fr_ctx* c) {
     c->d_rot = upload_persistent(c, R.rot_group.data(), R.rot_group.size());
     c->d_zr = upload_persistent(c, R.zr.data(), R.zr.size());
     c->d_zi = upload_persistent(c, R.zi.data(), R.zi.size());
+    if (R.ndig > 8) raise(FR_ERR_UNSUPPORTED, "more than 8 key-switching digits");
     // ModUp tables per level
     c->d_modup.assign(R.nq, nullptr);
+    c->d_modup_ntt.assign(R.nq, nullptr);
+    c->modup_ntt_n.assign(R.nq, 0);
     for (int l = 0; l < R.nq; ++l) {
         const int beta = R.digits_at(l), npos = l + 1 + R.np;
         std::vector<ModUpTab> tabs(beta);
@@ -617,7 +638,7 @@ void build_tables(fr_ctx* c) {
             R.digit_range(l, d, &lo, &hi);
             t.lo = lo;
             t.ns = hi - lo;
-            if (t.ns > FR_MAX_DIGIT_LIMBS) raise(FR_ERR_UNSUPPORTED, "digit wider than 16 limbs");
+            if (t.ns > 8) raise(FR_ERR_UNSUPPORTED, "key-switching digit wider than 8 limbs");
             std::vector<int> src;
             for (int i = lo; i < hi; ++i) src.push_back(i);
             for (int i = 0; i < t.ns; ++i) t.src_q[i] = R.primes[lo + i];
@@ -635,13 +656,22 @@ void build_tables(fr_ctx* c) {
             }
         }
         c->d_modup[l] = upload_persistent(c, tabs.data(), tabs.size());
+        std::vector<int> nt;
+        for (int d = 0; d < beta; ++d)
+            for (int pos = 0; pos < npos; ++pos) {
+                if (pos >= tabs[d].lo && pos < tabs[d].lo + tabs[d].ns) continue;
+                nt.push_back(d * npos + pos);
+                nt.push_back(pos <= l ? pos : R.nq + pos - l - 1);
+            }
+        c->modup_ntt_n[l] = (int)nt.size() / 2;
+        c->d_modup_ntt[l] = upload_persistent(c, nt.data(), nt.size());
     }
     // ModDown: P -> Q
     {
         P2QTab t;
         std::memset(&t, 0, sizeof(t));
         t.np = R.np;
-        if (R.np > FR_MAX_DIGIT_LIMBS) raise(FR_ERR_UNSUPPORTED, "more than 16 special primes");
+        if (R.np > 8) raise(FR_ERR_UNSUPPORTED, "more than 8 special primes");
         std::vector<int> src;
         for (int j = 0; j < R.np; ++j) src.push_back(R.nq + j);
         for (int j = 0; j < R.np; ++j) t.pq[j] = R.primes[R.nq + j];
@@ -675,6 +705,7 @@ void build_tables(fr_ctx* c) {
         for (int i = 0; i < l; ++i) {
             const u64 q = R.primes[i];
             t.q[i] = q;
+            t.one_s[i] = frh::shoup_quot(1, q);
             t.ql_mod[i] = ql % q;
             t.qlinv[i] = frh::invm(ql % q, q);
             t.qlinv_s[i] = frh::shoup_quot(t.qlinv[i], q);

@@ -14,13 +14,18 @@ struct PrimeMap {
     unsigned char idx[FR_MAX_PRIMES];
 };
 
-// A batch of N-point polynomials: poly p lives at base + (p / inner) * outer + (p % inner) * N.
+// A batch of N-point polynomials: poly p lives at base + (p / inner) * outer + (p % inner) * N
+// and uses prime pm.idx[p % pm.period]. With an index table (tab != nullptr, tab_n entries
+// of (offset, prime) pairs) poly p instead lives at base + (p / tab_n) * outer + tab[2e] * N,
+// e = p % tab_n, and uses prime tab[2e + 1].
 struct PolyBatch {
     u64* base;
     long long outer;
     int inner;
     int npolys;
     PrimeMap pm;
+    const int* tab = nullptr;
+    int tab_n = 0;
 };
 
 // Ring tables resident on the device for one parameter set.

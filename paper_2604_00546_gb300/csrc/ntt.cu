@@ -1,158 +1,272 @@
 // Batched negacyclic NTT / inverse NTT over 64-bit primes.
 //
 // Forward: Cooley-Tukey with twiddles psi^brev(k) (natural-order input,
-// evaluation order output: position k = A(psi^(2 brev(k)+1))). Inverse:
-// Gentleman-Sande with psi^-brev(k), then N^-1. The log N stages are split
-// in two shared-memory passes over an R x C view of the polynomial
-// (N = R * C): the first log R stages only couple elements of one column
-// (stride C), the remaining log C stages only couple elements of one row
-// (contiguous). Each pass loads a tile to shared memory once, runs its stages
-// there and writes back once, so a transform costs two streaming passes; for
-// a batch of limbs that fits in L2 the intermediate stays on chip.
+// evaluation-order output: position k = A(psi^(2 brev(k)+1))). Inverse:
+// Gentleman-Sande with psi^-brev(k), then N^-1.
+//
+// The log N stages are split in two passes over an R x C view of the
+// polynomial (N = R C): the first log R stages only couple elements of one
+// column (stride C), the remaining log C stages only couple elements of one
+// row (contiguous). Each pass loads its tile once and writes it once. Inside a
+// pass every thread keeps 8 elements in registers and runs up to 3 radix-2
+// stages on them; the elements are re-distributed through shared memory
+// between these 3-stage phases, so a 256-point sub-transform costs 2
+// exchanges instead of 8. Index arithmetic is shifts and masks only.
+//
+// Residues stay lazily reduced (Harvey): forward butterflies keep values in
+// [0, 4q), inverse butterflies in [0, 2q); the last pass returns [0, q).
+// Twiddle of the butterfly pairing x and x + 2^b, in either direction:
+// tw[(M + J) >> (b + 1)] where J is the global index of x and M = R for the
+// column pass, N for the row pass.
 #include "kernels.h"
 
 namespace {
 
 constexpr int kTC = 16;  // columns per tile in the column pass
 
-__device__ __forceinline__ u64* poly_ptr(const PolyBatch& b, int p, int N) {
+__device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* prime) {
+    if (b.tab) {
+        const int e = p % b.tab_n;
+        *prime = __ldg(b.tab + 2 * e + 1);
+        return b.base + (long long)(p / b.tab_n) * b.outer + (long long)__ldg(b.tab + 2 * e) * N;
+    }
+    *prime = b.pm.idx[p % b.pm.period];
     return b.base + (long long)(p / b.inner) * b.outer + (long long)(p % b.inner) * N;
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt_col(RingDev R, PolyBatch b, int logR) {
-    extern __shared__ u64 sm[];
-    const int N = R.N;
-    const int Rr = 1 << logR;
-    const int C = N >> logR;
-    const int p = blockIdx.y;
-    u64* x = poly_ptr(b, p, N);
-    const int pi = b.pm.idx[p % b.pm.period];
-    const DevPrime P = R.primes[pi];
-    const u64 q = P.q;
-    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
-    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
-    u64* s = sm;
-    u64* sw = sm + Rr * kTC;
-    u64* sws = sw + Rr;
-    const int col0 = blockIdx.x * kTC;
-    for (int i = threadIdx.x; i < Rr; i += blockDim.x) {
-        sw[i] = tw[i];
-        sws[i] = tws[i];
-    }
-    for (int e = threadIdx.x; e < Rr * kTC; e += blockDim.x) {
-        int r = e / kTC, c = e - r * kTC;
-        s[e] = x[(long long)r * C + col0 + c];
-    }
-    __syncthreads();
-    const int half = (Rr >> 1) * kTC;
-    if (!INV) {
-        for (int m = 1, h = Rr >> 1; m < Rr; m <<= 1, h >>= 1) {
-            for (int bf = threadIdx.x; bf < half; bf += blockDim.x) {
-                int c = bf % kTC, pr = bf / kTC;
-                int i = pr / h, u = pr - i * h;
-                int ra = i * 2 * h + u, rb = ra + h;
-                u64 U = s[ra * kTC + c];
-                u64 V = mul_shoup(s[rb * kTC + c], sw[m + i], sws[m + i], q);
-                s[ra * kTC + c] = add_mod(U, V, q);
-                s[rb * kTC + c] = sub_mod(U, V, q);
-            }
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < Rr * kTC; e += blockDim.x) {
-            int r = e / kTC, c = e - r * kTC;
-            x[(long long)r * C + col0 + c] = s[e];
-        }
-    } else {
-        for (int m = Rr >> 1, h = 1; m >= 1; m >>= 1, h <<= 1) {
-            for (int bf = threadIdx.x; bf < half; bf += blockDim.x) {
-                int c = bf % kTC, pr = bf / kTC;
-                int i = pr / h, u = pr - i * h;
-                int ra = i * 2 * h + u, rb = ra + h;
-                u64 U = s[ra * kTC + c];
-                u64 V = s[rb * kTC + c];
-                s[ra * kTC + c] = add_mod(U, V, q);
-                s[rb * kTC + c] = mul_shoup(sub_mod(U, V, q), sw[m + i], sws[m + i], q);
-            }
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < Rr * kTC; e += blockDim.x) {
-            int r = e / kTC, c = e - r * kTC;
-            x[(long long)r * C + col0 + c] = mul_shoup(s[e], P.ninv, P.ninv_s, q);
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 ws, u64 q) {
+    return x * w - __umul64hi(x, ws) * q;  // in [0, 2q)
+}
+
+// element index of register e of thread tau in a phase whose 3 bits start at LO
+template <int LO>
+__device__ __forceinline__ int phase_x(int tau, int e) {
+    return ((tau >> LO) << (LO + 3)) | (e << LO) | (tau & ((1 << LO) - 1));
+}
+
+template <int LOG, bool INV, int PH>
+struct PhaseInfo {
+    // forward phases take bits in descending order, inverse ones ascending;
+    // a phase covers the 3 bits [LO, LO + 3) and runs the stages on bits [BFROM, BTO)
+    static constexpr int LO = INV ? (3 * PH < LOG - 3 ? 3 * PH : LOG - 3) : (LOG - 3 * (PH + 1) > 0 ? LOG - 3 * (PH + 1) : 0);
+    static constexpr int BFROM = INV ? 3 * PH : LO;
+    static constexpr int BTO = INV ? (3 * PH + 3 < LOG ? 3 * PH + 3 : LOG) : LOG - 3 * PH;
+};
+
+struct Ctx {
+    long long Jbase, M;
+    const u64* tw;
+    const u64* tws;
+    u64 q;
+};
+
+// one radix-2 stage on bit B of the registers of a phase with base bit LO
+template <bool INV, int LO, int B>
+__device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
+    constexpr int lb = B - LO;
+    const u64 q2 = 2 * c.q;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if (e & (1 << lb)) continue;
+        const int e1 = e | (1 << lb);
+        const long long J = c.Jbase + phase_x<LO>(tau, e);
+        const long long idx = (c.M + J) >> (B + 1);
+        const u64 w = c.tw[idx], ws = c.tws[idx];
+        if (!INV) {
+            u64 X = v[e];
+            X = X >= q2 ? X - q2 : X;
+            const u64 T = shoup_lazy(v[e1], w, ws, c.q);
+            v[e] = X + T;
+            v[e1] = X - T + q2;
+        } else {
+            const u64 X = v[e], Y = v[e1];
+            u64 S = X + Y;
+            S = S >= q2 ? S - q2 : S;
+            v[e] = S;
+            v[e1] = shoup_lazy(X - Y + q2, w, ws, c.q);
         }
     }
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b, int logR, int bpc) {
+template <bool INV, int LO, int BFROM, int BTO, int K>
+__device__ __forceinline__ void stages(u64 (&v)[8], int tau, const Ctx& c) {
+    // forward: bits BTO-1 down to BFROM; inverse: BFROM up to BTO-1
+    if constexpr (K < BTO - BFROM) {
+        constexpr int B = INV ? BFROM + K : BTO - 1 - K;
+        stage<INV, LO, B>(v, tau, c);
+        stages<INV, LO, BFROM, BTO, K + 1>(v, tau, c);
+    }
+}
+
+template <int LOG, bool INV, int PH, class Ex>
+__device__ __forceinline__ void phases(u64 (&v)[8], int tau, const Ctx& c, Ex& ex) {
+    constexpr int P = (LOG + 2) / 3;
+    if constexpr (PH < P) {
+        using I = PhaseInfo<LOG, INV, PH>;
+        if constexpr (PH > 0) {
+            using Prev = PhaseInfo<LOG, INV, PH - 1>;
+            ex.template exchange<Prev::LO, I::LO>(v, tau);
+        }
+        stages<INV, I::LO, I::BFROM, I::BTO, 0>(v, tau, c);
+        phases<LOG, INV, PH + 1>(v, tau, c, ex);
+    }
+}
+
+template <int LOG, bool INV>
+struct LastLo {
+    static constexpr int v = PhaseInfo<LOG, INV, (LOG + 2) / 3 - 1>::LO;
+};
+
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
+    x = x >= 2 * q ? x - 2 * q : x;
+    return x >= q ? x - q : x;
+}
+
+// exchange through shared memory, column layout s[x][16]
+struct ColEx {
+    u64* s;
+    int col;
+    template <int LA, int LB>
+    __device__ __forceinline__ void exchange(u64 (&v)[8], int tau) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[phase_x<LA>(tau, e) * kTC + col] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = s[phase_x<LB>(tau, e) * kTC + col];
+        __syncthreads();
+    }
+};
+
+// exchange through shared memory, one padded row (index x + x/8)
+struct RowEx {
+    u64* s;
+    template <int LA, int LB>
+    __device__ __forceinline__ void exchange(u64 (&v)[8], int tau) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int xi = phase_x<LA>(tau, e);
+            s[xi + (xi >> 3)] = v[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int xi = phase_x<LB>(tau, e);
+            v[e] = s[xi + (xi >> 3)];
+        }
+        __syncthreads();
+    }
+};
+
+// column pass: one CTA = 16 columns x S rows; thread (tau, col) with col = threadIdx & 15
+template <int LOG, bool INV>
+__global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, PolyBatch b) {
+    constexpr int S = 1 << LOG;
     extern __shared__ u64 sm[];
+    u64* sw = sm + S * kTC;      // twiddles [0, S)
+    u64* sws = sw + S;
     const int N = R.N;
-    const int C = N >> logR;
+    const int C = N >> LOG;
     const int p = blockIdx.y;
-    u64* x = poly_ptr(b, p, N);
-    const int pi = b.pm.idx[p % b.pm.period];
+    int pi;
+    u64* x = poly_at(b, p, N, &pi);
     const u64 q = R.primes[pi].q;
     const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
     const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
-    const int tile = bpc * C;
-    const long long g0 = (long long)blockIdx.x * tile;
-    for (int e = threadIdx.x; e < tile; e += blockDim.x) sm[e] = x[g0 + e];
-    __syncthreads();
-    const int hc = C >> 1;
-    const int half = tile >> 1;
-    if (!INV) {
-        long long m = 1ll << logR;
-        for (int t = hc; t >= 1; t >>= 1, m <<= 1) {
-            for (int bf = threadIdx.x; bf < half; bf += blockDim.x) {
-                int blk = bf / hc, pp = bf - blk * hc;
-                int il = pp / t, u = pp - il * t;
-                int ja = blk * C + il * 2 * t + u, jb = ja + t;
-                long long widx = m + (g0 + ja) / (2 * t);
-                u64 U = sm[ja];
-                u64 V = mul_shoup(sm[jb], __ldg(tw + widx), __ldg(tws + widx), q);
-                sm[ja] = add_mod(U, V, q);
-                sm[jb] = sub_mod(U, V, q);
-            }
-            __syncthreads();
-        }
-    } else {
-        long long m = (long long)N >> 1;
-        for (int t = 1; t <= hc; t <<= 1, m >>= 1) {
-            for (int bf = threadIdx.x; bf < half; bf += blockDim.x) {
-                int blk = bf / hc, pp = bf - blk * hc;
-                int il = pp / t, u = pp - il * t;
-                int ja = blk * C + il * 2 * t + u, jb = ja + t;
-                long long widx = m + (g0 + ja) / (2 * t);
-                u64 U = sm[ja];
-                u64 V = sm[jb];
-                sm[ja] = add_mod(U, V, q);
-                sm[jb] = mul_shoup(sub_mod(U, V, q), __ldg(tw + widx), __ldg(tws + widx), q);
-            }
-            __syncthreads();
-        }
+    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+        sw[i] = tw[i];
+        sws[i] = tws[i];
     }
-    for (int e = threadIdx.x; e < tile; e += blockDim.x) x[g0 + e] = sm[e];
+    const int col = threadIdx.x & (kTC - 1);
+    const int tau = threadIdx.x >> 4;
+    const int gcol = blockIdx.x * kTC + col;
+    constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
+    constexpr int LL = LastLo<LOG, INV>::v;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
+    __syncthreads();
+    Ctx c{0, S, sw, sws, q};
+    ColEx ex{sm, col};
+    phases<LOG, INV, 0>(v, tau, c, ex);
+    if (INV) {
+        const DevPrime P = R.primes[pi];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            x[(long long)phase_x<LL>(tau, e) * C + gcol] = mul_shoup(v[e], P.ninv, P.ninv_s, q);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[(long long)phase_x<LL>(tau, e) * C + gcol] = v[e];
+    }
+}
+
+// row pass: one CTA = RPC rows of S contiguous elements, S/8 threads per row
+template <int LOG, int LOGR, bool INV>
+__global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
+    constexpr int S = 1 << LOG;
+    constexpr int TPR = S / 8;           // threads per row
+    constexpr int RPC = (256 / TPR < (1 << LOGR)) ? 256 / TPR : (1 << LOGR);  // rows per CTA
+    constexpr int SP = S + S / 8;        // padded row stride in shared memory
+    extern __shared__ u64 sm[];
+    const int N = R.N;
+    const int p = blockIdx.y;
+    int pi;
+    u64* x = poly_at(b, p, N, &pi);
+    const u64 q = R.primes[pi].q;
+    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
+    const int rloc = threadIdx.x / TPR;
+    const int tau = threadIdx.x % TPR;
+    const long long rho = (long long)blockIdx.x * RPC + rloc;
+    const long long Jbase = rho * S;
+    u64* xr = x + Jbase;
+    constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
+    constexpr int LL = LastLo<LOG, INV>::v;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
+    Ctx c{Jbase, N, tw, tws, q};
+    RowEx ex{sm + rloc * SP};
+    phases<LOG, INV, 0>(v, tau, c, ex);
+    if (INV) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = v[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = reduce4(v[e], q);
+    }
+}
+
+template <int LOGR, int LOGC>
+void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st) {
+    constexpr int SR = 1 << LOGR, SC = 1 << LOGC;
+    const int N = R.N;
+    dim3 gc((N >> LOGR) / kTC, b.npolys);
+    const int tc = kTC * SR / 8;
+    const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
+    constexpr int TPR = SC / 8, RPC = (256 / TPR < SR) ? 256 / TPR : SR;
+    dim3 gr(SR / RPC, b.npolys);
+    const size_t smr = (size_t)RPC * (SC + SC / 8) * sizeof(u64);
+    if (!inverse) {
+        k_ntt_col<LOGR, false><<<gc, tc, smc, st>>>(R, b);
+        k_ntt_row<LOGC, LOGR, false><<<gr, RPC * TPR, smr, st>>>(R, b);
+    } else {
+        k_ntt_row<LOGC, LOGR, true><<<gr, RPC * TPR, smr, st>>>(R, b);
+        k_ntt_col<LOGR, true><<<gc, tc, smc, st>>>(R, b);
+    }
 }
 
 }  // namespace
 
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s) {
     if (b.npolys <= 0) return;
-    const int logN = R.logN;
-    const int logR = logN / 2;
-    const int Rr = 1 << logR;
-    const int C = R.N >> logR;
-    int bpc = 2048 / C;
-    if (bpc < 1) bpc = 1;
-    if (bpc > Rr) bpc = Rr;
-    const size_t smc = (size_t)(Rr * kTC + 2 * Rr) * sizeof(u64);
-    const size_t smr = (size_t)bpc * C * sizeof(u64);
-    dim3 gc(C / kTC, b.npolys), gr(Rr / bpc, b.npolys);
-    if (!inverse) {
-        k_ntt_col<false><<<gc, 256, smc, s>>>(R, b, logR);
-        k_ntt_row<false><<<gr, 256, smr, s>>>(R, b, logR, bpc);
-    } else {
-        k_ntt_row<true><<<gr, 256, smr, s>>>(R, b, logR, bpc);
-        k_ntt_col<true><<<gc, 256, smc, s>>>(R, b, logR);
+    switch (R.logN) {
+        case 10: launch_ntt_t<5, 5>(R, b, inverse, s); break;
+        case 11: launch_ntt_t<5, 6>(R, b, inverse, s); break;
+        case 12: launch_ntt_t<6, 6>(R, b, inverse, s); break;
+        case 13: launch_ntt_t<6, 7>(R, b, inverse, s); break;
+        case 14: launch_ntt_t<7, 7>(R, b, inverse, s); break;
+        case 15: launch_ntt_t<7, 8>(R, b, inverse, s); break;
+        case 16: launch_ntt_t<8, 8>(R, b, inverse, s); break;
+        default: break;
     }
 }
