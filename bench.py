@@ -103,17 +103,19 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle: bounded sample of one query, extrapolated to the full query
 # ---------------------------------------------------------------------------
-def oracle_sample(cfgname, T, q, seed_key, seed_enc):
+def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None):
+    """Time a bounded sample of the oracle's work for one query computed at level lq."""
     import oracle
     from paper_2604_00546_gb300 import workloads as W
     c = W.CONFIGS[cfgname]
     oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
     ok = oc.keygen(seed_key)
-    L, n1, ell = oc.top, c["n1"], c["ell"]
+    L = oc.top if lq is None else lq
+    n1, ell = c["n1"], c["ell"]
     n2 = (ell + n1 - 1) // n1
     G = (len(T) + oc.n - 1) // oc.n
     d1, d2 = oracle.ps_split(c["cheb_degree"])
-    oq = ok.encrypt(np.tile(q, oc.n // ell), seed_enc)
+    oq = oc.drop(ok.encrypt(np.tile(q, oc.n // ell), seed_enc), oc.top, L)
     tm = {}
 
     def timed(name, f):
@@ -166,11 +168,12 @@ def run_reference(args):
     from paper_2604_00546_gb300 import workloads as W
     cfg = args.config
     T, q, _ = W.workload(cfg)
+    lq = W.work_level(cfg, args.level_mode)
     vals, lat, work = [], [], 0.0
     sample = cores = None
     t_all = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg))
+        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq)
         if s >= args.warmup:
             vals.append(v)
             lat.append(l)
@@ -182,7 +185,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(lat)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded Gaussian L2-normalised templates, 32 planted duplicates at cosine 0.8)",
-        "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": len(T), "log_n": 16},
+        "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": len(T), "log_n": 16,
+                   "work_level": lq},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
@@ -215,7 +219,7 @@ def run_ours(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     t0 = time.perf_counter()
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg))
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode))
     rots = ctx.required_rotations(mode)
     keys = ctx.keygen(rots, W.key_seed(cfg))
     t_keygen = time.perf_counter() - t0
@@ -225,12 +229,13 @@ def run_ours(args):
     dev_q = ctx.encrypt(keys, q, W.enc_seed(cfg)).upload()
     ctx.sync()
     t_setup = time.perf_counter() - t0
+    lq = ctx.work_level
 
-    def step(query):
-        return ctx.match(db, query, mode)
+    def step(cx, d, query):
+        return cx.match(d, query, mode)
 
     for _ in range(args.warmup):
-        out = step(dev_q)
+        out = step(ctx, db, dev_q)
     ctx.sync()
     # correctness of the last warm-up output (decrypted membership value vs FP64)
     from numpy.polynomial import chebyshev as npc
@@ -256,7 +261,7 @@ def run_ours(args):
     ev[0].record(stream)
     outs = []
     for i in range(args.steps):
-        outs.append(step(dev_q))
+        outs.append(step(ctx, db, dev_q))
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     n_launch = ctx.launch_count() - n_launch0
@@ -277,14 +282,14 @@ def run_ours(args):
         tmax = float(t.item())
     value = ws * K * args.steps / (tmax / 1000.0)
 
-    # end to end through the C ABI: host query -> H2D -> match -> D2H of the result
-    h2d = 2 * len(c["q_bits"]) * (1 << c["log_n"]) * 8
+    # end to end through the C ABI: host query -> H2D (the working-level limbs) -> match -> D2H
+    h2d = 2 * (lq + 1) * (1 << c["log_n"]) * 8
     e2e_t = []
     d2h = 0
     for i in range(max(1, min(args.steps, 5))):
         torch.cuda.synchronize()
         a = time.perf_counter()
-        res = step(host_q)
+        res = step(ctx, db, host_q)
         words = [r.export() for r in res]
         e2e_t.append(time.perf_counter() - a)
         d2h = sum(w.nbytes for w in words)
@@ -293,6 +298,31 @@ def run_ours(args):
         t = torch.tensor([float(np.mean(e2e_t))], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ws * K / float(t.item())
+
+    # the same query on the whole modulus chain (no level drop), for comparison
+    full = None
+    if args.level_mode == 1 and not args.no_full_chain and lq < len(c["q_bits"]) - 1:
+        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0))
+        ctx_f.load_keys(keys)
+        db_f = ctx_f.load_db(T)
+        dq_f = ctx_f.encrypt(keys, q, W.enc_seed(cfg)).upload()
+        for _ in range(2):
+            out = step(ctx_f, db_f, dq_f)
+        ctx_f.sync()
+        got_f = float(ctx_f.decrypt(keys, out[0])[0])
+        del out
+        nf = max(3, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        outs = [step(ctx_f, db_f, dq_f) for _ in range(nf)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_f = e0.elapsed_time(e1) / nf
+        del outs
+        full = {"work_level": len(c["q_bits"]) - 1, "ms_per_step": ms_f, "value": K / (ms_f / 1000.0),
+                "steps": nf, "membership_decrypted": got_f}
+        del db_f, ctx_f
 
     # roofline of the dominant region (largest device time)
     peak, peak_kind = load_peaks()
@@ -306,7 +336,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg))
+        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -318,8 +348,9 @@ def run_ours(args):
             "data": "synthetic (seeded Gaussian L2-normalised templates, 32 planted duplicates at cosine 0.8)",
             "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": K, "log_n": c["log_n"],
                        "q_limbs": len(c["q_bits"]), "p_limbs": len(c["p_bits"]), "dnum": c["dnum"],
+                       "work_level": lq, "level_mode": args.level_mode,
                        "parallelism": f"replicas x{ws}",
-                       "l2": "working set (6.7 GB diagonals + 9.5 GB keys) exceeds the 129 MB L2; no flush"},
+                       "l2": "working set (diagonals + evaluation keys, several GB) exceeds the 129 MB L2; no flush"},
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99)),
                            "mean": float(np.mean(lat))},
             "hbm_gbs_dominant": achieved,
@@ -327,6 +358,7 @@ def run_ours(args):
             "regions_ms_per_step": {r: regions[r]["ms"] / args.steps for r in regions},
             "gpu_launches": int(n_launch),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "full_chain": full,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "check": {"membership_decrypted": got, "membership_fp64": float(pref), "abs_err": abs(got - pref)},
@@ -346,6 +378,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="membership")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-full-chain", action="store_true")
+    ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

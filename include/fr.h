@@ -87,8 +87,13 @@ typedef struct {
     uint32_t cheb_degree;      /* Chebyshev degree n of the threshold (PS split must give d1 = 2) */
     double threshold;          /* tau in step(x - tau) */
     uint64_t hbm_budget_bytes; /* 0: no budget beyond the device */
-    int device;                /* CUDA device ordinal */
+    int device;                /* CUDA device ordinal; -1: client-only context (host key generation,
+                                  encryption, decryption; device calls fail with FR_ERR_CUDA) */
     void* cuda_stream;         /* optional cudaStream_t to run on (not owned); NULL: the context creates one */
+    uint32_t level_mode;       /* 0: the match runs at the query's top level (whole modulus chain);
+                                  1: the query is first dropped (limbs discarded) to the lowest level that
+                                  still leaves the threshold depth and one output level above 0:
+                                  2 + d2 with a Chebyshev degree, 2 without, capped at the top level */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.
@@ -119,7 +124,8 @@ fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
 /* Load a plaintext template database: row-major K x ell float32 (host pointer),
  * L2-normalised by the caller. Templates are packed per Section "Diagonal method
  * for rectangular matrices" (G = ceil(K / (N/2)) groups) and every pre-rotated
- * diagonal (Eq. eq:prerotation) is encoded on the device and kept in HBM. */
+ * diagonal (Eq. eq:prerotation) is encoded on the device and kept in HBM with the
+ * limbs of the context's working level (G * ell * (level+1) * N words). */
 fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
 
 /* Client-side encryption of one query q (ell values) replicated across the N/2 slots
@@ -136,7 +142,8 @@ fr_status fr_encrypt_slots(const fr_ctx* ctx, const fr_keys* keys, const double*
  * device ciphertexts in *out (array freed with fr_free_cts). */
 fr_status fr_match(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out);
 
-/* Client-side decryption + decoding of up to n_slots slot values (divided by the nominal scale). */
+/* Client-side decryption + decoding of up to n_slots slot values (divided by the nominal scale).
+ * At level >= 1 the plaintext is recovered exactly from limbs 0 and 1 (CRT, |m| < q0 q1 / 2). */
 fr_status fr_decrypt(const fr_ctx* ctx, const fr_keys* keys, const fr_ct* ct, double* slots, size_t n_slots);
 
 /* Export / import ciphertext words (format above). `words` must be >= 2 (level+1) N. */
@@ -177,6 +184,8 @@ uint64_t fr_launch_count(const fr_ctx* ctx);
 fr_status fr_ctx_primes(const fr_ctx* ctx, uint64_t* out, size_t cap, size_t* n);
 fr_status fr_ctx_info(const fr_ctx* ctx, uint32_t* n_slots, uint32_t* top_level, uint32_t* n_digits,
                       uint64_t* resident_bytes);
+/* Level at which fr_match computes (see fr_params.level_mode). */
+uint32_t fr_work_level(const fr_ctx* ctx);
 
 /* Chebyshev coefficients c_0..c_n of the step interpolant (host, no context). */
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out);

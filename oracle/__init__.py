@@ -95,6 +95,7 @@ def _declare(L):
     L.or_encrypt.argtypes = [vp, vp, f64p, C.c_uint64, u64p]
     L.or_decrypt_coeffs.argtypes = [vp, vp, u64p, C.c_int, i64p]
     L.or_decrypt.argtypes = [vp, vp, u64p, C.c_int, C.c_double, f64p]
+    L.or_decrypt_values.argtypes = [vp, vp, u64p, C.c_int, f64p]
     L.or_hoisted_rotate.argtypes = [vp, vp, u64p, C.c_int, np.ctypeslib.ndpointer(np.int64), C.c_int, u64p]
     L.or_rotate.argtypes = [vp, vp, u64p, C.c_int, C.c_long, u64p]
     L.or_rescale.argtypes = [vp, u64p, C.c_int, u64p]
@@ -110,15 +111,16 @@ def _declare(L):
     L.or_rotate_sum.argtypes = [vp, vp, u64p, C.c_int, C.c_int]
     L.or_diag_slots.argtypes = [f32p, C.c_long, C.c_int, C.c_int, C.c_long, C.c_int, C.c_long, f64p]
     L.or_bsgs_scores.restype = C.c_int
-    L.or_bsgs_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, C.c_int, u64p]
+    L.or_bsgs_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_bsgs_scores_range.restype = C.c_int
-    L.or_bsgs_scores_range.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, u64p]
+    L.or_bsgs_scores_range.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       u64p]
     L.or_giant_step.restype = C.c_int
-    L.or_giant_step.argtypes = [vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_long, C.c_int, u64p]
+    L.or_giant_step.argtypes = [vp, u64p, C.c_int, C.c_int, f32p, C.c_long, C.c_int, C.c_long, C.c_int, u64p]
     L.or_diag_scores.restype = C.c_int
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
-    L.or_match.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+    L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                            u64p, C.POINTER(C.c_int)]
     L.or_set_threads.argtypes = [C.c_int]
     L.or_get_threads.restype = C.c_int
@@ -275,6 +277,11 @@ class Keys:
         self.L.or_decrypt_coeffs(self.ctx.h, self.h, np.ascontiguousarray(ct, dtype=np.uint64), level, x)
         return x
 
+    def decrypt_values(self, ct, level):
+        x = np.empty(self.ctx.N, dtype=np.float64)
+        self.L.or_decrypt_values(self.ctx.h, self.h, np.ascontiguousarray(ct, dtype=np.uint64), level, x)
+        return x
+
     def decrypt(self, ct, level, scale=None):
         c = self.ctx
         scale = float(2.0 ** c.scale_bits) if scale is None else float(scale)
@@ -314,26 +321,30 @@ class Keys:
         self.L.or_rotate_sum(self.ctx.h, self.h, x, level, int(steps))
         return x
 
-    def bsgs_scores(self, qct, T, ell, n1):
+    def bsgs_scores(self, qct, T, ell, n1, level=None):
+        """Scores at level-1 of a query ct at `level` (default: the top level)."""
         c = self.ctx
+        level = c.top if level is None else level
         T = np.ascontiguousarray(T, dtype=np.float32)
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
-        out = np.empty((G, 2, c.top, c.N), dtype=np.uint64)
-        r = self.L.or_bsgs_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), T, K, ell, n1, out)
+        out = np.empty((G, 2, level, c.N), dtype=np.uint64)
+        r = self.L.or_bsgs_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, T, K, ell, n1,
+                                  out)
         if r < 0:
             raise ValueError("bad BSGS parameters")
         return out
 
-    def bsgs_scores_range(self, qct, T, ell, n1, j0, j1):
+    def bsgs_scores_range(self, qct, T, ell, n1, j0, j1, level=None):
         """Scores restricted to giant steps j0 <= j < j1 (a bounded sample of the BSGS work)."""
         c = self.ctx
+        level = c.top if level is None else level
         T = np.ascontiguousarray(T, dtype=np.float32)
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
-        out = np.empty((G, 2, c.top, c.N), dtype=np.uint64)
-        r = self.L.or_bsgs_scores_range(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), T, K, ell, n1,
-                                        int(j0), int(j1), out)
+        out = np.empty((G, 2, level, c.N), dtype=np.uint64)
+        r = self.L.or_bsgs_scores_range(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, T, K, ell,
+                                        n1, int(j0), int(j1), out)
         if r < 0:
             raise ValueError("bad BSGS parameters")
         return out
@@ -342,9 +353,10 @@ class Keys:
         """One giant step (diagonal encodes, MAC, rescale) on evaluation-form babies [n1][2][L+1][N]."""
         c = self.ctx
         T = np.ascontiguousarray(T, dtype=np.float32)
-        P = np.empty((2, c.top, c.N), dtype=np.uint64)
-        r = self.L.or_giant_step(c.h, np.ascontiguousarray(babies_eval, dtype=np.uint64), int(n1), T, T.shape[0],
-                                 int(ell), int(g), int(j), P)
+        level = babies_eval.shape[2] - 1
+        P = np.empty((2, level, c.N), dtype=np.uint64)
+        r = self.L.or_giant_step(c.h, np.ascontiguousarray(babies_eval, dtype=np.uint64), int(level), int(n1), T,
+                                 T.shape[0], int(ell), int(g), int(j), P)
         if r < 0:
             raise ValueError("bad giant step")
         return P
@@ -360,15 +372,17 @@ class Keys:
             raise ValueError("bad parameters")
         return out
 
-    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5):
+    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None):
+        """Full match of a top-level query ct, computed at working level `level` (default: top)."""
         c = self.ctx
+        lq = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
         cnt = 1 if mode == MODE_MEMBERSHIP else G
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
-        r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), T, K, ell, n1, mode,
+        r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
                             int(cheb_n), float(tau), out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")

@@ -545,16 +545,23 @@ void or_encode(const or_ctx* c, const double* z, int level, int scale_bits, u64*
     free(m);
 }
 
-/* decode of integer coefficients x (length N): z_j = Re m(zeta^(5^j)) / scale */
-void or_decode_coeffs(const or_ctx* c, const int64_t* x, double scale, double* z) {
+/* decode of coefficients x (length N): z_j = Re m(zeta^(5^j)) / scale */
+static void decode_values(const or_ctx* c, const double* x, double scale, double* z) {
     int n = c->n / 2;
     double* re = (double*)malloc(sizeof(double) * n);
     double* im = (double*)malloc(sizeof(double) * n);
-    for (int k = 0; k < n; k++) { re[k] = (double)x[k]; im[k] = (double)x[k + n]; }
+    for (int k = 0; k < n; k++) { re[k] = x[k]; im[k] = x[k + n]; }
     fft_special_fwd(c, re, im);
     for (int j = 0; j < n; j++) z[j] = re[j] / scale;
     free(re);
     free(im);
+}
+
+void or_decode_coeffs(const or_ctx* c, const int64_t* x, double scale, double* z) {
+    double* v = (double*)malloc(sizeof(double) * c->n);
+    for (int k = 0; k < c->n; k++) v[k] = (double)x[k];
+    decode_values(c, v, scale, z);
+    free(v);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -733,10 +740,48 @@ void or_decrypt_coeffs(const or_ctx* c, const or_keys* k, const u64* ct, int lev
     free(t);
 }
 
+/* m = c0 + c1 s as real numbers: centered CRT of limbs 0 and 1 when level >= 1
+ * (|m| < q0 q1 / 2), limb 0 alone at level 0. */
+void or_decrypt_values(const or_ctx* c, const or_keys* k, const u64* ct, int level, double* x) {
+    int N = c->n;
+    int nl = level >= 1 ? 2 : 1;
+    u64* v[2];
+    for (int i = 0; i < nl; i++) {
+        u64 q = c->p[i];
+        const u64* c0 = ct + (size_t)i * N;
+        const u64* c1 = ct + (size_t)(level + 1 + i) * N;
+        u64* s0 = (u64*)malloc(sizeof(u64) * N);
+        v[i] = (u64*)malloc(sizeof(u64) * N);
+        for (int j = 0; j < N; j++) s0[j] = mred_s(k->s[j], q);
+        ring_mul(c, i, c1, s0, v[i]);
+        for (int j = 0; j < N; j++) v[i][j] = madd(v[i][j], c0[j], q);
+        free(s0);
+    }
+    if (nl == 1) {
+        u64 q = c->p[0];
+        for (int j = 0; j < N; j++) x[j] = (v[0][j] > (q - 1) / 2) ? -(double)(q - v[0][j]) : (double)v[0][j];
+        free(v[0]);
+        return;
+    }
+    u64 q0 = c->p[0], q1 = c->p[1];
+    u64 q0inv = minv(q0 % q1, q1);
+    u128 Q = (u128)q0 * q1;
+    for (int j = 0; j < N; j++) {
+        u64 h = mmul(msub(v[1][j], v[0][j] % q1, q1), q0inv, q1);
+        u128 y = (u128)v[0][j] + (u128)q0 * h;   /* in [0, q0 q1) */
+        if (y > (Q - 1) / 2) x[j] = -(double)(Q - y);
+        else x[j] = (double)y;
+    }
+    free(v[0]);
+    free(v[1]);
+}
+
+static void decode_values(const or_ctx* c, const double* x, double scale, double* z);
+
 void or_decrypt(const or_ctx* c, const or_keys* k, const u64* ct, int level, double scale, double* z) {
-    int64_t* x = (int64_t*)malloc(sizeof(int64_t) * c->n);
-    or_decrypt_coeffs(c, k, ct, level, x);
-    or_decode_coeffs(c, x, scale, z);
+    double* x = (double*)malloc(sizeof(double) * c->n);
+    or_decrypt_values(c, k, ct, level, x);
+    decode_values(c, x, scale, z);
     free(x);
 }
 
@@ -1199,11 +1244,11 @@ static void ct_to_eval(const or_ctx* c, const u64* ct, int l, u64* out) {
 /* scores: out [G][2][L][N] at level L-1 (L = top level).                    */
 /* ------------------------------------------------------------------------ */
 /* One giant step j of group g (Algorithm 5, inner loop): babies B_i in evaluation
- * form [n1][2][L+1][N]; P = Rescale(sum_{i < n1, j n1 + i < ell} B_i (.) D'_{g, j n1 + i}),
+ * form [n1][2][L+1][N] at level L; P = Rescale(sum_{i < n1, j n1 + i < ell} B_i (.) D'_{g, j n1 + i}),
  * written at level L-1 ([2][L][N], coefficient form). */
-int or_giant_step(const or_ctx* c, const u64* babies, int n1, const float* T, long K, int ell, long g, int j,
+int or_giant_step(const or_ctx* c, const u64* babies, int L, int n1, const float* T, long K, int ell, long g, int j,
                   u64* P) {
-    int N = c->n, L = c->nq - 1;
+    int N = c->n;
     size_t cw = ct_words(c, L);
     int cnt = (j * n1 + n1 <= ell) ? n1 : ell - j * n1;
     if (cnt <= 0) return -1;
@@ -1232,10 +1277,11 @@ int or_giant_step(const or_ctx* c, const u64* babies, int n1, const float* T, lo
     return 0;
 }
 
-/* On-demand BSGS over giant steps j_begin <= j < j_end (all steps: 0..n2) */
-int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell,
+/* On-demand BSGS over giant steps j_begin <= j < j_end (all steps: 0..n2); the
+ * query ct is at level L (the working level), scores come out at level L-1. */
+int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
                          int n1, int j_begin, int j_end, u64* out) {
-    int N = c->n, L = c->nq - 1, n = N / 2;
+    int N = c->n, n = N / 2;
     if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
     int n2 = (ell + n1 - 1) / n1;
     if (j_begin < 0) j_begin = 0;
@@ -1254,7 +1300,7 @@ int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, cons
         u64* S = out + (size_t)g * cw1;
         memset(S, 0, sizeof(u64) * cw1);
         for (int j = j_begin; j < j_end; j++) {
-            or_giant_step(c, babies, n1, T, K, ell, g, j, P);
+            or_giant_step(c, babies, L, n1, T, K, ell, g, j, P);
             if (j > 0) {
                 or_rotate(c, k, P, L - 1, (long)j * n1, R);
                 or_add(c, S, R, L - 1, S);
@@ -1267,9 +1313,9 @@ int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, cons
     return (int)G;
 }
 
-int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell,
+int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
                    int n1, u64* out) {
-    return or_bsgs_scores_range(c, k, qct, T, K, ell, n1, 0, ell, out);
+    return or_bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, out);
 }
 
 /* Naive diagonal method (Eq. equ:diag), one hoisted rotation per diagonal and a
@@ -1307,28 +1353,35 @@ int or_diag_scores(const or_ctx* c, const or_keys* k, const u64* qct, const floa
     return (int)G;
 }
 
-/* Full match (Algorithms 5 and 6). mode 0: scores (G cts, level L-1);
- * mode 1: identification (G cts of p(S_k), level L-1-d2);
- * mode 2: membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots).
+/* Full match (Algorithms 5 and 6). The top-level query is first dropped to the
+ * working level lq (lq = top: the whole chain). mode 0: scores (G cts, level
+ * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
+ * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots).
  * Returns the number of output cts; *out_level receives their level. */
-int or_match(const or_ctx* c, or_keys* k, const u64* qct, const float* T, long K, int ell, int n1, int mode,
+int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
              int cheb_n, double tau, u64* out, int* out_level) {
-    int L = c->nq - 1, n = c->n / 2;
+    int top = c->nq - 1, n = c->n / 2;
+    if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
+    u64* q = (u64*)malloc(sizeof(u64) * ct_words(c, top));
+    or_drop(c, qct, top, lq, q);
     if (mode == 0) {
-        int r = or_bsgs_scores(c, k, qct, T, K, ell, n1, out);
-        *out_level = L - 1;
+        int r = or_bsgs_scores(c, k, q, lq, T, K, ell, n1, out);
+        *out_level = lq - 1;
+        free(q);
         return r;
     }
     int d1, d2;
     or_ps_split(cheb_n, &d1, &d2);
-    if (d1 != 2 || L - 1 - d2 < 0) return -1;
-    int lo = L - 1 - d2;
-    u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, L - 1) * G);
-    if (or_bsgs_scores(c, k, qct, T, K, ell, n1, S) < 0) { free(S); return -1; }
+    if (d1 != 2 || lq - 1 - d2 < 0) { free(q); return -1; }
+    int lo = lq - 1 - d2;
+    u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
+    if (or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S) < 0) { free(S); free(q); return -1; }
+    free(q);
     size_t cwo = ct_words(c, lo);
     if (mode == 1) {
-        for (long g = 0; g < G; g++) or_cheb_eval(c, k, S + (size_t)g * ct_words(c, L - 1), L - 1, cheb_n, tau, out + g * cwo);
+        for (long g = 0; g < G; g++)
+            or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, out + g * cwo);
         *out_level = lo;
         free(S);
         return (int)G;
@@ -1336,7 +1389,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, const float* T, long K
     u64* t = (u64*)malloc(sizeof(u64) * cwo);
     memset(out, 0, sizeof(u64) * cwo);
     for (long g = 0; g < G; g++) {
-        or_cheb_eval(c, k, S + (size_t)g * ct_words(c, L - 1), L - 1, cheb_n, tau, t);
+        or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, t);
         or_add(c, out, t, lo, out);
     }
     int steps = 0;

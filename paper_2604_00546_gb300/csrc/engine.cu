@@ -85,6 +85,7 @@ struct fr_ctx {
     double tau = 0.5;
     uint64_t budget = 0;
     int d1 = 0, d2 = 0;
+    int work_level = 0;                  // level of the query inside fr_match
     std::vector<ModUpTab*> d_modup;      // per level: digits_at(level) tables
     std::vector<int*> d_modup_ntt;       // per level: (offset, prime) of the ext positions to transform
     std::vector<int> modup_ntt_n;
@@ -552,17 +553,19 @@ fr_ct* new_dev_ct(fr_ctx* c, std::shared_ptr<DevBlock> blk, u64* p, int level, i
 }
 std::shared_ptr<DevBlock> new_block(fr_ctx* c, size_t words) { return std::make_shared<DevBlock>(c, dalloc(c, words)); }
 
-// device copy of a ciphertext (evaluation form); host cts are uploaded
-void to_device(fr_ctx* c, const fr_ct* ct, u64* dst, int cap) {
+// device copy of a ciphertext (evaluation form) with limbs 0..level (level < 0: all);
+// host cts are uploaded (only the kept limbs cross the bus)
+void to_device(fr_ctx* c, const fr_ct* ct, u64* dst, int cap, int level = -1) {
     const int N = c->R.N;
+    if (level < 0) level = ct->level;
     if (ct->on_dev) {
-        copy_cts(c, dst, cap, ct->dev, ct->cap, 1, ct->level);
+        copy_cts(c, dst, cap, ct->dev, ct->cap, 1, level);
         return;
     }
-    const size_t L1 = ct->level + 1;
-    CU(cudaMemcpy2DAsync(dst, (size_t)cap * N * 8, ct->host.data(), L1 * N * 8, L1 * N * 8, 2,
+    const size_t L1 = ct->level + 1, K1 = level + 1;
+    CU(cudaMemcpy2DAsync(dst, (size_t)cap * N * 8, ct->host.data(), L1 * N * 8, K1 * N * 8, 2,
                          cudaMemcpyHostToDevice, c->stream));
-    ntt_cts(c, dst, 1, ct->level, cap, false);
+    ntt_cts(c, dst, 1, level, cap, false);
 }
 
 void export_words(fr_ctx* c, const fr_ct* ct, u64* buf) {
@@ -775,6 +778,9 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
             build_leaves(c.get());
         }
         c->host_threads = std::max(1u, std::thread::hardware_concurrency());
+        if (prm->level_mode > 1) raise(FR_ERR_INVALID_ARG, "level_mode must be 0 or 1");
+        c->work_level = c->R.nq - 1;
+        if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->d2 : 0));
         if (prm->device < 0) {
             // client-only context: key generation, encryption and decryption on
             // the host; every device operation fails with FR_ERR_CUDA
@@ -907,7 +913,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
         if (!c || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
         if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
         CU(cudaSetDevice(c->device));
-        const int N = c->R.N, n = N / 2, nl = c->R.nq;
+        const int N = c->R.N, n = N / 2, nl = c->work_level + 1;
         std::unique_ptr<fr_db> db(new fr_db());
         db->ctx = c;
         db->K = (long long)K;
@@ -1069,10 +1075,10 @@ fr_status fr_decrypt(const fr_ctx* c, const fr_keys* k, const fr_ct* ct, double*
         const int N = c->R.N;
         std::vector<u64> w((size_t)2 * (ct->level + 1) * N);
         export_words(const_cast<fr_ctx*>(c), ct, w.data());
-        std::vector<int64_t> x(N);
-        frh::decrypt_coeffs(c->R, k->ks, w.data(), ct->level, x.data());
+        std::vector<double> x(N);
+        frh::decrypt_values(c->R, k->ks, w.data(), ct->level, x.data());
         std::vector<double> z(N / 2);
-        frh::decode_coeffs(c->R, x.data(), ct->scale, z.data());
+        frh::decode_values(c->R, x.data(), ct->scale, z.data());
         for (size_t i = 0; i < n_slots && i < z.size(); ++i) slots[i] = z[i];
     });
 }
@@ -1223,8 +1229,8 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
         if (!c || !db || !query || !out || !n_out) raise(FR_ERR_INVALID_ARG, "null argument");
         if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
         check_ct(c, query);
-        const int L = c->R.nq - 1;
-        if (query->level != L) raise(FR_ERR_LEVEL, "the query must be at the top level");
+        if (query->level != c->R.nq - 1) raise(FR_ERR_LEVEL, "the query must be at the top level");
+        const int L = c->work_level;
         if ((size_t)c->n1 * 2 * 128 * 8 > 200 * 1024)
             raise(FR_ERR_UNSUPPORTED, "n1 > 100: the MAC stages 2 n1 baby words per point in shared memory");
         if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
@@ -1236,7 +1242,7 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
         const int L1 = L + 1;
         // S1: query ingest (one H2D if host-resident) and baby steps B_i = Rot_i(q), hoisted (S2)
         Tmp babies(c, (size_t)n1 * ctw(c, L1));
-        to_device(c, query, babies.p, L1);
+        to_device(c, query, babies.p, L1, L);
         if (n1 > 1) {
             std::vector<long> ks;
             std::vector<u64*> outs;
@@ -1367,6 +1373,8 @@ fr_status fr_ctx_info(const fr_ctx* c, uint32_t* n_slots, uint32_t* top_level, u
     if (resident_bytes) *resident_bytes = c->resident;
     return FR_OK;
 }
+
+uint32_t fr_work_level(const fr_ctx* c) { return c ? (uint32_t)c->work_level : 0; }
 
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
     if (!out) return FR_ERR_INVALID_ARG;

@@ -70,6 +70,7 @@ void sample_uniform(u64 seed, u64 obj, uint32_t limb, u64 q, int n, u64* out);
 // slot encoding of n = N/2 real values at scale 2^scale_bits into integer coefficients
 void encode_coeffs(const Ring& R, const double* z, int scale_bits, int64_t* m);
 void decode_coeffs(const Ring& R, const int64_t* x, double scale, double* z);
+void decode_values(const Ring& R, const double* x, double scale, double* z);
 
 // Keys. Key-switching keys are [ndig][2][nq+np][N] in evaluation form.
 struct KeySet {
@@ -83,6 +84,8 @@ struct KeySet {
 void keygen(const Ring& R, u64 seed, const std::vector<u64>& galois, KeySet& K, int nthreads);
 void encrypt(const Ring& R, const KeySet& K, const double* z, u64 seed, u64* out /*[2][nq][N] coeff*/);
 void decrypt_coeffs(const Ring& R, const KeySet& K, const u64* ct, int level, int64_t* x);
+// plaintext coefficients as reals: centered CRT of limbs 0 and 1 (level >= 1) or limb 0
+void decrypt_values(const Ring& R, const KeySet& K, const u64* ct, int level, double* x);
 
 // Chebyshev interpolant of step(x - tau) at n+1 Chebyshev nodes; PS split.
 void cheb_coeffs(int n, double tau, std::vector<double>& c);

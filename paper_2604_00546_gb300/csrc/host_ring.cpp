@@ -346,10 +346,15 @@ void encode_coeffs(const Ring& R, const double* z, int scale_bits, int64_t* m) {
 }
 
 void decode_coeffs(const Ring& R, const int64_t* x, double scale, double* z) {
+    std::vector<double> v(x, x + R.N);
+    decode_values(R, v.data(), scale, z);
+}
+
+void decode_values(const Ring& R, const double* x, double scale, double* z) {
     const int n = R.N / 2;
     const u64 M = 2 * (u64)R.N;
     std::vector<double> re(n), im(n);
-    for (int k = 0; k < n; ++k) { re[k] = (double)x[k]; im[k] = (double)x[k + n]; }
+    for (int k = 0; k < n; ++k) { re[k] = x[k]; im[k] = x[k + n]; }
     bitrev_permute(re, im);
     for (int len = 2; len <= n; len <<= 1) {
         const int h = len >> 1;
@@ -509,6 +514,34 @@ void decrypt_coeffs(const Ring& R, const KeySet& K, const u64* ct, int level, in
     for (int j = 0; j < N; ++j) {
         u64 v = addm(a[j], ct[j], q);
         x[j] = v > (q - 1) / 2 ? -(int64_t)(q - v) : (int64_t)v;
+    }
+}
+
+void decrypt_values(const Ring& R, const KeySet& K, const u64* ct, int level, double* x) {
+    const int N = R.N;
+    const int nl = level >= 1 ? 2 : 1;
+    std::vector<std::vector<u64>> m(nl);
+    for (int i = 0; i < nl; ++i) {
+        const u64 q = R.primes[i];
+        m[i].assign(ct + (size_t)(level + 1 + i) * N, ct + (size_t)(level + 2 + i) * N);
+        ntt_fwd(R, i, m[i].data());
+        for (int j = 0; j < N; ++j) m[i][j] = mulm(m[i][j], K.s_eval[(size_t)i * N + j], q);
+        ntt_inv(R, i, m[i].data());
+        for (int j = 0; j < N; ++j) m[i][j] = addm(m[i][j], ct[(size_t)i * N + j], q);
+    }
+    const u64 q0 = R.primes[0];
+    if (nl == 1) {
+        for (int j = 0; j < N; ++j) x[j] = m[0][j] > (q0 - 1) / 2 ? -(double)(q0 - m[0][j]) : (double)m[0][j];
+        return;
+    }
+    const u64 q1 = R.primes[1];
+    const u64 q0inv = invm(q0 % q1, q1);
+    const u128 Q = (u128)q0 * q1;
+    for (int j = 0; j < N; ++j) {
+        // x = m0 + q0 * ((m1 - m0) q0^-1 mod q1), centered in (-Q/2, Q/2]
+        const u64 h = mulm(subm(m[1][j], m[0][j] % q1, q1), q0inv, q1);
+        const u128 y = (u128)m[0][j] + (u128)q0 * h;
+        x[j] = y > (Q - 1) / 2 ? -(double)(Q - y) : (double)y;
     }
 }
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "fr_load_db", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
-    "fr_ctx_primes", "fr_ctx_info", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
+    "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error",
 ]
 
@@ -49,6 +49,7 @@ class Params(C.Structure):
         ("p_bits", C.POINTER(C.c_uint32)), ("dnum", C.c_uint32), ("scale_bits", C.c_uint32), ("ell", C.c_uint32),
         ("n1", C.c_uint32), ("schedule", C.c_uint32), ("cheb_degree", C.c_uint32), ("threshold", C.c_double),
         ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
+        ("level_mode", C.c_uint32),
     ]
 
 
@@ -107,6 +108,7 @@ def load(build_if_missing: bool = True):
         "fr_ctx_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                              C.POINTER(C.c_uint64)]),
         "fr_cheb_coeffs": (st, [C.c_uint32, C.c_double, f64p]),
+        "fr_work_level": (C.c_uint32, [vp]),
         "fr_free_ct": (None, [vp]),
         "fr_free_cts": (None, [C.POINTER(vp), C.c_size_t]),
         "fr_free_keys": (None, [vp]),
@@ -170,13 +172,13 @@ class Context:
     """fr_ctx: parameters, primes, device tables."""
 
     def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
-                 hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0):
+                 hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0):
         L = load()
         self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
         self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
-                             C.c_void_p(cuda_stream) if cuda_stream else None)
+                             C.c_void_p(cuda_stream) if cuda_stream else None, level_mode)
         h = C.c_void_p()
         _check(L.fr_setup(C.byref(self.params), C.byref(h)))
         self.h = h
@@ -186,6 +188,7 @@ class Context:
         self.n1 = n1
         self.nq = len(q_bits)
         self.top = self.nq - 1
+        self.work_level = int(L.fr_work_level(self.h))
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -18,6 +18,9 @@ CONFIGS = {
     # mid-size parity case: several NTT tiles, two template groups with a ragged tail, full threshold
     "mid": dict(log_n=13, q_bits=[60] + [45] * 8, p_bits=[60, 60, 60], dnum=3, scale_bits=45, ell=64, n1=8,
                 cheb_degree=59, threshold=0.5, K=5000, mode=2, seed=6),
+    # deeper chain than the threshold needs: the match runs at a lower working level
+    "deep": dict(log_n=13, q_bits=[60] + [45] * 11, p_bits=[60, 60, 60], dnum=4, scale_bits=45, ell=64, n1=8,
+                 cheb_degree=59, threshold=0.5, K=5000, mode=2, seed=7, level_mode=1),
     # membership at the headline size: N=2^16, Q = 60 + 24 x 50, P = 4 x 60, dnum 6, Delta 2^50,
     # K = 2^15 templates of ell = 512, 32 near-duplicates at cosine 0.8, degree-59 threshold
     "membership": dict(log_n=16, q_bits=[60] + [50] * 24, p_bits=[60] * 4, dnum=6, scale_bits=50, ell=512, n1=32,
@@ -32,10 +35,33 @@ KEY_SEED = 0xC0FFEE00
 ENC_SEED = 0xE0C00000
 
 
-def ctx_params(cfg):
+def ctx_params(cfg, level_mode=None):
     c = CONFIGS[cfg] if isinstance(cfg, str) else cfg
-    return {k: c[k] for k in ("log_n", "q_bits", "p_bits", "dnum", "scale_bits", "ell", "n1", "cheb_degree",
-                              "threshold")}
+    p = {k: c[k] for k in ("log_n", "q_bits", "p_bits", "dnum", "scale_bits", "ell", "n1", "cheb_degree",
+                           "threshold")}
+    p["level_mode"] = c.get("level_mode", 0) if level_mode is None else level_mode
+    return p
+
+
+def work_level(cfg, level_mode=None):
+    """Working level of the match: the top level, or 2 + d2 (capped) in level mode 1."""
+    c = CONFIGS[cfg] if isinstance(cfg, str) else cfg
+    lm = c.get("level_mode", 0) if level_mode is None else level_mode
+    top = len(c["q_bits"]) - 1
+    if lm == 0:
+        return top
+    d2 = 0
+    if c["cheb_degree"]:
+        n = c["cheb_degree"]
+        best = None
+        for d1 in range(1, n + 2):
+            b = 1
+            while d1 * 2 ** (b - 1) < n:
+                b += 1
+            if best is None or d1 + b < best[0] or (d1 + b == best[0] and d1 > best[1]):
+                best = (d1 + b, d1, b)
+        d2 = best[2]
+    return min(top, 2 + d2)
 
 
 def templates(K, ell, seed):

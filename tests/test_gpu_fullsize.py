@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 CFG = "membership"
 
 
-@pytest.fixture(scope="module")
-def env():
+@pytest.fixture(scope="module", params=[0, 1], ids=["full_chain", "working_level"])
+def env(request):
     c = W.CONFIGS[CFG]
-    ctx = fr.Context(device=0, **W.ctx_params(CFG))
+    ctx = fr.Context(device=0, **W.ctx_params(CFG, level_mode=request.param))
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(CFG))
     ctx.load_keys(keys)
     T, q, planted = W.workload(CFG)
@@ -32,7 +32,8 @@ def env():
     qct = ctx.encrypt(keys, q, W.enc_seed(CFG))
     s = T.astype(np.float64) @ q
     p = np.polynomial.chebyshev.chebval(s, fr.cheb_coeffs(c["cheb_degree"], c["threshold"]))
-    return dict(c=c, ctx=ctx, keys=keys, T=T, q=q, planted=planted, db=db, qct=qct, s=s, p=p)
+    return dict(c=c, ctx=ctx, keys=keys, T=T, q=q, planted=planted, db=db, qct=qct, s=s, p=p,
+                lq=ctx.work_level)
 
 
 def test_scores_bit_exact_vs_oracle(env):
@@ -43,7 +44,8 @@ def test_scores_bit_exact_vs_oracle(env):
     ok = oc.keygen(W.key_seed(CFG))
     oq = ok.encrypt(np.tile(env["q"], oc.n // c["ell"]), W.enc_seed(CFG))
     assert np.array_equal(env["qct"].export(), oq)
-    ref = ok.bsgs_scores(oq, env["T"], c["ell"], c["n1"])
+    lq = env["lq"]
+    ref = ok.bsgs_scores(oc.drop(oq, oc.top, lq), env["T"], c["ell"], c["n1"], level=lq)
     assert np.array_equal(got, ref[0])
     dec = env["ctx"].decrypt(env["keys"], out[0])
     assert np.abs(dec - env["s"]).max() < 1e-4
@@ -63,7 +65,7 @@ def test_identification_decisions(env):
 
 def test_membership_sum(env):
     out = env["ctx"].match(env["db"], env["qct"], fr.FR_MODE_MEMBERSHIP)
-    assert len(out) == 1 and out[0].level == 24 - 1 - 6
+    assert len(out) == 1 and out[0].level == env["lq"] - 1 - 6
     dec = env["ctx"].decrypt(env["keys"], out[0])
     assert abs(dec[0] - env["p"].sum()) < 1e-2
     assert np.abs(dec - env["p"].sum()).max() < 1e-2

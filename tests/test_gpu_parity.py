@@ -42,6 +42,11 @@ def mid():
     return Env("mid", extra_rots=[3])
 
 
+@pytest.fixture(scope="module")
+def deep():
+    return Env("deep")
+
+
 def dev_copy(env, words, level):
     ct = env.ctx.import_ct(words, level)
     ct.upload()
@@ -188,3 +193,26 @@ def test_match_threshold_modes_mid(mid, mode):
     else:
         dec = mid.ctx.decrypt(mid.keys, out[0])
         assert abs(dec[0] - p.sum()) < 1e-2
+
+
+@pytest.mark.parametrize("mode", [fr.FR_MODE_SCORES, fr.FR_MODE_IDENTIFY, fr.FR_MODE_MEMBERSHIP])
+def test_match_at_working_level_deep(deep, mode):
+    """level_mode 1: the top-level query (11) is dropped to level 8 before the BSGS product."""
+    assert deep.ctx.work_level == 8 == W.work_level("deep")
+    db = deep.ctx.load_db(deep.T)
+    out = deep.ctx.match(db, deep.qct, mode)
+    ref, lvl = deep.ok.match(deep.oq, deep.T, deep.cfg["ell"], deep.cfg["n1"], mode, 59, 0.5, level=8)
+    assert len(out) == len(ref)
+    for g in range(len(out)):
+        assert out[g].level == lvl
+        assert np.array_equal(out[g].export(), ref[g]), g
+    s = deep.T.astype(np.float64) @ deep.q
+    if mode == fr.FR_MODE_SCORES:
+        dec = np.concatenate([deep.ctx.decrypt(deep.keys, o) for o in out])
+        assert np.abs(dec[: len(s)] - s).max() < 1e-4
+    elif mode == fr.FR_MODE_MEMBERSHIP:
+        n = deep.oc.n
+        sp = np.zeros(((len(s) + n - 1) // n) * n)
+        sp[: len(s)] = s
+        p = np.polynomial.chebyshev.chebval(sp, oracle.cheb_coeffs(59, 0.5))
+        assert abs(deep.ctx.decrypt(deep.keys, out[0])[0] - p.sum()) < 1e-2

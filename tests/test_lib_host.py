@@ -128,3 +128,26 @@ def test_required_rotations_of_context():
     assert s == list(range(1, 32)) + [32 * j for j in range(1, 16)]
     m = ctx.required_rotations(fr.FR_MODE_MEMBERSHIP)
     assert set(m) == set(s) | {1 << t for t in range(15)}
+
+
+def test_client_decrypt_crt_matches_oracle():
+    params = dict(log_n=10, q_bits=[40, 40, 40], p_bits=[60, 60], dnum=1, scale_bits=30, ell=32, n1=4)
+    ctx = fr.Context(device=-1, **params)
+    oc = oracle.Ctx(10, [40, 40, 40], [60, 60], 1, 30)
+    ok = oc.keygen(3)
+    keys = ctx.keygen([], 3)
+    rng = np.random.default_rng(2)
+    z = 2500.0 + rng.uniform(-1, 1, oc.n)
+    ct = ok.encrypt(z, 4)
+    for lvl in (2, 1):
+        w = oc.drop(ct, 2, lvl)
+        got = ctx.decrypt(keys, ctx.import_ct(w, lvl))
+        assert np.abs(got - z).max() < 1e-4
+        assert got.tobytes() == ok.decrypt(w, lvl).tobytes()
+
+
+def test_work_level_of_contexts():
+    for cfg, lm, expect in [("membership", 0, 24), ("membership", 1, 8), ("tiny", 1, 2), ("deep", 1, 8),
+                            ("mid", 1, 8)]:
+        ctx = fr.Context(device=-1, **W.ctx_params(cfg, level_mode=lm))
+        assert ctx.work_level == expect == W.work_level(cfg, lm)

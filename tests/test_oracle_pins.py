@@ -508,3 +508,40 @@ def test_match_modes_small():
     memb, lvl2 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5)
     m = k.decrypt(memb[0], lvl2)
     assert abs(m[0] - p.sum()) < 1e-2 and np.abs(m - p.sum()).max() < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# Decryption range and the working level
+# ---------------------------------------------------------------------------
+def test_decrypt_crt_two_limbs_beyond_first_prime():
+    """Values above q0 / (2 Delta) decrypt exactly from limbs 0 and 1 (centered CRT)."""
+    c = oracle.Ctx(10, [40, 40, 40], [60, 60], 1, 30)
+    k = c.keygen(3)
+    rng = np.random.default_rng(2)
+    z = 2500.0 + rng.uniform(-1, 1, c.n)     # constant term 2500 Delta > q0 / 2
+    ct = k.encrypt(z, 4)
+    assert np.abs(k.decrypt(ct, 2) - z).max() < 1e-4
+    assert np.abs(k.decrypt(c.drop(ct, 2, 1), 1) - z).max() < 1e-4
+    assert np.abs(k.decrypt(c.drop(ct, 2, 0), 0) - z).max() > 100      # one limb wraps
+
+
+def test_match_at_working_level_consistent():
+    c = oracle.Ctx(11, [60] + [40] * 10, [60, 60, 60], 4, 40)
+    k = c.keygen(41)
+    ell, K = 32, 900
+    T = _templates(K, ell, 8)
+    rng = np.random.default_rng(15)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k.encrypt(np.tile(q, c.n // ell), 5)
+    lq = 8
+    out, lvl = k.match(qct, T, ell, 4, oracle.MODE_SCORES, 59, 0.5, level=lq)
+    assert lvl == lq - 1
+    ref = k.bsgs_scores(c.drop(qct, c.top, lq), T, ell, 4, level=lq)
+    assert np.array_equal(out, ref)
+    assert np.abs(k.decrypt(out[0], lvl)[:K] - T.astype(np.float64) @ q).max() < 1e-4
+    memb, lvl2 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, level=lq)
+    assert lvl2 == 1
+    s = np.concatenate([T.astype(np.float64) @ q, np.zeros(c.n - K)])
+    p = np.polynomial.chebyshev.chebval(s, oracle.cheb_coeffs(59, 0.5))
+    assert abs(k.decrypt(memb[0], 1)[0] - p.sum()) < 1e-2
