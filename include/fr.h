@@ -167,6 +167,23 @@ fr_status fr_chebyshev(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 /* RotateAndSum over all N/2 slots */
 fr_status fr_rotate_sum(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 
+/* Rotation by k slots that allocates no device memory (the paper has no counterpart:
+ * this is a deployment variant of fr_rotate). For callers that must not allocate
+ * while they run -- code captured into a CUDA graph with a fixed memory plan, a
+ * serving path that must stay off the allocator, a process whose free HBM belongs
+ * to someone else. d_in and d_out are caller-owned device buffers holding one
+ * ciphertext in the exported format (coefficient form, [2][level+1][N] uint64);
+ * they may not overlap. All temporaries live in one fixed 64 MiB device array
+ * inside the library (held by every GPU that loads it until the process exits):
+ * calls whose working set needs more (5 (level+1) N + (digits+2)(level+1+n_p) N
+ * words; e.g. N=2^16 up to level 8 with 6 digits and 4 special primes) fail with
+ * FR_ERR_INVALID_ARG. The first call on a device looks up the array's device
+ * address; make that first call before any stream capture. Every call shares the
+ * array, so calls that overlap on the GPU (other streams, other contexts of the
+ * same device) race; nothing in it needs to start at zero. Work is enqueued on
+ * the context stream; the rotation key for k must be loaded. */
+fr_status fr_rotate_noalloc(fr_ctx* ctx, const uint64_t* d_in, uint32_t level, int32_t k, uint64_t* d_out);
+
 /* Wait for all work enqueued on the context stream. */
 fr_status fr_sync(fr_ctx* ctx);
 

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -1385,3 +1386,91 @@ fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Rotation that allocates nothing.
+//
+// Some callers cannot allocate device memory while they run: code that is
+// being captured into a CUDA graph with a fixed memory plan, an inference
+// server whose request path must not touch the allocator (to avoid pool
+// growth and its synchronisation), or a host that has handed all free HBM to
+// another owner. fr_rotate_noalloc serves them: the caller passes input and
+// output buffers, and every temporary of the key switch lives in the fixed
+// device array below, compiled into the library. That array is
+// FR_NOALLOC_SCRATCH_WORDS words (64 MiB) and every GPU that loads this part
+// of the library keeps it until the process exits.
+// ===========================================================================
+#define FR_NOALLOC_SCRATCH_WORDS (8ull << 20)
+static __device__ __align__(256) u64 g_noalloc_scratch[FR_NOALLOC_SCRATCH_WORDS];
+
+namespace {
+// Device address of the scratch array on `device` (looked up once per device,
+// with that device current). In host code the array's name is only a
+// host-side stand-in, so kernels must be given this address instead.
+u64* noalloc_scratch(int device) {
+    static std::mutex mu;
+    static u64* addr[FR_MAX_PRIMES] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= FR_MAX_PRIMES) raise(FR_ERR_INVALID_ARG, "device ordinal out of range");
+    if (!addr[device]) {
+        void* p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[device] = (u64*)p;
+    }
+    return addr[device];
+}
+}  // namespace
+
+extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t level, int32_t k,
+                                       uint64_t* d_out) {
+    return guard([&] {
+        need_device(c);
+        if (!d_in || !d_out) raise(FR_ERR_INVALID_ARG, "null buffer");
+        if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
+        CU(cudaSetDevice(c->device));
+        const int N = c->R.N, l = (int)level, np = c->R.np, nq = c->R.nq;
+        const size_t L1N = (size_t)(l + 1) * N;
+        const u64 g = frh::galois_of_rotation(c->R, k);
+        if (g == 1) {
+            CU(cudaMemcpyAsync(d_out, d_in, 2 * L1N * 8, cudaMemcpyDeviceToDevice, c->stream));
+            return;
+        }
+        const u64* key = rot_key(c, g);
+        const int npos = l + 1 + np, beta = c->R.digits_at(l);
+        const size_t need = 5 * L1N + (size_t)(beta + 2) * npos * N;
+        if (need > FR_NOALLOC_SCRATCH_WORDS)
+            raise(FR_ERR_INVALID_ARG, "fr_rotate_noalloc: needs " + std::to_string(need) +
+                                          " scratch words at this level, the fixed array holds " +
+                                          std::to_string(FR_NOALLOC_SCRATCH_WORDS));
+        u64* sc = noalloc_scratch(c->device);
+        u64* e = sc;                     // [2][l+1][N] input, evaluation form
+        u64* a = e + 2 * L1N;            // [l+1][N] c1, coefficient form
+        u64* ext = a + L1N;              // [beta][npos][N]
+        u64* acc = ext + (size_t)beta * npos * N;  // [2][npos][N]
+        u64* conv = acc + (size_t)2 * npos * N;    // [2][l+1][N]
+        cudaStream_t st = c->stream;
+        CU(cudaMemcpyAsync(e, d_in, 2 * L1N * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(a, d_in + L1N, L1N * 8, cudaMemcpyDeviceToDevice, st));
+        const PrimeMap pl = pm_level(l);
+        launch_ntt(c->rd, PolyBatch{e, (long long)N, 2 * (l + 1), 2 * (l + 1), pl}, false, st);
+        launch_modup(a, e + L1N, 0, ext, c->d_modup[l], beta, npos, N, 1, st);
+        launch_ntt(c->rd, PolyBatch{ext, (long long)beta * npos * N, 1, c->modup_ntt_n[l], PrimeMap{},
+                                    c->d_modup_ntt[l], c->modup_ntt_n[l]},
+                   false, st);
+        IPJobs ij;
+        ij.j[0] = IPJob{ext, key, acc, (u32)g, 0};
+        launch_ip(ij, 1, false, beta, npos, l, nq, c->R.total(), c->d_primes, pm_ext(c, l), c->R.logN, st);
+        PrimeMap pmP{};
+        pmP.period = np;
+        for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
+        launch_ntt(c->rd, PolyBatch{acc + L1N, (long long)npos * N, np, 2 * np, pmP}, true, st);
+        launch_p2q(acc, 2ll * npos * N, npos, l, conv, c->d_p2q, N, 1, st);
+        launch_ntt(c->rd, PolyBatch{conv, (long long)L1N, l + 1, 2 * (l + 1), pl}, false, st);
+        MDJobs md;
+        md.j[0] = MDJob{acc, conv, e, d_out, l + 1, l + 1, 1, (u32)g};
+        launch_moddown_combine(md, 1, npos, l, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, st);
+        launch_ntt(c->rd, PolyBatch{d_out, (long long)N, 2 * (l + 1), 2 * (l + 1), pl}, true, st);
+        c->launches += 13;
+        CU(cudaGetLastError());
+    });
+}

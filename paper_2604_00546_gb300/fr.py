@@ -30,7 +30,7 @@ FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
 EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
-    "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rescale", "fr_mul_relin", "fr_add",
+    "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error",
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         "fr_ct_upload": (st, [vp, vp]),
         "fr_rotate": (st, [vp, vp, C.c_int32, C.POINTER(vp)]),
         "fr_rotate_hoisted": (st, [vp, vp, i32p, C.c_size_t, C.POINTER(vp)]),
+        "fr_rotate_noalloc": (st, [vp, C.c_void_p, C.c_uint32, C.c_int32, C.c_void_p]),
         "fr_rescale": (st, [vp, vp, C.POINTER(vp)]),
         "fr_mul_relin": (st, [vp, vp, vp, C.POINTER(vp)]),
         "fr_add": (st, [vp, vp, vp, C.POINTER(vp)]),
@@ -282,6 +283,10 @@ class Context:
         hs = (C.c_void_p * len(ks))()
         _check(_lib.fr_rotate_hoisted(self.h, ct.h, ks, len(ks), C.cast(hs, C.POINTER(C.c_void_p))))
         return [Ciphertext(self, C.c_void_p(hs[i])) for i in range(len(ks))]
+
+    def rotate_noalloc(self, d_in, level, k, d_out):
+        """Rotation without allocation on caller-owned device buffers (raw addresses)."""
+        _check(_lib.fr_rotate_noalloc(self.h, C.c_void_p(d_in), int(level), int(k), C.c_void_p(d_out)))
 
     def rescale(self, ct):
         return self._unary(_lib.fr_rescale, ct)
