@@ -255,7 +255,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    ctx.profile(True)
     n_launch0 = ctx.launch_count()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
@@ -265,11 +264,6 @@ def run_ours(args):
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     n_launch = ctx.launch_count() - n_launch0
-    regions = {}
-    for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac", "misc"):
-        ms, nl, by = ctx.profile_read(r)
-        regions[r] = {"ms": ms, "launches": nl, "bytes": by}
-    ctx.profile(False)
     clocks = sampler.stop()
     for i in range(args.steps):
         lat.append(ev[i].elapsed_time(ev[i + 1]))
@@ -281,6 +275,21 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tmax = float(t.item())
     value = ws * K * args.steps / (tmax / 1000.0)
+
+    # per-region device time: the same steps again, eagerly, with CUDA events around every launch
+    ctx.profile(True)
+    for i in range(args.steps):
+        outs = step(ctx, db, dev_q)
+    torch.cuda.synchronize()
+    regions = {}
+    for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac", "misc"):
+        ms, nl, by = ctx.profile_read(r)
+        regions[r] = {"ms": ms, "launches": nl, "bytes": by}
+    stages = {}
+    for st in ("babies", "mac", "giants", "cheb", "sum"):
+        stages[st] = ctx.profile_read("stage:" + st)[0] / args.steps
+    ctx.profile(False)
+    del outs
 
     # end to end through the C ABI: host query -> H2D (the working-level limbs) -> match -> D2H
     h2d = 2 * (lq + 1) * (1 << c["log_n"]) * 8
@@ -356,6 +365,7 @@ def run_ours(args):
             "hbm_gbs_dominant": achieved,
             "roofline": roof,
             "regions_ms_per_step": {r: regions[r]["ms"] / args.steps for r in regions},
+            "stages_ms_per_step": stages,
             "gpu_launches": int(n_launch),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "full_chain": full,

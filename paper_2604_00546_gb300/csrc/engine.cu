@@ -15,6 +15,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -105,6 +106,7 @@ struct fr_ctx {
     std::map<std::string, Region> regions;
     uint64_t launches = 0;
     int host_threads = 1;
+    bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
 };
 
 struct fr_keys {
@@ -745,6 +747,10 @@ void build_leaves(fr_ctx* c) {
 
 DevBlock::~DevBlock() { dfree(ctx, p); }
 
+namespace {
+void drop_graphs(const fr_ctx* c, const fr_db* db);  // CUDA graphs of fr_match (defined below)
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -818,6 +824,7 @@ void fr_free(fr_ctx* c) {
     }
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c, nullptr);
     for (auto& kv : c->rotkeys) cudaFree(kv.second);
     if (c->relin) cudaFree(c->relin);
     for (void* p : c->owned) cudaFree(p);
@@ -955,6 +962,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
 
 void fr_free_db(fr_db* db) {
     if (!db) return;
+    if (db->ctx) drop_graphs(db->ctx, db);
     if (db->ctx) {
         cudaStreamSynchronize(db->ctx->stream);
         db->ctx->resident -= db->bytes;
@@ -1224,6 +1232,131 @@ fr_status fr_rotate_sum(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
 // pre-rotated diagonals (Algorithms 5 and 6; Eq. eq:prerotation), then the
 // Chebyshev threshold and, for membership, the group sum and RotateAndSum.
 // ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// shapes of the match outputs: count and level
+void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int* lo) {
+    const int L = c->work_level;
+    if (mode == FR_MODE_SCORES) {
+        *nout = (int)db->G;
+        *lo = L - 1;
+    } else {
+        *nout = mode == FR_MODE_IDENTIFY ? (int)db->G : 1;
+        *lo = L - 1 - c->d2;
+    }
+}
+
+// The whole match on a query already in HBM (evaluation form, level = work level,
+// cap = level + 1); writes the output ciphertexts (cap = level + 1) contiguously to out.
+void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64* out) {
+    const int L = c->work_level;
+    const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
+    const int n2 = (ell + n1 - 1) / n1;
+    const long long G = db->G;
+    const int L1 = L + 1;
+    // S2: baby steps B_i = Rot_i(q), hoisted (one ModUp for all of them)
+    std::unique_ptr<Prof> stage(new Prof(c, "stage:babies"));
+    Tmp babies(c, (size_t)n1 * ctw(c, L1));
+    copy_d2d(c, babies.p, q, ctw(c, L1));
+    if (n1 > 1) {
+        std::vector<long> ks;
+        std::vector<u64*> outs;
+        for (int i = 1; i < n1; ++i) {
+            ks.push_back(i);
+            outs.push_back(babies.p + (size_t)i * ctw(c, L1));
+        }
+        rotate_cts(c, L, {babies.p}, L1, ks, outs, L1, true);
+    }
+    // S3-S5 per group: MAC with pre-rotated diagonals, rescale, giant rotations, sum
+    stage.reset();
+    const bool scores_only = mode == FR_MODE_SCORES;
+    Tmp sbuf(c, scores_only ? 1 : (size_t)G * ctw(c, L));
+    u64* S = scores_only ? out : sbuf.p;
+    for (long long g = 0; g < G; ++g) {
+        stage.reset(new Prof(c, "stage:mac"));
+        Tmp Pj(c, (size_t)n2 * ctw(c, L1));
+        {
+            Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
+            launch_mac(babies.p, L1, db->diags + (size_t)g * ell * L1 * N, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N,
+                       c->stream);
+            c->launches++;
+        }
+        Tmp Gs(c, (size_t)n2 * ctw(c, L));
+        rescale(c, Pj.p, n2, L, L1, Gs.p, L);
+        stage.reset(new Prof(c, "stage:giants"));
+        if (n2 > 1) {
+            Tmp Pr(c, (size_t)(n2 - 1) * ctw(c, L));
+            copy_d2d(c, Pr.p, Gs.p + ctw(c, L), (size_t)(n2 - 1) * ctw(c, L));
+            std::vector<const u64*> in;
+            std::vector<long> ks;
+            std::vector<u64*> outs;
+            for (int j = 1; j < n2; ++j) {
+                in.push_back(Pr.p + (size_t)(j - 1) * ctw(c, L));
+                ks.push_back((long)j * n1);
+                outs.push_back(Gs.p + (size_t)j * ctw(c, L));
+            }
+            rotate_cts(c, L - 1, in, L, ks, outs, L, false);
+        }
+        Prof p(c, "misc");
+        launch_sum(Gs.p, L, ctw(c, L), n2, S + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->stream);
+        c->launches++;
+        stage.reset();
+    }
+    if (scores_only) return;
+    // S6: Chebyshev threshold on every group's scores (batched)
+    const int lo = L - 1 - c->d2;
+    if (mode == FR_MODE_IDENTIFY) {
+        stage.reset(new Prof(c, "stage:cheb"));
+        chebyshev(c, S, (int)G, L - 1, L, out, lo + 1);
+        return;
+    }
+    Tmp cbuf(c, (size_t)G * ctw(c, lo + 1));
+    stage.reset(new Prof(c, "stage:cheb"));
+    chebyshev(c, S, (int)G, L - 1, L, cbuf.p, lo + 1);
+    // S7: sum over groups, then RotateAndSum over all slots
+    stage.reset(new Prof(c, "stage:sum"));
+    {
+        Prof p(c, "misc");
+        launch_sum(cbuf.p, lo + 1, ctw(c, lo + 1), (int)G, out, lo + 1, lo, c->d_primes, N, c->stream);
+        c->launches++;
+    }
+    rotate_sum(c, out, lo + 1, lo);
+}
+
+}  // namespace
+
+// A match replayed as a CUDA graph: query staged in `in`, outputs left in `out`.
+struct MatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    u64* in = nullptr;
+    u64* out = nullptr;
+    int runs = 0;
+    uint64_t kernels = 0;
+};
+
+namespace {
+std::mutex g_graph_mu;
+std::map<std::tuple<const fr_ctx*, const fr_db*, int>, MatchGraph> g_graphs;
+
+void drop_graphs(const fr_ctx* c, const fr_db* db) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (std::get<0>(it->first) == c && (db == nullptr || std::get<1>(it->first) == db)) {
+            if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+            cudaFree(it->second.in);
+            cudaFree(it->second.out);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+}  // namespace
+
+extern "C" {
+
 fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out) {
     return guard([&] {
         need_device(c);
@@ -1236,82 +1369,57 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
             raise(FR_ERR_UNSUPPORTED, "n1 > 100: the MAC stages 2 n1 baby words per point in shared memory");
         if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
         if (mode != FR_MODE_SCORES && L - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+        if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
+            raise(FR_ERR_INVALID_ARG, "unknown mode");
         CU(cudaSetDevice(c->device));
-        const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
-        const int n2 = (ell + n1 - 1) / n1;
-        const long long G = db->G;
         const int L1 = L + 1;
-        // S1: query ingest (one H2D if host-resident) and baby steps B_i = Rot_i(q), hoisted (S2)
-        Tmp babies(c, (size_t)n1 * ctw(c, L1));
-        to_device(c, query, babies.p, L1, L);
-        if (n1 > 1) {
-            std::vector<long> ks;
-            std::vector<u64*> outs;
-            for (int i = 1; i < n1; ++i) {
-                ks.push_back(i);
-                outs.push_back(babies.p + (size_t)i * ctw(c, L1));
-            }
-            rotate_cts(c, L, {babies.p}, L1, ks, outs, L1, true);
-        }
-        // S3-S5 per group: MAC with pre-rotated diagonals, rescale, giant rotations, sum
-        auto sblk = new_block(c, (size_t)G * ctw(c, L));
-        for (long long g = 0; g < G; ++g) {
-            Tmp Pj(c, (size_t)n2 * ctw(c, L1));
-            {
-                Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-                launch_mac(babies.p, L1, db->diags + (size_t)g * ell * L1 * N, Pj.p, L1, L1, n1, n2, ell,
-                           c->d_primes, N, c->stream);
-                c->launches++;
-            }
-            Tmp Gs(c, (size_t)n2 * ctw(c, L));
-            rescale(c, Pj.p, n2, L, L1, Gs.p, L);
-            if (n2 > 1) {
-                Tmp Pr(c, (size_t)(n2 - 1) * ctw(c, L));
-                copy_d2d(c, Pr.p, Gs.p + ctw(c, L), (size_t)(n2 - 1) * ctw(c, L));
-                std::vector<const u64*> in;
-                std::vector<long> ks;
-                std::vector<u64*> outs;
-                for (int j = 1; j < n2; ++j) {
-                    in.push_back(Pr.p + (size_t)(j - 1) * ctw(c, L));
-                    ks.push_back((long)j * n1);
-                    outs.push_back(Gs.p + (size_t)j * ctw(c, L));
-                }
-                rotate_cts(c, L - 1, in, L, ks, outs, L, false);
-            }
-            Prof p(c, "misc");
-            launch_sum(Gs.p, L, ctw(c, L), n2, sblk->p + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->stream);
-            c->launches++;
-        }
-        std::vector<fr_ct*> res;
-        if (mode == FR_MODE_SCORES) {
-            for (long long g = 0; g < G; ++g) res.push_back(new_dev_ct(c, sblk, sblk->p + (size_t)g * ctw(c, L), L - 1, L));
+        int nout, lo;
+        match_shape(c, db, mode, &nout, &lo);
+        const size_t ow = (size_t)ctw(c, lo + 1);
+        auto oblk = new_block(c, (size_t)nout * ow);
+        if (c->prof || !c->use_graphs) {
+            // eager: S1 ingest (one H2D if host-resident) into a stream-ordered buffer
+            Tmp q(c, ctw(c, L1));
+            to_device(c, query, q.p, L1, L);
+            match_pipeline(c, db, q.p, mode, oblk->p);
         } else {
-            // S6: Chebyshev threshold on every group's scores (batched)
-            const int lo = L - 1 - c->d2;
-            auto cblk = new_block(c, (size_t)G * ctw(c, lo + 1));
-            chebyshev(c, sblk->p, (int)G, L - 1, L, cblk->p, lo + 1);
-            sblk.reset();
-            if (mode == FR_MODE_IDENTIFY) {
-                for (long long g = 0; g < G; ++g)
-                    res.push_back(new_dev_ct(c, cblk, cblk->p + (size_t)g * ctw(c, lo + 1), lo, lo + 1));
-            } else {
-                // S7: sum over groups, then RotateAndSum over all slots
-                auto mblk = new_block(c, ctw(c, lo + 1));
-                {
-                    Prof p(c, "misc");
-                    launch_sum(cblk->p, lo + 1, ctw(c, lo + 1), (int)G, mblk->p, lo + 1, lo, c->d_primes, N,
-                               c->stream);
-                    c->launches++;
-                }
-                cblk.reset();
-                rotate_sum(c, mblk->p, lo + 1, lo);
-                res.push_back(new_dev_ct(c, mblk, mblk->p, lo, lo + 1));
+            std::lock_guard<std::mutex> lock(g_graph_mu);
+            MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, db, (int)mode)];
+            if (!mg.in) {
+                CU(cudaMalloc(&mg.in, ctw(c, L1) * 8));
+                CU(cudaMalloc(&mg.out, (size_t)nout * ow * 8));
             }
+            to_device(c, query, mg.in, L1, L);
+            if (!mg.exec && mg.runs >= 1) {
+                // second call for this (database, mode): capture the pipeline once
+                const uint64_t k0 = c->launches;
+                cudaGraph_t graph;
+                CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                try {
+                    match_pipeline(c, db, mg.in, mode, mg.out);
+                } catch (...) {
+                    cudaStreamEndCapture(c->stream, &graph);
+                    throw;
+                }
+                CU(cudaStreamEndCapture(c->stream, &graph));
+                CU(cudaGraphInstantiate(&mg.exec, graph, 0));
+                cudaGraphDestroy(graph);
+                mg.kernels = c->launches - k0;
+                c->launches = k0;
+            }
+            if (mg.exec) {
+                CU(cudaGraphLaunch(mg.exec, c->stream));
+                c->launches += mg.kernels;
+            } else {
+                match_pipeline(c, db, mg.in, mode, mg.out);
+            }
+            mg.runs++;
+            copy_d2d(c, oblk->p, mg.out, (size_t)nout * ow);
         }
-        fr_ct** arr = new fr_ct*[res.size()];
-        for (size_t i = 0; i < res.size(); ++i) arr[i] = res[i];
+        fr_ct** arr = new fr_ct*[nout];
+        for (int i = 0; i < nout; ++i) arr[i] = new_dev_ct(c, oblk, oblk->p + (size_t)i * ow, lo, lo + 1);
         *out = arr;
-        *n_out = res.size();
+        *n_out = (size_t)nout;
     });
 }
 

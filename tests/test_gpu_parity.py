@@ -216,3 +216,21 @@ def test_match_at_working_level_deep(deep, mode):
         sp[: len(s)] = s
         p = np.polynomial.chebyshev.chebval(sp, oracle.cheb_coeffs(59, 0.5))
         assert abs(deep.ctx.decrypt(deep.keys, out[0])[0] - p.sum()) < 1e-2
+
+
+def test_match_graph_replay_bit_exact(mid):
+    """fr_match runs eagerly the first time, is captured as a CUDA graph the second
+    time and replayed afterwards; every call must equal the oracle."""
+    db = mid.ctx.load_db(mid.T)
+    rng = np.random.default_rng(21)
+    for call in range(4):
+        q = rng.standard_normal(mid.cfg["ell"])
+        q /= np.linalg.norm(q)
+        seed = 1000 + call
+        qct = mid.ctx.encrypt(mid.keys, q, seed)
+        if call % 2:
+            qct.upload()
+        out = mid.ctx.match(db, qct, fr.FR_MODE_MEMBERSHIP)
+        oq = mid.ok.encrypt(np.tile(q, mid.oc.n // mid.cfg["ell"]), seed)
+        ref, lvl = mid.ok.match(oq, mid.T, mid.cfg["ell"], mid.cfg["n1"], fr.FR_MODE_MEMBERSHIP, 59, 0.5)
+        assert np.array_equal(out[0].export(), ref[0]), call
