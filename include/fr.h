@@ -90,6 +90,11 @@ typedef struct {
     int device;                /* CUDA device ordinal; -1: client-only context (host key generation,
                                   encryption, decryption; device calls fail with FR_ERR_CUDA) */
     void* cuda_stream;         /* optional cudaStream_t to run on (not owned); NULL: the context creates one */
+    uint32_t db_tier;          /* template storage (plaintext diagonal tiers): 0 auto (stored when the
+                                  diagonals fit the budget / free HBM, else per-query encoding), 1 the
+                                  pre-rotated diagonals are encoded once and kept in HBM, 2 only the
+                                  FP32 templates are kept and each query encodes the diagonals of every
+                                  group on the device before its MAC */
     uint32_t level_mode;       /* 0: the match runs at the query's top level (whole modulus chain);
                                   1: the query is first dropped (limbs discarded) to the lowest level that
                                   still leaves the threshold depth and one output level above 0:
@@ -127,6 +132,10 @@ fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
  * diagonal (Eq. eq:prerotation) is encoded on the device and kept in HBM with the
  * limbs of the context's working level (G * ell * (level+1) * N words). */
 fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
+
+/* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding), its
+ * number of template groups G = ceil(K / (N/2)) and its resident bytes. */
+fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes);
 
 /* Client-side encryption of one query q (ell values) replicated across the N/2 slots
  * (numSlots/ell copies, Section "Packed matrices and batched multiplications"). */

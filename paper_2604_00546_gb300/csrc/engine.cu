@@ -107,6 +107,7 @@ struct fr_ctx {
     uint64_t launches = 0;
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
+    uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query
 };
 
 struct fr_keys {
@@ -137,7 +138,9 @@ struct fr_db {
     long long K = 0;
     int ell = 0;
     long long G = 0;
-    u64* diags = nullptr;
+    int tier = 1;            // 1: pre-rotated diagonals stored in HBM; 2: encoded per query from templates
+    u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]
+    float* templates = nullptr;  // tier 2: [K][ell] FP32
     size_t bytes = 0;
 };
 
@@ -531,6 +534,28 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     copy_cts(c, out, out_cap, v->p, vcap, B, ls - d2);
 }
 
+// Encode the pre-rotated diagonals D'_{g, d} (d < ell) of template group g at the
+// working level into dst [ell][level+1][N] (evaluation + Montgomery form).
+void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst) {
+    const int N = c->R.N, n = N / 2, nl = c->work_level + 1, ell = (int)c->ell;
+    const int chunk = 64;
+    Tmp z(c, (size_t)chunk * n * 2);
+    const PrimeMap pm = pm_level(nl - 1);
+    for (int d0 = 0; d0 < ell; d0 += chunk) {
+        const int nd = std::min(chunk, ell - d0);
+        u64* o = dst + (size_t)d0 * nl * N;
+        {
+            Prof p(c, "encode", 8.0 * N * nd * nl);
+            launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, (int)c->n1, z.p, o, nl, c->d_primes,
+                                c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->stream);
+            c->launches += 4;
+        }
+        ntt(c, o, (long long)nl * N, nl, nd * nl, pm, false);
+        launch_to_mont(o, N, pm, c->d_primes, (long long)nd * nl * N, c->stream);
+        c->launches++;
+    }
+}
+
 void rotate_sum(fr_ctx* c, u64* ct, int cap, int level) {
     const int n = c->R.N / 2;
     Tmp r(c, (size_t)ctw(c, cap));
@@ -786,6 +811,8 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         }
         c->host_threads = std::max(1u, std::thread::hardware_concurrency());
         if (prm->level_mode > 1) raise(FR_ERR_INVALID_ARG, "level_mode must be 0 or 1");
+        if (prm->db_tier > 2) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1 or 2");
+        c->db_tier = prm->db_tier;
         c->work_level = c->R.nq - 1;
         if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->d2 : 0));
         if (prm->device < 0) {
@@ -927,37 +954,51 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
         db->K = (long long)K;
         db->ell = (int)ell;
         db->G = ((long long)K + n - 1) / n;
-        const size_t words = (size_t)db->G * ell * nl * N;
-        db->bytes = words * 8;
-        if (c->budget && c->resident + db->bytes > c->budget)
-            raise(FR_ERR_HBM_BUDGET, "database diagonals exceed the HBM budget");
-        CU(cudaMalloc(&db->diags, db->bytes));
-        float* dT = nullptr;
-        CU(cudaMalloc(&dT, K * ell * sizeof(float)));
-        CU(cudaMemcpyAsync(dT, templates, K * ell * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-        const int chunk = 64;
-        Tmp z(c, (size_t)chunk * n * 2);
-        PrimeMap pm = pm_level(nl - 1);
-        for (long long g = 0; g < db->G; ++g) {
-            for (int d0 = 0; d0 < (int)ell; d0 += chunk) {
-                const int nd = std::min(chunk, (int)ell - d0);
-                u64* dst = db->diags + ((size_t)g * ell + d0) * nl * N;
-                {
-                    Prof p(c, "encode");
-                    launch_encode_diags(dT, (long long)K, (int)ell, c->R.logN - 1, g, d0, nd, (int)c->n1, z.p, dst,
-                                        nl, c->d_primes, c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->stream);
-                    c->launches += 4;
-                }
-                ntt(c, dst, (long long)nl * N, nl, nd * nl, pm, false);
-                launch_to_mont(dst, N, pm, c->d_primes, (long long)nd * nl * N, c->stream);
-                c->launches++;
-            }
+        const size_t tbytes = K * ell * sizeof(float);
+        const size_t dbytes = (size_t)db->G * ell * nl * N * 8;
+        // storage tier: the stored diagonals when they fit (budget, or free HBM minus a
+        // working margin of 2 groups of diagonals), else the templates and a per-query encode
+        int tier = (int)c->db_tier;
+        if (tier == 0) {
+            size_t free_b = 0, total_b = 0;
+            CU(cudaMemGetInfo(&free_b, &total_b));
+            const size_t margin = (size_t)2 * ell * nl * N * 8 + ((size_t)4 << 30);
+            const bool fits = c->budget ? c->resident + dbytes <= c->budget : dbytes + margin <= free_b;
+            tier = fits ? 1 : 2;
         }
-        CU(cudaStreamSynchronize(c->stream));
-        CU(cudaFree(dT));
+        db->tier = tier;
+        db->bytes = tier == 1 ? dbytes : tbytes;
+        if (c->budget && c->resident + db->bytes > c->budget)
+            raise(FR_ERR_HBM_BUDGET, "database exceeds the HBM budget");
+        float* dT = nullptr;
+        CU(cudaMalloc(&dT, tbytes));
+        CU(cudaMemcpyAsync(dT, templates, tbytes, cudaMemcpyHostToDevice, c->stream));
+        if (tier == 1) {
+            cudaError_t e = cudaMalloc(&db->diags, dbytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(dT);
+                raise(e == cudaErrorMemoryAllocation ? FR_ERR_HBM_BUDGET : FR_ERR_CUDA,
+                      std::string("cannot hold the database diagonals: ") + cudaGetErrorString(e));
+            }
+            for (long long g = 0; g < db->G; ++g) encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N);
+            CU(cudaStreamSynchronize(c->stream));
+            CU(cudaFree(dT));
+        } else {
+            db->templates = dT;
+            CU(cudaStreamSynchronize(c->stream));
+        }
         c->resident += db->bytes;
         *out = db.release();
     });
+}
+
+fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes) {
+    if (!db) return FR_ERR_INVALID_ARG;
+    if (tier) *tier = (uint32_t)db->tier;
+    if (groups) *groups = (uint64_t)db->G;
+    if (bytes) *bytes = (uint64_t)db->bytes;
+    return FR_OK;
 }
 
 void fr_free_db(fr_db* db) {
@@ -968,6 +1009,7 @@ void fr_free_db(fr_db* db) {
         db->ctx->resident -= db->bytes;
     }
     cudaFree(db->diags);
+    cudaFree(db->templates);
     delete db;
 }
 
@@ -1274,13 +1316,21 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64*
     const bool scores_only = mode == FR_MODE_SCORES;
     Tmp sbuf(c, scores_only ? 1 : (size_t)G * ctw(c, L));
     u64* S = scores_only ? out : sbuf.p;
+    std::unique_ptr<Tmp> dg;
+    if (db->tier == 2) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
     for (long long g = 0; g < G; ++g) {
+        const u64* D = db->diags + (size_t)g * ell * L1 * N;
+        if (db->tier == 2) {
+            // S3, tier C: encode this group's pre-rotated diagonals from the FP32 templates
+            stage.reset(new Prof(c, "stage:encode"));
+            encode_group(c, db->templates, db->K, g, dg->p);
+            D = dg->p;
+        }
         stage.reset(new Prof(c, "stage:mac"));
         Tmp Pj(c, (size_t)n2 * ctw(c, L1));
         {
             Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-            launch_mac(babies.p, L1, db->diags + (size_t)g * ell * L1 * N, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N,
-                       c->stream);
+            launch_mac(babies.p, L1, D, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N, c->stream);
             c->launches++;
         }
         Tmp Gs(c, (size_t)n2 * ctw(c, L));

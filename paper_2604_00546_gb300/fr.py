@@ -29,7 +29,7 @@ FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
 
 EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
-    "fr_load_db", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
+    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
@@ -49,7 +49,7 @@ class Params(C.Structure):
         ("p_bits", C.POINTER(C.c_uint32)), ("dnum", C.c_uint32), ("scale_bits", C.c_uint32), ("ell", C.c_uint32),
         ("n1", C.c_uint32), ("schedule", C.c_uint32), ("cheb_degree", C.c_uint32), ("threshold", C.c_double),
         ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-        ("level_mode", C.c_uint32),
+        ("db_tier", C.c_uint32), ("level_mode", C.c_uint32),
     ]
 
 
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
         "fr_keygen": (st, [vp, i32p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_load_keys": (st, [vp, vp]),
         "fr_load_db": (st, [vp, f32p, C.c_size_t, C.c_size_t, C.POINTER(vp)]),
+        "fr_db_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
         "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_match": (st, [vp, vp, vp, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t)]),
@@ -173,13 +174,13 @@ class Context:
     """fr_ctx: parameters, primes, device tables."""
 
     def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
-                 hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0):
+                 hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0, db_tier=0):
         L = load()
         self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
         self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
-                             C.c_void_p(cuda_stream) if cuda_stream else None, level_mode)
+                             C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode)
         h = C.c_void_p()
         _check(L.fr_setup(C.byref(self.params), C.byref(h)))
         self.h = h
@@ -341,6 +342,11 @@ class Database:
         self.ctx = ctx
         self.h = h
         self.K = K
+
+    def info(self):
+        t, g, b = C.c_uint32(), C.c_uint64(), C.c_uint64()
+        _check(_lib.fr_db_info(self.h, C.byref(t), C.byref(g), C.byref(b)))
+        return dict(tier=t.value, groups=g.value, bytes=b.value)
 
     def __del__(self):
         try:

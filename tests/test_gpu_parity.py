@@ -234,3 +234,30 @@ def test_match_graph_replay_bit_exact(mid):
         oq = mid.ok.encrypt(np.tile(q, mid.oc.n // mid.cfg["ell"]), seed)
         ref, lvl = mid.ok.match(oq, mid.T, mid.cfg["ell"], mid.cfg["n1"], fr.FR_MODE_MEMBERSHIP, 59, 0.5)
         assert np.array_equal(out[0].export(), ref[0]), call
+
+
+@pytest.mark.parametrize("mode", [fr.FR_MODE_SCORES, fr.FR_MODE_MEMBERSHIP])
+def test_per_query_encoding_tier_matches_stored_diagonals(mode):
+    """Tier C: only the FP32 templates stay in HBM and every query encodes the pre-rotated
+    diagonals of each group on the device; the result equals the stored-diagonal tier and
+    the oracle, bit for bit (two groups, ragged tail)."""
+    c = W.CONFIGS["mid"]
+    T, q, _ = W.workload("mid")
+    outs = []
+    for tier in (1, 2):
+        ctx = fr.Context(device=0, db_tier=tier, **W.ctx_params("mid"))
+        keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed("mid"))
+        ctx.load_keys(keys)
+        db = ctx.load_db(T)
+        assert db.info()["tier"] == tier and db.info()["groups"] == 2
+        qct = ctx.encrypt(keys, q, W.enc_seed("mid"))
+        outs.append([o.export() for o in ctx.match(db, qct, mode)])
+        outs.append([o.export() for o in ctx.match(db, qct, mode)])   # second call: graph capture
+    oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
+    ok = oc.keygen(W.key_seed("mid"))
+    oq = ok.encrypt(np.tile(q, oc.n // c["ell"]), W.enc_seed("mid"))
+    ref, _ = ok.match(oq, T, c["ell"], c["n1"], mode, 59, 0.5)
+    for o in outs:
+        assert len(o) == len(ref)
+        for g in range(len(ref)):
+            assert np.array_equal(o[g], ref[g])
