@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr int kTC = 16;  // columns per tile in the column pass
+constexpr int kTC = 8;   // columns per tile in the column pass
 
 __device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* prime) {
     if (b.tab) {
@@ -54,28 +54,34 @@ struct PhaseInfo {
 };
 
 struct Ctx {
-    long long Jbase, M;
+    int Jbase, M;    // global index of the tile's element 0; M = R (column pass) or N (row pass)
     const u64* tw;
     const u64* tws;
     u64 q;
 };
 
-// one radix-2 stage on bit B of the registers of a phase with base bit LO
+// one radix-2 stage on bit B of the registers of a phase with base bit LO; the
+// stage's four twiddle pairs are loaded before its butterflies run
 template <bool INV, int LO, int B>
 __device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
     constexpr int lb = B - LO;
     const u64 q2 = 2 * c.q;
+    u64 w[8], ws[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if (e & (1 << lb)) continue;
+        const int idx = (c.M + c.Jbase + phase_x<LO>(tau, e)) >> (B + 1);
+        w[e] = c.tw[idx];
+        ws[e] = c.tws[idx];
+    }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         if (e & (1 << lb)) continue;
         const int e1 = e | (1 << lb);
-        const long long J = c.Jbase + phase_x<LO>(tau, e);
-        const long long idx = (c.M + J) >> (B + 1);
-        const u64 w = c.tw[idx], ws = c.tws[idx];
         if (!INV) {
             u64 X = v[e];
             X = X >= q2 ? X - q2 : X;
-            const u64 T = shoup_lazy(v[e1], w, ws, c.q);
+            const u64 T = shoup_lazy(v[e1], w[e], ws[e], c.q);
             v[e] = X + T;
             v[e1] = X - T + q2;
         } else {
@@ -83,7 +89,7 @@ __device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
             u64 S = X + Y;
             S = S >= q2 ? S - q2 : S;
             v[e] = S;
-            v[e1] = shoup_lazy(X - Y + q2, w, ws, c.q);
+            v[e1] = shoup_lazy(X - Y + q2, w[e], ws[e], c.q);
         }
     }
 }
@@ -122,37 +128,41 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
     return x >= q ? x - q : x;
 }
 
-// exchange through shared memory, column layout s[x][16]
+// exchange through shared memory, column layout s[x'][8] with x' = x ^ (bit 3 of x):
+// the two rows a half-warp touches then fall in different 8-word bank halves
+__device__ __forceinline__ int col_row(int x) { return x ^ ((x >> 3) & 1); }
+
 struct ColEx {
     u64* s;
     int col;
     template <int LA, int LB>
     __device__ __forceinline__ void exchange(u64 (&v)[8], int tau) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) s[phase_x<LA>(tau, e) * kTC + col] = v[e];
+        for (int e = 0; e < 8; ++e) s[col_row(phase_x<LA>(tau, e)) * kTC + col] = v[e];
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = s[phase_x<LB>(tau, e) * kTC + col];
+        for (int e = 0; e < 8; ++e) v[e] = s[col_row(phase_x<LB>(tau, e)) * kTC + col];
         __syncthreads();
     }
 };
 
-// exchange through shared memory, one padded row (index x + x/8)
+// Shared-memory word of element x of a row: the low 4 bits are XORed with bits 4..6
+// (x4 -> bit 0, x5 -> bits 1 and 3, x6 -> bit 2). For 256-point rows this keeps every
+// half-warp access of the three phase layouts on 16 distinct 8-byte bank pairs.
+__device__ __forceinline__ int row_swz(int x) {
+    return x ^ ((x >> 4) & 1) ^ (((x >> 5) & 1) * 10) ^ (((x >> 6) & 1) << 2);
+}
+
+// exchange through shared memory, one row
 struct RowEx {
     u64* s;
     template <int LA, int LB>
     __device__ __forceinline__ void exchange(u64 (&v)[8], int tau) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int xi = phase_x<LA>(tau, e);
-            s[xi + (xi >> 3)] = v[e];
-        }
+        for (int e = 0; e < 8; ++e) s[row_swz(phase_x<LA>(tau, e))] = v[e];
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int xi = phase_x<LB>(tau, e);
-            v[e] = s[xi + (xi >> 3)];
-        }
+        for (int e = 0; e < 8; ++e) v[e] = s[row_swz(phase_x<LB>(tau, e))];
         __syncthreads();
     }
 };
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, Pol
         sws[i] = tws[i];
     }
     const int col = threadIdx.x & (kTC - 1);
-    const int tau = threadIdx.x >> 4;
+    const int tau = threadIdx.x / kTC;
     const int gcol = blockIdx.x * kTC + col;
     constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
     constexpr int LL = LastLo<LOG, INV>::v;
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
     constexpr int S = 1 << LOG;
     constexpr int TPR = S / 8;           // threads per row
     constexpr int RPC = (256 / TPR < (1 << LOGR)) ? 256 / TPR : (1 << LOGR);  // rows per CTA
-    constexpr int SP = S + S / 8;        // padded row stride in shared memory
+    constexpr int SP = S;                // row stride in shared memory (swizzled, no padding)
     extern __shared__ u64 sm[];
     const int N = R.N;
     const int p = blockIdx.y;
@@ -216,8 +226,8 @@ __global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
     const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
     const int rloc = threadIdx.x / TPR;
     const int tau = threadIdx.x % TPR;
-    const long long rho = (long long)blockIdx.x * RPC + rloc;
-    const long long Jbase = rho * S;
+    const int rho = blockIdx.x * RPC + rloc;
+    const int Jbase = rho * S;
     u64* xr = x + Jbase;
     constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
     constexpr int LL = LastLo<LOG, INV>::v;
@@ -245,7 +255,7 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
     constexpr int TPR = SC / 8, RPC = (256 / TPR < SR) ? 256 / TPR : SR;
     dim3 gr(SR / RPC, b.npolys);
-    const size_t smr = (size_t)RPC * (SC + SC / 8) * sizeof(u64);
+    const size_t smr = (size_t)RPC * SC * sizeof(u64);
     if (!inverse) {
         k_ntt_col<LOGR, false><<<gc, tc, smc, st>>>(R, b);
         k_ntt_row<LOGC, LOGR, false><<<gr, RPC * TPR, smr, st>>>(R, b);
