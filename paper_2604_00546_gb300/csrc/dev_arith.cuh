@@ -18,6 +18,7 @@ struct DevPrime {
     u64 r2;      // 2^128 mod q
     u64 ninv;    // N^-1 mod q
     u64 ninv_s;  // Shoup quotient of ninv
+    u64 one_s;   // floor(2^64 / q): Shoup quotient of 1 (x mod q for any 64-bit x)
 };
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {

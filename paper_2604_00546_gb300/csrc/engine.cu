@@ -76,7 +76,10 @@ struct Region {
 struct fr_ctx {
     frh::Ring R;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // the context stream (API calls are ordered on it)
+    cudaStream_t cur = nullptr;          // stream the internal helpers enqueue on
+    cudaStream_t side = nullptr;         // second stream for concurrent branches inside a match
+    std::vector<cudaEvent_t> evs;        // fork / join events (no timing)
     bool own_stream = false;
     RingDev rd{};
     DevPrime* d_primes = nullptr;
@@ -152,11 +155,11 @@ namespace {
 u64* dalloc(fr_ctx* c, size_t words) {
     if (words == 0) words = 1;
     void* p = nullptr;
-    CU(cudaMallocAsync(&p, words * sizeof(u64), c->stream));
+    CU(cudaMallocAsync(&p, words * sizeof(u64), c->cur));
     return (u64*)p;
 }
 void dfree(fr_ctx* c, void* p) {
-    if (p) cudaFreeAsync(p, c->stream);
+    if (p) cudaFreeAsync(p, c->cur);
 }
 struct Tmp {
     fr_ctx* c;
@@ -186,11 +189,11 @@ struct Prof {
         r->bytes += (uint64_t)bytes;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        cudaEventRecord(a, c->stream);
+        cudaEventRecord(a, c->cur);
     }
     ~Prof() {
         if (!r) return;
-        cudaEventRecord(b, c->stream);
+        cudaEventRecord(b, c->cur);
         r->pending.emplace_back(a, b);
         r->launches++;
     }
@@ -213,7 +216,7 @@ PrimeMap pm_ext(const fr_ctx* c, int level) {
 void ntt(fr_ctx* c, u64* base, long long outer, int inner, int npolys, const PrimeMap& pm, bool inv) {
     Prof p(c, "ntt", 16.0 * npolys * c->R.N);
     PolyBatch b{base, outer, inner, npolys, pm};
-    launch_ntt(c->rd, b, inv, c->stream);
+    launch_ntt(c->rd, b, inv, c->cur);
     c->launches += 2;
 }
 // forward NTT of the non-own positions of nj ModUp outputs [nj][beta][npos][N]
@@ -222,7 +225,7 @@ void ntt_modup(fr_ctx* c, u64* ext, int nj, int level) {
     const int cnt = c->modup_ntt_n[level];
     Prof p(c, "ntt", 16.0 * nj * cnt * c->R.N);
     PolyBatch b{ext, (long long)beta * npos * c->R.N, 1, nj * cnt, PrimeMap{}, c->d_modup_ntt[level], cnt};
-    launch_ntt(c->rd, b, false, c->stream);
+    launch_ntt(c->rd, b, false, c->cur);
     c->launches += 2;
 }
 // all limbs 0..level of a ciphertext batch [B][2][cap][N]
@@ -233,13 +236,13 @@ void ntt_cts(fr_ctx* c, u64* p, int B, int level, int cap, bool inv) {
 long long ctw(const fr_ctx* c, int cap) { return 2ll * cap * c->R.N; }
 
 void copy_d2d(fr_ctx* c, u64* dst, const u64* src, size_t words) {
-    CU(cudaMemcpyAsync(dst, src, words * sizeof(u64), cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpyAsync(dst, src, words * sizeof(u64), cudaMemcpyDeviceToDevice, c->cur));
 }
 // copy limbs 0..level of B cts from cap_s to cap_d layout
 void copy_cts(fr_ctx* c, u64* dst, int cap_d, const u64* src, int cap_s, int B, int level) {
     const size_t N = c->R.N;
     CU(cudaMemcpy2DAsync(dst, cap_d * N * 8, src, cap_s * N * 8, (level + 1) * N * 8, 2 * (size_t)B,
-                         cudaMemcpyDeviceToDevice, c->stream));
+                         cudaMemcpyDeviceToDevice, c->cur));
 }
 
 // ---------------------------------------------------------------------------
@@ -276,7 +279,7 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
         Prof p(c, "ip", W * ((same_key ? 1.0 : nj) * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos +
                              nj * 2.0 * npos));
         launch_ip(ij, nj, same_key && nj > 1, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level),
-                  c->R.logN, c->stream);
+                  c->R.logN, c->cur);
         c->launches++;
     }
     PrimeMap pmP{};
@@ -285,7 +288,7 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
     ntt(c, acc.p + (size_t)(level + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, true);
     {
         Prof p(c, "moddown", 8.0 * N * nj * 2.0 * (np + level + 1));
-        launch_p2q(acc.p, 2ll * npos * N, npos, level, conv.p, c->d_p2q, N, nj, c->stream);
+        launch_p2q(acc.p, 2ll * npos * N, npos, level, conv.p, c->d_p2q, N, nj, c->cur);
         c->launches++;
     }
     ntt(c, conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level), false);
@@ -304,7 +307,7 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
     double addw = 0;
     for (int j = 0; j < nj; ++j) addw += reqs[j].mode == 1 ? (level + 1) : reqs[j].mode == 2 ? 2.0 * (level + 1) : 0;
     Prof p(c, "moddown", 8.0 * N * (nj * 6.0 * (level + 1) + addw));
-    launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->stream);
+    launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->cur);
     c->launches++;
 }
 
@@ -322,7 +325,7 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
         Tmp ext(c, (size_t)beta * npos * N);
         {
             Prof p(c, "modup", 8.0 * N * (2.0 * (level + 1) + (double)beta * npos));
-            launch_modup(in.p, in.p + L1N, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->stream);
+            launch_modup(in.p, in.p + L1N, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->cur);
             c->launches++;
         }
         ntt_modup(c, ext.p, 1, level);
@@ -344,7 +347,7 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoiste
         Tmp ext(c, (size_t)nj * beta * npos * N);
         {
             Prof p(c, "modup", 8.0 * N * nj * (2.0 * (level + 1) + (double)beta * npos));
-            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nj, c->stream);
+            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nj, c->cur);
             c->launches++;
         }
         ntt_modup(c, ext.p, nj, level);
@@ -387,7 +390,7 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     const int N = c->R.N, l = level;
     Tmp last(c, (size_t)2 * B * N);
     CU(cudaMemcpy2DAsync(last.p, (size_t)N * 8, in + (size_t)l * N, (size_t)in_cap * N * 8, (size_t)N * 8,
-                         2 * (size_t)B, cudaMemcpyDeviceToDevice, c->stream));
+                         2 * (size_t)B, cudaMemcpyDeviceToDevice, c->cur));
     PrimeMap one{};
     one.period = 1;
     one.idx[0] = (unsigned char)l;
@@ -395,12 +398,12 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     Tmp lifted(c, (size_t)2 * B * l * N);
     {
         Prof p(c, "rescale", 8.0 * N * 2 * B * (1.0 + l));
-        launch_rescale_lift(last.p, lifted.p, c->d_rescale[l], l, N, 2 * B, c->stream);
+        launch_rescale_lift(last.p, lifted.p, c->d_rescale[l], l, N, 2 * B, c->cur);
         c->launches++;
     }
     ntt(c, lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1), false);
     Prof p(c, "rescale", 8.0 * N * 2 * B * 3.0 * l);
-    launch_rescale_combine(in, in_cap, lifted.p, out, out_cap, c->d_rescale[l], l, N, 2 * B, c->stream);
+    launch_rescale_combine(in, in_cap, lifted.p, out, out_cap, c->d_rescale[l], l, N, 2 * B, c->cur);
     c->launches++;
 }
 
@@ -420,7 +423,7 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
         for (int j = 0; j < nj; ++j) tj.j[j] = TensorJob{A[j0 + j], Bv[j0 + j], d.p + j * dw, a_cap, b_cap};
         {
             Prof p(c, "tensor", 8.0 * N * nj * 7.0 * (level + 1));
-            launch_tensor(tj, nj, level, c->d_primes, N, c->stream);
+            launch_tensor(tj, nj, level, c->d_primes, N, c->cur);
             c->launches++;
         }
         std::vector<KSReq> reqs;
@@ -434,7 +437,7 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
 void add_cts(fr_ctx* c, const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
              int o_cap, long long o_bs, int level, int B) {
     Prof p(c, "misc", 8.0 * c->R.N * B * 6.0 * (level + 1));
-    launch_add(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, B, c->d_primes, c->R.N, c->stream);
+    launch_add(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, B, c->d_primes, c->R.N, c->cur);
     c->launches++;
 }
 
@@ -467,7 +470,18 @@ const u64* cheb_consts(fr_ctx* c, int ls) {
 void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int out_cap) {
     const int N = c->R.N, d2 = c->d2;
     if (ls - d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the Chebyshev evaluation");
+    if (d2 + 2 > (int)c->evs.size()) raise(FR_ERR_UNSUPPORTED, "Chebyshev degree too large");
     const int nleaves = (int)c->leaves.size();
+    // Two concurrent branches: the giant powers T_{2^m} on the current stream, the
+    // leaves and the tree on the side stream; tree level s waits for T_{2^s} only.
+    cudaStream_t main = c->cur, side = c->side;
+    struct Restore {
+        fr_ctx* c;
+        cudaStream_t s;
+        ~Restore() { c->cur = s; }
+    } restore{c, main};
+    CU(cudaEventRecord(c->evs[0], main));
+    CU(cudaStreamWaitEvent(side, c->evs[0], 0));
     // giant powers T_{2^m}, m = 1..d2-1, T_{2^m} at level ls - m
     std::vector<std::unique_ptr<Tmp>> pw(d2);
     std::vector<int> pw_cap(d2, 0);
@@ -488,12 +502,14 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
         rescale(c, sq.p, B, lv, lv + 1, pw[m]->p, lv);
         for (int b = 0; b < B; ++b) {
             Prof p(c, "misc");
-            launch_double_sub(pw[m]->p + (size_t)b * ctw(c, lv), lv, lv - 1, c->d_delta, c->d_primes, N, c->stream);
+            launch_double_sub(pw[m]->p + (size_t)b * ctw(c, lv), lv, lv - 1, c->d_delta, c->d_primes, N, c->cur);
             c->launches++;
         }
+        CU(cudaEventRecord(c->evs[m], main));
         prev = pw[m]->p;
         prev_cap = lv;
     }
+    c->cur = side;
     // leaves: Rescale(T_1 round(c1 Delta) + round(c0 Delta) Delta)
     const u64* cc = cheb_consts(c, ls);
     const int L1 = ls + 1;
@@ -504,7 +520,7 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
             Prof p(c, "misc");
             launch_cheb_leaves(x + (size_t)b * ctw(c, x_cap), x_cap, pre.p + (size_t)b * nleaves * ctw(c, ls + 1),
                                ls + 1, ls, nleaves, cc, cc + (size_t)nleaves * L1, cc + (size_t)2 * nleaves * L1,
-                               c->d_primes, N, c->stream);
+                               c->d_primes, N, c->cur);
             c->launches++;
         }
         rescale(c, pre.p, B * nleaves, ls, ls + 1, v->p, ls);
@@ -512,6 +528,7 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     int vcap = ls;
     // tree: parents i = child(2i) * T_{2^s} + child(2i+1)
     for (int s = 1; s < d2; ++s) {
+        CU(cudaStreamWaitEvent(side, c->evs[s], 0));
         const int P = nleaves >> s;
         const int lc = ls - s;
         Tmp prod(c, (size_t)B * P * ctw(c, lc + 1));
@@ -532,6 +549,10 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
         vcap = lc;
     }
     copy_cts(c, out, out_cap, v->p, vcap, B, ls - d2);
+    // join the side branch back into the main stream
+    CU(cudaEventRecord(c->evs[d2], side));
+    c->cur = main;
+    CU(cudaStreamWaitEvent(main, c->evs[d2], 0));
 }
 
 // Encode the pre-rotated diagonals D'_{g, d} (d < ell) of template group g at the
@@ -547,11 +568,11 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
         {
             Prof p(c, "encode", 8.0 * N * nd * nl);
             launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, (int)c->n1, z.p, o, nl, c->d_primes,
-                                c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->stream);
+                                c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->cur);
             c->launches += 4;
         }
         ntt(c, o, (long long)nl * N, nl, nd * nl, pm, false);
-        launch_to_mont(o, N, pm, c->d_primes, (long long)nd * nl * N, c->stream);
+        launch_to_mont(o, N, pm, c->d_primes, (long long)nd * nl * N, c->cur);
         c->launches++;
     }
 }
@@ -592,7 +613,7 @@ void to_device(fr_ctx* c, const fr_ct* ct, u64* dst, int cap, int level = -1) {
     }
     const size_t L1 = ct->level + 1, K1 = level + 1;
     CU(cudaMemcpy2DAsync(dst, (size_t)cap * N * 8, ct->host.data(), L1 * N * 8, K1 * N * 8, 2,
-                         cudaMemcpyHostToDevice, c->stream));
+                         cudaMemcpyHostToDevice, c->cur));
     ntt_cts(c, dst, 1, level, cap, false);
 }
 
@@ -606,8 +627,8 @@ void export_words(fr_ctx* c, const fr_ct* ct, u64* buf) {
     Tmp t(c, 2 * L1 * N);
     copy_cts(c, t.p, (int)L1, ct->dev, ct->cap, 1, ct->level);
     ntt_cts(c, t.p, 1, ct->level, (int)L1, true);
-    CU(cudaMemcpyAsync(buf, t.p, 2 * L1 * N * 8, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemcpyAsync(buf, t.p, 2 * L1 * N * 8, cudaMemcpyDeviceToHost, c->cur));
+    CU(cudaStreamSynchronize(c->cur));
 }
 
 void need_device(const fr_ctx* c) {
@@ -637,6 +658,7 @@ void build_tables(fr_ctx* c) {
         dp[i].r2 = frh::mulm(r1, r1, q);
         dp[i].ninv = R.tabs[i].ninv;
         dp[i].ninv_s = frh::shoup_quot(R.tabs[i].ninv, q);
+        dp[i].one_s = frh::shoup_quot(1, q);
     }
     c->d_primes = upload_persistent(c, dp.data(), T);
     std::vector<u64> tw((size_t)T * N), tws((size_t)T * N), itw((size_t)T * N), itws((size_t)T * N);
@@ -833,12 +855,16 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
             CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
             c->own_stream = true;
         }
+        c->cur = c->stream;
+        CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        c->evs.resize(16);
+        for (auto& e : c->evs) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         cudaMemPool_t pool;
         CU(cudaDeviceGetDefaultMemPool(&pool, c->device));
         uint64_t thr = ~0ull;
         CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         build_tables(c.get());
-        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->cur));
         *out = c.release();
     });
 }
@@ -851,12 +877,15 @@ void fr_free(fr_ctx* c) {
     }
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->side);
     drop_graphs(c, nullptr);
     for (auto& kv : c->rotkeys) cudaFree(kv.second);
     if (c->relin) cudaFree(c->relin);
     for (void* p : c->owned) cudaFree(p);
     for (auto& r : c->regions)
         for (auto& e : r.second.pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (auto& e : c->evs) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -925,9 +954,9 @@ fr_status fr_load_keys(fr_ctx* c, const fr_keys* k) {
         auto up = [&](const std::vector<u64>& h) {
             u64* d = nullptr;
             CU(cudaMalloc(&d, words * 8));
-            CU(cudaMemcpyAsync(d, h.data(), words * 8, cudaMemcpyHostToDevice, c->stream));
-            launch_to_mont(d, c->R.N, pm, c->d_primes, (long long)words, c->stream);
-            CU(cudaStreamSynchronize(c->stream));
+            CU(cudaMemcpyAsync(d, h.data(), words * 8, cudaMemcpyHostToDevice, c->cur));
+            launch_to_mont(d, c->R.N, pm, c->d_primes, (long long)words, c->cur);
+            CU(cudaStreamSynchronize(c->cur));
             return d;
         };
         if (!c->relin) {
@@ -972,7 +1001,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
             raise(FR_ERR_HBM_BUDGET, "database exceeds the HBM budget");
         float* dT = nullptr;
         CU(cudaMalloc(&dT, tbytes));
-        CU(cudaMemcpyAsync(dT, templates, tbytes, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(dT, templates, tbytes, cudaMemcpyHostToDevice, c->cur));
         if (tier == 1) {
             cudaError_t e = cudaMalloc(&db->diags, dbytes);
             if (e != cudaSuccess) {
@@ -982,11 +1011,11 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
                       std::string("cannot hold the database diagonals: ") + cudaGetErrorString(e));
             }
             for (long long g = 0; g < db->G; ++g) encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N);
-            CU(cudaStreamSynchronize(c->stream));
+            CU(cudaStreamSynchronize(c->cur));
             CU(cudaFree(dT));
         } else {
             db->templates = dT;
-            CU(cudaStreamSynchronize(c->stream));
+            CU(cudaStreamSynchronize(c->cur));
         }
         c->resident += db->bytes;
         *out = db.release();
@@ -1102,7 +1131,7 @@ fr_status fr_ct_upload(fr_ctx* c, fr_ct* ct) {
         const int cap = ct->level + 1;
         auto blk = new_block(c, ctw(c, cap));
         to_device(c, ct, blk->p, cap);
-        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->cur));
         ct->block = blk;
         ct->dev = blk->p;
         ct->cap = cap;
@@ -1330,7 +1359,7 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64*
         Tmp Pj(c, (size_t)n2 * ctw(c, L1));
         {
             Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-            launch_mac(babies.p, L1, D, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N, c->stream);
+            launch_mac(babies.p, L1, D, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N, c->cur);
             c->launches++;
         }
         Tmp Gs(c, (size_t)n2 * ctw(c, L));
@@ -1350,7 +1379,7 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64*
             rotate_cts(c, L - 1, in, L, ks, outs, L, false);
         }
         Prof p(c, "misc");
-        launch_sum(Gs.p, L, ctw(c, L), n2, S + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->stream);
+        launch_sum(Gs.p, L, ctw(c, L), n2, S + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->cur);
         c->launches++;
         stage.reset();
     }
@@ -1369,7 +1398,7 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64*
     stage.reset(new Prof(c, "stage:sum"));
     {
         Prof p(c, "misc");
-        launch_sum(cbuf.p, lo + 1, ctw(c, lo + 1), (int)G, out, lo + 1, lo, c->d_primes, N, c->stream);
+        launch_sum(cbuf.p, lo + 1, ctw(c, lo + 1), (int)G, out, lo + 1, lo, c->d_primes, N, c->cur);
         c->launches++;
     }
     rotate_sum(c, out, lo + 1, lo);
@@ -1444,21 +1473,21 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
                 // second call for this (database, mode): capture the pipeline once
                 const uint64_t k0 = c->launches;
                 cudaGraph_t graph;
-                CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                CU(cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
                 try {
                     match_pipeline(c, db, mg.in, mode, mg.out);
                 } catch (...) {
-                    cudaStreamEndCapture(c->stream, &graph);
+                    cudaStreamEndCapture(c->cur, &graph);
                     throw;
                 }
-                CU(cudaStreamEndCapture(c->stream, &graph));
+                CU(cudaStreamEndCapture(c->cur, &graph));
                 CU(cudaGraphInstantiate(&mg.exec, graph, 0));
                 cudaGraphDestroy(graph);
                 mg.kernels = c->launches - k0;
                 c->launches = k0;
             }
             if (mg.exec) {
-                CU(cudaGraphLaunch(mg.exec, c->stream));
+                CU(cudaGraphLaunch(mg.exec, c->cur));
                 c->launches += mg.kernels;
             } else {
                 match_pipeline(c, db, mg.in, mode, mg.out);
@@ -1476,14 +1505,14 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
 fr_status fr_sync(fr_ctx* c) {
     return guard([&] {
         need_device(c);
-        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->cur));
     });
 }
 
 fr_status fr_profile(fr_ctx* c, int enable) {
     return guard([&] {
         if (!c) raise(FR_ERR_INVALID_ARG, "null argument");
-        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->cur));
         for (auto& r : c->regions) {
             for (auto& e : r.second.pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
             r.second.pending.clear();
@@ -1498,7 +1527,7 @@ fr_status fr_profile(fr_ctx* c, int enable) {
 fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* launches, uint64_t* bytes) {
     return guard([&] {
         if (!c || !region) raise(FR_ERR_INVALID_ARG, "null argument");
-        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->cur));
         Region& r = c->regions[region];
         for (auto& e : r.pending) {
             float t = 0;
@@ -1590,7 +1619,7 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
         const size_t L1N = (size_t)(l + 1) * N;
         const u64 g = frh::galois_of_rotation(c->R, k);
         if (g == 1) {
-            CU(cudaMemcpyAsync(d_out, d_in, 2 * L1N * 8, cudaMemcpyDeviceToDevice, c->stream));
+            CU(cudaMemcpyAsync(d_out, d_in, 2 * L1N * 8, cudaMemcpyDeviceToDevice, c->cur));
             return;
         }
         const u64* key = rot_key(c, g);
@@ -1606,7 +1635,7 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
         u64* ext = a + L1N;              // [beta][npos][N]
         u64* acc = ext + (size_t)beta * npos * N;  // [2][npos][N]
         u64* conv = acc + (size_t)2 * npos * N;    // [2][l+1][N]
-        cudaStream_t st = c->stream;
+        cudaStream_t st = c->cur;
         CU(cudaMemcpyAsync(e, d_in, 2 * L1N * 8, cudaMemcpyDeviceToDevice, st));
         CU(cudaMemcpyAsync(a, d_in + L1N, L1N * 8, cudaMemcpyDeviceToDevice, st));
         const PrimeMap pl = pm_level(l);

@@ -58,6 +58,7 @@ struct Ctx {
     const u64* tw;
     const u64* tws;
     u64 q;
+    bool grow;       // forward only: q < 2^57, values may grow by 2q per stage (16 stages < 33q < 2^62)
 };
 
 // one radix-2 stage on bit B of the registers of a phase with base bit LO; the
@@ -80,7 +81,7 @@ __device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
         const int e1 = e | (1 << lb);
         if (!INV) {
             u64 X = v[e];
-            X = X >= q2 ? X - q2 : X;
+            if (!c.grow) X = X >= q2 ? X - q2 : X;
             const u64 T = shoup_lazy(v[e1], w[e], ws[e], c.q);
             v[e] = X + T;
             v[e1] = X - T + q2;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, Pol
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
     __syncthreads();
-    Ctx c{0, S, sw, sws, q};
+    Ctx c{0, S, sw, sws, q, q < (1ull << 57)};
     ColEx ex{sm, col};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
@@ -234,12 +235,17 @@ __global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
     u64 v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
-    Ctx c{Jbase, N, tw, tws, q};
+    const bool grow = q < (1ull << 57);
+    Ctx c{Jbase, N, tw, tws, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = v[e];
+    } else if (grow) {
+        const u64 one_s = R.primes[pi].one_s;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = mul_shoup(v[e], 1, one_s, q);
     } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = reduce4(v[e], q);
