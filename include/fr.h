@@ -123,7 +123,9 @@ uint64_t fr_rotation_count(uint32_t ell, uint32_t n1, uint64_t groups, uint32_t 
  * stays in host memory. */
 fr_status fr_keygen(fr_ctx* ctx, const int32_t* rotations, size_t n_rot, uint64_t seed, fr_keys** out);
 
-/* Upload the evaluation keys of `keys` to HBM (resident until fr_free). */
+/* Upload the evaluation keys of `keys` to HBM (resident until fr_free). Only the limbs the
+ * context switches are kept: Q limbs 0..working level and the P limbs, in the digits present
+ * at that level; key switching above the working level then fails with FR_ERR_LEVEL. */
 fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
 
 /* Load a plaintext template database: row-major K x ell float32 (host pointer),

@@ -114,8 +114,9 @@ __device__ __forceinline__ void ip_body(const IPJobs& jobs, int nj, bool shared_
     }
 }
 
+// key layout [digit][2][T][N]: Q limbs at positions 0.., P limbs from position kp
 __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int nj, int shared_key, int beta, int npos,
-                                                 int level, int nq, int T, const DevPrime* __restrict__ primes,
+                                                 int level, int kp, int T, const DevPrime* __restrict__ primes,
                                                  const PrimeMap pos_prime, int logN) {
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int nj, int 
     if (k >= N) return;
     const int pi = pos_prime.idx[pos];
     const u64 q = primes[pi].q, qinv = primes[pi].qinv;
-    const int klimb = pos <= level ? pos : nq + (pos - (level + 1));
+    const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
     const bool sh = shared_key != 0;
     switch (beta) {
         case 1: ip_body<1>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
@@ -523,11 +524,11 @@ void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext,
     k_modup<<<g, kThreads, 0, s>>>(in, in_eval, in_job, ext, tabs, beta, npos, N);
 }
 
-void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int nq, int T,
+void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int kp, int T,
                const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s) {
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, npos, shared_key ? 1 : J);
-    k_ip<<<g, kThreads, 0, s>>>(jobs, J, shared_key ? 1 : 0, beta, npos, level, nq, T, primes, pos_prime, logN);
+    k_ip<<<g, kThreads, 0, s>>>(jobs, J, shared_key ? 1 : 0, beta, npos, level, kp, T, primes, pos_prime, logN);
 }
 
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,

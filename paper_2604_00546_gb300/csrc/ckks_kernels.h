@@ -36,7 +36,7 @@ struct RescaleTab {
 
 struct IPJob {
     const u64* ext;  // [beta][npos][N]
-    const u64* key;  // [ndig][2][T][N], Montgomery form
+    const u64* key;  // [digits][2][T][N], Montgomery form: Q limbs 0..kp-1, then P limbs
     u64* out;        // [2][npos][N]
     u32 galois;      // 1: no automorphism
     u32 pad;
@@ -68,7 +68,7 @@ struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s);
-void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int nq, int T,
+void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int kp, int T,
                const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s);
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
                 cudaStream_t s);

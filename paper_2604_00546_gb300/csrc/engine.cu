@@ -103,6 +103,8 @@ struct fr_ctx {
     std::map<u64, u64*> rotkeys;         // galois element -> key
     u64* relin = nullptr;
     size_t key_words = 0;
+    int key_level = 0;                   // keys hold Q limbs 0..key_level (the working level) and P
+    int key_limbs = 0;                   // key_level + 1 + np
     size_t resident = 0;
     std::vector<void*> owned;            // persistent device allocations
     bool prof = false;
@@ -278,7 +280,8 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
         const double W = 8.0 * N;
         Prof p(c, "ip", W * ((same_key ? 1.0 : nj) * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos +
                              nj * 2.0 * npos));
-        launch_ip(ij, nj, same_key && nj > 1, beta, npos, level, nq, c->R.total(), c->d_primes, pm_ext(c, level),
+        launch_ip(ij, nj, same_key && nj > 1, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes,
+                  pm_ext(c, level),
                   c->R.logN, c->cur);
         c->launches++;
     }
@@ -313,6 +316,7 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
 
 void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoisted) {
     if (reqs.empty()) return;
+    if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
     const int N = c->R.N;
     const int npos = level + 1 + c->R.np, beta = c->R.digits_at(level);
     const size_t L1N = (size_t)(level + 1) * N;
@@ -942,22 +946,34 @@ fr_status fr_load_keys(fr_ctx* c, const fr_keys* k) {
         if (k->logN != c->R.logN || k->nq != c->R.nq || k->np != c->R.np)
             raise(FR_ERR_INVALID_ARG, "keys were generated for other parameters");
         CU(cudaSetDevice(c->device));
-        const int T = c->R.total();
-        const size_t words = (size_t)c->R.ndig * 2 * T * c->R.N;
+        // keys are kept only for the limbs the context can switch: Q limbs 0..work level and P
+        const int T = c->R.total(), N = c->R.N, nq = c->R.nq, np = c->R.np;
+        const int wl = c->work_level, kd = c->R.digits_at(wl), Tk = wl + 1 + np;
+        const size_t words = (size_t)kd * 2 * Tk * N;
         c->key_words = words;
+        c->key_level = wl;
+        c->key_limbs = Tk;
         size_t need = words * 8 * (1 + k->ks.rot.size());
         if (c->budget && c->resident + need > c->budget)
             raise(FR_ERR_HBM_BUDGET, "evaluation keys exceed the HBM budget");
         PrimeMap pm{};
-        pm.period = T;
-        for (int i = 0; i < T; ++i) pm.idx[i] = (unsigned char)i;
+        pm.period = Tk;
+        for (int pos = 0; pos < Tk; ++pos) pm.idx[pos] = (unsigned char)(pos <= wl ? pos : nq + pos - wl - 1);
+        std::vector<u64> stage(words);
         auto up = [&](const std::vector<u64>& h) {
-            u64* d = nullptr;
-            CU(cudaMalloc(&d, words * 8));
-            CU(cudaMemcpyAsync(d, h.data(), words * 8, cudaMemcpyHostToDevice, c->cur));
-            launch_to_mont(d, c->R.N, pm, c->d_primes, (long long)words, c->cur);
+            for (int d = 0; d < kd; ++d)
+                for (int t = 0; t < 2; ++t)
+                    for (int pos = 0; pos < Tk; ++pos) {
+                        const int src = pos <= wl ? pos : nq + pos - wl - 1;
+                        std::memcpy(&stage[(((size_t)d * 2 + t) * Tk + pos) * N], &h[(((size_t)d * 2 + t) * T + src) * N],
+                                    (size_t)N * 8);
+                    }
+            u64* dptr = nullptr;
+            CU(cudaMalloc(&dptr, words * 8));
+            CU(cudaMemcpy(dptr, stage.data(), words * 8, cudaMemcpyHostToDevice));
+            launch_to_mont(dptr, N, pm, c->d_primes, (long long)words, c->cur);
             CU(cudaStreamSynchronize(c->cur));
-            return d;
+            return dptr;
         };
         if (!c->relin) {
             c->relin = up(k->ks.relin);
@@ -1646,7 +1662,9 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
                    false, st);
         IPJobs ij;
         ij.j[0] = IPJob{ext, key, acc, (u32)g, 0};
-        launch_ip(ij, 1, false, beta, npos, l, nq, c->R.total(), c->d_primes, pm_ext(c, l), c->R.logN, st);
+        if (l > c->key_level) raise(FR_ERR_LEVEL, "the loaded keys stop at the context's working level");
+        launch_ip(ij, 1, false, beta, npos, l, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, l), c->R.logN,
+                  st);
         PrimeMap pmP{};
         pmP.period = np;
         for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
