@@ -308,6 +308,27 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ws * K / float(t.item())
 
+    # batched launches: B distinct queries per pass (fr_match_batch), same database
+    batched = None
+    if args.batch > 1:
+        qs = [ctx.encrypt(keys, q, W.enc_seed(cfg, r)).upload() for r in range(args.batch)]
+        for _ in range(2):
+            outb = ctx.match_batch(db, qs, mode)
+        ctx.sync()
+        got_b = [float(ctx.decrypt(keys, o[0])[0]) for o in outb]
+        del outb
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nb = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        outs = [ctx.match_batch(db, qs, mode) for _ in range(nb)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / nb
+        del outs
+        batched = {"queries": args.batch, "ms_per_batch": ms_b, "value": args.batch * K / (ms_b / 1000.0),
+                   "unit": UNIT, "max_abs_err": max(abs(v - pref) for v in got_b)}
+
     # the same query on the whole modulus chain (no level drop), for comparison
     full = None
     if args.level_mode == 1 and not args.no_full_chain and lq < len(c["q_bits"]) - 1:
@@ -369,6 +390,7 @@ def run_ours(args):
             "gpu_launches": int(n_launch),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "full_chain": full,
+            "batched": batched,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "check": {"membership_decrypted": got, "membership_fp64": float(pref), "abs_err": abs(got - pref)},
@@ -390,6 +412,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-full-chain", action="store_true")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -153,6 +153,14 @@ fr_status fr_encrypt_slots(const fr_ctx* ctx, const fr_keys* keys, const double*
  * device ciphertexts in *out (array freed with fr_free_cts). */
 fr_status fr_match(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out);
 
+/* Encrypted match of n_queries (1..64) queries against one database in one pass
+ * (configuration "batched launches"): every stage runs once for the whole batch, each
+ * rotation key and each plaintext diagonal word is read once for all queries. The
+ * outputs of each query equal fr_match's for that query, bit for bit. Returns
+ * n_queries * (outputs per query) handles, query after query. */
+fr_status fr_match_batch(fr_ctx* ctx, const fr_db* db, const fr_ct* const* queries, size_t n_queries, fr_mode mode,
+                         fr_ct*** out, size_t* n_out);
+
 /* Client-side decryption + decoding of up to n_slots slot values (divided by the nominal scale).
  * At level >= 1 the plaintext is recovered exactly from limbs 0 and 1 (CRT, |m| < q0 q1 / 2). */
 fr_status fr_decrypt(const fr_ctx* ctx, const fr_keys* keys, const fr_ct* ct, double* slots, size_t n_slots);

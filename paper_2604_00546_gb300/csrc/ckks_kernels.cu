@@ -92,32 +92,24 @@ __device__ __forceinline__ void ip_job(const IPJob& J, const u64 (&k0)[BETA], co
 }
 
 template <int BETA>
-__device__ __forceinline__ void ip_body(const IPJobs& jobs, int nj, bool shared_key, int npos, int pos, int klimb,
-                                        int T, int k, u64 q, u64 qinv, int logN, int N) {
+__device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, int klimb, int T, int k, u64 q,
+                                        u64 qinv, int logN, int N) {
+    // one key group per blockIdx.z: its key words are read once and applied to every job of the group
+    const int g = blockIdx.z;
+    const u64* key = jobs.gkey[g];
     u64 k0[BETA], k1[BETA];
-    if (shared_key) {
-        const u64* key = jobs.j[0].key;
 #pragma unroll
-        for (int d = 0; d < BETA; ++d) {
-            k0[d] = key[(((long long)d * 2 + 0) * T + klimb) * N + k];
-            k1[d] = key[(((long long)d * 2 + 1) * T + klimb) * N + k];
-        }
-        for (int j = 0; j < nj; ++j) ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N);
-    } else {
-        const IPJob& J = jobs.j[blockIdx.z];
-#pragma unroll
-        for (int d = 0; d < BETA; ++d) {
-            k0[d] = J.key[(((long long)d * 2 + 0) * T + klimb) * N + k];
-            k1[d] = J.key[(((long long)d * 2 + 1) * T + klimb) * N + k];
-        }
-        ip_job<BETA>(J, k0, k1, npos, pos, k, q, qinv, logN, N);
+    for (int d = 0; d < BETA; ++d) {
+        k0[d] = key[(((long long)d * 2 + 0) * T + klimb) * N + k];
+        k1[d] = key[(((long long)d * 2 + 1) * T + klimb) * N + k];
     }
+    for (int j = jobs.gstart[g]; j < jobs.gstart[g + 1]; ++j) ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N);
 }
 
 // key layout [digit][2][T][N]: Q limbs at positions 0.., P limbs from position kp
-__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int nj, int shared_key, int beta, int npos,
-                                                 int level, int kp, int T, const DevPrime* __restrict__ primes,
-                                                 const PrimeMap pos_prime, int logN) {
+__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, int npos, int level, int kp, int T,
+                                                 const DevPrime* __restrict__ primes, const PrimeMap pos_prime,
+                                                 int logN) {
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pos = blockIdx.y;
@@ -125,16 +117,15 @@ __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int nj, int 
     const int pi = pos_prime.idx[pos];
     const u64 q = primes[pi].q, qinv = primes[pi].qinv;
     const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
-    const bool sh = shared_key != 0;
     switch (beta) {
-        case 1: ip_body<1>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 2: ip_body<2>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 3: ip_body<3>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 4: ip_body<4>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 5: ip_body<5>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 6: ip_body<6>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 7: ip_body<7>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        default: ip_body<8>(jobs, nj, sh, npos, pos, klimb, T, k, q, qinv, logN, N); break;  // beta <= 8
+        case 1: ip_body<1>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 2: ip_body<2>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 3: ip_body<3>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 4: ip_body<4>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 5: ip_body<5>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 6: ip_body<6>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        case 7: ip_body<7>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
+        default: ip_body<8>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;  // beta <= 8
     }
 }
 
@@ -262,62 +253,66 @@ __global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int 
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal MAC (on-demand BSGS, Eq. eq:prerotation): for every giant step j
-//   P_j[t][i][k] = sum_{b < n1, j n1 + b < ell} baby_b[t][i][k] * D'_{j n1 + b}[i][k]
-// A CTA owns TP evaluation points of one limb. Their n1 baby words (both
-// polys) are staged in shared memory once; JG thread groups then split the
-// n2 giant steps among themselves, so every plaintext diagonal word is read
-// exactly once and the babies once per query. Two accumulator pairs (even /
-// odd b) keep two independent multiply-add chains in flight.
+// Diagonal MAC (on-demand BSGS, Eq. eq:prerotation) for B queries at once:
+//   P_{b,j}[t][i][k] = sum_{i' < n1, j n1 + i' < ell} baby_{b,i'}[t][i][k] * D'_{j n1 + i'}[i][k]
+// A CTA owns TP evaluation points of one limb. The n1 baby words (both polys)
+// of its points are staged in shared memory for every query; JG thread groups
+// split the n2 giant steps. Every plaintext diagonal word is read once for all
+// B queries, eight at a time per thread to keep loads in flight.
 // ---------------------------------------------------------------------------
-template <int TP, int JG>
-__global__ void __launch_bounds__(TP * JG) k_mac(const u64* __restrict__ babies, int cap_b,
-                                                 const u64* __restrict__ diags, u64* __restrict__ out, int cap_o,
-                                                 int nl, int n1, int n2, int ell, const DevPrime* __restrict__ primes,
-                                                 int N) {
-    extern __shared__ u64 sb[];  // [n1][2][TP]
+template <int B>
+__global__ void __launch_bounds__(512) k_mac(const u64* __restrict__ babies, long long baby_q, int cap_b,
+                                             const u64* __restrict__ diags, u64* __restrict__ out, long long out_q,
+                                             int cap_o, int nl, int n1, int n2, int ell, int TP, int JG,
+                                             const DevPrime* __restrict__ primes, int N) {
+    extern __shared__ u64 sb[];  // [B][n1][2][TP]
     const int pl = threadIdx.x % TP;
     const int jg = threadIdx.x / TP;
     const int k = blockIdx.x * TP + pl;
     const int i = blockIdx.y;
     const u64 q = primes[i].q, qinv = primes[i].qinv;
-    for (int e = threadIdx.x; e < n1 * 2 * TP; e += TP * JG) {
-        const int b = e / (2 * TP), t = (e / TP) & 1, pp = e % TP;
-        sb[e] = babies[((long long)b * 2 + t) * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp];
+    const int per_q = n1 * 2 * TP;
+    for (int e = threadIdx.x; e < B * per_q; e += TP * JG) {
+        const int b = e / per_q, r = e % per_q;
+        const int ib = r / (2 * TP), t = (r / TP) & 1, pp = r % TP;
+        sb[e] = babies[(long long)b * baby_q + ((long long)ib * 2 + t) * cap_b * N + (long long)i * N +
+                       (long long)blockIdx.x * TP + pp];
     }
     __syncthreads();
     const long long dstride = (long long)nl * N;
     for (int j = jg; j < n2; j += JG) {
         const int cnt = min(n1, ell - j * n1);
-        Acc128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+        Acc128 acc[B][2];
+#pragma unroll
+        for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
         const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
-        int b = 0;
-#pragma unroll 4
-        for (; b + 1 < cnt; b += 2) {
-            const u64 d0 = __ldcs(D + (long long)b * dstride);
-            const u64 d1 = __ldcs(D + (long long)(b + 1) * dstride);
-            mac128(a0, sb[(b * 2 + 0) * TP + pl], d0);
-            mac128(a1, sb[(b * 2 + 1) * TP + pl], d0);
-            mac128(b0, sb[(b * 2 + 2) * TP + pl], d1);
-            mac128(b1, sb[(b * 2 + 3) * TP + pl], d1);
-            if ((b & 7) == 6) { fold(a0, q); fold(a1, q); fold(b0, q); fold(b1, q); }
+        for (int i0 = 0; i0 < cnt; i0 += 8) {
+            u64 d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = (i0 + u < cnt) ? __ldcs(D + (long long)(i0 + u) * dstride) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int ib = i0 + u;
+                if (ib >= cnt) break;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const u64* sq = sb + b * per_q + ib * 2 * TP + pl;
+                    mac128(acc[b][0], sq[0], d[u]);
+                    mac128(acc[b][1], sq[TP], d[u]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                fold(acc[b][0], q);
+                fold(acc[b][1], q);
+            }
         }
-        if (b < cnt) {
-            const u64 d0 = __ldcs(D + (long long)b * dstride);
-            mac128(a0, sb[(b * 2 + 0) * TP + pl], d0);
-            mac128(a1, sb[(b * 2 + 1) * TP + pl], d0);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            u64* O = out + (long long)b * out_q + (long long)j * 2 * cap_o * N;
+            O[(long long)i * N + k] = redc(acc[b][0].hi, acc[b][0].lo, q, qinv);
+            O[((long long)cap_o + i) * N + k] = redc(acc[b][1].hi, acc[b][1].lo, q, qinv);
         }
-        fold(a0, q); fold(a1, q); fold(b0, q); fold(b1, q);
-        // a + b: both halves below q, sum of highs below 2q + 1
-        u64 lo0 = a0.lo + b0.lo, hi0 = a0.hi + b0.hi + (lo0 < a0.lo ? 1ull : 0ull);
-        u64 lo1 = a1.lo + b1.lo, hi1 = a1.hi + b1.hi + (lo1 < a1.lo ? 1ull : 0ull);
-        hi0 = hi0 >= q ? hi0 - q : hi0;
-        hi0 = hi0 >= q ? hi0 - q : hi0;
-        hi1 = hi1 >= q ? hi1 - q : hi1;
-        hi1 = hi1 >= q ? hi1 - q : hi1;
-        u64* O = out + (long long)j * 2 * cap_o * N;
-        O[(long long)i * N + k] = redc(hi0, lo0, q, qinv);
-        O[((long long)cap_o + i) * N + k] = redc(hi1, lo1, q, qinv);
     }
 }
 
@@ -524,11 +519,11 @@ void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext,
     k_modup<<<g, kThreads, 0, s>>>(in, in_eval, in_job, ext, tabs, beta, npos, N);
 }
 
-void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int kp, int T,
-               const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s) {
+void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
+               const PrimeMap& pos_prime, int logN, cudaStream_t s) {
     const int N = 1 << logN;
-    dim3 g((N + kThreads - 1) / kThreads, npos, shared_key ? 1 : J);
-    k_ip<<<g, kThreads, 0, s>>>(jobs, J, shared_key ? 1 : 0, beta, npos, level, kp, T, primes, pos_prime, logN);
+    dim3 g((N + kThreads - 1) / kThreads, npos, jobs.ngroups);
+    k_ip<<<g, kThreads, 0, s>>>(jobs, beta, npos, level, kp, T, primes, pos_prime, logN);
 }
 
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
@@ -560,17 +555,34 @@ void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* pri
     k_tensor<<<g, kThreads, 0, s>>>(jobs, level, primes, N);
 }
 
-void launch_mac(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
-                const DevPrime* primes, int N, cudaStream_t s) {
-    constexpr int TP = 128, JG = 4;
-    const size_t sm = (size_t)n1 * 2 * TP * sizeof(u64);
+template <int B>
+static void launch_mac_t(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                         int cap_o, int nl, int n1, int n2, int ell, const DevPrime* primes, int N, cudaStream_t s) {
+    // points per CTA: staged babies (B n1 2 TP words) within 128 KiB; giant-step groups up to 512 threads
+    int TP = 128;
+    while (TP > 16 && (size_t)B * n1 * 2 * TP * 8 > (128u << 10)) TP >>= 1;
+    int JG = 512 / TP;
+    if (JG > n2) JG = n2;
+    if (JG < 1) JG = 1;
+    const size_t sm = (size_t)B * n1 * 2 * TP * sizeof(u64);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mac<TP, JG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_mac<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     dim3 g(N / TP, nl);
-    k_mac<TP, JG><<<g, TP * JG, sm, s>>>(babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, primes, N);
+    k_mac<B><<<g, TP * JG, sm, s>>>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
+}
+
+void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                int cap_o, int nl, int n1, int n2, int ell, int B, const DevPrime* primes, int N, cudaStream_t s) {
+    switch (B) {
+        case 1: launch_mac_t<1>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
+        case 2: launch_mac_t<2>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
+        case 3: launch_mac_t<3>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
+        case 4: launch_mac_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
+        default: break;  // the engine splits larger batches
+    }
 }
 
 void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,

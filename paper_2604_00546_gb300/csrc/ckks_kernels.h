@@ -62,14 +62,20 @@ struct TensorJob {
 
 // job lists travel as kernel parameters (no descriptor copies, capturable in graphs)
 #define FR_MAX_JOBS 64
-struct IPJobs { IPJob j[FR_MAX_JOBS]; };
+// jobs grouped by key: group g uses gkey[g] for jobs gstart[g] .. gstart[g+1]-1
+struct IPJobs {
+    IPJob j[FR_MAX_JOBS];
+    const u64* gkey[FR_MAX_JOBS];
+    int gstart[FR_MAX_JOBS + 1];
+    int ngroups;
+};
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s);
-void launch_ip(const IPJobs& jobs, int J, bool shared_key, int beta, int npos, int level, int kp, int T,
-               const DevPrime* primes, const PrimeMap& pos_prime, int logN, cudaStream_t s);
+void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
+               const PrimeMap& pos_prime, int logN, cudaStream_t s);
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
                 cudaStream_t s);
 void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,
@@ -78,8 +84,9 @@ void launch_rescale_lift(const u64* last, u64* lifted, const RescaleTab* tab, in
 void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out, int out_cap, const RescaleTab* tab,
                             int l, int N, int BT, cudaStream_t s);
 void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s);
-void launch_mac(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
-                const DevPrime* primes, int N, cudaStream_t s);
+// B <= 4 queries: babies of query b at babies + b * baby_q, outputs at out + b * out_q
+void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                int cap_o, int nl, int n1, int n2, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,
                 long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,

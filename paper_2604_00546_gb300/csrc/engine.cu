@@ -261,28 +261,39 @@ struct KSReq {
     int out_cap;
 };
 
-void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, bool shared) {
+// inner product + ModDown of up to FR_MAX_JOBS jobs; job j reads its ModUp output ext[j].
+// Jobs arrive sorted by key: consecutive jobs with one key form one group whose key
+// words are read once.
+void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, const std::vector<const u64*>& ext) {
     const int N = c->R.N, np = c->R.np, nq = c->R.nq;
     const int npos = level + 1 + np, beta = c->R.digits_at(level);
+    const int nj = (int)reqs.size();
     Tmp acc(c, (size_t)nj * 2 * npos * N);
     Tmp conv(c, (size_t)nj * 2 * (level + 1) * N);
     IPJobs ij;
+    ij.ngroups = 0;
+    int distinct_ext = 0;
     for (int j = 0; j < nj; ++j) {
-        ij.j[j].ext = shared ? ext : ext + (size_t)j * beta * npos * N;
-        ij.j[j].key = reqs[j].key;
+        ij.j[j].ext = ext[j];
+        ij.j[j].key = reqs[j]->key;
         ij.j[j].out = acc.p + (size_t)j * 2 * npos * N;
-        ij.j[j].galois = reqs[j].galois;
+        ij.j[j].galois = reqs[j]->galois;
         ij.j[j].pad = 0;
+        if (j == 0 || reqs[j]->key != reqs[j - 1]->key) {
+            ij.gkey[ij.ngroups] = reqs[j]->key;
+            ij.gstart[ij.ngroups] = j;
+            ij.ngroups++;
+        }
+        bool seen = false;
+        for (int i = 0; i < j && !seen; ++i) seen = ext[i] == ext[j];
+        distinct_ext += seen ? 0 : 1;
     }
-    bool same_key = true;
-    for (int j = 1; j < nj; ++j) same_key &= reqs[j].key == reqs[0].key;
+    ij.gstart[ij.ngroups] = nj;
     {
         const double W = 8.0 * N;
-        Prof p(c, "ip", W * ((same_key ? 1.0 : nj) * 2.0 * beta * npos + (shared ? 1.0 : nj) * beta * npos +
-                             nj * 2.0 * npos));
-        launch_ip(ij, nj, same_key && nj > 1, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes,
-                  pm_ext(c, level),
-                  c->R.logN, c->cur);
+        Prof p(c, "ip", W * npos * (ij.ngroups * 2.0 * beta + distinct_ext * (double)beta + nj * 2.0));
+        launch_ip(ij, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, level), c->R.logN,
+                  c->cur);
         c->launches++;
     }
     PrimeMap pmP{};
@@ -296,66 +307,75 @@ void ks_finish(fr_ctx* c, int level, const KSReq* reqs, int nj, const u64* ext, 
     }
     ntt(c, conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level), false);
     MDJobs md;
+    double addw = 0;
     for (int j = 0; j < nj; ++j) {
         MDJob& m = md.j[j];
         m.acc = acc.p + (size_t)j * 2 * npos * N;
         m.conv = conv.p + (size_t)j * 2 * (level + 1) * N;
-        m.add = reqs[j].add;
-        m.add_cap = reqs[j].add_cap;
-        m.out = reqs[j].out;
-        m.out_cap = reqs[j].out_cap;
-        m.mode = reqs[j].mode;
-        m.galois = reqs[j].galois;
+        m.add = reqs[j]->add;
+        m.add_cap = reqs[j]->add_cap;
+        m.out = reqs[j]->out;
+        m.out_cap = reqs[j]->out_cap;
+        m.mode = reqs[j]->mode;
+        m.galois = reqs[j]->galois;
+        addw += reqs[j]->mode == 1 ? (level + 1) : reqs[j]->mode == 2 ? 2.0 * (level + 1) : 0;
     }
-    double addw = 0;
-    for (int j = 0; j < nj; ++j) addw += reqs[j].mode == 1 ? (level + 1) : reqs[j].mode == 2 ? 2.0 * (level + 1) : 0;
     Prof p(c, "moddown", 8.0 * N * (nj * 6.0 * (level + 1) + addw));
     launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->cur);
     c->launches++;
 }
 
-void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs, bool hoisted) {
+// Hybrid key switching of a list of requests. Requests that switch the same
+// input polynomial share one ModUp (hoisting, Algorithm 1 step 1); the others
+// get one each. Inputs are processed in groups of up to 16, their jobs sorted by
+// key so that each key is read once per inner-product launch.
+void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs) {
     if (reqs.empty()) return;
     if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
     const int N = c->R.N;
     const int npos = level + 1 + c->R.np, beta = c->R.digits_at(level);
     const size_t L1N = (size_t)(level + 1) * N;
-    if (hoisted) {
-        // one ModUp shared by every rotation of the same ciphertext (Algorithm 1, step 1)
-        Tmp in(c, 2 * L1N);
-        copy_d2d(c, in.p + L1N, reqs[0].c, L1N);
-        copy_d2d(c, in.p, reqs[0].c, L1N);
-        ntt(c, in.p, (long long)L1N, level + 1, level + 1, pm_level(level), true);
-        Tmp ext(c, (size_t)beta * npos * N);
-        {
-            Prof p(c, "modup", 8.0 * N * (2.0 * (level + 1) + (double)beta * npos));
-            launch_modup(in.p, in.p + L1N, 0, ext.p, c->d_modup[level], beta, npos, N, 1, c->cur);
-            c->launches++;
+    std::vector<const u64*> ins;
+    std::vector<int> in_of(reqs.size());
+    for (size_t j = 0; j < reqs.size(); ++j) {
+        int u = -1;
+        for (size_t i = 0; i < ins.size(); ++i)
+            if (ins[i] == reqs[j].c) { u = (int)i; break; }
+        if (u < 0) {
+            u = (int)ins.size();
+            ins.push_back(reqs[j].c);
         }
-        ntt_modup(c, ext.p, 1, level);
-        const int chunk = 32;
-        for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
-            int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
-            ks_finish(c, level, &reqs[j0], nj, ext.p, true);
-        }
-        return;
+        in_of[j] = u;
     }
-    const int chunk = 16;
-    for (size_t j0 = 0; j0 < reqs.size(); j0 += chunk) {
-        int nj = (int)std::min<size_t>(chunk, reqs.size() - j0);
-        Tmp in(c, (size_t)2 * nj * L1N);  // [nj] coefficient-form copies, then [nj] evaluation-form copies
-        u64* in_e = in.p + (size_t)nj * L1N;
-        for (int j = 0; j < nj; ++j) copy_d2d(c, in_e + (size_t)j * L1N, reqs[j0 + j].c, L1N);
-        copy_d2d(c, in.p, in_e, (size_t)nj * L1N);
-        ntt(c, in.p, (long long)L1N, level + 1, nj * (level + 1), pm_level(level), true);
-        Tmp ext(c, (size_t)nj * beta * npos * N);
+    const int UCH = 16;
+    for (size_t u0 = 0; u0 < ins.size(); u0 += UCH) {
+        const int nu = (int)std::min<size_t>(UCH, ins.size() - u0);
+        Tmp in(c, (size_t)2 * nu * L1N);  // [nu] coefficient-form copies, then [nu] evaluation-form copies
+        u64* in_e = in.p + (size_t)nu * L1N;
+        for (int u = 0; u < nu; ++u) copy_d2d(c, in_e + (size_t)u * L1N, ins[u0 + u], L1N);
+        copy_d2d(c, in.p, in_e, (size_t)nu * L1N);
+        ntt(c, in.p, (long long)L1N, level + 1, nu * (level + 1), pm_level(level), true);
+        Tmp ext(c, (size_t)nu * beta * npos * N);
         {
-            Prof p(c, "modup", 8.0 * N * nj * (2.0 * (level + 1) + (double)beta * npos));
-            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nj, c->cur);
+            Prof p(c, "modup", 8.0 * N * nu * (2.0 * (level + 1) + (double)beta * npos));
+            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nu, c->cur);
             c->launches++;
         }
-        ntt_modup(c, ext.p, nj, level);
-        ks_finish(c, level, &reqs[j0], nj, ext.p, false);
+        ntt_modup(c, ext.p, nu, level);
+        std::vector<int> js;
+        for (size_t j = 0; j < reqs.size(); ++j)
+            if (in_of[j] >= (int)u0 && in_of[j] < (int)u0 + nu) js.push_back((int)j);
+        std::stable_sort(js.begin(), js.end(), [&](int a, int b) { return reqs[a].key < reqs[b].key; });
+        const size_t JCH = 32;
+        for (size_t j0 = 0; j0 < js.size(); j0 += JCH) {
+            std::vector<const KSReq*> rq;
+            std::vector<const u64*> ex;
+            for (size_t t = j0; t < std::min(js.size(), j0 + JCH); ++t) {
+                rq.push_back(&reqs[js[t]]);
+                ex.push_back(ext.p + (size_t)(in_of[js[t]] - (int)u0) * beta * npos * N);
+            }
+            ks_finish(c, level, rq, ex);
+        }
     }
 }
 
@@ -369,7 +389,7 @@ const u64* relin_key(fr_ctx* c) {
     return c->relin;
 }
 
-// rotations of B cts (or of one ct by several indices when hoisted)
+// rotations: in[j] by ks[j] (or, hoisted, in[0] by every ks[j])
 void rotate_cts(fr_ctx* c, int level, const std::vector<const u64*>& in, int in_cap, const std::vector<long>& ks,
                 const std::vector<u64*>& out, int out_cap, bool hoisted) {
     std::vector<KSReq> reqs;
@@ -383,12 +403,9 @@ void rotate_cts(fr_ctx* c, int level, const std::vector<const u64*>& in, int in_
         }
         reqs.push_back(KSReq{src + (size_t)in_cap * N, rot_key(c, g), (u32)g, 1, src, in_cap, out[j], out_cap});
     }
-    keyswitch(c, level, reqs, hoisted);
+    keyswitch(c, level, reqs);
 }
 
-// ---------------------------------------------------------------------------
-// rescale of B cts at `level` (divide by q_level)
-// ---------------------------------------------------------------------------
 void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, int out_cap) {
     if (level < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
     const int N = c->R.N, l = level;
@@ -434,7 +451,7 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
         for (int j = 0; j < nj; ++j)
             reqs.push_back(KSReq{d.p + j * dw + (size_t)2 * (level + 1) * N, relin_key(c), 1u, 2, d.p + j * dw,
                                  level + 1, out[j0 + j], out_cap});
-        keyswitch(c, level, reqs, false);
+        keyswitch(c, level, reqs);
     }
 }
 
@@ -581,12 +598,19 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
     }
 }
 
-void rotate_sum(fr_ctx* c, u64* ct, int cap, int level) {
+// RotateAndSum of B ciphertexts [B][2][cap][N] in place: ct <- ct + Rot_{2^t}(ct), t = 0..log2(n)-1
+void rotate_sum(fr_ctx* c, u64* ct, int cap, int level, int B = 1) {
     const int n = c->R.N / 2;
-    Tmp r(c, (size_t)ctw(c, cap));
+    Tmp r(c, (size_t)B * ctw(c, cap));
+    std::vector<const u64*> in;
+    std::vector<u64*> outs;
+    for (int b = 0; b < B; ++b) {
+        in.push_back(ct + (size_t)b * ctw(c, cap));
+        outs.push_back(r.p + (size_t)b * ctw(c, cap));
+    }
     for (long t = 1; t < n; t <<= 1) {
-        rotate_cts(c, level, {ct}, cap, {t}, {r.p}, cap, false);
-        add_cts(c, ct, cap, 0, r.p, cap, 0, ct, cap, 0, level, 1);
+        rotate_cts(c, level, in, cap, std::vector<long>(B, t), outs, cap, false);
+        add_cts(c, ct, cap, ctw(c, cap), r.p, cap, ctw(c, cap), ct, cap, ctw(c, cap), level, B);
     }
 }
 
@@ -1323,7 +1347,7 @@ fr_status fr_rotate_sum(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
 
 namespace {
 
-// shapes of the match outputs: count and level
+// shapes of the match outputs per query: count and level
 void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int* lo) {
     const int L = c->work_level;
     if (mode == FR_MODE_SCORES) {
@@ -1335,94 +1359,106 @@ void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int*
     }
 }
 
-// The whole match on a query already in HBM (evaluation form, level = work level,
-// cap = level + 1); writes the output ciphertexts (cap = level + 1) contiguously to out.
-void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, fr_mode mode, u64* out) {
+// The whole match for B queries already in HBM (q: [B][2][L+1][N], evaluation form,
+// level = work level); writes each query's output ciphertexts (cap = level + 1)
+// contiguously to out, query after query. Every stage runs once for the B queries:
+// one ModUp per query, key-grouped inner products, one MAC pass over the diagonals.
+void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mode, u64* out) {
     const int L = c->work_level;
     const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
     const int n2 = (ell + n1 - 1) / n1;
     const long long G = db->G;
     const int L1 = L + 1;
-    // S2: baby steps B_i = Rot_i(q), hoisted (one ModUp for all of them)
+    const size_t cw1 = (size_t)ctw(c, L1), cw = (size_t)ctw(c, L);
+    // S2: baby steps B_{b,i} = Rot_i(q_b), hoisted per query
     std::unique_ptr<Prof> stage(new Prof(c, "stage:babies"));
-    Tmp babies(c, (size_t)n1 * ctw(c, L1));
-    copy_d2d(c, babies.p, q, ctw(c, L1));
+    Tmp babies(c, (size_t)B * n1 * cw1);  // [B][n1][2][L1][N]
+    for (int b = 0; b < B; ++b) copy_d2d(c, babies.p + (size_t)b * n1 * cw1, q + (size_t)b * cw1, cw1);
     if (n1 > 1) {
-        std::vector<long> ks;
-        std::vector<u64*> outs;
-        for (int i = 1; i < n1; ++i) {
-            ks.push_back(i);
-            outs.push_back(babies.p + (size_t)i * ctw(c, L1));
+        std::vector<KSReq> reqs;
+        for (int b = 0; b < B; ++b) {
+            u64* q0 = babies.p + (size_t)b * n1 * cw1;
+            for (int i = 1; i < n1; ++i) {
+                const u64 g = frh::galois_of_rotation(c->R, i);
+                reqs.push_back(KSReq{q0 + (size_t)L1 * N, rot_key(c, g), (u32)g, 1, q0, L1, q0 + (size_t)i * cw1, L1});
+            }
         }
-        rotate_cts(c, L, {babies.p}, L1, ks, outs, L1, true);
+        keyswitch(c, L, reqs);
     }
-    // S3-S5 per group: MAC with pre-rotated diagonals, rescale, giant rotations, sum
+    // S3-S5 per group: (tier C: encode the group's diagonals), MAC, rescale, giant rotations, sum
     stage.reset();
     const bool scores_only = mode == FR_MODE_SCORES;
-    Tmp sbuf(c, scores_only ? 1 : (size_t)G * ctw(c, L));
-    u64* S = scores_only ? out : sbuf.p;
+    Tmp sbuf(c, scores_only ? 1 : (size_t)B * G * cw);
+    u64* S = scores_only ? out : sbuf.p;  // [B][G][2][L][N]
     std::unique_ptr<Tmp> dg;
     if (db->tier == 2) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
     for (long long g = 0; g < G; ++g) {
         const u64* D = db->diags + (size_t)g * ell * L1 * N;
         if (db->tier == 2) {
-            // S3, tier C: encode this group's pre-rotated diagonals from the FP32 templates
             stage.reset(new Prof(c, "stage:encode"));
             encode_group(c, db->templates, db->K, g, dg->p);
             D = dg->p;
         }
         stage.reset(new Prof(c, "stage:mac"));
-        Tmp Pj(c, (size_t)n2 * ctw(c, L1));
-        {
-            Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-            launch_mac(babies.p, L1, D, Pj.p, L1, L1, n1, n2, ell, c->d_primes, N, c->cur);
+        Tmp Pj(c, (size_t)B * n2 * cw1);  // [B][n2][2][L1][N]
+        for (int b0 = 0; b0 < B; b0 += 4) {
+            const int nb = std::min(4, B - b0);
+            Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + nb * (2.0 * n1 + 2.0 * n2)));
+            launch_mac(babies.p + (size_t)b0 * n1 * cw1, (long long)n1 * cw1, L1, D, Pj.p + (size_t)b0 * n2 * cw1,
+                       (long long)n2 * cw1, L1, L1, n1, n2, ell, nb, c->d_primes, N, c->cur);
             c->launches++;
         }
-        Tmp Gs(c, (size_t)n2 * ctw(c, L));
-        rescale(c, Pj.p, n2, L, L1, Gs.p, L);
+        Tmp Gs(c, (size_t)B * n2 * cw);  // [B][n2][2][L][N]
+        rescale(c, Pj.p, B * n2, L, L1, Gs.p, L);
         stage.reset(new Prof(c, "stage:giants"));
         if (n2 > 1) {
-            Tmp Pr(c, (size_t)(n2 - 1) * ctw(c, L));
-            copy_d2d(c, Pr.p, Gs.p + ctw(c, L), (size_t)(n2 - 1) * ctw(c, L));
-            std::vector<const u64*> in;
-            std::vector<long> ks;
-            std::vector<u64*> outs;
+            Tmp Pr(c, (size_t)B * n2 * cw);
+            copy_d2d(c, Pr.p, Gs.p, (size_t)B * n2 * cw);
+            std::vector<KSReq> reqs;
             for (int j = 1; j < n2; ++j) {
-                in.push_back(Pr.p + (size_t)(j - 1) * ctw(c, L));
-                ks.push_back((long)j * n1);
-                outs.push_back(Gs.p + (size_t)j * ctw(c, L));
+                const u64 gk = frh::galois_of_rotation(c->R, (long)j * n1);
+                const u64* key = rot_key(c, gk);
+                for (int b = 0; b < B; ++b) {
+                    const u64* src = Pr.p + ((size_t)b * n2 + j) * cw;
+                    reqs.push_back(KSReq{src + (size_t)L * N, key, (u32)gk, 1, src, L, Gs.p + ((size_t)b * n2 + j) * cw, L});
+                }
             }
-            rotate_cts(c, L - 1, in, L, ks, outs, L, false);
+            keyswitch(c, L - 1, reqs);
         }
-        Prof p(c, "misc");
-        launch_sum(Gs.p, L, ctw(c, L), n2, S + (size_t)g * ctw(c, L), L, L - 1, c->d_primes, N, c->cur);
-        c->launches++;
+        for (int b = 0; b < B; ++b) {
+            Prof p(c, "misc", 8.0 * N * 2.0 * L * (n2 + 1));
+            launch_sum(Gs.p + (size_t)b * n2 * cw, L, cw, n2, S + ((size_t)b * G + g) * cw, L, L - 1, c->d_primes, N,
+                       c->cur);
+            c->launches++;
+        }
         stage.reset();
     }
     if (scores_only) return;
-    // S6: Chebyshev threshold on every group's scores (batched)
+    // S6: Chebyshev threshold on every (query, group) score ciphertext (batched)
     const int lo = L - 1 - c->d2;
+    const size_t cwo = (size_t)ctw(c, lo + 1);
     if (mode == FR_MODE_IDENTIFY) {
         stage.reset(new Prof(c, "stage:cheb"));
-        chebyshev(c, S, (int)G, L - 1, L, out, lo + 1);
+        chebyshev(c, S, (int)(B * G), L - 1, L, out, lo + 1);
         return;
     }
-    Tmp cbuf(c, (size_t)G * ctw(c, lo + 1));
+    Tmp cbuf(c, (size_t)B * G * cwo);
     stage.reset(new Prof(c, "stage:cheb"));
-    chebyshev(c, S, (int)G, L - 1, L, cbuf.p, lo + 1);
-    // S7: sum over groups, then RotateAndSum over all slots
+    chebyshev(c, S, (int)(B * G), L - 1, L, cbuf.p, lo + 1);
+    // S7: per query, sum over groups, then RotateAndSum over all slots
     stage.reset(new Prof(c, "stage:sum"));
-    {
+    for (int b = 0; b < B; ++b) {
         Prof p(c, "misc");
-        launch_sum(cbuf.p, lo + 1, ctw(c, lo + 1), (int)G, out, lo + 1, lo, c->d_primes, N, c->cur);
+        launch_sum(cbuf.p + (size_t)b * G * cwo, lo + 1, cwo, (int)G, out + (size_t)b * cwo, lo + 1, lo, c->d_primes,
+                   N, c->cur);
         c->launches++;
     }
-    rotate_sum(c, out, lo + 1, lo);
+    rotate_sum(c, out, lo + 1, lo, B);
 }
 
 }  // namespace
 
-// A match replayed as a CUDA graph: query staged in `in`, outputs left in `out`.
+// A match replayed as a CUDA graph: queries staged in `in`, outputs left in `out`.
 struct MatchGraph {
     cudaGraphExec_t exec = nullptr;
     u64* in = nullptr;
@@ -1433,7 +1469,7 @@ struct MatchGraph {
 
 namespace {
 std::mutex g_graph_mu;
-std::map<std::tuple<const fr_ctx*, const fr_db*, int>, MatchGraph> g_graphs;
+std::map<std::tuple<const fr_ctx*, const fr_db*, int, int>, MatchGraph> g_graphs;
 
 void drop_graphs(const fr_ctx* c, const fr_db* db) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -1448,73 +1484,92 @@ void drop_graphs(const fr_ctx* c, const fr_db* db) {
         }
     }
 }
+
+// B queries: validate, stage, run (eagerly, or as a CUDA graph from the second call with
+// the same context, database, mode and batch size on), return B * nout handles.
+void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int B, fr_mode mode, fr_ct*** out,
+                   size_t* n_out) {
+    need_device(c);
+    if (!db || !queries || !out || !n_out || B < 1) raise(FR_ERR_INVALID_ARG, "null argument or empty batch");
+    if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
+    for (int b = 0; b < B; ++b) {
+        check_ct(c, queries[b]);
+        if (queries[b]->level != c->R.nq - 1) raise(FR_ERR_LEVEL, "queries must be at the top level");
+    }
+    const int L = c->work_level;
+    if ((size_t)c->n1 * 2 * 16 * 8 > (128u << 10))
+        raise(FR_ERR_UNSUPPORTED, "n1 too large for the MAC's shared-memory staging of the baby steps");
+    if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
+    if (mode != FR_MODE_SCORES && L - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+    if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
+        raise(FR_ERR_INVALID_ARG, "unknown mode");
+    CU(cudaSetDevice(c->device));
+    const int L1 = L + 1;
+    int nout, lo;
+    match_shape(c, db, mode, &nout, &lo);
+    const size_t ow = (size_t)ctw(c, lo + 1), iw = (size_t)ctw(c, L1);
+    auto oblk = new_block(c, (size_t)B * nout * ow);
+    if (c->prof || !c->use_graphs) {
+        Tmp q(c, (size_t)B * iw);
+        for (int b = 0; b < B; ++b) to_device(c, queries[b], q.p + (size_t)b * iw, L1, L);
+        match_pipeline(c, db, q.p, B, mode, oblk->p);
+    } else {
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, db, (int)mode, B)];
+        if (!mg.in) {
+            CU(cudaMalloc(&mg.in, (size_t)B * iw * 8));
+            CU(cudaMalloc(&mg.out, (size_t)B * nout * ow * 8));
+        }
+        for (int b = 0; b < B; ++b) to_device(c, queries[b], mg.in + (size_t)b * iw, L1, L);
+        if (!mg.exec && mg.runs >= 1) {
+            const uint64_t k0 = c->launches;
+            cudaGraph_t graph;
+            CU(cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
+            try {
+                match_pipeline(c, db, mg.in, B, mode, mg.out);
+            } catch (...) {
+                cudaStreamEndCapture(c->cur, &graph);
+                throw;
+            }
+            CU(cudaStreamEndCapture(c->cur, &graph));
+            CU(cudaGraphInstantiate(&mg.exec, graph, 0));
+            cudaGraphDestroy(graph);
+            mg.kernels = c->launches - k0;
+            c->launches = k0;
+        }
+        if (mg.exec) {
+            CU(cudaGraphLaunch(mg.exec, c->cur));
+            c->launches += mg.kernels;
+        } else {
+            match_pipeline(c, db, mg.in, B, mode, mg.out);
+        }
+        mg.runs++;
+        copy_d2d(c, oblk->p, mg.out, (size_t)B * nout * ow);
+    }
+    const size_t tot = (size_t)B * nout;
+    fr_ct** arr = new fr_ct*[tot];
+    for (size_t i = 0; i < tot; ++i) arr[i] = new_dev_ct(c, oblk, oblk->p + i * ow, lo, lo + 1);
+    *out = arr;
+    *n_out = tot;
+}
 }  // namespace
 
 extern "C" {
 
 fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode, fr_ct*** out, size_t* n_out) {
     return guard([&] {
-        need_device(c);
-        if (!c || !db || !query || !out || !n_out) raise(FR_ERR_INVALID_ARG, "null argument");
-        if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
-        check_ct(c, query);
-        if (query->level != c->R.nq - 1) raise(FR_ERR_LEVEL, "the query must be at the top level");
-        const int L = c->work_level;
-        if ((size_t)c->n1 * 2 * 128 * 8 > 200 * 1024)
-            raise(FR_ERR_UNSUPPORTED, "n1 > 100: the MAC stages 2 n1 baby words per point in shared memory");
-        if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
-        if (mode != FR_MODE_SCORES && L - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
-        if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
-            raise(FR_ERR_INVALID_ARG, "unknown mode");
-        CU(cudaSetDevice(c->device));
-        const int L1 = L + 1;
-        int nout, lo;
-        match_shape(c, db, mode, &nout, &lo);
-        const size_t ow = (size_t)ctw(c, lo + 1);
-        auto oblk = new_block(c, (size_t)nout * ow);
-        if (c->prof || !c->use_graphs) {
-            // eager: S1 ingest (one H2D if host-resident) into a stream-ordered buffer
-            Tmp q(c, ctw(c, L1));
-            to_device(c, query, q.p, L1, L);
-            match_pipeline(c, db, q.p, mode, oblk->p);
-        } else {
-            std::lock_guard<std::mutex> lock(g_graph_mu);
-            MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, db, (int)mode)];
-            if (!mg.in) {
-                CU(cudaMalloc(&mg.in, ctw(c, L1) * 8));
-                CU(cudaMalloc(&mg.out, (size_t)nout * ow * 8));
-            }
-            to_device(c, query, mg.in, L1, L);
-            if (!mg.exec && mg.runs >= 1) {
-                // second call for this (database, mode): capture the pipeline once
-                const uint64_t k0 = c->launches;
-                cudaGraph_t graph;
-                CU(cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
-                try {
-                    match_pipeline(c, db, mg.in, mode, mg.out);
-                } catch (...) {
-                    cudaStreamEndCapture(c->cur, &graph);
-                    throw;
-                }
-                CU(cudaStreamEndCapture(c->cur, &graph));
-                CU(cudaGraphInstantiate(&mg.exec, graph, 0));
-                cudaGraphDestroy(graph);
-                mg.kernels = c->launches - k0;
-                c->launches = k0;
-            }
-            if (mg.exec) {
-                CU(cudaGraphLaunch(mg.exec, c->cur));
-                c->launches += mg.kernels;
-            } else {
-                match_pipeline(c, db, mg.in, mode, mg.out);
-            }
-            mg.runs++;
-            copy_d2d(c, oblk->p, mg.out, (size_t)nout * ow);
-        }
-        fr_ct** arr = new fr_ct*[nout];
-        for (int i = 0; i < nout; ++i) arr[i] = new_dev_ct(c, oblk, oblk->p + (size_t)i * ow, lo, lo + 1);
-        *out = arr;
-        *n_out = (size_t)nout;
+        if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+        const fr_ct* qs[1] = {query};
+        match_queries(c, db, qs, 1, mode, out, n_out);
+    });
+}
+
+fr_status fr_match_batch(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, size_t n_queries, fr_mode mode,
+                         fr_ct*** out, size_t* n_out) {
+    return guard([&] {
+        if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+        if (n_queries > 64) raise(FR_ERR_INVALID_ARG, "at most 64 queries per batch");
+        match_queries(c, db, queries, (int)n_queries, mode, out, n_out);
     });
 }
 
@@ -1662,9 +1717,12 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
                    false, st);
         IPJobs ij;
         ij.j[0] = IPJob{ext, key, acc, (u32)g, 0};
+        ij.gkey[0] = key;
+        ij.gstart[0] = 0;
+        ij.gstart[1] = 1;
+        ij.ngroups = 1;
         if (l > c->key_level) raise(FR_ERR_LEVEL, "the loaded keys stop at the context's working level");
-        launch_ip(ij, 1, false, beta, npos, l, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, l), c->R.logN,
-                  st);
+        launch_ip(ij, beta, npos, l, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, l), c->R.logN, st);
         PrimeMap pmP{};
         pmP.period = np;
         for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);

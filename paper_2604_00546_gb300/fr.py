@@ -29,7 +29,7 @@ FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
 
 EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
-    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_decrypt", "fr_ct_export", "fr_ct_import",
+    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
         "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_match": (st, [vp, vp, vp, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t)]),
+        "fr_match_batch": (st, [vp, vp, C.POINTER(vp), C.c_size_t, C.c_int, C.POINTER(C.POINTER(vp)),
+                                C.POINTER(C.c_size_t)]),
         "fr_decrypt": (st, [vp, vp, vp, f64p, C.c_size_t]),
         "fr_ct_export": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_uint32), C.POINTER(C.c_double)]),
         "fr_ct_import": (st, [vp, u64p, C.c_uint32, C.c_double, C.POINTER(vp)]),
@@ -268,6 +270,17 @@ class Context:
         # release only the array (the handles are owned by the Ciphertext objects)
         _lib.fr_free_cts(arr, 0)
         return cts
+
+    def match_batch(self, db, queries, mode):
+        """One pass over several queries; returns one list of output ciphertexts per query."""
+        arr = C.POINTER(C.c_void_p)()
+        n = C.c_size_t()
+        hs = (C.c_void_p * len(queries))(*[q.h.value for q in queries])
+        _check(_lib.fr_match_batch(self.h, db.h, hs, len(queries), int(mode), C.byref(arr), C.byref(n)))
+        cts = [Ciphertext(self, C.c_void_p(arr[i])) for i in range(n.value)]
+        _lib.fr_free_cts(arr, 0)
+        per = n.value // len(queries)
+        return [cts[i * per:(i + 1) * per] for i in range(len(queries))]
 
     def _unary(self, fn, ct):
         h = C.c_void_p()

@@ -261,3 +261,26 @@ def test_per_query_encoding_tier_matches_stored_diagonals(mode):
         assert len(o) == len(ref)
         for g in range(len(ref)):
             assert np.array_equal(o[g], ref[g])
+
+
+@pytest.mark.parametrize("mode", [fr.FR_MODE_IDENTIFY, fr.FR_MODE_MEMBERSHIP])
+def test_match_batch_equals_oracle_per_query(mid, mode):
+    """fr_match_batch: three queries in one pass (shared ModUp groups, key-grouped inner
+    products, one MAC pass); each query's outputs equal the oracle's; the second call
+    replays the captured graph."""
+    db = mid.ctx.load_db(mid.T)
+    rng = np.random.default_rng(33)
+    qs, refs = [], []
+    for b in range(3):
+        q = rng.standard_normal(mid.cfg["ell"])
+        q /= np.linalg.norm(q)
+        qs.append(mid.ctx.encrypt(mid.keys, q, 2000 + b))
+        oq = mid.ok.encrypt(np.tile(q, mid.oc.n // mid.cfg["ell"]), 2000 + b)
+        refs.append(mid.ok.match(oq, mid.T, mid.cfg["ell"], mid.cfg["n1"], mode, 59, 0.5)[0])
+    for call in range(2):
+        outs = mid.ctx.match_batch(db, qs, mode)
+        assert len(outs) == 3
+        for b in range(3):
+            assert len(outs[b]) == len(refs[b])
+            for g in range(len(refs[b])):
+                assert np.array_equal(outs[b][g].export(), refs[b][g]), (call, b, g)
