@@ -213,6 +213,10 @@ fr_status fr_sync(fr_ctx* ctx);
  * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc". */
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
+/* Arithmetic ceiling of the NTT on `device`: forward butterflies (Harvey lazy
+ * reduction, Shoup twiddle product, 64-bit residues) per second with every operand in
+ * registers, measured by a short microbenchmark. Used as the ALU roofline peak. */
+fr_status fr_butterfly_peak(int device, double* butterflies_per_s);
 /* Number of kernel launches issued by the library so far. */
 uint64_t fr_launch_count(const fr_ctx* ctx);
 

@@ -1635,6 +1635,18 @@ fr_status fr_ctx_info(const fr_ctx* c, uint32_t* n_slots, uint32_t* top_level, u
 
 uint32_t fr_work_level(const fr_ctx* c) { return c ? (uint32_t)c->work_level : 0; }
 
+fr_status fr_butterfly_peak(int device, double* butterflies_per_s) {
+    return guard([&] {
+        if (!butterflies_per_s) raise(FR_ERR_INVALID_ARG, "null argument");
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+            raise(FR_ERR_CUDA, "no such CUDA device");
+        CU(cudaSetDevice(device));
+        *butterflies_per_s = measure_butterfly_peak(device);
+        CU(cudaGetLastError());
+    });
+}
+
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
     if (!out) return FR_ERR_INVALID_ARG;
     std::vector<double> c;

@@ -42,6 +42,8 @@ struct RingDev {
 
 // Batched negacyclic NTT (evaluation order: position k = value at psi^(2 brev(k)+1)).
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s);
+// Butterflies per second of the NTT's forward butterfly with operands in registers.
+double measure_butterfly_peak(int device);
 
 // Fast base conversion tables for one (source set, target list).
 struct BconvTab {

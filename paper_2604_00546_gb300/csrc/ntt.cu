@@ -271,7 +271,59 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     }
 }
 
+// Register-only throughput of the forward butterfly used above (Harvey lazy reduction,
+// Shoup twiddle product): the arithmetic ceiling of the NTT on this GPU, no memory traffic.
+__global__ void __launch_bounds__(256) k_butterfly_peak(u64 q, u64 w, u64 ws, int iters, u64* sink) {
+    u64 x[8], y[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        x[e] = (threadIdx.x * 8 + e) % q;
+        y[e] = (blockIdx.x * 8 + e + 1) % q;
+    }
+    const u64 q2 = 2 * q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            u64 X = x[e];
+            X = X >= q2 ? X - q2 : X;
+            const u64 T = shoup_lazy(y[e], w, ws, q);
+            x[e] = X + T;
+            y[e] = X - T + q2;
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc ^= x[e] ^ y[e];
+    if (acc == 0x5a5a5a5a5a5a5a5aull) sink[0] = acc;  // keeps the loop live
+}
+
 }  // namespace
+
+double measure_butterfly_peak(int device) {
+    // 60-bit prime; any twiddle works for a throughput measurement
+    const u64 q = 1152921504606830593ull, w = 0x0123456789abcdefull % q;
+    const u64 ws = (u64)(((unsigned __int128)w << 64) / q);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = nsm * 8, threads = 256, iters = 4096;
+    u64* sink = nullptr;
+    if (cudaMalloc(&sink, 8) != cudaSuccess) return 0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_butterfly_peak<<<blocks, threads>>>(q, w, ws, 64, sink);  // warm-up
+    cudaEventRecord(a);
+    k_butterfly_peak<<<blocks, threads>>>(q, w, ws, iters, sink);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    if (ms <= 0) return 0;
+    return (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+}
 
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s) {
     if (b.npolys <= 0) return;

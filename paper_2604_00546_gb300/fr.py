@@ -31,7 +31,7 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count",
+    "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error",
 ]
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
         "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_uint64)]),
         "fr_launch_count": (C.c_uint64, [vp]),
+        "fr_butterfly_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
         "fr_ctx_primes": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
         "fr_ctx_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                              C.POINTER(C.c_uint64)]),
@@ -380,6 +381,12 @@ def rotation_set(ell, n1, slots, which, membership=False):
     _check(L.fr_rotation_set(int(ell), int(n1), int(slots), int(which), 1 if membership else 0, out, out.size,
                              C.byref(n)))
     return [int(x) for x in out[: n.value]]
+
+
+def butterfly_peak(device=0):
+    v = C.c_double()
+    _check(load().fr_butterfly_peak(int(device), C.byref(v)))
+    return v.value
 
 
 def rotation_count(ell, n1, groups, schedule=0):
