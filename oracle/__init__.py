@@ -121,7 +121,9 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           u64p, C.POINTER(C.c_int)]
+                           C.c_int, u64p, C.POINTER(C.c_int)]
+    L.or_table_scores.restype = C.c_int
+    L.or_table_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_set_threads.argtypes = [C.c_int]
     L.or_get_threads.restype = C.c_int
 
@@ -335,6 +337,20 @@ class Keys:
             raise ValueError("bad BSGS parameters")
         return out
 
+    def table_scores(self, qct, T, ell, n1, level=None):
+        """Scores at level-1 by the rotated-query table of Algorithm 1 (BSGS-Diagonal)."""
+        c = self.ctx
+        level = c.top if level is None else level
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        K = T.shape[0]
+        G = (K + c.n - 1) // c.n
+        out = np.empty((G, 2, level, c.N), dtype=np.uint64)
+        r = self.L.or_table_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, T, K, ell, n1,
+                                   out)
+        if r < 0:
+            raise ValueError("bad BSGS parameters")
+        return out
+
     def bsgs_scores_range(self, qct, T, ell, n1, j0, j1, level=None):
         """Scores restricted to giant steps j0 <= j < j1 (a bounded sample of the BSGS work)."""
         c = self.ctx
@@ -372,8 +388,9 @@ class Keys:
             raise ValueError("bad parameters")
         return out
 
-    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None):
-        """Full match of a top-level query ct, computed at working level `level` (default: top)."""
+    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0):
+        """Full match of a top-level query ct, computed at working level `level` (default: top);
+        schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table."""
         c = self.ctx
         lq = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
@@ -383,7 +400,7 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
-                            int(cheb_n), float(tau), out, C.byref(lvl))
+                            int(cheb_n), float(tau), int(schedule), out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

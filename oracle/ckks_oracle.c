@@ -1318,24 +1318,20 @@ int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, con
     return or_bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, out);
 }
 
-/* Naive diagonal method (Eq. equ:diag), one hoisted rotation per diagonal and a
- * single rescale; used by the pins as the textbook reference. */
-int or_diag_scores(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell, u64* out) {
-    int N = c->n, L = c->nq - 1, n = N / 2;
-    if (ell <= 0 || n % ell != 0 || L < 1) return -1;
-    long G = (K + n - 1) / n;
+/* Sum over the ell diagonals of a table of rotated queries (Eq. equ:diagbsgsgroupsprecomp):
+ * S_g = Rescale(sum_{i < ell} rotQ[i] (.) diag_i(M_g)), plain (not pre-rotated) diagonals.
+ * rotQ: [ell][2][L+1][N] evaluation form at level L; out: [G][2][L][N] at level L-1. */
+static void scores_from_table(const or_ctx* c, const u64* rq, int L, const float* T, long K, int ell, long G,
+                              u64* out) {
+    int N = c->n;
     size_t cw = ct_words(c, L), cw1 = ct_words(c, L - 1);
-    long* rots = (long*)malloc(sizeof(long) * ell);
-    for (int i = 0; i < ell; i++) rots[i] = i;
-    u64* rq = (u64*)malloc(sizeof(u64) * cw * ell);
-    or_hoisted_rotate(c, k, qct, L, rots, ell, rq);
-    for (int i = 0; i < ell; i++) ct_to_eval(c, rq + (size_t)i * cw, L, rq + (size_t)i * cw);
     u64* pt = (u64*)malloc(sizeof(u64) * (size_t)(L + 1) * N);
     u64* acc = (u64*)malloc(sizeof(u64) * cw);
     for (long g = 0; g < G; g++) {
         memset(acc, 0, sizeof(u64) * cw);
         for (int d = 0; d < ell; d++) {
             diag_pt_eval(c, T, K, ell, g, d, 0, L, pt);
+#pragma omp parallel for collapse(2)
             for (int t = 0; t < 2; t++)
                 for (int li = 0; li <= L; li++) {
                     u64 q = c->p[li];
@@ -1349,24 +1345,79 @@ int or_diag_scores(const or_ctx* c, const or_keys* k, const u64* qct, const floa
             for (int li = 0; li <= L; li++) ntt_inv(c, li, acc + ((size_t)t * (L + 1) + li) * N);
         or_rescale(c, acc, L, out + (size_t)g * cw1);
     }
-    free(rots); free(rq); free(pt); free(acc);
+    free(pt);
+    free(acc);
+}
+
+/* Naive diagonal method (Eq. equ:diag), one hoisted rotation per diagonal and a
+ * single rescale; used by the pins as the textbook reference. */
+int or_diag_scores(const or_ctx* c, const or_keys* k, const u64* qct, const float* T, long K, int ell, u64* out) {
+    int N = c->n, L = c->nq - 1, n = N / 2;
+    if (ell <= 0 || n % ell != 0 || L < 1) return -1;
+    long G = (K + n - 1) / n;
+    size_t cw = ct_words(c, L);
+    long* rots = (long*)malloc(sizeof(long) * ell);
+    for (int i = 0; i < ell; i++) rots[i] = i;
+    u64* rq = (u64*)malloc(sizeof(u64) * cw * ell);
+    or_hoisted_rotate(c, k, qct, L, rots, ell, rq);
+    for (int i = 0; i < ell; i++) ct_to_eval(c, rq + (size_t)i * cw, L, rq + (size_t)i * cw);
+    scores_from_table(c, rq, L, T, K, ell, G, out);
+    free(rots);
+    free(rq);
+    return (int)G;
+}
+
+/* BSGS-Diagonal with the full table of rotated queries (Section "BSGS with
+ * precomputation across groups", Algorithm 1):
+ *   step 1: rotQ[b] = Rot_b(q) for b < n1, hoisted over one decomposition of q;
+ *   steps 2-3: for every baby b, one decomposition of rotQ[b] shared by its giant
+ *              rotations rotQ[j n1 + b] = Rot_{j n1}(rotQ[b]), 1 <= j, j n1 + b < ell;
+ *   step 4: per group, S_g = Rescale(sum_{i < ell} rotQ[i] (.) diag_i(M_g)).
+ * The query ct is at level L; scores come out at level L-1 ([G][2][L][N]). */
+int or_table_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                    int n1, u64* out) {
+    int N = c->n, n = N / 2;
+    if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
+    int n2 = (ell + n1 - 1) / n1;
+    long G = (K + n - 1) / n;
+    size_t cw = ct_words(c, L);
+    u64* rq = (u64*)malloc(sizeof(u64) * cw * ell);
+    long* rots = (long*)malloc(sizeof(long) * (n1 > n2 ? n1 : n2));
+    for (int b = 0; b < n1; b++) rots[b] = b;
+    or_hoisted_rotate(c, k, qct, L, rots, n1, rq);  /* rotQ[0 .. n1-1], coefficient form */
+    u64* giants = (u64*)malloc(sizeof(u64) * cw * n2);
+    for (int b = 0; b < n1; b++) {
+        int nj = 0;
+        for (int j = 1; j < n2 && j * n1 + b < ell; j++) rots[nj++] = (long)j * n1;
+        if (nj == 0) continue;
+        or_hoisted_rotate(c, k, rq + (size_t)b * cw, L, rots, nj, giants);
+        for (int t = 0; t < nj; t++) memcpy(rq + (size_t)((t + 1) * n1 + b) * cw, giants + (size_t)t * cw,
+                                            sizeof(u64) * cw);
+    }
+    for (int i = 0; i < ell; i++) ct_to_eval(c, rq + (size_t)i * cw, L, rq + (size_t)i * cw);
+    scores_from_table(c, rq, L, T, K, ell, G, out);
+    free(giants);
+    free(rots);
+    free(rq);
     return (int)G;
 }
 
 /* Full match (Algorithms 5 and 6). The top-level query is first dropped to the
- * working level lq (lq = top: the whole chain). mode 0: scores (G cts, level
+ * working level lq (lq = top: the whole chain). schedule 0: on-demand BSGS with
+ * pre-rotated diagonals; schedule 1: the rotated-query table of Algorithm 1. mode 0: scores (G cts, level
  * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
  * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, u64* out, int* out_level) {
+             int cheb_n, double tau, int schedule, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
     u64* q = (u64*)malloc(sizeof(u64) * ct_words(c, top));
     or_drop(c, qct, top, lq, q);
     if (mode == 0) {
-        int r = or_bsgs_scores(c, k, q, lq, T, K, ell, n1, out);
+        int r = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, out)
+                              : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, out);
         *out_level = lq - 1;
         free(q);
         return r;
@@ -1376,7 +1427,9 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     if (d1 != 2 || lq - 1 - d2 < 0) { free(q); return -1; }
     int lo = lq - 1 - d2;
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
-    if (or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S) < 0) { free(S); free(q); return -1; }
+    int rs = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, S)
+                           : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
+    if (rs < 0) { free(S); free(q); return -1; }
     free(q);
     size_t cwo = ct_words(c, lo);
     if (mode == 1) {

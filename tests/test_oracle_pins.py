@@ -398,6 +398,46 @@ def test_bsgs_special_cases(c1, k1):
     assert np.abs(got[:ell] - Tsq.astype(np.float64) @ q).max() < 1e-4
 
 
+def test_table_schedule_matches_plain_matvec(c1, k1):
+    """Algorithm 1 (rotated-query table): decrypts to the FP64 matvec for any n1; with
+    n1 = l (babies only) or n1 = 1 (giant rotations of q only) every table entry is one
+    hoisted rotation of q, so the scores are bit-identical to the naive diagonal method."""
+    K, ell = 64, 64
+    T = _templates(K, ell, 0xF00D0007)
+    rng = np.random.default_rng(21)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k1.encrypt(np.tile(q, c1.n // ell), 23)
+    ref = T.astype(np.float64) @ q
+    for n1 in (8, 5):
+        S = k1.table_scores(qct, T, ell, n1)
+        got = k1.decrypt(S[0], 1)
+        assert np.abs(got[:K] - ref).max() < 1e-4
+        assert np.abs(got[K:]).max() < 1e-4
+        # a different composition of rotations than the on-demand schedule: same values, other noise
+        assert not np.array_equal(S, k1.bsgs_scores(qct, T, ell, n1))
+    D = k1.diag_scores(qct, T, ell)
+    assert np.array_equal(k1.table_scores(qct, T, ell, ell), D)
+    assert np.array_equal(k1.table_scores(qct, T, ell, 1), D)
+
+
+def test_table_schedule_multi_group():
+    c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
+    k = c.keygen(78)
+    ell = 16
+    K = 2 * c.n + 37
+    T = _templates(K, ell, 6)
+    rng = np.random.default_rng(1)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k.encrypt(np.tile(q, c.n // ell), 3)
+    S = k.table_scores(qct, T, ell, 4)
+    assert S.shape[0] == 3
+    ref = T.astype(np.float64) @ q
+    got = np.concatenate([k.decrypt(S[g], 1) for g in range(3)])
+    assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+
+
 def test_multi_group_packing():
     """K > numSlots: G = ceil(K / numSlots) groups (Fig. 1), score of row t in slot t mod numSlots of group t div numSlots."""
     c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
@@ -508,6 +548,11 @@ def test_match_modes_small():
     memb, lvl2 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5)
     m = k.decrypt(memb[0], lvl2)
     assert abs(m[0] - p.sum()) < 1e-2 and np.abs(m - p.sum()).max() < 1e-2
+    # the table schedule (Algorithm 1) feeds the same threshold and sum
+    memt, lvl3 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, schedule=1)
+    assert lvl3 == lvl2
+    mt = k.decrypt(memt[0], lvl3)
+    assert np.abs(mt - p.sum()).max() < 1e-2
 
 
 # ---------------------------------------------------------------------------
