@@ -404,6 +404,34 @@ def run_ours(args):
                 "steps": nf, "membership_decrypted": got_f}
         del db_f, ctx_f
 
+    # the same query by the rotated-query table of Algorithm 1 (schedule 1), for comparison
+    table = None
+    if not args.no_table:
+        ctx_t = fr.Context(device=local, cuda_stream=stream.cuda_stream, schedule=1,
+                           **W.ctx_params(cfg, level_mode=args.level_mode))
+        ctx_t.load_keys(keys)
+        db_t = ctx_t.load_db(T)
+        dq_t = ctx_t.encrypt(keys, q, W.enc_seed(cfg)).upload()
+        for _ in range(2):
+            out = step(ctx_t, db_t, dq_t)
+        ctx_t.sync()
+        got_t = float(ctx_t.decrypt(keys, out[0])[0])
+        del out
+        nt = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        outs = [step(ctx_t, db_t, dq_t) for _ in range(nt)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_t = e0.elapsed_time(e1) / nt
+        del outs
+        table = {"schedule": "table (Algorithm 1)", "ms_per_step": ms_t, "value": K / (ms_t / 1000.0), "steps": nt,
+                 "rotations": fr.rotation_count(c["ell"], c["n1"], G, 1),
+                 "rotations_on_demand": fr.rotation_count(c["ell"], c["n1"], G, 0),
+                 "membership_abs_err": abs(got_t - pref)}
+        del db_t, ctx_t
+
     # roofline of the dominant region (largest device time)
     roof = roofline(regions, c["log_n"], local, fr)
     achieved = regions[roof["kernel"]]["bytes"] / (regions[roof["kernel"]]["ms"] / 1000.0) / 1e9
@@ -436,6 +464,7 @@ def run_ours(args):
             "gpu_launches": int(n_launch),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "full_chain": full,
+            "table_schedule": table,
             "batched": batched,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -457,6 +486,7 @@ def main():
     ap.add_argument("--config", default="membership")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-full-chain", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the table-schedule comparison")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
     ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")
     args = ap.parse_args()

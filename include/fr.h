@@ -83,7 +83,10 @@ typedef struct {
     uint32_t scale_bits;       /* Delta = 2^scale_bits */
     uint32_t ell;              /* template dimension (divides N/2) */
     uint32_t n1;               /* BSGS baby steps; n2 = ceil(ell / n1) */
-    uint32_t schedule;         /* 0: on-demand BSGS with pre-rotated diagonals (only schedule implemented) */
+    uint32_t schedule;         /* BSGS schedule: 0 on demand (Algorithms 5 and 6, diagonals pre-rotated per
+                                  giant step, Eq. eq:prerotation); 1 the rotated-query table of Algorithm 1
+                                  (all ell rotations of the query, plain diagonals); 2 auto: the table when
+                                  ell - n1 < G (n2 - 1) and it fits in HBM. Fixed per database at fr_load_db. */
     uint32_t cheb_degree;      /* Chebyshev degree n of the threshold (PS split must give d1 = 2) */
     double threshold;          /* tau in step(x - tau) */
     uint64_t hbm_budget_bytes; /* 0: no budget beyond the device */
@@ -136,8 +139,9 @@ fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
 fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
 
 /* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding), its
- * number of template groups G = ceil(K / (N/2)) and its resident bytes. */
-fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes);
+ * number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule
+ * its matches run (0 on demand, 1 table). Any out-pointer may be NULL. */
+fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes, uint32_t* schedule);
 
 /* Client-side encryption of one query q (ell values) replicated across the N/2 slots
  * (numSlots/ell copies, Section "Packed matrices and batched multiplications"). */

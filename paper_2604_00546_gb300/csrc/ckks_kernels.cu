@@ -317,6 +317,65 @@ __global__ void __launch_bounds__(512) k_mac(const u64* __restrict__ babies, lon
 }
 
 // ---------------------------------------------------------------------------
+// Table-schedule MAC (Algorithm 1, step 4): S_g = sum_{m < ell} rotQ[m] (.) D_{g,m}
+// for GG groups per CTA column. One thread per evaluation point of one limb; the two
+// table words of a point are read once for the GG groups, the diagonal words streamed.
+// table: [ell][2][cap_t][N]; diagonal m of group g, limb i at diags + g dgrp + (m nl + i) N
+// (Montgomery form); output of group g at out + g og, [2][cap_o][N].
+// ---------------------------------------------------------------------------
+template <int GG>
+__global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table, int cap_t,
+                                                   const u64* __restrict__ diags, long long dgrp, int G,
+                                                   u64* __restrict__ out, int cap_o, long long og, int nl, int ell,
+                                                   const DevPrime* __restrict__ primes, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    const int g0 = blockIdx.z * GG;
+    if (k >= N) return;
+    const u64 q = primes[i].q, qinv = primes[i].qinv;
+    const long long ts = 2ll * cap_t * N, ds = (long long)nl * N;
+    const u64* t0 = table + (long long)i * N + k;
+    const u64* t1 = t0 + (long long)cap_t * N;
+    const u64* d0 = diags + (long long)g0 * dgrp + (long long)i * N + k;
+    Acc128 acc[GG][2];
+#pragma unroll
+    for (int gg = 0; gg < GG; ++gg) acc[gg][0] = acc[gg][1] = Acc128{0, 0};
+    for (int m0 = 0; m0 < ell; m0 += 4) {
+        u64 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = m0 + u < ell;
+            a[u] = ok ? t0[(long long)(m0 + u) * ts] : 0ull;
+            b[u] = ok ? t1[(long long)(m0 + u) * ts] : 0ull;
+        }
+#pragma unroll
+        for (int gg = 0; gg < GG; ++gg) {
+            if (g0 + gg < G) {
+                u64 d[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    d[u] = m0 + u < ell ? __ldcs(d0 + gg * dgrp + (long long)(m0 + u) * ds) : 0ull;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    mac128(acc[gg][0], a[u], d[u]);
+                    mac128(acc[gg][1], b[u], d[u]);
+                }
+                fold(acc[gg][0], q);
+                fold(acc[gg][1], q);
+            }
+        }
+    }
+#pragma unroll
+    for (int gg = 0; gg < GG; ++gg) {
+        if (g0 + gg < G) {
+            u64* O = out + (long long)(g0 + gg) * og;
+            O[(long long)i * N + k] = redc(acc[gg][0].hi, acc[gg][0].lo, q, qinv);
+            O[((long long)cap_o + i) * N + k] = redc(acc[gg][1].hi, acc[gg][1].lo, q, qinv);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Elementwise helpers on ciphertext batches [B][2][cap][N] (evaluation form).
 // ---------------------------------------------------------------------------
 // out = a + b over limbs 0..level of both polys
@@ -511,7 +570,6 @@ __global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* 
 // ===========================================================================
 // launchers
 // ===========================================================================
-static inline dim3 g1(int N) { return dim3((N + kThreads - 1) / kThreads); }
 
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s) {
@@ -582,6 +640,18 @@ void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags
         case 3: launch_mac_t<3>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
         case 4: launch_mac_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
         default: break;  // the engine splits larger batches
+    }
+}
+
+void launch_mac_table(const u64* table, int cap_t, const u64* diags, long long dgrp, int G, u64* out, int cap_o,
+                      long long og, int nl, int ell, const DevPrime* primes, int N, cudaStream_t s) {
+    const int GG = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
+    dim3 g((N + kThreads - 1) / kThreads, nl, (G + GG - 1) / GG);
+    switch (GG) {
+        case 8: k_mac_table<8><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        case 4: k_mac_table<4><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        case 2: k_mac_table<2><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        default: k_mac_table<1><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
     }
 }
 

@@ -87,6 +87,10 @@ void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* pri
 // B <= 4 queries: babies of query b at babies + b * baby_q, outputs at out + b * out_q
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
                 int cap_o, int nl, int n1, int n2, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
+// Table schedule (Algorithm 1): out_g = sum_{m < ell} table[m] (.) D_{g,m} for g < G (evaluation form,
+// not rescaled); table [ell][2][cap_t][N], group g's diagonals at diags + g * dgrp.
+void launch_mac_table(const u64* table, int cap_t, const u64* diags, long long dgrp, int G, u64* out, int cap_o,
+                      long long og, int nl, int ell, const DevPrime* primes, int N, cudaStream_t s);
 void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,
                 long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,

@@ -144,6 +144,7 @@ struct fr_db {
     int ell = 0;
     long long G = 0;
     int tier = 1;            // 1: pre-rotated diagonals stored in HBM; 2: encoded per query from templates
+    int schedule = 0;        // 0: on-demand BSGS (diagonals pre-rotated by j n1); 1: rotated-query table (plain diagonals)
     u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]
     float* templates = nullptr;  // tier 2: [K][ell] FP32
     size_t bytes = 0;
@@ -576,9 +577,27 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     CU(cudaStreamWaitEvent(main, c->evs[d2], 0));
 }
 
-// Encode the pre-rotated diagonals D'_{g, d} (d < ell) of template group g at the
-// working level into dst [ell][level+1][N] (evaluation + Montgomery form).
-void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst) {
+// BSGS schedule of a database with G groups. Auto (2) takes the table of Algorithm 1
+// when it needs fewer key switches than the on-demand schedule, ell - n1 < G (n2 - 1)
+// (Section "Complexity analysis of our BSGS-Diagonal"), and the table fits in HBM.
+int choose_schedule(const fr_ctx* c, long long G) {
+    if (c->schedule != 2) return (int)c->schedule;
+    const long long ell = c->ell, n1 = c->n1, n2 = (ell + n1 - 1) / n1;
+    if (ell - n1 >= G * (n2 - 1)) return 0;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    const size_t table = (size_t)ell * ctw(c, c->work_level + 1) * 8;
+    return table + ((size_t)4 << 30) <= free_b ? 1 : 0;
+}
+
+// Pre-rotation block of the stored diagonals: n1 for the on-demand schedule (D' of
+// Eq. eq:prerotation), ell (no shift) for the table schedule.
+int db_n1_enc(const fr_ctx* c, const fr_db* db) { return db->schedule == 1 ? (int)c->ell : (int)c->n1; }
+
+// Encode the diagonals of template group g at the working level into dst
+// [ell][level+1][N] (evaluation + Montgomery form), diagonal d pre-rotated by
+// (d / n1_enc) n1_enc slots (n1_enc = ell: plain diagonals).
+void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst, int n1_enc) {
     const int N = c->R.N, n = N / 2, nl = c->work_level + 1, ell = (int)c->ell;
     const int chunk = 64;
     Tmp z(c, (size_t)chunk * n * 2);
@@ -588,7 +607,7 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
         u64* o = dst + (size_t)d0 * nl * N;
         {
             Prof p(c, "encode", 8.0 * N * nd * nl);
-            launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, (int)c->n1, z.p, o, nl, c->d_primes,
+            launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, n1_enc, z.p, o, nl, c->d_primes,
                                 c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->cur);
             c->launches += 4;
         }
@@ -847,7 +866,7 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         const uint32_t n = (uint32_t)c->R.N / 2;
         if (prm->ell == 0 || n % prm->ell != 0) raise(FR_ERR_INVALID_ARG, "ell must divide N/2");
         if (prm->n1 == 0 || prm->n1 > prm->ell) raise(FR_ERR_INVALID_ARG, "need 1 <= n1 <= ell");
-        if (prm->schedule != 0) raise(FR_ERR_UNSUPPORTED, "only the on-demand BSGS schedule (0) is implemented");
+        if (prm->schedule > 2) raise(FR_ERR_INVALID_ARG, "schedule must be 0 (on demand), 1 (table) or 2 (auto)");
         c->ell = prm->ell;
         c->n1 = prm->n1;
         c->schedule = prm->schedule;
@@ -1023,6 +1042,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
         db->K = (long long)K;
         db->ell = (int)ell;
         db->G = ((long long)K + n - 1) / n;
+        db->schedule = choose_schedule(c, db->G);
         const size_t tbytes = K * ell * sizeof(float);
         const size_t dbytes = (size_t)db->G * ell * nl * N * 8;
         // storage tier: the stored diagonals when they fit (budget, or free HBM minus a
@@ -1050,7 +1070,8 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
                 raise(e == cudaErrorMemoryAllocation ? FR_ERR_HBM_BUDGET : FR_ERR_CUDA,
                       std::string("cannot hold the database diagonals: ") + cudaGetErrorString(e));
             }
-            for (long long g = 0; g < db->G; ++g) encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N);
+            for (long long g = 0; g < db->G; ++g)
+                encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N, db_n1_enc(c, db.get()));
             CU(cudaStreamSynchronize(c->cur));
             CU(cudaFree(dT));
         } else {
@@ -1062,8 +1083,9 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
     });
 }
 
-fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes) {
+fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes, uint32_t* schedule) {
     if (!db) return FR_ERR_INVALID_ARG;
+    if (schedule) *schedule = (uint32_t)db->schedule;
     if (tier) *tier = (uint32_t)db->tier;
     if (groups) *groups = (uint64_t)db->G;
     if (bytes) *bytes = (uint64_t)db->bytes;
@@ -1359,11 +1381,11 @@ void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int*
     }
 }
 
-// The whole match for B queries already in HBM (q: [B][2][L+1][N], evaluation form,
-// level = work level); writes each query's output ciphertexts (cap = level + 1)
-// contiguously to out, query after query. Every stage runs once for the B queries:
-// one ModUp per query, key-grouped inner products, one MAC pass over the diagonals.
-void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mode, u64* out) {
+// S2-S5 by the on-demand schedule for B queries already in HBM (q: [B][2][L+1][N],
+// evaluation form, level = work level): scores S [B][G][2][L][N] at level L-1. Every
+// stage runs once for the B queries: one ModUp per query, key-grouped inner products,
+// one MAC pass over the diagonals.
+void ondemand_scores(fr_ctx* c, const fr_db* db, const u64* q, int B, u64* S) {
     const int L = c->work_level;
     const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
     const int n2 = (ell + n1 - 1) / n1;
@@ -1387,16 +1409,13 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mod
     }
     // S3-S5 per group: (tier C: encode the group's diagonals), MAC, rescale, giant rotations, sum
     stage.reset();
-    const bool scores_only = mode == FR_MODE_SCORES;
-    Tmp sbuf(c, scores_only ? 1 : (size_t)B * G * cw);
-    u64* S = scores_only ? out : sbuf.p;  // [B][G][2][L][N]
     std::unique_ptr<Tmp> dg;
     if (db->tier == 2) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
     for (long long g = 0; g < G; ++g) {
         const u64* D = db->diags + (size_t)g * ell * L1 * N;
         if (db->tier == 2) {
             stage.reset(new Prof(c, "stage:encode"));
-            encode_group(c, db->templates, db->K, g, dg->p);
+            encode_group(c, db->templates, db->K, g, dg->p, (int)c->n1);
             D = dg->p;
         }
         stage.reset(new Prof(c, "stage:mac"));
@@ -1433,6 +1452,82 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mod
         }
         stage.reset();
     }
+}
+
+// S2-S5 by the rotated-query table of Algorithm 1 for one query q ([2][L+1][N], evaluation
+// form, level = work level): rotQ[i] = Rot_i(q) for i < n1, hoisted over one ModUp of q;
+// rotQ[j n1 + i] = Rot_{j n1}(rotQ[i]), hoisted over one ModUp per baby (the key switch
+// shares the ModUp of equal inputs); then S_g = Rescale(sum_{m < ell} rotQ[m] (.) D_{g,m})
+// with plain diagonals, for every group, into S [G][2][L][N] at level L-1.
+void table_scores(fr_ctx* c, const fr_db* db, const u64* q, u64* S) {
+    const int L = c->work_level, L1 = L + 1;
+    const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
+    const int n2 = (ell + n1 - 1) / n1;
+    const long long G = db->G;
+    const size_t cw1 = (size_t)ctw(c, L1), cw = (size_t)ctw(c, L);
+    std::unique_ptr<Prof> stage(new Prof(c, "stage:babies"));
+    Tmp tab(c, (size_t)ell * cw1);  // [ell][2][L1][N]
+    copy_d2d(c, tab.p, q, cw1);
+    std::vector<KSReq> reqs;
+    for (int i = 1; i < n1; ++i) {
+        const u64 g = frh::galois_of_rotation(c->R, i);
+        reqs.push_back(KSReq{tab.p + (size_t)L1 * N, rot_key(c, g), (u32)g, 1, tab.p, L1, tab.p + (size_t)i * cw1, L1});
+    }
+    keyswitch(c, L, reqs);
+    stage.reset(new Prof(c, "stage:giants"));
+    reqs.clear();
+    for (int j = 1; j < n2; ++j) {
+        const u64 gk = frh::galois_of_rotation(c->R, (long)j * n1);
+        const u64* key = rot_key(c, gk);
+        for (int i = 0; i < n1 && j * n1 + i < ell; ++i) {
+            const u64* src = tab.p + (size_t)i * cw1;
+            reqs.push_back(KSReq{src + (size_t)L1 * N, key, (u32)gk, 1, src, L1, tab.p + (size_t)(j * n1 + i) * cw1, L1});
+        }
+    }
+    keyswitch(c, L, reqs);
+    // step 4: groups in chunks (tier C encodes a chunk of groups per pass)
+    const long long GC = db->tier == 2 ? std::min<long long>(G, 8) : G;
+    std::unique_ptr<Tmp> dg;
+    if (db->tier == 2) dg.reset(new Tmp(c, (size_t)GC * ell * L1 * N));
+    for (long long g0 = 0; g0 < G; g0 += GC) {
+        const int gc = (int)std::min<long long>(GC, G - g0);
+        const u64* D = db->diags + (size_t)g0 * ell * L1 * N;
+        if (db->tier == 2) {
+            stage.reset(new Prof(c, "stage:encode"));
+            for (int t = 0; t < gc; ++t)
+                encode_group(c, db->templates, db->K, g0 + t, dg->p + (size_t)t * ell * L1 * N, ell);
+            D = dg->p;
+        }
+        stage.reset(new Prof(c, "stage:mac"));
+        Tmp Pt(c, (size_t)gc * cw1);
+        {
+            const int GG = gc >= 8 ? 8 : gc >= 4 ? 4 : gc >= 2 ? 2 : 1;
+            Prof p(c, "mac", 8.0 * N * L1 * ((double)ell * gc + 2.0 * ell * ((gc + GG - 1) / GG) + 2.0 * gc));
+            launch_mac_table(tab.p, L1, D, (long long)ell * L1 * N, gc, Pt.p, L1, (long long)cw1, L1, ell, c->d_primes,
+                             N, c->cur);
+            c->launches++;
+        }
+        rescale(c, Pt.p, gc, L, L1, S + (size_t)g0 * cw, L);
+        stage.reset();
+    }
+}
+
+// The whole match for B queries already in HBM (q: [B][2][L+1][N], evaluation form,
+// level = work level); writes each query's output ciphertexts (cap = level + 1)
+// contiguously to out, query after query.
+void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mode, u64* out) {
+    const int L = c->work_level, N = c->R.N;
+    const long long G = db->G;
+    const size_t cw1 = (size_t)ctw(c, L + 1), cw = (size_t)ctw(c, L);
+    const bool scores_only = mode == FR_MODE_SCORES;
+    Tmp sbuf(c, scores_only ? 1 : (size_t)B * G * cw);
+    u64* S = scores_only ? out : sbuf.p;  // [B][G][2][L][N]
+    if (db->schedule == 1) {
+        for (int b = 0; b < B; ++b) table_scores(c, db, q + (size_t)b * cw1, S + (size_t)b * G * cw);
+    } else {
+        ondemand_scores(c, db, q, B, S);
+    }
+    std::unique_ptr<Prof> stage;
     if (scores_only) return;
     // S6: Chebyshev threshold on every (query, group) score ciphertext (batched)
     const int lo = L - 1 - c->d2;

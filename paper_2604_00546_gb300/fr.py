@@ -84,7 +84,7 @@ def load(build_if_missing: bool = True):
         "fr_keygen": (st, [vp, i32p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_load_keys": (st, [vp, vp]),
         "fr_load_db": (st, [vp, f32p, C.c_size_t, C.c_size_t, C.POINTER(vp)]),
-        "fr_db_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+        "fr_db_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_match": (st, [vp, vp, vp, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t)]),
@@ -358,9 +358,9 @@ class Database:
         self.K = K
 
     def info(self):
-        t, g, b = C.c_uint32(), C.c_uint64(), C.c_uint64()
-        _check(_lib.fr_db_info(self.h, C.byref(t), C.byref(g), C.byref(b)))
-        return dict(tier=t.value, groups=g.value, bytes=b.value)
+        t, g, b, sc = C.c_uint32(), C.c_uint64(), C.c_uint64(), C.c_uint32()
+        _check(_lib.fr_db_info(self.h, C.byref(t), C.byref(g), C.byref(b), C.byref(sc)))
+        return dict(tier=t.value, groups=g.value, bytes=b.value, schedule=sc.value)
 
     def __del__(self):
         try:
