@@ -156,6 +156,100 @@ def K_over(K, latency):
 
 
 # ---------------------------------------------------------------------------
+def run_serving(args):
+    """Serving loop: Poisson arrivals (20 req/s by default) for --serve-seconds, 70%
+    membership / 30% identification, each against one of 8 resident databases
+    (K in {2^12, 2^14, 2^15, 2^16, 2^17, 2^18}), N=2^16 at the working level. Requests
+    are submitted at their arrival times from a producer thread through fr_match_submit
+    (host-resident query ciphertexts, so every request crosses the bus) and collected
+    with fr_match_poll; latency is submission to the end of the request's batch on the
+    device. value = templates matched per second over the whole run."""
+    import threading as th
+
+    import torch
+
+    from numpy.polynomial import chebyshev as npc
+    from paper_2604_00546_gb300 import fr
+    from paper_2604_00546_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    cfg = "membership"
+    c = W.CONFIGS[cfg]
+    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode))
+    keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
+    ctx.load_keys(keys)
+    Ts = W.serving_databases(c["ell"])
+    dbs = [ctx.load_db(T) for T in Ts]
+    qv = W.serving_queries(16, c["ell"])
+    qcts = [ctx.encrypt(keys, v, W.enc_seed(cfg, 100 + i)) for i, v in enumerate(qv)]
+    reqs = W.serving_requests(args.serve_seconds, args.serve_rate)
+    # warm-up: one request per (database, mode) class through the loop
+    ctx.serve_start(max_batch=args.serve_batch, slots=args.serve_slots)
+    warm = [ctx.submit(dbs[d], qcts[0], m) for d in range(len(dbs)) for m in (1, 2)]
+    for t in warm:
+        ctx.poll(t)
+    torch.cuda.synchronize()
+    st0 = ctx.serve_stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter() + 0.2
+
+    def producer():
+        for i, (ta, mode, d, qi) in enumerate(reqs):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = ctx.submit(dbs[d], qcts[qi], mode)
+
+    pt = th.Thread(target=producer)
+    pt.start()
+    lat, checks = [], []
+    t_last = t0
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        outs, ms = ctx.poll(tickets[i], -1, with_latency=True)
+        t_last = time.perf_counter()
+        lat.append(ms)
+        ta, mode, d, qi = reqs[i]
+        if mode == 2 and len(checks) < 4:
+            s = Ts[d].astype(np.float64) @ qv[qi]
+            n = 1 << (c["log_n"] - 1)
+            sp = np.zeros(((len(s) + n - 1) // n) * n)
+            sp[: len(s)] = s
+            pref = npc.chebval(sp, fr.cheb_coeffs(c["cheb_degree"], c["threshold"])).sum()
+            checks.append(abs(float(ctx.decrypt(keys, outs[0])[0]) - pref))
+        del outs
+    pt.join()
+    clocks = sampler.stop()
+    st1 = ctx.serve_stats()
+    ctx.serve_stop()
+    wall = t_last - t0
+    templates = sum(len(Ts[d]) for _, _, d, _ in reqs)
+    n_mem = sum(1 for r in reqs if r[1] == 2)
+    batches = st1["batches"] - st0["batches"]
+    line = {
+        "metric": "serving loop: templates matched/s and p50/p99 request latency (Poisson arrivals, 8 databases)",
+        "value": templates / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "replicas",
+        "dtype": "u64", "data": "synthetic (seeded Gaussian L2-normalised templates and queries)",
+        "config": {"workload": "serving N=2^16 ell=512 deg59 work level %d, %d req/s for %g s, 70%% membership / "
+                               "30%% identification, 8 databases K in {2^12..2^18}" % (ctx.work_level, args.serve_rate,
+                                                                                         args.serve_seconds),
+                   "max_batch": args.serve_batch, "slots": args.serve_slots,
+                   "database_K": [len(T) for T in Ts]},
+        "requests": len(reqs), "membership_requests": n_mem, "wall_s": wall,
+        "requests_per_s": len(reqs) / wall,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(np.mean(lat)), "max": float(np.max(lat))},
+        "batches": batches, "mean_batch": len(reqs) / max(1, batches),
+        "max_concurrent_batches": st1["max_concurrent_batches"],
+        "membership_abs_err_sample": checks, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if ws > 1:
@@ -489,8 +583,15 @@ def main():
     ap.add_argument("--no-table", action="store_true", help="skip the table-schedule comparison")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
     ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")
+    ap.add_argument("--serving", action="store_true", help="run the serving-loop workload instead")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=2)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.serving:
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

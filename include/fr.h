@@ -165,6 +165,53 @@ fr_status fr_match(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mod
 fr_status fr_match_batch(fr_ctx* ctx, const fr_db* db, const fr_ct* const* queries, size_t n_queries, fr_mode mode,
                          fr_ct*** out, size_t* n_out);
 
+/* ---- Serving loop (continuous batching) ------------------------------------------
+ * The paper serves one query at a time (Section "Experimental setup"; the server side of
+ * the protocol in Fig. "HyDia protocol"). This loop runs the same match for many clients:
+ * fr_match_submit queues a request and returns a ticket at once; a worker thread of the
+ * context forms a batch from the oldest request's (database, mode) class (up to max_batch
+ * requests of that class in arrival order, a power of two), admits it when one of `slots`
+ * streams is free and its workspace fits the HBM left by the batches in flight, and runs
+ * it as fr_match_batch would, so batches on different slots overlap on the device while
+ * further requests arrive. Each request's outputs equal fr_match's for that query, bit
+ * for bit. Keys and databases stay resident. While the loop runs, other calls on the
+ * context are serialised with it; a database must stay alive until its requests are
+ * polled (fr_free_db waits for the ones in flight). */
+typedef struct {
+    uint32_t max_batch;        /* 1..64 requests per batch */
+    uint32_t slots;            /* 1..8 batches in flight */
+    uint64_t hbm_budget_bytes; /* workspace budget of the batches in flight; 0: free HBM at start - 4 GiB */
+} fr_serve_params;
+
+/* Start the loop (NULL params: max_batch 8, 2 slots, budget 0). FR_ERR_INVALID_ARG when it
+ * already runs. fr_match_submit starts it with the defaults when it is not running. */
+fr_status fr_serve_start(fr_ctx* ctx, const fr_serve_params* params);
+/* Finish every pending request, then stop the worker; unpolled outputs are freed.
+ * fr_free does this first. */
+fr_status fr_serve_stop(fr_ctx* ctx);
+/* Queue a match request (same arguments and checks as fr_match). The query handle may be
+ * freed after the call: host queries are copied (working-level limbs only), device queries
+ * share their storage. */
+fr_status fr_match_submit(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mode, uint64_t* ticket);
+/* Outputs of a ticket. block_ms: 0 returns at once, > 0 waits up to that many milliseconds,
+ * < 0 waits until done. FR_ERR_TIMEOUT when not finished (the ticket stays valid); on
+ * success the ticket is consumed and *out holds *n_out handles (as fr_match). A failed
+ * request returns its error once. Unknown tickets: FR_ERR_INVALID_ARG. latency_ms (may be
+ * NULL) receives the time from submission to the end of the request's batch on the device
+ * (host steady clock, read by a callback the batch's stream runs after its last kernel). */
+fr_status fr_match_poll(fr_ctx* ctx, uint64_t ticket, int block_ms, fr_ct*** out, size_t* n_out, double* latency_ms);
+/* Requests completed, batches run, requests pending or in flight, and the largest number of
+ * batches that were in flight at once. Any out-pointer may be NULL. */
+fr_status fr_serve_stats(fr_ctx* ctx, uint64_t* completed, uint64_t* batches, uint64_t* pending,
+                         uint64_t* max_concurrent);
+/* The loop's batch planner, for inspection: classes[i] is the class of the i-th pending
+ * request in arrival order; the next batch takes requests of classes[0]'s class, at most
+ * max_batch, rounded down to a power of two, halved while ws_base + B * ws_per_query >
+ * avail_bytes. Writes the chosen indices (capacity max_batch) and their count (0: none
+ * fits). Host only. */
+fr_status fr_serve_plan(const uint32_t* classes, size_t n, uint32_t max_batch, uint64_t avail_bytes,
+                        uint64_t ws_base, uint64_t ws_per_query, uint32_t* chosen, size_t* n_chosen);
+
 /* Client-side decryption + decoding of up to n_slots slot values (divided by the nominal scale).
  * At level >= 1 the plaintext is recovered exactly from limbs 0 and 1 (CRT, |m| < q0 q1 / 2). */
 fr_status fr_decrypt(const fr_ctx* ctx, const fr_keys* keys, const fr_ct* ct, double* slots, size_t n_slots);

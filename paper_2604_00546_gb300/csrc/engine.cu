@@ -10,7 +10,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <set>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -73,6 +77,8 @@ struct Region {
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
+struct Server;
+
 struct fr_ctx {
     frh::Ring R;
     int device = 0;
@@ -113,6 +119,8 @@ struct fr_ctx {
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query
+    std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
+    Server* server = nullptr;            // continuous-batching loop (fr_match_submit / fr_match_poll)
 };
 
 struct fr_keys {
@@ -671,6 +679,7 @@ void export_words(fr_ctx* c, const fr_ct* ct, u64* buf) {
         std::memcpy(buf, ct->host.data(), 2 * L1 * N * 8);
         return;
     }
+    std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
     Tmp t(c, 2 * L1 * N);
     copy_cts(c, t.p, (int)L1, ct->dev, ct->cap, 1, ct->level);
     ntt_cts(c, t.p, 1, ct->level, (int)L1, true);
@@ -839,10 +848,15 @@ void build_leaves(fr_ctx* c) {
 
 }  // namespace
 
-DevBlock::~DevBlock() { dfree(ctx, p); }
+DevBlock::~DevBlock() {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    dfree(ctx, p);
+}
 
 namespace {
 void drop_graphs(const fr_ctx* c, const fr_db* db);  // CUDA graphs of fr_match (defined below)
+void serve_shutdown(fr_ctx* c);                       // serving loop (defined below)
+void serve_drain_db(fr_ctx* c, const fr_db* db);
 }
 
 // ===========================================================================
@@ -923,6 +937,7 @@ void fr_free(fr_ctx* c) {
         return;
     }
     cudaSetDevice(c->device);
+    serve_shutdown(c);
     cudaStreamSynchronize(c->stream);
     cudaStreamSynchronize(c->side);
     drop_graphs(c, nullptr);
@@ -985,6 +1000,7 @@ void fr_free_keys(fr_keys* k) { delete k; }
 fr_status fr_load_keys(fr_ctx* c, const fr_keys* k) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!c || !k) raise(FR_ERR_INVALID_ARG, "null argument");
         if (k->logN != c->R.logN || k->nq != c->R.nq || k->np != c->R.np)
             raise(FR_ERR_INVALID_ARG, "keys were generated for other parameters");
@@ -1033,6 +1049,7 @@ fr_status fr_load_keys(fr_ctx* c, const fr_keys* k) {
 fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr_db** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!c || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
         if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
         CU(cudaSetDevice(c->device));
@@ -1094,6 +1111,7 @@ fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t
 
 void fr_free_db(fr_db* db) {
     if (!db) return;
+    if (db->ctx) serve_drain_db(db->ctx, db);
     if (db->ctx) drop_graphs(db->ctx, db);
     if (db->ctx) {
         cudaStreamSynchronize(db->ctx->stream);
@@ -1188,6 +1206,7 @@ fr_status fr_ct_info(const fr_ct* ct, uint32_t* level, int* on_device) {
 fr_status fr_ct_upload(fr_ctx* c, fr_ct* ct) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (ct->on_dev) return;
         const int cap = ct->level + 1;
@@ -1242,6 +1261,7 @@ static const u64* dev_view(fr_ctx* c, const fr_ct* ct, std::unique_ptr<Tmp>& hol
 fr_status fr_rotate_hoisted(fr_ctx* c, const fr_ct* ct, const int32_t* ks, size_t n, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (!ks || !out || n == 0) raise(FR_ERR_INVALID_ARG, "null argument");
         CU(cudaSetDevice(c->device));
@@ -1261,6 +1281,7 @@ fr_status fr_rotate_hoisted(fr_ctx* c, const fr_ct* ct, const int32_t* ks, size_
 fr_status fr_rotate(fr_ctx* c, const fr_ct* ct, int32_t k, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
         CU(cudaSetDevice(c->device));
@@ -1277,6 +1298,7 @@ fr_status fr_rotate(fr_ctx* c, const fr_ct* ct, int32_t k, fr_ct** out) {
 fr_status fr_rescale(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
         if (ct->level < 1) raise(FR_ERR_LEVEL, "cannot rescale at level 0");
@@ -1294,6 +1316,7 @@ fr_status fr_rescale(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
 fr_status fr_mul_relin(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, a);
         check_ct(c, b);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
@@ -1313,6 +1336,7 @@ fr_status fr_mul_relin(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
 fr_status fr_add(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, a);
         check_ct(c, b);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
@@ -1331,6 +1355,7 @@ fr_status fr_add(fr_ctx* c, const fr_ct* a, const fr_ct* b, fr_ct** out) {
 fr_status fr_chebyshev(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
         if (c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
@@ -1349,6 +1374,7 @@ fr_status fr_chebyshev(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
 fr_status fr_rotate_sum(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         check_ct(c, ct);
         if (!out) raise(FR_ERR_INVALID_ARG, "null argument");
         CU(cudaSetDevice(c->device));
@@ -1585,6 +1611,7 @@ void drop_graphs(const fr_ctx* c, const fr_db* db) {
 void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int B, fr_mode mode, fr_ct*** out,
                    size_t* n_out) {
     need_device(c);
+    std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
     if (!db || !queries || !out || !n_out || B < 1) raise(FR_ERR_INVALID_ARG, "null argument or empty batch");
     if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
     for (int b = 0; b < B; ++b) {
@@ -1647,7 +1674,455 @@ void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int 
     *out = arr;
     *n_out = tot;
 }
+
+void check_match_args(fr_ctx* c, const fr_db* db, const fr_ct* q, fr_mode mode) {
+    need_device(c);
+    if (!db) raise(FR_ERR_INVALID_ARG, "null database");
+    if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
+    check_ct(c, q);
+    if (q->level != c->R.nq - 1) raise(FR_ERR_LEVEL, "queries must be at the top level");
+    if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
+        raise(FR_ERR_INVALID_ARG, "unknown mode");
+    if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
+    if (mode != FR_MODE_SCORES && c->work_level - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop (continuous batching). fr_match_submit queues a request. A worker
+// thread forms a batch from the oldest request's (database, mode) class, admits it
+// when a slot (a stream pair of its own) is free and the batch's workspace fits the
+// HBM left by the batches in flight, enqueues it through match_pipeline on the slot's
+// streams and goes on admitting; slots retire as their work completes (a host callback
+// after the batch's last operation wakes the worker), so batches overlap on the device
+// while new requests keep arriving. fr_match_poll waits for a ticket's outputs.
+// ---------------------------------------------------------------------------
+using ServeClock = std::chrono::steady_clock;
+
+struct ServeReq {
+    uint64_t ticket = 0;
+    ServeClock::time_point t_submit;
+    const fr_db* db = nullptr;
+    fr_mode mode = FR_MODE_SCORES;
+    fr_ct q;  // private copy: host words of the working-level limbs, or the shared device block
+};
+
+struct ServeResult {
+    double latency_ms = 0;  // submit -> end of the batch's device work
+    fr_status st = FR_OK;
+    std::string err;
+    std::shared_ptr<DevBlock> blk;
+    size_t first = 0;  // word offset of the request's first output
+    int nout = 0, lo = 0;
+    size_t ow = 0;
+};
+
+struct ServeSlot {
+    cudaStream_t s = nullptr, side = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    bool finished = false;  // set by the host callback enqueued after the batch
+    ServeClock::time_point t_finish;
+    const fr_db* db = nullptr;
+    std::vector<uint64_t> tickets;
+    std::vector<ServeClock::time_point> t_submit;
+    std::shared_ptr<DevBlock> out;
+    int nout = 0, lo = 0;
+    size_t ow = 0;
+    uint64_t reserved = 0;
+    std::string err;
+};
+
+struct SlotCb {
+    Server* S;
+    int k;
+};
+
 }  // namespace
+
+struct Server {
+    fr_ctx* c = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;       // worker: new request, finished slot, stop
+    std::condition_variable cv_done;  // pollers
+    std::deque<ServeReq> pending;
+    std::map<uint64_t, ServeResult> done;
+    std::set<uint64_t> inflight;
+    std::vector<ServeSlot> slots;
+    std::vector<SlotCb> cbs;
+    uint32_t max_batch = 8;
+    uint64_t avail = 0, reserved = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    uint64_t n_done = 0, n_batches = 0, max_busy = 0;
+};
+
+namespace {
+
+// Upper bound of the device workspace of one batch: base + B * per_query bytes.
+void match_workspace(const fr_ctx* c, const fr_db* db, fr_mode mode, uint64_t* base, uint64_t* per_query) {
+    const double N = c->R.N;
+    const int L = c->work_level, L1 = L + 1;
+    const double n1 = c->n1, ell = c->ell, n2 = std::ceil(ell / n1), G = (double)db->G;
+    const double beta = c->R.digits_at(L), npos = L1 + c->R.np;
+    const double cw1 = 2.0 * L1 * N, cw = 2.0 * L * N;
+    int nout, lo;
+    match_shape(c, db, mode, &nout, &lo);
+    double per = cw1 + nout * 2.0 * (lo + 1) * N + G * cw;
+    if (db->schedule != 1) per += (n1 + n2) * cw1 + 2.0 * n2 * cw;
+    if (mode != FR_MODE_SCORES) per += G * 54.0 * cw;  // threshold: powers, leaves, tree temporaries
+    double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N;  // key-switch scratch
+    if (db->schedule == 1) b += ell * cw1 + G * cw1;
+    if (db->tier == 2) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
+    *base = (uint64_t)(b * 8.0 * 1.25);
+    *per_query = (uint64_t)(per * 8.0 * 1.25);
+}
+
+void CUDART_CB slot_finished(void* p) {
+    SlotCb* cb = static_cast<SlotCb*>(p);
+    {
+        std::lock_guard<std::mutex> lk(cb->S->mu);
+        cb->S->slots[cb->k].finished = true;
+        cb->S->slots[cb->k].t_finish = ServeClock::now();
+    }
+    cb->S->cv.notify_all();
+}
+
+// Move finished slots' outputs to the done map. Called with S->mu held.
+void serve_retire(Server* S) {
+    bool any = false;
+    for (auto& sl : S->slots) {
+        if (!sl.busy || !sl.finished) continue;
+        const cudaError_t e = sl.err.empty() ? cudaEventQuery(sl.ev) : cudaSuccess;
+        for (size_t b = 0; b < sl.tickets.size(); ++b) {
+            ServeResult r;
+            r.latency_ms = std::chrono::duration<double, std::milli>(sl.t_finish - sl.t_submit[b]).count();
+            if (!sl.err.empty()) {
+                r.st = FR_ERR_CUDA;
+                r.err = sl.err;
+            } else if (e != cudaSuccess) {
+                r.st = FR_ERR_CUDA;
+                r.err = std::string("batch failed on the device: ") + cudaGetErrorString(e);
+            } else {
+                r.blk = sl.out;
+                r.first = b * (size_t)sl.nout * sl.ow;
+                r.nout = sl.nout;
+                r.lo = sl.lo;
+                r.ow = sl.ow;
+            }
+            S->done[sl.tickets[b]] = std::move(r);
+            S->inflight.erase(sl.tickets[b]);
+        }
+        S->n_done += sl.tickets.size();
+        S->n_batches++;
+        S->reserved -= sl.reserved;
+        sl.busy = false;
+        sl.finished = false;
+        sl.tickets.clear();
+        sl.db = nullptr;
+        sl.err.clear();
+        sl.out.reset();
+        any = true;
+    }
+    if (any) S->cv_done.notify_all();
+}
+
+// Admit one batch if a slot is free and memory allows. Called with lk held; releases
+// it while the batch is enqueued. Returns true when a batch was launched.
+bool serve_admit(Server* S, std::unique_lock<std::mutex>& lk) {
+    fr_ctx* c = S->c;
+    int k = -1;
+    for (size_t i = 0; i < S->slots.size(); ++i)
+        if (!S->slots[i].busy) { k = (int)i; break; }
+    if (k < 0 || S->pending.empty()) return false;
+    // classes in arrival order: requests with the oldest request's (database, mode) are class 0
+    const size_t n = S->pending.size();
+    std::vector<uint32_t> cls(n), idx(std::max<uint32_t>(S->max_batch, 1));
+    const fr_db* db = S->pending[0].db;
+    const fr_mode mode = S->pending[0].mode;
+    for (size_t i = 0; i < n; ++i) cls[i] = (S->pending[i].db == db && S->pending[i].mode == mode) ? 0u : 1u;
+    uint64_t ws_base, ws_q;
+    match_workspace(c, db, mode, &ws_base, &ws_q);
+    const uint64_t free_now = S->avail > S->reserved ? S->avail - S->reserved : 0;
+    int B = frh::plan_batch(cls.data(), n, S->max_batch, free_now, ws_base, ws_q, idx.data());
+    if (B == 0) {
+        if (S->reserved > 0) return false;  // wait for batches in flight to release memory
+        B = 1;                              // nothing in flight: run the oldest request alone
+        idx[0] = 0;
+    }
+    std::vector<ServeReq> batch;
+    {
+        std::vector<bool> take(n, false);
+        for (int b = 0; b < B; ++b) take[idx[b]] = true;
+        std::deque<ServeReq> rest;
+        for (size_t i = 0; i < n; ++i) {
+            if (take[i]) batch.push_back(std::move(S->pending[i]));
+            else rest.push_back(std::move(S->pending[i]));
+        }
+        S->pending.swap(rest);
+    }
+    ServeSlot& sl = S->slots[k];
+    sl.busy = true;
+    sl.finished = false;
+    sl.db = db;
+    sl.tickets.clear();
+    sl.t_submit.clear();
+    for (auto& r : batch) {
+        sl.tickets.push_back(r.ticket);
+        sl.t_submit.push_back(r.t_submit);
+        S->inflight.insert(r.ticket);
+    }
+    sl.reserved = ws_base + (uint64_t)B * ws_q;
+    S->reserved += sl.reserved;
+    uint64_t busy = 0;
+    for (auto& x : S->slots) busy += x.busy;
+    S->max_busy = std::max(S->max_busy, busy);
+    lk.unlock();
+    std::string err;
+    try {
+        std::lock_guard<std::recursive_mutex> cl(c->mu);
+        struct Swap {
+            fr_ctx* c;
+            cudaStream_t cur, side;
+            ~Swap() { c->cur = cur; c->side = side; }
+        } swap{c, c->cur, c->side};
+        c->cur = sl.s;
+        c->side = sl.side;
+        const int L = c->work_level, L1 = L + 1;
+        int nout, lo;
+        match_shape(c, db, mode, &nout, &lo);
+        const size_t ow = (size_t)ctw(c, lo + 1), iw = (size_t)ctw(c, L1);
+        auto oblk = new_block(c, (size_t)B * nout * ow);
+        {
+            Tmp q(c, (size_t)B * iw);
+            for (int b = 0; b < B; ++b) to_device(c, &batch[b].q, q.p + (size_t)b * iw, L1, L);
+            match_pipeline(c, db, q.p, B, mode, oblk->p);
+        }
+        CU(cudaEventRecord(sl.ev, sl.s));
+        sl.out = oblk;
+        sl.nout = nout;
+        sl.lo = lo;
+        sl.ow = ow;
+        CU(cudaLaunchHostFunc(sl.s, slot_finished, &S->cbs[k]));
+    } catch (const FrError& e) {
+        err = e.msg.empty() ? "batch failed" : e.msg;
+    } catch (const std::exception& e) {
+        err = e.what();
+    }
+    lk.lock();
+    if (!err.empty()) {
+        // nothing more was enqueued after the failure: retire the slot with the error
+        sl.err = err;
+        sl.finished = true;
+        sl.t_finish = ServeClock::now();
+        sl.out.reset();
+    }
+    return true;
+}
+
+void serve_loop(Server* S) {
+    cudaSetDevice(S->c->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        serve_retire(S);
+        bool busy = false;
+        for (auto& sl : S->slots) busy = busy || sl.busy;
+        if (S->stop && S->pending.empty() && !busy) break;
+        bool launched = false;
+        while (!S->pending.empty() && serve_admit(S, lk)) {
+            launched = true;
+            serve_retire(S);
+        }
+        if (launched) continue;
+        S->cv.wait(lk);
+    }
+}
+
+void serve_start(fr_ctx* c, uint32_t max_batch, uint32_t nslots, uint64_t budget) {
+    if (c->server) raise(FR_ERR_INVALID_ARG, "the serving loop is already running");
+    if (max_batch < 1 || max_batch > 64) raise(FR_ERR_INVALID_ARG, "max_batch must be 1..64");
+    if (nslots < 1 || nslots > 8) raise(FR_ERR_INVALID_ARG, "slots must be 1..8");
+    CU(cudaSetDevice(c->device));
+    std::unique_ptr<Server> S(new Server());
+    S->c = c;
+    S->max_batch = max_batch;
+    if (budget) {
+        S->avail = budget;
+    } else {
+        size_t free_b = 0, total_b = 0;
+        CU(cudaMemGetInfo(&free_b, &total_b));
+        const size_t margin = (size_t)4 << 30;
+        S->avail = free_b > margin ? free_b - margin : 0;
+    }
+    S->slots.resize(nslots);
+    for (uint32_t k = 0; k < nslots; ++k) {
+        CU(cudaStreamCreateWithFlags(&S->slots[k].s, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&S->slots[k].side, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&S->slots[k].ev, cudaEventDisableTiming));
+        S->cbs.push_back(SlotCb{S.get(), (int)k});
+    }
+    Server* sp = S.get();
+    S->th = std::thread([sp] { serve_loop(sp); });
+    c->server = S.release();
+}
+
+void serve_shutdown(fr_ctx* c) {
+    Server* S = c->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto& sl : S->slots) {
+        cudaStreamSynchronize(sl.s);
+        cudaStreamSynchronize(sl.side);
+    }
+    S->done.clear();
+    for (auto& sl : S->slots) {
+        cudaEventDestroy(sl.ev);
+        cudaStreamDestroy(sl.s);
+        cudaStreamDestroy(sl.side);
+    }
+    c->server = nullptr;
+    delete S;
+}
+
+void serve_drain_db(fr_ctx* c, const fr_db* db) {
+    Server* S = c ? c->server : nullptr;
+    if (!S) return;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto uses = [&] {
+        for (auto& r : S->pending)
+            if (r.db == db) return true;
+        for (auto& sl : S->slots)
+            if (sl.busy && sl.db == db) return true;
+        return false;
+    };
+    S->cv_done.wait(lk, [&] { return !uses(); });
+}
+
+}  // namespace
+
+extern "C" {
+
+fr_status fr_serve_start(fr_ctx* c, const fr_serve_params* p) {
+    return guard([&] {
+        need_device(c);
+        serve_start(c, p ? p->max_batch : 8, p ? p->slots : 2, p ? p->hbm_budget_bytes : 0);
+    });
+}
+
+fr_status fr_serve_stop(fr_ctx* c) {
+    return guard([&] {
+        need_device(c);
+        serve_shutdown(c);
+    });
+}
+
+fr_status fr_match_submit(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode, uint64_t* ticket) {
+    return guard([&] {
+        if (!ticket) raise(FR_ERR_INVALID_ARG, "null ticket pointer");
+        check_match_args(c, db, query, mode);
+        if (!c->server) serve_start(c, 8, 2, 0);
+        ServeReq r;
+        r.db = db;
+        r.mode = mode;
+        const int L = c->work_level, N = c->R.N;
+        r.q.ctx = c;
+        r.q.scale = query->scale;
+        if (query->on_dev) {
+            r.q = *query;
+        } else {
+            // keep only the limbs the match uses (the query is dropped to the working level)
+            r.q.level = L;
+            r.q.cap = L + 1;
+            r.q.on_dev = false;
+            r.q.host.resize((size_t)2 * (L + 1) * N);
+            const size_t src_l = (size_t)query->level + 1;
+            for (int t = 0; t < 2; ++t)
+                std::memcpy(r.q.host.data() + (size_t)t * (L + 1) * N, query->host.data() + (size_t)t * src_l * N,
+                            (size_t)(L + 1) * N * 8);
+        }
+        Server* S = c->server;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r.ticket = S->next_ticket++;
+            r.t_submit = ServeClock::now();
+            *ticket = r.ticket;
+            S->pending.push_back(std::move(r));
+        }
+        S->cv.notify_all();
+    });
+}
+
+fr_status fr_match_poll(fr_ctx* c, uint64_t ticket, int block_ms, fr_ct*** out, size_t* n_out, double* latency_ms) {
+    return guard([&] {
+        need_device(c);
+        if (!out || !n_out) raise(FR_ERR_INVALID_ARG, "null argument");
+        Server* S = c->server;
+        if (!S) raise(FR_ERR_INVALID_ARG, "no serving loop on this context");
+        ServeResult r;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            auto known = [&] {
+                if (S->done.count(ticket) || S->inflight.count(ticket)) return true;
+                for (auto& q : S->pending)
+                    if (q.ticket == ticket) return true;
+                return false;
+            };
+            if (!known()) raise(FR_ERR_INVALID_ARG, "unknown ticket");
+            auto ready = [&] { return S->done.count(ticket) > 0; };
+            if (!ready()) {
+                if (block_ms < 0) S->cv_done.wait(lk, ready);
+                else if (block_ms > 0) S->cv_done.wait_for(lk, std::chrono::milliseconds(block_ms), ready);
+            }
+            if (!ready()) raise(FR_ERR_TIMEOUT, "request not finished");
+            r = std::move(S->done[ticket]);
+            S->done.erase(ticket);
+        }
+        if (latency_ms) *latency_ms = r.latency_ms;
+        if (r.st != FR_OK) raise(r.st, r.err);
+        fr_ct** arr = new fr_ct*[r.nout];
+        for (int i = 0; i < r.nout; ++i) arr[i] = new_dev_ct(c, r.blk, r.blk->p + r.first + (size_t)i * r.ow, r.lo, r.lo + 1);
+        *out = arr;
+        *n_out = (size_t)r.nout;
+    });
+}
+
+fr_status fr_serve_stats(fr_ctx* c, uint64_t* completed, uint64_t* batches, uint64_t* pending,
+                         uint64_t* max_concurrent) {
+    return guard([&] {
+        need_device(c);
+        Server* S = c->server;
+        uint64_t a = 0, b = 0, p = 0, m = 0;
+        if (S) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            a = S->n_done;
+            b = S->n_batches;
+            p = S->pending.size() + S->inflight.size();
+            m = S->max_busy;
+        }
+        if (completed) *completed = a;
+        if (batches) *batches = b;
+        if (pending) *pending = p;
+        if (max_concurrent) *max_concurrent = m;
+    });
+}
+
+fr_status fr_serve_plan(const uint32_t* classes, size_t n, uint32_t max_batch, uint64_t avail_bytes,
+                        uint64_t ws_base, uint64_t ws_per_query, uint32_t* chosen, size_t* n_chosen) {
+    return guard([&] {
+        if ((n && !classes) || !chosen || !n_chosen) raise(FR_ERR_INVALID_ARG, "null argument");
+        std::vector<uint32_t> idx(std::max<uint32_t>(max_batch, 1));
+        const int B = frh::plan_batch(classes, n, max_batch, avail_bytes, ws_base, ws_per_query, idx.data());
+        for (int b = 0; b < B; ++b) chosen[b] = idx[b];
+        *n_chosen = (size_t)B;
+    });
+}
+
+}  // extern "C"
 
 extern "C" {
 
@@ -1671,6 +2146,7 @@ fr_status fr_match_batch(fr_ctx* c, const fr_db* db, const fr_ct* const* queries
 fr_status fr_sync(fr_ctx* c) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         CU(cudaStreamSynchronize(c->cur));
     });
 }
@@ -1790,6 +2266,7 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
                                        uint64_t* d_out) {
     return guard([&] {
         need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!d_in || !d_out) raise(FR_ERR_INVALID_ARG, "null buffer");
         if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
         CU(cudaSetDevice(c->device));

@@ -102,4 +102,12 @@ enum RotVariant { RV_ONDEMAND = 0, RV_CPU_BSGS = 1, RV_HYDIA_DG = 2, RV_TBS_ONLI
                   RV_TBE_TOTAL = 5, RV_TABLE = 6 };
 bool rotation_set(uint32_t ell, uint32_t n1, uint32_t slots, int variant, bool membership, std::vector<long>& out);
 
+// Continuous-batching planner. Pending requests are given by class id (one class per
+// (database, mode)) in arrival order. The next batch serves the oldest request's class:
+// up to max_batch requests of that class in arrival order, the count rounded down to a
+// power of two, then halved while ws_base + B ws_per_query exceeds avail. Returns B
+// (0 when not even one request fits) and writes the chosen indices to idx.
+int plan_batch(const uint32_t* cls, size_t n, uint32_t max_batch, uint64_t avail, uint64_t ws_base,
+               uint64_t ws_per_query, uint32_t* idx);
+
 }  // namespace frh

@@ -634,4 +634,16 @@ bool rotation_set(uint32_t ell, uint32_t n1, uint32_t slots, int variant, bool m
     return true;
 }
 
+int plan_batch(const uint32_t* cls, size_t n, uint32_t max_batch, uint64_t avail, uint64_t ws_base,
+               uint64_t ws_per_query, uint32_t* idx) {
+    if (n == 0 || max_batch == 0) return 0;
+    uint32_t cnt = 0;
+    for (size_t i = 0; i < n && cnt < max_batch; ++i)
+        if (cls[i] == cls[0]) idx[cnt++] = (uint32_t)i;
+    uint32_t B = 1;
+    while (B * 2 <= cnt) B *= 2;
+    while (B > 0 && ws_base + (uint64_t)B * ws_per_query > avail) B /= 2;
+    return (int)B;
+}
+
 }  // namespace frh

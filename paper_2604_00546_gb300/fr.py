@@ -33,8 +33,13 @@ EXPORTED = [
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
-    "fr_free", "fr_last_error",
+    "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
+    "fr_serve_stats", "fr_serve_plan",
 ]
+
+
+class ServeParams(C.Structure):
+    _fields_ = [("max_batch", C.c_uint32), ("slots", C.c_uint32), ("hbm_budget_bytes", C.c_uint64)]
 
 
 class FrError(RuntimeError):
@@ -120,6 +125,16 @@ def load(build_if_missing: bool = True):
         "fr_free_db": (None, [vp]),
         "fr_free": (None, [vp]),
         "fr_last_error": (C.c_char_p, []),
+        "fr_serve_start": (st, [vp, C.POINTER(ServeParams)]),
+        "fr_serve_stop": (st, [vp]),
+        "fr_match_submit": (st, [vp, vp, vp, C.c_int, C.POINTER(C.c_uint64)]),
+        "fr_match_poll": (st, [vp, C.c_uint64, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t),
+                               C.POINTER(C.c_double)]),
+        "fr_serve_stats": (st, [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                C.POINTER(C.c_uint64)]),
+        "fr_serve_plan": (st, [np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), C.c_size_t, C.c_uint32,
+                               C.c_uint64, C.c_uint64, C.c_uint64,
+                               np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), C.POINTER(C.c_size_t)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -283,6 +298,39 @@ class Context:
         per = n.value // len(queries)
         return [cts[i * per:(i + 1) * per] for i in range(len(queries))]
 
+    # -- serving loop (continuous batching) ------------------------------------------
+    def serve_start(self, max_batch=8, slots=2, hbm_budget_bytes=0):
+        p = ServeParams(int(max_batch), int(slots), int(hbm_budget_bytes))
+        _check(_lib.fr_serve_start(self.h, C.byref(p)))
+
+    def serve_stop(self):
+        _check(_lib.fr_serve_stop(self.h))
+
+    def submit(self, db, query, mode):
+        """Queue a match request; returns its ticket."""
+        t = C.c_uint64()
+        _check(_lib.fr_match_submit(self.h, db.h, query.h, int(mode), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket, block_ms=-1, with_latency=False):
+        """Outputs of a ticket (list of ciphertexts), or None when not finished within block_ms;
+        with_latency: (outputs, submit-to-device-completion milliseconds)."""
+        arr = C.POINTER(C.c_void_p)()
+        n = C.c_size_t()
+        lat = C.c_double()
+        st = _lib.fr_match_poll(self.h, C.c_uint64(ticket), int(block_ms), C.byref(arr), C.byref(n), C.byref(lat))
+        if st == FR_ERR_TIMEOUT:
+            return None
+        _check(st)
+        cts = [Ciphertext(self, C.c_void_p(arr[i])) for i in range(n.value)]
+        _lib.fr_free_cts(arr, 0)
+        return (cts, lat.value) if with_latency else cts
+
+    def serve_stats(self):
+        a, b, p, m = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(_lib.fr_serve_stats(self.h, C.byref(a), C.byref(b), C.byref(p), C.byref(m)))
+        return dict(completed=a.value, batches=b.value, outstanding=p.value, max_concurrent_batches=m.value)
+
     def _unary(self, fn, ct):
         h = C.c_void_p()
         _check(fn(self.h, ct.h, C.byref(h)))
@@ -380,6 +428,16 @@ def rotation_set(ell, n1, slots, which, membership=False):
     n = C.c_size_t()
     _check(L.fr_rotation_set(int(ell), int(n1), int(slots), int(which), 1 if membership else 0, out, out.size,
                              C.byref(n)))
+    return [int(x) for x in out[: n.value]]
+
+
+def serve_plan(classes, max_batch, avail_bytes, ws_base, ws_per_query):
+    """The serving loop's batch planner (host only): indices of the next batch."""
+    cls = np.ascontiguousarray(classes, dtype=np.uint32)
+    out = np.zeros(max(1, int(max_batch)), dtype=np.uint32)
+    n = C.c_size_t()
+    _check(load().fr_serve_plan(cls, len(cls), int(max_batch), int(avail_bytes), int(ws_base), int(ws_per_query),
+                                out, C.byref(n)))
     return [int(x) for x in out[: n.value]]
 
 

@@ -116,3 +116,36 @@ def key_seed(cfg):
 def enc_seed(cfg, request=0):
     c = CONFIGS[cfg] if isinstance(cfg, str) else cfg
     return ENC_SEED + c["seed"] + request
+
+
+# Serving loop: Poisson arrivals against 8 resident databases. The six listed database
+# sizes are assigned to the 8 databases cyclically (db d has K = SERVING_SIZES[d mod 6]).
+SERVING_SIZES = [1 << 12, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18]
+SERVING_DBS = 8
+SERVING_SEED = 0x5E7E0000
+
+
+def serving_databases(ell=512):
+    """Template sets of the 8 serving databases (seeded Gaussian, L2-normalised, float32)."""
+    return [templates(SERVING_SIZES[d % len(SERVING_SIZES)], ell, SERVING_SEED + d) for d in range(SERVING_DBS)]
+
+
+def serving_requests(duration_s=60.0, rate=20.0, membership_share=0.7, n_queries=16, seed=SERVING_SEED):
+    """Request stream: arrival times (Poisson process of `rate` per second over duration_s),
+    mode (membership with probability membership_share, else identification), database
+    index (uniform over the 8) and query index (uniform over a pool of n_queries)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration_s:
+            break
+        mode = 2 if rng.random() < membership_share else 1
+        out.append((t, mode, int(rng.integers(SERVING_DBS)), int(rng.integers(n_queries))))
+    return out
+
+
+def serving_queries(n_queries=16, ell=512, seed=SERVING_SEED + 100):
+    rng = np.random.default_rng(seed)
+    return [unit(rng, ell) for _ in range(n_queries)]
+
