@@ -155,6 +155,21 @@ def K_over(K, latency):
     return K / latency
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """Largest value of x over all ranks (x itself on one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world_size, units_per_rank, max_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world_size * units_per_rank / (max_ms / 1000.0)
+
+
 # ---------------------------------------------------------------------------
 def run_serving(args):
     """Serving loop: Poisson arrivals (20 req/s by default) for --serve-seconds, 70%
@@ -413,12 +428,8 @@ def run_ours(args):
         lat.append(ev[i].elapsed_time(ev[i + 1]))
     total_ms = ev[0].elapsed_time(ev[-1])
     del outs
-    tmax = total_ms
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = ws * K * args.steps / (tmax / 1000.0)
+    tmax = max_over_ranks(total_ms, dist, dev)
+    value = whole_job_value(ws, K * args.steps, tmax)
 
     # per-region device time: the same steps again, eagerly, with CUDA events around every launch
     ctx.profile(True)
@@ -446,11 +457,7 @@ def run_ours(args):
         words = [r.export() for r in res]
         e2e_t.append(time.perf_counter() - a)
         d2h = sum(w.nbytes for w in words)
-    e2e_value = K / float(np.mean(e2e_t))
-    if dist:
-        t = torch.tensor([float(np.mean(e2e_t))], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_value = ws * K / float(t.item())
+    e2e_value = whole_job_value(ws, K, 1000.0 * max_over_ranks(float(np.mean(e2e_t)), dist, dev))
 
     # batched launches: B distinct queries per pass (fr_match_batch), same database
     batched = None
