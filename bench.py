@@ -103,8 +103,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle: bounded sample of one query, extrapolated to the full query
 # ---------------------------------------------------------------------------
-def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None):
-    """Time a bounded sample of the oracle's work for one query computed at level lq."""
+def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None, reps=5):
+    """Time a bounded sample of the oracle's work for one query computed at level lq: each
+    primitive of the query is timed `reps` times (mean taken), about 10 s of CPU work."""
     import oracle
     from paper_2604_00546_gb300 import workloads as W
     c = W.CONFIGS[cfgname]
@@ -118,10 +119,16 @@ def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None):
     oq = oc.drop(ok.encrypt(np.tile(q, oc.n // ell), seed_enc), oc.top, L)
     tm = {}
 
+    spent = [0.0]
+
     def timed(name, f):
-        t0 = time.perf_counter()
-        r = f()
-        tm[name] = time.perf_counter() - t0
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = f()
+            ts.append(time.perf_counter() - t0)
+        tm[name] = float(np.mean(ts))
+        spent[0] += float(np.sum(ts))
         return r
 
     timed("h1", lambda: ok.hoisted_rotate(oq, L, [1]))
@@ -143,8 +150,8 @@ def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None):
     n_mul = (2 ** (d2 - 1) - 1) + (d2 - 1)
     steps_sum = int(np.log2(oc.n))
     latency = babies + G * (n2 * tm["giant"] + (n2 - 1) * tm["rot_giant"] + n_mul * tm["mul_mid"]) + steps_sum * tm["rot_sum"]
-    work = sum(tm.values())
-    sample = (f"oracle timed on: hoisted rotations by {{1}} and {{1,2}} at level {L} (baby cost = t1 + {n1 - 2} x marginal), "
+    work = spent[0]
+    sample = (f"oracle timed ({reps} repetitions each, mean) on: hoisted rotations by {{1}} and {{1,2}} at level {L} (baby cost = t1 + {n1 - 2} x marginal), "
               f"one giant step (encode {n1} diagonals + MAC + rescale, x{n2}), one giant rotation at level {L - 1} "
               f"(x{n2 - 1}), one ct x ct + relin + rescale at level {mid} (x{n_mul}), one rotation at level {lo} "
               f"(x{steps_sum}); extrapolated query latency {latency:.1f} s from {work:.1f} s of CPU work")
@@ -282,7 +289,7 @@ def run_reference(args):
     sample = cores = None
     t_all = time.perf_counter()
     for s in range(args.warmup + args.steps):
-        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq)
+        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq, reps=1)
         if s >= args.warmup:
             vals.append(v)
             lat.append(l)
