@@ -55,7 +55,9 @@ struct PhaseInfo {
 
 struct Ctx {
     int Jbase, M;    // global index of the tile's element 0; M = R (column pass) or N (row pass)
-    const u64* tw;
+    int cb, TT;      // shared-memory twiddle table of the CTA: stage B's entries start at
+                     // TT - (TT >> B) and hold global indices from cb >> (B + 1) on
+    const u64* tw;   // (shared memory)
     const u64* tws;
     u64 q;
     bool grow;       // forward only: q < 2^57, values may grow by 2q per stage (16 stages < 33q < 2^62)
@@ -72,8 +74,9 @@ __device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
     for (int e = 0; e < 8; ++e) {
         if (e & (1 << lb)) continue;
         const int idx = (c.M + c.Jbase + phase_x<LO>(tau, e)) >> (B + 1);
-        w[e] = c.tw[idx];
-        ws[e] = c.tws[idx];
+        const int li = idx - (c.cb >> (B + 1)) + c.TT - (c.TT >> B);
+        w[e] = c.tw[li];
+        ws[e] = c.tws[li];
     }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -148,10 +151,11 @@ struct ColEx {
 };
 
 // Shared-memory word of element x of a row: the low 4 bits are XORed with bits 4..6
-// (x4 -> bit 0, x5 -> bits 1 and 3, x6 -> bit 2). For 256-point rows this keeps every
-// half-warp access of the three phase layouts on 16 distinct 8-byte bank pairs.
+// (x4 -> bit 0, x5 -> bit 2, x6 -> bits 1 and 3). For 256-point rows this keeps every
+// half-warp access of the forward (bits from 5, 2, 0) and inverse (0, 3, 5) phase layouts
+// on 16 distinct 8-byte bank pairs.
 __device__ __forceinline__ int row_swz(int x) {
-    return x ^ ((x >> 4) & 1) ^ (((x >> 5) & 1) * 10) ^ (((x >> 6) & 1) << 2);
+    return x ^ ((x >> 4) & 1) ^ (((x >> 5) & 1) << 2) ^ (((x >> 6) & 1) * 10);
 }
 
 // exchange through shared memory, one row
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, Pol
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
     __syncthreads();
-    Ctx c{0, S, sw, sws, q, q < (1ull << 57)};
+    Ctx c{0, S, 0, 0, sw, sws, q, q < (1ull << 57)};
     ColEx ex{sm, col};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
@@ -235,8 +239,22 @@ __global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
     u64 v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
+    // the twiddles of the CTA's rows, stage by stage (contiguous global ranges), into shared memory
+    constexpr int TT = RPC * S;
+    u64* stw = sm + RPC * SP;
+    u64* stws = stw + (TT - RPC);
+    const int cb = N + blockIdx.x * RPC * S;
+#pragma unroll
+    for (int B = 0; B < LOG; ++B) {
+        const int cnt = TT >> (B + 1), off = TT - (TT >> B), g0 = cb >> (B + 1);
+        for (int i = threadIdx.x; i < cnt; i += RPC * TPR) {
+            stw[off + i] = tw[g0 + i];
+            stws[off + i] = tws[g0 + i];
+        }
+    }
+    __syncthreads();
     const bool grow = q < (1ull << 57);
-    Ctx c{Jbase, N, tw, tws, q, grow};
+    Ctx c{Jbase, N, cb, TT, stw, stws, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
@@ -261,7 +279,14 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
     constexpr int TPR = SC / 8, RPC = (256 / TPR < SR) ? 256 / TPR : SR;
     dim3 gr(SR / RPC, b.npolys);
-    const size_t smr = (size_t)RPC * SC * sizeof(u64);
+    // rows, then the rows' twiddles (w and Shoup quotient) of every stage
+    constexpr size_t smr = (size_t)(RPC * SC + 2 * (RPC * SC - RPC)) * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ntt_row<LOGC, LOGR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        cudaFuncSetAttribute(k_ntt_row<LOGC, LOGR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        attr = true;
+    }
     if (!inverse) {
         k_ntt_col<LOGR, false><<<gc, tc, smc, st>>>(R, b);
         k_ntt_row<LOGC, LOGR, false><<<gr, RPC * TPR, smr, st>>>(R, b);
