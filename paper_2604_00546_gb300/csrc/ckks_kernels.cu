@@ -46,6 +46,8 @@ __device__ __forceinline__ void modup_body(const ModUpTab& T, const u64* __restr
 __global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, const u64* __restrict__ in_eval,
                                                     long long in_job, u64* __restrict__ ext,
                                                     const ModUpTab* __restrict__ tabs, int beta, int npos, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int d = blockIdx.y;
     const int j = blockIdx.z;
@@ -110,6 +112,8 @@ __device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, i
 __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, int npos, int level, int kp, int T,
                                                  const DevPrime* __restrict__ primes, const PrimeMap pos_prime,
                                                  int logN) {
+    pdl_wait();
+    pdl_trigger();
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pos = blockIdx.y;
@@ -153,6 +157,8 @@ __device__ __forceinline__ void p2q_body(const u64* __restrict__ x, u64* __restr
 __global__ void __launch_bounds__(kThreads) k_p2q(const u64* __restrict__ acc, long long acc_job, int npos,
                                                   int level, u64* __restrict__ conv, const P2QTab* __restrict__ tab,
                                                   int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
     const int j = blockIdx.z;
@@ -177,6 +183,8 @@ __global__ void __launch_bounds__(kThreads) k_moddown_combine(const MDJobs jobs,
                                                               const u64* __restrict__ pinv,
                                                               const u64* __restrict__ pinv_s,
                                                               const DevPrime* __restrict__ primes, int logN) {
+    pdl_wait();
+    pdl_trigger();
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % (level + 1);
@@ -204,6 +212,8 @@ __global__ void __launch_bounds__(kThreads) k_moddown_combine(const MDJobs jobs,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_rescale_lift(const u64* __restrict__ last, u64* __restrict__ lifted,
                                                            const RescaleTab* __restrict__ tab, int l, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int bt = blockIdx.y;
     if (k >= N) return;
@@ -223,6 +233,8 @@ __global__ void __launch_bounds__(kThreads) k_rescale_combine(const u64* __restr
                                                               const u64* __restrict__ lifted, u64* __restrict__ out,
                                                               int out_cap, const RescaleTab* __restrict__ tab, int l,
                                                               int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % l;
     const int bt = blockIdx.y / l;
@@ -239,6 +251,8 @@ __global__ void __launch_bounds__(kThreads) k_rescale_combine(const u64* __restr
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int level,
                                                      const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     const TensorJob& J = jobs.j[blockIdx.z];
@@ -265,6 +279,8 @@ __global__ void __launch_bounds__(512) k_mac(const u64* __restrict__ babies, lon
                                              const u64* __restrict__ diags, u64* __restrict__ out, long long out_q,
                                              int cap_o, int nl, int n1, int n2, int ell, int TP, int JG,
                                              const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ u64 sb[];  // [B][n1][2][TP]
     const int pl = threadIdx.x % TP;
     const int jg = threadIdx.x / TP;
@@ -328,6 +344,8 @@ __global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table
                                                    const u64* __restrict__ diags, long long dgrp, int G,
                                                    u64* __restrict__ out, int cap_o, long long og, int nl, int ell,
                                                    const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     const int g0 = blockIdx.z * GG;
@@ -381,6 +399,8 @@ __global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table
 // out = a + b over limbs 0..level of both polys
 __global__ void k_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
                       int o_cap, long long o_bs, int level, const DevPrime* primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % (level + 1);
     const int t = blockIdx.y / (level + 1);
@@ -395,6 +415,8 @@ __global__ void k_add(const u64* a, int a_cap, long long a_bs, const u64* b, int
 // sum of J ciphertexts (stride js) into out
 __global__ void k_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level,
                       const DevPrime* primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % (level + 1);
     const int t = blockIdx.y / (level + 1);
@@ -408,6 +430,8 @@ __global__ void k_sum(const u64* a, int cap, long long js, int J, u64* out, int 
 // Chebyshev leaves: out[leaf] = x * cb[leaf] + (c0 += ca[leaf])   (before rescale)
 __global__ void k_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, const u64* cb,
                               const u64* cb_s, const u64* ca, const DevPrime* primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % (level + 1);
     const int t = blockIdx.y / (level + 1);
@@ -422,6 +446,8 @@ __global__ void k_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int 
 
 // x <- 2 x - c (c added to the constant term: every evaluation point of c0)
 __global__ void k_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y % (level + 1);
     const int t = blockIdx.y / (level + 1);
@@ -434,6 +460,8 @@ __global__ void k_double_sub(u64* x, int cap, int level, const u64* cres, const 
 }
 
 __global__ void k_to_mont(u64* x, long long n_per_poly, PrimeMap pm, const DevPrime* primes, long long total) {
+    pdl_wait();
+    pdl_trigger();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int p = (int)(e / n_per_poly);
@@ -465,6 +493,8 @@ __device__ __forceinline__ void fft_inv_bfly(cplx& a, cplx& b, double wr, double
 // z[x] = diag_d(M_k)[(x - shift) mod n], diag_d(M_k)[b ell + r] = T[(k B + b) ell + r][(r + d) mod ell]
 __global__ void k_diag_gather(const float* __restrict__ T, long long K, int ell, int n, long long grp, int d0, int nd,
                               int n1, cplx* __restrict__ z) {
+    pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int di = blockIdx.y;
     if (x >= n || di >= nd) return;
@@ -482,6 +512,8 @@ __global__ void k_diag_gather(const float* __restrict__ T, long long K, int ell,
 // first log2(R) stages (len = n .. 2n/R): columns of stride n/R; one tile of 16 columns
 __global__ void __launch_bounds__(256) k_fft_col(cplx* z, int logn, int logR, const unsigned* rot, const double* zr,
                                                  const double* zi) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ cplx sc[];
     const int n = 1 << logn, Rr = 1 << logR, C = n >> logR;
     const int TC = 16;
@@ -515,6 +547,8 @@ __global__ void __launch_bounds__(256) k_fft_col(cplx* z, int logn, int logR, co
 // remaining stages (len = C .. 2) inside contiguous blocks of C
 __global__ void __launch_bounds__(256) k_fft_row(cplx* z, int logn, int logR, int bpc, const unsigned* rot,
                                                  const double* zr, const double* zi) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ cplx sc[];
     const int n = 1 << logn, C = n >> logR;
     const long long M = 4ll * n;
@@ -539,6 +573,8 @@ __global__ void __launch_bounds__(256) k_fft_row(cplx* z, int logn, int logR, in
 // bit reversal, scaling, rounding and residues: out [nd][nl][N] (coefficient form)
 __global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* __restrict__ out, int nl,
                              const DevPrime* __restrict__ primes, int scale_bits) {
+    pdl_wait();
+    pdl_trigger();
     const int n = 1 << logn;
     const int N = 2 * n;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -574,43 +610,43 @@ __global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* 
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, beta, J);
-    k_modup<<<g, kThreads, 0, s>>>(in, in_eval, in_job, ext, tabs, beta, npos, N);
+    launch_k(k_modup, dim3(g), dim3(kThreads), 0, s, in, in_eval, in_job, ext, tabs, beta, npos, N);
 }
 
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
                const PrimeMap& pos_prime, int logN, cudaStream_t s) {
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, npos, jobs.ngroups);
-    k_ip<<<g, kThreads, 0, s>>>(jobs, beta, npos, level, kp, T, primes, pos_prime, logN);
+    launch_k(k_ip, dim3(g), dim3(kThreads), 0, s, jobs, beta, npos, level, kp, T, primes, pos_prime, logN);
 }
 
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
                 cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2, J);
-    k_p2q<<<g, kThreads, 0, s>>>(acc, acc_job, npos, level, conv, tab, N);
+    launch_k(k_p2q, dim3(g), dim3(kThreads), 0, s, acc, acc_job, npos, level, conv, tab, N);
 }
 
 void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,
                             const DevPrime* primes, int logN, cudaStream_t s) {
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), J);
-    k_moddown_combine<<<g, kThreads, 0, s>>>(jobs, npos, level, pinv, pinv_s, primes, logN);
+    launch_k(k_moddown_combine, dim3(g), dim3(kThreads), 0, s, jobs, npos, level, pinv, pinv_s, primes, logN);
 }
 
 void launch_rescale_lift(const u64* last, u64* lifted, const RescaleTab* tab, int l, int N, int BT, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, BT);
-    k_rescale_lift<<<g, kThreads, 0, s>>>(last, lifted, tab, l, N);
+    launch_k(k_rescale_lift, dim3(g), dim3(kThreads), 0, s, last, lifted, tab, l, N);
 }
 
 void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out, int out_cap, const RescaleTab* tab,
                             int l, int N, int BT, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, BT * l);
-    k_rescale_combine<<<g, kThreads, 0, s>>>(x, x_cap, lifted, out, out_cap, tab, l, N);
+    launch_k(k_rescale_combine, dim3(g), dim3(kThreads), 0, s, x, x_cap, lifted, out, out_cap, tab, l, N);
 }
 
 void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, level + 1, J);
-    k_tensor<<<g, kThreads, 0, s>>>(jobs, level, primes, N);
+    launch_k(k_tensor, dim3(g), dim3(kThreads), 0, s, jobs, level, primes, N);
 }
 
 template <int B>
@@ -629,7 +665,7 @@ static void launch_mac_t(const u64* babies, long long baby_q, int cap_b, const u
         attr = true;
     }
     dim3 g(N / TP, nl);
-    k_mac<B><<<g, TP * JG, sm, s>>>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
+    launch_k(k_mac<B>, dim3(g), dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
 }
 
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
@@ -648,41 +684,41 @@ void launch_mac_table(const u64* table, int cap_t, const u64* diags, long long d
     const int GG = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
     dim3 g((N + kThreads - 1) / kThreads, nl, (G + GG - 1) / GG);
     switch (GG) {
-        case 8: k_mac_table<8><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
-        case 4: k_mac_table<4><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
-        case 2: k_mac_table<2><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
-        default: k_mac_table<1><<<g, kThreads, 0, s>>>(table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        case 8: launch_k(k_mac_table<8>, dim3(g), dim3(kThreads), 0, s, table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        case 4: launch_k(k_mac_table<4>, dim3(g), dim3(kThreads), 0, s, table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        case 2: launch_k(k_mac_table<2>, dim3(g), dim3(kThreads), 0, s, table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
+        default: launch_k(k_mac_table<1>, dim3(g), dim3(kThreads), 0, s, table, cap_t, diags, dgrp, G, out, cap_o, og, nl, ell, primes, N); break;
     }
 }
 
 void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out, int o_cap,
                 long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), B);
-    k_add<<<g, kThreads, 0, s>>>(a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, primes, N);
+    launch_k(k_add, dim3(g), dim3(kThreads), 0, s, a, a_cap, a_bs, b, b_cap, b_bs, out, o_cap, o_bs, level, primes, N);
 }
 
 void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,
                 int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1));
-    k_sum<<<g, kThreads, 0, s>>>(a, cap, js, J, out, o_cap, level, primes, N);
+    launch_k(k_sum, dim3(g), dim3(kThreads), 0, s, a, cap, js, J, out, o_cap, level, primes, N);
 }
 
 void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
                         const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), nleaves);
-    k_cheb_leaves<<<g, kThreads, 0, s>>>(x, x_cap, out, o_cap, level, cb, cb_s, ca, primes, N);
+    launch_k(k_cheb_leaves, dim3(g), dim3(kThreads), 0, s, x, x_cap, out, o_cap, level, cb, cb_s, ca, primes, N);
 }
 
 void launch_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1));
-    k_double_sub<<<g, kThreads, 0, s>>>(x, cap, level, cres, primes, N);
+    launch_k(k_double_sub, dim3(g), dim3(kThreads), 0, s, x, cap, level, cres, primes, N);
 }
 
 void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,
                     cudaStream_t s) {
     long long blocks = (total + kThreads - 1) / kThreads;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_to_mont<<<(unsigned)blocks, kThreads, 0, s>>>(x, n_per_poly, pm, primes, total);
+    launch_k(k_to_mont, dim3((unsigned)blocks), dim3(kThreads), 0, s, x, n_per_poly, pm, primes, total);
 }
 
 void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
@@ -692,14 +728,14 @@ void launch_encode_diags(const float* T, long long K, int ell, int logn, long lo
     cplx* z = (cplx*)zbuf;
     {
         dim3 g((n + kThreads - 1) / kThreads, nd);
-        k_diag_gather<<<g, kThreads, 0, s>>>(T, K, ell, n, grp, d0, nd, n1, z);
+        launch_k(k_diag_gather, dim3(g), dim3(kThreads), 0, s, T, K, ell, n, grp, d0, nd, n1, z);
     }
     const int logR = logn / 2;
     const int Rr = 1 << logR, C = n >> logR;
     {
         dim3 g(C / 16, nd);
         const size_t sm = (size_t)Rr * 16 * sizeof(cplx);
-        k_fft_col<<<g, 256, sm, s>>>(z, logn, logR, rot, zr, zi);
+        launch_k(k_fft_col, dim3(g), dim3(256), sm, s, z, logn, logR, rot, zr, zi);
     }
     {
         int bpc = 1024 / C;
@@ -707,10 +743,10 @@ void launch_encode_diags(const float* T, long long K, int ell, int logn, long lo
         if (bpc > Rr) bpc = Rr;
         dim3 g(Rr / bpc, nd);
         const size_t sm = (size_t)bpc * C * sizeof(cplx);
-        k_fft_row<<<g, 256, sm, s>>>(z, logn, logR, bpc, rot, zr, zi);
+        launch_k(k_fft_row, dim3(g), dim3(256), sm, s, z, logn, logR, bpc, rot, zr, zi);
     }
     {
         dim3 g((2 * n + kThreads - 1) / kThreads, nd);
-        k_fft_finish<<<g, kThreads, 0, s>>>(z, logn, nd, out_coeff, nl, primes, scale_bits);
+        launch_k(k_fft_finish, dim3(g), dim3(kThreads), 0, s, z, logn, nd, out_coeff, nl, primes, scale_bits);
     }
 }

@@ -5,6 +5,32 @@
 
 #include "dev_arith.cuh"
 
+// Programmatic dependent launch. Every kernel of the library starts with pdl_wait(), so it
+// touches no memory before the kernel ahead of it in the stream has completed and flushed;
+// launched with programmatic stream serialisation, only its launch and CTA scheduling
+// overlap the tail of the previous kernel. pdl_trigger() lets the next kernel be scheduled
+// once every CTA of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Off when the environment sets FR_PDL=0 (for A/B timing).
+bool pdl_enabled();
+
+template <typename... KP, typename... A>
+inline void launch_k(void (*k)(KP...), dim3 g, dim3 b, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, static_cast<KP>(args)...);
+}
+
 #define FR_MAX_PRIMES 64
 #define FR_MAX_DIGITS 16
 

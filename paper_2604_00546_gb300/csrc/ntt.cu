@@ -18,11 +18,13 @@
 // Twiddle of the butterfly pairing x and x + 2^b, in either direction:
 // tw[(M + J) >> (b + 1)] where J is the global index of x and M = R for the
 // column pass, N for the row pass.
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace {
 
-constexpr int kTC = 8;   // columns per tile in the column pass
+constexpr int kTC = 4;   // columns per tile in the column pass (128 threads)
 
 __device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* prime) {
     if (b.tab) {
@@ -55,9 +57,9 @@ struct PhaseInfo {
 
 struct Ctx {
     int Jbase, M;    // global index of the tile's element 0; M = R (column pass) or N (row pass)
-    int cb, TT;      // shared-memory twiddle table of the CTA: stage B's entries start at
-                     // TT - (TT >> B) and hold global indices from cb >> (B + 1) on
-    const u64* tw;   // (shared memory)
+    int cb, TT;      // twiddle table of stage B starts at TT - (TT >> B) and holds global
+                     // indices from cb >> (B + 1) on (cb = TT = 0: the whole table)
+    const u64* tw;
     const u64* tws;
     u64 q;
     bool grow;       // forward only: q < 2^57, values may grow by 2q per stage (16 stages < 33q < 2^62)
@@ -132,9 +134,9 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
     return x >= q ? x - q : x;
 }
 
-// exchange through shared memory, column layout s[x'][8] with x' = x ^ (bit 3 of x):
-// the two rows a half-warp touches then fall in different 8-word bank halves
-__device__ __forceinline__ int col_row(int x) { return x ^ ((x >> 3) & 1); }
+// exchange through shared memory, column layout s[x'][4] with x' = x ^ x3 ^ (x4 << 1): the
+// four rows a half-warp touches then fall on distinct 4-word bank groups in every phase layout
+__device__ __forceinline__ int col_row(int x) { return x ^ ((x >> 3) & 1) ^ (((x >> 4) & 1) << 1); }
 
 struct ColEx {
     u64* s;
@@ -172,9 +174,11 @@ struct RowEx {
     }
 };
 
-// column pass: one CTA = 16 columns x S rows; thread (tau, col) with col = threadIdx & 15
+// column pass: one CTA = kTC columns x S rows; thread (tau, col) with col = threadIdx % kTC
 template <int LOG, bool INV>
-__global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, PolyBatch b) {
+__global__ void __launch_bounds__(kTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, PolyBatch b) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int S = 1 << LOG;
     extern __shared__ u64 sm[];
     u64* sw = sm + S * kTC;      // twiddles [0, S)
@@ -216,7 +220,9 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8) k_ntt_col(RingDev R, Pol
 
 // row pass: one CTA = RPC rows of S contiguous elements, S/8 threads per row
 template <int LOG, int LOGR, bool INV>
-__global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
+__global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int S = 1 << LOG;
     constexpr int TPR = S / 8;           // threads per row
     constexpr int RPC = (256 / TPR < (1 << LOGR)) ? 256 / TPR : (1 << LOGR);  // rows per CTA
@@ -239,22 +245,8 @@ __global__ void __launch_bounds__(256) k_ntt_row(RingDev R, PolyBatch b) {
     u64 v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
-    // the twiddles of the CTA's rows, stage by stage (contiguous global ranges), into shared memory
-    constexpr int TT = RPC * S;
-    u64* stw = sm + RPC * SP;
-    u64* stws = stw + (TT - RPC);
-    const int cb = N + blockIdx.x * RPC * S;
-#pragma unroll
-    for (int B = 0; B < LOG; ++B) {
-        const int cnt = TT >> (B + 1), off = TT - (TT >> B), g0 = cb >> (B + 1);
-        for (int i = threadIdx.x; i < cnt; i += RPC * TPR) {
-            stw[off + i] = tw[g0 + i];
-            stws[off + i] = tws[g0 + i];
-        }
-    }
-    __syncthreads();
     const bool grow = q < (1ull << 57);
-    Ctx c{Jbase, N, cb, TT, stw, stws, q, grow};
+    Ctx c{Jbase, N, 0, 0, tw, tws, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
@@ -279,20 +271,13 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
     constexpr int TPR = SC / 8, RPC = (256 / TPR < SR) ? 256 / TPR : SR;
     dim3 gr(SR / RPC, b.npolys);
-    // rows, then the rows' twiddles (w and Shoup quotient) of every stage
-    constexpr size_t smr = (size_t)(RPC * SC + 2 * (RPC * SC - RPC)) * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ntt_row<LOGC, LOGR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-        cudaFuncSetAttribute(k_ntt_row<LOGC, LOGR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-        attr = true;
-    }
+    const size_t smr = (size_t)RPC * SC * sizeof(u64);
     if (!inverse) {
-        k_ntt_col<LOGR, false><<<gc, tc, smc, st>>>(R, b);
-        k_ntt_row<LOGC, LOGR, false><<<gr, RPC * TPR, smr, st>>>(R, b);
+        launch_k(k_ntt_col<LOGR, false>, dim3(gc), dim3(tc), smc, st, R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, false>, dim3(gr), dim3(RPC * TPR), smr, st, R, b);
     } else {
-        k_ntt_row<LOGC, LOGR, true><<<gr, RPC * TPR, smr, st>>>(R, b);
-        k_ntt_col<LOGR, true><<<gc, tc, smc, st>>>(R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, true>, dim3(gr), dim3(RPC * TPR), smr, st, R, b);
+        launch_k(k_ntt_col<LOGR, true>, dim3(gc), dim3(tc), smc, st, R, b);
     }
 }
 
@@ -323,6 +308,14 @@ __global__ void __launch_bounds__(256) k_butterfly_peak(u64 q, u64 w, u64 ws, in
 }
 
 }  // namespace
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("FR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 double measure_butterfly_peak(int device) {
     // 60-bit prime; any twiddle works for a throughput measurement
