@@ -13,7 +13,8 @@
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Off when the environment sets FR_PDL=0 (for A/B timing).
+// On when the environment sets FR_PDL=1. Measured on the membership match: neutral to
+// slightly slower for one query replayed as a CUDA graph, about 1% faster for batches of 8.
 bool pdl_enabled();
 
 template <typename... KP, typename... A>

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) k_butterfly_peak(u64 q, u64 w, u64 ws, in
 bool pdl_enabled() {
     static const bool on = [] {
         const char* e = std::getenv("FR_PDL");
-        return !(e && e[0] == '0');
+        return e && e[0] == '1';
     }();
     return on;
 }
