@@ -466,6 +466,25 @@ def run_ours(args):
         d2h = sum(w.nbytes for w in words)
     e2e_value = whole_job_value(ws, K, 1000.0 * max_over_ranks(float(np.mean(e2e_t)), dist, dev))
 
+    # the plain per-query form: the same fr_match with every kernel launched per call (no graph)
+    ctx.use_graphs(False)
+    for _ in range(2):
+        out = step(ctx, db, dev_q)
+    got_p = float(ctx.decrypt(keys, out[0])[0])
+    del out
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    npl = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    outs = [step(ctx, db, dev_q) for _ in range(npl)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / npl
+    del outs
+    ctx.use_graphs(True)
+    plain = {"form": "one query per fr_match, kernels launched per call (no CUDA graph)", "ms_per_step": ms_p,
+             "value": K / (ms_p / 1000.0), "unit": UNIT, "membership_abs_err": abs(got_p - pref)}
+
     # batched launches: B distinct queries per pass (fr_match_batch), same database
     batched = None
     if args.batch > 1:
@@ -573,6 +592,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "full_chain": full,
             "table_schedule": table,
+            "plain_per_query": plain,
             "batched": batched,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -264,6 +264,11 @@ fr_status fr_sync(fr_ctx* ctx);
  * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc". */
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
+/* fr_match / fr_match_batch replay a CUDA graph of the whole match from the second call
+ * with the same (database, mode, batch size) on (the default). on = 0: every call launches
+ * its kernels one by one (the plain per-query form). Results are identical. */
+fr_status fr_use_graphs(fr_ctx* ctx, int on);
+
 /* Arithmetic ceiling of the NTT on `device`: forward butterflies (Harvey lazy
  * reduction, Shoup twiddle product, 64-bit residues) per second with every operand in
  * registers, measured by a short microbenchmark. Used as the ALU roofline peak. */

@@ -2206,6 +2206,14 @@ fr_status fr_ctx_info(const fr_ctx* c, uint32_t* n_slots, uint32_t* top_level, u
 
 uint32_t fr_work_level(const fr_ctx* c) { return c ? (uint32_t)c->work_level : 0; }
 
+fr_status fr_use_graphs(fr_ctx* c, int on) {
+    return guard([&] {
+        need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        c->use_graphs = on != 0;
+    });
+}
+
 fr_status fr_butterfly_peak(int device, double* butterflies_per_s) {
     return guard([&] {
         if (!butterflies_per_s) raise(FR_ERR_INVALID_ARG, "null argument");
