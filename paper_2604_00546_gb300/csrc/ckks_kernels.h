@@ -72,6 +72,15 @@ struct IPJobs {
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
+// Forward NTT of the P -> Q conversions of a ModDown fused with its combine: poly p of b is
+// (job p / (2(level+1)), component, limb); the transformed values never reach memory, the
+// jobs' outputs do (as launch_moddown_combine would write them).
+void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
+                        const u64* pinv, const u64* pinv_s, cudaStream_t s);
+// Forward NTT of a rescale's lifted last limb fused with its combine: poly p of b is
+// (ct component p / l, limb p % l); writes out = (x - NTT(lifted)) q_l^-1.
+void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
+                        const RescaleTab* tab, int l, cudaStream_t s);
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s);
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,

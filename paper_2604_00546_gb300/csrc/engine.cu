@@ -314,7 +314,6 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
         launch_p2q(acc.p, 2ll * npos * N, npos, level, conv.p, c->d_p2q, N, nj, c->cur);
         c->launches++;
     }
-    ntt(c, conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level), false);
     MDJobs md;
     double addw = 0;
     for (int j = 0; j < nj; ++j) {
@@ -329,9 +328,11 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
         m.galois = reqs[j]->galois;
         addw += reqs[j]->mode == 1 ? (level + 1) : reqs[j]->mode == 2 ? 2.0 * (level + 1) : 0;
     }
-    Prof p(c, "moddown", 8.0 * N * (nj * 6.0 * (level + 1) + addw));
-    launch_moddown_combine(md, nj, npos, level, c->d_pinv, c->d_pinv_s, c->d_primes, c->R.logN, c->cur);
-    c->launches++;
+    // forward NTT of the conversions with the combine as its epilogue
+    Prof p(c, "ntt", 16.0 * nj * 2 * (level + 1) * N + 8.0 * N * (nj * 4.0 * (level + 1) + addw));
+    PolyBatch pb{conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level)};
+    launch_ntt_moddown(c->rd, pb, md, npos, level, c->d_pinv, c->d_pinv_s, c->cur);
+    c->launches += 2;
 }
 
 // Hybrid key switching of a list of requests. Requests that switch the same
@@ -431,10 +432,11 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
         launch_rescale_lift(last.p, lifted.p, c->d_rescale[l], l, N, 2 * B, c->cur);
         c->launches++;
     }
-    ntt(c, lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1), false);
-    Prof p(c, "rescale", 8.0 * N * 2 * B * 3.0 * l);
-    launch_rescale_combine(in, in_cap, lifted.p, out, out_cap, c->d_rescale[l], l, N, 2 * B, c->cur);
-    c->launches++;
+    // forward NTT of the lifted limb with the combine as its epilogue
+    Prof p(c, "ntt", 16.0 * 2 * B * l * N + 8.0 * N * 2 * B * 2.0 * l);
+    PolyBatch pb{lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1)};
+    launch_ntt_rescale(c->rd, pb, in, in_cap, out, out_cap, c->d_rescale[l], l, c->cur);
+    c->launches += 2;
 }
 
 // ---------------------------------------------------------------------------

@@ -19,8 +19,9 @@
 // tw[(M + J) >> (b + 1)] where J is the global index of x and M = R for the
 // column pass, N for the row pass.
 #include <cstdlib>
+#include <type_traits>
 
-#include "kernels.h"
+#include "ckks_kernels.h"
 
 namespace {
 
@@ -218,9 +219,50 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
     }
 }
 
+// Epilogues of the forward row pass (the last pass of a forward transform): instead of
+// storing the transformed value v (canonical) of poly p at index k in place, the fused
+// epilogue finishes the operation the transform belonged to.
+struct EpiStore {};
+
+// ModDown combine: poly p = (job, component t, limb i) of the P -> Q conversions; out =
+// (acc_Q - v) P^-1 (+ sigma_g(c0) for rotations, + the ct addend for relinearisation).
+struct EpiModDown {
+    MDJobs jobs;
+    int npos, level, logN;
+    const u64* pinv;
+    const u64* pinv_s;
+    __device__ __forceinline__ void put(int p, int k, u64 v, u64 q) const {
+        const int L1 = level + 1, N = 1 << logN;
+        const int j = p / (2 * L1), r = p % (2 * L1), t = r / L1, i = r % L1;
+        const MDJob& J = jobs.j[j];
+        const u64 a = J.acc[((long long)t * npos + i) * N + k];
+        u64 w = mul_shoup(sub_mod(a, v, q), pinv[i], pinv_s[i], q);
+        if (J.mode == 1) {
+            if (t == 0) w = add_mod(w, J.add[(long long)i * N + galois_src_index((u32)k, J.galois, logN)], q);
+        } else if (J.mode == 2) {
+            w = add_mod(w, J.add[((long long)t * J.add_cap + i) * N + k], q);
+        }
+        J.out[((long long)t * J.out_cap + i) * N + k] = w;
+    }
+};
+
+// Rescale combine: poly p = (ct component bt, limb i) of the lifted last limb;
+// out = (x - v) q_l^-1.
+struct EpiRescale {
+    const u64* x;
+    u64* out;
+    const RescaleTab* tab;
+    int x_cap, out_cap, l, N;
+    __device__ __forceinline__ void put(int p, int k, u64 v, u64 q) const {
+        const int bt = p / l, i = p % l;
+        const u64 a = x[((long long)bt * x_cap + i) * N + k];
+        out[((long long)bt * out_cap + i) * N + k] = mul_shoup(sub_mod(a, v, q), tab->qlinv[i], tab->qlinv_s[i], q);
+    }
+};
+
 // row pass: one CTA = RPC rows of S contiguous elements, S/8 threads per row
-template <int LOG, int LOGR, bool INV>
-__global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b) {
+template <int LOG, int LOGR, bool INV, class E>
+__global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b, E epi) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
@@ -249,7 +291,15 @@ __global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b) {
     Ctx c{Jbase, N, 0, 0, tw, tws, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
-    if (INV) {
+    if constexpr (!std::is_same<E, EpiStore>::value) {
+        static_assert(!INV, "epilogues follow forward transforms");
+        const u64 one_s = R.primes[pi].one_s;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const u64 fv = grow ? mul_shoup(v[e], 1, one_s, q) : reduce4(v[e], q);
+            epi.put(p, Jbase + phase_x<LL>(tau, e), fv, q);
+        }
+    } else if (INV) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) xr[phase_x<LL>(tau, e)] = v[e];
     } else if (grow) {
@@ -262,8 +312,8 @@ __global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b) {
     }
 }
 
-template <int LOGR, int LOGC>
-void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st) {
+template <int LOGR, int LOGC, class E = EpiStore>
+void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi = E()) {
     constexpr int SR = 1 << LOGR, SC = 1 << LOGC;
     const int N = R.N;
     dim3 gc((N >> LOGR) / kTC, b.npolys);
@@ -274,9 +324,9 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     const size_t smr = (size_t)RPC * SC * sizeof(u64);
     if (!inverse) {
         launch_k(k_ntt_col<LOGR, false>, dim3(gc), dim3(tc), smc, st, R, b);
-        launch_k(k_ntt_row<LOGC, LOGR, false>, dim3(gr), dim3(RPC * TPR), smr, st, R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, false, E>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, epi);
     } else {
-        launch_k(k_ntt_row<LOGC, LOGR, true>, dim3(gr), dim3(RPC * TPR), smr, st, R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, true, EpiStore>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, EpiStore{});
         launch_k(k_ntt_col<LOGR, true>, dim3(gc), dim3(tc), smc, st, R, b);
     }
 }
@@ -343,16 +393,33 @@ double measure_butterfly_peak(int device) {
     return (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
 }
 
-void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s) {
+template <class E>
+void launch_ntt_e(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s, const E& epi) {
     if (b.npolys <= 0) return;
     switch (R.logN) {
-        case 10: launch_ntt_t<5, 5>(R, b, inverse, s); break;
-        case 11: launch_ntt_t<5, 6>(R, b, inverse, s); break;
-        case 12: launch_ntt_t<6, 6>(R, b, inverse, s); break;
-        case 13: launch_ntt_t<6, 7>(R, b, inverse, s); break;
-        case 14: launch_ntt_t<7, 7>(R, b, inverse, s); break;
-        case 15: launch_ntt_t<7, 8>(R, b, inverse, s); break;
-        case 16: launch_ntt_t<8, 8>(R, b, inverse, s); break;
+        case 10: launch_ntt_t<5, 5, E>(R, b, inverse, s, epi); break;
+        case 11: launch_ntt_t<5, 6, E>(R, b, inverse, s, epi); break;
+        case 12: launch_ntt_t<6, 6, E>(R, b, inverse, s, epi); break;
+        case 13: launch_ntt_t<6, 7, E>(R, b, inverse, s, epi); break;
+        case 14: launch_ntt_t<7, 7, E>(R, b, inverse, s, epi); break;
+        case 15: launch_ntt_t<7, 8, E>(R, b, inverse, s, epi); break;
+        case 16: launch_ntt_t<8, 8, E>(R, b, inverse, s, epi); break;
         default: break;
     }
+}
+
+void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s) {
+    launch_ntt_e(R, b, inverse, s, EpiStore{});
+}
+
+void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
+                        const u64* pinv, const u64* pinv_s, cudaStream_t s) {
+    EpiModDown e{jobs, npos, level, R.logN, pinv, pinv_s};
+    launch_ntt_e(R, b, false, s, e);
+}
+
+void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
+                        const RescaleTab* tab, int l, cudaStream_t s) {
+    EpiRescale e{x, out, tab, x_cap, out_cap, l, R.N};
+    launch_ntt_e(R, b, false, s, e);
 }
