@@ -108,29 +108,22 @@ __device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, i
     for (int j = jobs.gstart[g]; j < jobs.gstart[g + 1]; ++j) ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N);
 }
 
-// key layout [digit][2][T][N]: Q limbs at positions 0.., P limbs from position kp
-__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int beta, int npos, int level, int kp, int T,
-                                                 const DevPrime* __restrict__ primes, const PrimeMap pos_prime,
-                                                 int logN) {
+// key layout [digit][2][T][N]: Q limbs at positions 0.., P limbs from position kp. One
+// instantiation per digit count, so the registers a launch needs follow its beta.
+template <int BETA>
+__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int npos, int level, int kp, int T,
+                                                 const DevPrime* __restrict__ primes, int pbase, int logN) {
     pdl_wait();
     pdl_trigger();
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pos = blockIdx.y;
     if (k >= N) return;
-    const int pi = pos_prime.idx[pos];
+    // positions 0..level are Q limbs 0..level; the P limbs follow (prime indices from pbase)
+    const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
     const u64 q = primes[pi].q, qinv = primes[pi].qinv;
     const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
-    switch (beta) {
-        case 1: ip_body<1>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 2: ip_body<2>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 3: ip_body<3>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 4: ip_body<4>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 5: ip_body<5>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 6: ip_body<6>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        case 7: ip_body<7>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;
-        default: ip_body<8>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N); break;  // beta <= 8
-    }
+    ip_body<BETA>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N);
 }
 
 // ---------------------------------------------------------------------------
@@ -617,7 +610,14 @@ void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T,
                const PrimeMap& pos_prime, int logN, cudaStream_t s) {
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, npos, jobs.ngroups);
-    launch_k(k_ip, dim3(g), dim3(kThreads), 0, s, jobs, beta, npos, level, kp, T, primes, pos_prime, logN);
+    const int pbase = npos > level + 1 ? pos_prime.idx[level + 1] : 0;
+    switch (beta) {
+#define FR_IP_CASE(B) \
+    case B: launch_k(k_ip<B>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN); break;
+        FR_IP_CASE(1) FR_IP_CASE(2) FR_IP_CASE(3) FR_IP_CASE(4) FR_IP_CASE(5) FR_IP_CASE(6) FR_IP_CASE(7)
+        default: launch_k(k_ip<8>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN); break;
+#undef FR_IP_CASE
+    }
 }
 
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
