@@ -262,12 +262,12 @@ struct EpiRescale {
 
 // row pass: one CTA = RPC rows of S contiguous elements, S/8 threads per row
 template <int LOG, int LOGR, bool INV, class E>
-__global__ void __launch_bounds__(256, 5) k_ntt_row(RingDev R, PolyBatch b, E epi) {
+__global__ void __launch_bounds__(128, 10) k_ntt_row(RingDev R, PolyBatch b, E epi) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
     constexpr int TPR = S / 8;           // threads per row
-    constexpr int RPC = (256 / TPR < (1 << LOGR)) ? 256 / TPR : (1 << LOGR);  // rows per CTA
+    constexpr int RPC = (128 / TPR < (1 << LOGR)) ? 128 / TPR : (1 << LOGR);  // rows per CTA (128 threads)
     constexpr int SP = S;                // row stride in shared memory (swizzled, no padding)
     extern __shared__ u64 sm[];
     const int N = R.N;
@@ -319,7 +319,7 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     dim3 gc((N >> LOGR) / kTC, b.npolys);
     const int tc = kTC * SR / 8;
     const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
-    constexpr int TPR = SC / 8, RPC = (256 / TPR < SR) ? 256 / TPR : SR;
+    constexpr int TPR = SC / 8, RPC = (128 / TPR < SR) ? 128 / TPR : SR;
     dim3 gr(SR / RPC, b.npolys);
     const size_t smr = (size_t)RPC * SC * sizeof(u64);
     if (!inverse) {
