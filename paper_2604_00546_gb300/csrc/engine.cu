@@ -315,7 +315,6 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
         c->launches++;
     }
     MDJobs md;
-    double addw = 0;
     for (int j = 0; j < nj; ++j) {
         MDJob& m = md.j[j];
         m.acc = acc.p + (size_t)j * 2 * npos * N;
@@ -326,10 +325,11 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
         m.out_cap = reqs[j]->out_cap;
         m.mode = reqs[j]->mode;
         m.galois = reqs[j]->galois;
-        addw += reqs[j]->mode == 1 ? (level + 1) : reqs[j]->mode == 2 ? 2.0 * (level + 1) : 0;
     }
     // forward NTT of the conversions with the combine as its epilogue
-    Prof p(c, "ntt", 16.0 * nj * 2 * (level + 1) * N + 8.0 * N * (nj * 4.0 * (level + 1) + addw));
+    // the region counts the transform's 16 B per coefficient (its butterflies); the fused
+    // epilogue's reads of acc and the addend are not added
+    Prof p(c, "ntt", 16.0 * nj * 2 * (level + 1) * N);
     PolyBatch pb{conv.p, (long long)(level + 1) * N, level + 1, nj * 2 * (level + 1), pm_level(level)};
     launch_ntt_moddown(c->rd, pb, md, npos, level, c->d_pinv, c->d_pinv_s, c->cur);
     c->launches += 2;
@@ -433,7 +433,7 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
         c->launches++;
     }
     // forward NTT of the lifted limb with the combine as its epilogue
-    Prof p(c, "ntt", 16.0 * 2 * B * l * N + 8.0 * N * 2 * B * 2.0 * l);
+    Prof p(c, "ntt", 16.0 * 2 * B * l * N);
     PolyBatch pb{lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1)};
     launch_ntt_rescale(c->rd, pb, in, in_cap, out, out_cap, c->d_rescale[l], l, c->cur);
     c->launches += 2;
