@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int 
 // B queries, eight at a time per thread to keep loads in flight.
 // ---------------------------------------------------------------------------
 template <int B>
-__global__ void __launch_bounds__(512) k_mac(const u64* __restrict__ babies, long long baby_q, int cap_b,
+__global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __restrict__ babies, long long baby_q, int cap_b,
                                              const u64* __restrict__ diags, u64* __restrict__ out, long long out_q,
                                              int cap_o, int nl, int n1, int n2, int ell, int TP, int JG,
                                              const DevPrime* __restrict__ primes, int N) {
@@ -289,39 +289,61 @@ __global__ void __launch_bounds__(512) k_mac(const u64* __restrict__ babies, lon
     }
     __syncthreads();
     const long long dstride = (long long)nl * N;
-    for (int j = jg; j < n2; j += JG) {
+    // the thread's work is a sequence of batches (giant step j, 8 diagonals from i0); the
+    // diagonal words of the next batch are loaded while the current batch is multiplied
+    int j = jg, i0 = 0;
+    if (j >= n2) return;
+    auto load = [&](int jj, int ii, u64 (&d)[8]) {
+        const int cnt = min(n1, ell - jj * n1);
+        const u64* D = diags + ((long long)jj * n1 + ii) * dstride + (long long)i * N + k;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d[u] = (ii + u < cnt) ? __ldcs(D + (long long)u * dstride) : 0ull;
+    };
+    u64 d[8];
+    load(j, i0, d);
+    Acc128 acc[B][2];
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
+    for (;;) {
         const int cnt = min(n1, ell - j * n1);
-        Acc128 acc[B][2];
+        // next batch
+        int jn = j, in = i0 + 8;
+        if (in >= cnt) {
+            jn = j + JG;
+            in = 0;
+        }
+        u64 dn[8];
+        if (jn < n2) load(jn, in, dn);
 #pragma unroll
-        for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
-        const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
-        for (int i0 = 0; i0 < cnt; i0 += 8) {
-            u64 d[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) d[u] = (i0 + u < cnt) ? __ldcs(D + (long long)(i0 + u) * dstride) : 0ull;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int ib = i0 + u;
-                if (ib >= cnt) break;
-#pragma unroll
-                for (int b = 0; b < B; ++b) {
-                    const u64* sq = sb + b * per_q + ib * 2 * TP + pl;
-                    mac128(acc[b][0], sq[0], d[u]);
-                    mac128(acc[b][1], sq[TP], d[u]);
-                }
-            }
+        for (int u = 0; u < 8; ++u) {
+            const int ib = i0 + u;
+            if (ib >= cnt) break;
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                fold(acc[b][0], q);
-                fold(acc[b][1], q);
+                const u64* sq = sb + b * per_q + ib * 2 * TP + pl;
+                mac128(acc[b][0], sq[0], d[u]);
+                mac128(acc[b][1], sq[TP], d[u]);
             }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            u64* O = out + (long long)b * out_q + (long long)j * 2 * cap_o * N;
-            O[(long long)i * N + k] = redc(acc[b][0].hi, acc[b][0].lo, q, qinv);
-            O[((long long)cap_o + i) * N + k] = redc(acc[b][1].hi, acc[b][1].lo, q, qinv);
+            fold(acc[b][0], q);
+            fold(acc[b][1], q);
         }
+        if (jn != j) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                u64* O = out + (long long)b * out_q + (long long)j * 2 * cap_o * N;
+                O[(long long)i * N + k] = redc(acc[b][0].hi, acc[b][0].lo, q, qinv);
+                O[((long long)cap_o + i) * N + k] = redc(acc[b][1].hi, acc[b][1].lo, q, qinv);
+                acc[b][0] = acc[b][1] = Acc128{0, 0};
+            }
+        }
+        if (jn >= n2) break;
+        j = jn;
+        i0 = in;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d[u] = dn[u];
     }
 }
 
