@@ -284,13 +284,12 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
     for (int e = threadIdx.x; e < B * per_q; e += TP * JG) {
         const int b = e / per_q, r = e % per_q;
         const int ib = r / (2 * TP), t = (r / TP) & 1, pp = r % TP;
-        sb[e] = babies[(long long)b * baby_q + ((long long)ib * 2 + t) * cap_b * N + (long long)i * N +
-                       (long long)blockIdx.x * TP + pp];
+        sb[e] = split30(babies[(long long)b * baby_q + ((long long)ib * 2 + t) * cap_b * N + (long long)i * N +
+                               (long long)blockIdx.x * TP + pp]);
     }
     __syncthreads();
     const long long dstride = (long long)nl * N;
-    // the thread's work is a sequence of batches (giant step j, 8 diagonals from i0); the
-    // diagonal words of the next batch are loaded while the current batch is multiplied
+    // the thread's work is a sequence of batches (giant step j, 8 diagonals from i0)
     int j = jg, i0 = 0;
     if (j >= n2) return;
     auto load = [&](int jj, int ii, u64 (&d)[8]) {
@@ -299,34 +298,39 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 #pragma unroll
         for (int u = 0; u < 8; ++u) d[u] = (ii + u < cnt) ? __ldcs(D + (long long)u * dstride) : 0ull;
     };
-    u64 d[8];
-    load(j, i0, d);
     Acc128 acc[B][2];
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
     for (;;) {
         const int cnt = min(n1, ell - j * n1);
+        u64 d[8];
+        load(j, i0, d);
         // next batch
         int jn = j, in = i0 + 8;
         if (in >= cnt) {
             jn = j + JG;
             in = 0;
         }
-        u64 dn[8];
-        if (jn < n2) load(jn, in, dn);
+        // 8 products per component in 30-bit partial sums, then one carry into acc
+        Acc3 p[B][2];
+#pragma unroll
+        for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = Acc3{0, 0, 0};
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int ib = i0 + u;
             if (ib >= cnt) break;
+            const u64 ds = split30(d[u]);
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const u64* sq = sb + b * per_q + ib * 2 * TP + pl;
-                mac128(acc[b][0], sq[0], d[u]);
-                mac128(acc[b][1], sq[TP], d[u]);
+                mac30(p[b][0], sq[0], ds);
+                mac30(p[b][1], sq[TP], ds);
             }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
+            flush30(acc[b][0], p[b][0]);
+            flush30(acc[b][1], p[b][1]);
             fold(acc[b][0], q);
             fold(acc[b][1], q);
         }
@@ -342,8 +346,6 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
         if (jn >= n2) break;
         j = jn;
         i0 = in;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) d[u] = dn[u];
     }
 }
 

@@ -51,6 +51,35 @@ __device__ __forceinline__ void mac128(Acc128& a, u64 x, u64 y) {
     a.hi += h + (a.lo < l ? 1ull : 0ull);
 }
 
+// Products of residues below 2^60 from 30-bit halves: x = xh 2^30 + xl, y = yh 2^30 + yl,
+// x y = xl yl + (xl yh + xh yl) 2^30 + xh yh 2^60. Each partial product is below 2^60, so up
+// to 8 products sum in three 64-bit words (a1 takes two per product) with no carries; each
+// term is one 32 x 32 -> 64-bit multiply-add.
+struct Acc3 {
+    u64 a0, a1, a2;
+};
+__device__ __forceinline__ u64 split30(u64 x) { return (x & 0x3fffffffull) | ((x >> 30) << 32); }
+__device__ __forceinline__ void mac30(Acc3& a, u64 xs, u64 ys) {
+    const u32 xl = (u32)xs, xh = (u32)(xs >> 32), yl = (u32)ys, yh = (u32)(ys >> 32);
+    a.a0 += (u64)xl * yl;
+    a.a1 += (u64)xl * yh;
+    a.a1 += (u64)xh * yl;
+    a.a2 += (u64)xh * yh;
+}
+// acc += a0 + a1 2^30 + a2 2^60, then a = 0
+__device__ __forceinline__ void flush30(Acc128& acc, Acc3& a) {
+    u64 lo = a.a0, hi = 0;
+    u64 t = a.a1 << 30;
+    lo += t;
+    hi += (a.a1 >> 34) + (lo < t ? 1ull : 0ull);
+    t = a.a2 << 60;
+    lo += t;
+    hi += (a.a2 >> 4) + (lo < t ? 1ull : 0ull);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+    a.a0 = a.a1 = a.a2 = 0;
+}
+
 // a * b mod q for two variable residues: REDC(REDC(a b) * R^2)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const DevPrime& P) {
     u64 t = redc(__umul64hi(a, b), a * b, P.q, P.qinv);
