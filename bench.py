@@ -652,6 +652,7 @@ def run_ours(args):
                                     else 0.0) for r in regions},
             "stages_ms_per_step": stages,
             "gpu_launches": int(n_launch),
+            "ntt_autotune": ctx.ntt_tuning(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "full_chain": full,
             "table_schedule": table,

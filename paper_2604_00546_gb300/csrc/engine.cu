@@ -15,6 +15,7 @@
 #include <condition_variable>
 #include <deque>
 #include <set>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -119,6 +120,7 @@ struct fr_ctx {
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query
+    double ntt_tune_us[FR_NTT_BUCKETS * 4] = {};  // tuner times: bucket x tile shape (forward + inverse)
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
     Server* server = nullptr;            // continuous-batching loop (fr_match_submit / fr_match_poll)
 };
@@ -928,6 +930,10 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         build_tables(c.get());
         CU(cudaStreamSynchronize(c->cur));
+        // NTT tile shapes per batch-size bucket, timed on this GPU (FR_NTT_TUNE=0: defaults)
+        const char* tune = std::getenv("FR_NTT_TUNE");
+        if (!(tune && tune[0] == '0')) tune_ntt(c->rd, c->cur, c->ntt_tune_us, 3);
+        CU(cudaGetLastError());
         *out = c.release();
     });
 }
@@ -2207,6 +2213,28 @@ fr_status fr_ctx_info(const fr_ctx* c, uint32_t* n_slots, uint32_t* top_level, u
 }
 
 uint32_t fr_work_level(const fr_ctx* c) { return c ? (uint32_t)c->work_level : 0; }
+
+fr_status fr_ntt_tuning(const fr_ctx* c, uint32_t* shapes, double* us) {
+    return guard([&] {
+        need_device(c);
+        for (int b = 0; b < FR_NTT_BUCKETS; ++b) {
+            if (shapes) shapes[b] = c->rd.ntt_shape[b];
+            for (int sh = 0; sh < 4 && us; ++sh) us[b * 4 + sh] = c->ntt_tune_us[b * 4 + sh];
+        }
+    });
+}
+
+fr_status fr_ntt_set_shapes(fr_ctx* c, const uint32_t* shapes) {
+    return guard([&] {
+        need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        if (!shapes) raise(FR_ERR_INVALID_ARG, "null argument");
+        for (int b = 0; b < FR_NTT_BUCKETS; ++b)
+            if (shapes[b] > 3) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..3");
+        for (int b = 0; b < FR_NTT_BUCKETS; ++b) c->rd.ntt_shape[b] = (unsigned char)shapes[b];
+        drop_graphs(c, nullptr);  // captured graphs hold the previous launch shapes
+    });
+}
 
 fr_status fr_use_graphs(fr_ctx* c, int on) {
     return guard([&] {

@@ -55,6 +55,12 @@ struct PolyBatch {
     int tab_n = 0;
 };
 
+// NTT batch-size buckets for the tuned tile shapes: <= 4, <= 16, <= 64, larger.
+#define FR_NTT_BUCKETS 4
+__host__ __device__ inline int ntt_bucket(int npolys) {
+    return npolys <= 4 ? 0 : npolys <= 16 ? 1 : npolys <= 64 ? 2 : 3;
+}
+
 // Ring tables resident on the device for one parameter set.
 struct RingDev {
     int logN;
@@ -65,10 +71,13 @@ struct RingDev {
     const u64* tws;          // Shoup quotients
     const u64* itw;          // [nprimes][N] psi^-brev(k)
     const u64* itws;
+    unsigned char ntt_shape[FR_NTT_BUCKETS];  // tile shape per batch-size bucket (see launch_ntt)
 };
 
 // Batched negacyclic NTT (evaluation order: position k = value at psi^(2 brev(k)+1)).
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s);
+// Autotuner of the NTT tile shapes (see ntt.cu); us: 4 x 4 times in microseconds, or null.
+void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps);
 // Butterflies per second of the NTT's forward butterfly with operands in registers.
 double measure_butterfly_peak(int device);
 

@@ -25,7 +25,6 @@
 
 namespace {
 
-constexpr int kTC = 4;   // columns per tile in the column pass (128 threads)
 
 __device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* prime) {
     if (b.tab) {
@@ -135,20 +134,25 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q) {
     return x >= q ? x - q : x;
 }
 
-// exchange through shared memory, column layout s[x'][4] with x' = x ^ x3 ^ (x4 << 1): the
-// four rows a half-warp touches then fall on distinct 4-word bank groups in every phase layout
-__device__ __forceinline__ int col_row(int x) { return x ^ ((x >> 3) & 1) ^ (((x >> 4) & 1) << 1); }
+// exchange through shared memory, column layout s[x'][KTC]. With 4 columns x' = x ^ x3 ^
+// (x4 << 1), with 8 columns x' = x ^ x3: the rows a half-warp touches then fall on distinct
+// bank groups in every phase layout.
+template <int KTC>
+__device__ __forceinline__ int col_row(int x) {
+    return KTC == 4 ? x ^ ((x >> 3) & 1) ^ (((x >> 4) & 1) << 1) : x ^ ((x >> 3) & 1);
+}
 
+template <int KTC>
 struct ColEx {
     u64* s;
     int col;
     template <int LA, int LB>
     __device__ __forceinline__ void exchange(u64 (&v)[8], int tau) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) s[col_row(phase_x<LA>(tau, e)) * kTC + col] = v[e];
+        for (int e = 0; e < 8; ++e) s[col_row<KTC>(phase_x<LA>(tau, e)) * KTC + col] = v[e];
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = s[col_row(phase_x<LB>(tau, e)) * kTC + col];
+        for (int e = 0; e < 8; ++e) v[e] = s[col_row<KTC>(phase_x<LB>(tau, e)) * KTC + col];
         __syncthreads();
     }
 };
@@ -175,14 +179,14 @@ struct RowEx {
     }
 };
 
-// column pass: one CTA = kTC columns x S rows; thread (tau, col) with col = threadIdx % kTC
-template <int LOG, bool INV>
-__global__ void __launch_bounds__(kTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, PolyBatch b) {
+// column pass: one CTA = KTC columns x S rows; thread (tau, col) with col = threadIdx % KTC
+template <int LOG, bool INV, int KTC>
+__global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, PolyBatch b) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
     extern __shared__ u64 sm[];
-    u64* sw = sm + S * kTC;      // twiddles [0, S)
+    u64* sw = sm + S * KTC;      // twiddles [0, S)
     u64* sws = sw + S;
     const int N = R.N;
     const int C = N >> LOG;
@@ -196,9 +200,9 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
         sw[i] = tw[i];
         sws[i] = tws[i];
     }
-    const int col = threadIdx.x & (kTC - 1);
-    const int tau = threadIdx.x / kTC;
-    const int gcol = blockIdx.x * kTC + col;
+    const int col = threadIdx.x & (KTC - 1);
+    const int tau = threadIdx.x / KTC;
+    const int gcol = blockIdx.x * KTC + col;
     constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
     constexpr int LL = LastLo<LOG, INV>::v;
     u64 v[8];
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(kTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
     for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
     __syncthreads();
     Ctx c{0, S, 0, 0, sw, sws, q, q < (1ull << 57)};
-    ColEx ex{sm, col};
+    ColEx<KTC> ex{sm, col};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
         const DevPrime P = R.primes[pi];
@@ -260,14 +264,14 @@ struct EpiRescale {
     }
 };
 
-// row pass: one CTA = RPC rows of S contiguous elements, S/8 threads per row
-template <int LOG, int LOGR, bool INV, class E>
-__global__ void __launch_bounds__(128, 10) k_ntt_row(RingDev R, PolyBatch b, E epi) {
+// row pass: one CTA = RPC rows of S contiguous elements (RT threads), S/8 threads per row
+template <int LOG, int LOGR, bool INV, class E, int RT>
+__global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, PolyBatch b, E epi) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
     constexpr int TPR = S / 8;           // threads per row
-    constexpr int RPC = (128 / TPR < (1 << LOGR)) ? 128 / TPR : (1 << LOGR);  // rows per CTA (128 threads)
+    constexpr int RPC = (RT / TPR < (1 << LOGR)) ? RT / TPR : (1 << LOGR);  // rows per CTA
     constexpr int SP = S;                // row stride in shared memory (swizzled, no padding)
     extern __shared__ u64 sm[];
     const int N = R.N;
@@ -312,22 +316,36 @@ __global__ void __launch_bounds__(128, 10) k_ntt_row(RingDev R, PolyBatch b, E e
     }
 }
 
-template <int LOGR, int LOGC, class E = EpiStore>
-void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi = E()) {
+template <int LOGR, int LOGC, class E, int KTC, int RT>
+void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
     constexpr int SR = 1 << LOGR, SC = 1 << LOGC;
     const int N = R.N;
-    dim3 gc((N >> LOGR) / kTC, b.npolys);
-    const int tc = kTC * SR / 8;
-    const size_t smc = (size_t)(SR * kTC + 2 * SR) * sizeof(u64);
-    constexpr int TPR = SC / 8, RPC = (128 / TPR < SR) ? 128 / TPR : SR;
+    dim3 gc((N >> LOGR) / KTC, b.npolys);
+    const int tc = KTC * SR / 8;
+    const size_t smc = (size_t)(SR * KTC + 2 * SR) * sizeof(u64);
+    constexpr int TPR = SC / 8, RPC = (RT / TPR < SR) ? RT / TPR : SR;
     dim3 gr(SR / RPC, b.npolys);
     const size_t smr = (size_t)RPC * SC * sizeof(u64);
     if (!inverse) {
-        launch_k(k_ntt_col<LOGR, false>, dim3(gc), dim3(tc), smc, st, R, b);
-        launch_k(k_ntt_row<LOGC, LOGR, false, E>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, epi);
+        launch_k(k_ntt_col<LOGR, false, KTC>, dim3(gc), dim3(tc), smc, st, R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, false, E, RT>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, epi);
     } else {
-        launch_k(k_ntt_row<LOGC, LOGR, true, EpiStore>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, EpiStore{});
-        launch_k(k_ntt_col<LOGR, true>, dim3(gc), dim3(tc), smc, st, R, b);
+        launch_k(k_ntt_row<LOGC, LOGR, true, EpiStore, RT>, dim3(gr), dim3(RPC * TPR), smr, st, R, b, EpiStore{});
+        launch_k(k_ntt_col<LOGR, true, KTC>, dim3(gc), dim3(tc), smc, st, R, b);
+    }
+}
+
+// Tile shape of a launch: bit 0 set = 8 columns per column-pass CTA (else 4), bit 1 set =
+// 256-thread row-pass CTAs (else 128). Chosen per batch-size bucket by the tuner (RingDev
+// holds the table); sizes other than N = 2^15, 2^16 use shape 0.
+template <int LOGR, int LOGC, class E>
+void launch_ntt_s(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
+    const int shape = (LOGR + LOGC >= 15) ? R.ntt_shape[ntt_bucket(b.npolys)] : 0;
+    switch (shape) {
+        case 1: launch_ntt_t<LOGR, LOGC, E, 8, 128>(R, b, inverse, st, epi); break;
+        case 2: launch_ntt_t<LOGR, LOGC, E, 4, 256>(R, b, inverse, st, epi); break;
+        case 3: launch_ntt_t<LOGR, LOGC, E, 8, 256>(R, b, inverse, st, epi); break;
+        default: launch_ntt_t<LOGR, LOGC, E, 4, 128>(R, b, inverse, st, epi); break;
     }
 }
 
@@ -397,19 +415,67 @@ template <class E>
 void launch_ntt_e(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s, const E& epi) {
     if (b.npolys <= 0) return;
     switch (R.logN) {
-        case 10: launch_ntt_t<5, 5, E>(R, b, inverse, s, epi); break;
-        case 11: launch_ntt_t<5, 6, E>(R, b, inverse, s, epi); break;
-        case 12: launch_ntt_t<6, 6, E>(R, b, inverse, s, epi); break;
-        case 13: launch_ntt_t<6, 7, E>(R, b, inverse, s, epi); break;
-        case 14: launch_ntt_t<7, 7, E>(R, b, inverse, s, epi); break;
-        case 15: launch_ntt_t<7, 8, E>(R, b, inverse, s, epi); break;
-        case 16: launch_ntt_t<8, 8, E>(R, b, inverse, s, epi); break;
+        case 10: launch_ntt_t<5, 5, E, 4, 128>(R, b, inverse, s, epi); break;
+        case 11: launch_ntt_t<5, 6, E, 4, 128>(R, b, inverse, s, epi); break;
+        case 12: launch_ntt_t<6, 6, E, 4, 128>(R, b, inverse, s, epi); break;
+        case 13: launch_ntt_t<6, 7, E, 4, 128>(R, b, inverse, s, epi); break;
+        case 14: launch_ntt_t<7, 7, E, 4, 128>(R, b, inverse, s, epi); break;
+        case 15: launch_ntt_s<7, 8, E>(R, b, inverse, s, epi); break;
+        case 16: launch_ntt_s<8, 8, E>(R, b, inverse, s, epi); break;
         default: break;
     }
 }
 
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s) {
     launch_ntt_e(R, b, inverse, s, EpiStore{});
+}
+
+// Times every tile shape of the forward + inverse transform for one batch size per bucket
+// (CUDA events, best of `reps`) on a scratch buffer of zero residues and keeps the fastest
+// shape per bucket in R.ntt_shape; us[bucket * 4 + shape] receives the times.
+void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
+    for (int bk = 0; bk < FR_NTT_BUCKETS; ++bk) R.ntt_shape[bk] = 0;
+    if (R.logN < 15) return;
+    const int sizes[FR_NTT_BUCKETS] = {4, 16, 64, 256};
+    const int maxp = sizes[FR_NTT_BUCKETS - 1];
+    u64* buf = nullptr;
+    if (cudaMallocAsync(&buf, (size_t)maxp * R.N * 8, s) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaMemsetAsync(buf, 0, (size_t)maxp * R.N * 8, s);
+    cudaEvent_t a, e;
+    cudaEventCreate(&a);
+    cudaEventCreate(&e);
+    unsigned char best[FR_NTT_BUCKETS];
+    for (int bk = 0; bk < FR_NTT_BUCKETS; ++bk) {
+        PolyBatch pb{buf, 0, sizes[bk], sizes[bk], PrimeMap{}};
+        pb.pm.period = 1;
+        pb.pm.idx[0] = 0;
+        double tbest = 1e30;
+        best[bk] = 0;
+        for (int sh = 0; sh < 4; ++sh) {
+            R.ntt_shape[bk] = (unsigned char)sh;
+            double t = 1e30;
+            for (int r = 0; r <= reps; ++r) {  // first run warms up
+                cudaEventRecord(a, s);
+                launch_ntt(R, pb, false, s);
+                launch_ntt(R, pb, true, s);
+                cudaEventRecord(e, s);
+                cudaEventSynchronize(e);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, e);
+                if (r > 0) t = t < ms * 1000.0 ? t : ms * 1000.0;
+            }
+            if (us) us[bk * 4 + sh] = t;
+            if (t < tbest) {
+                tbest = t;
+                best[bk] = (unsigned char)sh;
+            }
+        }
+    }
+    for (int bk = 0; bk < FR_NTT_BUCKETS; ++bk) R.ntt_shape[bk] = best[bk];
+    cudaEventDestroy(a);
+    cudaEventDestroy(e);
+    cudaFreeAsync(buf, s);
+    cudaStreamSynchronize(s);
 }
 
 void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
