@@ -21,6 +21,19 @@ __device__ __forceinline__ void fold(Acc128& a, u64 q) {
 // in: coefficient form, job j at in + j * in_job; in_eval: evaluation form (same layout)
 // ext: [J][beta][npos][N]
 // ---------------------------------------------------------------------------
+// sum_i ys_i [B/b_i]_t mod t from split residues: 30-bit multiply-accumulate, the high word
+// reduced mod t, then one Montgomery reduction (hat_m carries the 2^64 factor)
+template <int NS>
+__device__ __forceinline__ u64 bconv_sum(const u64 (&ys)[NS], const u64 (&hat_m)[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES],
+                                         int pos, u64 t, u64 tinv, u64 t_one_s) {
+    Acc3 a{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < NS; ++i) mac30(a, ys[i], hat_m[i][pos]);
+    Acc128 acc{0, 0};
+    flush30(acc, a);
+    return redc(mul_shoup(acc.hi, 1, t_one_s, t), acc.lo, t, tinv);
+}
+
 template <int NS>
 __device__ __forceinline__ void modup_body(const ModUpTab& T, const u64* __restrict__ x,
                                            const u64* __restrict__ xe, u64* __restrict__ out, int npos, int N,
@@ -28,17 +41,11 @@ __device__ __forceinline__ void modup_body(const ModUpTab& T, const u64* __restr
     u64 ys[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i)
-        ys[i] = mul_shoup(x[(long long)(T.lo + i) * N + k], T.inv_hat[i], T.inv_hat_s[i], T.src_q[i]);
+        ys[i] = split30(mul_shoup(x[(long long)(T.lo + i) * N + k], T.inv_hat[i], T.inv_hat_s[i], T.src_q[i]));
     for (int pos = 0; pos < npos; ++pos) {
         u64 v;
-        if (pos >= T.lo && pos < T.lo + NS) {
-            v = xe[(long long)pos * N + k];
-        } else {
-            const u64 t = T.tq[pos];
-            v = 0;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) v = add_mod(v, mul_shoup(ys[i], T.hat[i][pos], T.hat_s[i][pos], t), t);
-        }
+        if (pos >= T.lo && pos < T.lo + NS) v = xe[(long long)pos * N + k];
+        else v = bconv_sum<NS>(ys, T.hat_m, pos, T.tq[pos], T.tinv[pos], T.t_one_s[pos]);
         out[(long long)pos * N + k] = v;
     }
 }
@@ -137,14 +144,9 @@ __device__ __forceinline__ void p2q_body(const u64* __restrict__ x, u64* __restr
     u64 ys[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i)
-        ys[i] = mul_shoup(x[(long long)(level + 1 + i) * N + k], tab->inv_hat[i], tab->inv_hat_s[i], tab->pq[i]);
-    for (int i = 0; i <= level; ++i) {
-        const u64 q = tab->qq[i];
-        u64 v = 0;
-#pragma unroll
-        for (int jj = 0; jj < NP; ++jj) v = add_mod(v, mul_shoup(ys[jj], tab->hat[jj][i], tab->hat_s[jj][i], q), q);
-        o[(long long)i * N + k] = v;
-    }
+        ys[i] = split30(mul_shoup(x[(long long)(level + 1 + i) * N + k], tab->inv_hat[i], tab->inv_hat_s[i], tab->pq[i]));
+    for (int i = 0; i <= level; ++i)
+        o[(long long)i * N + k] = bconv_sum<NP>(ys, tab->hat_m, i, tab->qq[i], tab->qinv[i], tab->q_one_s[i]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_p2q(const u64* __restrict__ acc, long long acc_job, int npos,

@@ -6,13 +6,16 @@
 
 // ModUp constants of one digit at one level: sources are the digit's Q limbs
 // [lo, lo + ns); targets are every position of Q_l u P.
+// FastBConv constants. hat_m holds [B/b_i]_t in Montgomery form (times 2^64 mod t), split into
+// 30-bit halves (low half in bits 0..29, high half in bits 32..61) for the multiply-accumulate;
+// tinv = t^-1 mod 2^64 and t_one_s = floor(2^64 / t) reduce the sum.
 struct ModUpTab {
     int ns, lo;
     u64 src_q[FR_MAX_DIGIT_LIMBS];
     u64 inv_hat[FR_MAX_DIGIT_LIMBS], inv_hat_s[FR_MAX_DIGIT_LIMBS];
     u64 tq[FR_MAX_PRIMES];
-    u64 hat[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
-    u64 hat_s[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+    u64 tinv[FR_MAX_PRIMES], t_one_s[FR_MAX_PRIMES];
+    u64 hat_m[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
 };
 
 // ModDown constants: sources are the P limbs, targets Q limbs 0..l
@@ -21,8 +24,8 @@ struct P2QTab {
     u64 pq[FR_MAX_DIGIT_LIMBS];
     u64 inv_hat[FR_MAX_DIGIT_LIMBS], inv_hat_s[FR_MAX_DIGIT_LIMBS];
     u64 qq[FR_MAX_PRIMES];
-    u64 hat[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
-    u64 hat_s[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
+    u64 qinv[FR_MAX_PRIMES], q_one_s[FR_MAX_PRIMES];
+    u64 hat_m[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES];
 };
 
 // Rescale constants at level l (divide by q_l)

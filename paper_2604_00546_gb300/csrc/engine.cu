@@ -703,6 +703,15 @@ void check_ct(const fr_ctx* c, const fr_ct* ct) {
     if (ct->level < 0 || ct->level >= c->R.nq) raise(FR_ERR_LEVEL, "ciphertext level out of range");
 }
 
+// q^-1 mod 2^64 for odd q (Newton iteration)
+u64 inv_mod_2_64(u64 q) {
+    u64 inv = 1;
+    for (int i = 0; i < 7; ++i) inv *= 2 - q * inv;
+    return inv;
+}
+// 30-bit halves of a residue below 2^60: low half in bits 0..29, high half in bits 32..61
+u64 split30_host(u64 x) { return (x & 0x3fffffffull) | ((x >> 30) << 32); }
+
 void build_tables(fr_ctx* c) {
     const frh::Ring& R = c->R;
     const int N = R.N, T = R.total();
@@ -757,14 +766,16 @@ void build_tables(fr_ctx* c) {
             for (int i = 0; i < t.ns; ++i) t.src_q[i] = R.primes[lo + i];
             for (int pos = 0; pos < npos; ++pos) {
                 const int pi = pos <= l ? pos : R.nq + pos - l - 1;
-                t.tq[pos] = R.primes[pi];
+                const u64 tp = R.primes[pi];
+                t.tq[pos] = tp;
+                t.tinv[pos] = inv_mod_2_64(tp);
+                t.t_one_s[pos] = (u64)(((unsigned __int128)1 << 64) / tp);
                 std::vector<u64> ih, ht;
                 frh::bconv_consts(R, src, pi, ih, ht);
                 for (int i = 0; i < t.ns; ++i) {
                     t.inv_hat[i] = ih[i];
                     t.inv_hat_s[i] = frh::shoup_quot(ih[i], R.primes[lo + i]);
-                    t.hat[i][pos] = ht[i];
-                    t.hat_s[i][pos] = frh::shoup_quot(ht[i], R.primes[pi]);
+                    t.hat_m[i][pos] = split30_host((u64)(((unsigned __int128)ht[i] << 64) % tp));
                 }
             }
         }
@@ -793,11 +804,12 @@ void build_tables(fr_ctx* c) {
             t.qq[i] = R.primes[i];
             std::vector<u64> ih, ht;
             frh::bconv_consts(R, src, i, ih, ht);
+            t.qinv[i] = inv_mod_2_64(R.primes[i]);
+            t.q_one_s[i] = (u64)(((unsigned __int128)1 << 64) / R.primes[i]);
             for (int j = 0; j < R.np; ++j) {
                 t.inv_hat[j] = ih[j];
                 t.inv_hat_s[j] = frh::shoup_quot(ih[j], t.pq[j]);
-                t.hat[j][i] = ht[j];
-                t.hat_s[j][i] = frh::shoup_quot(ht[j], R.primes[i]);
+                t.hat_m[j][i] = split30_host((u64)(((unsigned __int128)ht[j] << 64) % R.primes[i]));
             }
             u64 P = 1;
             for (int j = 0; j < R.np; ++j) P = frh::mulm(P, t.pq[j] % R.primes[i], R.primes[i]);
