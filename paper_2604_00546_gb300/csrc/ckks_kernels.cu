@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 // for GG groups per CTA column. One thread per evaluation point of one limb; the two
 // table words of a point are read once for the GG groups, the diagonal words streamed.
 // table: [ell][2][cap_t][N]; diagonal m of group g, limb i at diags + g dgrp + (m nl + i) N
-// (Montgomery form); output of group g at out + g og, [2][cap_o][N].
+// (Montgomery form); output of group g at out + g og, [2][cap_o][N]. Products use the 30-bit
+// split multiply-accumulate (four per carry step).
 // ---------------------------------------------------------------------------
 template <int GG>
 __global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table, int cap_t,
@@ -382,21 +383,21 @@ __global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool ok = m0 + u < ell;
-            a[u] = ok ? t0[(long long)(m0 + u) * ts] : 0ull;
-            b[u] = ok ? t1[(long long)(m0 + u) * ts] : 0ull;
+            a[u] = split30(ok ? t0[(long long)(m0 + u) * ts] : 0ull);
+            b[u] = split30(ok ? t1[(long long)(m0 + u) * ts] : 0ull);
         }
 #pragma unroll
         for (int gg = 0; gg < GG; ++gg) {
             if (g0 + gg < G) {
-                u64 d[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    d[u] = m0 + u < ell ? __ldcs(d0 + gg * dgrp + (long long)(m0 + u) * ds) : 0ull;
+                Acc3 p0{0, 0, 0}, p1{0, 0, 0};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    mac128(acc[gg][0], a[u], d[u]);
-                    mac128(acc[gg][1], b[u], d[u]);
+                    const u64 d = split30(m0 + u < ell ? __ldcs(d0 + gg * dgrp + (long long)(m0 + u) * ds) : 0ull);
+                    mac30(p0, a[u], d);
+                    mac30(p1, b[u], d);
                 }
+                flush30(acc[gg][0], p0);
+                flush30(acc[gg][1], p1);
                 fold(acc[gg][0], q);
                 fold(acc[gg][1], q);
             }
