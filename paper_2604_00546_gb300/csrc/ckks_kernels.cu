@@ -294,39 +294,45 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
     // the thread's work is a sequence of batches (giant step j, 8 diagonals from i0)
     int j = jg, i0 = 0;
     if (j >= n2) return;
-    auto load = [&](int jj, int ii, u64 (&d)[8]) {
-        const int cnt = min(n1, ell - jj * n1);
-        const u64* D = diags + ((long long)jj * n1 + ii) * dstride + (long long)i * N + k;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) d[u] = (ii + u < cnt) ? __ldcs(D + (long long)u * dstride) : 0ull;
-    };
+    const u64* sbase = sb + pl;
+    const int TP2 = 2 * TP;
     Acc128 acc[B][2];
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
     for (;;) {
         const int cnt = min(n1, ell - j * n1);
-        u64 d[8];
-        load(j, i0, d);
-        // next batch
-        int jn = j, in = i0 + 8;
-        if (in >= cnt) {
-            jn = j + JG;
-            in = 0;
-        }
-        // 8 products per component in 30-bit partial sums, then one carry into acc
+        const u64* D = diags + ((long long)j * n1 + i0) * dstride + (long long)i * N + k;
+        const u64* s0 = sbase + i0 * TP2;
         Acc3 p[B][2];
 #pragma unroll
         for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = Acc3{0, 0, 0};
+        if (i0 + 8 <= cnt) {
+            // full batch: no bounds checks
+            u64 d[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int ib = i0 + u;
-            if (ib >= cnt) break;
-            const u64 ds = split30(d[u]);
+            for (int u = 0; u < 8; ++u) {
+                d[u] = __ldcs(D);
+                D += dstride;
+            }
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                const u64* sq = sb + b * per_q + ib * 2 * TP + pl;
-                mac30(p[b][0], sq[0], ds);
-                mac30(p[b][1], sq[TP], ds);
+            for (int u = 0; u < 8; ++u) {
+                const u64 ds = split30(d[u]);
+                const u64* sq = s0 + u * TP2;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    mac30(p[b][0], sq[b * per_q], ds);
+                    mac30(p[b][1], sq[b * per_q + TP], ds);
+                }
+            }
+        } else {
+            for (int u = 0; i0 + u < cnt; ++u) {
+                const u64 ds = split30(__ldcs(D + (long long)u * dstride));
+                const u64* sq = s0 + u * TP2;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    mac30(p[b][0], sq[b * per_q], ds);
+                    mac30(p[b][1], sq[b * per_q + TP], ds);
+                }
             }
         }
 #pragma unroll
@@ -335,6 +341,12 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
             flush30(acc[b][1], p[b][1]);
             fold(acc[b][0], q);
             fold(acc[b][1], q);
+        }
+        // next batch
+        int jn = j, in = i0 + 8;
+        if (in >= cnt) {
+            jn = j + JG;
+            in = 0;
         }
         if (jn != j) {
 #pragma unroll
