@@ -265,13 +265,15 @@ fr_status fr_sync(fr_ctx* ctx);
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
 /* NTT autotuner (run by fr_setup on device contexts unless the environment sets
- * FR_NTT_TUNE=0): for N >= 2^15 it times each tile shape of a forward + inverse transform on
- * this GPU for one batch size per bucket (<= 4, <= 16, <= 64, > 64 limb-polynomials; best of
- * 3 runs after a warm-up) and keeps the fastest. Shapes: bit 0 = 8 columns per column-pass
- * CTA (else 4), bit 1 = 256-thread row-pass CTAs (else 128). shapes[4] receives the chosen
- * shape per bucket, us[16] (may be NULL) the measured microseconds, bucket-major. */
+ * FR_NTT_TUNE=0): for N >= 2^15 it times each shape of a forward + inverse transform on this
+ * GPU for one batch size per bucket (<= 4, <= 16, <= 64, > 64 limb-polynomials; best of 3
+ * runs after a warm-up) and keeps the fastest. Shapes 0..3: two-pass kernels, bit 0 = 8
+ * columns per column-pass CTA (else 4), bit 1 = 256-thread row-pass CTAs (else 128); shape 4
+ * (N = 2^16 only): one launch per transform, a cluster of 8 CTAs per polynomial exchanging
+ * through distributed shared memory. shapes[4] receives the chosen shape per bucket, us[20]
+ * (may be NULL) the measured microseconds, bucket-major (-1: shape not available). */
 fr_status fr_ntt_tuning(const fr_ctx* ctx, uint32_t* shapes, double* us);
-/* Override the tile shape per bucket (shapes[4], each 0..3); drops the captured match graphs.
+/* Override the shape per bucket (shapes[4], each 0..4); drops the captured match graphs.
  * Every shape computes the same transform, bit for bit. */
 fr_status fr_ntt_set_shapes(fr_ctx* ctx, const uint32_t* shapes);
 

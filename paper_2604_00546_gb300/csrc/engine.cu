@@ -120,7 +120,7 @@ struct fr_ctx {
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query
-    double ntt_tune_us[FR_NTT_BUCKETS * 4] = {};  // tuner times: bucket x tile shape (forward + inverse)
+    double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
     Server* server = nullptr;            // continuous-batching loop (fr_match_submit / fr_match_poll)
 };
@@ -2233,7 +2233,8 @@ fr_status fr_ntt_tuning(const fr_ctx* c, uint32_t* shapes, double* us) {
         need_device(c);
         for (int b = 0; b < FR_NTT_BUCKETS; ++b) {
             if (shapes) shapes[b] = c->rd.ntt_shape[b];
-            for (int sh = 0; sh < 4 && us; ++sh) us[b * 4 + sh] = c->ntt_tune_us[b * 4 + sh];
+            for (int sh = 0; sh < FR_NTT_SHAPES && us; ++sh)
+                us[b * FR_NTT_SHAPES + sh] = c->ntt_tune_us[b * FR_NTT_SHAPES + sh];
         }
     });
 }
@@ -2244,7 +2245,7 @@ fr_status fr_ntt_set_shapes(fr_ctx* c, const uint32_t* shapes) {
         std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!shapes) raise(FR_ERR_INVALID_ARG, "null argument");
         for (int b = 0; b < FR_NTT_BUCKETS; ++b)
-            if (shapes[b] > 3) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..3");
+            if (shapes[b] >= FR_NTT_SHAPES) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..4");
         for (int b = 0; b < FR_NTT_BUCKETS; ++b) c->rd.ntt_shape[b] = (unsigned char)shapes[b];
         drop_graphs(c, nullptr);  // captured graphs hold the previous launch shapes
     });

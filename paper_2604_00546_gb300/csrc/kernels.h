@@ -57,6 +57,7 @@ struct PolyBatch {
 
 // NTT batch-size buckets for the tuned tile shapes: <= 4, <= 16, <= 64, larger.
 #define FR_NTT_BUCKETS 4
+#define FR_NTT_SHAPES 5
 __host__ __device__ inline int ntt_bucket(int npolys) {
     return npolys <= 4 ? 0 : npolys <= 16 ? 1 : npolys <= 64 ? 2 : 3;
 }
@@ -76,7 +77,8 @@ struct RingDev {
 
 // Batched negacyclic NTT (evaluation order: position k = value at psi^(2 brev(k)+1)).
 void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s);
-// Autotuner of the NTT tile shapes (see ntt.cu); us: 4 x 4 times in microseconds, or null.
+// Autotuner of the NTT tile shapes (see ntt.cu); us: FR_NTT_BUCKETS x FR_NTT_SHAPES times in
+// microseconds (-1: shape not available), or null.
 void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps);
 // Butterflies per second of the NTT's forward butterfly with operands in registers.
 double measure_butterfly_peak(int device);

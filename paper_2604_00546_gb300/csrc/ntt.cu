@@ -18,6 +18,7 @@
 // Twiddle of the butterfly pairing x and x + 2^b, in either direction:
 // tw[(M + J) >> (b + 1)] where J is the global index of x and M = R for the
 // column pass, N for the row pass.
+#include <cooperative_groups.h>
 #include <cstdlib>
 #include <type_traits>
 
@@ -316,6 +317,106 @@ __global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, P
     }
 }
 
+// Single-launch NTT of N = 2^16 (256 x 256) for small batches. A cluster of 8 CTAs of 1024
+// threads holds one polynomial, 64 KiB per CTA. Forward: CTA c transforms columns
+// [32c, 32c + 32) (column pass, exchanges in buffer A), then writes every result straight
+// into the receive buffer (B) of the CTA owning its row block [32r, 32r + 32) through
+// distributed shared memory; after the cluster barrier each CTA runs the row pass on its
+// 32 rows (exchanges in A) and stores them. Inverse: row pass first (rows from global,
+// exchanges in B), results to the column owners' A, then the column pass (exchanges in B).
+// The intermediate never goes through global memory and the transform is one launch.
+constexpr int kClusterCtas = 8;
+constexpr size_t kClusterSmem = (size_t)(2 * 8192 + 2 * 256) * sizeof(u64);
+
+template <bool INV, class E>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
+    k_ntt_cluster(RingDev R, PolyBatch b, E epi) {
+    pdl_wait();
+    pdl_trigger();
+    namespace cg = cooperative_groups;
+    constexpr int LOG = 8, S = 256;
+    extern __shared__ u64 sm[];
+    u64* A = sm;              // 32 rows x 256 (row layout) / 256 rows x 32 columns (column layout)
+    u64* Bb = sm + 8192;
+    u64* sw = sm + 16384;     // column-pass twiddles [0, 256)
+    u64* sws = sw + S;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int N = R.N;
+    const int p = blockIdx.y;
+    int pi;
+    u64* x = poly_at(b, p, N, &pi);
+    const u64 q = R.primes[pi].q;
+    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+        sw[i] = tw[i];
+        sws[i] = tws[i];
+    }
+    const bool grow = q < (1ull << 57);
+    // column-pass coordinates: column 32 rank + col, rows phase_x(tauc, e)
+    const int col = threadIdx.x & 31, tauc = threadIdx.x >> 5;
+    const int gcol = rank * 32 + col;
+    // row-pass coordinates: row 32 rank + rloc, elements phase_x(taur, e)
+    const int rloc = threadIdx.x >> 5, taur = threadIdx.x & 31;
+    const int rho = rank * 32 + rloc;
+    u64 v[8];
+    if constexpr (!INV) {
+        constexpr int L0 = PhaseInfo<LOG, false, 0>::LO, LL = LastLo<LOG, false>::v;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tauc, e) * S + gcol];
+        __syncthreads();
+        Ctx c{0, S, 0, 0, sw, sws, q, grow};
+        ColEx<32> exc{A, col};
+        phases<LOG, false, 0>(v, tauc, c, exc);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int row = phase_x<LL>(tauc, e);
+            u64* dst = cl.map_shared_rank(Bb, row >> 5);
+            dst[(row & 31) * S + gcol] = v[e];
+        }
+        cl.sync();
+        u64* br = Bb + rloc * S;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = br[phase_x<L0>(taur, e)];
+        Ctx cr{rho * S, N, 0, 0, tw, tws, q, grow};
+        RowEx exr{A + rloc * S};
+        phases<LOG, false, 0>(v, taur, cr, exr);
+        const u64 one_s = R.primes[pi].one_s;
+        u64* xr = x + (long long)rho * S;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const u64 fv = grow ? mul_shoup(v[e], 1, one_s, q) : reduce4(v[e], q);
+            if constexpr (std::is_same<E, EpiStore>::value) xr[phase_x<LL>(taur, e)] = fv;
+            else epi.put(p, rho * S + phase_x<LL>(taur, e), fv, q);
+        }
+    } else {
+        constexpr int L0 = PhaseInfo<LOG, true, 0>::LO, LL = LastLo<LOG, true>::v;
+        const u64* xr = x + (long long)rho * S;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(taur, e)];
+        Ctx cr{rho * S, N, 0, 0, tw, tws, q, false};
+        RowEx exr{Bb + rloc * S};
+        phases<LOG, true, 0>(v, taur, cr, exr);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = phase_x<LL>(taur, e);
+            u64* dst = cl.map_shared_rank(A, k >> 5);
+            dst[rho * 32 + (k & 31)] = v[e];
+        }
+        cl.sync();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = A[phase_x<L0>(tauc, e) * 32 + col];
+        Ctx c{0, S, 0, 0, sw, sws, q, false};
+        ColEx<32> exc{Bb, col};
+        phases<LOG, true, 0>(v, tauc, c, exc);
+        const DevPrime P = R.primes[pi];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            x[(long long)phase_x<LL>(tauc, e) * S + gcol] = mul_shoup(v[e], P.ninv, P.ninv_s, q);
+    }
+}
+
 template <int LOGR, int LOGC, class E, int KTC, int RT>
 void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
     constexpr int SR = 1 << LOGR, SC = 1 << LOGC;
@@ -335,12 +436,33 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     }
 }
 
-// Tile shape of a launch: bit 0 set = 8 columns per column-pass CTA (else 4), bit 1 set =
-// 256-thread row-pass CTAs (else 128). Chosen per batch-size bucket by the tuner (RingDev
+// Tile shape of a launch: 0..3 are the two-pass kernels, bit 0 set = 8 columns per
+// column-pass CTA (else 4), bit 1 set = 256-thread row-pass CTAs (else 128); 4 is the
+// single-launch cluster kernel (N = 2^16). Chosen per batch-size bucket by the tuner (RingDev
 // holds the table); sizes other than N = 2^15, 2^16 use shape 0.
+template <class E>
+void launch_ntt_cluster(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ntt_cluster<false, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmem);
+        cudaFuncSetAttribute(k_ntt_cluster<true, EpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kClusterSmem);
+        attr = true;
+    }
+    const dim3 g(kClusterCtas, b.npolys);
+    if (!inverse) launch_k(k_ntt_cluster<false, E>, g, dim3(1024), kClusterSmem, st, R, b, epi);
+    else launch_k(k_ntt_cluster<true, EpiStore>, g, dim3(1024), kClusterSmem, st, R, b, EpiStore{});
+}
+
 template <int LOGR, int LOGC, class E>
 void launch_ntt_s(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
     const int shape = (LOGR + LOGC >= 15) ? R.ntt_shape[ntt_bucket(b.npolys)] : 0;
+    if constexpr (LOGR == 8 && LOGC == 8) {
+        if (shape == 4) {
+            launch_ntt_cluster(R, b, inverse, st, epi);
+            return;
+        }
+    }
     switch (shape) {
         case 1: launch_ntt_t<LOGR, LOGC, E, 8, 128>(R, b, inverse, st, epi); break;
         case 2: launch_ntt_t<LOGR, LOGC, E, 4, 256>(R, b, inverse, st, epi); break;
@@ -435,7 +557,10 @@ void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t
 // shape per bucket in R.ntt_shape; us[bucket * 4 + shape] receives the times.
 void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
     for (int bk = 0; bk < FR_NTT_BUCKETS; ++bk) R.ntt_shape[bk] = 0;
+    if (us)
+        for (int i = 0; i < FR_NTT_BUCKETS * FR_NTT_SHAPES; ++i) us[i] = 0;
     if (R.logN < 15) return;
+    const int nshapes = R.logN == 16 ? FR_NTT_SHAPES : FR_NTT_SHAPES - 1;  // the cluster kernel is N = 2^16 only
     const int sizes[FR_NTT_BUCKETS] = {4, 16, 64, 256};
     const int maxp = sizes[FR_NTT_BUCKETS - 1];
     u64* buf = nullptr;
@@ -451,7 +576,7 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
         pb.pm.idx[0] = 0;
         double tbest = 1e30;
         best[bk] = 0;
-        for (int sh = 0; sh < 4; ++sh) {
+        for (int sh = 0; sh < nshapes; ++sh) {
             R.ntt_shape[bk] = (unsigned char)sh;
             double t = 1e30;
             for (int r = 0; r <= reps; ++r) {  // first run warms up
@@ -464,7 +589,8 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
                 cudaEventElapsedTime(&ms, a, e);
                 if (r > 0) t = t < ms * 1000.0 ? t : ms * 1000.0;
             }
-            if (us) us[bk * 4 + sh] = t;
+            if (cudaGetLastError() != cudaSuccess) t = 1e30;  // a shape this GPU cannot launch
+            if (us) us[bk * FR_NTT_SHAPES + sh] = t < 1e29 ? t : -1.0;
             if (t < tbest) {
                 tbest = t;
                 best[bk] = (unsigned char)sh;

@@ -304,10 +304,10 @@ class Context:
     def ntt_tuning(self):
         """Tile shape chosen per NTT batch bucket and the tuner's times (us, bucket x shape)."""
         shapes = np.zeros(4, dtype=np.uint32)
-        us = np.zeros(16, dtype=np.float64)
+        us = np.zeros(20, dtype=np.float64)
         _check(_lib.fr_ntt_tuning(self.h, shapes, us))
         return dict(buckets=["<=4", "<=16", "<=64", ">64"], shapes=[int(x) for x in shapes],
-                    us=us.reshape(4, 4).round(2).tolist())
+                    us=us.reshape(4, 5).round(2).tolist())
 
     def ntt_set_shapes(self, shapes):
         _check(_lib.fr_ntt_set_shapes(self.h, np.ascontiguousarray(shapes, dtype=np.uint32)))
