@@ -52,7 +52,8 @@ def check_scores(ctx, keys, orc, T, n1, seed, schedule=0):
     s = T.astype(np.float64) @ q
     dec = np.concatenate([ctx.decrypt(keys, o) for o in out])
     assert np.abs(dec[: len(s)] - s).max() < 1e-4
-    assert np.abs(dec[len(s):]).max() < 1e-4   # padding rows score 0
+    if len(dec) > len(s):
+        assert np.abs(dec[len(s):]).max() < 1e-4   # padding rows score 0
 
 
 def test_single_template(orc):
