@@ -477,20 +477,6 @@ __global__ void k_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int 
 }
 
 // x <- 2 x - c (c added to the constant term: every evaluation point of c0)
-__global__ void k_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N) {
-    pdl_wait();
-    pdl_trigger();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y % (level + 1);
-    const int t = blockIdx.y / (level + 1);
-    if (k >= N) return;
-    const u64 q = primes[i].q;
-    u64* p = x + ((long long)t * cap + i) * N + k;
-    u64 v = add_mod(*p, *p, q);
-    if (t == 0) v = sub_mod(v, cres[i], q);
-    *p = v;
-}
-
 __global__ void k_to_mont(u64* x, long long n_per_poly, PrimeMap pm, const DevPrime* primes, long long total) {
     pdl_wait();
     pdl_trigger();
@@ -746,11 +732,6 @@ void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level,
                         const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), nleaves);
     launch_k(k_cheb_leaves, dim3(g), dim3(kThreads), 0, s, x, x_cap, out, o_cap, level, cb, cb_s, ca, primes, N);
-}
-
-void launch_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N, cudaStream_t s) {
-    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1));
-    launch_k(k_double_sub, dim3(g), dim3(kThreads), 0, s, x, cap, level, cres, primes, N);
 }
 
 void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,

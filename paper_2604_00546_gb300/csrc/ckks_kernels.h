@@ -48,12 +48,13 @@ struct IPJob {
 struct MDJob {
     const u64* acc;   // [2][npos][N]
     const u64* conv;  // [2][level+1][N]
-    const u64* add;   // mode 1: c0 limbs (stride N); mode 2: ct with add_cap
+    const u64* add;   // modes 1, 3: c0 limbs (stride N); mode 2: ct with add_cap
     u64* out;         // ct with out_cap
     int out_cap;
     int add_cap;
-    int mode;         // 0 none, 1 rotation addend sigma_g(c0), 2 ct addend
+    int mode;         // 0 none, 1 rotation addend sigma_g(c0), 2 ct addend, 3 rotation + ct addend
     u32 galois;
+    const u64* add2;  // mode 3: ct with add_cap added to both components
 };
 
 struct TensorJob {
@@ -81,9 +82,12 @@ struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
                         const u64* pinv, const u64* pinv_s, cudaStream_t s);
 // Forward NTT of a rescale's lifted last limb fused with its combine: poly p of b is
-// (ct component p / l, limb p % l); writes out = (x - NTT(lifted)) q_l^-1.
+// (ct component p / l, limb p % l); writes out = (x - NTT(lifted)) q_l^-1, then mode 1 adds
+// the matching component of the ct at add + (p / l / 2) add_bs (cap add_cap), mode 2 doubles
+// and subtracts cres[i] from component 0.
 void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
-                        const RescaleTab* tab, int l, cudaStream_t s);
+                        const RescaleTab* tab, int l, int mode, const u64* add, int add_cap, long long add_bs,
+                        const u64* cres, cudaStream_t s);
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s);
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
@@ -109,7 +113,6 @@ void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap,
                 int N, cudaStream_t s);
 void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
                         const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s);
-void launch_double_sub(u64* x, int cap, int level, const u64* cres, const DevPrime* primes, int N, cudaStream_t s);
 void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,
                     cudaStream_t s);
 void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,

@@ -270,6 +270,7 @@ struct KSReq {
     int add_cap;
     u64* out;
     int out_cap;
+    const u64* add2 = nullptr;  // mode 3
 };
 
 // inner product + ModDown of up to FR_MAX_JOBS jobs; job j reads its ModUp output ext[j].
@@ -327,6 +328,7 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
         m.out_cap = reqs[j]->out_cap;
         m.mode = reqs[j]->mode;
         m.galois = reqs[j]->galois;
+        m.add2 = reqs[j]->add2;
     }
     // forward NTT of the conversions with the combine as its epilogue
     // the region counts the transform's 16 B per coefficient (its butterflies); the fused
@@ -418,7 +420,17 @@ void rotate_cts(fr_ctx* c, int level, const std::vector<const u64*>& in, int in_
     keyswitch(c, level, reqs);
 }
 
-void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, int out_cap) {
+// options of the rescale's fused epilogue (EpiRescale modes)
+struct RescaleEpi {
+    int mode = 0;
+    const u64* add = nullptr;
+    int add_cap = 0;
+    long long add_bs = 0;
+    const u64* cres = nullptr;
+};
+
+void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, int out_cap,
+             const RescaleEpi& ep = RescaleEpi()) {
     if (level < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
     const int N = c->R.N, l = level;
     Tmp last(c, (size_t)2 * B * N);
@@ -437,7 +449,8 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     // forward NTT of the lifted limb with the combine as its epilogue
     Prof p(c, "ntt", 16.0 * 2 * B * l * N);
     PolyBatch pb{lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1)};
-    launch_ntt_rescale(c->rd, pb, in, in_cap, out, out_cap, c->d_rescale[l], l, c->cur);
+    launch_ntt_rescale(c->rd, pb, in, in_cap, out, out_cap, c->d_rescale[l], l, ep.mode, ep.add, ep.add_cap, ep.add_bs,
+                       ep.cres, c->cur);
     c->launches += 2;
 }
 
@@ -533,12 +546,10 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
         mul_relin(c, lv, A, prev_cap, A, prev_cap, O, lv + 1);
         pw[m].reset(new Tmp(c, (size_t)B * ctw(c, lv)));
         pw_cap[m] = lv;
-        rescale(c, sq.p, B, lv, lv + 1, pw[m]->p, lv);
-        for (int b = 0; b < B; ++b) {
-            Prof p(c, "misc");
-            launch_double_sub(pw[m]->p + (size_t)b * ctw(c, lv), lv, lv - 1, c->d_delta, c->d_primes, N, c->cur);
-            c->launches++;
-        }
+        RescaleEpi dsub;  // T_2k = 2 T_k^2 - 1: doubling and the constant in the rescale's epilogue
+        dsub.mode = 2;
+        dsub.cres = c->d_delta;
+        rescale(c, sq.p, B, lv, lv + 1, pw[m]->p, lv, dsub);
         CU(cudaEventRecord(c->evs[m], main));
         prev = pw[m]->p;
         prev_cap = lv;
@@ -576,9 +587,12 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
             }
         mul_relin(c, lc, A, vcap, Bv, pw_cap[s], O, lc + 1);
         std::unique_ptr<Tmp> w(new Tmp(c, (size_t)B * P * ctw(c, lc)));
-        rescale(c, prod.p, B * P, lc, lc + 1, w->p, lc);
-        add_cts(c, w->p, lc, ctw(c, lc), v->p + ctw(c, vcap), vcap, 2 * ctw(c, vcap), w->p, lc, ctw(c, lc), lc - 1,
-                B * P);
+        RescaleEpi addc;  // + child(2i+1), the odd children, in the rescale's epilogue
+        addc.mode = 1;
+        addc.add = v->p + ctw(c, vcap);
+        addc.add_cap = vcap;
+        addc.add_bs = 2 * ctw(c, vcap);
+        rescale(c, prod.p, B * P, lc, lc + 1, w->p, lc, addc);
         v = std::move(w);
         vcap = lc;
     }
@@ -631,18 +645,27 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
 
 // RotateAndSum of B ciphertexts [B][2][cap][N] in place: ct <- ct + Rot_{2^t}(ct), t = 0..log2(n)-1
 void rotate_sum(fr_ctx* c, u64* ct, int cap, int level, int B = 1) {
-    const int n = c->R.N / 2;
-    Tmp r(c, (size_t)B * ctw(c, cap));
-    std::vector<const u64*> in;
-    std::vector<u64*> outs;
-    for (int b = 0; b < B; ++b) {
-        in.push_back(ct + (size_t)b * ctw(c, cap));
-        outs.push_back(r.p + (size_t)b * ctw(c, cap));
-    }
+    // x <- x + Rot_{2^t}(x): the addition is the epilogue of each rotation's ModDown, writing
+    // into the other of two buffers
+    const int n = c->R.N / 2, N = c->R.N;
+    const size_t cw = (size_t)ctw(c, cap);
+    Tmp r(c, (size_t)B * cw);
+    u64* buf[2] = {ct, r.p};
+    int cur = 0;
     for (long t = 1; t < n; t <<= 1) {
-        rotate_cts(c, level, in, cap, std::vector<long>(B, t), outs, cap, false);
-        add_cts(c, ct, cap, ctw(c, cap), r.p, cap, ctw(c, cap), ct, cap, ctw(c, cap), level, B);
+        const u64 g = frh::galois_of_rotation(c->R, t);
+        const u64* key = rot_key(c, g);
+        std::vector<KSReq> reqs;
+        for (int b = 0; b < B; ++b) {
+            const u64* src = buf[cur] + (size_t)b * cw;
+            KSReq rq{src + (size_t)cap * N, key, (u32)g, 3, src, cap, buf[1 - cur] + (size_t)b * cw, cap};
+            rq.add2 = src;
+            reqs.push_back(rq);
+        }
+        keyswitch(c, level, reqs);
+        cur = 1 - cur;
     }
+    if (cur) copy_d2d(c, ct, r.p, (size_t)B * cw);
 }
 
 // ---------------------------------------------------------------------------

@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
 struct EpiStore {};
 
 // ModDown combine: poly p = (job, component t, limb i) of the P -> Q conversions; out =
-// (acc_Q - v) P^-1 (+ sigma_g(c0) for rotations, + the ct addend for relinearisation).
+// (acc_Q - v) P^-1 (+ sigma_g(c0) for rotations, + the ct addend for relinearisation; a
+// rotation may add a ciphertext as well, as in x + Rot(x)).
 struct EpiModDown {
     MDJobs jobs;
     int npos, level, logN;
@@ -242,8 +243,9 @@ struct EpiModDown {
         const MDJob& J = jobs.j[j];
         const u64 a = J.acc[((long long)t * npos + i) * N + k];
         u64 w = mul_shoup(sub_mod(a, v, q), pinv[i], pinv_s[i], q);
-        if (J.mode == 1) {
+        if (J.mode == 1 || J.mode == 3) {
             if (t == 0) w = add_mod(w, J.add[(long long)i * N + galois_src_index((u32)k, J.galois, logN)], q);
+            if (J.mode == 3) w = add_mod(w, J.add2[((long long)t * J.add_cap + i) * N + k], q);
         } else if (J.mode == 2) {
             w = add_mod(w, J.add[((long long)t * J.add_cap + i) * N + k], q);
         }
@@ -252,16 +254,29 @@ struct EpiModDown {
 };
 
 // Rescale combine: poly p = (ct component bt, limb i) of the lifted last limb;
-// out = (x - v) q_l^-1.
+// out = (x - v) q_l^-1, then (mode 1) + the matching component of an addend ct, or
+// (mode 2) doubled with cres_i subtracted from component 0 (2 T^2 - 1 of the Chebyshev powers).
 struct EpiRescale {
     const u64* x;
     u64* out;
     const RescaleTab* tab;
     int x_cap, out_cap, l, N;
+    int mode;
+    const u64* add;     // mode 1: ct b at add + b add_bs, component t at + t add_cap N
+    int add_cap;
+    long long add_bs;
+    const u64* cres;    // mode 2: [l] constants
     __device__ __forceinline__ void put(int p, int k, u64 v, u64 q) const {
         const int bt = p / l, i = p % l;
         const u64 a = x[((long long)bt * x_cap + i) * N + k];
-        out[((long long)bt * out_cap + i) * N + k] = mul_shoup(sub_mod(a, v, q), tab->qlinv[i], tab->qlinv_s[i], q);
+        u64 r = mul_shoup(sub_mod(a, v, q), tab->qlinv[i], tab->qlinv_s[i], q);
+        if (mode == 1) {
+            r = add_mod(r, add[(long long)(bt >> 1) * add_bs + ((long long)(bt & 1) * add_cap + i) * N + k], q);
+        } else if (mode == 2) {
+            r = add_mod(r, r, q);
+            if ((bt & 1) == 0) r = sub_mod(r, cres[i], q);
+        }
+        out[((long long)bt * out_cap + i) * N + k] = r;
     }
 };
 
@@ -611,7 +626,8 @@ void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs
 }
 
 void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
-                        const RescaleTab* tab, int l, cudaStream_t s) {
-    EpiRescale e{x, out, tab, x_cap, out_cap, l, R.N};
+                        const RescaleTab* tab, int l, int mode, const u64* add, int add_cap, long long add_bs,
+                        const u64* cres, cudaStream_t s) {
+    EpiRescale e{x, out, tab, x_cap, out_cap, l, R.N, mode, add, add_cap, add_bs, cres};
     launch_ntt_e(R, b, false, s, e);
 }
