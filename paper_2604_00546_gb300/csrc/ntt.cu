@@ -514,12 +514,12 @@ __global__ void __launch_bounds__(256) k_butterfly_peak(u64 q, u64 w, u64 ws, in
 
 }  // namespace
 
-bool pdl_enabled() {
-    static const bool on = [] {
+int pdl_mode() {
+    static const int m = [] {
         const char* e = std::getenv("FR_PDL");
-        return e && e[0] == '1';
+        return e && e[0] == '0' ? 0 : e && e[0] == '1' ? 1 : 2;
     }();
-    return on;
+    return m;
 }
 
 double measure_butterfly_peak(int device) {
