@@ -320,6 +320,15 @@ def run_identify(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / steps
     del outs
+    # one eager profiled query: device time per region and per stage
+    ctx.profile(True)
+    outs = ctx.match(db, dq, fr.FR_MODE_IDENTIFY)
+    torch.cuda.synchronize()
+    regions = {r: ctx.profile_read(r)[0] for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac",
+                                                   "misc", "encode")}
+    stages = {st: ctx.profile_read("stage:" + st)[0] for st in ("babies", "encode", "mac", "giants", "cheb")}
+    ctx.profile(False)
+    del outs
     line = {
         "metric": "identification: templates matched/s and query latency at N=2^16, K=2^20",
         "value": K / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps, "ms_per_step": ms,
@@ -330,6 +339,7 @@ def run_identify(args):
                    "work_level": ctx.work_level, "db_bytes": info["bytes"]},
         "check": {"max_abs_err_threshold": float(np.abs(dec - p).max()), "decisions_agree_outside_margin": agree,
                   "planted_found": int(len(set(planted.tolist()) & found)), "planted": int(len(planted))},
+        "regions_ms": regions, "stages_ms": stages,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
