@@ -545,13 +545,13 @@ __global__ void __launch_bounds__(256) k_fft_col(cplx* z, int logn, int logR, co
     __syncthreads();
     for (int len = n; len >= 2 * C; len >>= 1) {
         const int hrow = (len >> 1) / C;  // half block in rows
-        const long long lq = (long long)len << 2, gap = M / lq;
+        const long long lq = (long long)len << 2, gap = M / lq;  // powers of two
         for (int bf = threadIdx.x; bf < (Rr >> 1) * TC; bf += blockDim.x) {
             int c = bf % TC, pr = bf / TC;
             int blk = pr / hrow, u = pr - blk * hrow;
             int ra = blk * 2 * hrow + u, rb = ra + hrow;
             const int j = (col0 + c) + u * C;  // position inside the len-block
-            const long long idx = (lq - (long long)(rot[j] % lq)) * gap;
+            const long long idx = (lq - (long long)(rot[j] & (unsigned)(lq - 1))) * gap;
             fft_inv_bfly(sc[ra * TC + c], sc[rb * TC + c], zr[idx], zi[idx]);
         }
         __syncthreads();
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(256) k_fft_row(cplx* z, int logn, int logR, in
         for (int bf = threadIdx.x; bf < tile / 2; bf += blockDim.x) {
             int blk = bf / h, u = bf - blk * h;
             int a = blk * len + u, b = a + h;
-            const long long idx = (lq - (long long)(rot[u] % lq)) * gap;
+            const long long idx = (lq - (long long)(rot[u] & (unsigned)(lq - 1))) * gap;
             fft_inv_bfly(sc[a], sc[b], zr[idx], zi[idx]);
         }
         __syncthreads();
@@ -606,16 +606,13 @@ __global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* 
     const double delta = ldexp(1.0, scale_bits);
     const long long m = llround(__dmul_rn(__dmul_rn(v, inv_n), delta));
     u64* o = out + (long long)di * nl * N;
+    // m mod q_i for the signed coefficient: |m| reduced with the Shoup quotient of 1
+    const bool neg = m < 0;
+    const u64 a = neg ? (u64)(-(m + 1)) : (u64)m;
     for (int i = 0; i < nl; ++i) {
-        const u64 q = primes[i].q;
-        u64 r;
-        if (m >= 0) {
-            r = (u64)m % q;
-        } else {
-            u64 a = (u64)(-(m + 1)) % q;
-            r = q - 1 - a;
-        }
-        o[(long long)i * N + c] = r;
+        const DevPrime& P = primes[i];
+        const u64 ra = mul_shoup(a, 1, P.one_s, P.q);
+        o[(long long)i * N + c] = neg ? P.q - 1 - ra : ra;
     }
 }
 

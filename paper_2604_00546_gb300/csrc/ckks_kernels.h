@@ -76,6 +76,8 @@ struct IPJobs {
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
+// Forward NTT that stores its values in Montgomery form (x 2^64 mod q), in place.
+void launch_ntt_tomont(const RingDev& R, const PolyBatch& b, cudaStream_t s);
 // Forward NTT of the P -> Q conversions of a ModDown fused with its combine: poly p of b is
 // (job p / (2(level+1)), component, limb); the transformed values never reach memory, the
 // jobs' outputs do (as launch_moddown_combine would write them).

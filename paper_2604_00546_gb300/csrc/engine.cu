@@ -637,9 +637,13 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
                                 c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->cur);
             c->launches += 4;
         }
-        ntt(c, o, (long long)nl * N, nl, nd * nl, pm, false);
-        launch_to_mont(o, N, pm, c->d_primes, (long long)nd * nl * N, c->cur);
-        c->launches++;
+        {
+            // forward NTT with the Montgomery conversion in its epilogue
+            Prof p(c, "ntt", 16.0 * nd * nl * N);
+            PolyBatch pb{o, (long long)nl * N, nl, nd * nl, pm};
+            launch_ntt_tomont(c->rd, pb, c->cur);
+            c->launches += 2;
+        }
     }
 }
 

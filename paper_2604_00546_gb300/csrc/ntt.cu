@@ -229,6 +229,9 @@ __global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
 // epilogue finishes the operation the transform belonged to.
 struct EpiStore {};
 
+// Montgomery form of the transformed value, stored in place (template diagonals).
+struct EpiToMont {};
+
 // ModDown combine: poly p = (job, component t, limb i) of the P -> Q conversions; out =
 // (acc_Q - v) P^-1 (+ sigma_g(c0) for rotations, + the ct addend for relinearisation; a
 // rotation may add a ciphertext as well, as in x + Rot(x)).
@@ -311,7 +314,13 @@ __global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, P
     Ctx c{Jbase, N, 0, 0, tw, tws, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
-    if constexpr (!std::is_same<E, EpiStore>::value) {
+    if constexpr (std::is_same<E, EpiToMont>::value) {
+        static_assert(!INV, "epilogues follow forward transforms");
+        const DevPrime P = R.primes[pi];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            xr[phase_x<LL>(tau, e)] = to_mont(grow ? mul_shoup(v[e], 1, P.one_s, q) : reduce4(v[e], q), P);
+    } else if constexpr (!std::is_same<E, EpiStore>::value) {
         static_assert(!INV, "epilogues follow forward transforms");
         const u64 one_s = R.primes[pi].one_s;
 #pragma unroll
@@ -403,6 +412,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
         for (int e = 0; e < 8; ++e) {
             const u64 fv = grow ? mul_shoup(v[e], 1, one_s, q) : reduce4(v[e], q);
             if constexpr (std::is_same<E, EpiStore>::value) xr[phase_x<LL>(taur, e)] = fv;
+            else if constexpr (std::is_same<E, EpiToMont>::value) xr[phase_x<LL>(taur, e)] = to_mont(fv, R.primes[pi]);
             else epi.put(p, rho * S + phase_x<LL>(taur, e), fv, q);
         }
     } else {
@@ -617,6 +627,10 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
     cudaEventDestroy(e);
     cudaFreeAsync(buf, s);
     cudaStreamSynchronize(s);
+}
+
+void launch_ntt_tomont(const RingDev& R, const PolyBatch& b, cudaStream_t s) {
+    launch_ntt_e(R, b, false, s, EpiToMont{});
 }
 
 void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
