@@ -599,7 +599,7 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
         PolyBatch pb{buf, 0, sizes[bk], sizes[bk], PrimeMap{}};
         pb.pm.period = 1;
         pb.pm.idx[0] = 0;
-        double tbest = 1e30;
+        double tbest = 1e30, t0 = 1e30;
         best[bk] = 0;
         for (int sh = 0; sh < nshapes; ++sh) {
             R.ntt_shape[bk] = (unsigned char)sh;
@@ -616,7 +616,9 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
             }
             if (cudaGetLastError() != cudaSuccess) t = 1e30;  // a shape this GPU cannot launch
             if (us) us[bk * FR_NTT_SHAPES + sh] = t < 1e29 ? t : -1.0;
-            if (t < tbest) {
+            // another shape replaces the default only when at least 3% faster (timing noise)
+            if (sh == 0) t0 = t;
+            if (sh == 0 ? t < tbest : t < tbest && t < 0.97 * t0) {
                 tbest = t;
                 best[bk] = (unsigned char)sh;
             }

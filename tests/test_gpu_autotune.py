@@ -38,7 +38,12 @@ def test_tuner_picks_the_fastest_measured_shape(big):
     assert us.shape == (4, 5) and (us[:, :4] > 0).all()
     for b in range(4):
         avail = np.where(us[b] > 0, us[b], np.inf)
-        assert t["shapes"][b] == int(np.argmin(avail))
+        sh = t["shapes"][b]
+        # the default shape stays unless another is the fastest by at least 3%
+        if sh == 0:
+            assert avail[1:].min() >= 0.97 * avail[0] or avail[1:].min() >= avail[0]
+        else:
+            assert avail[sh] == avail.min() and avail[sh] < 0.97 * avail[0]
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
