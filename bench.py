@@ -390,7 +390,7 @@ def run_reference(args):
 # DRAM traffic of the NTT passes from one ncu capture (bytes read + written per byte of
 # algorithmic traffic, summed over the column and row pass), valid for the NTT source whose
 # SHA-256 is given; the bench reports null once the source differs.
-NTT_TRAFFIC = {"sha256": "ca899bdb746974950eadb405a62912a5d9d1f6cd36e15328027483782c63be12", "dram_per_alg_byte": 1.76,
+NTT_TRAFFIC = {"sha256": "82b1b5733e395743570ddf78ed8a9297ad629e05dfd31fb0a778698839c711fe", "dram_per_alg_byte": 1.76,
                "source": "profiles/ntt_membership_N65536_level8.md"}
 
 
