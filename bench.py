@@ -335,7 +335,8 @@ def run_identify(args):
         "higher_is_better": True, "dtype": "u64",
         "data": "synthetic (seeded Gaussian L2-normalised templates, 32 planted duplicates at cosine 0.8)",
         "config": {"workload": "identify N=2^16 K=2^20 ell=512 n1=32 deg59", "K": K, "groups": info["groups"],
-                   "tier": "per-query diagonal encoding on device" if info["tier"] == 2 else "stored diagonals",
+                   "tier": {1: "stored diagonals", 2: "per-query diagonal encoding on device",
+                            3: "stored integer coefficients, per-query residues and NTT"}[info["tier"]],
                    "work_level": ctx.work_level, "db_bytes": info["bytes"]},
         "check": {"max_abs_err_threshold": float(np.abs(dec - p).max()), "decisions_agree_outside_margin": agree,
                   "planted_found": int(len(set(planted.tolist()) & found)), "planted": int(len(planted))},
@@ -697,7 +698,7 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=8)
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--identify", action="store_true", help="run the K=2^20 identification workload instead")
-    ap.add_argument("--identify-tier", type=int, default=2, choices=[0, 1, 2])
+    ap.add_argument("--identify-tier", type=int, default=2, choices=[0, 1, 2, 3])
     args = ap.parse_args()
     if args.serving:
         run_serving(args)

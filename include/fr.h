@@ -93,11 +93,14 @@ typedef struct {
     int device;                /* CUDA device ordinal; -1: client-only context (host key generation,
                                   encryption, decryption; device calls fail with FR_ERR_CUDA) */
     void* cuda_stream;         /* optional cudaStream_t to run on (not owned); NULL: the context creates one */
-    uint32_t db_tier;          /* template storage (plaintext diagonal tiers): 0 auto (stored when the
-                                  diagonals fit the budget / free HBM, else per-query encoding), 1 the
-                                  pre-rotated diagonals are encoded once and kept in HBM, 2 only the
-                                  FP32 templates are kept and each query encodes the diagonals of every
-                                  group on the device before its MAC */
+    uint32_t db_tier;          /* template storage (plaintext diagonal tiers): 0 auto (tier 1 when the
+                                  diagonals fit the budget / free HBM, else tier 3 when its coefficients
+                                  fit, else tier 2); 1 (A) the pre-rotated diagonals are encoded once and
+                                  kept in HBM in evaluation form at the working level; 3 (B) their rounded
+                                  integer coefficients are kept (8 B per coefficient, 1/(level+1) of tier
+                                  1) and each query forms the residues and NTTs; 2 (C) only the FP32
+                                  templates are kept and each query encodes the diagonals of every group
+                                  on the device before its MAC */
     uint32_t level_mode;       /* 0: the match runs at the query's top level (whole modulus chain);
                                   1: the query is first dropped (limbs discarded) to the lowest level that
                                   still leaves the threshold depth and one output level above 0:
@@ -138,7 +141,8 @@ fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
  * limbs of the context's working level (G * ell * (level+1) * N words). */
 fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
 
-/* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding), its
+/* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding, 3 stored
+ * integer coefficients), its
  * number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule
  * its matches run (0 on demand, 1 table). Any out-pointer may be NULL. */
 fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes, uint32_t* schedule);

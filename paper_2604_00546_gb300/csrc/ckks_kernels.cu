@@ -588,32 +588,64 @@ __global__ void __launch_bounds__(256) k_fft_row(cplx* z, int logn, int logR, in
     for (int e = threadIdx.x; e < tile; e += blockDim.x) x[e] = sc[e];
 }
 
-// bit reversal, scaling, rounding and residues: out [nd][nl][N] (coefficient form)
-__global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* __restrict__ out, int nl,
-                             const DevPrime* __restrict__ primes, int scale_bits) {
-    pdl_wait();
-    pdl_trigger();
+// coefficient c of the encoded diagonal di: bit reversal, times 1/n and Delta, rounded half
+// away from zero
+__device__ __forceinline__ long long fft_coef(const cplx* __restrict__ z, int logn, int di, int c, int scale_bits) {
     const int n = 1 << logn;
-    const int N = 2 * n;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int di = blockIdx.y;
-    if (c >= N || di >= nd) return;
     const int cc = c < n ? c : c - n;
     const int src = __brev(cc) >> (32 - logn);
     const cplx w = z[(long long)di * n + src];
     const double v = c < n ? w.r : w.i;
     const double inv_n = 1.0 / (double)n;
     const double delta = ldexp(1.0, scale_bits);
-    const long long m = llround(__dmul_rn(__dmul_rn(v, inv_n), delta));
-    u64* o = out + (long long)di * nl * N;
-    // m mod q_i for the signed coefficient: |m| reduced with the Shoup quotient of 1
+    return llround(__dmul_rn(__dmul_rn(v, inv_n), delta));
+}
+
+// m mod q for a signed coefficient: |m| reduced with the Shoup quotient of 1
+__device__ __forceinline__ u64 coef_residue(long long m, const DevPrime& P) {
     const bool neg = m < 0;
     const u64 a = neg ? (u64)(-(m + 1)) : (u64)m;
-    for (int i = 0; i < nl; ++i) {
-        const DevPrime& P = primes[i];
-        const u64 ra = mul_shoup(a, 1, P.one_s, P.q);
-        o[(long long)i * N + c] = neg ? P.q - 1 - ra : ra;
-    }
+    const u64 ra = mul_shoup(a, 1, P.one_s, P.q);
+    return neg ? P.q - 1 - ra : ra;
+}
+
+// rounding and residues: out [nd][nl][N] (coefficient form)
+__global__ void k_fft_finish(const cplx* __restrict__ z, int logn, int nd, u64* __restrict__ out, int nl,
+                             const DevPrime* __restrict__ primes, int scale_bits) {
+    pdl_wait();
+    pdl_trigger();
+    const int N = 2 << logn;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int di = blockIdx.y;
+    if (c >= N || di >= nd) return;
+    const long long m = fft_coef(z, logn, di, c, scale_bits);
+    u64* o = out + (long long)di * nl * N;
+    for (int i = 0; i < nl; ++i) o[(long long)i * N + c] = coef_residue(m, primes[i]);
+}
+
+// rounding only: the integer coefficients m [nd][N] (storage tier B)
+__global__ void k_fft_round(const cplx* __restrict__ z, int logn, int nd, long long* __restrict__ out,
+                            int scale_bits) {
+    pdl_wait();
+    pdl_trigger();
+    const int N = 2 << logn;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int di = blockIdx.y;
+    if (c >= N || di >= nd) return;
+    out[(long long)di * N + c] = fft_coef(z, logn, di, c, scale_bits);
+}
+
+// residues of stored integer coefficients: m [nd][N] -> out [nd][nl][N]
+__global__ void k_coef_residues(const long long* __restrict__ m, int nd, u64* __restrict__ out, int nl,
+                                const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int di = blockIdx.y;
+    if (c >= N || di >= nd) return;
+    const long long v = m[(long long)di * N + c];
+    u64* o = out + (long long)di * nl * N;
+    for (int i = 0; i < nl; ++i) o[(long long)i * N + c] = coef_residue(v, primes[i]);
 }
 
 }  // namespace
@@ -738,11 +770,9 @@ void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevP
     launch_k(k_to_mont, dim3((unsigned)blocks), dim3(kThreads), 0, s, x, n_per_poly, pm, primes, total);
 }
 
-void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
-                         void* zbuf, u64* out_coeff, int nl, const DevPrime* primes, int scale_bits,
-                         const unsigned* rot, const double* zr, const double* zi, cudaStream_t s) {
+static void encode_fft(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                       cplx* z, const unsigned* rot, const double* zr, const double* zi, cudaStream_t s) {
     const int n = 1 << logn;
-    cplx* z = (cplx*)zbuf;
     {
         dim3 g((n + kThreads - 1) / kThreads, nd);
         launch_k(k_diag_gather, dim3(g), dim3(kThreads), 0, s, T, K, ell, n, grp, d0, nd, n1, z);
@@ -762,8 +792,30 @@ void launch_encode_diags(const float* T, long long K, int ell, int logn, long lo
         const size_t sm = (size_t)bpc * C * sizeof(cplx);
         launch_k(k_fft_row, dim3(g), dim3(256), sm, s, z, logn, logR, bpc, rot, zr, zi);
     }
-    {
-        dim3 g((2 * n + kThreads - 1) / kThreads, nd);
-        launch_k(k_fft_finish, dim3(g), dim3(kThreads), 0, s, z, logn, nd, out_coeff, nl, primes, scale_bits);
-    }
+}
+
+void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                         void* zbuf, u64* out_coeff, int nl, const DevPrime* primes, int scale_bits,
+                         const unsigned* rot, const double* zr, const double* zi, cudaStream_t s) {
+    const int n = 1 << logn;
+    cplx* z = (cplx*)zbuf;
+    encode_fft(T, K, ell, logn, grp, d0, nd, n1, z, rot, zr, zi, s);
+    dim3 g((2 * n + kThreads - 1) / kThreads, nd);
+    launch_k(k_fft_finish, dim3(g), dim3(kThreads), 0, s, z, logn, nd, out_coeff, nl, primes, scale_bits);
+}
+
+void launch_encode_diags_int(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                             void* zbuf, long long* out_int, int scale_bits, const unsigned* rot, const double* zr,
+                             const double* zi, cudaStream_t s) {
+    const int n = 1 << logn;
+    cplx* z = (cplx*)zbuf;
+    encode_fft(T, K, ell, logn, grp, d0, nd, n1, z, rot, zr, zi, s);
+    dim3 g((2 * n + kThreads - 1) / kThreads, nd);
+    launch_k(k_fft_round, dim3(g), dim3(kThreads), 0, s, z, logn, nd, out_int, scale_bits);
+}
+
+void launch_coef_residues(const long long* m, int nd, u64* out, int nl, const DevPrime* primes, int N,
+                          cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, nd);
+    launch_k(k_coef_residues, dim3(g), dim3(kThreads), 0, s, m, nd, out, nl, primes, N);
 }

@@ -120,3 +120,10 @@ void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevP
 void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
                          void* zbuf, u64* out_coeff, int nl, const DevPrime* primes, int scale_bits,
                          const unsigned* rot, const double* zr, const double* zi, cudaStream_t s);
+// Storage tier B: the same encoding up to the rounded integer coefficients, out_int [nd][N].
+void launch_encode_diags_int(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,
+                             void* zbuf, long long* out_int, int scale_bits, const unsigned* rot, const double* zr,
+                             const double* zi, cudaStream_t s);
+// Residues of stored integer coefficients: m [nd][N] -> out [nd][nl][N] (coefficient form).
+void launch_coef_residues(const long long* m, int nd, u64* out, int nl, const DevPrime* primes, int N,
+                          cudaStream_t s);

@@ -119,7 +119,7 @@ struct fr_ctx {
     uint64_t launches = 0;
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
-    uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query
+    uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query, 3 stored coefficients
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
     Server* server = nullptr;            // continuous-batching loop (fr_match_submit / fr_match_poll)
@@ -153,10 +153,13 @@ struct fr_db {
     long long K = 0;
     int ell = 0;
     long long G = 0;
-    int tier = 1;            // 1: pre-rotated diagonals stored in HBM; 2: encoded per query from templates
+    int tier = 1;            // 1 (A): pre-rotated diagonals stored in HBM (evaluation form, every limb);
+                             // 2 (C): encoded per query from the FP32 templates;
+                             // 3 (B): rounded integer coefficients stored, residues + NTT per query
     int schedule = 0;        // 0: on-demand BSGS (diagonals pre-rotated by j n1); 1: rotated-query table (plain diagonals)
     u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]
     float* templates = nullptr;  // tier 2: [K][ell] FP32
+    long long* coeffs = nullptr; // tier 3: [G][ell][N] integer coefficients of the diagonals
     size_t bytes = 0;
 };
 
@@ -686,6 +689,42 @@ fr_ct* new_dev_ct(fr_ctx* c, std::shared_ptr<DevBlock> blk, u64* p, int level, i
     ct->dev = p;
     return ct;
 }
+// Storage tier B: the rounded integer coefficients [ell][N] of group g's diagonals (same
+// encoding as encode_group up to the rounding).
+void encode_group_int(fr_ctx* c, const float* dT, long long K, long long g, long long* dst, int n1_enc) {
+    const int N = c->R.N, n = N / 2, ell = (int)c->ell;
+    const int chunk = 64;
+    Tmp z(c, (size_t)chunk * n * 2);
+    for (int d0 = 0; d0 < ell; d0 += chunk) {
+        const int nd = std::min(chunk, ell - d0);
+        Prof p(c, "encode", 8.0 * N * nd);
+        launch_encode_diags_int(dT, K, ell, c->R.logN - 1, g, d0, nd, n1_enc, z.p, dst + (size_t)d0 * N,
+                                c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->cur);
+        c->launches += 4;
+    }
+}
+
+// Storage tier B, per query: residues of the stored coefficients at the working level, then
+// the forward NTT with the Montgomery conversion: dst [ell][level+1][N] as encode_group writes.
+void expand_group(fr_ctx* c, const long long* src, u64* dst) {
+    const int N = c->R.N, nl = c->work_level + 1, ell = (int)c->ell;
+    const int chunk = 64;
+    const PrimeMap pm = pm_level(nl - 1);
+    for (int d0 = 0; d0 < ell; d0 += chunk) {
+        const int nd = std::min(chunk, ell - d0);
+        u64* o = dst + (size_t)d0 * nl * N;
+        {
+            Prof p(c, "encode", 8.0 * N * nd * (1.0 + nl));
+            launch_coef_residues(src + (size_t)d0 * N, nd, o, nl, c->d_primes, N, c->cur);
+            c->launches++;
+        }
+        Prof p(c, "ntt", 16.0 * nd * nl * N);
+        PolyBatch pb{o, (long long)nl * N, nl, nd * nl, pm};
+        launch_ntt_tomont(c->rd, pb, c->cur);
+        c->launches += 2;
+    }
+}
+
 std::shared_ptr<DevBlock> new_block(fr_ctx* c, size_t words) { return std::make_shared<DevBlock>(c, dalloc(c, words)); }
 
 // device copy of a ciphertext (evaluation form) with limbs 0..level (level < 0: all);
@@ -937,7 +976,7 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         }
         c->host_threads = std::max(1u, std::thread::hardware_concurrency());
         if (prm->level_mode > 1) raise(FR_ERR_INVALID_ARG, "level_mode must be 0 or 1");
-        if (prm->db_tier > 2) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1 or 2");
+        if (prm->db_tier > 3) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1, 2 or 3");
         c->db_tier = prm->db_tier;
         c->work_level = c->R.nq - 1;
         if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->d2 : 0));
@@ -1109,33 +1148,43 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
         db->schedule = choose_schedule(c, db->G);
         const size_t tbytes = K * ell * sizeof(float);
         const size_t dbytes = (size_t)db->G * ell * nl * N * 8;
-        // storage tier: the stored diagonals when they fit (budget, or free HBM minus a
-        // working margin of 2 groups of diagonals), else the templates and a per-query encode
+        // storage tier: the stored diagonals when they fit (budget, or free HBM minus a working
+        // margin of 2 groups of diagonals), else the stored integer coefficients, else the
+        // templates and a per-query encode
+        const size_t ibytes = (size_t)db->G * ell * N * 8;
         int tier = (int)c->db_tier;
         if (tier == 0) {
             size_t free_b = 0, total_b = 0;
             CU(cudaMemGetInfo(&free_b, &total_b));
             const size_t margin = (size_t)2 * ell * nl * N * 8 + ((size_t)4 << 30);
-            const bool fits = c->budget ? c->resident + dbytes <= c->budget : dbytes + margin <= free_b;
-            tier = fits ? 1 : 2;
+            auto fits = [&](size_t b) { return c->budget ? c->resident + b <= c->budget : b + margin <= free_b; };
+            tier = fits(dbytes) ? 1 : fits(ibytes) ? 3 : 2;
         }
         db->tier = tier;
-        db->bytes = tier == 1 ? dbytes : tbytes;
+        db->bytes = tier == 1 ? dbytes : tier == 3 ? ibytes : tbytes;
         if (c->budget && c->resident + db->bytes > c->budget)
             raise(FR_ERR_HBM_BUDGET, "database exceeds the HBM budget");
         float* dT = nullptr;
         CU(cudaMalloc(&dT, tbytes));
         CU(cudaMemcpyAsync(dT, templates, tbytes, cudaMemcpyHostToDevice, c->cur));
-        if (tier == 1) {
-            cudaError_t e = cudaMalloc(&db->diags, dbytes);
+        if (tier == 1 || tier == 3) {
+            void* p = nullptr;
+            cudaError_t e = cudaMalloc(&p, tier == 1 ? dbytes : ibytes);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 cudaFree(dT);
                 raise(e == cudaErrorMemoryAllocation ? FR_ERR_HBM_BUDGET : FR_ERR_CUDA,
                       std::string("cannot hold the database diagonals: ") + cudaGetErrorString(e));
             }
-            for (long long g = 0; g < db->G; ++g)
-                encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N, db_n1_enc(c, db.get()));
+            for (long long g = 0; g < db->G; ++g) {
+                if (tier == 1) {
+                    db->diags = (u64*)p;
+                    encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N, db_n1_enc(c, db.get()));
+                } else {
+                    db->coeffs = (long long*)p;
+                    encode_group_int(c, dT, (long long)K, g, db->coeffs + (size_t)g * ell * N, db_n1_enc(c, db.get()));
+                }
+            }
             CU(cudaStreamSynchronize(c->cur));
             CU(cudaFree(dT));
         } else {
@@ -1166,6 +1215,7 @@ void fr_free_db(fr_db* db) {
     }
     cudaFree(db->diags);
     cudaFree(db->templates);
+    cudaFree(db->coeffs);
     delete db;
 }
 
@@ -1483,12 +1533,16 @@ void ondemand_scores(fr_ctx* c, const fr_db* db, const u64* q, int B, u64* S) {
     // S3-S5 per group: (tier C: encode the group's diagonals), MAC, rescale, giant rotations, sum
     stage.reset();
     std::unique_ptr<Tmp> dg;
-    if (db->tier == 2) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
+    if (db->tier != 1) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
     for (long long g = 0; g < G; ++g) {
         const u64* D = db->diags + (size_t)g * ell * L1 * N;
         if (db->tier == 2) {
             stage.reset(new Prof(c, "stage:encode"));
             encode_group(c, db->templates, db->K, g, dg->p, (int)c->n1);
+            D = dg->p;
+        } else if (db->tier == 3) {
+            stage.reset(new Prof(c, "stage:encode"));
+            expand_group(c, db->coeffs + (size_t)g * ell * N, dg->p);
             D = dg->p;
         }
         stage.reset(new Prof(c, "stage:mac"));
@@ -1561,9 +1615,9 @@ void table_scores(fr_ctx* c, const fr_db* db, const u64* q, u64* S) {
     }
     keyswitch(c, L, reqs);
     // step 4: groups in chunks (tier C encodes a chunk of groups per pass)
-    const long long GC = db->tier == 2 ? std::min<long long>(G, 8) : G;
+    const long long GC = db->tier != 1 ? std::min<long long>(G, 8) : G;
     std::unique_ptr<Tmp> dg;
-    if (db->tier == 2) dg.reset(new Tmp(c, (size_t)GC * ell * L1 * N));
+    if (db->tier != 1) dg.reset(new Tmp(c, (size_t)GC * ell * L1 * N));
     for (long long g0 = 0; g0 < G; g0 += GC) {
         const int gc = (int)std::min<long long>(GC, G - g0);
         const u64* D = db->diags + (size_t)g0 * ell * L1 * N;
@@ -1571,6 +1625,11 @@ void table_scores(fr_ctx* c, const fr_db* db, const u64* q, u64* S) {
             stage.reset(new Prof(c, "stage:encode"));
             for (int t = 0; t < gc; ++t)
                 encode_group(c, db->templates, db->K, g0 + t, dg->p + (size_t)t * ell * L1 * N, ell);
+            D = dg->p;
+        } else if (db->tier == 3) {
+            stage.reset(new Prof(c, "stage:encode"));
+            for (int t = 0; t < gc; ++t)
+                expand_group(c, db->coeffs + (size_t)(g0 + t) * ell * N, dg->p + (size_t)t * ell * L1 * N);
             D = dg->p;
         }
         stage.reset(new Prof(c, "stage:mac"));
@@ -1822,7 +1881,7 @@ void match_workspace(const fr_ctx* c, const fr_db* db, fr_mode mode, uint64_t* b
     if (mode != FR_MODE_SCORES) per += G * 54.0 * cw;  // threshold: powers, leaves, tree temporaries
     double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N;  // key-switch scratch
     if (db->schedule == 1) b += ell * cw1 + G * cw1;
-    if (db->tier == 2) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
+    if (db->tier != 1) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
     *base = (uint64_t)(b * 8.0 * 1.25);
     *per_query = (uint64_t)(per * 8.0 * 1.25);
 }

@@ -238,13 +238,14 @@ def test_match_graph_replay_bit_exact(mid):
 
 @pytest.mark.parametrize("mode", [fr.FR_MODE_SCORES, fr.FR_MODE_MEMBERSHIP])
 def test_per_query_encoding_tier_matches_stored_diagonals(mode):
-    """Tier C: only the FP32 templates stay in HBM and every query encodes the pre-rotated
-    diagonals of each group on the device; the result equals the stored-diagonal tier and
-    the oracle, bit for bit (two groups, ragged tail)."""
+    """Tier C (2): only the FP32 templates stay in HBM and every query encodes the pre-rotated
+    diagonals of each group on the device; tier B (3): their rounded integer coefficients stay
+    and every query forms residues and NTTs. Each equals the stored-diagonal tier and the
+    oracle, bit for bit (two groups, ragged tail)."""
     c = W.CONFIGS["mid"]
     T, q, _ = W.workload("mid")
     outs = []
-    for tier in (1, 2):
+    for tier in (1, 2, 3):
         ctx = fr.Context(device=0, db_tier=tier, **W.ctx_params("mid"))
         keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed("mid"))
         ctx.load_keys(keys)

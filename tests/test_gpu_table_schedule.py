@@ -43,9 +43,10 @@ def test_table_scores_tiny():
     assert np.abs(ctx.decrypt(keys, out[0])[: len(s)] - s).max() < 1e-4
 
 
-@pytest.mark.parametrize("tier", [1, 2])
+@pytest.mark.parametrize("tier", [1, 2, 3])
 def test_table_scores_and_membership_mid(tier):
-    """Two groups with a ragged tail; tier 2 encodes the plain diagonals per query."""
+    """Two groups with a ragged tail; tier 2 encodes the plain diagonals per query, tier 3
+    expands their stored integer coefficients per query."""
     c, ctx, keys, T, q, oc, ok, qct, oq = setup("mid", 1, tier=tier)
     db = ctx.load_db(T)
     assert db.info()["schedule"] == 1 and db.info()["tier"] == tier and db.info()["groups"] == 2
