@@ -141,6 +141,9 @@ fr_status fr_load_keys(fr_ctx* ctx, const fr_keys* keys);
  * limbs of the context's working level (G * ell * (level+1) * N words). */
 fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, fr_db** out);
 
+/* Storage tier for the databases loaded from now on (as fr_params.db_tier: 0 auto, 1, 2, 3). */
+fr_status fr_set_db_tier(fr_ctx* ctx, uint32_t tier);
+
 /* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding, 3 stored
  * integer coefficients), its
  * number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule
@@ -168,6 +171,17 @@ fr_status fr_match(fr_ctx* ctx, const fr_db* db, const fr_ct* query, fr_mode mod
  * n_queries * (outputs per query) handles, query after query. */
 fr_status fr_match_batch(fr_ctx* ctx, const fr_db* db, const fr_ct* const* queries, size_t n_queries, fr_mode mode,
                          fr_ct*** out, size_t* n_out);
+
+/* Encrypted match of n_queries (1..64) queries, query b against database dbs[b] (configuration
+ * "batched launches": many queries against databases of uneven sizes). The baby steps of all
+ * queries run as one batch and the giant rotations of each group index as one batch (every
+ * rotation key read once per batch); each query's diagonals are multiplied in its own MAC, and
+ * a database encoded per query (tiers 2, 3) is encoded once per group for all its queries. The
+ * threshold runs on all score ciphertexts at once. Outputs: query after query, G_b each (1 for
+ * membership), each query's equal to fr_match's for it, bit for bit. Replayed as a CUDA graph
+ * from the second call with the same databases and mode. */
+fr_status fr_match_multi(fr_ctx* ctx, const fr_db* const* dbs, const fr_ct* const* queries, size_t n_queries,
+                         fr_mode mode, fr_ct*** out, size_t* n_out);
 
 /* ---- Serving loop (continuous batching) ------------------------------------------
  * The paper serves one query at a time (Section "Experimental setup"; the server side of

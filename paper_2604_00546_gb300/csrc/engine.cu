@@ -1504,21 +1504,33 @@ void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int*
     }
 }
 
-// S2-S5 by the on-demand schedule for B queries already in HBM (q: [B][2][L+1][N],
-// evaluation form, level = work level): scores S [B][G][2][L][N] at level L-1. Every
-// stage runs once for the B queries: one ModUp per query, key-grouped inner products,
-// one MAC pass over the diagonals.
-void ondemand_scores(fr_ctx* c, const fr_db* db, const u64* q, int B, u64* S) {
+// A batch: query b matches database dbs[b]; its score ciphertexts are S + soff[b] (in
+// ciphertexts of 2 L limb-polys), soff[B] the total.
+struct BatchPlan {
+    std::vector<const fr_db*> dbs;
+    std::vector<long long> soff;
+    explicit BatchPlan(const std::vector<const fr_db*>& d) : dbs(d), soff(d.size() + 1, 0) {
+        for (size_t b = 0; b < d.size(); ++b) soff[b + 1] = soff[b] + d[b]->G;
+    }
+};
+
+// S2-S5 by the on-demand schedule for the queries qs of a batch (q: [B][2][L+1][N], evaluation
+// form, level = work level): their scores at level L-1 into S per the plan. Every stage runs
+// once for these queries: one ModUp per query, key-grouped inner products; then group by group
+// (over the queries whose database has that group) one MAC per query, one rescale, the giant
+// rotations with each key read once, the sums. A database encoded per query (tiers B, C) is
+// encoded once per group for all its queries.
+void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vector<int>& qs, u64* S) {
     const int L = c->work_level;
     const int N = c->R.N, n1 = (int)c->n1, ell = (int)c->ell;
     const int n2 = (ell + n1 - 1) / n1;
-    const long long G = db->G;
     const int L1 = L + 1;
+    const int B = (int)qs.size();
     const size_t cw1 = (size_t)ctw(c, L1), cw = (size_t)ctw(c, L);
     // S2: baby steps B_{b,i} = Rot_i(q_b), hoisted per query
     std::unique_ptr<Prof> stage(new Prof(c, "stage:babies"));
     Tmp babies(c, (size_t)B * n1 * cw1);  // [B][n1][2][L1][N]
-    for (int b = 0; b < B; ++b) copy_d2d(c, babies.p + (size_t)b * n1 * cw1, q + (size_t)b * cw1, cw1);
+    for (int b = 0; b < B; ++b) copy_d2d(c, babies.p + (size_t)b * n1 * cw1, q + (size_t)qs[b] * cw1, cw1);
     if (n1 > 1) {
         std::vector<KSReq> reqs;
         for (int b = 0; b < B; ++b) {
@@ -1530,56 +1542,80 @@ void ondemand_scores(fr_ctx* c, const fr_db* db, const u64* q, int B, u64* S) {
         }
         keyswitch(c, L, reqs);
     }
-    // S3-S5 per group: (tier C: encode the group's diagonals), MAC, rescale, giant rotations, sum
+    // S3-S5 group by group: (tiers B, C: encode the group's diagonals), MAC, rescale, giant
+    // rotations, sum; at most 8 databases encoded per query in flight
     stage.reset();
-    std::unique_ptr<Tmp> dg;
-    if (db->tier != 1) dg.reset(new Tmp(c, (size_t)ell * L1 * N));
-    for (long long g = 0; g < G; ++g) {
-        const u64* D = db->diags + (size_t)g * ell * L1 * N;
-        if (db->tier == 2) {
-            stage.reset(new Prof(c, "stage:encode"));
-            encode_group(c, db->templates, db->K, g, dg->p, (int)c->n1);
-            D = dg->p;
-        } else if (db->tier == 3) {
-            stage.reset(new Prof(c, "stage:encode"));
-            expand_group(c, db->coeffs + (size_t)g * ell * N, dg->p);
-            D = dg->p;
-        }
-        stage.reset(new Prof(c, "stage:mac"));
-        Tmp Pj(c, (size_t)B * n2 * cw1);  // [B][n2][2][L1][N]
-        // one query per launch: the products dominate the diagonal reads, and a launch over
-        // 2-4 queries measured slower per query (1.73 ms for 2 vs 0.75 ms for 1 at level 8)
-        for (int b0 = 0; b0 < B; ++b0) {
-            const int nb = 1;
-            Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + nb * (2.0 * n1 + 2.0 * n2)));
-            launch_mac(babies.p + (size_t)b0 * n1 * cw1, (long long)n1 * cw1, L1, D, Pj.p + (size_t)b0 * n2 * cw1,
-                       (long long)n2 * cw1, L1, L1, n1, n2, ell, nb, c->d_primes, N, c->cur);
-            c->launches++;
-        }
-        Tmp Gs(c, (size_t)B * n2 * cw);  // [B][n2][2][L][N]
-        rescale(c, Pj.p, B * n2, L, L1, Gs.p, L);
-        stage.reset(new Prof(c, "stage:giants"));
-        if (n2 > 1) {
-            Tmp Pr(c, (size_t)B * n2 * cw);
-            copy_d2d(c, Pr.p, Gs.p, (size_t)B * n2 * cw);
-            std::vector<KSReq> reqs;
-            for (int j = 1; j < n2; ++j) {
-                const u64 gk = frh::galois_of_rotation(c->R, (long)j * n1);
-                const u64* key = rot_key(c, gk);
-                for (int b = 0; b < B; ++b) {
-                    const u64* src = Pr.p + ((size_t)b * n2 + j) * cw;
-                    reqs.push_back(KSReq{src + (size_t)L * N, key, (u32)gk, 1, src, L, Gs.p + ((size_t)b * n2 + j) * cw, L});
+    long long Gmax = 0;
+    for (int b = 0; b < B; ++b) Gmax = std::max(Gmax, P.dbs[qs[b]]->G);
+    for (long long g = 0; g < Gmax; ++g) {
+        std::vector<int> sel;  // positions in qs of the queries whose database has group g
+        for (int b = 0; b < B; ++b)
+            if (g < P.dbs[qs[b]]->G) sel.push_back(b);
+        for (size_t s0 = 0; s0 < sel.size();) {
+            std::vector<const fr_db*> enc;  // databases encoded for this chunk
+            size_t s1 = s0;
+            for (; s1 < sel.size(); ++s1) {
+                const fr_db* d = P.dbs[qs[sel[s1]]];
+                if (d->tier == 1 || std::find(enc.begin(), enc.end(), d) != enc.end()) continue;
+                if (enc.size() == 8) break;
+                enc.push_back(d);
+            }
+            const int nb = (int)(s1 - s0);
+            std::unique_ptr<Tmp> dg;
+            if (!enc.empty()) {
+                stage.reset(new Prof(c, "stage:encode"));
+                dg.reset(new Tmp(c, enc.size() * (size_t)ell * L1 * N));
+                for (size_t e = 0; e < enc.size(); ++e) {
+                    u64* dst = dg->p + e * (size_t)ell * L1 * N;
+                    if (enc[e]->tier == 2) encode_group(c, enc[e]->templates, enc[e]->K, g, dst, (int)c->n1);
+                    else expand_group(c, enc[e]->coeffs + (size_t)g * ell * N, dst);
                 }
             }
-            keyswitch(c, L - 1, reqs);
+            auto diag_of = [&](const fr_db* d) -> const u64* {
+                if (d->tier == 1) return d->diags + (size_t)g * ell * L1 * N;
+                const size_t e = std::find(enc.begin(), enc.end(), d) - enc.begin();
+                return dg->p + e * (size_t)ell * L1 * N;
+            };
+            stage.reset(new Prof(c, "stage:mac"));
+            Tmp Pj(c, (size_t)nb * n2 * cw1);  // [nb][n2][2][L1][N]
+            // one query per launch: the products dominate the diagonal reads, and a launch over
+            // 2-4 queries measured slower per query (1.73 ms for 2 vs 0.75 ms for 1 at level 8)
+            for (int t = 0; t < nb; ++t) {
+                const int b = sel[s0 + t];
+                Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
+                launch_mac(babies.p + (size_t)b * n1 * cw1, (long long)n1 * cw1, L1, diag_of(P.dbs[qs[b]]),
+                           Pj.p + (size_t)t * n2 * cw1, (long long)n2 * cw1, L1, L1, n1, n2, ell, 1, c->d_primes, N,
+                           c->cur);
+                c->launches++;
+            }
+            Tmp Gs(c, (size_t)nb * n2 * cw);  // [nb][n2][2][L][N]
+            rescale(c, Pj.p, nb * n2, L, L1, Gs.p, L);
+            stage.reset(new Prof(c, "stage:giants"));
+            if (n2 > 1) {
+                Tmp Pr(c, (size_t)nb * n2 * cw);
+                copy_d2d(c, Pr.p, Gs.p, (size_t)nb * n2 * cw);
+                std::vector<KSReq> reqs;
+                for (int j = 1; j < n2; ++j) {
+                    const u64 gk = frh::galois_of_rotation(c->R, (long)j * n1);
+                    const u64* key = rot_key(c, gk);
+                    for (int t = 0; t < nb; ++t) {
+                        const u64* src = Pr.p + ((size_t)t * n2 + j) * cw;
+                        reqs.push_back(KSReq{src + (size_t)L * N, key, (u32)gk, 1, src, L,
+                                             Gs.p + ((size_t)t * n2 + j) * cw, L});
+                    }
+                }
+                keyswitch(c, L - 1, reqs);
+            }
+            for (int t = 0; t < nb; ++t) {
+                const int b = sel[s0 + t];
+                Prof p(c, "misc", 8.0 * N * 2.0 * L * (n2 + 1));
+                launch_sum(Gs.p + (size_t)t * n2 * cw, L, cw, n2, S + ((size_t)P.soff[qs[b]] + g) * cw, L, L - 1,
+                           c->d_primes, N, c->cur);
+                c->launches++;
+            }
+            stage.reset();
+            s0 = s1;
         }
-        for (int b = 0; b < B; ++b) {
-            Prof p(c, "misc", 8.0 * N * 2.0 * L * (n2 + 1));
-            launch_sum(Gs.p + (size_t)b * n2 * cw, L, cw, n2, S + ((size_t)b * G + g) * cw, L, L - 1, c->d_primes, N,
-                       c->cur);
-            c->launches++;
-        }
-        stage.reset();
     }
 }
 
@@ -1647,20 +1683,23 @@ void table_scores(fr_ctx* c, const fr_db* db, const u64* q, u64* S) {
 }
 
 // The whole match for B queries already in HBM (q: [B][2][L+1][N], evaluation form,
-// level = work level); writes each query's output ciphertexts (cap = level + 1)
-// contiguously to out, query after query.
-void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mode, u64* out) {
+// level = work level), query b against dbs[b]; writes each query's output ciphertexts
+// (cap = level + 1) contiguously to out, query after query.
+void match_pipeline(fr_ctx* c, const std::vector<const fr_db*>& dbs, const u64* q, fr_mode mode, u64* out) {
     const int L = c->work_level, N = c->R.N;
-    const long long G = db->G;
+    const int B = (int)dbs.size();
+    const BatchPlan P(dbs);
+    const long long total = P.soff[B];
     const size_t cw1 = (size_t)ctw(c, L + 1), cw = (size_t)ctw(c, L);
     const bool scores_only = mode == FR_MODE_SCORES;
-    Tmp sbuf(c, scores_only ? 1 : (size_t)B * G * cw);
-    u64* S = scores_only ? out : sbuf.p;  // [B][G][2][L][N]
-    if (db->schedule == 1) {
-        for (int b = 0; b < B; ++b) table_scores(c, db, q + (size_t)b * cw1, S + (size_t)b * G * cw);
-    } else {
-        ondemand_scores(c, db, q, B, S);
+    Tmp sbuf(c, scores_only ? 1 : (size_t)total * cw);
+    u64* S = scores_only ? out : sbuf.p;  // scores of query b from S + soff[b] cw
+    std::vector<int> od;
+    for (int b = 0; b < B; ++b) {
+        if (dbs[b]->schedule == 1) table_scores(c, dbs[b], q + (size_t)b * cw1, S + (size_t)P.soff[b] * cw);
+        else od.push_back(b);
     }
+    if (!od.empty()) ondemand_scores(c, P, q, od, S);
     std::unique_ptr<Prof> stage;
     if (scores_only) return;
     // S6: Chebyshev threshold on every (query, group) score ciphertext (batched)
@@ -1668,21 +1707,28 @@ void match_pipeline(fr_ctx* c, const fr_db* db, const u64* q, int B, fr_mode mod
     const size_t cwo = (size_t)ctw(c, lo + 1);
     if (mode == FR_MODE_IDENTIFY) {
         stage.reset(new Prof(c, "stage:cheb"));
-        chebyshev(c, S, (int)(B * G), L - 1, L, out, lo + 1);
+        chebyshev(c, S, (int)total, L - 1, L, out, lo + 1);
         return;
     }
-    Tmp cbuf(c, (size_t)B * G * cwo);
+    Tmp cbuf(c, (size_t)total * cwo);
     stage.reset(new Prof(c, "stage:cheb"));
-    chebyshev(c, S, (int)(B * G), L - 1, L, cbuf.p, lo + 1);
-    // S7: per query, sum over groups, then RotateAndSum over all slots
+    chebyshev(c, S, (int)total, L - 1, L, cbuf.p, lo + 1);
+    // S7: per query, sum over its groups, then RotateAndSum over all slots
     stage.reset(new Prof(c, "stage:sum"));
     for (int b = 0; b < B; ++b) {
         Prof p(c, "misc");
-        launch_sum(cbuf.p + (size_t)b * G * cwo, lo + 1, cwo, (int)G, out + (size_t)b * cwo, lo + 1, lo, c->d_primes,
-                   N, c->cur);
+        launch_sum(cbuf.p + (size_t)P.soff[b] * cwo, lo + 1, cwo, (int)dbs[b]->G, out + (size_t)b * cwo, lo + 1, lo,
+                   c->d_primes, N, c->cur);
         c->launches++;
     }
     rotate_sum(c, out, lo + 1, lo, B);
+}
+
+// Number of output ciphertexts of a batch and the offset of each query's first output.
+long long match_outputs(const std::vector<const fr_db*>& dbs, fr_mode mode, std::vector<long long>& first) {
+    first.assign(dbs.size() + 1, 0);
+    for (size_t b = 0; b < dbs.size(); ++b) first[b + 1] = first[b] + (mode == FR_MODE_MEMBERSHIP ? 1 : dbs[b]->G);
+    return first.back();
 }
 
 }  // namespace
@@ -1698,12 +1744,14 @@ struct MatchGraph {
 
 namespace {
 std::mutex g_graph_mu;
-std::map<std::tuple<const fr_ctx*, const fr_db*, int, int>, MatchGraph> g_graphs;
+// key: context, the database of each query, mode
+std::map<std::tuple<const fr_ctx*, std::vector<const fr_db*>, int>, MatchGraph> g_graphs;
 
 void drop_graphs(const fr_ctx* c, const fr_db* db) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end();) {
-        if (std::get<0>(it->first) == c && (db == nullptr || std::get<1>(it->first) == db)) {
+        const auto& v = std::get<1>(it->first);
+        if (std::get<0>(it->first) == c && (db == nullptr || std::find(v.begin(), v.end(), db) != v.end())) {
             if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
             cudaFree(it->second.in);
             cudaFree(it->second.out);
@@ -1714,15 +1762,18 @@ void drop_graphs(const fr_ctx* c, const fr_db* db) {
     }
 }
 
-// B queries: validate, stage, run (eagerly, or as a CUDA graph from the second call with
-// the same context, database, mode and batch size on), return B * nout handles.
-void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int B, fr_mode mode, fr_ct*** out,
-                   size_t* n_out) {
+// B queries, query b against dbs[b]: validate, stage, run (eagerly, or as a CUDA graph from
+// the second call with the same context, databases and mode on), return the output handles,
+// query after query.
+void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct* const* queries, fr_mode mode,
+                   fr_ct*** out, size_t* n_out) {
     need_device(c);
     std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
-    if (!db || !queries || !out || !n_out || B < 1) raise(FR_ERR_INVALID_ARG, "null argument or empty batch");
-    if (db->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
+    const int B = (int)dbs.size();
+    if (!queries || !out || !n_out || B < 1) raise(FR_ERR_INVALID_ARG, "null argument or empty batch");
     for (int b = 0; b < B; ++b) {
+        if (!dbs[b]) raise(FR_ERR_INVALID_ARG, "null database");
+        if (dbs[b]->ctx != c) raise(FR_ERR_INVALID_ARG, "database belongs to another context");
         check_ct(c, queries[b]);
         if (queries[b]->level != c->R.nq - 1) raise(FR_ERR_LEVEL, "queries must be at the top level");
     }
@@ -1735,20 +1786,22 @@ void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int 
         raise(FR_ERR_INVALID_ARG, "unknown mode");
     CU(cudaSetDevice(c->device));
     const int L1 = L + 1;
-    int nout, lo;
-    match_shape(c, db, mode, &nout, &lo);
+    int nout0, lo;
+    match_shape(c, dbs[0], mode, &nout0, &lo);
+    std::vector<long long> first;
+    const long long tot = match_outputs(dbs, mode, first);
     const size_t ow = (size_t)ctw(c, lo + 1), iw = (size_t)ctw(c, L1);
-    auto oblk = new_block(c, (size_t)B * nout * ow);
+    auto oblk = new_block(c, (size_t)tot * ow);
     if (c->prof || !c->use_graphs) {
         Tmp q(c, (size_t)B * iw);
         for (int b = 0; b < B; ++b) to_device(c, queries[b], q.p + (size_t)b * iw, L1, L);
-        match_pipeline(c, db, q.p, B, mode, oblk->p);
+        match_pipeline(c, dbs, q.p, mode, oblk->p);
     } else {
         std::lock_guard<std::mutex> lock(g_graph_mu);
-        MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, db, (int)mode, B)];
+        MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, dbs, (int)mode)];
         if (!mg.in) {
             CU(cudaMalloc(&mg.in, (size_t)B * iw * 8));
-            CU(cudaMalloc(&mg.out, (size_t)B * nout * ow * 8));
+            CU(cudaMalloc(&mg.out, (size_t)tot * ow * 8));
         }
         for (int b = 0; b < B; ++b) to_device(c, queries[b], mg.in + (size_t)b * iw, L1, L);
         if (!mg.exec && mg.runs >= 1) {
@@ -1756,7 +1809,7 @@ void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int 
             cudaGraph_t graph;
             CU(cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
             try {
-                match_pipeline(c, db, mg.in, B, mode, mg.out);
+                match_pipeline(c, dbs, mg.in, mode, mg.out);
             } catch (...) {
                 cudaStreamEndCapture(c->cur, &graph);
                 throw;
@@ -1771,16 +1824,15 @@ void match_queries(fr_ctx* c, const fr_db* db, const fr_ct* const* queries, int 
             CU(cudaGraphLaunch(mg.exec, c->cur));
             c->launches += mg.kernels;
         } else {
-            match_pipeline(c, db, mg.in, B, mode, mg.out);
+            match_pipeline(c, dbs, mg.in, mode, mg.out);
         }
         mg.runs++;
-        copy_d2d(c, oblk->p, mg.out, (size_t)B * nout * ow);
+        copy_d2d(c, oblk->p, mg.out, (size_t)tot * ow);
     }
-    const size_t tot = (size_t)B * nout;
     fr_ct** arr = new fr_ct*[tot];
-    for (size_t i = 0; i < tot; ++i) arr[i] = new_dev_ct(c, oblk, oblk->p + i * ow, lo, lo + 1);
+    for (long long i = 0; i < tot; ++i) arr[i] = new_dev_ct(c, oblk, oblk->p + (size_t)i * ow, lo, lo + 1);
     *out = arr;
-    *n_out = tot;
+    *n_out = (size_t)tot;
 }
 
 void check_match_args(fr_ctx* c, const fr_db* db, const fr_ct* q, fr_mode mode) {
@@ -2004,7 +2056,7 @@ bool serve_admit(Server* S, std::unique_lock<std::mutex>& lk) {
         {
             Tmp q(c, (size_t)B * iw);
             for (int b = 0; b < B; ++b) to_device(c, &batch[b].q, q.p + (size_t)b * iw, L1, L);
-            match_pipeline(c, db, q.p, B, mode, oblk->p);
+            match_pipeline(c, std::vector<const fr_db*>(B, db), q.p, mode, oblk->p);
         }
         CU(cudaEventRecord(sl.ev, sl.s));
         sl.out = oblk;
@@ -2238,7 +2290,7 @@ fr_status fr_match(fr_ctx* c, const fr_db* db, const fr_ct* query, fr_mode mode,
     return guard([&] {
         if (!c) raise(FR_ERR_INVALID_ARG, "null context");
         const fr_ct* qs[1] = {query};
-        match_queries(c, db, qs, 1, mode, out, n_out);
+        match_queries(c, std::vector<const fr_db*>(1, db), qs, mode, out, n_out);
     });
 }
 
@@ -2247,7 +2299,17 @@ fr_status fr_match_batch(fr_ctx* c, const fr_db* db, const fr_ct* const* queries
     return guard([&] {
         if (!c) raise(FR_ERR_INVALID_ARG, "null context");
         if (n_queries > 64) raise(FR_ERR_INVALID_ARG, "at most 64 queries per batch");
-        match_queries(c, db, queries, (int)n_queries, mode, out, n_out);
+        match_queries(c, std::vector<const fr_db*>(n_queries, db), queries, mode, out, n_out);
+    });
+}
+
+fr_status fr_match_multi(fr_ctx* c, const fr_db* const* dbs, const fr_ct* const* queries, size_t n_queries,
+                         fr_mode mode, fr_ct*** out, size_t* n_out) {
+    return guard([&] {
+        if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+        if (!dbs) raise(FR_ERR_INVALID_ARG, "null argument");
+        if (n_queries > 64) raise(FR_ERR_INVALID_ARG, "at most 64 queries per batch");
+        match_queries(c, std::vector<const fr_db*>(dbs, dbs + n_queries), queries, mode, out, n_out);
     });
 }
 
@@ -2334,6 +2396,15 @@ fr_status fr_ntt_set_shapes(fr_ctx* c, const uint32_t* shapes) {
             if (shapes[b] >= FR_NTT_SHAPES) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..4");
         for (int b = 0; b < FR_NTT_BUCKETS; ++b) c->rd.ntt_shape[b] = (unsigned char)shapes[b];
         drop_graphs(c, nullptr);  // captured graphs hold the previous launch shapes
+    });
+}
+
+fr_status fr_set_db_tier(fr_ctx* c, uint32_t tier) {
+    return guard([&] {
+        need_device(c);
+        if (tier > 3) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1, 2 or 3");
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        c->db_tier = tier;
     });
 }
 

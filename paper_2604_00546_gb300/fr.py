@@ -29,7 +29,7 @@ FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
 
 EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
-    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_decrypt", "fr_ct_export", "fr_ct_import",
+    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
@@ -94,6 +94,9 @@ def load(build_if_missing: bool = True):
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_match": (st, [vp, vp, vp, C.c_int, C.POINTER(C.POINTER(vp)), C.POINTER(C.c_size_t)]),
         "fr_match_batch": (st, [vp, vp, C.POINTER(vp), C.c_size_t, C.c_int, C.POINTER(C.POINTER(vp)),
+                                C.POINTER(C.c_size_t)]),
+        "fr_set_db_tier": (st, [vp, C.c_uint32]),
+        "fr_match_multi": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.c_size_t, C.c_int, C.POINTER(C.POINTER(vp)),
                                 C.POINTER(C.c_size_t)]),
         "fr_decrypt": (st, [vp, vp, vp, f64p, C.c_size_t]),
         "fr_ct_export": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_uint32), C.POINTER(C.c_double)]),
@@ -250,7 +253,11 @@ class Context:
     def load_keys(self, keys):
         _check(_lib.fr_load_keys(self.h, keys.h))
 
-    def load_db(self, templates):
+    def load_db(self, templates, tier=None):
+        """Upload a template database; tier (0 auto, 1, 2, 3) sets the storage tier for this
+        and later loads."""
+        if tier is not None:
+            _check(_lib.fr_set_db_tier(self.h, int(tier)))
         T = np.ascontiguousarray(templates, dtype=np.float32)
         h = C.c_void_p()
         _check(_lib.fr_load_db(self.h, T, T.shape[0], T.shape[1], C.byref(h)))
@@ -348,6 +355,22 @@ class Context:
         a, b, p, m = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
         _check(_lib.fr_serve_stats(self.h, C.byref(a), C.byref(b), C.byref(p), C.byref(m)))
         return dict(completed=a.value, batches=b.value, outstanding=p.value, max_concurrent_batches=m.value)
+
+    def match_multi(self, dbs, queries, mode):
+        """Query b against database dbs[b], all in one pass; one list of outputs per query."""
+        arr = C.POINTER(C.c_void_p)()
+        n = C.c_size_t()
+        hq = (C.c_void_p * len(queries))(*[q.h.value for q in queries])
+        hd = (C.c_void_p * len(dbs))(*[d.h.value for d in dbs])
+        _check(_lib.fr_match_multi(self.h, hd, hq, len(queries), int(mode), C.byref(arr), C.byref(n)))
+        cts = [Ciphertext(self, C.c_void_p(arr[i])) for i in range(n.value)]
+        _lib.fr_free_cts(arr, 0)
+        out, i = [], 0
+        for d in dbs:
+            k = 1 if int(mode) == FR_MODE_MEMBERSHIP else d.info()["groups"]
+            out.append(cts[i:i + k])
+            i += k
+        return out
 
     def _unary(self, fn, ct):
         h = C.c_void_p()
