@@ -317,6 +317,10 @@ uint32_t fr_work_level(const fr_ctx* ctx);
 /* Chebyshev coefficients c_0..c_n of the step interpolant (host, no context). */
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out);
 
+/* Release handles. Free a context's ciphertexts before the context: a device ciphertext
+ * returns its memory through it. A database may outlive its context: fr_free releases the
+ * database's device memory, and fr_free_db then only releases the handle. Keys do not depend
+ * on a context. */
 void fr_free_ct(fr_ct* ct);
 void fr_free_cts(fr_ct** cts, size_t n);
 void fr_free_keys(fr_keys* keys);

@@ -121,6 +121,7 @@ struct fr_ctx {
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query, 3 stored coefficients
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
+    std::set<fr_db*> dbs;                // databases loaded and not yet freed
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
     Server* server = nullptr;            // continuous-batching loop (fr_match_submit / fr_match_poll)
 };
@@ -1027,6 +1028,15 @@ void fr_free(fr_ctx* c) {
     cudaStreamSynchronize(c->stream);
     cudaStreamSynchronize(c->side);
     drop_graphs(c, nullptr);
+    for (fr_db* db : c->dbs) {  // databases still alive keep their handle, not their memory
+        cudaFree(db->diags);
+        cudaFree(db->templates);
+        cudaFree(db->coeffs);
+        db->diags = nullptr;
+        db->templates = nullptr;
+        db->coeffs = nullptr;
+        db->ctx = nullptr;
+    }
     for (auto& kv : c->rotkeys) cudaFree(kv.second);
     if (c->relin) cudaFree(c->relin);
     for (void* p : c->owned) cudaFree(p);
@@ -1192,6 +1202,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
             CU(cudaStreamSynchronize(c->cur));
         }
         c->resident += db->bytes;
+        c->dbs.insert(db.get());
         *out = db.release();
     });
 }
@@ -1207,6 +1218,11 @@ fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t
 
 void fr_free_db(fr_db* db) {
     if (!db) return;
+    if (!db->ctx) {  // its context was freed first, with the device memory
+        delete db;
+        return;
+    }
+    db->ctx->dbs.erase(db);
     if (db->ctx) serve_drain_db(db->ctx, db);
     if (db->ctx) drop_graphs(db->ctx, db);
     if (db->ctx) {

@@ -158,18 +158,37 @@ def _check(status):
 # ---------------------------------------------------------------------------
 # object layer
 # ---------------------------------------------------------------------------
-class Ciphertext:
+class _Handle:
+    """A library object owned by a context. The context is freed only after every object it owns
+    (a finaliser order Python does not guarantee for objects collected in one reference cycle)."""
+
+    def _register(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+        self._live = True
+        ctx._live += 1
+
+    def _release(self, free_fn):
+        if not getattr(self, "_live", False):
+            return
+        self._live = False
+        try:
+            if self.h is not None and self.h.value and _lib is not None and self.ctx.h is not None:
+                free_fn(self.h)
+        finally:
+            self.h = None
+            self.ctx._dep_freed()
+
+
+class Ciphertext(_Handle):
     """Library-owned ciphertext handle."""
 
     def __init__(self, ctx, handle):
-        self.ctx = ctx
-        self.h = C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle
+        self._register(ctx, C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle)
 
     def __del__(self):
         try:
-            if self.h and self.h.value and _lib is not None:
-                _lib.fr_free_ct(self.h)
-                self.h = None
+            self._release(_lib.fr_free_ct)
         except Exception:
             pass
 
@@ -206,6 +225,8 @@ class Context:
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
                              C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode)
         h = C.c_void_p()
+        self._live = 0          # library objects of this context still alive
+        self._closing = False
         _check(L.fr_setup(C.byref(self.params), C.byref(h)))
         self.h = h
         self.N = 1 << log_n
@@ -217,9 +238,20 @@ class Context:
         self.work_level = int(L.fr_work_level(self.h))
 
     def close(self):
-        if getattr(self, "h", None) and self.h.value:
+        """Free the context once every object it owns is freed (now, if none is left)."""
+        self._closing = True
+        if getattr(self, "_live", 0) == 0:
+            self._free_now()
+
+    def _dep_freed(self):
+        self._live -= 1
+        if self._closing and self._live == 0:
+            self._free_now()
+
+    def _free_now(self):
+        if getattr(self, "h", None) is not None and self.h.value:
             _lib.fr_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -426,24 +458,20 @@ class Context:
         return int(_lib.fr_launch_count(self.h))
 
 
-class Keys:
+class Keys(_Handle):
     def __init__(self, ctx, h):
-        self.ctx = ctx
-        self.h = h
+        self._register(ctx, h)
 
     def __del__(self):
         try:
-            if self.h and self.h.value and _lib is not None:
-                _lib.fr_free_keys(self.h)
-                self.h = None
+            self._release(_lib.fr_free_keys)
         except Exception:
             pass
 
 
-class Database:
+class Database(_Handle):
     def __init__(self, ctx, h, K):
-        self.ctx = ctx
-        self.h = h
+        self._register(ctx, h)
         self.K = K
 
     def info(self):
@@ -453,9 +481,7 @@ class Database:
 
     def __del__(self):
         try:
-            if self.h and self.h.value and _lib is not None:
-                _lib.fr_free_db(self.h)
-                self.h = None
+            self._release(_lib.fr_free_db)
         except Exception:
             pass
 
