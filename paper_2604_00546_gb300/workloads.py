@@ -149,3 +149,16 @@ def serving_queries(n_queries=16, ell=512, seed=SERVING_SEED + 100):
     rng = np.random.default_rng(seed)
     return [unit(rng, ell) for _ in range(n_queries)]
 
+
+# Batched launches: 64 queries against 64 databases of uneven sizes, K_d = round(2^U(10, 17)).
+MULTI_SEED = 0x3A7C0000
+
+
+def multi_sizes(n=64, seed=MULTI_SEED):
+    rng = np.random.default_rng(seed)
+    return [int(round(2.0 ** rng.uniform(10, 17))) for _ in range(n)]
+
+
+def multi_database(d, K, ell=512, seed=MULTI_SEED):
+    return templates(K, ell, seed + 1 + d)
+
