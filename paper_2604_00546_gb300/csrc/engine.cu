@@ -1814,7 +1814,27 @@ void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct*
         match_pipeline(c, dbs, q.p, mode, oblk->p);
     } else {
         std::lock_guard<std::mutex> lock(g_graph_mu);
-        MatchGraph& mg = g_graphs[std::make_tuple((const fr_ctx*)c, dbs, (int)mode)];
+        const auto key = std::make_tuple((const fr_ctx*)c, dbs, (int)mode);
+        if (!g_graphs.count(key)) {
+            // at most kMaxGraphs graphs per context (each holds the workspace of its batch):
+            // drop the least used one first
+            constexpr size_t kMaxGraphs = 16;
+            size_t mine = 0;
+            auto victim = g_graphs.end();
+            for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+                if (std::get<0>(it->first) != c) continue;
+                ++mine;
+                if (victim == g_graphs.end() || it->second.runs < victim->second.runs) victim = it;
+            }
+            if (mine >= kMaxGraphs && victim != g_graphs.end()) {
+                CU(cudaStreamSynchronize(c->cur));
+                if (victim->second.exec) cudaGraphExecDestroy(victim->second.exec);
+                cudaFree(victim->second.in);
+                cudaFree(victim->second.out);
+                g_graphs.erase(victim);
+            }
+        }
+        MatchGraph& mg = g_graphs[key];
         if (!mg.in) {
             CU(cudaMalloc(&mg.in, (size_t)B * iw * 8));
             CU(cudaMalloc(&mg.out, (size_t)tot * ow * 8));
