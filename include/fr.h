@@ -255,6 +255,14 @@ fr_status fr_chebyshev(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 /* RotateAndSum over all N/2 slots */
 fr_status fr_rotate_sum(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 
+/* Membership aggregation over parts (Algorithm 5's tail; block-sharded matching): the mod-q
+ * sum of the n ciphertexts in parts[] (all at one level), then RotateAndSum over all N/2 slots.
+ * Given the FR_MODE_IDENTIFY outputs of every template group of a database -- for example
+ * gathered from processes that each hold a range of the groups -- the result is bit-identical to
+ * FR_MODE_MEMBERSHIP on the whole database. parts stay owned by the caller; *out is a new
+ * handle. FR_ERR_INVALID_ARG for n == 0 or null pointers, FR_ERR_LEVEL for mixed levels. */
+fr_status fr_membership_reduce(fr_ctx* ctx, const fr_ct* const* parts, size_t n, fr_ct** out);
+
 /* Rotation by k slots that allocates no device memory (the paper has no counterpart:
  * this is a deployment variant of fr_rotate). For callers that must not allocate
  * while they run -- code captured into a CUDA graph with a fixed memory plan, a

@@ -1484,6 +1484,33 @@ fr_status fr_chebyshev(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
     });
 }
 
+// Membership tail over threshold ciphertexts that come from several places (the groups of a
+// database split across processes): the mod-q sum of all parts, then RotateAndSum over all slots
+// (Algorithm 5's aggregation). Parts must share one level. With the FR_MODE_IDENTIFY outputs of
+// every group as parts, the result equals FR_MODE_MEMBERSHIP on the whole database bit for bit:
+// the sum is exact and independent of the order of its terms.
+fr_status fr_membership_reduce(fr_ctx* c, const fr_ct* const* parts, size_t n, fr_ct** out) {
+    return guard([&] {
+        need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        if (!parts || !out || n == 0) raise(FR_ERR_INVALID_ARG, "null argument or no parts");
+        for (size_t i = 0; i < n; ++i) {
+            check_ct(c, parts[i]);
+            if (parts[i]->level != parts[0]->level) raise(FR_ERR_LEVEL, "parts at different levels");
+        }
+        CU(cudaSetDevice(c->device));
+        const int l = parts[0]->level, L1 = l + 1;
+        const size_t cw = (size_t)ctw(c, L1);
+        Tmp stage(c, n * cw);
+        for (size_t i = 0; i < n; ++i) to_device(c, parts[i], stage.p + i * cw, L1);
+        auto blk = new_block(c, cw);
+        launch_sum(stage.p, L1, (long long)cw, (int)n, blk->p, L1, l, c->d_primes, c->R.N, c->cur);
+        c->launches++;
+        rotate_sum(c, blk->p, L1, l);
+        *out = new_dev_ct(c, blk, blk->p, l, L1);
+    });
+}
+
 fr_status fr_rotate_sum(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
     return guard([&] {
         need_device(c);

@@ -31,7 +31,7 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_ntt_tuning", "fr_ntt_set_shapes",
+    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
     "fr_serve_stats", "fr_serve_plan",
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "fr_add": (st, [vp, vp, vp, C.POINTER(vp)]),
         "fr_chebyshev": (st, [vp, vp, C.POINTER(vp)]),
         "fr_rotate_sum": (st, [vp, vp, C.POINTER(vp)]),
+        "fr_membership_reduce": (st, [vp, C.POINTER(vp), C.c_size_t, C.POINTER(vp)]),
         "fr_sync": (st, [vp]),
         "fr_profile": (st, [vp, C.c_int]),
         "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
@@ -432,6 +433,14 @@ class Context:
 
     def rotate_sum(self, ct):
         return self._unary(_lib.fr_rotate_sum, ct)
+
+    def membership_reduce(self, parts):
+        """Mod-q sum of threshold ciphertexts (one level), then RotateAndSum: the membership
+        result of the groups the parts came from."""
+        hs = (C.c_void_p * len(parts))(*[p.h.value for p in parts])
+        h = C.c_void_p()
+        _check(_lib.fr_membership_reduce(self.h, hs, len(parts), C.byref(h)))
+        return Ciphertext(self, h)
 
     def mul_relin(self, a, b):
         h = C.c_void_p()

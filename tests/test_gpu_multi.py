@@ -65,3 +65,24 @@ def test_multi_pair_matches_oracle(env):
     oq = ok.encrypt(np.tile(env["qv"][qi], oc.n // c["ell"]), 78)
     ref, _ = ok.match(oq, env["Ts"][di], c["ell"], c["n1"], fr.FR_MODE_MEMBERSHIP, 59, 0.5)
     assert np.array_equal(outs[1][0].export(), ref[0])
+
+
+def test_graph_cache_eviction_keeps_results(env):
+    """More distinct database lists than the per-context graph cache holds (16): every list is
+    matched twice (eager, then captured), the least used graphs are dropped, and a list whose
+    graph was dropped still gives the same outputs when it comes back."""
+    ctx, keys, dbs = env["ctx"], env["keys"], env["dbs"]
+    combos = [(i, j) for i in range(len(dbs)) for j in range(len(dbs)) if i != j]   # 20 lists
+    q = [ctx.encrypt(keys, env["qv"][0], 91), ctx.encrypt(keys, env["qv"][1], 92)]
+    first = {}
+    for i, j in combos:
+        for _ in range(2):
+            outs = ctx.match_multi([dbs[i], dbs[j]], q, fr.FR_MODE_SCORES)
+            got = [[o.export() for o in out] for out in outs]
+            if (i, j) in first:
+                assert all(np.array_equal(a, b) for x, y in zip(got, first[(i, j)]) for a, b in zip(x, y))
+            first[(i, j)] = got
+    for i, j in combos[:3]:   # dropped by now
+        outs = ctx.match_multi([dbs[i], dbs[j]], q, fr.FR_MODE_SCORES)
+        got = [[o.export() for o in out] for out in outs]
+        assert all(np.array_equal(a, b) for x, y in zip(got, first[(i, j)]) for a, b in zip(x, y))
