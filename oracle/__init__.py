@@ -124,6 +124,14 @@ def _declare(L):
                            C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_table_scores.restype = C.c_int
     L.or_table_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
+    L.or_encrypt_db.argtypes = [vp, vp, f32p, C.c_long, C.c_int, C.c_int, C.c_uint64, C.c_int, u64p]
+    L.or_enc_giant_step.restype = C.c_int
+    L.or_enc_giant_step.argtypes = [vp, vp, u64p, C.c_int, C.c_int, u64p, C.c_int, C.c_int, C.c_int, u64p]
+    L.or_enc_bsgs_scores.restype = C.c_int
+    L.or_enc_bsgs_scores.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, u64p]
+    L.or_match_enc.restype = C.c_int
+    L.or_match_enc.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
+                               C.c_double, u64p, C.POINTER(C.c_int)]
     L.or_set_threads.argtypes = [C.c_int]
     L.or_get_threads.restype = C.c_int
 
@@ -405,6 +413,49 @@ class Keys:
             raise ValueError("match failed")
         level = lvl.value
         w = 2 * (level + 1) * c.N          # output ciphertexts are packed back to back
+        return out[: cnt * w].reshape(cnt, 2, level + 1, c.N).copy(), level
+
+    # -- encrypted database (enroller-side pre-rotation, lazy relinearisation) ------------
+    def encrypt_db(self, T, ell, n1, seed, level=None):
+        """The G*ell encrypted pre-rotated diagonals [G][ell][2][level+1][N] (coefficient form)."""
+        c = self.ctx
+        level = c.top if level is None else int(level)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        K = T.shape[0]
+        G = (K + c.n - 1) // c.n
+        out = np.empty((G, ell, 2, level + 1, c.N), dtype=np.uint64)
+        self.L.or_encrypt_db(c.h, self.h, T, K, ell, n1, int(seed), level, out)
+        return out
+
+    def enc_scores(self, qct, E, n1, level=None):
+        """Scores at level-1 of a query ct at `level` (default: top) against encrypted diagonals E."""
+        c = self.ctx
+        level = c.top if level is None else level
+        E = np.ascontiguousarray(E, dtype=np.uint64)
+        G, ell, el = E.shape[0], E.shape[1], E.shape[3] - 1
+        out = np.empty((G, 2, level, c.N), dtype=np.uint64)
+        r = self.L.or_enc_bsgs_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, E, el, G, ell,
+                                      n1, out)
+        if r < 0:
+            raise ValueError("bad arguments")
+        return out
+
+    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None):
+        """Full match of a top-level query ct against encrypted diagonals E, at working level
+        `level` (default: top); returns (outputs, their level)."""
+        c = self.ctx
+        lq = c.top if level is None else int(level)
+        E = np.ascontiguousarray(E, dtype=np.uint64)
+        G, ell, el = E.shape[0], E.shape[1], E.shape[3] - 1
+        cnt = 1 if mode == MODE_MEMBERSHIP else G
+        out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)
+        lvl = C.c_int(0)
+        r = self.L.or_match_enc(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, E, el, int(K), ell,
+                                n1, mode, int(cheb_n), float(tau), out, C.byref(lvl))
+        if r < 0:
+            raise ValueError("match failed")
+        level = lvl.value
+        w = 2 * (level + 1) * c.N
         return out[: cnt * w].reshape(cnt, 2, level + 1, c.N).copy(), level
 
 

@@ -988,9 +988,26 @@ static const u64* relin_key(const or_ctx* c, or_keys* k) {
     return k->relin;
 }
 
-void or_mul_relin(const or_ctx* c, or_keys* k, const u64* a, const u64* b, int l, u64* out) {
+/* out (a ct [2][l+1][N], coefficient form) += KS_{s^2}(d2): the relinearisation of (d0,d1,d2)
+ * with (d0,d1) already in out */
+static void relin_add(const or_ctx* c, or_keys* k, const u64* d2, int l, u64* out) {
     int N = c->n, npos = l + 1 + c->np;
     int beta = beta_at(c, l);
+    const u64* rk = relin_key(c, k);
+    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * npos * N);
+    u64* acc0 = (u64*)malloc(sizeof(u64) * (size_t)npos * N);
+    u64* acc1 = (u64*)malloc(sizeof(u64) * (size_t)npos * N);
+    u64* ks = (u64*)malloc(sizeof(u64) * (size_t)2 * (l + 1) * N);
+    modup(c, d2, l, ext);
+    keyswitch_ip(c, ext, l, rk, 1, acc0, acc1);
+    moddown(c, acc0, l, ks);
+    moddown(c, acc1, l, ks + (size_t)(l + 1) * N);
+    or_add(c, out, ks, l, out);
+    free(ext); free(acc0); free(acc1); free(ks);
+}
+
+void or_mul_relin(const or_ctx* c, or_keys* k, const u64* a, const u64* b, int l, u64* out) {
+    int N = c->n;
     u64* d2 = (u64*)malloc(sizeof(u64) * (size_t)(l + 1) * N);
 #pragma omp parallel for schedule(dynamic)
     for (int i = 0; i <= l; i++) {
@@ -1013,17 +1030,8 @@ void or_mul_relin(const or_ctx* c, or_keys* k, const u64* a, const u64* b, int l
         ntt_inv(c, i, o0); ntt_inv(c, i, o1); ntt_inv(c, i, o2);
         free(A0); free(A1); free(B0); free(B1);
     }
-    const u64* rk = relin_key(c, k);
-    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * npos * N);
-    u64* acc0 = (u64*)malloc(sizeof(u64) * (size_t)npos * N);
-    u64* acc1 = (u64*)malloc(sizeof(u64) * (size_t)npos * N);
-    u64* ks = (u64*)malloc(sizeof(u64) * (size_t)2 * (l + 1) * N);
-    modup(c, d2, l, ext);
-    keyswitch_ip(c, ext, l, rk, 1, acc0, acc1);
-    moddown(c, acc0, l, ks);
-    moddown(c, acc1, l, ks + (size_t)(l + 1) * N);
-    or_add(c, out, ks, l, out);
-    free(d2); free(ext); free(acc0); free(acc1); free(ks);
+    relin_add(c, k, d2, l, out);
+    free(d2);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1402,6 +1410,37 @@ int or_table_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, co
     return (int)G;
 }
 
+/* Threshold and aggregation of the G score cts S [G][2][lq][N] at level lq-1 (Algorithm 5
+ * lines for the comparison and the sum, Algorithm 6 for identification): mode 1 writes the
+ * G cts p(S_k) at level lq-1-d2; mode 2 writes sum_k p(S_k) after RotateAndSum over all slots. */
+static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq, int mode, int cheb_n, double tau,
+                      u64* out, int* out_level) {
+    int n = c->n / 2;
+    int d1, d2;
+    or_ps_split(cheb_n, &d1, &d2);
+    if (d1 != 2 || lq - 1 - d2 < 0) return -1;
+    int lo = lq - 1 - d2;
+    size_t cwo = ct_words(c, lo);
+    if (mode == 1) {
+        for (long g = 0; g < G; g++)
+            or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, out + g * cwo);
+        *out_level = lo;
+        return (int)G;
+    }
+    u64* t = (u64*)malloc(sizeof(u64) * cwo);
+    memset(out, 0, sizeof(u64) * cwo);
+    for (long g = 0; g < G; g++) {
+        or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, t);
+        or_add(c, out, t, lo, out);
+    }
+    int steps = 0;
+    while ((1 << steps) < n) steps++;
+    or_rotate_sum(c, k, out, lo, steps);
+    *out_level = lo;
+    free(t);
+    return 1;
+}
+
 /* Full match (Algorithms 5 and 6). The top-level query is first dropped to the
  * working level lq (lq = top: the whole chain). schedule 0: on-demand BSGS with
  * pre-rotated diagonals; schedule 1: the rotated-query table of Algorithm 1. mode 0: scores (G cts, level
@@ -1425,33 +1464,147 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     int d1, d2;
     or_ps_split(cheb_n, &d1, &d2);
     if (d1 != 2 || lq - 1 - d2 < 0) { free(q); return -1; }
-    int lo = lq - 1 - d2;
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
     int rs = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, S)
                            : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);
-    size_t cwo = ct_words(c, lo);
-    if (mode == 1) {
-        for (long g = 0; g < G; g++)
-            or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, out + g * cwo);
-        *out_level = lo;
-        free(S);
-        return (int)G;
-    }
-    u64* t = (u64*)malloc(sizeof(u64) * cwo);
-    memset(out, 0, sizeof(u64) * cwo);
-    for (long g = 0; g < G; g++) {
-        or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, t);
-        or_add(c, out, t, lo, out);
-    }
-    int steps = 0;
-    while ((1 << steps) < n) steps++;
-    or_rotate_sum(c, k, out, lo, steps);
-    *out_level = lo;
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, out, out_level);
     free(S);
-    free(t);
-    return 1;
+    return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Encrypted database: the paper's own setting (Section "BSGS with pre-rotated */
+/* diagonals on GPU", with the pre-rotation done by the enroller on the       */
+/* plaintext before encryption, Section 5.3.3, and lazy relinearisation,      */
+/* Sections 4.1 and 5.2):                                                     */
+/*   enrollment: E_{k,d} = Enc(Rot_{-j n1}(diag_d(M_k))), d = j n1 + i         */
+/*   online, for group k and giant step j:                                     */
+/*     (d0,d1,d2) = sum_i B_i (x) E_{k, j n1 + i}  (tensor products summed)     */
+/*     P = Rescale((d0,d1) + KS_{s^2}(d2))         (one relinearisation)        */
+/*     S_k += Rot_{j n1}(P)   (P itself for j = 0)                             */
+/* ------------------------------------------------------------------------ */
+/* Enrollment of a K x ell template matrix: the G*ell diagonal cts, [G][ell][2][level+1][N]
+ * coefficient form. Diagonal d of group g is the pre-rotated plaintext diagonal
+ * (Eq. eq:prerotation, shift (d / n1) n1) encrypted at the top level with seed + g*ell + d
+ * and dropped to `level`. */
+void or_encrypt_db(const or_ctx* c, const or_keys* k, const float* T, long K, int ell, int n1, u64 seed, int level,
+                   u64* out) {
+    int N = c->n, n = N / 2, top = c->nq - 1;
+    long G = (K + n - 1) / n;
+    double* z = (double*)malloc(sizeof(double) * n);
+    u64* full = (u64*)malloc(sizeof(u64) * ct_words(c, top));
+    for (long g = 0; g < G; g++)
+        for (int d = 0; d < ell; d++) {
+            or_diag_slots(T, K, ell, n, g, d, (long)(d / n1) * n1, z);
+            or_encrypt(c, k, z, seed + (u64)(g * ell + d), full);
+            or_drop(c, full, top, level, out + (size_t)(g * ell + d) * ct_words(c, level));
+        }
+    free(z);
+    free(full);
+}
+
+/* One giant step j of group g with encrypted diagonals E ([ell][2][el+1][N] coefficient form,
+ * el >= L): babies in evaluation form [n1][2][L+1][N] at level L; P written at level L-1. */
+int or_enc_giant_step(const or_ctx* c, or_keys* k, const u64* babies, int L, int n1, const u64* E, int el, int ell,
+                      int j, u64* P) {
+    int N = c->n;
+    size_t cw = ct_words(c, L), ew = ct_words(c, el);
+    int cnt = (j * n1 + n1 <= ell) ? n1 : ell - j * n1;
+    if (cnt <= 0 || el < L) return -1;
+    u64* ev = (u64*)malloc(sizeof(u64) * cw * cnt);
+    for (int i = 0; i < cnt; i++) {
+        or_drop(c, E + (size_t)(j * n1 + i) * ew, el, L, ev + (size_t)i * cw);
+        ct_to_eval(c, ev + (size_t)i * cw, L, ev + (size_t)i * cw);
+    }
+    /* d = (d0, d1) followed by d2: [3][L+1][N] */
+    u64* d = (u64*)malloc(sizeof(u64) * (size_t)3 * (L + 1) * N);
+#pragma omp parallel for schedule(dynamic)
+    for (int li = 0; li <= L; li++) {
+        u64 q = c->p[li];
+        u64* o0 = d + (size_t)li * N;
+        u64* o1 = d + (size_t)(L + 1 + li) * N;
+        u64* o2 = d + (size_t)(2 * (L + 1) + li) * N;
+        for (int x = 0; x < N; x++) {
+            u64 s0 = 0, s1 = 0, s2 = 0;
+            for (int i = 0; i < cnt; i++) {
+                const u64* b = babies + (size_t)i * cw;
+                const u64* e = ev + (size_t)i * cw;
+                u64 b0 = b[(size_t)li * N + x], b1 = b[(size_t)(L + 1 + li) * N + x];
+                u64 e0 = e[(size_t)li * N + x], e1 = e[(size_t)(L + 1 + li) * N + x];
+                s0 = madd(s0, mmul(b0, e0, q), q);
+                s1 = madd(s1, madd(mmul(b0, e1, q), mmul(b1, e0, q), q), q);
+                s2 = madd(s2, mmul(b1, e1, q), q);
+            }
+            o0[x] = s0;
+            o1[x] = s1;
+            o2[x] = s2;
+        }
+        ntt_inv(c, li, o0);
+        ntt_inv(c, li, o1);
+        ntt_inv(c, li, o2);
+    }
+    relin_add(c, k, d + (size_t)2 * (L + 1) * N, L, d);
+    or_rescale(c, d, L, P);
+    free(ev);
+    free(d);
+    return 0;
+}
+
+/* On-demand BSGS over an encrypted database ([G][ell][2][el+1][N]); the query ct is at level L,
+ * scores come out at level L-1 ([G][2][L][N]). */
+int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const u64* E, int el, long G, int ell,
+                       int n1, u64* out) {
+    int n = c->n / 2;
+    if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1 || el < L) return -1;
+    int n2 = (ell + n1 - 1) / n1;
+    size_t cw = ct_words(c, L), cw1 = ct_words(c, L - 1), ew = ct_words(c, el);
+    long* rots = (long*)malloc(sizeof(long) * n1);
+    for (int i = 0; i < n1; i++) rots[i] = i;
+    u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
+    or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
+    for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
+    u64* P = (u64*)malloc(sizeof(u64) * cw1);
+    u64* R = (u64*)malloc(sizeof(u64) * cw1);
+    for (long g = 0; g < G; g++) {
+        u64* S = out + (size_t)g * cw1;
+        memset(S, 0, sizeof(u64) * cw1);
+        for (int j = 0; j < n2; j++) {
+            or_enc_giant_step(c, k, babies, L, n1, E + (size_t)g * ell * ew, el, ell, j, P);
+            if (j > 0) {
+                or_rotate(c, k, P, L - 1, (long)j * n1, R);
+                or_add(c, S, R, L - 1, S);
+            } else {
+                or_add(c, S, P, L - 1, S);
+            }
+        }
+    }
+    free(rots); free(babies); free(P); free(R);
+    return (int)G;
+}
+
+/* Full match against an encrypted database at level el (>= lq); modes as in or_match. */
+int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64* E, int el, long K, int ell, int n1,
+                 int mode, int cheb_n, double tau, u64* out, int* out_level) {
+    int top = c->nq - 1, n = c->n / 2;
+    if (lq < 1 || lq > top || el < lq) return -1;
+    long G = (K + n - 1) / n;
+    u64* q = (u64*)malloc(sizeof(u64) * ct_words(c, top));
+    or_drop(c, qct, top, lq, q);
+    if (mode == 0) {
+        int r = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, out);
+        *out_level = lq - 1;
+        free(q);
+        return r;
+    }
+    u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
+    int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, S);
+    free(q);
+    if (rs < 0) { free(S); return -1; }
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, out, out_level);
+    free(S);
+    return r;
 }
 
 void or_set_threads(int t) {

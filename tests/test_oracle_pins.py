@@ -590,3 +590,88 @@ def test_match_at_working_level_consistent():
     s = np.concatenate([T.astype(np.float64) @ q, np.zeros(c.n - K)])
     p = np.polynomial.chebyshev.chebval(s, oracle.cheb_coeffs(59, 0.5))
     assert abs(k.decrypt(memb[0], 1)[0] - p.sum()) < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# Encrypted database (enroller-side pre-rotation, Section 5.3.3; lazy relinearisation)
+# ---------------------------------------------------------------------------
+def test_encrypted_db_decrypts_to_prerotated_diagonals():
+    """Enrollment: each ciphertext decrypts to its diagonal rotated by -j n1 slots (Eq.
+    eq:prerotation applied to the plaintext), read straight from the templates."""
+    c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
+    k = c.keygen(90)
+    ell, n1, K = 16, 4, c.n + 70           # two groups, the second ragged
+    T = _templates(K, ell, 9)
+    E = k.encrypt_db(T, ell, n1, 500, level=1)
+    assert E.shape == (2, ell, 2, 2, c.N)
+    B = c.n // ell
+    for g, d in [(0, 0), (0, 5), (1, 11), (1, 15)]:
+        z = k.decrypt(E[g, d], 1)
+        shift = (d // n1) * n1
+        for x in range(0, c.n, 37):
+            y = (x - shift) % c.n
+            b, r = divmod(y, ell)
+            row = (g * B + b) * ell + r
+            ref = float(T[row, (r + d) % ell]) if row < K else 0.0
+            assert abs(z[x] - ref) < 1e-6
+    # the enroller encrypts at the top level and drops limbs: the low limbs are the top-level ones
+    top = k.encrypt_db(T[:c.n], ell, n1, 500)
+    assert np.array_equal(c.drop(top[0, 7], c.top, 1), E[0, 7])
+
+
+def test_encrypted_db_trivial_encryption_is_plaintext_path():
+    """With trivial encryptions (m, 0) of the pre-rotated diagonals, the c1 parts of the
+    tensor products and d2 vanish, the relinearisation adds KS(0) = 0, and the encrypted-database
+    scores equal the plaintext-database scores bit for bit."""
+    c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
+    k = c.keygen(91)
+    ell, n1, K = 16, 4, c.n + 70
+    T = _templates(K, ell, 10)
+    rng = np.random.default_rng(3)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k.encrypt(np.tile(q, c.n // ell), 6)
+    G = 2
+    E = np.zeros((G, ell, 2, c.top + 1, c.N), dtype=np.uint64)
+    for g in range(G):
+        for d in range(ell):
+            E[g, d, 0] = c.encode(oracle.diag_slots(T, ell, c.n, g, d, (d // n1) * n1))
+    got = k.enc_scores(qct, E, n1)
+    assert np.array_equal(got, k.bsgs_scores(qct, T, ell, n1))
+
+
+def test_encrypted_db_scores_and_match():
+    """Real encryptions: scores decrypt to the FP64 inner products; the threshold and the
+    membership sum follow them as in the plaintext-database match."""
+    c = oracle.Ctx(11, [60] + [40] * 8, [60, 60, 60], 3, 40)
+    k = c.keygen(92)
+    ell, n1, K = 32, 4, 700
+    T = _templates(K, ell, 11)
+    q = T[3].astype(np.float64)
+    rng = np.random.default_rng(16)
+    for idx in (10, 650):
+        u = rng.standard_normal(ell)
+        u -= (u @ q) * q
+        u /= np.linalg.norm(u)
+        T[idx] = (0.8 * q + 0.6 * u).astype(np.float32)
+    qct = k.encrypt(np.tile(q, c.n // ell), 9)
+    lq = 7
+    E = k.encrypt_db(T, ell, n1, 600, level=lq)
+    s = T.astype(np.float64) @ q
+    S, lvl = k.match_enc(qct, E, K, n1, oracle.MODE_SCORES, level=lq)
+    assert lvl == lq - 1
+    got = k.decrypt(S[0], lvl)
+    assert np.abs(got[:K] - s).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+    # not the plaintext path's bits (another product), the same values
+    Sp, _ = k.match(qct, T, ell, n1, oracle.MODE_SCORES, level=lq)
+    assert not np.array_equal(S, Sp)
+    p = np.polynomial.chebyshev.chebval(np.concatenate([s, np.zeros(c.n - K)]), oracle.cheb_coeffs(59, 0.5))
+    ident, l1 = k.match_enc(qct, E, K, n1, oracle.MODE_IDENTIFY, level=lq)
+    assert l1 == lq - 1 - 6
+    gi = k.decrypt(ident[0], l1)
+    assert np.abs(gi - p).max() < 1e-2
+    far = np.abs(s - 0.5) > 0.02
+    assert np.array_equal((gi[:K] >= 0.5)[far], (s >= 0.5)[far])
+    memb, l2 = k.match_enc(qct, E, K, n1, oracle.MODE_MEMBERSHIP, level=lq)
+    assert l2 == l1
+    assert np.abs(k.decrypt(memb[0], l2) - p.sum()).max() < 1e-2
