@@ -144,9 +144,28 @@ fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, 
 /* Storage tier for the databases loaded from now on (as fr_params.db_tier: 0 auto, 1, 2, 3). */
 fr_status fr_set_db_tier(fr_ctx* ctx, uint32_t tier);
 
+/* Encrypted database (the paper's own setting, Section 5.3; the variant with enroller-side
+ * pre-rotation, Section 5.3.3). fr_encrypt_db is enroller (client) side and runs on the host:
+ * for the K x ell FP32 templates (row-major, K >= 1, ell = the context's ell) it writes the
+ * G * ell ciphertexts E_{g,d} = Enc_pk(Rot_{-j n1}(diag_d(M_g))), d = j n1 + i, g < G =
+ * ceil(K / (N/2)), each pre-rotated by the context's n1 and encrypted with seed + g*ell + d,
+ * to out in the export format ([G][ell][2][level+1][N] u64, coefficient form; words >=
+ * G*ell*2*(level+1)*N). The limbs 0..level are those of a top-level encryption with the
+ * same seed. Errors: FR_ERR_INVALID_ARG (null pointers, K = 0, ell, small buffer),
+ * FR_ERR_LEVEL (level >= number of Q primes). */
+fr_status fr_encrypt_db(const fr_ctx* ctx, const fr_keys* keys, const float* templates, size_t K, size_t ell,
+                        uint32_t level, uint64_t seed, uint64_t* out, size_t words);
+/* Server side: load the G * ell ciphertexts written by fr_encrypt_db (level >= the working
+ * level; the limbs above it are dropped) as a database of storage tier 4, resident in HBM in
+ * evaluation form. Matches against it take, per group and giant step j, the ct x ct products
+ * sum_i Rot_i(q) (x) E_{g, j n1 + i}, relinearise once (lazy relinearisation; the relinearisation
+ * key must be loaded), rescale and rotate by j n1; the threshold and the slot sum follow as for
+ * plaintext databases. Inputs are copied. Errors: FR_ERR_INVALID_ARG, FR_ERR_LEVEL,
+ * FR_ERR_FORMAT (a residue not below its prime), FR_ERR_HBM_BUDGET. */
+fr_status fr_load_db_encrypted(fr_ctx* ctx, const uint64_t* cts, size_t K, size_t ell, uint32_t level, fr_db** out);
+
 /* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding, 3 stored
- * integer coefficients), its
- * number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule
+ * integer coefficients, 4 encrypted diagonals), its number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule
  * its matches run (0 on demand, 1 table). Any out-pointer may be NULL. */
 fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes, uint32_t* schedule);
 

@@ -364,6 +364,84 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 }
 
 // ---------------------------------------------------------------------------
+// Encrypted-database MAC (ct x ct with lazy relinearisation, the paper's setting of
+// Section 5.3): for every giant step j, pointwise per limb,
+//   (d0, d1, d2)_j = sum_{i < n1, j n1 + i < ell} B_i (x) E_{j n1 + i}
+//   d0 += b0 e0,  d1 += b0 e1 + b1 e0,  d2 += b1 e1.
+// babies: [n1][2][cap_b][N] evaluation form; diags: [ell][2][nl][N] evaluation form in
+// Montgomery form, so one REDC of the sum gives it in plain form; out: [n2][3][cap_o][N].
+// Tiling as k_mac (babies of a point tile staged in shared memory as 30-bit halves, giant
+// steps over the thread rows). Diagonals go in batches of 4: d1 takes two products per
+// diagonal, and 8 products are what one 30-bit split sum holds without a carry step.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babies, int cap_b,
+                                                   const u64* __restrict__ diags, u64* __restrict__ out, int cap_o,
+                                                   int nl, int n1, int n2, int ell, int TP, int JG,
+                                                   const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ u64 sb[];  // [n1][2][TP]
+    const int pl = threadIdx.x % TP;
+    const int jg = threadIdx.x / TP;
+    const int k = blockIdx.x * TP + pl;
+    const int i = blockIdx.y;
+    const u64 q = primes[i].q, qinv = primes[i].qinv;
+    for (int e = threadIdx.x; e < n1 * 2 * TP; e += TP * JG) {
+        const int ib = e / (2 * TP), t = (e / TP) & 1, pp = e % TP;
+        sb[e] = split30(babies[((long long)ib * 2 + t) * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp]);
+    }
+    __syncthreads();
+    const long long dstride = 2LL * nl * N;  // one diagonal ciphertext
+    const long long cstride = (long long)nl * N;
+    for (int j = jg; j < n2; j += JG) {
+        const int cnt = min(n1, ell - j * n1);
+        const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
+        Acc128 a0{0, 0}, a1{0, 0}, a2{0, 0};
+        for (int i0 = 0; i0 < cnt; i0 += 4) {
+            Acc3 p0{0, 0, 0}, p1{0, 0, 0}, p2{0, 0, 0};
+            const u64* sq = sb + (size_t)i0 * 2 * TP + pl;
+            if (i0 + 4 <= cnt) {
+                u64 e0[4], e1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    e0[u] = __ldcs(D + u * dstride);
+                    e1[u] = __ldcs(D + u * dstride + cstride);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const u64 s0 = split30(e0[u]), s1 = split30(e1[u]);
+                    const u64 b0 = sq[u * 2 * TP], b1 = sq[u * 2 * TP + TP];
+                    mac30(p0, b0, s0);
+                    mac30(p1, b0, s1);
+                    mac30(p1, b1, s0);
+                    mac30(p2, b1, s1);
+                }
+            } else {
+                for (int u = 0; i0 + u < cnt; ++u) {
+                    const u64 s0 = split30(__ldcs(D + u * dstride)), s1 = split30(__ldcs(D + u * dstride + cstride));
+                    const u64 b0 = sq[u * 2 * TP], b1 = sq[u * 2 * TP + TP];
+                    mac30(p0, b0, s0);
+                    mac30(p1, b0, s1);
+                    mac30(p1, b1, s0);
+                    mac30(p2, b1, s1);
+                }
+            }
+            flush30(a0, p0);
+            flush30(a1, p1);
+            flush30(a2, p2);
+            fold(a0, q);
+            fold(a1, q);
+            fold(a2, q);
+            D += 4 * dstride;
+        }
+        u64* O = out + (long long)j * 3 * cap_o * N + (long long)i * N + k;
+        O[0] = redc(a0.hi, a0.lo, q, qinv);
+        O[(long long)cap_o * N] = redc(a1.hi, a1.lo, q, qinv);
+        O[2LL * cap_o * N] = redc(a2.hi, a2.lo, q, qinv);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Table-schedule MAC (Algorithm 1, step 4): S_g = sum_{m < ell} rotQ[m] (.) D_{g,m}
 // for GG groups per CTA column. One thread per evaluation point of one limb; the two
 // table words of a point are read once for the GG groups, the diagonal words streamed.
@@ -731,6 +809,24 @@ void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags
         case 4: launch_mac_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
         default: break;  // the engine splits larger batches
     }
+}
+
+void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
+                   const DevPrime* primes, int N, cudaStream_t s) {
+    // points per CTA: staged babies (n1 2 TP words) within 128 KiB; giant-step rows up to 512 threads
+    int TP = 128;
+    while (TP > 16 && (size_t)n1 * 2 * TP * 8 > (128u << 10)) TP >>= 1;
+    int JG = 512 / TP;
+    if (JG > n2) JG = n2;
+    if (JG < 1) JG = 1;
+    const size_t sm = (size_t)n1 * 2 * TP * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mac_ct, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 g(N / TP, nl);
+    launch_k(k_mac_ct, dim3(g), dim3(TP * JG), sm, s, babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
 }
 
 void launch_mac_table(const u64* table, int cap_t, const u64* diags, long long dgrp, int G, u64* out, int cap_o,

@@ -103,6 +103,10 @@ void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out
                             int l, int N, int BT, cudaStream_t s);
 void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s);
 // B <= 4 queries: babies of query b at babies + b * baby_q, outputs at out + b * out_q
+// Encrypted-database MAC: (d0, d1, d2)_j = sum_i B_i (x) E_{j n1 + i} for every giant step j.
+// babies [n1][2][cap_b][N]; diags [ell][2][nl][N] (evaluation form, Montgomery); out [n2][3][cap_o][N].
+void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
+                   const DevPrime* primes, int N, cudaStream_t s);
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
                 int cap_o, int nl, int n1, int n2, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 // Table schedule (Algorithm 1): out_g = sum_{m < ell} table[m] (.) D_{g,m} for g < G (evaluation form,

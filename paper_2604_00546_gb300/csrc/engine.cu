@@ -156,9 +156,10 @@ struct fr_db {
     long long G = 0;
     int tier = 1;            // 1 (A): pre-rotated diagonals stored in HBM (evaluation form, every limb);
                              // 2 (C): encoded per query from the FP32 templates;
-                             // 3 (B): rounded integer coefficients stored, residues + NTT per query
+                             // 3 (B): rounded integer coefficients stored, residues + NTT per query;
+                             // 4 (E): encrypted pre-rotated diagonals (ciphertexts, evaluation form)
     int schedule = 0;        // 0: on-demand BSGS (diagonals pre-rotated by j n1); 1: rotated-query table (plain diagonals)
-    u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]
+    u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]; tier 4: [G][ell][2][level+1][N] (Montgomery form)
     float* templates = nullptr;  // tier 2: [K][ell] FP32
     long long* coeffs = nullptr; // tier 3: [G][ell][N] integer coefficients of the diagonals
     size_t bytes = 0;
@@ -1207,6 +1208,74 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
     });
 }
 
+fr_status fr_encrypt_db(const fr_ctx* c, const fr_keys* k, const float* templates, size_t K, size_t ell,
+                        uint32_t level, uint64_t seed, uint64_t* out, size_t words) {
+    return guard([&] {
+        if (!c || !k || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
+        if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
+        if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
+        const size_t N = c->R.N, n = N / 2, G = (K + n - 1) / n;
+        if (words < G * ell * 2 * (level + 1) * N) raise(FR_ERR_INVALID_ARG, "output buffer too small");
+        const int threads = std::max(1, (int)std::thread::hardware_concurrency());
+        frh::encrypt_diagonals(c->R, k->ks, templates, (long long)K, (int)ell, (int)c->n1, (int)level, seed, threads,
+                               out);
+    });
+}
+
+fr_status fr_load_db_encrypted(fr_ctx* c, const uint64_t* cts, size_t K, size_t ell, uint32_t level, fr_db** out) {
+    return guard([&] {
+        need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        if (!cts || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
+        if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
+        const int L = c->work_level, L1 = L + 1, N = c->R.N, n = N / 2;
+        if ((int)level < L || (int)level >= c->R.nq)
+            raise(FR_ERR_LEVEL, "diagonal ciphertexts must be at or above the working level");
+        CU(cudaSetDevice(c->device));
+        std::unique_ptr<fr_db> db(new fr_db());
+        db->ctx = c;
+        db->K = (long long)K;
+        db->ell = (int)ell;
+        db->G = ((long long)K + n - 1) / n;
+        db->tier = 4;
+        db->schedule = 0;  // the stored diagonals are pre-rotated for the on-demand schedule
+        const size_t ncts = (size_t)db->G * ell, lw = (size_t)level + 1;
+        for (size_t e = 0; e < ncts; ++e)
+            for (int t = 0; t < 2; ++t)
+                for (int i = 0; i < L1; ++i) {
+                    const u64 q = c->R.primes[i];
+                    const uint64_t* p = cts + ((e * 2 + t) * lw + i) * N;
+                    for (int x = 0; x < N; ++x)
+                        if (p[x] >= q) raise(FR_ERR_FORMAT, "residue not below its prime");
+                }
+        db->bytes = ncts * 2 * L1 * (size_t)N * 8;
+        if (c->budget && c->resident + db->bytes > c->budget)
+            raise(FR_ERR_HBM_BUDGET, "database exceeds the HBM budget");
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, db->bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            raise(e == cudaErrorMemoryAllocation ? FR_ERR_HBM_BUDGET : FR_ERR_CUDA,
+                  std::string("cannot hold the encrypted diagonals: ") + cudaGetErrorString(e));
+        }
+        db->diags = (u64*)p;
+        // limbs 0..L of both components, 64 ciphertexts per copy; then NTT into Montgomery form
+        for (size_t e0 = 0; e0 < ncts; e0 += 64) {
+            const size_t ne = std::min<size_t>(64, ncts - e0);
+            u64* dst = db->diags + e0 * 2 * L1 * N;
+            CU(cudaMemcpy2DAsync(dst, (size_t)L1 * N * 8, cts + e0 * 2 * lw * N, lw * N * 8, (size_t)L1 * N * 8, 2 * ne,
+                                 cudaMemcpyHostToDevice, c->cur));
+            PolyBatch pb{dst, (long long)L1 * N, L1, (int)(2 * ne * L1), pm_level(L)};
+            launch_ntt_tomont(c->rd, pb, c->cur);
+            c->launches++;
+        }
+        CU(cudaStreamSynchronize(c->cur));
+        c->resident += db->bytes;
+        c->dbs.insert(db.get());
+        *out = db.release();
+    });
+}
+
 fr_status fr_db_info(const fr_db* db, uint32_t* tier, uint64_t* groups, uint64_t* bytes, uint32_t* schedule) {
     if (!db) return FR_ERR_INVALID_ARG;
     if (schedule) *schedule = (uint32_t)db->schedule;
@@ -1599,7 +1668,7 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             size_t s1 = s0;
             for (; s1 < sel.size(); ++s1) {
                 const fr_db* d = P.dbs[qs[sel[s1]]];
-                if (d->tier == 1 || std::find(enc.begin(), enc.end(), d) != enc.end()) continue;
+                if (d->tier == 1 || d->tier == 4 || std::find(enc.begin(), enc.end(), d) != enc.end()) continue;
                 if (enc.size() == 8) break;
                 enc.push_back(d);
             }
@@ -1616,6 +1685,7 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             }
             auto diag_of = [&](const fr_db* d) -> const u64* {
                 if (d->tier == 1) return d->diags + (size_t)g * ell * L1 * N;
+                if (d->tier == 4) return d->diags + (size_t)g * ell * 2 * L1 * N;
                 const size_t e = std::find(enc.begin(), enc.end(), d) - enc.begin();
                 return dg->p + e * (size_t)ell * L1 * N;
             };
@@ -1623,13 +1693,37 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             Tmp Pj(c, (size_t)nb * n2 * cw1);  // [nb][n2][2][L1][N]
             // one query per launch: the products dominate the diagonal reads, and a launch over
             // 2-4 queries measured slower per query (1.73 ms for 2 vs 0.75 ms for 1 at level 8)
-            for (int t = 0; t < nb; ++t) {
+            int nenc = 0;  // queries of the chunk against encrypted databases
+            for (int t = 0; t < nb; ++t) nenc += P.dbs[qs[sel[s0 + t]]]->tier == 4;
+            std::unique_ptr<Tmp> D3;  // their unrelinearised products, [nenc][n2][3][L1][N]
+            if (nenc) D3.reset(new Tmp(c, (size_t)nenc * n2 * 3 * L1 * N));
+            std::vector<KSReq> relin;
+            for (int t = 0, e = 0; t < nb; ++t) {
                 const int b = sel[s0 + t];
+                const fr_db* d = P.dbs[qs[b]];
+                if (d->tier == 4) {
+                    // ct x ct products summed per giant step; one relinearisation each (below)
+                    u64* o = D3->p + (size_t)e++ * n2 * 3 * L1 * N;
+                    Prof p(c, "mac", 8.0 * N * L1 * (2.0 * ell + 2.0 * n1 + 3.0 * n2));
+                    launch_mac_ct(babies.p + (size_t)b * n1 * cw1, L1, diag_of(d), o, L1, L1, n1, n2, ell, c->d_primes,
+                                  N, c->cur);
+                    c->launches++;
+                    for (int j = 0; j < n2; ++j) {
+                        const u64* dj = o + (size_t)j * 3 * L1 * N;
+                        relin.push_back(KSReq{dj + (size_t)2 * L1 * N, relin_key(c), 1u, 2, dj, L1,
+                                              Pj.p + ((size_t)t * n2 + j) * cw1, L1});
+                    }
+                    continue;
+                }
                 Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-                launch_mac(babies.p + (size_t)b * n1 * cw1, (long long)n1 * cw1, L1, diag_of(P.dbs[qs[b]]),
+                launch_mac(babies.p + (size_t)b * n1 * cw1, (long long)n1 * cw1, L1, diag_of(d),
                            Pj.p + (size_t)t * n2 * cw1, (long long)n2 * cw1, L1, L1, n1, n2, ell, 1, c->d_primes, N,
                            c->cur);
                 c->launches++;
+            }
+            if (!relin.empty()) {
+                stage.reset(new Prof(c, "stage:relin"));
+                keyswitch(c, L, relin);
             }
             Tmp Gs(c, (size_t)nb * n2 * cw);  // [nb][n2][2][L][N]
             rescale(c, Pj.p, nb * n2, L, L1, Gs.p, L);
@@ -1996,7 +2090,8 @@ void match_workspace(const fr_ctx* c, const fr_db* db, fr_mode mode, uint64_t* b
     if (mode != FR_MODE_SCORES) per += G * 54.0 * cw;  // threshold: powers, leaves, tree temporaries
     double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N;  // key-switch scratch
     if (db->schedule == 1) b += ell * cw1 + G * cw1;
-    if (db->tier != 1) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
+    if (db->tier == 4) per += 3.0 * n2 * L1 * N;  // unrelinearised products of the giant steps
+    if (db->tier != 1 && db->tier != 4) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
     *base = (uint64_t)(b * 8.0 * 1.25);
     *per_query = (uint64_t)(per * 8.0 * 1.25);
 }

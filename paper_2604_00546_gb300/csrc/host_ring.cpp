@@ -476,7 +476,11 @@ void keygen(const Ring& R, u64 seed, const std::vector<u64>& galois, KeySet& K, 
 }
 
 void encrypt(const Ring& R, const KeySet& K, const double* z, u64 seed, u64* out) {
-    const int N = R.N, nq = R.nq;
+    encrypt_level(R, K, z, seed, R.nq - 1, (int)std::thread::hardware_concurrency(), out);
+}
+
+void encrypt_level(const Ring& R, const KeySet& K, const double* z, u64 seed, int level, int nthreads, u64* out) {
+    const int N = R.N, nq = level + 1;
     std::vector<int64_t> m(N);
     encode_coeffs(R, z, R.scale_bits, m.data());
     std::vector<int8_t> v(N);
@@ -484,7 +488,7 @@ void encrypt(const Ring& R, const KeySet& K, const double* z, u64 seed, u64* out
     sample_ternary(seed, kObjEncV, N, v.data());
     sample_cbd(seed, kObjEncE0, N, e0.data());
     sample_cbd(seed, kObjEncE1, N, e1.data());
-    parallel_for(nq, (int)std::thread::hardware_concurrency(), [&](int i) {
+    parallel_for(nq, nthreads, [&](int i) {
         const u64 q = R.primes[i];
         std::vector<u64> V(N);
         for (int j = 0; j < N; ++j) V[j] = resid(v[j], q);
@@ -501,6 +505,25 @@ void encrypt(const Ring& R, const KeySet& K, const double* z, u64 seed, u64* out
             c0[j] = addm(addm(c0[j], resid(e0[j], q), q), resid(m[j], q), q);
             c1[j] = addm(c1[j], resid(e1[j], q), q);
         }
+    });
+}
+
+void encrypt_diagonals(const Ring& R, const KeySet& K, const float* T, long long rows, int ell, int n1, int level,
+                       u64 seed, int nthreads, u64* out) {
+    const int n = R.N / 2;
+    const long long G = (rows + n - 1) / n, B = n / ell;
+    const size_t cw = (size_t)2 * (level + 1) * R.N;
+    parallel_for((int)(G * ell), nthreads, [&](int e) {
+        const long long g = e / ell;
+        const int d = e % ell;
+        const long long shift = (long long)(d / n1) * n1;
+        std::vector<double> z(n);
+        for (int x = 0; x < n; ++x) {
+            const long long y = ((x - shift) % n + n) % n;
+            const long long row = (g * B + y / ell) * ell + y % ell;
+            z[x] = row < rows ? (double)T[(size_t)row * ell + (size_t)((y % ell + d) % ell)] : 0.0;
+        }
+        encrypt_level(R, K, z.data(), seed + (u64)e, level, 1, out + (size_t)e * cw);
     });
 }
 

@@ -29,7 +29,7 @@ FR_MODE_SCORES, FR_MODE_IDENTIFY, FR_MODE_MEMBERSHIP = 0, 1, 2
 
 EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
-    "fr_load_db", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
+    "fr_load_db", "fr_encrypt_db", "fr_load_db_encrypted", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
     "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
         "fr_keygen": (st, [vp, i32p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_load_keys": (st, [vp, vp]),
         "fr_load_db": (st, [vp, f32p, C.c_size_t, C.c_size_t, C.POINTER(vp)]),
+        "fr_encrypt_db": (st, [vp, vp, f32p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_uint64, u64p, C.c_size_t]),
+        "fr_load_db_encrypted": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.POINTER(vp)]),
         "fr_db_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
@@ -295,6 +297,24 @@ class Context:
         h = C.c_void_p()
         _check(_lib.fr_load_db(self.h, T, T.shape[0], T.shape[1], C.byref(h)))
         return Database(self, h, T.shape[0])
+
+    def encrypt_db(self, keys, templates, level=None, seed=0):
+        """Enroller side: the G*ell encrypted pre-rotated diagonals of the templates,
+        [G][ell][2][level+1][N] (export format), at `level` (default: the working level)."""
+        T = np.ascontiguousarray(templates, dtype=np.float32)
+        K, ell = T.shape
+        level = self.work_level if level is None else int(level)
+        G = -(-K // self.n)
+        out = np.empty((G, ell, 2, level + 1, self.N), dtype=np.uint64)
+        _check(_lib.fr_encrypt_db(self.h, keys.h, T, K, ell, level, int(seed), out, out.size))
+        return out
+
+    def load_db_encrypted(self, cts, K):
+        """Server side: a database (storage tier 4) of the encrypted diagonals from encrypt_db."""
+        E = np.ascontiguousarray(cts, dtype=np.uint64)
+        h = C.c_void_p()
+        _check(_lib.fr_load_db_encrypted(self.h, E, int(K), E.shape[1], E.shape[3] - 1, C.byref(h)))
+        return Database(self, h, int(K))
 
     def encrypt(self, keys, q, seed):
         q = np.ascontiguousarray(q, dtype=np.float64)

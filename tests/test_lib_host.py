@@ -73,6 +73,24 @@ def test_client_primes_keys_and_encryption_match_oracle(cfg):
     assert np.abs(z - np.tile(q, oc.n // c["ell"])).max() < 1e-6
 
 
+@pytest.mark.parametrize("level", [2, 8])
+def test_enroller_encrypted_diagonals_match_oracle(level):
+    """Encrypted-database enrollment (host code of the library): the pre-rotated diagonals of a
+    two-group database, encrypted at `level`, equal the oracle's bit for bit."""
+    c = W.CONFIGS["mid"]
+    ctx = fr.Context(device=-1, **W.ctx_params("mid"))
+    oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
+    keys = ctx.keygen([1], W.key_seed("mid"))
+    ok = oc.keygen(W.key_seed("mid"))
+    T = W.templates(ctx.n + 300, c["ell"], W.DATASET_SEED + 90)
+    E = ctx.encrypt_db(keys, T, level=level, seed=0xABC)
+    assert E.shape == (2, c["ell"], 2, level + 1, oc.N)
+    assert np.array_equal(E, ok.encrypt_db(T, c["ell"], c["n1"], 0xABC, level=level))
+    with pytest.raises(fr.FrError) as e:
+        ctx.encrypt_db(keys, T, level=len(c["q_bits"]))
+    assert e.value.status == fr.FR_ERR_LEVEL
+
+
 def test_import_rejects_unreduced_words():
     c = W.CONFIGS["tiny"]
     ctx = fr.Context(device=-1, **W.ctx_params("tiny"))
