@@ -124,7 +124,8 @@ def _declare(L):
                            C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_table_scores.restype = C.c_int
     L.or_table_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
-    L.or_encrypt_db.argtypes = [vp, vp, f32p, C.c_long, C.c_int, C.c_int, C.c_uint64, C.c_int, u64p]
+    L.or_encrypt_db.argtypes = [vp, vp, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, u64p]
+    L.or_prerotate_db.argtypes = [vp, vp, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int, u64p]
     L.or_enc_giant_step.restype = C.c_int
     L.or_enc_giant_step.argtypes = [vp, vp, u64p, C.c_int, C.c_int, u64p, C.c_int, C.c_int, C.c_int, u64p]
     L.or_enc_bsgs_scores.restype = C.c_int
@@ -416,15 +417,25 @@ class Keys:
         return out[: cnt * w].reshape(cnt, 2, level + 1, c.N).copy(), level
 
     # -- encrypted database (enroller-side pre-rotation, lazy relinearisation) ------------
-    def encrypt_db(self, T, ell, n1, seed, level=None):
-        """The G*ell encrypted pre-rotated diagonals [G][ell][2][level+1][N] (coefficient form)."""
+    def encrypt_db(self, T, ell, n1, seed, level=None, prerotate=True):
+        """The G*ell encrypted diagonals [G][ell][2][level+1][N] (coefficient form), pre-rotated
+        by the enroller (prerotate) or plain (for the server's pre-rotation)."""
         c = self.ctx
         level = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
         out = np.empty((G, ell, 2, level + 1, c.N), dtype=np.uint64)
-        self.L.or_encrypt_db(c.h, self.h, T, K, ell, n1, int(seed), level, out)
+        self.L.or_encrypt_db(c.h, self.h, T, K, ell, n1, 1 if prerotate else 0, int(seed), level, out)
+        return out
+
+    def prerotate_db(self, E, n1, level):
+        """Server-side pre-rotation of plain encrypted diagonals E, at `level`."""
+        c = self.ctx
+        E = np.ascontiguousarray(E, dtype=np.uint64)
+        G, ell, el = E.shape[0], E.shape[1], E.shape[3] - 1
+        out = np.empty((G, ell, 2, level + 1, c.N), dtype=np.uint64)
+        self.L.or_prerotate_db(c.h, self.h, E, el, G, ell, n1, int(level), out)
         return out
 
     def enc_scores(self, qct, E, n1, level=None):

@@ -1486,23 +1486,46 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
 /*     S_k += Rot_{j n1}(P)   (P itself for j = 0)                             */
 /* ------------------------------------------------------------------------ */
 /* Enrollment of a K x ell template matrix: the G*ell diagonal cts, [G][ell][2][level+1][N]
- * coefficient form. Diagonal d of group g is the pre-rotated plaintext diagonal
- * (Eq. eq:prerotation, shift (d / n1) n1) encrypted at the top level with seed + g*ell + d
- * and dropped to `level`. */
-void or_encrypt_db(const or_ctx* c, const or_keys* k, const float* T, long K, int ell, int n1, u64 seed, int level,
-                   u64* out) {
+ * coefficient form. Diagonal d of group g is the plaintext diagonal, pre-rotated by the enroller
+ * when prerotate != 0 (Eq. eq:prerotation, shift (d / n1) n1; Section 5.3.3) and left plain
+ * otherwise (the server pre-rotates, or_prerotate_db), encrypted at the top level with
+ * seed + g*ell + d and dropped to `level`. */
+void or_encrypt_db(const or_ctx* c, const or_keys* k, const float* T, long K, int ell, int n1, int prerotate,
+                   u64 seed, int level, u64* out) {
     int N = c->n, n = N / 2, top = c->nq - 1;
     long G = (K + n - 1) / n;
     double* z = (double*)malloc(sizeof(double) * n);
     u64* full = (u64*)malloc(sizeof(u64) * ct_words(c, top));
     for (long g = 0; g < G; g++)
         for (int d = 0; d < ell; d++) {
-            or_diag_slots(T, K, ell, n, g, d, (long)(d / n1) * n1, z);
+            or_diag_slots(T, K, ell, n, g, d, prerotate ? (long)(d / n1) * n1 : 0, z);
             or_encrypt(c, k, z, seed + (u64)(g * ell + d), full);
             or_drop(c, full, top, level, out + (size_t)(g * ell + d) * ct_words(c, level));
         }
     free(z);
     free(full);
+}
+
+/* Server-side pre-rotation of encrypted diagonals (Section 5.3, offline phase of the GPU
+ * variant with pre-rotated diagonals): the plain diagonal cts E [G][ell][2][el+1][N] are dropped
+ * to level L, and diagonal d = j n1 + i with j >= 1 is rotated by -j n1 (a key switch with the
+ * key of the negative giant step). out: [G][ell][2][L+1][N] coefficient form. */
+void or_prerotate_db(const or_ctx* c, const or_keys* k, const u64* E, int el, long G, int ell, int n1, int L,
+                     u64* out) {
+    size_t ew = ct_words(c, el), cw = ct_words(c, L);
+    u64* t = (u64*)malloc(sizeof(u64) * cw);
+    for (long g = 0; g < G; g++)
+        for (int d = 0; d < ell; d++) {
+            u64* o = out + (size_t)(g * ell + d) * cw;
+            int j = d / n1;
+            if (j == 0) {
+                or_drop(c, E + (size_t)(g * ell + d) * ew, el, L, o);
+            } else {
+                or_drop(c, E + (size_t)(g * ell + d) * ew, el, L, t);
+                or_rotate(c, k, t, L, -(long)j * n1, o);
+            }
+        }
+    free(t);
 }
 
 /* One giant step j of group g with encrypted diagonals E ([ell][2][el+1][N] coefficient form,

@@ -675,3 +675,34 @@ def test_encrypted_db_scores_and_match():
     memb, l2 = k.match_enc(qct, E, K, n1, oracle.MODE_MEMBERSHIP, level=lq)
     assert l2 == l1
     assert np.abs(k.decrypt(memb[0], l2) - p.sum()).max() < 1e-2
+
+
+def test_server_prerotation_of_encrypted_diagonals():
+    """Server-side pre-rotation (the GPU variant of Section 5.3 that rotates encrypted diagonals
+    at load with negative giant-step keys): the rotated ciphertexts decrypt to the same
+    pre-rotated diagonals the enroller variant encrypts, and the match decrypts to the FP64
+    inner products; the bits differ from the enroller variant (key-switch noise)."""
+    c = oracle.Ctx(10, [60, 40, 40], [60, 60, 60], 1, 40)
+    k = c.keygen(93)
+    ell, n1, K = 16, 4, c.n + 70
+    T = _templates(K, ell, 12)
+    plain = k.encrypt_db(T, ell, n1, 700, prerotate=False)
+    pre = k.prerotate_db(plain, n1, 2)
+    tbe = k.encrypt_db(T, ell, n1, 700, level=2)
+    for g, d in [(0, 2), (0, 9), (1, 14)]:
+        zp = k.decrypt(plain[g, d], c.top)
+        z = k.decrypt(pre[g, d], 2)
+        assert np.abs(z - k.decrypt(tbe[g, d], 2)).max() < 1e-6
+        assert np.abs(z - np.roll(zp, (d // n1) * n1)).max() < 1e-6      # Rot_{-j n1}: slot x <- x - j n1
+        if d >= n1:
+            assert not np.array_equal(pre[g, d], tbe[g, d])
+        else:
+            assert np.array_equal(pre[g, d], tbe[g, d])
+    rng = np.random.default_rng(4)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k.encrypt(np.tile(q, c.n // ell), 8)
+    S = k.enc_scores(qct, pre, n1, level=2)
+    got = np.concatenate([k.decrypt(S[g], 1) for g in range(2)])
+    s = T.astype(np.float64) @ q
+    assert np.abs(got[:K] - s).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
