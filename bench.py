@@ -453,7 +453,10 @@ def run_encrypted(args):
     cfg = "membership"
     c = W.CONFIGS[cfg]
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode))
-    keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
+    # with the negative giant-step keys of the server-side pre-rotation variant
+    rots = set(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP))
+    rots |= set(fr.rotation_set(c["ell"], c["n1"], ctx.n, fr.FR_KEYS_TBS_TOTAL, True))
+    keys = ctx.keygen(sorted(rots), W.key_seed(cfg))
     ctx.load_keys(keys)
     T, q, planted = W.workload(cfg)
     K = len(T)
@@ -489,6 +492,16 @@ def run_encrypted(args):
     del outs
     ms_pt, outs = timed(lambda: ctx.match(dbp, qct, mode), args.steps)
     del outs
+    # server-side pre-rotation: plain diagonals enrolled, rotated by -j n1 at load
+    Ep = ctx.encrypt_db(keys, T, seed=0xE3000, prerotate=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dbs_ = ctx.load_db_encrypted(Ep, K, prerotated=False)
+    load_tbs_s = time.perf_counter() - t0
+    del Ep
+    ms_tbs, outs = timed(lambda: ctx.match(dbs_, qct, mode), args.steps)
+    err_tbs = abs(float(ctx.decrypt(keys, outs[0])[0]) - pref)
+    del outs, dbs_
     B = max(1, args.batch)
     qb = [ctx.encrypt(keys, q, W.enc_seed(cfg, 300 + i)).upload() for i in range(B)]
     ms_b, outs = timed(lambda: ctx.match_batch(db, qb, mode), max(2, args.steps // 4))
@@ -517,6 +530,8 @@ def run_encrypted(args):
                    "frac": (mac_gbs / hbm) if mac_gbs else None, "peak_gbs": hbm, "peak": hbm_src},
         "stages_ms_eager": stages,
         "enroll_s_host": enroll_s, "load_s": load_s,
+        "server_prerotation": {"load_s": load_tbs_s, "ms_per_step": ms_tbs, "value": K / (ms_tbs / 1000.0),
+                               "unit": UNIT, "membership_abs_err": err_tbs},
         "membership_abs_err": err, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -144,25 +144,29 @@ fr_status fr_load_db(fr_ctx* ctx, const float* templates, size_t K, size_t ell, 
 /* Storage tier for the databases loaded from now on (as fr_params.db_tier: 0 auto, 1, 2, 3). */
 fr_status fr_set_db_tier(fr_ctx* ctx, uint32_t tier);
 
-/* Encrypted database (the paper's own setting, Section 5.3; the variant with enroller-side
- * pre-rotation, Section 5.3.3). fr_encrypt_db is enroller (client) side and runs on the host:
- * for the K x ell FP32 templates (row-major, K >= 1, ell = the context's ell) it writes the
- * G * ell ciphertexts E_{g,d} = Enc_pk(Rot_{-j n1}(diag_d(M_g))), d = j n1 + i, g < G =
- * ceil(K / (N/2)), each pre-rotated by the context's n1 and encrypted with seed + g*ell + d,
- * to out in the export format ([G][ell][2][level+1][N] u64, coefficient form; words >=
- * G*ell*2*(level+1)*N). The limbs 0..level are those of a top-level encryption with the
- * same seed. Errors: FR_ERR_INVALID_ARG (null pointers, K = 0, ell, small buffer),
- * FR_ERR_LEVEL (level >= number of Q primes). */
+/* Encrypted database (the paper's own setting, Section 5.3). fr_encrypt_db is enroller (client)
+ * side and runs on the host: for the K x ell FP32 templates (row-major, K >= 1, ell = the
+ * context's ell) it writes the G * ell ciphertexts of the diagonals diag_d(M_g), g < G =
+ * ceil(K / (N/2)), each encrypted under pk with seed + g*ell + d, to out in the export format
+ * ([G][ell][2][level+1][N] u64, coefficient form; words >= G*ell*2*(level+1)*N). With prerotate
+ * != 0 the enroller pre-rotates each plaintext diagonal d = j n1 + i by -j n1 slots before
+ * encrypting it (Eq. eq:prerotation, the variant of Section 5.3.3; n1 is the context's); with
+ * prerotate = 0 the diagonals are plain and the server pre-rotates them at load. The limbs
+ * 0..level are those of a top-level encryption with the same seed. Errors: FR_ERR_INVALID_ARG
+ * (null pointers, K = 0, ell, small buffer), FR_ERR_LEVEL (level >= number of Q primes). */
 fr_status fr_encrypt_db(const fr_ctx* ctx, const fr_keys* keys, const float* templates, size_t K, size_t ell,
-                        uint32_t level, uint64_t seed, uint64_t* out, size_t words);
+                        int prerotate, uint32_t level, uint64_t seed, uint64_t* out, size_t words);
 /* Server side: load the G * ell ciphertexts written by fr_encrypt_db (level >= the working
  * level; the limbs above it are dropped) as a database of storage tier 4, resident in HBM in
- * evaluation form. Matches against it take, per group and giant step j, the ct x ct products
+ * evaluation form. prerotated says how they were enrolled. If 0, the server rotates diagonal
+ * j n1 + i, j >= 1, by -j n1 at load (the keys of the negative giant steps -j n1 must be loaded;
+ * they are not needed afterwards). Matches take, per group and giant step j, the ct x ct products
  * sum_i Rot_i(q) (x) E_{g, j n1 + i}, relinearise once (lazy relinearisation; the relinearisation
  * key must be loaded), rescale and rotate by j n1; the threshold and the slot sum follow as for
- * plaintext databases. Inputs are copied. Errors: FR_ERR_INVALID_ARG, FR_ERR_LEVEL,
- * FR_ERR_FORMAT (a residue not below its prime), FR_ERR_HBM_BUDGET. */
-fr_status fr_load_db_encrypted(fr_ctx* ctx, const uint64_t* cts, size_t K, size_t ell, uint32_t level, fr_db** out);
+ * plaintext databases. Inputs are copied. Errors: FR_ERR_INVALID_ARG (also a missing key),
+ * FR_ERR_LEVEL, FR_ERR_FORMAT (a residue not below its prime), FR_ERR_HBM_BUDGET. */
+fr_status fr_load_db_encrypted(fr_ctx* ctx, const uint64_t* cts, size_t K, size_t ell, uint32_t level, int prerotated,
+                               fr_db** out);
 
 /* Storage tier chosen for a database (1 stored diagonals, 2 per-query encoding, 3 stored
  * integer coefficients, 4 encrypted diagonals), its number of template groups G = ceil(K / (N/2)), its resident bytes and the BSGS schedule

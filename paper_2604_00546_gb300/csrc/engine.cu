@@ -1209,7 +1209,7 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
 }
 
 fr_status fr_encrypt_db(const fr_ctx* c, const fr_keys* k, const float* templates, size_t K, size_t ell,
-                        uint32_t level, uint64_t seed, uint64_t* out, size_t words) {
+                        int prerotate, uint32_t level, uint64_t seed, uint64_t* out, size_t words) {
     return guard([&] {
         if (!c || !k || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
         if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
@@ -1217,12 +1217,13 @@ fr_status fr_encrypt_db(const fr_ctx* c, const fr_keys* k, const float* template
         const size_t N = c->R.N, n = N / 2, G = (K + n - 1) / n;
         if (words < G * ell * 2 * (level + 1) * N) raise(FR_ERR_INVALID_ARG, "output buffer too small");
         const int threads = std::max(1, (int)std::thread::hardware_concurrency());
-        frh::encrypt_diagonals(c->R, k->ks, templates, (long long)K, (int)ell, (int)c->n1, (int)level, seed, threads,
-                               out);
+        frh::encrypt_diagonals(c->R, k->ks, templates, (long long)K, (int)ell, (int)c->n1, prerotate != 0, (int)level,
+                               seed, threads, out);
     });
 }
 
-fr_status fr_load_db_encrypted(fr_ctx* c, const uint64_t* cts, size_t K, size_t ell, uint32_t level, fr_db** out) {
+fr_status fr_load_db_encrypted(fr_ctx* c, const uint64_t* cts, size_t K, size_t ell, uint32_t level, int prerotated,
+                               fr_db** out) {
     return guard([&] {
         need_device(c);
         std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
@@ -1251,6 +1252,8 @@ fr_status fr_load_db_encrypted(fr_ctx* c, const uint64_t* cts, size_t K, size_t 
         db->bytes = ncts * 2 * L1 * (size_t)N * 8;
         if (c->budget && c->resident + db->bytes > c->budget)
             raise(FR_ERR_HBM_BUDGET, "database exceeds the HBM budget");
+        if (!prerotated)  // the negative giant-step keys of the server-side pre-rotation
+            for (long j = 1; j * (long)c->n1 < (long)ell; ++j) rot_key(c, frh::galois_of_rotation(c->R, -j * (long)c->n1));
         void* p = nullptr;
         cudaError_t e = cudaMalloc(&p, db->bytes);
         if (e != cudaSuccess) {
@@ -1259,14 +1262,45 @@ fr_status fr_load_db_encrypted(fr_ctx* c, const uint64_t* cts, size_t K, size_t 
                   std::string("cannot hold the encrypted diagonals: ") + cudaGetErrorString(e));
         }
         db->diags = (u64*)p;
-        // limbs 0..L of both components, 64 ciphertexts per copy; then NTT into Montgomery form
+        // limbs 0..L of both components, 64 ciphertexts per copy, then the NTT (into Montgomery
+        // form when the enroller pre-rotated them)
         for (size_t e0 = 0; e0 < ncts; e0 += 64) {
             const size_t ne = std::min<size_t>(64, ncts - e0);
             u64* dst = db->diags + e0 * 2 * L1 * N;
             CU(cudaMemcpy2DAsync(dst, (size_t)L1 * N * 8, cts + e0 * 2 * lw * N, lw * N * 8, (size_t)L1 * N * 8, 2 * ne,
                                  cudaMemcpyHostToDevice, c->cur));
-            PolyBatch pb{dst, (long long)L1 * N, L1, (int)(2 * ne * L1), pm_level(L)};
-            launch_ntt_tomont(c->rd, pb, c->cur);
+            if (prerotated) {
+                PolyBatch pb{dst, (long long)L1 * N, L1, (int)(2 * ne * L1), pm_level(L)};
+                launch_ntt_tomont(c->rd, pb, c->cur);
+                c->launches++;
+            } else {
+                ntt(c, dst, (long long)L1 * N, L1, (int)(2 * ne * L1), pm_level(L), false);
+            }
+        }
+        if (!prerotated) {
+            // server-side pre-rotation (Eq. eq:prerotation on ciphertexts): diagonal j n1 + i,
+            // j >= 1, is rotated by -j n1 with the negative giant-step key, 64 at a time into
+            // scratch and copied back; then the whole database into Montgomery form
+            const int n1 = (int)c->n1;
+            const size_t cw1 = (size_t)2 * L1 * N;
+            std::vector<size_t> todo;
+            for (size_t e = 0; e < ncts; ++e)
+                if ((int)(e % ell) >= n1) todo.push_back(e);
+            Tmp rot(c, 64 * cw1);
+            for (size_t t0 = 0; t0 < todo.size(); t0 += 64) {
+                const size_t nt = std::min<size_t>(64, todo.size() - t0);
+                std::vector<KSReq> reqs;
+                for (size_t t = 0; t < nt; ++t) {
+                    const size_t e = todo[t0 + t];
+                    const long j = (long)(e % ell) / n1;
+                    const u64 gk = frh::galois_of_rotation(c->R, -j * n1);
+                    const u64* src = db->diags + e * cw1;
+                    reqs.push_back(KSReq{src + (size_t)L1 * N, rot_key(c, gk), (u32)gk, 1, src, L1, rot.p + t * cw1, L1});
+                }
+                keyswitch(c, L, reqs);
+                for (size_t t = 0; t < nt; ++t) copy_d2d(c, db->diags + todo[t0 + t] * cw1, rot.p + t * cw1, cw1);
+            }
+            launch_to_mont(db->diags, N, pm_level(L), c->d_primes, (long long)(ncts * cw1), c->cur);
             c->launches++;
         }
         CU(cudaStreamSynchronize(c->cur));

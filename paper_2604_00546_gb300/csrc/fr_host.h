@@ -86,10 +86,10 @@ void encrypt(const Ring& R, const KeySet& K, const double* z, u64 seed, u64* out
 // limbs 0..level of the top-level encryption with the same seed ([2][level+1][N] coefficient form)
 void encrypt_level(const Ring& R, const KeySet& K, const double* z, u64 seed, int level, int nthreads, u64* out);
 // Enrollment of an encrypted database: the G ell diagonals of the rows x ell matrix T, each
-// pre-rotated by -(d / n1) n1 slots and encrypted at `level` with seed + g ell + d, written
-// [G][ell][2][level+1][N] (coefficient form).
-void encrypt_diagonals(const Ring& R, const KeySet& K, const float* T, long long rows, int ell, int n1, int level,
-                       u64 seed, int nthreads, u64* out);
+// pre-rotated by -(d / n1) n1 slots when prerotate is set (plain otherwise) and encrypted at
+// `level` with seed + g ell + d, written [G][ell][2][level+1][N] (coefficient form).
+void encrypt_diagonals(const Ring& R, const KeySet& K, const float* T, long long rows, int ell, int n1, bool prerotate,
+                       int level, u64 seed, int nthreads, u64* out);
 void decrypt_coeffs(const Ring& R, const KeySet& K, const u64* ct, int level, int64_t* x);
 // plaintext coefficients as reals: centered CRT of limbs 0 and 1 (level >= 1) or limb 0
 void decrypt_values(const Ring& R, const KeySet& K, const u64* ct, int level, double* x);

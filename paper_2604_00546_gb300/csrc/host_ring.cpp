@@ -508,15 +508,15 @@ void encrypt_level(const Ring& R, const KeySet& K, const double* z, u64 seed, in
     });
 }
 
-void encrypt_diagonals(const Ring& R, const KeySet& K, const float* T, long long rows, int ell, int n1, int level,
-                       u64 seed, int nthreads, u64* out) {
+void encrypt_diagonals(const Ring& R, const KeySet& K, const float* T, long long rows, int ell, int n1, bool prerotate,
+                       int level, u64 seed, int nthreads, u64* out) {
     const int n = R.N / 2;
     const long long G = (rows + n - 1) / n, B = n / ell;
     const size_t cw = (size_t)2 * (level + 1) * R.N;
     parallel_for((int)(G * ell), nthreads, [&](int e) {
         const long long g = e / ell;
         const int d = e % ell;
-        const long long shift = (long long)(d / n1) * n1;
+        const long long shift = prerotate ? (long long)(d / n1) * n1 : 0;
         std::vector<double> z(n);
         for (int x = 0; x < n; ++x) {
             const long long y = ((x - shift) % n + n) % n;

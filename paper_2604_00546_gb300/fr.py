@@ -89,8 +89,9 @@ def load(build_if_missing: bool = True):
         "fr_keygen": (st, [vp, i32p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_load_keys": (st, [vp, vp]),
         "fr_load_db": (st, [vp, f32p, C.c_size_t, C.c_size_t, C.POINTER(vp)]),
-        "fr_encrypt_db": (st, [vp, vp, f32p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_uint64, u64p, C.c_size_t]),
-        "fr_load_db_encrypted": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.POINTER(vp)]),
+        "fr_encrypt_db": (st, [vp, vp, f32p, C.c_size_t, C.c_size_t, C.c_int, C.c_uint32, C.c_uint64, u64p,
+                               C.c_size_t]),
+        "fr_load_db_encrypted": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_int, C.POINTER(vp)]),
         "fr_db_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "fr_encrypt": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
         "fr_encrypt_slots": (st, [vp, vp, f64p, C.c_size_t, C.c_uint64, C.POINTER(vp)]),
@@ -298,22 +299,24 @@ class Context:
         _check(_lib.fr_load_db(self.h, T, T.shape[0], T.shape[1], C.byref(h)))
         return Database(self, h, T.shape[0])
 
-    def encrypt_db(self, keys, templates, level=None, seed=0):
-        """Enroller side: the G*ell encrypted pre-rotated diagonals of the templates,
-        [G][ell][2][level+1][N] (export format), at `level` (default: the working level)."""
+    def encrypt_db(self, keys, templates, level=None, seed=0, prerotate=True):
+        """Enroller side: the G*ell encrypted diagonals of the templates, [G][ell][2][level+1][N]
+        (export format), at `level` (default: the working level); pre-rotated by the enroller
+        (prerotate) or plain, for the server to pre-rotate at load."""
         T = np.ascontiguousarray(templates, dtype=np.float32)
         K, ell = T.shape
         level = self.work_level if level is None else int(level)
         G = -(-K // self.n)
         out = np.empty((G, ell, 2, level + 1, self.N), dtype=np.uint64)
-        _check(_lib.fr_encrypt_db(self.h, keys.h, T, K, ell, level, int(seed), out, out.size))
+        _check(_lib.fr_encrypt_db(self.h, keys.h, T, K, ell, 1 if prerotate else 0, level, int(seed), out, out.size))
         return out
 
-    def load_db_encrypted(self, cts, K):
+    def load_db_encrypted(self, cts, K, prerotated=True):
         """Server side: a database (storage tier 4) of the encrypted diagonals from encrypt_db."""
         E = np.ascontiguousarray(cts, dtype=np.uint64)
         h = C.c_void_p()
-        _check(_lib.fr_load_db_encrypted(self.h, E, int(K), E.shape[1], E.shape[3] - 1, C.byref(h)))
+        _check(_lib.fr_load_db_encrypted(self.h, E, int(K), E.shape[1], E.shape[3] - 1, 1 if prerotated else 0,
+                                         C.byref(h)))
         return Database(self, h, int(K))
 
     def encrypt(self, keys, q, seed):

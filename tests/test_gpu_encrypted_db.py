@@ -1,5 +1,6 @@
-"""GPU parity of the encrypted-database match (storage tier 4; the paper's setting with
-enroller-side pre-rotation, Section 5.3.3, and lazy relinearisation).
+"""GPU parity of the encrypted-database match (storage tier 4; the paper's setting, with the
+diagonals pre-rotated by the enroller, Section 5.3.3, or by the server at load, Section 5.3,
+and lazy relinearisation).
 
 The enroller's ciphertexts come from the library's host code and must equal the oracle's bit
 for bit. Every match output (scores, identification, membership) must equal the oracle's
@@ -18,19 +19,26 @@ pytestmark = pytest.mark.gpu
 
 
 class Env:
-    def __init__(self, cfg, enroll_level=None):
+    def __init__(self, cfg, enroll_level=None, server_prerotation=False):
         c = W.CONFIGS[cfg]
         self.c = c
         self.ctx = fr.Context(device=0, **W.ctx_params(cfg))
-        self.keys = self.ctx.keygen(self.ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
+        rots = self.ctx.required_rotations(fr.FR_MODE_MEMBERSHIP)
+        if server_prerotation:   # the negative giant steps -j n1
+            rots = sorted(set(rots) | set(fr.rotation_set(c["ell"], c["n1"], self.ctx.n, fr.FR_KEYS_TBS_TOTAL, True)))
+        self.keys = self.ctx.keygen(rots, W.key_seed(cfg))
         self.ctx.load_keys(self.keys)
         self.oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
         self.ok = self.oc.keygen(W.key_seed(cfg))
         self.T, self.q, _ = W.workload(cfg)
         self.lq = self.ctx.work_level
         self.el = self.lq if enroll_level is None else enroll_level
-        self.E = self.ctx.encrypt_db(self.keys, self.T, level=self.el, seed=0xE1000)
-        self.db = self.ctx.load_db_encrypted(self.E, len(self.T))
+        pre = not server_prerotation
+        self.E = self.ctx.encrypt_db(self.keys, self.T, level=self.el, seed=0xE1000, prerotate=pre)
+        self.db = self.ctx.load_db_encrypted(self.E, len(self.T), prerotated=pre)
+        # what the server holds, per the oracle: the enroller's ciphertexts, or the oracle's
+        # server-side pre-rotation of the plain ones
+        self.E_server = self.E if pre else self.ok.prerotate_db(self.E, c["n1"], self.lq)
         self.qct = self.ctx.encrypt(self.keys, self.q, W.enc_seed(cfg))
         self.oq = self.ok.encrypt(np.tile(self.q, self.oc.n // c["ell"]), W.enc_seed(cfg))
 
@@ -38,6 +46,12 @@ class Env:
 @pytest.fixture(scope="module")
 def mid():
     return Env("mid")
+
+
+@pytest.fixture(scope="module")
+def tbs():
+    # plain encrypted diagonals, pre-rotated by the server at load with the negative giant keys
+    return Env("mid", server_prerotation=True)
 
 
 @pytest.fixture(scope="module")
@@ -52,11 +66,16 @@ def test_enrollment_matches_oracle(mid):
     assert mid.db.info()["tier"] == 4 and mid.db.info()["schedule"] == 0
 
 
-@pytest.mark.parametrize("env_name", ["mid", "deep"])
+def test_plain_enrollment_matches_oracle(tbs):
+    ref = tbs.ok.encrypt_db(tbs.T, tbs.c["ell"], tbs.c["n1"], 0xE1000, level=tbs.el, prerotate=False)
+    assert np.array_equal(tbs.E, ref)
+
+
+@pytest.mark.parametrize("env_name", ["mid", "deep", "tbs"])
 @pytest.mark.parametrize("mode", [fr.FR_MODE_SCORES, fr.FR_MODE_IDENTIFY, fr.FR_MODE_MEMBERSHIP])
 def test_match_matches_oracle(env_name, mode, request):
     env = request.getfixturevalue(env_name)
-    ref, lvl = env.ok.match_enc(env.oq, env.E, len(env.T), env.c["n1"], mode, env.c["cheb_degree"],
+    ref, lvl = env.ok.match_enc(env.oq, env.E_server, len(env.T), env.c["n1"], mode, env.c["cheb_degree"],
                                 env.c["threshold"], level=env.lq)
     for call in range(2):   # eager, then the captured graph
         outs = env.ctx.match(env.db, env.qct, mode)
@@ -110,6 +129,9 @@ def test_refusals(mid):
     assert e.value.status == fr.FR_ERR_FORMAT
     with pytest.raises(fr.FrError) as e:
         ctx.encrypt_db(mid.keys, mid.T[:, :32])
+    assert e.value.status == fr.FR_ERR_INVALID_ARG
+    with pytest.raises(fr.FrError) as e:     # server-side pre-rotation without the negative giant keys
+        ctx.load_db_encrypted(mid.E, len(mid.T), prerotated=False)
     assert e.value.status == fr.FR_ERR_INVALID_ARG
 
 

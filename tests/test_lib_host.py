@@ -86,6 +86,9 @@ def test_enroller_encrypted_diagonals_match_oracle(level):
     E = ctx.encrypt_db(keys, T, level=level, seed=0xABC)
     assert E.shape == (2, c["ell"], 2, level + 1, oc.N)
     assert np.array_equal(E, ok.encrypt_db(T, c["ell"], c["n1"], 0xABC, level=level))
+    P = ctx.encrypt_db(keys, T, level=level, seed=0xABC, prerotate=False)     # plain diagonals
+    assert np.array_equal(P, ok.encrypt_db(T, c["ell"], c["n1"], 0xABC, level=level, prerotate=False))
+    assert np.array_equal(P[:, :c["n1"]], E[:, :c["n1"]]) and not np.array_equal(P, E)
     with pytest.raises(fr.FrError) as e:
         ctx.encrypt_db(keys, T, level=len(c["q_bits"]))
     assert e.value.status == fr.FR_ERR_LEVEL
