@@ -121,7 +121,7 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           C.c_int, u64p, C.POINTER(C.c_int)]
+                           C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_table_scores.restype = C.c_int
     L.or_table_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_encrypt_db.argtypes = [vp, vp, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, u64p]
@@ -132,7 +132,9 @@ def _declare(L):
     L.or_enc_bsgs_scores.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, u64p]
     L.or_match_enc.restype = C.c_int
     L.or_match_enc.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
-                               C.c_double, u64p, C.POINTER(C.c_int)]
+                               C.c_double, C.c_int, u64p, C.POINTER(C.c_int)]
+    L.or_rotate_sum_radix.restype = C.c_int
+    L.or_rotate_sum_radix.argtypes = [vp, vp, u64p, C.c_int, C.c_int, C.c_int]
     L.or_set_threads.argtypes = [C.c_int]
     L.or_get_threads.restype = C.c_int
 
@@ -327,9 +329,13 @@ class Keys:
             raise ValueError("unsupported Chebyshev degree / level")
         return out
 
-    def rotate_sum(self, ct, level, steps):
+    def rotate_sum(self, ct, level, steps, radix=2):
+        """RotateAndSum over 2^steps slots, in radix `radix` (2: one rotation per step)."""
         x = np.ascontiguousarray(ct, dtype=np.uint64).copy()
-        self.L.or_rotate_sum(self.ctx.h, self.h, x, level, int(steps))
+        if radix == 2:
+            self.L.or_rotate_sum(self.ctx.h, self.h, x, level, int(steps))
+        elif self.L.or_rotate_sum_radix(self.ctx.h, self.h, x, level, int(steps), int(radix)) < 0:
+            raise ValueError("radix must be a power of two")
         return x
 
     def bsgs_scores(self, qct, T, ell, n1, level=None):
@@ -397,7 +403,7 @@ class Keys:
             raise ValueError("bad parameters")
         return out
 
-    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0):
+    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2):
         """Full match of a top-level query ct, computed at working level `level` (default: top);
         schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table."""
         c = self.ctx
@@ -409,7 +415,7 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
-                            int(cheb_n), float(tau), int(schedule), out, C.byref(lvl))
+                            int(cheb_n), float(tau), int(schedule), int(sum_radix), out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value
@@ -451,7 +457,7 @@ class Keys:
             raise ValueError("bad arguments")
         return out
 
-    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None):
+    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None, sum_radix=2):
         """Full match of a top-level query ct against encrypted diagonals E, at working level
         `level` (default: top); returns (outputs, their level)."""
         c = self.ctx
@@ -462,7 +468,7 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)
         lvl = C.c_int(0)
         r = self.L.or_match_enc(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, E, el, int(K), ell,
-                                n1, mode, int(cheb_n), float(tau), out, C.byref(lvl))
+                                n1, mode, int(cheb_n), float(tau), int(sum_radix), out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

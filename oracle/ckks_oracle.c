@@ -1208,6 +1208,28 @@ void or_rotate_sum(const or_ctx* c, const or_keys* k, u64* ct, int l, int steps)
     free(r);
 }
 
+/* RotateAndSum in radix r (a power of two): with s = 1, r, r^2, ... below 2^steps, each step
+ * x <- x + sum_{t=1}^{rr-1} Rot_{t s}(x), rr = min(r, 2^steps / s), the rr-1 rotations hoisted
+ * over one decomposition of x (Section "Hoisting and double hoisting"). Same total in every
+ * slot as the radix-2 form; r = 2 is or_rotate_sum itself. */
+int or_rotate_sum_radix(const or_ctx* c, const or_keys* k, u64* ct, int l, int steps, int r) {
+    if (r < 2 || (r & (r - 1))) return -1;
+    if (r == 2) { or_rotate_sum(c, k, ct, l, steps); return 0; }
+    long n = 1L << steps;
+    size_t w = ct_words(c, l);
+    long* rots = (long*)malloc(sizeof(long) * r);
+    u64* rt = (u64*)malloc(sizeof(u64) * w * r);
+    for (long s_ = 1; s_ < n; s_ *= r) {
+        long rr = n / s_ < r ? n / s_ : r;
+        for (long t = 1; t < rr; t++) rots[t - 1] = t * s_;
+        or_hoisted_rotate(c, k, ct, l, rots, (int)(rr - 1), rt);
+        for (long t = 1; t < rr; t++) or_add(c, ct, rt + (size_t)(t - 1) * w, l, ct);
+    }
+    free(rots);
+    free(rt);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* HyDia packing (Section "Diagonal method for rectangular matrices", Fig. 1) */
 /* and the pre-rotated diagonal of Eq. eq:prerotation.                       */
@@ -1414,7 +1436,7 @@ int or_table_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, co
  * lines for the comparison and the sum, Algorithm 6 for identification): mode 1 writes the
  * G cts p(S_k) at level lq-1-d2; mode 2 writes sum_k p(S_k) after RotateAndSum over all slots. */
 static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq, int mode, int cheb_n, double tau,
-                      u64* out, int* out_level) {
+                      int sum_radix, u64* out, int* out_level) {
     int n = c->n / 2;
     int d1, d2;
     or_ps_split(cheb_n, &d1, &d2);
@@ -1435,7 +1457,7 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
     }
     int steps = 0;
     while ((1 << steps) < n) steps++;
-    or_rotate_sum(c, k, out, lo, steps);
+    if (or_rotate_sum_radix(c, k, out, lo, steps, sum_radix) < 0) { free(t); return -1; }
     *out_level = lo;
     free(t);
     return 1;
@@ -1445,10 +1467,10 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
  * working level lq (lq = top: the whole chain). schedule 0: on-demand BSGS with
  * pre-rotated diagonals; schedule 1: the rotated-query table of Algorithm 1. mode 0: scores (G cts, level
  * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
- * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots).
+ * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, int schedule, u64* out, int* out_level) {
+             int cheb_n, double tau, int schedule, int sum_radix, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
@@ -1469,7 +1491,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
                            : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, sum_radix, out, out_level);
     free(S);
     return r;
 }
@@ -1609,7 +1631,7 @@ int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const
 
 /* Full match against an encrypted database at level el (>= lq); modes as in or_match. */
 int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64* E, int el, long K, int ell, int n1,
-                 int mode, int cheb_n, double tau, u64* out, int* out_level) {
+                 int mode, int cheb_n, double tau, int sum_radix, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top || el < lq) return -1;
     long G = (K + n - 1) / n;
@@ -1625,7 +1647,7 @@ int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64*
     int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, S);
     free(q);
     if (rs < 0) { free(S); return -1; }
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, sum_radix, out, out_level);
     free(S);
     return r;
 }

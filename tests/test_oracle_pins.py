@@ -335,6 +335,21 @@ def test_rotate_sum_gives_total_in_every_slot(c1, k1):
     steps = int(np.log2(c1.n))
     r = k1.rotate_sum(ct, 2, steps)
     assert np.abs(k1.decrypt(r, 2) - z.sum()).max() < 1e-5
+    # radix r: hoisted rotations by t s, t < r, per step; the same total, other key-switch noise
+    for radix in (4, 8, 32):
+        rr = k1.rotate_sum(ct, 2, steps, radix=radix)
+        assert np.abs(k1.decrypt(rr, 2) - z.sum()).max() < 1e-5
+        assert not np.array_equal(rr, r)
+    # one radix-4 step over 4 slots is x + Rot_1(x) + Rot_2(x) + Rot_3(x), hoisted rotations
+    # being the individual ones (reading R6b)
+    x = ct.copy()
+    for t in (1, 2, 3):
+        x = c1.add(x, k1.rotate(ct, 2, t), 2)
+    assert np.array_equal(k1.rotate_sum(ct, 2, 2, radix=4), x)
+    # partial sums: 8 slots in radix 4 = one radix-4 step (s = 1) and one radix-2 step (s = 4)
+    y = k1.rotate_sum(ct, 2, 2, radix=4)
+    y = c1.add(y, k1.rotate(y, 2, 4), 2)
+    assert np.array_equal(k1.rotate_sum(ct, 2, 3, radix=4), y)
 
 
 # ---------------------------------------------------------------------------
@@ -553,6 +568,10 @@ def test_match_modes_small():
     assert lvl3 == lvl2
     mt = k.decrypt(memt[0], lvl3)
     assert np.abs(mt - p.sum()).max() < 1e-2
+    # RotateAndSum in radix 8 (hoisted rotations per step): the same sum
+    memr, lvl4 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, sum_radix=8)
+    assert lvl4 == lvl2 and not np.array_equal(memr, memb)
+    assert np.abs(k.decrypt(memr[0], lvl4) - p.sum()).max() < 1e-2
 
 
 # ---------------------------------------------------------------------------
