@@ -105,6 +105,12 @@ typedef struct {
                                   1: the query is first dropped (limbs discarded) to the lowest level that
                                   still leaves the threshold depth and one output level above 0:
                                   2 + d2 with a Chebyshev degree, 2 without, capped at the top level */
+    uint32_t sum_radix;        /* RotateAndSum of the membership result (Algorithm 5's aggregation):
+                                  0 or 2: x <- x + Rot_{2^t}(x), one rotation per step (the paper's
+                                  power-of-two keys); r = 4, 8, ..., 64: x <- x + sum_{t<r} Rot_{t s}(x)
+                                  with s = 1, r, r^2, ..., the r-1 rotations of a step hoisted over one
+                                  ModUp (fewer, wider steps; keys t s, see fr_required_rotations). Same
+                                  total in every slot, other key-switch noise. */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.

@@ -120,6 +120,7 @@ struct fr_ctx {
     int host_threads = 1;
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query, 3 stored coefficients
+    int sum_radix = 2;                   // RotateAndSum radix (2: one rotation per step)
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::set<fr_db*> dbs;                // databases loaded and not yet freed
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
@@ -654,10 +655,39 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
 
 // RotateAndSum of B ciphertexts [B][2][cap][N] in place: ct <- ct + Rot_{2^t}(ct), t = 0..log2(n)-1
 void rotate_sum(fr_ctx* c, u64* ct, int cap, int level, int B = 1) {
-    // x <- x + Rot_{2^t}(x): the addition is the epilogue of each rotation's ModDown, writing
-    // into the other of two buffers
     const int n = c->R.N / 2, N = c->R.N;
     const size_t cw = (size_t)ctw(c, cap);
+    if (c->sum_radix > 2) {
+        // radix r: x <- x + sum_{t=1}^{rr-1} Rot_{t s}(x), s = 1, r, r^2, ..., rr = min(r, n / s).
+        // The rr-1 rotations of a ciphertext share one ModUp (hoisting); each lands in its slot
+        // of a per-ciphertext group [x, Rot_s(x), ..., Rot_{(rr-1)s}(x)] that one sum folds back
+        // into x. r = 2 is the loop below.
+        const int r = c->sum_radix;
+        Tmp grp(c, (size_t)B * r * cw);
+        for (long st = 1; st < n; st *= r) {
+            const int rr = (int)std::min<long>(r, n / st);
+            std::vector<KSReq> reqs;
+            for (int b = 0; b < B; ++b) {
+                const u64* src = ct + (size_t)b * cw;
+                u64* g0 = grp.p + (size_t)b * r * cw;
+                copy_d2d(c, g0, src, cw);
+                for (int t = 1; t < rr; ++t) {
+                    const u64 g = frh::galois_of_rotation(c->R, (long)t * st);
+                    reqs.push_back(KSReq{src + (size_t)cap * N, rot_key(c, g), (u32)g, 1, src, cap, g0 + (size_t)t * cw, cap});
+                }
+            }
+            keyswitch(c, level, reqs);
+            for (int b = 0; b < B; ++b) {
+                Prof p(c, "misc", 8.0 * N * 2.0 * (level + 1) * (rr + 1));
+                launch_sum(grp.p + (size_t)b * r * cw, cap, (long long)cw, rr, ct + (size_t)b * cw, cap, level, c->d_primes,
+                           N, c->cur);
+                c->launches++;
+            }
+        }
+        return;
+    }
+    // x <- x + Rot_{2^t}(x): the addition is the epilogue of each rotation's ModDown, writing
+    // into the other of two buffers
     Tmp r(c, (size_t)B * cw);
     u64* buf[2] = {ct, r.p};
     int cur = 0;
@@ -980,6 +1010,9 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         if (prm->level_mode > 1) raise(FR_ERR_INVALID_ARG, "level_mode must be 0 or 1");
         if (prm->db_tier > 3) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1, 2 or 3");
         c->db_tier = prm->db_tier;
+        c->sum_radix = prm->sum_radix ? (int)prm->sum_radix : 2;
+        if (c->sum_radix < 2 || c->sum_radix > 64 || (c->sum_radix & (c->sum_radix - 1)))
+            raise(FR_ERR_INVALID_ARG, "sum_radix must be 0 or a power of two in [2, 64]");
         c->work_level = c->R.nq - 1;
         if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->d2 : 0));
         if (prm->device < 0) {
@@ -1072,7 +1105,15 @@ fr_status fr_required_rotations(const fr_ctx* c, fr_mode mode, int32_t* out, siz
     return guard([&] {
         if (!c || !n) raise(FR_ERR_INVALID_ARG, "null argument");
         std::vector<long> v;
-        frh::rotation_set(c->ell, c->n1, (uint32_t)c->R.N / 2, frh::RV_ONDEMAND, mode == FR_MODE_MEMBERSHIP, v);
+        const bool radix = mode == FR_MODE_MEMBERSHIP && c->sum_radix > 2;
+        frh::rotation_set(c->ell, c->n1, (uint32_t)c->R.N / 2, frh::RV_ONDEMAND, mode == FR_MODE_MEMBERSHIP && !radix, v);
+        if (radix) {  // RotateAndSum in radix r: t s for t < r, s = 1, r, r^2, ...
+            std::set<long> all(v.begin(), v.end());
+            const long ns = c->R.N / 2;
+            for (long st = 1; st < ns; st *= c->sum_radix)
+                for (long t = 1; t < std::min<long>(c->sum_radix, ns / st); ++t) all.insert(t * st);
+            v.assign(all.begin(), all.end());
+        }
         *n = v.size();
         for (size_t i = 0; i < v.size() && i < cap && out; ++i) out[i] = (int32_t)v[i];
     });
