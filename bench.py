@@ -450,8 +450,8 @@ def run_encrypted(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
-    cfg = "membership"
-    c = W.CONFIGS[cfg]
+    cfg = dict(W.CONFIGS["membership"], ell=args.db_ell)   # --db-ell: a smaller case for profiling
+    c = cfg
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
     # with the negative giant-step keys of the server-side pre-rotation variant
     rots = set(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP))
@@ -521,7 +521,8 @@ def run_encrypted(args):
         "value": K / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "ms_per_step": ms,
         "higher_is_better": True, "dtype": "u64",
         "data": "synthetic (seeded Gaussian L2-normalised templates, 32 near-duplicates at cosine 0.8)",
-        "config": {"workload": "encrypted DB N=2^16 K=2^15 ell=512 n1=%d deg59 work level %d" % (c["n1"], ctx.work_level),
+        "config": {"workload": "encrypted DB N=2^16 K=2^15 ell=%d n1=%d deg59 work level %d" % (c["ell"], c["n1"],
+                                                                                                 ctx.work_level),
                    "storage_tier": db.info()["tier"], "db_bytes": db.info()["bytes"]},
         "form": "CUDA graph replay, inputs resident",
         "batched": {"queries": B, "ms_per_pass": ms_b, "value": B * K / (ms_b / 1000.0), "unit": UNIT},
@@ -882,7 +883,7 @@ def main():
     ap.add_argument("--no-full-chain", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the table-schedule comparison")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
-    ap.add_argument("--sum-radix", type=int, default=8, choices=[2, 4, 8, 16, 32],
+    ap.add_argument("--sum-radix", type=int, default=4, choices=[2, 4, 8, 16, 32],
                     help="RotateAndSum radix of the membership result (2: one rotation per step)")
     ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")
     ap.add_argument("--serving", action="store_true", help="run the serving-loop workload instead")
@@ -897,6 +898,7 @@ def main():
     ap.add_argument("--identify-tier", type=int, default=2, choices=[0, 1, 2, 3])
     ap.add_argument("--encrypted-db", action="store_true",
                     help="run the encrypted-database membership workload instead")
+    ap.add_argument("--db-ell", type=int, default=512, help="template dimension of --encrypted-db (512: the workload)")
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
