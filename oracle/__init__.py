@@ -121,7 +121,9 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+                           C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+    L.or_bsgs_scores_hoisted.restype = C.c_int
+    L.or_bsgs_scores_hoisted.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_table_scores.restype = C.c_int
     L.or_table_scores.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_encrypt_db.argtypes = [vp, vp, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, u64p]
@@ -338,16 +340,17 @@ class Keys:
             raise ValueError("radix must be a power of two")
         return x
 
-    def bsgs_scores(self, qct, T, ell, n1, level=None):
-        """Scores at level-1 of a query ct at `level` (default: the top level)."""
+    def bsgs_scores(self, qct, T, ell, n1, level=None, hoist=False):
+        """Scores at level-1 of a query ct at `level` (default: the top level); hoist: the giant
+        steps of a group share one ModDown."""
         c = self.ctx
         level = c.top if level is None else level
         T = np.ascontiguousarray(T, dtype=np.float32)
         K = T.shape[0]
         G = (K + c.n - 1) // c.n
         out = np.empty((G, 2, level, c.N), dtype=np.uint64)
-        r = self.L.or_bsgs_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, T, K, ell, n1,
-                                  out)
+        fn = self.L.or_bsgs_scores_hoisted if hoist else self.L.or_bsgs_scores
+        r = fn(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, T, K, ell, n1, out)
         if r < 0:
             raise ValueError("bad BSGS parameters")
         return out
@@ -403,7 +406,7 @@ class Keys:
             raise ValueError("bad parameters")
         return out
 
-    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2):
+    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2, hoist=False):
         """Full match of a top-level query ct, computed at working level `level` (default: top);
         schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table."""
         c = self.ctx
@@ -415,7 +418,8 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
-                            int(cheb_n), float(tau), int(schedule), int(sum_radix), out, C.byref(lvl))
+                            int(cheb_n), float(tau), int(schedule), int(sum_radix), 1 if hoist else 0, out,
+                            C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

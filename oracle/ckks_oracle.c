@@ -1348,6 +1348,68 @@ int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, con
     return or_bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, out);
 }
 
+/* On-demand BSGS whose giant-step key switches of one group share a single ModDown (double
+ * hoisting after Bossuat et al., Section "Hoisting and double hoisting"): with P_j the
+ * rescaled giant-step products at level l = L-1 and IP0_j, IP1_j the inner products of
+ * ModUp(P_j.a) under the automorphism of Rot_{j n1} with its key (in Q_l u P, evaluation form),
+ *   S_k = P_0 + (sum_{j>=1} sigma_j(P_j.b) + ModDown(sum_{j>=1} IP0_j), ModDown(sum_{j>=1} IP1_j)).
+ * With one giant rotation (n2 = 2) this is P_0 + Rot_{n1}(P_1) itself. */
+int or_bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                           int n1, u64* out) {
+    int N = c->n, n = N / 2;
+    if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
+    int n2 = (ell + n1 - 1) / n1;
+    long G = (K + n - 1) / n;
+    int l = L - 1, npos = l + 1 + c->np, beta = beta_at(c, l);
+    size_t cw = ct_words(c, L), cw1 = ct_words(c, l), ew = (size_t)npos * N;
+    long* rots = (long*)malloc(sizeof(long) * n1);
+    for (int i = 0; i < n1; i++) rots[i] = i;
+    u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
+    or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
+    for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
+    u64* P = (u64*)malloc(sizeof(u64) * cw1);
+    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * ew);
+    u64* evk = (u64*)malloc(sizeof(u64) * evk_words(c));
+    u64* a0 = (u64*)malloc(sizeof(u64) * ew);
+    u64* a1 = (u64*)malloc(sizeof(u64) * ew);
+    u64* s0 = (u64*)malloc(sizeof(u64) * ew);
+    u64* s1 = (u64*)malloc(sizeof(u64) * ew);
+    u64* t = (u64*)malloc(sizeof(u64) * N);
+    u64* md = (u64*)malloc(sizeof(u64) * cw1);
+    for (long g = 0; g < G; g++) {
+        u64* S = out + (size_t)g * cw1;
+        or_giant_step(c, babies, L, n1, T, K, ell, g, 0, S);
+        memset(s0, 0, sizeof(u64) * ew);
+        memset(s1, 0, sizeof(u64) * ew);
+        for (int j = 1; j < n2; j++) {
+            or_giant_step(c, babies, L, n1, T, K, ell, g, j, P);
+            u64 gk = or_galois(c, (long)j * n1);
+            modup(c, P + (size_t)(l + 1) * N, l, ext);
+            or_make_evk(c, k, 0, gk, evk);
+            keyswitch_ip(c, ext, l, evk, gk, a0, a1);
+            for (int pos = 0; pos < npos; pos++) {
+                u64 q = c->p[ext_limb(c, l, pos)];
+                for (int x = 0; x < N; x++) {
+                    s0[(size_t)pos * N + x] = madd(s0[(size_t)pos * N + x], a0[(size_t)pos * N + x], q);
+                    s1[(size_t)pos * N + x] = madd(s1[(size_t)pos * N + x], a1[(size_t)pos * N + x], q);
+                }
+            }
+            for (int i = 0; i <= l; i++) {   /* sigma_j(P_j.b), coefficient form */
+                u64 q = c->p[i];
+                automorph_coef(c, gk, q, P + (size_t)i * N, t);
+                for (int x = 0; x < N; x++) S[(size_t)i * N + x] = madd(S[(size_t)i * N + x], t[x], q);
+            }
+        }
+        if (n2 > 1) {
+            moddown(c, s0, l, md);
+            moddown(c, s1, l, md + (size_t)(l + 1) * N);
+            or_add(c, S, md, l, S);
+        }
+    }
+    free(rots); free(babies); free(P); free(ext); free(evk); free(a0); free(a1); free(s0); free(s1); free(t); free(md);
+    return (int)G;
+}
+
 /* Sum over the ell diagonals of a table of rotated queries (Eq. equ:diagbsgsgroupsprecomp):
  * S_g = Rescale(sum_{i < ell} rotQ[i] (.) diag_i(M_g)), plain (not pre-rotated) diagonals.
  * rotQ: [ell][2][L+1][N] evaluation form at level L; out: [G][2][L][N] at level L-1. */
@@ -1465,12 +1527,13 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
 
 /* Full match (Algorithms 5 and 6). The top-level query is first dropped to the
  * working level lq (lq = top: the whole chain). schedule 0: on-demand BSGS with
- * pre-rotated diagonals; schedule 1: the rotated-query table of Algorithm 1. mode 0: scores (G cts, level
+ * pre-rotated diagonals (hoist: the giant steps of a group share one ModDown); schedule 1: the
+ * rotated-query table of Algorithm 1. mode 0: scores (G cts, level
  * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
  * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, int schedule, int sum_radix, u64* out, int* out_level) {
+             int cheb_n, double tau, int schedule, int sum_radix, int hoist, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
@@ -1478,6 +1541,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     or_drop(c, qct, top, lq, q);
     if (mode == 0) {
         int r = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, out)
+                : hoist       ? or_bsgs_scores_hoisted(c, k, q, lq, T, K, ell, n1, out)
                               : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, out);
         *out_level = lq - 1;
         free(q);
@@ -1488,6 +1552,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     if (d1 != 2 || lq - 1 - d2 < 0) { free(q); return -1; }
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
     int rs = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, S)
+             : hoist       ? or_bsgs_scores_hoisted(c, k, q, lq, T, K, ell, n1, S)
                            : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);

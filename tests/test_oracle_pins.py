@@ -413,6 +413,26 @@ def test_bsgs_special_cases(c1, k1):
     assert np.abs(got[:ell] - Tsq.astype(np.float64) @ q).max() < 1e-4
 
 
+def test_giant_steps_with_one_moddown(c1, k1):
+    """Double hoisting of the giant steps (one ModDown per group over the summed inner
+    products): the FP64 matvec again; with a single giant rotation (n2 = 2) it is the rotation
+    itself, bit for bit; with more, other bits (ModDown is linear only up to its rounding)."""
+    K, ell = 64, 64
+    T = _templates(K, ell, 0xF00D0009)
+    rng = np.random.default_rng(22)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k1.encrypt(np.tile(q, c1.n // ell), 24)
+    ref = T.astype(np.float64) @ q
+    for n1 in (8, 5):
+        S = k1.bsgs_scores(qct, T, ell, n1, hoist=True)
+        got = k1.decrypt(S[0], 1)
+        assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+        assert not np.array_equal(S, k1.bsgs_scores(qct, T, ell, n1))
+    assert np.array_equal(k1.bsgs_scores(qct, T, ell, 32, hoist=True), k1.bsgs_scores(qct, T, ell, 32))
+    assert np.array_equal(k1.bsgs_scores(qct, T, ell, 64, hoist=True), k1.bsgs_scores(qct, T, ell, 64))
+
+
 def test_table_schedule_matches_plain_matvec(c1, k1):
     """Algorithm 1 (rotated-query table): decrypts to the FP64 matvec for any n1; with
     n1 = l (babies only) or n1 = 1 (giant rotations of q only) every table entry is one
@@ -468,6 +488,9 @@ def test_multi_group_packing():
     assert S.shape[0] == 3
     ref = T.astype(np.float64) @ q
     got = np.concatenate([k.decrypt(S[g], 1) for g in range(3)])
+    assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+    Sh = k.bsgs_scores(qct, T, ell, 4, hoist=True)       # one ModDown per group
+    got = np.concatenate([k.decrypt(Sh[g], 1) for g in range(3)])
     assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
 
 
@@ -572,6 +595,10 @@ def test_match_modes_small():
     memr, lvl4 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, sum_radix=8)
     assert lvl4 == lvl2 and not np.array_equal(memr, memb)
     assert np.abs(k.decrypt(memr[0], lvl4) - p.sum()).max() < 1e-2
+    # giant steps sharing one ModDown per group: the same sum
+    memh, lvl5 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, hoist=True)
+    assert lvl5 == lvl2 and not np.array_equal(memh, memb)
+    assert np.abs(k.decrypt(memh[0], lvl5) - p.sum()).max() < 1e-2
 
 
 # ---------------------------------------------------------------------------
