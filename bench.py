@@ -198,7 +198,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
     Ts = W.serving_databases(c["ell"])
@@ -292,7 +292,7 @@ def run_identify(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, db_tier=args.identify_tier,
-                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_IDENTIFY), W.key_seed(cfg))
     ctx.load_keys(keys)
     db = ctx.load_db(T)
@@ -365,7 +365,7 @@ def run_multi(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
     sizes = W.multi_sizes(args.multi_n)
@@ -452,7 +452,7 @@ def run_encrypted(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cfg = dict(W.CONFIGS["membership"], ell=args.db_ell)   # --db-ell: a smaller case for profiling
     c = cfg
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
     # with the negative giant-step keys of the server-side pre-rotation variant
     rots = set(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP))
     rots |= set(fr.rotation_set(c["ell"], c["n1"], ctx.n, fr.FR_KEYS_TBS_TOTAL, True))
@@ -651,7 +651,7 @@ def run_ours(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     t0 = time.perf_counter()
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
     rots = ctx.required_rotations(mode)
     keys = ctx.keygen(rots, W.key_seed(cfg))
     t_keygen = time.perf_counter() - t0
@@ -775,7 +775,7 @@ def run_ours(args):
     # the same query on the whole modulus chain (no level drop), for comparison
     full = None
     if args.level_mode == 1 and not args.no_full_chain and lq < len(c["q_bits"]) - 1:
-        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix)
+        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
         ctx_f.load_keys(keys)
         db_f = ctx_f.load_db(T)
         dq_f = ctx_f.encrypt(keys, q, W.enc_seed(cfg)).upload()
@@ -801,7 +801,7 @@ def run_ours(args):
     table = None
     if not args.no_table:
         ctx_t = fr.Context(device=local, cuda_stream=stream.cuda_stream, schedule=1,
-                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix)
+                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
         ctx_t.load_keys(keys)
         db_t = ctx_t.load_db(T)
         dq_t = ctx_t.encrypt(keys, q, W.enc_seed(cfg)).upload()
@@ -844,6 +844,7 @@ def run_ours(args):
             "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": K, "log_n": c["log_n"],
                        "q_limbs": len(c["q_bits"]), "p_limbs": len(c["p_bits"]), "dnum": c["dnum"],
                        "work_level": lq, "level_mode": args.level_mode, "sum_radix": args.sum_radix,
+                       "hoist_giants": args.hoist_giants,
                        "parallelism": f"replicas x{ws}",
                        "l2": "working set (diagonals + evaluation keys, several GB) exceeds the 129 MB L2; no flush"},
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99)),
@@ -883,6 +884,8 @@ def main():
     ap.add_argument("--no-full-chain", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the table-schedule comparison")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--hoist-giants", type=int, default=1, choices=[0, 1],
+                    help="giant steps of a (query, group) share one ModDown (0: one per rotation)")
     ap.add_argument("--sum-radix", type=int, default=4, choices=[2, 4, 8, 16, 32],
                     help="RotateAndSum radix of the membership result (2: one rotation per step)")
     ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")

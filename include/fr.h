@@ -111,6 +111,11 @@ typedef struct {
                                   with s = 1, r, r^2, ..., the r-1 rotations of a step hoisted over one
                                   ModUp (fewer, wider steps; keys t s, see fr_required_rotations). Same
                                   total in every slot, other key-switch noise. */
+    uint32_t hoist_giants;     /* on-demand schedule: 0 one ModDown per giant-step rotation (the rotations
+                                  of Algorithms 5 and 6 as written); 1 the giant steps of a (query, group)
+                                  share one ModDown: their inner products are summed in Q_l u P and
+                                  S = P_0 + sum_j sigma_j(P_j.b) + ModDown(sum_j IP_j) (double hoisting,
+                                  Section "Hoisting and double hoisting"). Same values, other noise. */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.

@@ -131,10 +131,11 @@ def _declare(L):
     L.or_enc_giant_step.restype = C.c_int
     L.or_enc_giant_step.argtypes = [vp, vp, u64p, C.c_int, C.c_int, u64p, C.c_int, C.c_int, C.c_int, u64p]
     L.or_enc_bsgs_scores.restype = C.c_int
-    L.or_enc_bsgs_scores.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, u64p]
+    L.or_enc_bsgs_scores.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int,
+                                     u64p]
     L.or_match_enc.restype = C.c_int
     L.or_match_enc.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
-                               C.c_double, C.c_int, u64p, C.POINTER(C.c_int)]
+                               C.c_double, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_rotate_sum_radix.restype = C.c_int
     L.or_rotate_sum_radix.argtypes = [vp, vp, u64p, C.c_int, C.c_int, C.c_int]
     L.or_set_threads.argtypes = [C.c_int]
@@ -448,7 +449,7 @@ class Keys:
         self.L.or_prerotate_db(c.h, self.h, E, el, G, ell, n1, int(level), out)
         return out
 
-    def enc_scores(self, qct, E, n1, level=None):
+    def enc_scores(self, qct, E, n1, level=None, hoist=False):
         """Scores at level-1 of a query ct at `level` (default: top) against encrypted diagonals E."""
         c = self.ctx
         level = c.top if level is None else level
@@ -456,12 +457,12 @@ class Keys:
         G, ell, el = E.shape[0], E.shape[1], E.shape[3] - 1
         out = np.empty((G, 2, level, c.N), dtype=np.uint64)
         r = self.L.or_enc_bsgs_scores(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), level, E, el, G, ell,
-                                      n1, out)
+                                      n1, 1 if hoist else 0, out)
         if r < 0:
             raise ValueError("bad arguments")
         return out
 
-    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None, sum_radix=2):
+    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None, sum_radix=2, hoist=False):
         """Full match of a top-level query ct against encrypted diagonals E, at working level
         `level` (default: top); returns (outputs, their level)."""
         c = self.ctx
@@ -472,7 +473,8 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)
         lvl = C.c_int(0)
         r = self.L.or_match_enc(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, E, el, int(K), ell,
-                                n1, mode, int(cheb_n), float(tau), int(sum_radix), out, C.byref(lvl))
+                                n1, mode, int(cheb_n), float(tau), int(sum_radix), 1 if hoist else 0, out,
+                                C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

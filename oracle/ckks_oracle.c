@@ -1662,10 +1662,51 @@ int or_enc_giant_step(const or_ctx* c, or_keys* k, const u64* babies, int L, int
     return 0;
 }
 
+/* S += sum_{j>=1} Rot_{j n1}(P_j) with one ModDown for all j (the double-hoisted giant steps of
+ * or_bsgs_scores_hoisted): Ps holds P_1 .. P_{n2-1} at level l, coefficient form. */
+static void giant_sum_hoisted(const or_ctx* c, const or_keys* k, u64* S, const u64* Ps, int n2, int n1, int l) {
+    int N = c->n, npos = l + 1 + c->np, beta = beta_at(c, l);
+    size_t cw1 = ct_words(c, l), ew = (size_t)npos * N;
+    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * ew);
+    u64* evk = (u64*)malloc(sizeof(u64) * evk_words(c));
+    u64* a0 = (u64*)malloc(sizeof(u64) * ew);
+    u64* a1 = (u64*)malloc(sizeof(u64) * ew);
+    u64* s0 = (u64*)calloc(ew, sizeof(u64));
+    u64* s1 = (u64*)calloc(ew, sizeof(u64));
+    u64* t = (u64*)malloc(sizeof(u64) * N);
+    u64* md = (u64*)malloc(sizeof(u64) * cw1);
+    for (int j = 1; j < n2; j++) {
+        const u64* P = Ps + (size_t)(j - 1) * cw1;
+        u64 gk = or_galois(c, (long)j * n1);
+        modup(c, P + (size_t)(l + 1) * N, l, ext);
+        or_make_evk(c, k, 0, gk, evk);
+        keyswitch_ip(c, ext, l, evk, gk, a0, a1);
+        for (int pos = 0; pos < npos; pos++) {
+            u64 q = c->p[ext_limb(c, l, pos)];
+            for (int x = 0; x < N; x++) {
+                s0[(size_t)pos * N + x] = madd(s0[(size_t)pos * N + x], a0[(size_t)pos * N + x], q);
+                s1[(size_t)pos * N + x] = madd(s1[(size_t)pos * N + x], a1[(size_t)pos * N + x], q);
+            }
+        }
+        for (int i = 0; i <= l; i++) {
+            u64 q = c->p[i];
+            automorph_coef(c, gk, q, P + (size_t)i * N, t);
+            for (int x = 0; x < N; x++) S[(size_t)i * N + x] = madd(S[(size_t)i * N + x], t[x], q);
+        }
+    }
+    if (n2 > 1) {
+        moddown(c, s0, l, md);
+        moddown(c, s1, l, md + (size_t)(l + 1) * N);
+        or_add(c, S, md, l, S);
+    }
+    free(ext); free(evk); free(a0); free(a1); free(s0); free(s1); free(t); free(md);
+}
+
 /* On-demand BSGS over an encrypted database ([G][ell][2][el+1][N]); the query ct is at level L,
- * scores come out at level L-1 ([G][2][L][N]). */
+ * scores come out at level L-1 ([G][2][L][N]); hoist: the giant steps of a group share one
+ * ModDown. */
 int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const u64* E, int el, long G, int ell,
-                       int n1, u64* out) {
+                       int n1, int hoist, u64* out) {
     int n = c->n / 2;
     if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1 || el < L) return -1;
     int n2 = (ell + n1 - 1) / n1;
@@ -1677,9 +1718,17 @@ int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const
     for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
     u64* P = (u64*)malloc(sizeof(u64) * cw1);
     u64* R = (u64*)malloc(sizeof(u64) * cw1);
+    u64* Ps = hoist ? (u64*)malloc(sizeof(u64) * cw1 * (n2 > 1 ? n2 - 1 : 1)) : NULL;
     for (long g = 0; g < G; g++) {
         u64* S = out + (size_t)g * cw1;
         memset(S, 0, sizeof(u64) * cw1);
+        if (hoist) {
+            or_enc_giant_step(c, k, babies, L, n1, E + (size_t)g * ell * ew, el, ell, 0, S);
+            for (int j = 1; j < n2; j++)
+                or_enc_giant_step(c, k, babies, L, n1, E + (size_t)g * ell * ew, el, ell, j, Ps + (size_t)(j - 1) * cw1);
+            giant_sum_hoisted(c, k, S, Ps, n2, n1, L - 1);
+            continue;
+        }
         for (int j = 0; j < n2; j++) {
             or_enc_giant_step(c, k, babies, L, n1, E + (size_t)g * ell * ew, el, ell, j, P);
             if (j > 0) {
@@ -1690,26 +1739,26 @@ int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const
             }
         }
     }
-    free(rots); free(babies); free(P); free(R);
+    free(rots); free(babies); free(P); free(R); free(Ps);
     return (int)G;
 }
 
 /* Full match against an encrypted database at level el (>= lq); modes as in or_match. */
 int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64* E, int el, long K, int ell, int n1,
-                 int mode, int cheb_n, double tau, int sum_radix, u64* out, int* out_level) {
+                 int mode, int cheb_n, double tau, int sum_radix, int hoist, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top || el < lq) return -1;
     long G = (K + n - 1) / n;
     u64* q = (u64*)malloc(sizeof(u64) * ct_words(c, top));
     or_drop(c, qct, top, lq, q);
     if (mode == 0) {
-        int r = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, out);
+        int r = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, hoist, out);
         *out_level = lq - 1;
         free(q);
         return r;
     }
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
-    int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, S);
+    int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, hoist, S);
     free(q);
     if (rs < 0) { free(S); return -1; }
     int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, sum_radix, out, out_level);

@@ -364,6 +364,42 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 }
 
 // ---------------------------------------------------------------------------
+// Sums of rotations sharing one ModDown (double hoisting after Bossuat et al.): the inner
+// products IP_j of the rotations summed into one accumulator per sum, in Q_l u P, together
+// with P sigma_j(b_j) on the Q positions of component 0. ModDown then returns
+// sum_j sigma_j(b_j) + ModDown(sum_j IP_j): (x + P y - conv(x_P)) P^-1 = ModDown(x) + y
+// exactly, since the P positions of P y are zero.
+// One thread per (component, position, point); the jobs of one sum are applied in order, so
+// accumulators are never written by two threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_giant_acc(const AccJobs jobs, u64* __restrict__ outs, int npos,
+                                                        int level, const DevPrime* __restrict__ primes, int pbase,
+                                                        const u64* __restrict__ pmod, const u64* __restrict__ pmod_s,
+                                                        int logN) {
+    pdl_wait();
+    pdl_trigger();
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y, t = blockIdx.z;
+    if (k >= N) return;
+    const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
+    const u64 q = primes[pi].q;
+    const long long off = ((long long)t * npos + pos) * N + k;
+    const bool addb = t == 0 && pos <= level;
+    const u64 pm = addb ? pmod[pos] : 0, pms = addb ? pmod_s[pos] : 0;
+    for (int j = 0; j < jobs.n; ++j) {
+        const AccJob& J = jobs.j[j];
+        u64* o = outs + (long long)J.dst * 2 * npos * N + off;
+        u64 v = add_mod(*o, J.acc[off], q);
+        if (addb) {
+            const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
+            v = add_mod(v, mul_shoup(J.b[(long long)pos * N + src], pm, pms, q), q);
+        }
+        *o = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Encrypted-database MAC (ct x ct with lazy relinearisation, the paper's setting of
 // Section 5.3): for every giant step j, pointwise per limb,
 //   (d0, d1, d2)_j = sum_{i < n1, j n1 + i < ell} B_i (x) E_{j n1 + i}
@@ -809,6 +845,13 @@ void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags
         case 4: launch_mac_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
         default: break;  // the engine splits larger batches
     }
+}
+
+void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const DevPrime* primes, int pbase,
+                      const u64* pmod, const u64* pmod_s, int logN, cudaStream_t s) {
+    const int N = 1 << logN;
+    dim3 g((N + kThreads - 1) / kThreads, npos, 2);
+    launch_k(k_giant_acc, g, dim3(kThreads), 0, s, jobs, outs, npos, level, primes, pbase, pmod, pmod_s, logN);
 }
 
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,

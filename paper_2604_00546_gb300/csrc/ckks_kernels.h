@@ -74,6 +74,14 @@ struct IPJobs {
     int ngroups;
 };
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
+// One inner product folded into the accumulator of its sum of rotations (double hoisting).
+struct AccJob {
+    const u64* acc;  // [2][npos][N] inner product (evaluation form)
+    const u64* b;    // c0 of the rotated ciphertext, limbs 0..level (stride N)
+    u32 galois;
+    int dst;         // accumulator index
+};
+struct AccJobs { AccJob j[FR_MAX_JOBS]; int n; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
 // Forward NTT that stores its values in Montgomery form (x 2^64 mod q), in place.
@@ -103,6 +111,10 @@ void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out
                             int l, int N, int BT, cudaStream_t s);
 void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s);
 // B <= 4 queries: babies of query b at babies + b * baby_q, outputs at out + b * out_q
+// Sums of rotations with one ModDown (double hoisting): for each job, outs[dst] += acc and,
+// on the Q positions of component 0, += P sigma_g(b). outs: [ndst][2][npos][N].
+void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const DevPrime* primes, int pbase,
+                      const u64* pmod, const u64* pmod_s, int logN, cudaStream_t s);
 // Encrypted-database MAC: (d0, d1, d2)_j = sum_i B_i (x) E_{j n1 + i} for every giant step j.
 // babies [n1][2][cap_b][N]; diags [ell][2][nl][N] (evaluation form, Montgomery); out [n2][3][cap_o][N].
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,

@@ -104,6 +104,7 @@ struct fr_ctx {
     P2QTab* d_p2q = nullptr;
     std::vector<RescaleTab*> d_rescale;  // per level (index level), level >= 1
     u64 *d_pinv = nullptr, *d_pinv_s = nullptr;
+    u64 *d_pmod = nullptr, *d_pmod_s = nullptr;  // [P]_{q_i} and Shoup quotients, Q primes
     u64* d_delta = nullptr;              // Delta mod q_i
     std::map<int, u64*> d_cheb;          // per input level: leaf constants [3][nleaves][level+1]
     std::vector<std::pair<double, double>> leaves;  // Chebyshev leaves (c0, c1), BFS order
@@ -121,6 +122,7 @@ struct fr_ctx {
     bool use_graphs = true;              // replay fr_match as a CUDA graph after its first call
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query, 3 stored coefficients
     int sum_radix = 2;                   // RotateAndSum radix (2: one rotation per step)
+    bool hoist_giants = false;           // giant steps of a group share one ModDown
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::set<fr_db*> dbs;                // databases loaded and not yet freed
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
@@ -277,6 +279,7 @@ struct KSReq {
     u64* out;
     int out_cap;
     const u64* add2 = nullptr;  // mode 3
+    int sum_dst = -1;           // keyswitch_sums: index of the sum the rotation belongs to
 };
 
 // inner product + ModDown of up to FR_MAX_JOBS jobs; job j reads its ModUp output ext[j].
@@ -349,9 +352,8 @@ void ks_finish(fr_ctx* c, int level, const std::vector<const KSReq*>& reqs, cons
 // input polynomial share one ModUp (hoisting, Algorithm 1 step 1); the others
 // get one each. Inputs are processed in groups of up to 16, their jobs sorted by
 // key so that each key is read once per inner-product launch.
-void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs) {
-    if (reqs.empty()) return;
-    if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
+template <class F>
+void modup_chunks(fr_ctx* c, int level, const std::vector<KSReq>& reqs, F finish) {
     const int N = c->R.N;
     const int npos = level + 1 + c->R.np, beta = c->R.digits_at(level);
     const size_t L1N = (size_t)(level + 1) * N;
@@ -394,8 +396,95 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs) {
                 rq.push_back(&reqs[js[t]]);
                 ex.push_back(ext.p + (size_t)(in_of[js[t]] - (int)u0) * beta * npos * N);
             }
-            ks_finish(c, level, rq, ex);
+            finish(rq, ex);
         }
+    }
+}
+
+void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs) {
+    if (reqs.empty()) return;
+    if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
+    modup_chunks(c, level, reqs,
+                 [&](const std::vector<const KSReq*>& rq, const std::vector<const u64*>& ex) { ks_finish(c, level, rq, ex); });
+}
+
+// Sums of rotations that share one ModDown per sum (double hoisting after Bossuat et al.):
+// out[o] = base[o] + sum over the requests r with r.sum_dst = o of Rot(r), where a request is
+// a rotation (mode 1: r.c the a part, r.add its b part, r.galois, r.key). Every request gets
+// its own ModUp (hoisted where inputs repeat) and inner product; the inner products of a sum
+// and P sigma(b) are folded into one accumulator in Q_l u P (k_giant_acc), and one ModDown
+// with base[o] as its addend ends the sum: base + sum_r sigma_r(b_r) + ModDown(sum_r IP_r).
+void keyswitch_sums(fr_ctx* c, int level, const std::vector<KSReq>& reqs, const std::vector<const u64*>& base,
+                    int base_cap, const std::vector<u64*>& out, int out_cap) {
+    if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
+    const int N = c->R.N, np = c->R.np, nq = c->R.nq;
+    const int npos = level + 1 + np, beta = c->R.digits_at(level);
+    const int ndst = (int)out.size();
+    const size_t aw = (size_t)2 * npos * N;
+    Tmp accs(c, (size_t)ndst * aw);
+    CU(cudaMemsetAsync(accs.p, 0, (size_t)ndst * aw * 8, c->cur));
+    const int pbase = nq;
+    modup_chunks(c, level, reqs, [&](const std::vector<const KSReq*>& rq, const std::vector<const u64*>& ex) {
+        const int nj = (int)rq.size();
+        Tmp acc(c, (size_t)nj * aw);
+        IPJobs ij;
+        ij.ngroups = 0;
+        for (int j = 0; j < nj; ++j) {
+            ij.j[j] = IPJob{ex[j], rq[j]->key, acc.p + (size_t)j * aw, rq[j]->galois, 0};
+            if (j == 0 || rq[j]->key != rq[j - 1]->key) {
+                ij.gkey[ij.ngroups] = rq[j]->key;
+                ij.gstart[ij.ngroups] = j;
+                ij.ngroups++;
+            }
+        }
+        ij.gstart[ij.ngroups] = nj;
+        {
+            Prof p(c, "ip", 8.0 * N * npos * (ij.ngroups * 2.0 * beta + nj * (double)beta + nj * 2.0));
+            launch_ip(ij, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, level), c->R.logN,
+                      c->cur);
+            c->launches++;
+        }
+        AccJobs aj;
+        aj.n = nj;
+        for (int j = 0; j < nj; ++j) {
+            if (rq[j]->sum_dst < 0 || rq[j]->sum_dst >= ndst) raise(FR_ERR_INTERNAL, "sum index out of range");
+            aj.j[j] = AccJob{acc.p + (size_t)j * aw, rq[j]->add, rq[j]->galois, rq[j]->sum_dst};
+        }
+        Prof p(c, "misc", 8.0 * N * (nj * (aw / N + (double)(level + 1)) + 2.0 * ndst * (aw / N)));
+        launch_giant_acc(aj, accs.p, npos, level, c->d_primes, pbase, c->d_pmod, c->d_pmod_s, c->R.logN, c->cur);
+        c->launches++;
+    });
+    // one ModDown per sum: P limbs to coefficients, P -> Q conversion, forward NTT + combine
+    PrimeMap pmP{};
+    pmP.period = np;
+    for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
+    ntt(c, accs.p + (size_t)(level + 1) * N, (long long)npos * N, np, ndst * 2 * np, pmP, true);
+    Tmp conv(c, (size_t)ndst * 2 * (level + 1) * N);
+    {
+        Prof p(c, "moddown", 8.0 * N * ndst * 2.0 * (np + level + 1));
+        launch_p2q(accs.p, (long long)aw, npos, level, conv.p, c->d_p2q, N, ndst, c->cur);
+        c->launches++;
+    }
+    for (int o0 = 0; o0 < ndst; o0 += FR_MAX_JOBS) {
+        const int no = std::min(FR_MAX_JOBS, ndst - o0);
+        MDJobs md;
+        for (int o = 0; o < no; ++o) {
+            MDJob& m = md.j[o];
+            m.acc = accs.p + (size_t)(o0 + o) * aw;
+            m.conv = conv.p + (size_t)(o0 + o) * 2 * (level + 1) * N;
+            m.add = base[o0 + o];
+            m.add_cap = base_cap;
+            m.out = out[o0 + o];
+            m.out_cap = out_cap;
+            m.mode = 2;
+            m.galois = 1;
+            m.add2 = nullptr;
+        }
+        Prof p(c, "ntt", 16.0 * no * 2 * (level + 1) * N);
+        PolyBatch pb{conv.p + (size_t)o0 * 2 * (level + 1) * N, (long long)(level + 1) * N, level + 1,
+                     no * 2 * (level + 1), pm_level(level)};
+        launch_ntt_moddown(c->rd, pb, md, npos, level, c->d_pinv, c->d_pinv_s, c->cur);
+        c->launches += 2;
     }
 }
 
@@ -897,7 +986,7 @@ void build_tables(fr_ctx* c) {
         std::vector<int> src;
         for (int j = 0; j < R.np; ++j) src.push_back(R.nq + j);
         for (int j = 0; j < R.np; ++j) t.pq[j] = R.primes[R.nq + j];
-        std::vector<u64> pinv(R.nq), pinv_s(R.nq);
+        std::vector<u64> pinv(R.nq), pinv_s(R.nq), pmod(R.nq), pmod_s(R.nq);
         for (int i = 0; i < R.nq; ++i) {
             t.qq[i] = R.primes[i];
             std::vector<u64> ih, ht;
@@ -913,10 +1002,14 @@ void build_tables(fr_ctx* c) {
             for (int j = 0; j < R.np; ++j) P = frh::mulm(P, t.pq[j] % R.primes[i], R.primes[i]);
             pinv[i] = frh::invm(P, R.primes[i]);
             pinv_s[i] = frh::shoup_quot(pinv[i], R.primes[i]);
+            pmod[i] = P;
+            pmod_s[i] = frh::shoup_quot(P, R.primes[i]);
         }
         c->d_p2q = upload_persistent(c, &t, 1);
         c->d_pinv = upload_persistent(c, pinv.data(), pinv.size());
         c->d_pinv_s = upload_persistent(c, pinv_s.data(), pinv_s.size());
+        c->d_pmod = upload_persistent(c, pmod.data(), pmod.size());
+        c->d_pmod_s = upload_persistent(c, pmod_s.data(), pmod_s.size());
     }
     // rescale tables
     c->d_rescale.assign(R.nq, nullptr);
@@ -1011,6 +1104,8 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         if (prm->db_tier > 3) raise(FR_ERR_INVALID_ARG, "db_tier must be 0, 1, 2 or 3");
         c->db_tier = prm->db_tier;
         c->sum_radix = prm->sum_radix ? (int)prm->sum_radix : 2;
+        if (prm->hoist_giants > 1) raise(FR_ERR_INVALID_ARG, "hoist_giants must be 0 or 1");
+        c->hoist_giants = prm->hoist_giants == 1;
         if (c->sum_radix < 2 || c->sum_radix > 64 || (c->sum_radix & (c->sum_radix - 1)))
             raise(FR_ERR_INVALID_ARG, "sum_radix must be 0 or a power of two in [2, 64]");
         c->work_level = c->R.nq - 1;
@@ -1803,6 +1898,30 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             Tmp Gs(c, (size_t)nb * n2 * cw);  // [nb][n2][2][L][N]
             rescale(c, Pj.p, nb * n2, L, L1, Gs.p, L);
             stage.reset(new Prof(c, "stage:giants"));
+            if (n2 > 1 && c->hoist_giants) {
+                // S = P_0 + sum_j Rot_{j n1}(P_j) with one ModDown per (query, group)
+                std::vector<KSReq> reqs;
+                std::vector<const u64*> base;
+                std::vector<u64*> outp;
+                for (int t = 0; t < nb; ++t) {
+                    base.push_back(Gs.p + (size_t)t * n2 * cw);
+                    outp.push_back(S + ((size_t)P.soff[qs[sel[s0 + t]]] + g) * cw);
+                }
+                for (int j = 1; j < n2; ++j) {
+                    const u64 gk = frh::galois_of_rotation(c->R, (long)j * n1);
+                    const u64* key = rot_key(c, gk);
+                    for (int t = 0; t < nb; ++t) {
+                        const u64* src = Gs.p + ((size_t)t * n2 + j) * cw;
+                        KSReq r{src + (size_t)L * N, key, (u32)gk, 1, src, L, nullptr, L};
+                        r.sum_dst = t;
+                        reqs.push_back(r);
+                    }
+                }
+                keyswitch_sums(c, L - 1, reqs, base, L, outp, L);
+                stage.reset();
+                s0 = s1;
+                continue;
+            }
             if (n2 > 1) {
                 Tmp Pr(c, (size_t)nb * n2 * cw);
                 copy_d2d(c, Pr.p, Gs.p, (size_t)nb * n2 * cw);

@@ -19,10 +19,11 @@ pytestmark = pytest.mark.gpu
 
 
 class Env:
-    def __init__(self, cfg, enroll_level=None, server_prerotation=False):
+    def __init__(self, cfg, enroll_level=None, server_prerotation=False, hoist=False):
         c = W.CONFIGS[cfg]
         self.c = c
-        self.ctx = fr.Context(device=0, **W.ctx_params(cfg))
+        self.hoist = hoist
+        self.ctx = fr.Context(device=0, hoist_giants=1 if hoist else 0, **W.ctx_params(cfg))
         rots = self.ctx.required_rotations(fr.FR_MODE_MEMBERSHIP)
         if server_prerotation:   # the negative giant steps -j n1
             rots = sorted(set(rots) | set(fr.rotation_set(c["ell"], c["n1"], self.ctx.n, fr.FR_KEYS_TBS_TOTAL, True)))
@@ -55,6 +56,12 @@ def tbs():
 
 
 @pytest.fixture(scope="module")
+def hoisted():
+    # giant steps sharing one ModDown per group
+    return Env("mid", hoist=True)
+
+
+@pytest.fixture(scope="module")
 def deep():
     # enrolled at the top level; the server keeps the limbs of its lower working level
     return Env("deep", enroll_level=len(W.CONFIGS["deep"]["q_bits"]) - 1)
@@ -71,12 +78,12 @@ def test_plain_enrollment_matches_oracle(tbs):
     assert np.array_equal(tbs.E, ref)
 
 
-@pytest.mark.parametrize("env_name", ["mid", "deep", "tbs"])
+@pytest.mark.parametrize("env_name", ["mid", "deep", "tbs", "hoisted"])
 @pytest.mark.parametrize("mode", [fr.FR_MODE_SCORES, fr.FR_MODE_IDENTIFY, fr.FR_MODE_MEMBERSHIP])
 def test_match_matches_oracle(env_name, mode, request):
     env = request.getfixturevalue(env_name)
     ref, lvl = env.ok.match_enc(env.oq, env.E_server, len(env.T), env.c["n1"], mode, env.c["cheb_degree"],
-                                env.c["threshold"], level=env.lq)
+                                env.c["threshold"], level=env.lq, hoist=env.hoist)
     for call in range(2):   # eager, then the captured graph
         outs = env.ctx.match(env.db, env.qct, mode)
         assert len(outs) == ref.shape[0]

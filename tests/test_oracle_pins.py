@@ -684,6 +684,8 @@ def test_encrypted_db_trivial_encryption_is_plaintext_path():
             E[g, d, 0] = c.encode(oracle.diag_slots(T, ell, c.n, g, d, (d // n1) * n1))
     got = k.enc_scores(qct, E, n1)
     assert np.array_equal(got, k.bsgs_scores(qct, T, ell, n1))
+    # the same with the giant steps sharing one ModDown
+    assert np.array_equal(k.enc_scores(qct, E, n1, hoist=True), k.bsgs_scores(qct, T, ell, n1, hoist=True))
 
 
 def test_encrypted_db_scores_and_match():
