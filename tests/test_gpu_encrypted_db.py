@@ -163,3 +163,19 @@ def test_headline_size_scores_decrypt():
     far = np.abs(s - c["threshold"]) > 0.02
     assert np.array_equal((ident >= 0.5)[far], (s >= c["threshold"])[far])
     assert set(np.flatnonzero(ident >= 0.5)) >= set(int(i) for i in planted)
+
+
+def test_serving_loop_with_encrypted_database(mid):
+    """Requests against an encrypted database through fr_match_submit / fr_match_poll give the
+    outputs of fr_match."""
+    ctx, keys = mid.ctx, mid.keys
+    qs = [ctx.encrypt(keys, mid.q, 700 + i) for i in range(3)]
+    ref = [[o.export() for o in ctx.match(mid.db, q, fr.FR_MODE_IDENTIFY)] for q in qs]
+    ctx.serve_start(max_batch=4, slots=2)
+    try:
+        tickets = [ctx.submit(mid.db, q, fr.FR_MODE_IDENTIFY) for q in qs]
+        for t, r in zip(tickets, ref):
+            outs = ctx.poll(t)
+            assert all(np.array_equal(o.export(), x) for o, x in zip(outs, r))
+    finally:
+        ctx.serve_stop()
