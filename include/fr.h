@@ -341,6 +341,11 @@ fr_status fr_ntt_set_shapes(fr_ctx* ctx, const uint32_t* shapes);
  * with the same (database, mode, batch size) on (the default). on = 0: every call launches
  * its kernels one by one (the plain per-query form). Results are identical. */
 fr_status fr_use_graphs(fr_ctx* ctx, int on);
+/* Failure injection (tests of the error paths; host side, no device fault): the after-th
+ * stream-ordered device allocation of this context from now on (0: the next one) fails as if
+ * HBM were exhausted, so the call that makes it returns FR_ERR_HBM_BUDGET; after < 0 disables
+ * it. The context stays usable after the failed call. */
+fr_status fr_inject_alloc_failure(fr_ctx* ctx, int64_t after);
 
 /* Arithmetic ceiling of the NTT on `device`: forward butterflies (Harvey lazy
  * reduction, Shoup twiddle product, 64-bit residues) per second with every operand in

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <exception>
 #include <set>
 #include <cstdlib>
 #include <cstring>
@@ -115,6 +116,8 @@ struct fr_ctx {
     int key_limbs = 0;                   // key_level + 1 + np
     size_t resident = 0;
     std::vector<void*> owned;            // persistent device allocations
+    long long fail_alloc_after = -1;     // failure injection: the device allocation that fails (-1 none)
+    std::vector<void*>* defer_free = nullptr;  // frees held back while a two-stream section unwinds
     bool prof = false;
     std::map<std::string, Region> regions;
     uint64_t launches = 0;
@@ -175,12 +178,19 @@ namespace {
 // ---------------------------------------------------------------------------
 u64* dalloc(fr_ctx* c, size_t words) {
     if (words == 0) words = 1;
+    if (c->fail_alloc_after >= 0 && c->fail_alloc_after-- == 0)
+        raise(FR_ERR_HBM_BUDGET, "injected device allocation failure");
     void* p = nullptr;
     CU(cudaMallocAsync(&p, words * sizeof(u64), c->cur));
     return (u64*)p;
 }
 void dfree(fr_ctx* c, void* p) {
-    if (p) cudaFreeAsync(p, c->cur);
+    if (!p) return;
+    if (c->defer_free && std::uncaught_exceptions() > 0) {  // unwinding a two-stream section
+        c->defer_free->push_back(p);
+        return;
+    }
+    cudaFreeAsync(p, c->cur);
 }
 struct Tmp {
     fr_ctx* c;
@@ -617,11 +627,27 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     // Two concurrent branches: the giant powers T_{2^m} on the current stream, the
     // leaves and the tree on the side stream; tree level s waits for T_{2^s} only.
     cudaStream_t main = c->cur, side = c->side;
-    struct Restore {
+    // Declared first, destroyed last. If an exception unwinds this function, the buffers its
+    // locals free are held back (dfree) until both branches have finished, so no kernel still
+    // queued on either stream can touch memory the pool has taken back.
+    struct JoinOnUnwind {
         fr_ctx* c;
-        cudaStream_t s;
-        ~Restore() { c->cur = s; }
-    } restore{c, main};
+        cudaStream_t main, side;
+        std::vector<void*> held;
+        std::vector<void*>* prev;
+        JoinOnUnwind(fr_ctx* cc, cudaStream_t m, cudaStream_t s) : c(cc), main(m), side(s), prev(cc->defer_free) {
+            c->defer_free = &held;
+        }
+        ~JoinOnUnwind() {
+            c->defer_free = prev;
+            c->cur = main;
+            if (held.empty()) return;
+            cudaStreamSynchronize(side);
+            cudaStreamSynchronize(main);
+            for (void* p : held) cudaFreeAsync(p, main);
+            cudaGetLastError();
+        }
+    } join_on_unwind(c, main, side);
     CU(cudaEventRecord(c->evs[0], main));
     CU(cudaStreamWaitEvent(side, c->evs[0], 0));
     // giant powers T_{2^m}, m = 1..d2-1, T_{2^m} at level ls - m
@@ -2162,7 +2188,9 @@ void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct*
             try {
                 match_pipeline(c, dbs, mg.in, mode, mg.out);
             } catch (...) {
-                cudaStreamEndCapture(c->cur, &graph);
+                graph = nullptr;
+                if (cudaStreamEndCapture(c->cur, &graph) == cudaSuccess && graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
                 throw;
             }
             CU(cudaStreamEndCapture(c->cur, &graph));
@@ -2765,6 +2793,14 @@ fr_status fr_use_graphs(fr_ctx* c, int on) {
         need_device(c);
         std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         c->use_graphs = on != 0;
+    });
+}
+
+fr_status fr_inject_alloc_failure(fr_ctx* c, int64_t after) {
+    return guard([&] {
+        if (!c) raise(FR_ERR_INVALID_ARG, "null context");
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        c->fail_alloc_after = after < 0 ? -1 : (long long)after;
     });
 }
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_encrypt_db", "fr_load_db_encrypted", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_ntt_tuning", "fr_ntt_set_shapes",
+    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
     "fr_serve_stats", "fr_serve_plan",
@@ -123,6 +123,7 @@ def load(build_if_missing: bool = True):
         "fr_launch_count": (C.c_uint64, [vp]),
         "fr_butterfly_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
         "fr_use_graphs": (st, [vp, C.c_int]),
+        "fr_inject_alloc_failure": (st, [vp, C.c_int64]),
         "fr_ntt_tuning": (st, [vp, np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), f64p]),
         "fr_ntt_set_shapes": (st, [vp, np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")]),
         "fr_ctx_primes": (st, [vp, u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -377,6 +378,10 @@ class Context:
 
     def ntt_set_shapes(self, shapes):
         _check(_lib.fr_ntt_set_shapes(self.h, np.ascontiguousarray(shapes, dtype=np.uint32)))
+
+    def inject_alloc_failure(self, after):
+        """Make the after-th device allocation from now fail (FR_ERR_HBM_BUDGET); -1: off."""
+        _check(_lib.fr_inject_alloc_failure(self.h, int(after)))
 
     def use_graphs(self, on=True):
         """Replay matches as CUDA graphs (default) or launch every kernel per call."""
