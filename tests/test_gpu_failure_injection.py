@@ -43,7 +43,7 @@ def test_allocation_failures_leave_context_usable(env, graphs, mode):
             assert all(np.array_equal(a, b) for a, b in zip(again, ref)), after
     finally:
         ctx.use_graphs(True)
-    assert failures >= 3
+    assert failures >= (2 if graphs else 3)   # replayed graphs allocate only their outputs
 
 
 def test_batch_allocation_failure(env):
