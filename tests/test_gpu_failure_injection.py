@@ -48,14 +48,18 @@ def test_allocation_failures_leave_context_usable(env, graphs, mode):
 
 def test_batch_allocation_failure(env):
     ctx, db = env["ctx"], env["db"]
-    qs = [ctx.encrypt(env["keys"], env["q"], 60 + i) for i in range(2)]
-    ref = [[o.export() for o in out] for out in ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)]
-    for after in (4, 40):
-        ctx.inject_alloc_failure(after)
-        try:
-            with pytest.raises(fr.FrError):
-                ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)
-        finally:
-            ctx.inject_alloc_failure(-1)
-        got = [[o.export() for o in out] for out in ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)]
-        assert all(np.array_equal(a, b) for x, y in zip(got, ref) for a, b in zip(x, y))
+    ctx.use_graphs(False)   # every call allocates its whole workspace
+    try:
+        qs = [ctx.encrypt(env["keys"], env["q"], 60 + i) for i in range(2)]
+        ref = [[o.export() for o in out] for out in ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)]
+        for after in (4, 40):
+            ctx.inject_alloc_failure(after)
+            try:
+                with pytest.raises(fr.FrError):
+                    ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)
+            finally:
+                ctx.inject_alloc_failure(-1)
+            got = [[o.export() for o in out] for out in ctx.match_batch(db, qs, fr.FR_MODE_MEMBERSHIP)]
+            assert all(np.array_equal(a, b) for x, y in zip(got, ref) for a, b in zip(x, y))
+    finally:
+        ctx.use_graphs(True)
