@@ -231,7 +231,7 @@ class Context:
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
                              C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode, sum_radix,
-                             1 if hoist_giants else 0)
+                             int(hoist_giants))
         h = C.c_void_p()
         self._live = 0          # library objects of this context still alive
         self._closing = False

@@ -172,3 +172,24 @@ def test_work_level_of_contexts():
                             ("mid", 1, 8)]:
         ctx = fr.Context(device=-1, **W.ctx_params(cfg, level_mode=lm))
         assert ctx.work_level == expect == W.work_level(cfg, lm)
+
+
+def test_radix_rotation_key_set_and_parameter_checks():
+    """RotateAndSum in radix r needs the keys t s (t < r, s = 1, r, r^2, ...) instead of the
+    powers of two; the parameters are checked by fr_setup on the host."""
+    base = W.ctx_params("mid")
+    ctx8 = fr.Context(device=-1, sum_radix=8, **base)
+    assert set(ctx8.required_rotations(fr.FR_MODE_MEMBERSHIP)) == {t * s for s in (1, 8, 64, 512) for t in range(1, 8)}
+    ctx4 = fr.Context(device=-1, sum_radix=4, **base)
+    r4 = set(ctx4.required_rotations(fr.FR_MODE_MEMBERSHIP))
+    assert {t * 4 ** e for e in range(6) for t in (1, 2, 3)} <= r4 and 2048 in r4     # 4096 = 4^6: six steps
+    ctx2 = fr.Context(device=-1, **base)
+    assert {1 << t for t in range(12)} <= set(ctx2.required_rotations(fr.FR_MODE_MEMBERSHIP))
+    # identification needs no slot sum: the same keys for every radix
+    assert ctx8.required_rotations(fr.FR_MODE_IDENTIFY) == ctx2.required_rotations(fr.FR_MODE_IDENTIFY)
+    for bad in (dict(sum_radix=6), dict(sum_radix=128), dict(hoist_giants=2)):
+        with pytest.raises(fr.FrError) as e:
+            fr.Context(device=-1, **base, **bad)
+        assert e.value.status == fr.FR_ERR_INVALID_ARG
+    ctx2.inject_alloc_failure(3)      # host-side setting; no device allocation on a client context
+    ctx2.inject_alloc_failure(-1)
