@@ -327,8 +327,25 @@ def run_identify(args):
     regions = {r: ctx.profile_read(r)[0] for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac",
                                                    "misc", "encode")}
     stages = {st: ctx.profile_read("stage:" + st)[0] for st in ("babies", "encode", "mac", "giants", "cheb")}
+    ntt_bytes = ctx.profile_read("ntt")[2]
     ctx.profile(False)
     del outs
+    # the encoder against the measured FP64 rate: 5 n log2 n operations per diagonal FFT
+    # (n = N/2 complex points), G ell diagonals per query when they are encoded per query
+    n = 1 << (c["log_n"] - 1)
+    fft_ops = 5.0 * n * (c["log_n"] - 1) * info["groups"] * c["ell"] if info["tier"] == 2 else 0.0
+    fp64 = fr.fp64_peak(local) / 1e9
+    roofline = None
+    if fft_ops and regions["encode"] > 0:
+        ach = fft_ops / (regions["encode"] / 1000.0) / 1e9
+        roofline = {"kernel": "encoder (gather, FP64 special FFT, rounding to residues)", "bound": "fp64",
+                    "achieved": ach, "peak": fp64, "unit": "GFLOP/s", "frac": ach / fp64 if fp64 else None,
+                    "flops_per_query": fft_ops, "peak_kind": "measured: register-only FP64 FMA loop (fr_fp64_peak)"}
+    # the NTTs against the measured butterfly rate (the region counts 16 B per coefficient)
+    bfly = fr.butterfly_peak(local) / 1e9
+    ntt_g = (ntt_bytes / 16.0 * (c["log_n"] / 2.0)) / (regions["ntt"] / 1000.0) / 1e9 if regions["ntt"] > 0 else 0.0
+    ntt_view = {"achieved": ntt_g, "peak": bfly, "unit": "Gbutterfly/s", "frac": ntt_g / bfly if bfly else None,
+                "bound": "alu", "peak_kind": "measured: register-only butterfly loop (fr_butterfly_peak)"}
     line = {
         "metric": "identification: templates matched/s and query latency at N=2^16, K=2^20",
         "value": K / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps, "ms_per_step": ms,
@@ -341,6 +358,7 @@ def run_identify(args):
         "check": {"max_abs_err_threshold": float(np.abs(dec - p).max()), "decisions_agree_outside_margin": agree,
                   "planted_found": int(len(set(planted.tolist()) & found)), "planted": int(len(planted))},
         "regions_ms": regions, "stages_ms": stages,
+        "roofline": roofline, "ntt_alu": ntt_view,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

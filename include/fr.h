@@ -351,6 +351,10 @@ fr_status fr_inject_alloc_failure(fr_ctx* ctx, int64_t after);
  * reduction, Shoup twiddle product, 64-bit residues) per second with every operand in
  * registers, measured by a short microbenchmark. Used as the ALU roofline peak. */
 fr_status fr_butterfly_peak(int device, double* butterflies_per_s);
+/* FP64 operations per second on `device`: eight independent fused multiply-add chains per
+ * thread with register operands, 8 CTAs of 256 threads per SM (an FMA counts as two). The
+ * ceiling of the encoder's FP64 special FFT. FR_ERR_CUDA without such a device. */
+fr_status fr_fp64_peak(int device, double* flops_per_s);
 /* Number of kernel launches issued by the library so far. */
 uint64_t fr_launch_count(const fr_ctx* ctx);
 

@@ -958,3 +958,46 @@ void launch_coef_residues(const long long* m, int nd, u64* out, int nl, const De
     dim3 g((N + kThreads - 1) / kThreads, nd);
     launch_k(k_coef_residues, dim3(g), dim3(kThreads), 0, s, m, nd, out, nl, primes, N);
 }
+
+namespace {
+
+// Register-only FP64 fused multiply-add throughput (the ceiling of the encoder's FFT): eight
+// independent chains per thread, x <- x a + b, with a slightly below 1 so values stay finite.
+__global__ void __launch_bounds__(256) k_fp64_peak(double a, double b, int iters, double* sink) {
+    double x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = 1.0 + 1e-3 * (threadIdx.x * 8 + e);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = __fma_rn(x[e], a, b);
+    }
+    double acc = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc += x[e];
+    if (acc == -1.0) sink[0] = acc;  // keeps the loop live
+}
+
+}  // namespace
+
+double measure_fp64_peak(int device) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = nsm * 8, threads = 256, iters = 4096;
+    double* sink = nullptr;
+    if (cudaMalloc(&sink, 8) != cudaSuccess) return 0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_fp64_peak<<<blocks, threads>>>(0.999999, 1e-9, 64, sink);  // warm-up
+    cudaEventRecord(a);
+    k_fp64_peak<<<blocks, threads>>>(0.999999, 1e-9, iters, sink);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    if (ms <= 0) return 0;
+    return 2.0 * blocks * threads * 8.0 * iters / (ms * 1e-3);  // an FMA is two operations
+}

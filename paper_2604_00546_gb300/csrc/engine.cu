@@ -2816,6 +2816,18 @@ fr_status fr_butterfly_peak(int device, double* butterflies_per_s) {
     });
 }
 
+fr_status fr_fp64_peak(int device, double* flops_per_s) {
+    return guard([&] {
+        if (!flops_per_s) raise(FR_ERR_INVALID_ARG, "null argument");
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+            raise(FR_ERR_CUDA, "no such CUDA device");
+        CU(cudaSetDevice(device));
+        *flops_per_s = measure_fp64_peak(device);
+        CU(cudaGetLastError());
+    });
+}
+
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
     if (!out) return FR_ERR_INVALID_ARG;
     std::vector<double> c;

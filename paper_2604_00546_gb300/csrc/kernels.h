@@ -90,6 +90,8 @@ void launch_ntt(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t
 void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps);
 // Butterflies per second of the NTT's forward butterfly with operands in registers.
 double measure_butterfly_peak(int device);
+// FP64 operations per second of fused multiply-adds with operands in registers.
+double measure_fp64_peak(int device);
 
 // Fast base conversion tables for one (source set, target list).
 struct BconvTab {

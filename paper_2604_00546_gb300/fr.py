@@ -31,7 +31,7 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_encrypt_db", "fr_load_db_encrypted", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
+    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_fp64_peak", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
     "fr_serve_stats", "fr_serve_plan",
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
                                  C.POINTER(C.c_uint64)]),
         "fr_launch_count": (C.c_uint64, [vp]),
         "fr_butterfly_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
+        "fr_fp64_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
         "fr_use_graphs": (st, [vp, C.c_int]),
         "fr_inject_alloc_failure": (st, [vp, C.c_int64]),
         "fr_ntt_tuning": (st, [vp, np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS"), f64p]),
@@ -551,6 +552,14 @@ def serve_plan(classes, max_batch, avail_bytes, ws_base, ws_per_query):
 def butterfly_peak(device=0):
     v = C.c_double()
     _check(load().fr_butterfly_peak(int(device), C.byref(v)))
+    return v.value
+
+
+def fp64_peak(device=0):
+    """Measured FP64 operations per second (register-only fused multiply-adds)."""
+    L = load()
+    v = C.c_double()
+    _check(L.fr_fp64_peak(int(device), C.byref(v)))
     return v.value
 
 
