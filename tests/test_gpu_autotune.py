@@ -62,3 +62,13 @@ def test_every_shape_is_bit_exact(big, shape):
         assert np.array_equal(ctx.rescale(ct).export(), big["ref_rs"])
     finally:
         ctx.ntt_set_shapes(saved)
+
+
+def test_measured_peaks_are_plausible():
+    """The register-only ceilings the bench divides by: the NTT butterfly (64-bit integer
+    pipes) and the FP64 fused multiply-add (the encoder's FFT). Both well above zero and
+    below what any GB300 could do (2070 MHz x 152 SMs bounds them)."""
+    bfly = fr.butterfly_peak(0)
+    fp64 = fr.fp64_peak(0)
+    assert 1e11 < bfly < 1e13
+    assert 1e11 < fp64 < 1e13
