@@ -270,7 +270,10 @@ fr_status fr_decrypt(const fr_ctx* ctx, const fr_keys* keys, const fr_ct* ct, do
 
 /* Export / import ciphertext words (format above). `words` must be >= 2 (level+1) N. */
 fr_status fr_ct_export(const fr_ct* ct, uint64_t* buf, size_t words, uint32_t* level, double* scale);
+/* Import copies the words into a host ciphertext of the context: FR_ERR_LEVEL for a level
+ * beyond the top, FR_ERR_FORMAT for a residue not below its prime. */
 fr_status fr_ct_import(const fr_ctx* ctx, const uint64_t* buf, uint32_t level, double scale, fr_ct** out);
+/* Level of a ciphertext and whether it is resident in HBM (either out-pointer may be NULL). */
 fr_status fr_ct_info(const fr_ct* ct, uint32_t* level, int* on_device);
 /* Move a host ciphertext into HBM (NTT form); no-op if already there. */
 fr_status fr_ct_upload(fr_ctx* ctx, fr_ct* ct);
@@ -280,9 +283,11 @@ fr_status fr_ct_upload(fr_ctx* ctx, fr_ct* ct);
 fr_status fr_rotate(fr_ctx* ctx, const fr_ct* ct, int32_t k, fr_ct** out);
 /* hoisted rotations of one ciphertext by ks[0..n) (one shared ModUp) */
 fr_status fr_rotate_hoisted(fr_ctx* ctx, const fr_ct* ct, const int32_t* ks, size_t n, fr_ct** out);
+/* Division by the last prime with the centered lift; the level drops by one (FR_ERR_LEVEL at 0). */
 fr_status fr_rescale(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 /* ct x ct product with relinearisation (no rescale); both at the same level */
 fr_status fr_mul_relin(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
+/* Sum mod q at the lower of the two levels. */
 fr_status fr_add(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
 /* Chebyshev threshold p(x) of the context's degree and threshold */
 fr_status fr_chebyshev(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
@@ -315,6 +320,7 @@ fr_status fr_membership_reduce(fr_ctx* ctx, const fr_ct* const* parts, size_t n,
 fr_status fr_rotate_noalloc(fr_ctx* ctx, const uint64_t* d_in, uint32_t level, int32_t k, uint64_t* d_out);
 
 /* Wait for all work enqueued on the context stream. */
+/* Wait until the context's queued device work has finished. */
 fr_status fr_sync(fr_ctx* ctx);
 
 /* Per-region device timing (CUDA events on the context stream). enable=1 clears and
@@ -377,6 +383,7 @@ void fr_free_cts(fr_ct** cts, size_t n);
 void fr_free_keys(fr_keys* keys);
 void fr_free_db(fr_db* db);
 void fr_free(fr_ctx* ctx);
+/* Message of the last failed call on this thread (owned by the library). */
 const char* fr_last_error(void);
 
 #ifdef __cplusplus
