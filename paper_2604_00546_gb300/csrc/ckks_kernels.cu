@@ -404,11 +404,13 @@ __global__ void __launch_bounds__(kThreads) k_giant_acc(const AccJobs jobs, u64*
 // Section 5.3): for every giant step j, pointwise per limb,
 //   (d0, d1, d2)_j = sum_{i < n1, j n1 + i < ell} B_i (x) E_{j n1 + i}
 //   d0 += b0 e0,  d1 += b0 e1 + b1 e0,  d2 += b1 e1.
+// The middle term takes one product (Karatsuba): d1 = sum (b0 + b1)(e0 + e1) - d0 - d2, the
+// same residue mod q as the two products it replaces.
 // babies: [n1][2][cap_b][N] evaluation form; diags: [ell][2][nl][N] evaluation form in
-// Montgomery form, so one REDC of the sum gives it in plain form; out: [n2][3][cap_o][N].
-// Tiling as k_mac (babies of a point tile staged in shared memory as 30-bit halves, giant
-// steps over the thread rows). Diagonals go in batches of 4: d1 takes two products per
-// diagonal, and 8 products are what one 30-bit split sum holds without a carry step.
+// Montgomery form (e0 R + e1 R = (e0 + e1) R), so one REDC of each sum gives it in plain form;
+// out: [n2][3][cap_o][N]. Tiling as k_mac: the babies of a point tile are staged in shared
+// memory as 30-bit halves of b0, b1 and b0 + b1, giant steps run over the thread rows.
+// Diagonals go in batches of 4 (one carry step per batch).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babies, int cap_b,
                                                    const u64* __restrict__ diags, u64* __restrict__ out, int cap_o,
@@ -416,15 +418,20 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
                                                    const DevPrime* __restrict__ primes, int N) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ u64 sb[];  // [n1][2][TP]
+    extern __shared__ u64 sb[];  // [n1][3][TP]: b0, b1, b0 + b1
     const int pl = threadIdx.x % TP;
     const int jg = threadIdx.x / TP;
     const int k = blockIdx.x * TP + pl;
     const int i = blockIdx.y;
     const u64 q = primes[i].q, qinv = primes[i].qinv;
-    for (int e = threadIdx.x; e < n1 * 2 * TP; e += TP * JG) {
-        const int ib = e / (2 * TP), t = (e / TP) & 1, pp = e % TP;
-        sb[e] = split30(babies[((long long)ib * 2 + t) * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp]);
+    for (int e = threadIdx.x; e < n1 * TP; e += TP * JG) {
+        const int ib = e / TP, pp = e % TP;
+        const u64* src = babies + (long long)ib * 2 * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp;
+        const u64 b0 = src[0], b1 = src[(long long)cap_b * N];
+        u64* dst = sb + (size_t)ib * 3 * TP + pp;
+        dst[0] = split30(b0);
+        dst[TP] = split30(b1);
+        dst[2 * TP] = split30(add_mod(b0, b1, q));
     }
     __syncthreads();
     const long long dstride = 2LL * nl * N;  // one diagonal ciphertext
@@ -432,10 +439,10 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
     for (int j = jg; j < n2; j += JG) {
         const int cnt = min(n1, ell - j * n1);
         const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
-        Acc128 a0{0, 0}, a1{0, 0}, a2{0, 0};
+        Acc128 a0{0, 0}, am{0, 0}, a2{0, 0};
         for (int i0 = 0; i0 < cnt; i0 += 4) {
-            Acc3 p0{0, 0, 0}, p1{0, 0, 0}, p2{0, 0, 0};
-            const u64* sq = sb + (size_t)i0 * 2 * TP + pl;
+            Acc3 p0{0, 0, 0}, pm{0, 0, 0}, p2{0, 0, 0};
+            const u64* sq = sb + (size_t)i0 * 3 * TP + pl;
             if (i0 + 4 <= cnt) {
                 u64 e0[4], e1[4];
 #pragma unroll
@@ -445,35 +452,34 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const u64 s0 = split30(e0[u]), s1 = split30(e1[u]);
-                    const u64 b0 = sq[u * 2 * TP], b1 = sq[u * 2 * TP + TP];
-                    mac30(p0, b0, s0);
-                    mac30(p1, b0, s1);
-                    mac30(p1, b1, s0);
-                    mac30(p2, b1, s1);
+                    const u64* bq = sq + u * 3 * TP;
+                    mac30(p0, bq[0], split30(e0[u]));
+                    mac30(p2, bq[TP], split30(e1[u]));
+                    mac30(pm, bq[2 * TP], split30(add_mod(e0[u], e1[u], q)));
                 }
             } else {
                 for (int u = 0; i0 + u < cnt; ++u) {
-                    const u64 s0 = split30(__ldcs(D + u * dstride)), s1 = split30(__ldcs(D + u * dstride + cstride));
-                    const u64 b0 = sq[u * 2 * TP], b1 = sq[u * 2 * TP + TP];
-                    mac30(p0, b0, s0);
-                    mac30(p1, b0, s1);
-                    mac30(p1, b1, s0);
-                    mac30(p2, b1, s1);
+                    const u64 f0 = __ldcs(D + u * dstride), f1 = __ldcs(D + u * dstride + cstride);
+                    const u64* bq = sq + u * 3 * TP;
+                    mac30(p0, bq[0], split30(f0));
+                    mac30(p2, bq[TP], split30(f1));
+                    mac30(pm, bq[2 * TP], split30(add_mod(f0, f1, q)));
                 }
             }
             flush30(a0, p0);
-            flush30(a1, p1);
+            flush30(am, pm);
             flush30(a2, p2);
             fold(a0, q);
-            fold(a1, q);
+            fold(am, q);
             fold(a2, q);
             D += 4 * dstride;
         }
+        const u64 d0 = redc(a0.hi, a0.lo, q, qinv), d2 = redc(a2.hi, a2.lo, q, qinv);
+        const u64 dm = redc(am.hi, am.lo, q, qinv);
         u64* O = out + (long long)j * 3 * cap_o * N + (long long)i * N + k;
-        O[0] = redc(a0.hi, a0.lo, q, qinv);
-        O[(long long)cap_o * N] = redc(a1.hi, a1.lo, q, qinv);
-        O[2LL * cap_o * N] = redc(a2.hi, a2.lo, q, qinv);
+        O[0] = d0;
+        O[(long long)cap_o * N] = sub_mod(sub_mod(dm, d0, q), d2, q);
+        O[2LL * cap_o * N] = d2;
     }
 }
 
@@ -856,13 +862,13 @@ void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const
 
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
                    const DevPrime* primes, int N, cudaStream_t s) {
-    // points per CTA: staged babies (n1 2 TP words) within 128 KiB; giant-step rows up to 512 threads
+    // points per CTA: staged babies (n1 3 TP words) within 128 KiB; giant-step rows up to 512 threads
     int TP = 128;
-    while (TP > 16 && (size_t)n1 * 2 * TP * 8 > (128u << 10)) TP >>= 1;
+    while (TP > 16 && (size_t)n1 * 3 * TP * 8 > (128u << 10)) TP >>= 1;
     int JG = 512 / TP;
     if (JG > n2) JG = n2;
     if (JG < 1) JG = 1;
-    const size_t sm = (size_t)n1 * 2 * TP * sizeof(u64);
+    const size_t sm = (size_t)n1 * 3 * TP * sizeof(u64);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_mac_ct, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
