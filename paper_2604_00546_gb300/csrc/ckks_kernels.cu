@@ -833,11 +833,8 @@ static void launch_mac_t(const u64* babies, long long baby_q, int cap_b, const u
     if (JG > n2) JG = n2;
     if (JG < 1) JG = 1;
     const size_t sm = (size_t)B * n1 * 2 * TP * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mac<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(k_mac<B>, 200 * 1024, attr);
     dim3 g(N / TP, nl);
     launch_k(k_mac<B>, dim3(g), dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
 }
@@ -869,11 +866,8 @@ void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int
     if (JG > n2) JG = n2;
     if (JG < 1) JG = 1;
     const size_t sm = (size_t)n1 * 3 * TP * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mac_ct, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(k_mac_ct, 200 * 1024, attr);
     dim3 g(N / TP, nl);
     launch_k(k_mac_ct, dim3(g), dim3(TP * JG), sm, s, babies, cap_b, diags, out, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
 }

@@ -1,6 +1,7 @@
 // Kernel launchers shared by the engine (host-callable, device pointers only).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 #include "dev_arith.cuh"
@@ -38,6 +39,18 @@ inline void launch_k(void (*k)(KP...), dim3 g, dim3 b, size_t smem, cudaStream_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k, static_cast<KP>(args)...);
+}
+
+// cudaFuncSetAttribute acts on the current device only: raise kernel k's dynamic shared memory
+// limit once per device (bit d of `done` marks device d).
+template <class K>
+inline void smem_limit_once(K* k, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done.fetch_or(bit, std::memory_order_release);
 }
 
 #define FR_MAX_PRIMES 64

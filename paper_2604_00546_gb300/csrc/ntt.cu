@@ -467,13 +467,9 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
 // holds the table); sizes other than N = 2^15, 2^16 use shape 0.
 template <class E>
 void launch_ntt_cluster(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ntt_cluster<false, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmem);
-        cudaFuncSetAttribute(k_ntt_cluster<true, EpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kClusterSmem);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> fwd{0}, inv{0};
+    smem_limit_once(k_ntt_cluster<false, E>, (int)kClusterSmem, fwd);
+    smem_limit_once(k_ntt_cluster<true, EpiStore>, (int)kClusterSmem, inv);
     const dim3 g(kClusterCtas, b.npolys);
     if (!inverse) launch_k(k_ntt_cluster<false, E>, g, dim3(1024), kClusterSmem, st, R, b, epi);
     else launch_k(k_ntt_cluster<true, EpiStore>, g, dim3(1024), kClusterSmem, st, R, b, EpiStore{});
