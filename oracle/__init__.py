@@ -103,6 +103,11 @@ def _declare(L):
     L.or_add.argtypes = [vp, u64p, u64p, C.c_int, u64p]
     L.or_mul_relin.argtypes = [vp, vp, u64p, u64p, C.c_int, u64p]
     L.or_cheb_coeffs.argtypes = [C.c_int, C.c_double, f64p]
+    L.or_cheb_coeffs_lo.argtypes = [C.c_int, C.c_double, C.c_double, f64p]
+    L.or_f4_eval.restype = C.c_int
+    L.or_f4_eval.argtypes = [vp, vp, u64p, C.c_int, u64p]
+    L.or_comparator_eval.restype = C.c_int
+    L.or_comparator_eval.argtypes = [vp, vp, u64p, C.c_int, C.c_int, C.c_double, C.c_int, u64p]
     L.or_ps_split.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.or_cheb_ps_eval_fp64.restype = C.c_double
     L.or_cheb_ps_eval_fp64.argtypes = [f64p, C.c_int, C.c_double]
@@ -121,7 +126,7 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+                           C.c_int, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_bsgs_scores_hoisted.restype = C.c_int
     L.or_bsgs_scores_hoisted.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_table_scores.restype = C.c_int
@@ -332,6 +337,24 @@ class Keys:
             raise ValueError("unsupported Chebyshev degree / level")
         return out
 
+    def f4_eval(self, ct, level):
+        """(1 + f_4(y)) / 2 of the ct y at `level`, at level - 4 (hybrid comparator's second part)."""
+        out = np.empty((2, level - 3, self.ctx.N), dtype=np.uint64)
+        if self.L.or_f4_eval(self.ctx.h, self.h, np.ascontiguousarray(ct, dtype=np.uint64), level, out) < 0:
+            raise ValueError("level too low")
+        return out
+
+    def comparator_eval(self, ct, level, n, tau, comparator):
+        """Threshold of the match: comparator 0 = cheb_eval; 1 = hybrid (depth d2 + 4)."""
+        d1, d2 = ps_split(n)
+        dep = d2 + (4 if comparator == 1 else 0)
+        out = np.empty((2, level - dep + 1, self.ctx.N), dtype=np.uint64)
+        r = self.L.or_comparator_eval(self.ctx.h, self.h, np.ascontiguousarray(ct, dtype=np.uint64), level, int(n),
+                                      float(tau), int(comparator), out)
+        if r < 0:
+            raise ValueError("unsupported comparator / level")
+        return out
+
     def rotate_sum(self, ct, level, steps, radix=2):
         """RotateAndSum over 2^steps slots, in radix `radix` (2: one rotation per step)."""
         x = np.ascontiguousarray(ct, dtype=np.uint64).copy()
@@ -407,9 +430,11 @@ class Keys:
             raise ValueError("bad parameters")
         return out
 
-    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2, hoist=False):
+    def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2, hoist=False,
+              comparator=0):
         """Full match of a top-level query ct, computed at working level `level` (default: top);
-        schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table."""
+        schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table;
+        comparator 0: the step interpolant (the paper's GPU path), 1: the hybrid comparator."""
         c = self.ctx
         lq = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
@@ -419,8 +444,8 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)   # large enough for any output level
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
-                            int(cheb_n), float(tau), int(schedule), int(sum_radix), 1 if hoist else 0, out,
-                            C.byref(lvl))
+                            int(cheb_n), float(tau), int(comparator), int(schedule), int(sum_radix),
+                            1 if hoist else 0, out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value
@@ -523,9 +548,10 @@ def sample_uniform(seed, obj, limb, q, n):
     return out
 
 
-def cheb_coeffs(n, tau):
+def cheb_coeffs(n, tau, low=0.0):
+    """Chebyshev interpolant at the n + 1 nodes of f = 1 for x >= tau, `low` below."""
     out = np.empty(n + 1, dtype=np.float64)
-    lib().or_cheb_coeffs(int(n), float(tau), out)
+    lib().or_cheb_coeffs_lo(int(n), float(tau), float(low), out)
     return out
 
 

@@ -1065,18 +1065,22 @@ static void add_const_res(const or_ctx* c, u64* ct, int l, int64_t v, int times_
 /* Chebyshev nodes, evaluated by Paterson-Stockmeyer with d1 = 2 and the     */
 /* Chebyshev division p = q T_M + r.                                         */
 /* ------------------------------------------------------------------------ */
-void or_cheb_coeffs(int n, double tau, double* cf) {
+/* interpolant of f(x) = 1 for x >= tau, `low` below (low = 0: step(x - tau); low = -1:
+ * sign(x - tau), the input of the hybrid comparator) */
+void or_cheb_coeffs_lo(int n, double tau, double low, double* cf) {
     for (int k = 0; k <= n; k++) {
         double s = 0.0;
         for (int j = 0; j <= n; j++) {
             double theta = M_PI * ((double)j + 0.5) / (double)(n + 1);
             double x = cos(theta);
-            double f = (x >= tau) ? 1.0 : 0.0;
+            double f = (x >= tau) ? 1.0 : low;
             s = s + f * cos((double)k * theta);
         }
         cf[k] = s * ((k == 0 ? 1.0 : 2.0) / (double)(n + 1));
     }
 }
+
+void or_cheb_coeffs(int n, double tau, double* cf) { or_cheb_coeffs_lo(n, tau, 0.0, cf); }
 
 /* PS split: argmin d1+d2 with d1 * 2^(d2-1) >= n; ties -> larger d1 */
 void or_ps_split(int n, int* d1_out, int* d2_out) {
@@ -1160,14 +1164,16 @@ static u64* cheb_eval_rec(cheb_state* S, const double* cf, int len) {
     return o;
 }
 
-/* ct at level ls -> out at level ls - d2; returns d2, or -1 if the PS split has d1 != 2 */
-int or_cheb_eval(const or_ctx* c, or_keys* k, const u64* ct, int ls, int n, double tau, u64* out) {
+/* sum_k cf[k] T_k(ct) for the degree-n interpolant of f = 1 above tau, `low` below:
+ * ct at level ls -> out at level ls - d2; returns d2, or -1 if the PS split has d1 != 2 */
+static int cheb_eval_lo(const or_ctx* c, or_keys* k, const u64* ct, int ls, int n, double tau, double low,
+                        u64* out) {
     int d1, d2;
     or_ps_split(n, &d1, &d2);
     if (d1 != 2 || d2 < 1 || ls - d2 < 0) return -1;
     int len = 1 << d2;
     double* cf = (double*)calloc(len, sizeof(double));
-    or_cheb_coeffs(n, tau, cf);
+    or_cheb_coeffs_lo(n, tau, low, cf);
     cheb_state S;
     S.c = c; S.k = k; S.ls = ls;
     S.x = (u64*)malloc(sizeof(u64) * ct_words(c, ls));
@@ -1193,6 +1199,112 @@ int or_cheb_eval(const or_ctx* c, or_keys* k, const u64* ct, int ls, int n, doub
     for (int m = 1; m < d2; m++) free(S.pw[m]);
     free(S.pw); free(S.x); free(cf);
     return d2;
+}
+
+/* the paper's GPU comparator: the interpolant of step(x - tau) (Eq. eq:cheb-sign) */
+int or_cheb_eval(const or_ctx* c, or_keys* k, const u64* ct, int ls, int n, double tau, u64* out) {
+    return cheb_eval_lo(c, k, ct, ls, n, tau, 0.0, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hybrid comparator (Section "HyDia": a lower-depth Chebyshev approximation  */
+/* followed by a fixed-degree polynomial of Cheon et al. 2020; reading R27):  */
+/*   y = the degree-n Chebyshev interpolant of sign(x - tau), as above;       */
+/*   out = (1 + f_4(y)) / 2 with f_4(y) = sum_{i=0}^{4} C(2i, i) 4^-i y (1 - y^2)^i */
+/*       = (315 y - 420 y^3 + 378 y^5 - 180 y^7 + 35 y^9) / 128,              */
+/* the odd polynomial with f_4'(y) = (315/128)(1 - y^2)^4 and f_4(1) = 1, which  */
+/* pushes every y near +-1 closer to +-1.                                     */
+/* (1 + f_4(y)) / 2 = 1/2 + sum_k a_k y^k, a_k = coefficient / 256, in depth 4:  */
+/*   y2 = y y, y4 = y2 y2, y8 = y4 y4 (each rescaled);                          */
+/*   u_k = Rescale(y round(a_k Delta)), u_1 with the constant round(Delta/2) Delta; */
+/*   t3 = u3 y2, v7 = u7 y2, t5 = u5 y4, t7 = v7 y4, t9 = u9 y8 (each rescaled);  */
+/*   out = t9 + t7 + t5 + t3 + u1 at level l - 4 (higher terms dropped to it).   */
+/* ------------------------------------------------------------------------ */
+static const int F4_NUM[5] = {315, -420, 378, -180, 35};   /* of y, y^3, y^5, y^7, y^9; / 128 */
+
+/* ct * round(v) + round(cst) Delta (in c0), then Rescale: level l -> l - 1 */
+static void scalar_rescale(const or_ctx* c, const u64* ct, int l, double v, double cst, u64* out) {
+    double delta = ldexp(1.0, c->scale_bits);
+    u64* t = (u64*)malloc(sizeof(u64) * ct_words(c, l));
+    memcpy(t, ct, sizeof(u64) * ct_words(c, l));
+    mul_int(c, t, l, llround(v * delta));
+    if (cst != 0.0) add_const_res(c, t, l, llround(cst * delta), 1);
+    or_rescale(c, t, l, out);
+    free(t);
+}
+
+/* a (x) b with relinearisation at level l, then Rescale: -> level l - 1 */
+static void mul_rescale(const or_ctx* c, or_keys* k, const u64* a, const u64* b, int l, u64* out) {
+    u64* p = (u64*)malloc(sizeof(u64) * ct_words(c, l));
+    or_mul_relin(c, k, a, b, l, p);
+    or_rescale(c, p, l, out);
+    free(p);
+}
+
+/* a copy of ct at level l dropped to level l2 <= l */
+static u64* dropped(const or_ctx* c, const u64* ct, int l, int l2) {
+    u64* o = (u64*)malloc(sizeof(u64) * ct_words(c, l));
+    memcpy(o, ct, sizeof(u64) * ct_words(c, l));
+    if (l2 < l) or_drop(c, o, l, l2, o);
+    return o;
+}
+
+/* (1 + f_4(y)) / 2 of y at level l -> out at level l - 4; -1 if l < 4 */
+int or_f4_eval(const or_ctx* c, or_keys* k, const u64* y, int l, u64* out) {
+    if (l < 4) return -1;
+    u64* y2 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 1));
+    u64* y4 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 2));
+    u64* y8 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 3));
+    mul_rescale(c, k, y, y, l, y2);
+    mul_rescale(c, k, y2, y2, l - 1, y4);
+    mul_rescale(c, k, y4, y4, l - 2, y8);
+    u64* u[5];
+    for (int i = 0; i < 5; i++) {
+        u[i] = (u64*)malloc(sizeof(u64) * ct_words(c, l - 1));
+        scalar_rescale(c, y, l, (double)F4_NUM[i] / 256.0, i == 0 ? 0.5 : 0.0, u[i]);
+    }
+    u64* t3 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 2));
+    u64* v7 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 2));
+    u64* t5 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 3));
+    u64* t7 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 3));
+    u64* t9 = (u64*)malloc(sizeof(u64) * ct_words(c, l - 4));
+    mul_rescale(c, k, u[1], y2, l - 1, t3);
+    mul_rescale(c, k, u[3], y2, l - 1, v7);
+    u64* u5 = dropped(c, u[2], l - 1, l - 2);
+    mul_rescale(c, k, u5, y4, l - 2, t5);
+    mul_rescale(c, k, v7, y4, l - 2, t7);
+    u64* u9 = dropped(c, u[4], l - 1, l - 3);
+    mul_rescale(c, k, u9, y8, l - 3, t9);
+    /* sum at level l - 4 */
+    u64* a7 = dropped(c, t7, l - 3, l - 4);
+    u64* a5 = dropped(c, t5, l - 3, l - 4);
+    u64* a3 = dropped(c, t3, l - 2, l - 4);
+    u64* a1 = dropped(c, u[0], l - 1, l - 4);
+    or_add(c, t9, a7, l - 4, out);
+    or_add(c, out, a5, l - 4, out);
+    or_add(c, out, a3, l - 4, out);
+    or_add(c, out, a1, l - 4, out);
+    for (int i = 0; i < 5; i++) free(u[i]);
+    free(y2); free(y4); free(y8); free(t3); free(v7); free(t5); free(t7); free(t9);
+    free(u5); free(u9); free(a7); free(a5); free(a3); free(a1);
+    return 4;
+}
+
+/* Threshold of the match: comparator 0, the paper's GPU path (step interpolant, depth d2);
+ * comparator 1, the hybrid (sign interpolant then (1 + f_4) / 2, depth d2 + 4).
+ * ct at level ls -> out at level ls - depth; returns the depth or -1. */
+int or_comparator_eval(const or_ctx* c, or_keys* k, const u64* ct, int ls, int n, double tau, int comparator,
+                       u64* out) {
+    if (comparator == 0) return cheb_eval_lo(c, k, ct, ls, n, tau, 0.0, out);
+    if (comparator != 1) return -1;
+    int d1, d2;
+    or_ps_split(n, &d1, &d2);
+    if (d1 != 2 || ls - d2 - 4 < 0) return -1;
+    u64* y = (u64*)malloc(sizeof(u64) * ct_words(c, ls - d2));
+    if (cheb_eval_lo(c, k, ct, ls, n, tau, -1.0, y) < 0) { free(y); return -1; }
+    int r = or_f4_eval(c, k, y, ls - d2, out);
+    free(y);
+    return r < 0 ? -1 : d2 + 4;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1497,24 +1609,32 @@ int or_table_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, co
 /* Threshold and aggregation of the G score cts S [G][2][lq][N] at level lq-1 (Algorithm 5
  * lines for the comparison and the sum, Algorithm 6 for identification): mode 1 writes the
  * G cts p(S_k) at level lq-1-d2; mode 2 writes sum_k p(S_k) after RotateAndSum over all slots. */
-static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq, int mode, int cheb_n, double tau,
-                      int sum_radix, u64* out, int* out_level) {
-    int n = c->n / 2;
+/* depth of the threshold: d2 of the PS split (+ 4 for the hybrid comparator), -1 if unsupported */
+static int comparator_depth(int cheb_n, int comparator) {
     int d1, d2;
     or_ps_split(cheb_n, &d1, &d2);
-    if (d1 != 2 || lq - 1 - d2 < 0) return -1;
-    int lo = lq - 1 - d2;
+    if (d1 != 2 || comparator < 0 || comparator > 1) return -1;
+    return d2 + (comparator == 1 ? 4 : 0);
+}
+
+static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq, int mode, int cheb_n, double tau,
+                      int comparator, int sum_radix, u64* out, int* out_level) {
+    int n = c->n / 2;
+    int dep = comparator_depth(cheb_n, comparator);
+    if (dep < 0 || lq - 1 - dep < 0) return -1;
+    int lo = lq - 1 - dep;
     size_t cwo = ct_words(c, lo);
     if (mode == 1) {
         for (long g = 0; g < G; g++)
-            or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, out + g * cwo);
+            or_comparator_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, comparator,
+                               out + g * cwo);
         *out_level = lo;
         return (int)G;
     }
     u64* t = (u64*)malloc(sizeof(u64) * cwo);
     memset(out, 0, sizeof(u64) * cwo);
     for (long g = 0; g < G; g++) {
-        or_cheb_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, t);
+        or_comparator_eval(c, k, S + (size_t)g * ct_words(c, lq - 1), lq - 1, cheb_n, tau, comparator, t);
         or_add(c, out, t, lo, out);
     }
     int steps = 0;
@@ -1533,7 +1653,8 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
  * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, int schedule, int sum_radix, int hoist, u64* out, int* out_level) {
+             int cheb_n, double tau, int comparator, int schedule, int sum_radix, int hoist, u64* out,
+             int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
@@ -1547,16 +1668,15 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
         free(q);
         return r;
     }
-    int d1, d2;
-    or_ps_split(cheb_n, &d1, &d2);
-    if (d1 != 2 || lq - 1 - d2 < 0) { free(q); return -1; }
+    int dep = comparator_depth(cheb_n, comparator);
+    if (dep < 0 || lq - 1 - dep < 0) { free(q); return -1; }
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
     int rs = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, S)
              : hoist       ? or_bsgs_scores_hoisted(c, k, q, lq, T, K, ell, n1, S)
                            : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, sum_radix, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, comparator, sum_radix, out, out_level);
     free(S);
     return r;
 }
@@ -1761,7 +1881,7 @@ int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64*
     int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, hoist, S);
     free(q);
     if (rs < 0) { free(S); return -1; }
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, sum_radix, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, 0, sum_radix, out, out_level);
     free(S);
     return r;
 }

@@ -557,6 +557,91 @@ def test_homomorphic_chebyshev_matches_fp64():
 
 
 # ---------------------------------------------------------------------------
+# Hybrid comparator (Section "HyDia": lower-depth Chebyshev + Cheon et al. 2020's fixed
+# polynomial; reading R27)
+# ---------------------------------------------------------------------------
+def f4_closed(y):
+    """f_4(y) = sum_{i=0}^{4} C(2i, i) 4^-i y (1 - y^2)^i (Cheon, Kim, Kim 2020), the closed form."""
+    from math import comb
+    return sum(comb(2 * i, i) / 4.0 ** i * y * (1 - y * y) ** i for i in range(5))
+
+
+def test_f4_closed_form_properties():
+    """f_4 is odd, f_4(+-1) = +-1, f_4'(y) = (315/128)(1 - y^2)^4, and |f_4| <= 1 on [-1, 1]."""
+    ys = np.linspace(-1, 1, 2001)
+    assert np.abs(f4_closed(-ys) + f4_closed(ys)).max() < 1e-14
+    assert abs(f4_closed(1.0) - 1.0) < 1e-15
+    h = 1e-6
+    d = (f4_closed(ys[1:-1] + h) - f4_closed(ys[1:-1] - h)) / (2 * h)
+    assert np.abs(d - 315.0 / 128.0 * (1 - ys[1:-1] ** 2) ** 4).max() < 1e-7
+    assert np.abs(f4_closed(ys)).max() <= 1.0 + 1e-15
+
+
+def test_sign_interpolant_is_twice_step_minus_one():
+    """The sign(x - tau) interpolant is 2 (step interpolant) - T_0, since the interpolation is
+    linear in the sampled function; and it interpolates sign at the nodes."""
+    for n in (13, 59):
+        st = oracle.cheb_coeffs(n, 0.5)
+        sg = oracle.cheb_coeffs(n, 0.5, low=-1.0)
+        ref = 2 * st
+        ref[0] -= 1.0
+        assert np.abs(sg - ref).max() < 1e-12
+        theta = np.pi * (np.arange(n + 1) + 0.5) / (n + 1)
+        xj = np.cos(theta)
+        assert np.abs(np.polynomial.chebyshev.chebval(xj, sg) - np.where(xj >= 0.5, 1.0, -1.0)).max() < 1e-11
+
+
+def test_homomorphic_f4_matches_closed_form():
+    c = oracle.Ctx(11, [60] + [40] * 8, [60, 60, 60], 3, 40)
+    k = c.keygen(23)
+    rng = np.random.default_rng(17)
+    z = rng.uniform(-1.02, 1.02, c.n)
+    ct = k.encrypt(z, 6)
+    out = k.f4_eval(ct, c.top)
+    got = k.decrypt(out, c.top - 4)
+    assert np.abs(got - (1 + f4_closed(z)) / 2).max() < 1e-4
+
+
+def test_homomorphic_hybrid_comparator_matches_fp64_and_depth():
+    c = oracle.Ctx(11, [60] + [40] * 9, [60, 60, 60], 4, 40)
+    k = c.keygen(29)
+    rng = np.random.default_rng(19)
+    z = rng.uniform(-1, 1, c.n)
+    ct = k.encrypt(z, 7)
+    n = 13
+    d1, d2 = oracle.ps_split(n)
+    out = k.comparator_eval(ct, c.top, n, 0.5, 1)
+    assert out.shape[1] == c.top - d2 - 4 + 1
+    y = np.polynomial.chebyshev.chebval(z, oracle.cheb_coeffs(n, 0.5, low=-1.0))
+    got = k.decrypt(out, c.top - d2 - 4)
+    assert np.abs(got - (1 + f4_closed(y)) / 2).max() < 1e-3
+    # comparator 0 is the plain Chebyshev evaluation, bit for bit
+    assert np.array_equal(k.comparator_eval(ct, c.top, n, 0.5, 0), k.cheb_eval(ct, c.top, n, 0.5))
+
+
+def test_hybrid_comparator_makes_membership_a_count():
+    """On the headline workload's FP64 scores (K = 2^15, 32 planted at cosine 0.8), the hybrid's
+    per-slot values sum to the number of matches within 0.5 (non-matches contribute < 0.5 in
+    all), where the plain degree-59 step interpolant adds about 12.8; decisions agree outside
+    the 0.02 margin and the error there is below 0.015 (reading R27)."""
+    from paper_2604_00546_gb300 import workloads as W
+    T, q, planted = W.workload("membership")
+    s = T.astype(np.float64) @ q
+    sg = oracle.cheb_coeffs(59, 0.5, low=-1.0)
+    h = (1 + f4_closed(np.polynomial.chebyshev.chebval(s, sg))) / 2
+    match = s >= 0.5
+    assert match.sum() == len(planted)
+    assert abs(h[~match].sum()) < 0.5 and abs(h.sum() - len(planted)) < 0.5
+    plain = np.polynomial.chebyshev.chebval(s, oracle.cheb_coeffs(59, 0.5))
+    assert plain[~match].sum() > 10
+    xs = np.linspace(-1, 1, 200001)
+    hx = (1 + f4_closed(np.polynomial.chebyshev.chebval(xs, sg))) / 2
+    far = np.abs(xs - 0.5) > 0.02
+    assert np.all((hx[far] >= 0.5) == (xs[far] >= 0.5))
+    assert np.abs(hx[far] - (xs[far] >= 0.5)).max() < 0.015
+
+
+# ---------------------------------------------------------------------------
 # Full pipeline, small: identification and membership (Algorithms 5 and 6)
 # ---------------------------------------------------------------------------
 def test_match_modes_small():
@@ -599,6 +684,38 @@ def test_match_modes_small():
     memh, lvl5 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, hoist=True)
     assert lvl5 == lvl2 and not np.array_equal(memh, memb)
     assert np.abs(k.decrypt(memh[0], lvl5) - p.sum()).max() < 1e-2
+
+
+def test_match_hybrid_comparator_small():
+    """The hybrid comparator in the match: 4 more levels, each slot (1 + f_4(p_sign(s))) / 2,
+    and the membership sum is the count of the rows at or above the threshold."""
+    c = oracle.Ctx(11, [60] + [40] * 12, [60, 60, 60], 4, 40)
+    k = c.keygen(37)
+    ell, K = 32, 700
+    T = _templates(K, ell, 9)
+    q = T[5].astype(np.float64)
+    rng = np.random.default_rng(16)
+    for idx in (11, 300, 640):
+        u = rng.standard_normal(ell)
+        u -= (u @ q) * q
+        u /= np.linalg.norm(u)
+        T[idx] = (0.8 * q + 0.6 * u).astype(np.float32)
+    T[5] = (0.3 * q + np.sqrt(1 - 0.09) * u).astype(np.float32)   # the query's own row off the threshold
+    qct = k.encrypt(np.tile(q, c.n // ell), 10)
+    s = np.concatenate([T.astype(np.float64) @ q, np.zeros(c.n - K)])
+    y = np.polynomial.chebyshev.chebval(s, oracle.cheb_coeffs(59, 0.5, low=-1.0))
+    h = (1 + f4_closed(y)) / 2
+    lq = 12
+    ident, lvl = k.match(qct, T, ell, 4, oracle.MODE_IDENTIFY, 59, 0.5, level=lq, comparator=1)
+    assert lvl == lq - 1 - 6 - 4
+    assert np.abs(k.decrypt(ident[0], lvl) - h).max() < 1e-2
+    memb, lvl2 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, level=lq, comparator=1)
+    assert lvl2 == lvl
+    m = k.decrypt(memb[0], lvl2)
+    # at ell = 32 some random rows also score above 0.5; no score falls inside the margin, so
+    # the sum is the count of rows at or above the threshold
+    assert np.all(np.abs(s - 0.5) > 0.02)
+    assert abs(m[0] - h.sum()) < 1e-2 and abs(m[0] - (s >= 0.5).sum()) < 0.05
 
 
 # ---------------------------------------------------------------------------
