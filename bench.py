@@ -101,61 +101,32 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle: bounded sample of one query, extrapolated to the full query
+# CPU oracle: whole membership queries, timed
 # ---------------------------------------------------------------------------
-def oracle_sample(cfgname, T, q, seed_key, seed_enc, lq=None, reps=5):
-    """Time a bounded sample of the oracle's work for one query computed at level lq: each
-    primitive of the query is timed `reps` times (mean taken), about 10 s of CPU work."""
+def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_queries=1, sum_radix=4, hoist=True):
+    """Time whole membership queries of the CPU oracle (the same match the library computes,
+    bit for bit: on-demand BSGS at working level lq, by default with giant steps sharing one
+    ModDown and RotateAndSum in radix 4). Key generation and encryption happen before the timed region;
+    the oracle derives each rotation key inside the query, as it stands. Runs one query, then
+    more while the time spent stays under budget_s, at most max_queries.
+    Returns (seconds per query list, threads used, membership ciphertext of the first query)."""
     import oracle
     from paper_2604_00546_gb300 import workloads as W
     c = W.CONFIGS[cfgname]
     oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
     ok = oc.keygen(seed_key)
-    L = oc.top if lq is None else lq
-    n1, ell = c["n1"], c["ell"]
-    n2 = (ell + n1 - 1) // n1
-    G = (len(T) + oc.n - 1) // oc.n
-    d1, d2 = oracle.ps_split(c["cheb_degree"])
-    oq = oc.drop(ok.encrypt(np.tile(q, oc.n // ell), seed_enc), oc.top, L)
-    tm = {}
-
-    spent = [0.0]
-
-    def timed(name, f):
-        ts = []
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            r = f()
-            ts.append(time.perf_counter() - t0)
-        tm[name] = float(np.mean(ts))
-        spent[0] += float(np.sum(ts))
-        return r
-
-    timed("h1", lambda: ok.hoisted_rotate(oq, L, [1]))
-    timed("h2", lambda: ok.hoisted_rotate(oq, L, [1, 2]))
-    rng = np.random.default_rng(0)
-    bab = np.empty((n1, 2, L + 1, oc.N), dtype=np.uint64)
-    for i in range(L + 1):
-        bab[:, :, i, :] = rng.integers(0, oc.primes[i], size=(n1, 2, oc.N), dtype=np.uint64)
-    timed("giant", lambda: ok.giant_step(bab, n1, T, ell, 0, 1))
-    x23 = oc.drop(oq, L, L - 1)
-    timed("rot_giant", lambda: ok.rotate(x23, L - 1, n1))
-    mid = L - 1 - d2 // 2
-    xm = oc.drop(oq, L, mid)
-    timed("mul_mid", lambda: oc.rescale(ok.mul_relin(xm, xm, mid), mid))
-    lo = L - 1 - d2
-    xl = oc.drop(oq, L, lo)
-    timed("rot_sum", lambda: ok.rotate(xl, lo, 1))
-    babies = tm["h1"] + (n1 - 2) * (tm["h2"] - tm["h1"])
-    n_mul = (2 ** (d2 - 1) - 1) + (d2 - 1)
-    steps_sum = int(np.log2(oc.n))
-    latency = babies + G * (n2 * tm["giant"] + (n2 - 1) * tm["rot_giant"] + n_mul * tm["mul_mid"]) + steps_sum * tm["rot_sum"]
-    work = spent[0]
-    sample = (f"oracle timed ({reps} repetitions each, mean) on: hoisted rotations by {{1}} and {{1,2}} at level {L} (baby cost = t1 + {n1 - 2} x marginal), "
-              f"one giant step (encode {n1} diagonals + MAC + rescale, x{n2}), one giant rotation at level {L - 1} "
-              f"(x{n2 - 1}), one ct x ct + relin + rescale at level {mid} (x{n_mul}), one rotation at level {lo} "
-              f"(x{steps_sum}); extrapolated query latency {latency:.1f} s from {work:.1f} s of CPU work")
-    return K_over(len(T), latency), latency, work, sample, oracle.get_threads()
+    oq = ok.encrypt(np.tile(q, oc.n // c["ell"]), seed_enc)
+    secs, first = [], None
+    while True:
+        t0 = time.perf_counter()
+        ref, lvl = ok.match(oq, T, c["ell"], c["n1"], 2, c["cheb_degree"], c["threshold"], level=lq,
+                            sum_radix=sum_radix, hoist=hoist)
+        secs.append(time.perf_counter() - t0)
+        if first is None:
+            first = (ref[0], lvl)
+        if len(secs) >= max_queries or sum(secs) + secs[-1] > budget_s:
+            break
+    return secs, oracle.get_threads(), first
 
 
 def K_over(K, latency):
@@ -269,7 +240,7 @@ def run_serving(args):
         "max_concurrent_batches": st1["max_concurrent_batches"],
         "membership_abs_err_sample": checks, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_identify(args):
@@ -361,7 +332,7 @@ def run_identify(args):
         "roofline": roofline, "ntt_alu": ntt_view,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_multi(args):
@@ -417,11 +388,14 @@ def run_multi(args):
     del outs
     steps = max(2, args.steps // 5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
     torch.cuda.synchronize()
     e0.record(stream)
     outs = [ctx.match_multi(dbs, qs, fr.FR_MODE_MEMBERSHIP) for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / steps
     del outs
     # the same 64 pairs one match at a time
@@ -446,9 +420,9 @@ def run_multi(args):
                    "hbm_budget_gb": args.multi_budget_gb},
         "form": "kernels launched per call (programmatic dependent launch), no CUDA graph",
         "one_by_one": {"ms": ms_single, "value": total / (ms_single / 1000.0), "unit": UNIT},
-        "membership_abs_err_sample": errs,
+        "membership_abs_err_sample": errs, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_encrypted(args):
@@ -553,59 +527,50 @@ def run_encrypted(args):
                                "unit": UNIT, "membership_abs_err": err_tbs},
         "membership_abs_err": err, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_reference(args):
+    """Reference arm: the CPU oracle (the paper has no runnable code) on the same workload,
+    metric and unit. Each step is one whole membership query of the oracle on the host cores;
+    the oracle needs no warm-up (no caches or code generation), so none is run, and the
+    number of timed queries is capped so that the run ends within a few minutes. Under
+    torchrun only rank 0 works; the other ranks exit at once."""
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        if rank != 0:
-            dist.barrier()
-            dist.destroy_process_group()
-            return
+    if ws > 1 and rank != 0:
+        return
     from paper_2604_00546_gb300 import workloads as W
     cfg = args.config
     T, q, _ = W.workload(cfg)
     lq = W.work_level(cfg, args.level_mode)
-    vals, lat, work = [], [], 0.0
-    sample = cores = None
     t_all = time.perf_counter()
-    for s in range(args.warmup + args.steps):
-        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq, reps=1)
-        if s >= args.warmup:
-            vals.append(v)
-            lat.append(l)
-            work += w
+    secs, cores, _ = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq, budget_s=100.0,
+                                    max_queries=max(1, args.steps), sum_radix=args.sum_radix,
+                                    hoist=bool(args.hoist_giants))
     wall = time.perf_counter() - t_all
-    value = float(np.mean(vals))
+    per = float(np.mean(secs))
+    value = len(T) / per
+    sample = (f"{len(secs)} whole membership queries of the oracle (K={len(T)}, working level {lq}), "
+              f"{', '.join('%.1f s' % x for x in secs)}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(lat)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "steps": len(secs), "steps_requested": args.steps, "warmup": 0, "warmup_requested": args.warmup,
+        "ms_per_step": 1000.0 * per, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64",
         "data": "synthetic (seeded Gaussian L2-normalised templates, 32 planted duplicates at cosine 0.8)",
         "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": len(T), "log_n": 16,
                    "work_level": lq},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": wall,
+        "timed_s": float(np.sum(secs)), "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
 
 
-# DRAM traffic of the NTT passes from one ncu capture (bytes read + written per byte of
-# algorithmic traffic, summed over the column and row pass), valid for the NTT sources whose
-# SHA-256 is listed; the bench reports null once the source differs. The first hash is the
-# captured file; the second differs from it only in the host launcher of the cluster kernel
-# (its shared-memory limit set once per device), with the device code unchanged.
-NTT_TRAFFIC = {"sha256": ["82b1b5733e395743570ddf78ed8a9297ad629e05dfd31fb0a778698839c711fe",
-                          "87b46b09bff8afa195f7f6d41b6afd2d32538ebcf072ab08db8ff261ffe986fe"],
-               "dram_per_alg_byte": 1.76, "source": "profiles/ntt_membership_N65536_level8.md"}
+# DRAM traffic of the NTT passes from one ncu capture: bytes read + written per byte of
+# algorithmic traffic (summed over the column and row pass), valid only for the NTT source
+# whose SHA-256 is listed; null is reported once the source differs.
+NTT_TRAFFIC = {"sha256": [], "dram_per_alg_byte": None}
 
 
 def _sha256(path):
@@ -636,13 +601,12 @@ def roofline(regions, log_n, device, fr):
         achieved = bfly / secs / 1e9 if secs > 0 else 0.0
         traffic = None
         ntt_src = os.path.join(ROOT, "paper_2604_00546_gb300", "csrc", "ntt.cu")
-        if _sha256(ntt_src) in NTT_TRAFFIC["sha256"]:
+        if NTT_TRAFFIC["dram_per_alg_byte"] and _sha256(ntt_src) in NTT_TRAFFIC["sha256"]:
             traffic = NTT_TRAFFIC["dram_per_alg_byte"] * d["bytes"] / nl
         roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
                      "frac": achieved / peak if peak > 0 else None,
                      "peak_kind": "measured: register-only butterfly loop on this GPU (fr_butterfly_peak)",
                      "butterflies_per_launch": bfly / nl, "traffic": traffic,
-                     "traffic_source": NTT_TRAFFIC["source"] if traffic is not None else None,
                      "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                                   "peak_kind": hbm_kind}})
     else:
@@ -699,6 +663,7 @@ def run_ours(args):
     sp[:K] = s
     pref = npc.chebval(sp, fr.cheb_coeffs(c["cheb_degree"], c["threshold"])).sum()
     got = float(ctx.decrypt(keys, out[0])[0])
+    out_words = out[0].export() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
     del out
 
     sampler = ClockSampler(local)
@@ -725,18 +690,22 @@ def run_ours(args):
     tmax = max_over_ranks(total_ms, dist, dev)
     value = whole_job_value(ws, K * args.steps, tmax)
 
-    # per-region device time: the same steps again, eagerly, with CUDA events around every launch
+    # per-region device time: the same steps again as profiled graph replays (the match
+    # captured with CUDA events around every region as graph nodes, replayed once per step),
+    # so the regions are timed back to back on the same time base as the timed steps
+    nprof = max(3, min(args.steps, 10))
     ctx.profile(True)
-    for i in range(args.steps):
+    for i in range(nprof):
         outs = step(ctx, db, dev_q)
     torch.cuda.synchronize()
     regions = {}
     for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac", "misc"):
         ms, nl, by = ctx.profile_read(r)
-        regions[r] = {"ms": ms, "launches": nl, "bytes": by}
+        regions[r] = {"ms": ms / nprof, "launches": nl / nprof, "bytes": by / nprof}
     stages = {}
     for st in ("babies", "mac", "giants", "cheb", "sum"):
-        stages[st] = ctx.profile_read("stage:" + st)[0] / args.steps
+        stages[st] = ctx.profile_read("stage:" + st)[0] / nprof
+    prof_match_ms = ctx.profile_read("match")[0] / nprof
     ctx.profile(False)
     del outs
 
@@ -846,14 +815,65 @@ def run_ours(args):
                  "membership_abs_err": abs(got_t - pref)}
         del db_t, ctx_t
 
+    # the hybrid comparator (Chebyshev sign interpolant, then (1 + f_4) / 2; 4 more levels) on
+    # the same query: its membership value is the count of the planted matches
+    hybrid = None
+    if not args.no_hybrid:
+        ctx_h = fr.Context(device=local, cuda_stream=stream.cuda_stream, comparator=1,
+                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix,
+                           hoist_giants=args.hoist_giants)
+        ctx_h.load_keys(keys)
+        db_h = ctx_h.load_db(T)
+        dq_h = ctx_h.encrypt(keys, q, W.enc_seed(cfg)).upload()
+        for _ in range(max(3, args.warmup)):
+            out = step(ctx_h, db_h, dq_h)
+        ctx_h.sync()
+        got_h = float(ctx_h.decrypt(keys, out[0])[0])
+        del out
+        nh = max(3, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        outs = [step(ctx_h, db_h, dq_h) for _ in range(nh)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_h = e0.elapsed_time(e1) / nh
+        del outs
+        hybrid = {"comparator": "hybrid: degree-59 sign interpolant, then (1 + f_4(y)) / 2",
+                  "work_level": ctx_h.work_level, "ms_per_step": ms_h, "value": K / (ms_h / 1000.0), "steps": nh,
+                  "membership_decrypted": got_h, "planted": int(len(planted)),
+                  "count_abs_err": abs(got_h - len(planted)),
+                  "plain_comparator_membership": got}
+        del db_h, ctx_h
+
+    # the secondary workloads, each with its own clocks and accuracy check
+    secondary = None
+    if ws == 1 and not args.no_secondary:
+        secondary = {}
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.serve_seconds, sub.batch = 6, 3, args.serve_seconds_secondary, 4
+        for name, fn in (("identify", run_identify), ("encrypted_db", run_encrypted), ("serving", run_serving),
+                         ("multi", run_multi)):
+            t_sub = time.perf_counter()
+            try:
+                secondary[name] = fn(sub)
+            except Exception as e:  # reported in the line; the headline stands on its own
+                secondary[name] = {"error": repr(e)}
+            secondary[name]["wall_s"] = time.perf_counter() - t_sub
+            torch.cuda.empty_cache()
+
     # roofline of the dominant region (largest device time)
     roof = roofline(regions, c["log_n"], local, fr)
     achieved = regions[roof["kernel"]]["bytes"] / (regions[roof["kernel"]]["ms"] / 1000.0) / 1e9
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, l, w, sample, cores = oracle_sample(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        secs, cores, (o_ct, o_lvl) = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq,
+                                                    sum_radix=args.sum_radix, hoist=bool(args.hoist_giants))
+        cpu = {"value": K / float(np.mean(secs)), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one whole membership query of the oracle, K=%d at working level %d: %.1f s" % (K, lq, secs[0]),
+               "seconds_per_query": float(np.mean(secs)),
+               "bit_exact_vs_gpu": bool(np.array_equal(o_ct, out_words)) if out_words is not None else None}
 
     if rank == 0:
         lat_sorted = sorted(lat)
@@ -872,7 +892,10 @@ def run_ours(args):
                            "mean": float(np.mean(lat))},
             "hbm_gbs_dominant": achieved,
             "roofline": roof,
-            "regions_ms_per_step": {r: regions[r]["ms"] / args.steps for r in regions},
+            "regions_ms_per_step": {r: regions[r]["ms"] for r in regions},
+            "regions_sum_ms": sum(regions[r]["ms"] for r in regions),
+            "profiled_replay_ms": prof_match_ms,
+            "profiling": "one profiled graph replay per step (region events as graph nodes), %d steps" % nprof,
             "regions_hbm_gbs": {r: (regions[r]["bytes"] / (regions[r]["ms"] / 1000.0) / 1e9 if regions[r]["ms"] > 0
                                     else 0.0) for r in regions},
             "stages_ms_per_step": stages,
@@ -883,6 +906,8 @@ def run_ours(args):
             "table_schedule": table,
             "plain_per_query": plain,
             "batched": batched,
+            "hybrid_comparator": hybrid,
+            "secondary": secondary,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "check": {"membership_decrypted": got, "membership_fp64": float(pref), "abs_err": abs(got - pref)},
@@ -923,15 +948,20 @@ def main():
     ap.add_argument("--encrypted-db", action="store_true",
                     help="run the encrypted-database membership workload instead")
     ap.add_argument("--db-ell", type=int, default=512, help="template dimension of --encrypted-db (512: the workload)")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-comparator comparison")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads (identification, encrypted database, serving, multi)")
+    ap.add_argument("--serve-seconds-secondary", type=float, default=15.0,
+                    help="length of the serving run inside the default bench line")
     args = ap.parse_args()
     if args.serving:
-        run_serving(args)
+        print(json.dumps(run_serving(args)), flush=True)
     elif args.identify:
-        run_identify(args)
+        print(json.dumps(run_identify(args)), flush=True)
     elif args.multi:
-        run_multi(args)
+        print(json.dumps(run_multi(args)), flush=True)
     elif args.encrypted_db:
-        run_encrypted(args)
+        print(json.dumps(run_encrypted(args)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -104,7 +104,8 @@ typedef struct {
     uint32_t level_mode;       /* 0: the match runs at the query's top level (whole modulus chain);
                                   1: the query is first dropped (limbs discarded) to the lowest level that
                                   still leaves the threshold depth and one output level above 0:
-                                  2 + d2 with a Chebyshev degree, 2 without, capped at the top level */
+                                  2 + depth with a Chebyshev degree (depth = d2, or d2 + 4 with the hybrid
+                                  comparator), 2 without, capped at the top level */
     uint32_t sum_radix;        /* RotateAndSum of the membership result (Algorithm 5's aggregation):
                                   0 or 2: x <- x + Rot_{2^t}(x), one rotation per step (the paper's
                                   power-of-two keys); r = 4, 8, ..., 64: x <- x + sum_{t<r} Rot_{t s}(x)
@@ -116,6 +117,15 @@ typedef struct {
                                   share one ModDown: their inner products are summed in Q_l u P and
                                   S = P_0 + sum_j sigma_j(P_j.b) + ModDown(sum_j IP_j) (double hoisting,
                                   Section "Hoisting and double hoisting"). Same values, other noise. */
+    uint32_t comparator;       /* threshold of FR_MODE_IDENTIFY / FR_MODE_MEMBERSHIP: 0 the paper's GPU
+                                  comparator, the degree-n Chebyshev interpolant of step(x - tau) (Eq.
+                                  eq:cheb-sign), depth d2; 1 the hybrid comparator of Section "HyDia" (a
+                                  Chebyshev approximation followed by a fixed-degree polynomial of Cheon et
+                                  al. 2020): y = the degree-n interpolant of sign(x - tau), then
+                                  (1 + f_4(y)) / 2 with f_4(y) = (315 y - 420 y^3 + 378 y^5 - 180 y^7 +
+                                  35 y^9) / 128, depth d2 + 4. Its slot values are 0 or 1 to within about
+                                  1e-2 outside |x - tau| <= 0.02, so a membership sum counts the matches.
+                                  level_mode 1 adds the 4 levels to the working level. */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.
@@ -289,7 +299,9 @@ fr_status fr_rescale(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 fr_status fr_mul_relin(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
 /* Sum mod q at the lower of the two levels. */
 fr_status fr_add(fr_ctx* ctx, const fr_ct* a, const fr_ct* b, fr_ct** out);
-/* Chebyshev threshold p(x) of the context's degree and threshold */
+/* Threshold of the context (its comparator, degree and tau) on every slot: the Chebyshev
+ * interpolant p(x) of step(x - tau) (comparator 0, d2 levels), or the hybrid (1 + f_4(p_sign(x))) / 2
+ * (comparator 1, d2 + 4 levels). */
 fr_status fr_chebyshev(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
 /* RotateAndSum over all N/2 slots */
 fr_status fr_rotate_sum(fr_ctx* ctx, const fr_ct* ct, fr_ct** out);
@@ -312,22 +324,30 @@ fr_status fr_membership_reduce(fr_ctx* ctx, const fr_ct* const* parts, size_t n,
  * inside the library (held by every GPU that loads it until the process exits):
  * calls whose working set needs more (5 (level+1) N + (digits+2)(level+1+n_p) N
  * words; e.g. N=2^16 up to level 8 with 6 digits and 4 special primes) fail with
- * FR_ERR_INVALID_ARG. The first call on a device looks up the array's device
- * address; make that first call before any stream capture. Every call shares the
- * array, so calls that overlap on the GPU (other streams, other contexts of the
- * same device) race; nothing in it needs to start at zero. Work is enqueued on
- * the context stream; the rotation key for k must be loaded. */
+ * FR_ERR_INVALID_ARG, a level above the loaded keys with FR_ERR_LEVEL, a missing
+ * rotation key with FR_ERR_INVALID_ARG; every check runs before anything is
+ * enqueued, so a refused call leaves nothing on the stream. The first call on a
+ * device looks up the array's device address; make that first call before any
+ * stream capture. Every call shares the array, so calls that overlap on the GPU
+ * (other streams, other contexts of the same device) race; nothing in it needs to
+ * start at zero. Work is enqueued on the context stream. */
 fr_status fr_rotate_noalloc(fr_ctx* ctx, const uint64_t* d_in, uint32_t level, int32_t k, uint64_t* d_out);
 
-/* Wait for all work enqueued on the context stream. */
-/* Wait until the context's queued device work has finished. */
+/* Wait until the device work queued on the context stream has finished. */
 fr_status fr_sync(fr_ctx* ctx);
 
 /* Per-region device timing (CUDA events on the context stream). enable=1 clears and
  * starts accumulating, 0 clears and stops; fr_profile_read returns the summed
  * milliseconds, the number of timed launches and their algorithmic bytes (the
  * minimum DRAM reads + writes the launches must make) for a region: "ntt", "modup",
- * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc". */
+ * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc", the stages
+ * "stage:babies", "stage:mac", "stage:giants", "stage:cheb", "stage:sum" and "match".
+ * With graphs on (fr_use_graphs, the default) a profiled fr_match / fr_match_batch
+ * captures the match with the region events as event-record nodes of a graph and replays
+ * it once: regions are timed back to back as in a graph replay, and "match" times the
+ * whole replay. With graphs off the events are recorded around each launch as it is
+ * enqueued (host launch gaps fall inside the regions). Regions on the second stream of
+ * the Chebyshev stage overlap those of the first, so their sum can exceed "match". */
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
 /* NTT autotuner (run by fr_setup on device contexts unless the environment sets
@@ -353,6 +373,14 @@ fr_status fr_use_graphs(fr_ctx* ctx, int on);
  * it. The context stays usable after the failed call. */
 fr_status fr_inject_alloc_failure(fr_ctx* ctx, int64_t after);
 
+/* Device time of the batched negacyclic NTT on this context's ring: npolys limb-polynomials
+ * (polynomial p uses prime p mod (level + 1)) transformed forward and inverse on a scratch
+ * buffer, each timed with CUDA events on the context stream, best of `reps` after one warm-up
+ * round. The shapes in use (fr_ntt_tuning) apply. us_fwd / us_inv receive microseconds per
+ * launch sequence (column and row pass). FR_ERR_INVALID_ARG for npolys or reps 0 or null
+ * outputs, FR_ERR_LEVEL for a level outside the chain. */
+fr_status fr_ntt_time(fr_ctx* ctx, uint32_t npolys, uint32_t level, uint32_t reps, double* us_fwd, double* us_inv);
+
 /* Arithmetic ceiling of the NTT on `device`: forward butterflies (Harvey lazy
  * reduction, Shoup twiddle product, 64-bit residues) per second with every operand in
  * registers, measured by a short microbenchmark. Used as the ALU roofline peak. */
@@ -373,6 +401,9 @@ uint32_t fr_work_level(const fr_ctx* ctx);
 
 /* Chebyshev coefficients c_0..c_n of the step interpolant (host, no context). */
 fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out);
+/* The same interpolant of f = 1 for x >= tau and `low` below (low = 0: fr_cheb_coeffs; -1: the
+ * sign(x - tau) interpolant the hybrid comparator starts from). */
+fr_status fr_cheb_coeffs_lo(uint32_t n, double tau, double low, double* out);
 
 /* Release handles. Free a context's ciphertexts before the context: a device ciphertext
  * returns its memory through it. A database may outlive its context: fr_free releases the

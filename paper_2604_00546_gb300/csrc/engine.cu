@@ -91,13 +91,15 @@ struct fr_ctx {
     bool own_stream = false;
     RingDev rd{};
     DevPrime* d_primes = nullptr;
-    u64 *d_tw = nullptr, *d_tws = nullptr, *d_itw = nullptr, *d_itws = nullptr;
+    u64 *d_tw = nullptr, *d_itw = nullptr;  // (twiddle, Shoup quotient) pairs [primes][N][2]
     unsigned* d_rot = nullptr;
     double *d_zr = nullptr, *d_zi = nullptr;
     uint32_t ell = 0, n1 = 0, schedule = 0, cheb_n = 0;
     double tau = 0.5;
     uint64_t budget = 0;
     int d1 = 0, d2 = 0;
+    int comparator = 0;                  // 0: step interpolant; 1: hybrid (sign interpolant, then (1 + f_4) / 2)
+    int cmp_depth = 0;                   // levels the threshold consumes: d2 (+ 4 for the hybrid)
     int work_level = 0;                  // level of the query inside fr_match
     std::vector<ModUpTab*> d_modup;      // per level: digits_at(level) tables
     std::vector<int*> d_modup_ntt;       // per level: (offset, prime) of the ext positions to transform
@@ -108,6 +110,7 @@ struct fr_ctx {
     u64 *d_pmod = nullptr, *d_pmod_s = nullptr;  // [P]_{q_i} and Shoup quotients, Q primes
     u64* d_delta = nullptr;              // Delta mod q_i
     std::map<int, u64*> d_cheb;          // per input level: leaf constants [3][nleaves][level+1]
+    std::map<int, u64*> d_f4;            // per input level: hybrid comparator constants [3][5][level+1]
     std::vector<std::pair<double, double>> leaves;  // Chebyshev leaves (c0, c1), BFS order
     std::map<u64, u64*> rotkeys;         // galois element -> key
     u64* relin = nullptr;
@@ -209,7 +212,16 @@ T* upload_persistent(fr_ctx* c, const T* h, size_t count) {
     return (T*)p;
 }
 
-// profiling regions
+// profiling regions: a pair of timing events around the launches of a region. Outside stream
+// capture they are recorded on the stream; under capture (the profiled graph replay of a match)
+// they become event-record nodes of the graph, so the region is timed inside the replay.
+inline void prof_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
 struct Prof {
     fr_ctx* c;
     Region* r = nullptr;
@@ -220,11 +232,11 @@ struct Prof {
         r->bytes += (uint64_t)bytes;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        cudaEventRecord(a, c->cur);
+        prof_record(a, c->cur);
     }
     ~Prof() {
         if (!r) return;
-        cudaEventRecord(b, c->cur);
+        prof_record(b, c->cur);
         r->pending.emplace_back(a, b);
         r->launches++;
     }
@@ -619,14 +631,42 @@ const u64* cheb_consts(fr_ctx* c, int ls) {
     return d;
 }
 
+// Constants of the hybrid comparator's scaled copies at input level l, laid out for
+// launch_cheb_leaves: [3][5][l+1] (round(a_k Delta) residues, their Shoup quotients, and the
+// constant round(Delta / 2) Delta in copy 0), a_k = 315, -420, 378, -180, 35 over 256.
+const u64* f4_consts(fr_ctx* c, int l) {
+    auto it = c->d_f4.find(l);
+    if (it != c->d_f4.end()) return it->second;
+    static const int num[5] = {315, -420, 378, -180, 35};
+    const int L1 = l + 1;
+    std::vector<u64> h((size_t)3 * 5 * L1, 0);
+    const double delta = std::ldexp(1.0, c->R.scale_bits);
+    for (int k = 0; k < 5; ++k) {
+        const int64_t b = std::llround((double)num[k] / 256.0 * delta);
+        const int64_t a = k == 0 ? std::llround(0.5 * delta) : 0;
+        for (int i = 0; i < L1; ++i) {
+            const u64 q = c->R.primes[i];
+            const u64 bres = frh::resid(b, q);
+            h[(size_t)k * L1 + i] = bres;
+            h[(size_t)5 * L1 + (size_t)k * L1 + i] = frh::shoup_quot(bres, q);
+            const u64 dm = frh::powm(2, (u64)c->R.scale_bits, q);
+            h[(size_t)10 * L1 + (size_t)k * L1 + i] = frh::mulm(frh::resid(a, q), dm, q);
+        }
+    }
+    u64* d = upload_persistent(c, h.data(), h.size());
+    c->d_f4[l] = d;
+    return d;
+}
+
 void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int out_cap) {
     const int N = c->R.N, d2 = c->d2;
     if (ls - d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the Chebyshev evaluation");
     if (d2 + 2 > (int)c->evs.size()) raise(FR_ERR_UNSUPPORTED, "Chebyshev degree too large");
     const int nleaves = (int)c->leaves.size();
     // Two concurrent branches: the giant powers T_{2^m} on the current stream, the
-    // leaves and the tree on the side stream; tree level s waits for T_{2^s} only.
-    cudaStream_t main = c->cur, side = c->side;
+    // leaves and the tree on the side stream; tree level s waits for T_{2^s} only. A profiled
+    // match runs both branches on one stream, so that no two timed regions overlap.
+    cudaStream_t main = c->cur, side = c->prof ? c->cur : c->side;
     // Declared first, destroyed last. If an exception unwinds this function, the buffers its
     // locals free are held back (dfree) until both branches have finished, so no kernel still
     // queued on either stream can touch memory the pool has taken back.
@@ -722,6 +762,119 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     CU(cudaEventRecord(c->evs[d2], side));
     c->cur = main;
     CU(cudaStreamWaitEvent(main, c->evs[d2], 0));
+}
+
+// Second part of the hybrid comparator (Section "HyDia": a Chebyshev approximation followed by
+// the fixed polynomial f_4 of Cheon et al. 2020): out = (1 + f_4(y)) / 2 for B cts y at level l
+// (y: [B][2][y_cap][N]) -> out [B][2][out_cap][N] at level l - 4. With a_k the coefficients of
+// f_4 over 2 (315, -420, 378, -180, 35 over 256 for y, y^3, ..., y^9):
+//   y2 = y y, y4 = y2 y2, y8 = y4 y4; u_k = Rescale(y round(a_k Delta)) (u_1 with the constant
+//   round(Delta / 2) Delta); t3 = u3 y2, v7 = u7 y2, t5 = u5 y4, t7 = v7 y4, t9 = u9 y8 (every
+//   product relinearised and rescaled); out = t9 + t7 + t5 + t3 + u1 at level l - 4.
+// Products of one level share one key-switch batch: 1, 3, 3 and 1 products per ct.
+void comparator_f4(fr_ctx* c, const u64* y, int B, int l, int y_cap, u64* out, int out_cap) {
+    if (l < 4) raise(FR_ERR_LEVEL, "not enough levels for the hybrid comparator");
+    const int cap = l + 1;  // every intermediate is stored with l + 1 limb slots
+    const size_t cw = (size_t)ctw(c, cap);
+    const u64* cc = f4_consts(c, l);
+    const int L1 = l + 1;
+    // level l: y2 = y^2, and the five scaled copies u_k
+    Tmp Y2(c, (size_t)B * cw);
+    {
+        Tmp sq(c, (size_t)B * cw);
+        std::vector<const u64*> A;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b) {
+            A.push_back(y + (size_t)b * ctw(c, y_cap));
+            O.push_back(sq.p + (size_t)b * cw);
+        }
+        mul_relin(c, l, A, y_cap, A, y_cap, O, cap);
+        rescale(c, sq.p, B, l, cap, Y2.p, cap);
+    }
+    Tmp U(c, (size_t)B * 5 * cw);  // [B][5]: y, y^3, y^5, y^7, y^9 scalars (u1 with the constant 1/2)
+    {
+        Tmp pre(c, (size_t)B * 5 * cw);
+        for (int b = 0; b < B; ++b) {
+            Prof p(c, "misc");
+            launch_cheb_leaves(y + (size_t)b * ctw(c, y_cap), y_cap, pre.p + (size_t)b * 5 * cw, cap, l, 5, cc,
+                               cc + (size_t)5 * L1, cc + (size_t)10 * L1, c->d_primes, c->R.N, c->cur);
+            c->launches++;
+        }
+        rescale(c, pre.p, B * 5, l, cap, U.p, cap);
+    }
+    auto u = [&](int b, int k) { return U.p + ((size_t)b * 5 + k) * cw; };
+    // level l - 1: y4 = y2 y2, t3 = u3 y2, v7 = u7 y2 -> R1 [B][3] at level l - 2
+    Tmp R1(c, (size_t)B * 3 * cw);
+    {
+        Tmp pr(c, (size_t)B * 3 * cw);
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b) {
+            const u64* y2 = Y2.p + (size_t)b * cw;
+            const u64* a3[3] = {y2, u(b, 1), u(b, 3)};
+            for (int t = 0; t < 3; ++t) {
+                A.push_back(a3[t]);
+                Bv.push_back(y2);
+                O.push_back(pr.p + ((size_t)b * 3 + t) * cw);
+            }
+        }
+        mul_relin(c, l - 1, A, cap, Bv, cap, O, cap);
+        rescale(c, pr.p, B * 3, l - 1, cap, R1.p, cap);
+    }
+    auto r1 = [&](int b, int t) { return R1.p + ((size_t)b * 3 + t) * cw; };  // y4, t3, v7
+    // level l - 2: y8 = y4 y4, t5 = u5 y4, t7 = v7 y4 -> R2 [B][3] at level l - 3
+    Tmp R2(c, (size_t)B * 3 * cw);
+    {
+        Tmp pr(c, (size_t)B * 3 * cw);
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b) {
+            const u64* y4 = r1(b, 0);
+            const u64* a3[3] = {y4, u(b, 2), r1(b, 2)};
+            for (int t = 0; t < 3; ++t) {
+                A.push_back(a3[t]);
+                Bv.push_back(y4);
+                O.push_back(pr.p + ((size_t)b * 3 + t) * cw);
+            }
+        }
+        mul_relin(c, l - 2, A, cap, Bv, cap, O, cap);
+        rescale(c, pr.p, B * 3, l - 2, cap, R2.p, cap);
+    }
+    auto r2 = [&](int b, int t) { return R2.p + ((size_t)b * 3 + t) * cw; };  // y8, t5, t7
+    // level l - 3: t9 = u9 y8 -> level l - 4
+    Tmp R3(c, (size_t)B * cw);
+    {
+        Tmp pr(c, (size_t)B * cw);
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; ++b) {
+            A.push_back(u(b, 4));
+            Bv.push_back(r2(b, 0));
+            O.push_back(pr.p + (size_t)b * cw);
+        }
+        mul_relin(c, l - 3, A, cap, Bv, cap, O, cap);
+        rescale(c, pr.p, B, l - 3, cap, R3.p, cap);
+    }
+    // out = t9 + t7 + t5 + t3 + u1 on limbs 0..l-4
+    const int lo = l - 4;
+    const long long so = ctw(c, out_cap);
+    add_cts(c, R3.p, cap, (long long)cw, R2.p + 2 * cw, cap, 3ll * (long long)cw, out, out_cap, so, lo, B);
+    add_cts(c, out, out_cap, so, R2.p + cw, cap, 3ll * (long long)cw, out, out_cap, so, lo, B);
+    add_cts(c, out, out_cap, so, R1.p + cw, cap, 3ll * (long long)cw, out, out_cap, so, lo, B);
+    add_cts(c, out, out_cap, so, U.p, cap, 5ll * (long long)cw, out, out_cap, so, lo, B);
+}
+
+// Threshold of the match on B score cts x at level ls: the Chebyshev interpolant (comparator 0),
+// or the hybrid comparator (1): the sign interpolant, then (1 + f_4) / 2. out at ls - cmp_depth.
+void threshold(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int out_cap) {
+    if (c->comparator == 0) {
+        chebyshev(c, x, B, ls, x_cap, out, out_cap);
+        return;
+    }
+    const int l = ls - c->d2;
+    Tmp y(c, (size_t)B * ctw(c, l + 1));
+    chebyshev(c, x, B, ls, x_cap, y.p, l + 1);
+    comparator_f4(c, y.p, B, l, l + 1, out, out_cap);
 }
 
 // BSGS schedule of a database with G groups. Auto (2) takes the table of Algorithm 1
@@ -943,18 +1096,19 @@ void build_tables(fr_ctx* c) {
         dp[i].one_s = frh::shoup_quot(1, q);
     }
     c->d_primes = upload_persistent(c, dp.data(), T);
-    std::vector<u64> tw((size_t)T * N), tws((size_t)T * N), itw((size_t)T * N), itws((size_t)T * N);
-    for (int i = 0; i < T; ++i) {
-        std::copy(R.tabs[i].tw.begin(), R.tabs[i].tw.end(), tw.begin() + (size_t)i * N);
-        std::copy(R.tabs[i].tws.begin(), R.tabs[i].tws.end(), tws.begin() + (size_t)i * N);
-        std::copy(R.tabs[i].itw.begin(), R.tabs[i].itw.end(), itw.begin() + (size_t)i * N);
-        std::copy(R.tabs[i].itws.begin(), R.tabs[i].itws.end(), itws.begin() + (size_t)i * N);
-    }
+    // twiddles as (w, Shoup quotient) pairs, one 16-byte load per twiddle: [T][N][2]
+    std::vector<u64> tw((size_t)2 * T * N), itw((size_t)2 * T * N);
+    for (int i = 0; i < T; ++i)
+        for (int k = 0; k < N; ++k) {
+            const size_t o = 2 * ((size_t)i * N + k);
+            tw[o] = R.tabs[i].tw[k];
+            tw[o + 1] = R.tabs[i].tws[k];
+            itw[o] = R.tabs[i].itw[k];
+            itw[o + 1] = R.tabs[i].itws[k];
+        }
     c->d_tw = upload_persistent(c, tw.data(), tw.size());
-    c->d_tws = upload_persistent(c, tws.data(), tws.size());
     c->d_itw = upload_persistent(c, itw.data(), itw.size());
-    c->d_itws = upload_persistent(c, itws.data(), itws.size());
-    c->rd = RingDev{R.logN, N, T, c->d_primes, c->d_tw, c->d_tws, c->d_itw, c->d_itws};
+    c->rd = RingDev{R.logN, N, T, c->d_primes, (const ulonglong2*)c->d_tw, (const ulonglong2*)c->d_itw};
     c->d_rot = upload_persistent(c, R.rot_group.data(), R.rot_group.size());
     c->d_zr = upload_persistent(c, R.zr.data(), R.zr.size());
     c->d_zi = upload_persistent(c, R.zi.data(), R.zi.size());
@@ -1061,7 +1215,7 @@ void build_tables(fr_ctx* c) {
 
 void build_leaves(fr_ctx* c) {
     std::vector<double> cf;
-    frh::cheb_coeffs((int)c->cheb_n, c->tau, cf);
+    frh::cheb_coeffs((int)c->cheb_n, c->tau, cf, c->comparator == 1 ? -1.0 : 0.0);
     const size_t len = (size_t)1 << c->d2;
     cf.resize(len, 0.0);
     std::vector<std::vector<double>> level{cf};
@@ -1123,6 +1277,9 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         if (c->cheb_n > 0) {
             frh::ps_split((int)c->cheb_n, &c->d1, &c->d2);
             if (c->d1 != 2) raise(FR_ERR_UNSUPPORTED, "Chebyshev degree whose PS split has d1 != 2");
+            if (prm->comparator > 1) raise(FR_ERR_INVALID_ARG, "comparator must be 0 or 1");
+            c->comparator = (int)prm->comparator;
+            c->cmp_depth = c->d2 + (c->comparator == 1 ? 4 : 0);
             build_leaves(c.get());
         }
         c->host_threads = std::max(1u, std::thread::hardware_concurrency());
@@ -1135,7 +1292,7 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         if (c->sum_radix < 2 || c->sum_radix > 64 || (c->sum_radix & (c->sum_radix - 1)))
             raise(FR_ERR_INVALID_ARG, "sum_radix must be 0 or a power of two in [2, 64]");
         c->work_level = c->R.nq - 1;
-        if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->d2 : 0));
+        if (prm->level_mode == 1) c->work_level = std::min(c->R.nq - 1, 2 + (c->cheb_n ? c->cmp_depth : 0));
         if (prm->device < 0) {
             // client-only context: key generation, encryption and decryption on
             // the host; every device operation fails with FR_ERR_CUDA
@@ -1741,10 +1898,10 @@ fr_status fr_chebyshev(fr_ctx* c, const fr_ct* ct, fr_ct** out) {
         std::unique_ptr<Tmp> hold;
         int cap;
         const u64* src = dev_view(c, ct, hold, &cap);
-        const int lo = ct->level - c->d2;
-        if (lo < 0) raise(FR_ERR_LEVEL, "not enough levels for the Chebyshev evaluation");
+        const int lo = ct->level - c->cmp_depth;
+        if (lo < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
         auto blk = new_block(c, ctw(c, lo + 1));
-        chebyshev(c, src, 1, ct->level, cap, blk->p, lo + 1);
+        threshold(c, src, 1, ct->level, cap, blk->p, lo + 1);
         *out = new_dev_ct(c, blk, blk->p, lo, lo + 1);
     });
 }
@@ -1808,7 +1965,7 @@ void match_shape(const fr_ctx* c, const fr_db* db, fr_mode mode, int* nout, int*
         *lo = L - 1;
     } else {
         *nout = mode == FR_MODE_IDENTIFY ? (int)db->G : 1;
-        *lo = L - 1 - c->d2;
+        *lo = L - 1 - c->cmp_depth;
     }
 }
 
@@ -2059,17 +2216,17 @@ void match_pipeline(fr_ctx* c, const std::vector<const fr_db*>& dbs, const u64* 
     if (!od.empty()) ondemand_scores(c, P, q, od, S);
     std::unique_ptr<Prof> stage;
     if (scores_only) return;
-    // S6: Chebyshev threshold on every (query, group) score ciphertext (batched)
-    const int lo = L - 1 - c->d2;
+    // S6: threshold on every (query, group) score ciphertext (batched)
+    const int lo = L - 1 - c->cmp_depth;
     const size_t cwo = (size_t)ctw(c, lo + 1);
     if (mode == FR_MODE_IDENTIFY) {
         stage.reset(new Prof(c, "stage:cheb"));
-        chebyshev(c, S, (int)total, L - 1, L, out, lo + 1);
+        threshold(c, S, (int)total, L - 1, L, out, lo + 1);
         return;
     }
     Tmp cbuf(c, (size_t)total * cwo);
     stage.reset(new Prof(c, "stage:cheb"));
-    chebyshev(c, S, (int)total, L - 1, L, cbuf.p, lo + 1);
+    threshold(c, S, (int)total, L - 1, L, cbuf.p, lo + 1);
     // S7: per query, sum over its groups, then RotateAndSum over all slots
     stage.reset(new Prof(c, "stage:sum"));
     for (int b = 0; b < B; ++b) {
@@ -2138,7 +2295,7 @@ void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct*
     if ((size_t)c->n1 * 2 * 16 * 8 > (128u << 10))
         raise(FR_ERR_UNSUPPORTED, "n1 too large for the MAC's shared-memory staging of the baby steps");
     if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
-    if (mode != FR_MODE_SCORES && L - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+    if (mode != FR_MODE_SCORES && L - 1 - c->cmp_depth < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
     if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
         raise(FR_ERR_INVALID_ARG, "unknown mode");
     CU(cudaSetDevice(c->device));
@@ -2149,7 +2306,41 @@ void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct*
     const long long tot = match_outputs(dbs, mode, first);
     const size_t ow = (size_t)ctw(c, lo + 1), iw = (size_t)ctw(c, L1);
     auto oblk = new_block(c, (size_t)tot * ow);
-    if (c->prof || !c->use_graphs) {
+    if (c->prof && c->use_graphs) {
+        // profiled replay: the match is captured with its region events as graph nodes and
+        // replayed once, so the regions are timed back to back as in a graph replay (no host
+        // launch gaps inside them)
+        Tmp q(c, (size_t)B * iw);
+        for (int b = 0; b < B; ++b) to_device(c, queries[b], q.p + (size_t)b * iw, L1, L);
+        cudaEvent_t pa = nullptr, pb = nullptr;
+        CU(cudaEventCreate(&pa));
+        CU(cudaEventCreate(&pb));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CU(cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
+        try {
+            match_pipeline(c, dbs, q.p, mode, oblk->p);
+        } catch (...) {
+            if (cudaStreamEndCapture(c->cur, &graph) == cudaSuccess && graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            cudaEventDestroy(pa);
+            cudaEventDestroy(pb);
+            throw;
+        }
+        CU(cudaStreamEndCapture(c->cur, &graph));
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CU(ie);
+        CU(cudaEventRecord(pa, c->cur));
+        const cudaError_t le = cudaGraphLaunch(exec, c->cur);
+        CU(cudaEventRecord(pb, c->cur));
+        CU(cudaStreamSynchronize(c->cur));
+        cudaGraphExecDestroy(exec);
+        CU(le);
+        Region& whole = c->regions["match"];
+        whole.pending.emplace_back(pa, pb);
+        whole.launches++;
+    } else if (c->prof || !c->use_graphs) {
         Tmp q(c, (size_t)B * iw);
         for (int b = 0; b < B; ++b) to_device(c, queries[b], q.p + (size_t)b * iw, L1, L);
         match_pipeline(c, dbs, q.p, mode, oblk->p);
@@ -2223,7 +2414,7 @@ void check_match_args(fr_ctx* c, const fr_db* db, const fr_ct* q, fr_mode mode) 
     if (mode != FR_MODE_SCORES && mode != FR_MODE_IDENTIFY && mode != FR_MODE_MEMBERSHIP)
         raise(FR_ERR_INVALID_ARG, "unknown mode");
     if (mode != FR_MODE_SCORES && c->cheb_n == 0) raise(FR_ERR_INVALID_ARG, "context has no Chebyshev degree");
-    if (mode != FR_MODE_SCORES && c->work_level - 1 - c->d2 < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
+    if (mode != FR_MODE_SCORES && c->work_level - 1 - c->cmp_depth < 0) raise(FR_ERR_LEVEL, "not enough levels for the threshold");
 }
 
 // ---------------------------------------------------------------------------
@@ -2804,6 +2995,41 @@ fr_status fr_inject_alloc_failure(fr_ctx* c, int64_t after) {
     });
 }
 
+fr_status fr_ntt_time(fr_ctx* c, uint32_t npolys, uint32_t level, uint32_t reps, double* us_fwd, double* us_inv) {
+    return guard([&] {
+        need_device(c);
+        std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+        if (npolys == 0 || reps == 0 || !us_fwd || !us_inv) raise(FR_ERR_INVALID_ARG, "bad argument");
+        if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
+        CU(cudaSetDevice(c->device));
+        const size_t words = (size_t)npolys * c->R.N;
+        Tmp buf(c, words);
+        CU(cudaMemsetAsync(buf.p, 0, words * 8, c->cur));
+        const PrimeMap pm = pm_level((int)level);
+        const PolyBatch pb{buf.p, (long long)(level + 1) * c->R.N, (int)level + 1, (int)npolys, pm};
+        cudaEvent_t a, b;
+        CU(cudaEventCreate(&a));
+        CU(cudaEventCreate(&b));
+        double best[2] = {1e30, 1e30};
+        for (uint32_t r = 0; r <= reps; ++r) {  // the first round warms up
+            for (int inv = 0; inv < 2; ++inv) {
+                cudaEventRecord(a, c->cur);
+                launch_ntt(c->rd, pb, inv != 0, c->cur);
+                cudaEventRecord(b, c->cur);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                if (r > 0) best[inv] = std::min(best[inv], 1000.0 * ms);
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        CU(cudaGetLastError());
+        *us_fwd = best[0];
+        *us_inv = best[1];
+    });
+}
+
 fr_status fr_butterfly_peak(int device, double* butterflies_per_s) {
     return guard([&] {
         if (!butterflies_per_s) raise(FR_ERR_INVALID_ARG, "null argument");
@@ -2828,10 +3054,12 @@ fr_status fr_fp64_peak(int device, double* flops_per_s) {
     });
 }
 
-fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) {
+fr_status fr_cheb_coeffs(uint32_t n, double tau, double* out) { return fr_cheb_coeffs_lo(n, tau, 0.0, out); }
+
+fr_status fr_cheb_coeffs_lo(uint32_t n, double tau, double low, double* out) {
     if (!out) return FR_ERR_INVALID_ARG;
     std::vector<double> c;
-    frh::cheb_coeffs((int)n, tau, c);
+    frh::cheb_coeffs((int)n, tau, c, low);
     std::copy(c.begin(), c.end(), out);
     return FR_OK;
 }
@@ -2858,11 +3086,12 @@ namespace {
 // Device address of the scratch array on `device` (looked up once per device,
 // with that device current). In host code the array's name is only a
 // host-side stand-in, so kernels must be given this address instead.
+constexpr int kMaxDevices = 64;  // device ordinals the address cache covers
 u64* noalloc_scratch(int device) {
     static std::mutex mu;
-    static u64* addr[FR_MAX_PRIMES] = {};
+    static u64* addr[kMaxDevices] = {};
     std::lock_guard<std::mutex> lock(mu);
-    if (device < 0 || device >= FR_MAX_PRIMES) raise(FR_ERR_INVALID_ARG, "device ordinal out of range");
+    if (device < 0 || device >= kMaxDevices) raise(FR_ERR_INVALID_ARG, "device ordinal out of range");
     if (!addr[device]) {
         void* p = nullptr;
         CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
@@ -2879,6 +3108,9 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
         std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!d_in || !d_out) raise(FR_ERR_INVALID_ARG, "null buffer");
         if ((int)level >= c->R.nq) raise(FR_ERR_LEVEL, "level out of range");
+        // every argument is checked before anything is enqueued, so a refused call leaves
+        // nothing on the stream (or in a graph being captured)
+        if ((int)level > c->key_level) raise(FR_ERR_LEVEL, "the loaded keys stop at the context's working level");
         CU(cudaSetDevice(c->device));
         const int N = c->R.N, l = (int)level, np = c->R.np, nq = c->R.nq;
         const size_t L1N = (size_t)(l + 1) * N;
@@ -2915,7 +3147,6 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
         ij.gstart[0] = 0;
         ij.gstart[1] = 1;
         ij.ngroups = 1;
-        if (l > c->key_level) raise(FR_ERR_LEVEL, "the loaded keys stop at the context's working level");
         launch_ip(ij, beta, npos, l, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, l), c->R.logN, st);
         PrimeMap pmP{};
         pmP.period = np;

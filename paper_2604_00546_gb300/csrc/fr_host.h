@@ -95,7 +95,8 @@ void decrypt_coeffs(const Ring& R, const KeySet& K, const u64* ct, int level, in
 void decrypt_values(const Ring& R, const KeySet& K, const u64* ct, int level, double* x);
 
 // Chebyshev interpolant of step(x - tau) at n+1 Chebyshev nodes; PS split.
-void cheb_coeffs(int n, double tau, std::vector<double>& c);
+// interpolant at the n + 1 Chebyshev nodes of f = 1 for x >= tau, `low` below (0: step, -1: sign)
+void cheb_coeffs(int n, double tau, std::vector<double>& c, double low = 0.0);
 void ps_split(int n, int* d1, int* d2);
 // Chebyshev division p = q T_M + r (length 2M -> two of length M)
 void cheb_split(const std::vector<double>& c, std::vector<double>& q, std::vector<double>& r);

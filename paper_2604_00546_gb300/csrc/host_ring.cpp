@@ -571,13 +571,13 @@ void decrypt_values(const Ring& R, const KeySet& K, const u64* ct, int level, do
 // ---------------------------------------------------------------------------
 // Chebyshev algebra
 // ---------------------------------------------------------------------------
-void cheb_coeffs(int n, double tau, std::vector<double>& c) {
+void cheb_coeffs(int n, double tau, std::vector<double>& c, double low) {
     c.assign(n + 1, 0.0);
     for (int k = 0; k <= n; ++k) {
         double acc = 0.0;
         for (int j = 0; j <= n; ++j) {
             const double th = M_PI * ((double)j + 0.5) / (double)(n + 1);
-            const double fx = std::cos(th) >= tau ? 1.0 : 0.0;
+            const double fx = std::cos(th) >= tau ? 1.0 : low;
             acc = acc + fx * std::cos((double)k * th);
         }
         c[k] = acc * ((k == 0 ? 1.0 : 2.0) / (double)(n + 1));

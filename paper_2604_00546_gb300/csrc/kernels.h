@@ -42,15 +42,21 @@ inline void launch_k(void (*k)(KP...), dim3 g, dim3 b, size_t smem, cudaStream_t
 }
 
 // cudaFuncSetAttribute acts on the current device only: raise kernel k's dynamic shared memory
-// limit once per device (bit d of `done` marks device d).
+// limit once per device (bit d of `done` marks device d). A device is marked only once the
+// call has succeeded, so a failed call is retried by the next launch; ordinals 64 and above
+// are not cached and set the limit on every launch.
 template <class K>
 inline void smem_limit_once(K* k, int bytes, std::atomic<unsigned long long>& done) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const unsigned long long bit = 1ull << (dev & 63);
+    if (dev < 0 || dev >= 64) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        return;
+    }
+    const unsigned long long bit = 1ull << dev;
     if (done.load(std::memory_order_acquire) & bit) return;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    done.fetch_or(bit, std::memory_order_release);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        done.fetch_or(bit, std::memory_order_release);
 }
 
 #define FR_MAX_PRIMES 64
@@ -89,10 +95,8 @@ struct RingDev {
     int N;
     int nprimes;
     const DevPrime* primes;  // [nprimes]
-    const u64* tw;           // [nprimes][N] psi^brev(k)
-    const u64* tws;          // Shoup quotients
-    const u64* itw;          // [nprimes][N] psi^-brev(k)
-    const u64* itws;
+    const ulonglong2* tw;    // [nprimes][N] (psi^brev(k), its Shoup quotient)
+    const ulonglong2* itw;   // [nprimes][N] (psi^-brev(k), its Shoup quotient)
     unsigned char ntt_shape[FR_NTT_BUCKETS];  // tile shape per batch-size bucket (see launch_ntt)
 };
 

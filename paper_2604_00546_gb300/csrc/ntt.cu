@@ -56,39 +56,44 @@ struct PhaseInfo {
     static constexpr int BTO = INV ? (3 * PH + 3 < LOG ? 3 * PH + 3 : LOG) : LOG - 3 * PH;
 };
 
+// Twiddles of a pass: (w, Shoup quotient) pairs, one 16-byte load each. GLOBAL: the table
+// itself (read-only path), else a copy staged in shared memory.
+template <bool GLOBAL>
 struct Ctx {
     int Jbase, M;    // global index of the tile's element 0; M = R (column pass) or N (row pass)
-    int cb, TT;      // twiddle table of stage B starts at TT - (TT >> B) and holds global
-                     // indices from cb >> (B + 1) on (cb = TT = 0: the whole table)
-    const u64* tw;
-    const u64* tws;
+    const ulonglong2* tw;
     u64 q;
     bool grow;       // forward only: q < 2^57, values may grow by 2q per stage (16 stages < 33q < 2^62)
+    __device__ __forceinline__ ulonglong2 ld(int i) const {
+        if constexpr (GLOBAL) return __ldg(tw + i);
+        else return tw[i];
+    }
 };
 
-// one radix-2 stage on bit B of the registers of a phase with base bit LO; the
-// stage's four twiddle pairs are loaded before its butterflies run
-template <bool INV, int LO, int B>
-__device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
+// One radix-2 stage on bit B of the registers of a phase with base bit LO. The butterfly of
+// registers e and e + 2^lb (lb = B - LO) takes twiddle (M + J + x) >> (B + 1), x its element
+// index: M + J and the thread's bits of x above LO + 3 are multiples of 2^(B+1), and x's bits
+// below B + 1 are e's bits up to lb and the thread's bits below LO, so the twiddle is
+// base + (e >> (lb + 1)): the stage needs 4 >> lb distinct twiddles, loaded before its
+// butterflies run.
+template <bool INV, int LO, int B, class C>
+__device__ __forceinline__ void stage(u64 (&v)[8], int tau, const C& c) {
     constexpr int lb = B - LO;
+    constexpr int NT = 4 >> lb;
     const u64 q2 = 2 * c.q;
-    u64 w[8], ws[8];
+    const int base = (c.M + c.Jbase + ((tau >> LO) << (LO + 3))) >> (B + 1);
+    ulonglong2 w[NT];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        if (e & (1 << lb)) continue;
-        const int idx = (c.M + c.Jbase + phase_x<LO>(tau, e)) >> (B + 1);
-        const int li = idx - (c.cb >> (B + 1)) + c.TT - (c.TT >> B);
-        w[e] = c.tw[li];
-        ws[e] = c.tws[li];
-    }
+    for (int u = 0; u < NT; ++u) w[u] = c.ld(base + u);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         if (e & (1 << lb)) continue;
         const int e1 = e | (1 << lb);
+        const ulonglong2 t = w[e >> (lb + 1)];
         if (!INV) {
             u64 X = v[e];
             if (!c.grow) X = X >= q2 ? X - q2 : X;
-            const u64 T = shoup_lazy(v[e1], w[e], ws[e], c.q);
+            const u64 T = shoup_lazy(v[e1], t.x, t.y, c.q);
             v[e] = X + T;
             v[e1] = X - T + q2;
         } else {
@@ -96,13 +101,13 @@ __device__ __forceinline__ void stage(u64 (&v)[8], int tau, const Ctx& c) {
             u64 S = X + Y;
             S = S >= q2 ? S - q2 : S;
             v[e] = S;
-            v[e1] = shoup_lazy(X - Y + q2, w[e], ws[e], c.q);
+            v[e1] = shoup_lazy(X - Y + q2, t.x, t.y, c.q);
         }
     }
 }
 
-template <bool INV, int LO, int BFROM, int BTO, int K>
-__device__ __forceinline__ void stages(u64 (&v)[8], int tau, const Ctx& c) {
+template <bool INV, int LO, int BFROM, int BTO, int K, class C>
+__device__ __forceinline__ void stages(u64 (&v)[8], int tau, const C& c) {
     // forward: bits BTO-1 down to BFROM; inverse: BFROM up to BTO-1
     if constexpr (K < BTO - BFROM) {
         constexpr int B = INV ? BFROM + K : BTO - 1 - K;
@@ -111,8 +116,8 @@ __device__ __forceinline__ void stages(u64 (&v)[8], int tau, const Ctx& c) {
     }
 }
 
-template <int LOG, bool INV, int PH, class Ex>
-__device__ __forceinline__ void phases(u64 (&v)[8], int tau, const Ctx& c, Ex& ex) {
+template <int LOG, bool INV, int PH, class Ex, class C>
+__device__ __forceinline__ void phases(u64 (&v)[8], int tau, const C& c, Ex& ex) {
     constexpr int P = (LOG + 2) / 3;
     if constexpr (PH < P) {
         using I = PhaseInfo<LOG, INV, PH>;
@@ -187,20 +192,15 @@ __global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
     pdl_trigger();
     constexpr int S = 1 << LOG;
     extern __shared__ u64 sm[];
-    u64* sw = sm + S * KTC;      // twiddles [0, S)
-    u64* sws = sw + S;
+    ulonglong2* sw = reinterpret_cast<ulonglong2*>(sm + S * KTC);  // twiddles [0, S)
     const int N = R.N;
     const int C = N >> LOG;
     const int p = blockIdx.y;
     int pi;
     u64* x = poly_at(b, p, N, &pi);
     const u64 q = R.primes[pi].q;
-    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
-    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) {
-        sw[i] = tw[i];
-        sws[i] = tws[i];
-    }
+    const ulonglong2* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) sw[i] = __ldg(tw + i);
     const int col = threadIdx.x & (KTC - 1);
     const int tau = threadIdx.x / KTC;
     const int gcol = blockIdx.x * KTC + col;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, 
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
     __syncthreads();
-    Ctx c{0, S, 0, 0, sw, sws, q, q < (1ull << 57)};
+    Ctx<false> c{0, S, sw, q, q < (1ull << 57)};
     ColEx<KTC> ex{sm, col};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if (INV) {
@@ -298,8 +298,7 @@ __global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, P
     int pi;
     u64* x = poly_at(b, p, N, &pi);
     const u64 q = R.primes[pi].q;
-    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
-    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
+    const ulonglong2* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
     const int rloc = threadIdx.x / TPR;
     const int tau = threadIdx.x % TPR;
     const int rho = blockIdx.x * RPC + rloc;
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, P
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
     const bool grow = q < (1ull << 57);
-    Ctx c{Jbase, N, 0, 0, tw, tws, q, grow};
+    Ctx<true> c{Jbase, N, tw, q, grow};
     RowEx ex{sm + rloc * SP};
     phases<LOG, INV, 0>(v, tau, c, ex);
     if constexpr (std::is_same<E, EpiToMont>::value) {
@@ -362,8 +361,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
     extern __shared__ u64 sm[];
     u64* A = sm;              // 32 rows x 256 (row layout) / 256 rows x 32 columns (column layout)
     u64* Bb = sm + 8192;
-    u64* sw = sm + 16384;     // column-pass twiddles [0, 256)
-    u64* sws = sw + S;
+    ulonglong2* sw = reinterpret_cast<ulonglong2*>(sm + 16384);  // column-pass twiddles [0, 256)
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int N = R.N;
@@ -371,12 +369,8 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
     int pi;
     u64* x = poly_at(b, p, N, &pi);
     const u64 q = R.primes[pi].q;
-    const u64* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
-    const u64* tws = (INV ? R.itws : R.tws) + (size_t)pi * N;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) {
-        sw[i] = tw[i];
-        sws[i] = tws[i];
-    }
+    const ulonglong2* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) sw[i] = __ldg(tw + i);
     const bool grow = q < (1ull << 57);
     // column-pass coordinates: column 32 rank + col, rows phase_x(tauc, e)
     const int col = threadIdx.x & 31, tauc = threadIdx.x >> 5;
@@ -390,7 +384,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tauc, e) * S + gcol];
         __syncthreads();
-        Ctx c{0, S, 0, 0, sw, sws, q, grow};
+        Ctx<false> c{0, S, sw, q, grow};
         ColEx<32> exc{A, col};
         phases<LOG, false, 0>(v, tauc, c, exc);
 #pragma unroll
@@ -403,7 +397,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
         u64* br = Bb + rloc * S;
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = br[phase_x<L0>(taur, e)];
-        Ctx cr{rho * S, N, 0, 0, tw, tws, q, grow};
+        Ctx<true> cr{rho * S, N, tw, q, grow};
         RowEx exr{A + rloc * S};
         phases<LOG, false, 0>(v, taur, cr, exr);
         const u64 one_s = R.primes[pi].one_s;
@@ -420,7 +414,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
         const u64* xr = x + (long long)rho * S;
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(taur, e)];
-        Ctx cr{rho * S, N, 0, 0, tw, tws, q, false};
+        Ctx<true> cr{rho * S, N, tw, q, false};
         RowEx exr{Bb + rloc * S};
         phases<LOG, true, 0>(v, taur, cr, exr);
 #pragma unroll
@@ -432,7 +426,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
         cl.sync();
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = A[phase_x<L0>(tauc, e) * 32 + col];
-        Ctx c{0, S, 0, 0, sw, sws, q, false};
+        Ctx<false> c{0, S, sw, q, false};
         ColEx<32> exc{Bb, col};
         phases<LOG, true, 0>(v, tauc, c, exc);
         const DevPrime P = R.primes[pi];

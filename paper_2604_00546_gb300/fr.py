@@ -31,8 +31,8 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_encrypt_db", "fr_load_db_encrypted", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_fp64_peak", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
-    "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
+    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_fp64_peak", "fr_ntt_time", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
+    "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_cheb_coeffs_lo", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
     "fr_serve_stats", "fr_serve_plan",
 ]
@@ -55,7 +55,7 @@ class Params(C.Structure):
         ("n1", C.c_uint32), ("schedule", C.c_uint32), ("cheb_degree", C.c_uint32), ("threshold", C.c_double),
         ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("db_tier", C.c_uint32), ("level_mode", C.c_uint32), ("sum_radix", C.c_uint32),
-        ("hoist_giants", C.c_uint32),
+        ("hoist_giants", C.c_uint32), ("comparator", C.c_uint32),
     ]
 
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
                                  C.POINTER(C.c_uint64)]),
         "fr_launch_count": (C.c_uint64, [vp]),
         "fr_butterfly_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
+        "fr_ntt_time": (st, [vp, C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "fr_fp64_peak": (st, [C.c_int, C.POINTER(C.c_double)]),
         "fr_use_graphs": (st, [vp, C.c_int]),
         "fr_inject_alloc_failure": (st, [vp, C.c_int64]),
@@ -131,6 +132,7 @@ def load(build_if_missing: bool = True):
         "fr_ctx_info": (st, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                              C.POINTER(C.c_uint64)]),
         "fr_cheb_coeffs": (st, [C.c_uint32, C.c_double, f64p]),
+        "fr_cheb_coeffs_lo": (st, [C.c_uint32, C.c_double, C.c_double, f64p]),
         "fr_work_level": (C.c_uint32, [vp]),
         "fr_free_ct": (None, [vp]),
         "fr_free_cts": (None, [C.POINTER(vp), C.c_size_t]),
@@ -225,14 +227,14 @@ class Context:
 
     def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
                  hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0, db_tier=0, sum_radix=0,
-                 hoist_giants=0):
+                 hoist_giants=0, comparator=0):
         L = load()
         self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
         self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
                              C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode, sum_radix,
-                             int(hoist_giants))
+                             int(hoist_giants), int(comparator))
         h = C.c_void_p()
         self._live = 0          # library objects of this context still alive
         self._closing = False
@@ -376,6 +378,13 @@ class Context:
         _check(_lib.fr_ntt_tuning(self.h, shapes, us))
         return dict(buckets=["<=4", "<=16", "<=64", ">64"], shapes=[int(x) for x in shapes],
                     us=us.reshape(4, 5).round(2).tolist())
+
+    def ntt_time(self, npolys, level=None, reps=5):
+        """(forward us, inverse us) of one batched NTT of npolys limb-polynomials."""
+        f, i = C.c_double(), C.c_double()
+        lvl = self.work_level if level is None else int(level)
+        _check(_lib.fr_ntt_time(self.h, int(npolys), lvl, int(reps), C.byref(f), C.byref(i)))
+        return f.value, i.value
 
     def ntt_set_shapes(self, shapes):
         _check(_lib.fr_ntt_set_shapes(self.h, np.ascontiguousarray(shapes, dtype=np.uint32)))
@@ -567,7 +576,8 @@ def rotation_count(ell, n1, groups, schedule=0):
     return int(load().fr_rotation_count(int(ell), int(n1), int(groups), int(schedule)))
 
 
-def cheb_coeffs(n, tau):
+def cheb_coeffs(n, tau, low=0.0):
+    """Interpolant at the n + 1 Chebyshev nodes of 1 for x >= tau, `low` below (-1: sign)."""
     out = np.empty(n + 1, dtype=np.float64)
-    _check(load().fr_cheb_coeffs(int(n), float(tau), out))
+    _check(load().fr_cheb_coeffs_lo(int(n), float(tau), float(low), out))
     return out

@@ -21,6 +21,9 @@ CONFIGS = {
     # deeper chain than the threshold needs: the match runs at a lower working level
     "deep": dict(log_n=13, q_bits=[60] + [45] * 11, p_bits=[60, 60, 60], dnum=4, scale_bits=45, ell=64, n1=8,
                  cheb_degree=59, threshold=0.5, K=5000, mode=2, seed=7, level_mode=1),
+    # mid-size case deep enough for the hybrid comparator (degree 59 + f_4: 10 levels, working level 12)
+    "mid_hybrid": dict(log_n=13, q_bits=[60] + [45] * 13, p_bits=[60, 60, 60], dnum=4, scale_bits=45, ell=64, n1=8,
+                       cheb_degree=59, threshold=0.5, K=5000, mode=2, seed=8, level_mode=1, duplicates=6),
     # membership at the headline size: N=2^16, Q = 60 + 24 x 50, P = 4 x 60, dnum 6, Delta 2^50,
     # K = 2^15 templates of ell = 512, 32 near-duplicates at cosine 0.8, degree-59 threshold
     "membership": dict(log_n=16, q_bits=[60] + [50] * 24, p_bits=[60] * 4, dnum=6, scale_bits=50, ell=512, n1=32,
@@ -43,8 +46,9 @@ def ctx_params(cfg, level_mode=None):
     return p
 
 
-def work_level(cfg, level_mode=None):
-    """Working level of the match: the top level, or 2 + d2 (capped) in level mode 1."""
+def work_level(cfg, level_mode=None, comparator=0):
+    """Working level of the match: the top level, or 2 + d2 (capped) in level mode 1, with 4
+    levels more for the hybrid comparator (comparator 1)."""
     c = CONFIGS[cfg] if isinstance(cfg, str) else cfg
     lm = c.get("level_mode", 0) if level_mode is None else level_mode
     top = len(c["q_bits"]) - 1
@@ -60,7 +64,7 @@ def work_level(cfg, level_mode=None):
                 b += 1
             if best is None or d1 + b < best[0] or (d1 + b == best[0] and d1 > best[1]):
                 best = (d1 + b, d1, b)
-        d2 = best[2]
+        d2 = best[2] + (4 if comparator == 1 else 0)
     return min(top, 2 + d2)
 
 
