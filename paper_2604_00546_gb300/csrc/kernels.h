@@ -84,7 +84,7 @@ struct PolyBatch {
 
 // NTT batch-size buckets for the tuned tile shapes: <= 4, <= 16, <= 64, larger.
 #define FR_NTT_BUCKETS 4
-#define FR_NTT_SHAPES 5
+#define FR_NTT_SHAPES 6
 __host__ __device__ inline int ntt_bucket(int npolys) {
     return npolys <= 4 ? 0 : npolys <= 16 ? 1 : npolys <= 64 ? 2 : 3;
 }

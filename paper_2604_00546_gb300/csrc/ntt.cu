@@ -187,7 +187,7 @@ struct RowEx {
 
 // column pass: one CTA = KTC columns x S rows; thread (tau, col) with col = threadIdx % KTC
 template <int LOG, bool INV, int KTC>
-__global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(RingDev R, PolyBatch b) {
+__global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(const __grid_constant__ RingDev R, const __grid_constant__ PolyBatch b) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
@@ -285,7 +285,8 @@ struct EpiRescale {
 
 // row pass: one CTA = RPC rows of S contiguous elements (RT threads), S/8 threads per row
 template <int LOG, int LOGR, bool INV, class E, int RT>
-__global__ void __launch_bounds__(RT, RT == 128 ? 10 : 5) k_ntt_row(RingDev R, PolyBatch b, E epi) {
+__global__ void __launch_bounds__(RT, RT == 128 ? 9 : 4) k_ntt_row(const __grid_constant__ RingDev R, const __grid_constant__ PolyBatch b,
+                                                                   const __grid_constant__ E epi) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = 1 << LOG;
@@ -353,7 +354,8 @@ constexpr size_t kClusterSmem = (size_t)(2 * 8192 + 2 * 256) * sizeof(u64);
 
 template <bool INV, class E>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
-    k_ntt_cluster(RingDev R, PolyBatch b, E epi) {
+    k_ntt_cluster(const __grid_constant__ RingDev R, const __grid_constant__ PolyBatch b,
+                  const __grid_constant__ E epi) {
     pdl_wait();
     pdl_trigger();
     namespace cg = cooperative_groups;
@@ -436,6 +438,205 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Radix-16 passes for N = 2^16 (tile shape 5): every thread keeps 16 residues and runs 4
+// stages per shared-memory exchange, so each 256-point pass is two 4-stage phases with one
+// exchange (radix 8: three phases, two exchanges) and a stage on register bit lb loads
+// 8 >> lb twiddles for its 8 butterflies. Forward phases take register bits 4..7 then 0..3,
+// inverse ones 0..3 then 4..7. Residues whose 16 elements are contiguous in memory move as
+// 16-byte vectors.
+// ---------------------------------------------------------------------------
+template <int LO>
+__device__ __forceinline__ int px16(int tau, int e) {
+    return ((tau >> LO) << (LO + 4)) | (e << LO) | (tau & ((1 << LO) - 1));
+}
+
+template <bool INV, int LO, int B, class C>
+__device__ __forceinline__ void stage16(u64 (&v)[16], int tau, const C& c) {
+    constexpr int lb = B - LO;
+    constexpr int NT = 8 >> lb;
+    const u64 q2 = 2 * c.q;
+    const int base = (c.M + c.Jbase + ((tau >> LO) << (LO + 4))) >> (B + 1);
+    ulonglong2 w[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) w[u] = c.ld(base + u);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        if (e & (1 << lb)) continue;
+        const int e1 = e | (1 << lb);
+        const ulonglong2 t = w[e >> (lb + 1)];
+        if (!INV) {
+            u64 X = v[e];
+            if (!c.grow) X = X >= q2 ? X - q2 : X;
+            const u64 T = shoup_lazy(v[e1], t.x, t.y, c.q);
+            v[e] = X + T;
+            v[e1] = X - T + q2;
+        } else {
+            const u64 X = v[e], Y = v[e1];
+            u64 S = X + Y;
+            S = S >= q2 ? S - q2 : S;
+            v[e] = S;
+            v[e1] = shoup_lazy(X - Y + q2, t.x, t.y, c.q);
+        }
+    }
+}
+
+// the four stages of a phase whose register bits start at LO: forward bits LO+3 .. LO,
+// inverse LO .. LO+3
+template <bool INV, int LO, class C>
+__device__ __forceinline__ void phase16(u64 (&v)[16], int tau, const C& c) {
+    if constexpr (!INV) {
+        stage16<false, LO, LO + 3>(v, tau, c);
+        stage16<false, LO, LO + 2>(v, tau, c);
+        stage16<false, LO, LO + 1>(v, tau, c);
+        stage16<false, LO, LO>(v, tau, c);
+    } else {
+        stage16<true, LO, LO>(v, tau, c);
+        stage16<true, LO, LO + 1>(v, tau, c);
+        stage16<true, LO, LO + 2>(v, tau, c);
+        stage16<true, LO, LO + 3>(v, tau, c);
+    }
+}
+
+// Shared-memory word of element x of a 256-point row: x ^ ((x >> 4) & 15). A half-warp (one
+// row's 16 threads) then touches 16 distinct 8-byte bank pairs both when it stores elements
+// e << 4 | tau and when it loads tau << 4 | e (and the reverse).
+__device__ __forceinline__ int sw16(int x) { return x ^ ((x >> 4) & 15); }
+
+// column pass: one CTA = 8 columns x 256 rows, thread (tau, col) = (threadIdx / 8, threadIdx % 8)
+template <bool INV>
+__global__ void __launch_bounds__(128, 4) k_ntt_col16(const __grid_constant__ RingDev R,
+                                                      const __grid_constant__ PolyBatch b) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int S = 256, KTC = 8;
+    extern __shared__ u64 sm[];                                    // [S][KTC] rows swizzled
+    ulonglong2* sw = reinterpret_cast<ulonglong2*>(sm + S * KTC);  // twiddles [0, S)
+    const int N = R.N;
+    const int C = N >> 8;
+    const int p = blockIdx.y;
+    int pi;
+    u64* x = poly_at(b, p, N, &pi);
+    const u64 q = R.primes[pi].q;
+    const ulonglong2* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) sw[i] = __ldg(tw + i);
+    const int col = threadIdx.x & (KTC - 1);
+    const int tau = threadIdx.x / KTC;
+    const int gcol = blockIdx.x * KTC + col;
+    constexpr int L0 = INV ? 0 : 4, L1 = INV ? 4 : 0;
+    u64 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = x[(long long)px16<L0>(tau, e) * C + gcol];
+    __syncthreads();
+    Ctx<false> c{0, S, sw, q, q < (1ull << 57)};
+    phase16<INV, L0>(v, tau, c);
+    // rows x and x + 16 of one load phase fall in different bank halves: row' = x ^ bit 4 of x
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int r = px16<L0>(tau, e);
+        sm[(r ^ ((r >> 4) & 1)) * KTC + col] = v[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int r = px16<L1>(tau, e);
+        v[e] = sm[(r ^ ((r >> 4) & 1)) * KTC + col];
+    }
+    phase16<INV, L1>(v, tau, c);
+    if (INV) {
+        const DevPrime P = R.primes[pi];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            x[(long long)px16<L1>(tau, e) * C + gcol] = mul_shoup(v[e], P.ninv, P.ninv_s, q);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) x[(long long)px16<L1>(tau, e) * C + gcol] = v[e];
+    }
+}
+
+// row pass: one CTA = 8 rows of 256 contiguous elements, 16 threads per row
+template <bool INV, class E>
+__global__ void __launch_bounds__(128, 4) k_ntt_row16(const __grid_constant__ RingDev R,
+                                                      const __grid_constant__ PolyBatch b,
+                                                      const __grid_constant__ E epi) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int S = 256, TPR = 16, RPC = 8;
+    extern __shared__ u64 sm[];  // [RPC][S] swizzled
+    const int N = R.N;
+    const int p = blockIdx.y;
+    int pi;
+    u64* x = poly_at(b, p, N, &pi);
+    const u64 q = R.primes[pi].q;
+    const ulonglong2* tw = (INV ? R.itw : R.tw) + (size_t)pi * N;
+    const int rloc = threadIdx.x / TPR;
+    const int tau = threadIdx.x % TPR;
+    const int rho = blockIdx.x * RPC + rloc;
+    const int Jbase = rho * S;
+    u64* xr = x + Jbase;
+    constexpr int L0 = INV ? 0 : 4, L1 = INV ? 4 : 0;
+    u64 v[16];
+    if constexpr (L0 == 0) {
+        // the thread's 16 elements are contiguous: eight 16-byte loads
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(xr + tau * 16);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const ulonglong2 t = src[h];
+            v[2 * h] = t.x;
+            v[2 * h + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = xr[px16<L0>(tau, e)];
+    }
+    const bool grow = q < (1ull << 57);
+    Ctx<true> c{Jbase, N, tw, q, INV ? false : grow};
+    phase16<INV, L0>(v, tau, c);
+    u64* s = sm + rloc * S;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) s[sw16(px16<L0>(tau, e))] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = s[sw16(px16<L1>(tau, e))];
+    phase16<INV, L1>(v, tau, c);
+    if constexpr (INV) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) xr[px16<L1>(tau, e)] = v[e];
+    } else {
+        const u64 one_s = R.primes[pi].one_s;
+        u64 o[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) o[e] = grow ? mul_shoup(v[e], 1, one_s, q) : reduce4(v[e], q);
+        if constexpr (std::is_same<E, EpiStore>::value) {
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(xr + tau * 16);
+#pragma unroll
+            for (int h = 0; h < 8; ++h) dst[h] = make_ulonglong2(o[2 * h], o[2 * h + 1]);
+        } else if constexpr (std::is_same<E, EpiToMont>::value) {
+            const DevPrime P = R.primes[pi];
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(xr + tau * 16);
+#pragma unroll
+            for (int h = 0; h < 8; ++h) dst[h] = make_ulonglong2(to_mont(o[2 * h], P), to_mont(o[2 * h + 1], P));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) epi.put(p, Jbase + tau * 16 + e, o[e], q);
+        }
+    }
+}
+
+template <class E>
+void launch_ntt_r16(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
+    const int N = R.N;
+    const dim3 gc((N >> 8) / 8, b.npolys), gr(256 / 8, b.npolys);
+    const size_t smc = (size_t)(256 * 8 + 2 * 256) * sizeof(u64), smr = (size_t)8 * 256 * sizeof(u64);
+    if (!inverse) {
+        launch_k(k_ntt_col16<false>, gc, dim3(128), smc, st, R, b);
+        launch_k(k_ntt_row16<false, E>, gr, dim3(128), smr, st, R, b, epi);
+    } else {
+        launch_k(k_ntt_row16<true, EpiStore>, gr, dim3(128), smr, st, R, b, EpiStore{});
+        launch_k(k_ntt_col16<true>, gc, dim3(128), smc, st, R, b);
+    }
+}
+
 template <int LOGR, int LOGC, class E, int KTC, int RT>
 void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
     constexpr int SR = 1 << LOGR, SC = 1 << LOGC;
@@ -455,10 +656,11 @@ void launch_ntt_t(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     }
 }
 
-// Tile shape of a launch: 0..3 are the two-pass kernels, bit 0 set = 8 columns per
+// Tile shape of a launch: 0..3 are the radix-8 two-pass kernels, bit 0 set = 8 columns per
 // column-pass CTA (else 4), bit 1 set = 256-thread row-pass CTAs (else 128); 4 is the
-// single-launch cluster kernel (N = 2^16). Chosen per batch-size bucket by the tuner (RingDev
-// holds the table); sizes other than N = 2^15, 2^16 use shape 0.
+// single-launch cluster kernel and 5 the radix-16 two-pass kernels (both N = 2^16). Chosen per
+// batch-size bucket by the tuner (RingDev holds the table); sizes other than N = 2^15, 2^16
+// use shape 0.
 template <class E>
 void launch_ntt_cluster(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t st, const E& epi) {
     static std::atomic<unsigned long long> fwd{0}, inv{0};
@@ -475,6 +677,10 @@ void launch_ntt_s(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream
     if constexpr (LOGR == 8 && LOGC == 8) {
         if (shape == 4) {
             launch_ntt_cluster(R, b, inverse, st, epi);
+            return;
+        }
+        if (shape == 5) {
+            launch_ntt_r16(R, b, inverse, st, epi);
             return;
         }
     }
@@ -575,7 +781,7 @@ void tune_ntt(RingDev& R, cudaStream_t s, double* us, int reps) {
     if (us)
         for (int i = 0; i < FR_NTT_BUCKETS * FR_NTT_SHAPES; ++i) us[i] = 0;
     if (R.logN < 15) return;
-    const int nshapes = R.logN == 16 ? FR_NTT_SHAPES : FR_NTT_SHAPES - 1;  // the cluster kernel is N = 2^16 only
+    const int nshapes = R.logN == 16 ? FR_NTT_SHAPES : FR_NTT_SHAPES - 2;  // shapes 4 and 5 are N = 2^16 only
     const int sizes[FR_NTT_BUCKETS] = {4, 16, 64, 256};
     const int maxp = sizes[FR_NTT_BUCKETS - 1];
     u64* buf = nullptr;

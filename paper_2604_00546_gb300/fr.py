@@ -374,10 +374,10 @@ class Context:
     def ntt_tuning(self):
         """Tile shape chosen per NTT batch bucket and the tuner's times (us, bucket x shape)."""
         shapes = np.zeros(4, dtype=np.uint32)
-        us = np.zeros(20, dtype=np.float64)
+        us = np.zeros(24, dtype=np.float64)
         _check(_lib.fr_ntt_tuning(self.h, shapes, us))
         return dict(buckets=["<=4", "<=16", "<=64", ">64"], shapes=[int(x) for x in shapes],
-                    us=us.reshape(4, 5).round(2).tolist())
+                    us=us.reshape(4, 6).round(2).tolist())
 
     def ntt_time(self, npolys, level=None, reps=5):
         """(forward us, inverse us) of one batched NTT of npolys limb-polynomials."""

@@ -16,8 +16,10 @@ query against them.
   terms.
 
 Ciphertexts cross processes in the library's export format: coefficient form,
-[2][level+1][N] uint64. Collectives are torch.distributed object collectives, so the same code
-runs over gloo (CPU) and NCCL.
+[2][level+1][N] uint64, packed into one int64 tensor per rank and moved with tensor
+collectives (broadcast of the query, point-to-point send/recv of the per-group outputs to the
+destination rank). Over NCCL the tensors live on the rank's GPU (the current CUDA device); over
+gloo on the host. No kernel of the library ever reads another rank's memory.
 
 The engine is any object with the `fr.Context` methods used here: match, import_ct and
 membership_reduce. Outputs expose `export()`.
@@ -48,18 +50,41 @@ def template_shard(T: np.ndarray, slots: int, world: int, rank: int):
     return T[g0 * slots:min(g1 * slots, K)], (g0, g1)
 
 
+def _coll_device(dist):
+    """Where collective tensors live: the current CUDA device for NCCL, the host otherwise."""
+    import torch
+    if dist.get_backend() == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
+def _to_tensor(words, device):
+    import torch
+    flat = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1).view(np.int64)
+    return torch.from_numpy(flat).to(device)
+
+
+def _to_words(t, shape):
+    return t.cpu().numpy().view(np.uint64).reshape(shape)
+
+
 def share_query(engine, query, dist=None, src: int = 0):
     """The query ciphertext on every rank. `src` passes its handle and exports it; the other
-    ranks pass None and import what src broadcasts."""
+    ranks pass None and import what src broadcasts (a shape header, then the words)."""
     if dist is None or dist.get_world_size() == 1:
         return query
+    import torch
+    dev = _coll_device(dist)
     rank = dist.get_rank()
-    box = [query.export() if rank == src else None]
-    dist.broadcast_object_list(box, src=src)
+    w = query.export() if rank == src else None
+    hdr = torch.tensor(list(w.shape) if w is not None else [0, 0, 0], dtype=torch.int64, device=dev)
+    dist.broadcast(hdr, src=src)
+    shape = tuple(int(x) for x in hdr.tolist())
+    buf = _to_tensor(w, dev) if w is not None else torch.empty(int(np.prod(shape)), dtype=torch.int64, device=dev)
+    dist.broadcast(buf, src=src)
     if rank == src:
         return query
-    w = box[0]
-    return engine.import_ct(w, w.shape[1] - 1)
+    return engine.import_ct(_to_words(buf, shape), shape[1] - 1)
 
 
 def sharded_match(engine, db, query, mode: int, dist=None, dst: int = 0):
@@ -80,17 +105,31 @@ def sharded_match(engine, db, query, mode: int, dist=None, dst: int = 0):
     if world == 1:
         parts = outs
     else:
-        payload = None if rank == dst else [o.export() for o in outs]
-        gathered = [None] * world if rank == dst else None
-        dist.gather_object(payload, gathered, dst=dst)
+        import torch
+        dev = _coll_device(dist)
         if rank != dst:
+            # header (count, limbs, N), then every output's words in group order
+            words = [o.export() for o in outs]
+            shape = words[0].shape if words else (2, 0, 0)
+            hdr = torch.tensor([len(words), shape[1], shape[2]], dtype=torch.int64, device=dev)
+            dist.send(hdr, dst=dst)
+            if words:
+                dist.send(_to_tensor(np.stack(words), dev), dst=dst)
             return None
         parts = []
         for r in range(world):
             if r == dst:
                 parts.extend(outs)
-            else:
-                parts.extend(engine.import_ct(w, w.shape[1] - 1) for w in gathered[r])
+                continue
+            hdr = torch.empty(3, dtype=torch.int64, device=dev)
+            dist.recv(hdr, src=r)
+            n, limbs, N = (int(x) for x in hdr.tolist())
+            if n == 0:
+                continue
+            buf = torch.empty(n * 2 * limbs * N, dtype=torch.int64, device=dev)
+            dist.recv(buf, src=r)
+            words = _to_words(buf, (n, 2, limbs, N))
+            parts.extend(engine.import_ct(words[i], limbs - 1) for i in range(n))
     if mode != fr.FR_MODE_MEMBERSHIP:
         return parts
     if not parts:

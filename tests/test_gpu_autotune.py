@@ -1,6 +1,6 @@
-"""GPU tests of the NTT tile-shape autotuner: fr_setup times every shape (four two-pass tile
-shapes and the single-launch cluster kernel) per batch bucket at N=2^16 and keeps the
-fastest; every shape gives the same transforms, so a rotation at
+"""GPU tests of the NTT tile-shape autotuner: fr_setup times every shape (four radix-8
+two-pass tile shapes, the single-launch cluster kernel and the radix-16 two-pass kernels) per
+batch bucket at N=2^16 and keeps the fastest; every shape gives the same transforms, so a rotation at
 N=2^16 (which runs inverse and forward NTTs of several batch sizes) is bit-identical to the
 oracle under each forced shape."""
 import numpy as np
@@ -35,7 +35,7 @@ def big():
 def test_tuner_picks_the_fastest_measured_shape(big):
     t = big["ctx"].ntt_tuning()
     us = np.array(t["us"])
-    assert us.shape == (4, 5) and (us[:, :4] > 0).all()
+    assert us.shape == (4, 6) and (us[:, :4] > 0).all()
     for b in range(4):
         avail = np.where(us[b] > 0, us[b], np.inf)
         sh = t["shapes"][b]
@@ -46,7 +46,7 @@ def test_tuner_picks_the_fastest_measured_shape(big):
             assert avail[sh] == avail.min() and avail[sh] < 0.97 * avail[0]
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
 def test_every_shape_is_bit_exact(big, shape):
     ctx = big["ctx"]
     saved = ctx.ntt_tuning()["shapes"]

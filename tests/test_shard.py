@@ -1,9 +1,11 @@
 """Block-sharded matching (the multi-process form of Algorithms 5 and 6) on the CPU.
 
 Template groups are split across gloo ranks. Each rank's per-group outputs come from the oracle,
-standing in for one GPU's library calls. The exchange and reduction logic of shard.py must then
-reproduce the single-process oracle result bit for bit, for identification (groups gathered in
-order) and membership (mod-q sum, then RotateAndSum). A rank that holds no group is covered too.
+standing in for one GPU's library calls. The exchange and reduction logic of shard.py (the path
+`bench.py --shard` runs: query broadcast as a tensor, per-group ciphertexts sent to rank 0 with
+point-to-point tensor transfers, mod-q sum and RotateAndSum there) must then reproduce the
+single-process oracle result bit for bit, for identification (groups gathered in order) and
+membership, at world sizes 2 and 4. A rank that holds no group is covered too.
 """
 import os
 import socket
@@ -35,6 +37,16 @@ def test_group_range_covers_groups_once():
             assert max(sizes) - min(sizes) <= 1 and sizes == sorted(sizes, reverse=True)
     with pytest.raises(ValueError):
         shard.group_range(3, 2, 2)
+
+
+def test_identification_database_splits_evenly():
+    """The 32 groups of the K = 2^20 database over 1..8 ranks: every group once, sizes within one."""
+    T = np.zeros((1 << 20, 1), dtype=np.float32)
+    for world in range(1, 9):
+        parts = [shard.template_shard(T, 1 << 15, world, r) for r in range(world)]
+        assert sum(p.shape[0] for p, _ in parts) == 1 << 20
+        sizes = [g1 - g0 for _, (g0, g1) in parts]
+        assert sum(sizes) == 32 and max(sizes) - min(sizes) <= 1
 
 
 def test_template_shards_rejoin():
