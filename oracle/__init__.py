@@ -126,7 +126,9 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           C.c_int, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+                           C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+    L.or_bsgs_scores_pq.restype = C.c_int
+    L.or_bsgs_scores_pq.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, u64p]
     L.or_bsgs_scores_hoisted.restype = C.c_int
     L.or_bsgs_scores_hoisted.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, u64p]
     L.or_table_scores.restype = C.c_int
@@ -364,6 +366,21 @@ class Keys:
             raise ValueError("radix must be a power of two")
         return x
 
+    def bsgs_scores_pq(self, qct, T, ell, n1, level=None, hoist=False, pq=True):
+        """Scores at level-1 with the baby steps kept in Q_l u P (pq) or not; hoist: giant steps
+        sharing one ModDown per group."""
+        c = self.ctx
+        L = c.top if level is None else int(level)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        K = T.shape[0]
+        G = (K + c.n - 1) // c.n
+        out = np.empty((G, 2, L, c.N), dtype=np.uint64)
+        r = self.L.or_bsgs_scores_pq(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), L, T, K, ell, n1,
+                                     1 if pq else 0, 1 if hoist else 0, out)
+        if r < 0:
+            raise ValueError("bad parameters")
+        return out
+
     def bsgs_scores(self, qct, T, ell, n1, level=None, hoist=False):
         """Scores at level-1 of a query ct at `level` (default: the top level); hoist: the giant
         steps of a group share one ModDown."""
@@ -431,10 +448,11 @@ class Keys:
         return out
 
     def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2, hoist=False,
-              comparator=0):
+              comparator=0, babies_pq=False):
         """Full match of a top-level query ct, computed at working level `level` (default: top);
         schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table;
-        comparator 0: the step interpolant (the paper's GPU path), 1: the hybrid comparator."""
+        comparator 0: the step interpolant (the paper's GPU path), 1: the hybrid comparator;
+        babies_pq: the baby steps stay in Q_l u P (one ModDown per giant step)."""
         c = self.ctx
         lq = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
@@ -445,7 +463,7 @@ class Keys:
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
                             int(cheb_n), float(tau), int(comparator), int(schedule), int(sum_radix),
-                            1 if hoist else 0, out, C.byref(lvl))
+                            1 if hoist else 0, 1 if babies_pq else 0, out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

@@ -1419,22 +1419,143 @@ int or_giant_step(const or_ctx* c, const u64* babies, int L, int n1, const float
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Baby steps kept in Q_l u P (double hoisting of the baby steps, after       */
+/* Bossuat et al.; Section "Hoisting and double hoisting"): the rotations    */
+/* B_i = Rot_i(q) are left before their ModDown, in the extended basis,      */
+/*   B_i = (P sigma_i(q.b) + IP0_i, IP1_i),  B_0 = (P q.b, P q.a)             */
+/* (evaluation form over every limb of Q_l u P; P q is zero on the P limbs), */
+/* the plaintext diagonals are encoded over every limb of Q_l u P, and each  */
+/* giant step takes one ModDown of its sum, then the rescale:                */
+/*   P_j = Rescale(ModDown(sum_i B_i (.) D'_{j n1 + i})).                     */
+/* ModDown(P x) = x exactly, so with n1 = 1 this is the plain schedule.       */
+/* ------------------------------------------------------------------------ */
+/* babies [n1][2][npos][N] of the query qct (coefficient form, level L) */
+static void babies_pq(const or_ctx* c, const or_keys* k, const u64* qct, int L, int n1, u64* babies) {
+    int N = c->n, npos = L + 1 + c->np, beta = beta_at(c, L);
+    size_t bw = (size_t)2 * npos * N;
+    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * npos * N);
+    modup(c, qct + (size_t)(L + 1) * N, L, ext);
+    u64* qe = (u64*)malloc(sizeof(u64) * ct_words(c, L));   /* q in evaluation form */
+    memcpy(qe, qct, sizeof(u64) * ct_words(c, L));
+    for (int t = 0; t < 2; t++)
+        for (int i = 0; i <= L; i++) ntt_fwd(c, i, qe + ((size_t)t * (L + 1) + i) * N);
+    u64* evk = (u64*)malloc(sizeof(u64) * evk_words(c));
+    u64* tmp = (u64*)malloc(sizeof(u64) * N);
+    for (int r = 0; r < n1; r++) {
+        u64* B = babies + (size_t)r * bw;
+        u64 g = or_galois(c, r);
+        if (r == 0 || g == 1) {
+            memset(B, 0, sizeof(u64) * bw);
+        } else {
+            or_make_evk(c, k, 0, g, evk);
+            keyswitch_ip(c, ext, L, evk, g, B, B + (size_t)npos * N);
+        }
+        for (int i = 0; i <= L; i++) {   /* + P sigma_r(q.b) (r = 0: P q.b and P q.a) */
+            u64 q = c->p[i], Pm = 1 % q;
+            for (int j = 0; j < c->np; j++) Pm = mmul(Pm, c->p[c->nq + j] % q, q);
+            const u64* b = qe + (size_t)i * N;
+            if (r == 0 || g == 1) {
+                const u64* a = qe + (size_t)(L + 1 + i) * N;
+                for (int x = 0; x < N; x++) {
+                    B[(size_t)i * N + x] = mmul(b[x], Pm, q);
+                    B[(size_t)(npos + i) * N + x] = mmul(a[x], Pm, q);
+                }
+            } else {
+                automorph_eval(c, g, b, tmp);
+                for (int x = 0; x < N; x++) B[(size_t)i * N + x] = madd(B[(size_t)i * N + x], mmul(tmp[x], Pm, q), q);
+            }
+        }
+    }
+    free(ext); free(qe); free(evk); free(tmp);
+}
+
+/* plaintext diagonal in evaluation form over every limb of Q_l u P: [npos][N] */
+static void diag_pt_eval_pq(const or_ctx* c, const float* T, long K, int ell, long k, int d, long shift, int l,
+                            u64* out) {
+    int N = c->n, n = N / 2, npos = l + 1 + c->np;
+    double* z = (double*)malloc(sizeof(double) * n);
+    int64_t* m = (int64_t*)malloc(sizeof(int64_t) * N);
+    or_diag_slots(T, K, ell, n, k, d, shift, z);
+    or_encode_coeffs(c, z, c->scale_bits, m);
+    for (int pos = 0; pos < npos; pos++) {
+        int li = ext_limb(c, l, pos);
+        u64 q = c->p[li];
+        for (int x = 0; x < N; x++) out[(size_t)pos * N + x] = mred_s(m[x], q);
+        ntt_fwd(c, li, out + (size_t)pos * N);
+    }
+    free(z); free(m);
+}
+
+/* giant step j of group g from babies in Q_L u P: P = Rescale(ModDown(sum_i B_i (.) D'_{g, j n1 + i})),
+ * [2][L][N] coefficient form at level L-1 */
+static int giant_step_pq(const or_ctx* c, const u64* babies, int L, int n1, const float* T, long K, int ell, long g,
+                         int j, u64* P) {
+    int N = c->n, npos = L + 1 + c->np;
+    size_t bw = (size_t)2 * npos * N;
+    int cnt = (j * n1 + n1 <= ell) ? n1 : ell - j * n1;
+    if (cnt <= 0) return -1;
+    u64* pts = (u64*)malloc(sizeof(u64) * (size_t)cnt * npos * N);
+    u64* acc = (u64*)malloc(sizeof(u64) * bw);
+    u64* md = (u64*)malloc(sizeof(u64) * ct_words(c, L));
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < cnt; i++)
+        diag_pt_eval_pq(c, T, K, ell, g, j * n1 + i, (long)j * n1, L, pts + (size_t)i * npos * N);
+#pragma omp parallel for schedule(dynamic)
+    for (int pos = 0; pos < npos; pos++) {
+        u64 q = c->p[ext_limb(c, L, pos)];
+        for (int t = 0; t < 2; t++) {
+            u64* a = acc + ((size_t)t * npos + pos) * N;
+            memset(a, 0, sizeof(u64) * N);
+            for (int i = 0; i < cnt; i++) {
+                const u64* b = babies + (size_t)i * bw + ((size_t)t * npos + pos) * N;
+                const u64* d = pts + ((size_t)i * npos + pos) * N;
+                for (int x = 0; x < N; x++) a[x] = madd(a[x], mmul(b[x], d[x], q), q);
+            }
+        }
+    }
+    moddown(c, acc, L, md);
+    moddown(c, acc + (size_t)npos * N, L, md + (size_t)(L + 1) * N);
+    or_rescale(c, md, L, P);
+    free(pts); free(acc); free(md);
+    return 0;
+}
+
 /* On-demand BSGS over giant steps j_begin <= j < j_end (all steps: 0..n2); the
  * query ct is at level L (the working level), scores come out at level L-1. */
-int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
-                         int n1, int j_begin, int j_end, u64* out) {
+/* the query's babies: Rot_i(q) in evaluation form [n1][2][L+1][N] (pq = 0), or kept in Q_L u P
+ * before their ModDown [n1][2][npos][N] (pq = 1) */
+static u64* make_babies(const or_ctx* c, const or_keys* k, const u64* qct, int L, int n1, int pq) {
+    size_t cw = ct_words(c, L);
+    if (pq) {
+        u64* b = (u64*)malloc(sizeof(u64) * (size_t)n1 * 2 * (L + 1 + c->np) * c->n);
+        babies_pq(c, k, qct, L, n1, b);
+        return b;
+    }
+    long* rots = (long*)malloc(sizeof(long) * n1);
+    for (int i = 0; i < n1; i++) rots[i] = i;
+    u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
+    or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
+    for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
+    free(rots);
+    return babies;
+}
+
+static int giant_step_any(const or_ctx* c, const u64* babies, int pq, int L, int n1, const float* T, long K, int ell,
+                          long g, int j, u64* P) {
+    return pq ? giant_step_pq(c, babies, L, n1, T, K, ell, g, j, P) : or_giant_step(c, babies, L, n1, T, K, ell, g, j, P);
+}
+
+static int bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                             int n1, int j_begin, int j_end, int pq, u64* out) {
     int N = c->n, n = N / 2;
     if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
     int n2 = (ell + n1 - 1) / n1;
     if (j_begin < 0) j_begin = 0;
     if (j_end > n2) j_end = n2;
     long G = (K + n - 1) / n;
-    size_t cw = ct_words(c, L), cw1 = ct_words(c, L - 1);
-    long* rots = (long*)malloc(sizeof(long) * n1);
-    for (int i = 0; i < n1; i++) rots[i] = i;
-    u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
-    or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
-    for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
+    size_t cw1 = ct_words(c, L - 1);
+    u64* babies = make_babies(c, k, qct, L, n1, pq);
     u64* P = (u64*)malloc(sizeof(u64) * cw1);
     u64* R = (u64*)malloc(sizeof(u64) * cw1);
     (void)N;
@@ -1442,7 +1563,7 @@ int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int 
         u64* S = out + (size_t)g * cw1;
         memset(S, 0, sizeof(u64) * cw1);
         for (int j = j_begin; j < j_end; j++) {
-            or_giant_step(c, babies, L, n1, T, K, ell, g, j, P);
+            giant_step_any(c, babies, pq, L, n1, T, K, ell, g, j, P);
             if (j > 0) {
                 or_rotate(c, k, P, L - 1, (long)j * n1, R);
                 or_add(c, S, R, L - 1, S);
@@ -1451,14 +1572,24 @@ int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int 
             }
         }
     }
-    free(rots); free(babies); free(P); free(R);
+    free(babies); free(P); free(R);
     return (int)G;
+}
+
+int or_bsgs_scores_range(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                         int n1, int j_begin, int j_end, u64* out) {
+    return bsgs_scores_range(c, k, qct, L, T, K, ell, n1, j_begin, j_end, 0, out);
 }
 
 int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
                    int n1, u64* out) {
-    return or_bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, out);
+    return bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, 0, out);
 }
+
+/* the same with the baby steps kept in Q_L u P (pq = 1) or not (0); hoist: giant steps sharing
+ * one ModDown per group */
+int or_bsgs_scores_pq(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                      int n1, int pq, int hoist, u64* out);
 
 /* On-demand BSGS whose giant-step key switches of one group share a single ModDown (double
  * hoisting after Bossuat et al., Section "Hoisting and double hoisting"): with P_j the
@@ -1466,19 +1597,15 @@ int or_bsgs_scores(const or_ctx* c, const or_keys* k, const u64* qct, int L, con
  * ModUp(P_j.a) under the automorphism of Rot_{j n1} with its key (in Q_l u P, evaluation form),
  *   S_k = P_0 + (sum_{j>=1} sigma_j(P_j.b) + ModDown(sum_{j>=1} IP0_j), ModDown(sum_{j>=1} IP1_j)).
  * With one giant rotation (n2 = 2) this is P_0 + Rot_{n1}(P_1) itself. */
-int or_bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
-                           int n1, u64* out) {
+static int bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K,
+                               int ell, int n1, int pq, u64* out) {
     int N = c->n, n = N / 2;
     if (ell <= 0 || n % ell != 0 || n1 < 1 || n1 > ell || L < 1) return -1;
     int n2 = (ell + n1 - 1) / n1;
     long G = (K + n - 1) / n;
     int l = L - 1, npos = l + 1 + c->np, beta = beta_at(c, l);
-    size_t cw = ct_words(c, L), cw1 = ct_words(c, l), ew = (size_t)npos * N;
-    long* rots = (long*)malloc(sizeof(long) * n1);
-    for (int i = 0; i < n1; i++) rots[i] = i;
-    u64* babies = (u64*)malloc(sizeof(u64) * cw * n1);
-    or_hoisted_rotate(c, k, qct, L, rots, n1, babies);
-    for (int i = 0; i < n1; i++) ct_to_eval(c, babies + (size_t)i * cw, L, babies + (size_t)i * cw);
+    size_t cw1 = ct_words(c, l), ew = (size_t)npos * N;
+    u64* babies = make_babies(c, k, qct, L, n1, pq);
     u64* P = (u64*)malloc(sizeof(u64) * cw1);
     u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * ew);
     u64* evk = (u64*)malloc(sizeof(u64) * evk_words(c));
@@ -1490,11 +1617,11 @@ int or_bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, in
     u64* md = (u64*)malloc(sizeof(u64) * cw1);
     for (long g = 0; g < G; g++) {
         u64* S = out + (size_t)g * cw1;
-        or_giant_step(c, babies, L, n1, T, K, ell, g, 0, S);
+        giant_step_any(c, babies, pq, L, n1, T, K, ell, g, 0, S);
         memset(s0, 0, sizeof(u64) * ew);
         memset(s1, 0, sizeof(u64) * ew);
         for (int j = 1; j < n2; j++) {
-            or_giant_step(c, babies, L, n1, T, K, ell, g, j, P);
+            giant_step_any(c, babies, pq, L, n1, T, K, ell, g, j, P);
             u64 gk = or_galois(c, (long)j * n1);
             modup(c, P + (size_t)(l + 1) * N, l, ext);
             or_make_evk(c, k, 0, gk, evk);
@@ -1518,8 +1645,19 @@ int or_bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, in
             or_add(c, S, md, l, S);
         }
     }
-    free(rots); free(babies); free(P); free(ext); free(evk); free(a0); free(a1); free(s0); free(s1); free(t); free(md);
+    free(babies); free(P); free(ext); free(evk); free(a0); free(a1); free(s0); free(s1); free(t); free(md);
     return (int)G;
+}
+
+int or_bsgs_scores_hoisted(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                           int n1, u64* out) {
+    return bsgs_scores_hoisted(c, k, qct, L, T, K, ell, n1, 0, out);
+}
+
+int or_bsgs_scores_pq(const or_ctx* c, const or_keys* k, const u64* qct, int L, const float* T, long K, int ell,
+                      int n1, int pq, int hoist, u64* out) {
+    return hoist ? bsgs_scores_hoisted(c, k, qct, L, T, K, ell, n1, pq, out)
+                 : bsgs_scores_range(c, k, qct, L, T, K, ell, n1, 0, ell, pq, out);
 }
 
 /* Sum over the ell diagonals of a table of rotated queries (Eq. equ:diagbsgsgroupsprecomp):
@@ -1647,13 +1785,14 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
 
 /* Full match (Algorithms 5 and 6). The top-level query is first dropped to the
  * working level lq (lq = top: the whole chain). schedule 0: on-demand BSGS with
- * pre-rotated diagonals (hoist: the giant steps of a group share one ModDown); schedule 1: the
+ * pre-rotated diagonals (hoist: the giant steps of a group share one ModDown; babies_pq: the
+ * baby steps stay in Q_l u P, one ModDown per giant step); schedule 1: the
  * rotated-query table of Algorithm 1. mode 0: scores (G cts, level
  * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
  * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, int comparator, int schedule, int sum_radix, int hoist, u64* out,
+             int cheb_n, double tau, int comparator, int schedule, int sum_radix, int hoist, int babies_pq, u64* out,
              int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
@@ -1662,8 +1801,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     or_drop(c, qct, top, lq, q);
     if (mode == 0) {
         int r = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, out)
-                : hoist       ? or_bsgs_scores_hoisted(c, k, q, lq, T, K, ell, n1, out)
-                              : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, out);
+                              : or_bsgs_scores_pq(c, k, q, lq, T, K, ell, n1, babies_pq, hoist, out);
         *out_level = lq - 1;
         free(q);
         return r;
@@ -1672,8 +1810,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
     if (dep < 0 || lq - 1 - dep < 0) { free(q); return -1; }
     u64* S = (u64*)malloc(sizeof(u64) * ct_words(c, lq - 1) * G);
     int rs = schedule == 1 ? or_table_scores(c, k, q, lq, T, K, ell, n1, S)
-             : hoist       ? or_bsgs_scores_hoisted(c, k, q, lq, T, K, ell, n1, S)
-                           : or_bsgs_scores(c, k, q, lq, T, K, ell, n1, S);
+                           : or_bsgs_scores_pq(c, k, q, lq, T, K, ell, n1, babies_pq, hoist, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);
     int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, comparator, sum_radix, out, out_level);

@@ -433,6 +433,28 @@ def test_giant_steps_with_one_moddown(c1, k1):
     assert np.array_equal(k1.bsgs_scores(qct, T, ell, 64, hoist=True), k1.bsgs_scores(qct, T, ell, 64))
 
 
+def test_baby_steps_in_extended_basis(c1, k1):
+    """Baby steps kept in Q_l u P, one ModDown per giant step (double hoisting of the baby steps):
+    the FP64 matvec again, with and without the giant steps sharing one ModDown; with n1 = 1 the
+    only baby is P q, whose ModDown is q exactly, so the scores equal the plain schedule bit for
+    bit; with more babies the bits differ (ModDown is linear only up to its rounding)."""
+    K, ell = 64, 64
+    T = _templates(K, ell, 0xF00D000A)
+    rng = np.random.default_rng(23)
+    q = rng.standard_normal(ell)
+    q /= np.linalg.norm(q)
+    qct = k1.encrypt(np.tile(q, c1.n // ell), 25)
+    ref = T.astype(np.float64) @ q
+    for n1 in (8, 5, 64):
+        for hoist in (False, True):
+            S = k1.bsgs_scores_pq(qct, T, ell, n1, hoist=hoist)
+            got = k1.decrypt(S[0], 1)
+            assert np.abs(got[:K] - ref).max() < 1e-4 and np.abs(got[K:]).max() < 1e-4
+            assert not np.array_equal(S, k1.bsgs_scores(qct, T, ell, n1, hoist=hoist))
+    assert np.array_equal(k1.bsgs_scores_pq(qct, T, ell, 1), k1.bsgs_scores(qct, T, ell, 1))
+    assert np.array_equal(k1.bsgs_scores_pq(qct, T, ell, 8, pq=False), k1.bsgs_scores(qct, T, ell, 8))
+
+
 def test_table_schedule_matches_plain_matvec(c1, k1):
     """Algorithm 1 (rotated-query table): decrypts to the FP64 matvec for any n1; with
     n1 = l (babies only) or n1 = 1 (giant rotations of q only) every table entry is one
@@ -684,6 +706,10 @@ def test_match_modes_small():
     memh, lvl5 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, hoist=True)
     assert lvl5 == lvl2 and not np.array_equal(memh, memb)
     assert np.abs(k.decrypt(memh[0], lvl5) - p.sum()).max() < 1e-2
+    # baby steps kept in Q_l u P: the same sum
+    memq, lvl6 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, hoist=True, babies_pq=True)
+    assert lvl6 == lvl2 and not np.array_equal(memq, memh)
+    assert np.abs(k.decrypt(memq[0], lvl6) - p.sum()).max() < 1e-2
 
 
 def test_match_hybrid_comparator_small():
