@@ -103,7 +103,8 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle: whole membership queries, timed
 # ---------------------------------------------------------------------------
-def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_queries=1, sum_radix=4, hoist=True):
+def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_queries=1, sum_radix=4, hoist=True,
+                   babies_pq=False):
     """Time whole membership queries of the CPU oracle (the same match the library computes,
     bit for bit: on-demand BSGS at working level lq, by default with giant steps sharing one
     ModDown and RotateAndSum in radix 4). Key generation and encryption happen before the timed region;
@@ -112,7 +113,7 @@ def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_quer
     Returns (seconds per query list, threads used, membership ciphertext of the first query)."""
     import oracle
     from paper_2604_00546_gb300 import workloads as W
-    c = W.CONFIGS[cfgname]
+    c = W.CONFIGS[cfgname] if isinstance(cfgname, str) else cfgname
     oc = oracle.Ctx(c["log_n"], c["q_bits"], c["p_bits"], c["dnum"], c["scale_bits"])
     ok = oc.keygen(seed_key)
     oq = ok.encrypt(np.tile(q, oc.n // c["ell"]), seed_enc)
@@ -120,7 +121,7 @@ def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_quer
     while True:
         t0 = time.perf_counter()
         ref, lvl = ok.match(oq, T, c["ell"], c["n1"], 2, c["cheb_degree"], c["threshold"], level=lq,
-                            sum_radix=sum_radix, hoist=hoist)
+                            sum_radix=sum_radix, hoist=hoist, babies_pq=babies_pq)
         secs.append(time.perf_counter() - t0)
         if first is None:
             first = (ref[0], lvl)
@@ -169,7 +170,8 @@ def run_serving(args):
     torch.cuda.set_device(local)
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
     Ts = W.serving_databases(c["ell"])
@@ -263,7 +265,8 @@ def run_identify(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, db_tier=args.identify_tier,
-                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_IDENTIFY), W.key_seed(cfg))
     ctx.load_keys(keys)
     db = ctx.load_db(T)
@@ -354,7 +357,8 @@ def run_multi(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
     sizes = W.multi_sizes(args.multi_n)
@@ -559,7 +563,8 @@ def run_sharded(args):
     Ts, (g0, g1) = shard.template_shard(T, slots, ws, rank)
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, db_tier=args.identify_tier,
                      **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix,
-                     hoist_giants=args.hoist_giants)
+                     hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
     db = ctx.load_db(Ts) if g1 > g0 else None
@@ -612,6 +617,81 @@ def run_sharded(args):
         D.destroy_process_group()
 
 
+def run_tensor_probe(args):
+    """The tensor-core question of an exact NTT: the measured dense INT8 rate of this GPU (cuBLAS
+    through torch._int_mm, 8192^3, int8 x int8 -> int32) beside the bf16 rate, and the rate an
+    exact tensor-core NTT would need to beat the CUDA-core NTT measured here. An exact product of
+    residues below 2^60 split into 8-bit limbs takes 64 int8 multiply-adds; a 2^16-point NTT as
+    two dense 256-point DFT passes (four-step form) takes 2 x 2^16 x 256 modular products per
+    polynomial, so 2 x 2^16 x 256 x 64 x 2 int8 operations, against the CUDA-core transform's
+    measured microseconds per polynomial (fr_ntt_time, 1024 polynomials)."""
+    import torch
+
+    from paper_2604_00546_gb300 import fr
+    from paper_2604_00546_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 8192
+
+    def rate(fn, flops):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(10):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return flops / (best / 1000.0)
+
+    a8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+    b8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+    int8_ops = rate(lambda: torch._int_mm(a8, b8), 2.0 * n ** 3)
+    a16 = torch.randn(n, n, dtype=torch.bfloat16, device=dev)
+    b16 = torch.randn(n, n, dtype=torch.bfloat16, device=dev)
+    bf16_flops = rate(lambda: a16 @ b16, 2.0 * n ** 3)
+    ctx = fr.Context(device=local, **W.ctx_params("membership", level_mode=1))
+    npol = 1024
+    f_us, i_us = ctx.ntt_time(npol, ctx.work_level, 5)
+    per_poly_s = 0.5 * (f_us + i_us) * 1e-6 / npol
+    ops_per_poly = 2.0 * (1 << 16) * 256 * 64 * 2
+    line = {
+        "metric": "tensor-core question of the exact NTT", "int8_dense_ops_per_s": int8_ops,
+        "bf16_dense_flops_per_s": bf16_flops, "int8_over_bf16": int8_ops / bf16_flops,
+        "cuda_core_ntt_us_per_poly": per_poly_s * 1e6, "int8_ops_per_poly_dense_dft": ops_per_poly,
+        "int8_ops_per_s_needed_to_match": ops_per_poly / per_poly_s,
+        "int8_time_per_poly_us_at_measured_rate": ops_per_poly / int8_ops * 1e6,
+        "verdict": "tensor cores slower" if ops_per_poly / int8_ops > per_poly_s else "tensor cores faster",
+    }
+    return line
+
+
+def run_ntt_sweep(args):
+    """The batched NTT alone (fr_ntt_time) at the headline ring (N = 2^16, working level 8,
+    shapes picked by the tuner): microseconds per forward and inverse launch sequence and
+    butterflies per second against the register-only butterfly rate, per batch size. With one
+    size it is also the small case the NTT's ncu captures run on."""
+    from paper_2604_00546_gb300 import fr
+    from paper_2604_00546_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    ctx = fr.Context(device=local, **W.ctx_params("membership", level_mode=1))
+    peak = fr.butterfly_peak(local)
+    rows = []
+    for n in args.ntt_sizes:
+        f, i = ctx.ntt_time(n, ctx.work_level, 5)
+        bf = n * (1 << 15) * 16.0
+        rows.append({"polys": n, "fwd_us": f, "inv_us": i, "fwd_frac": bf / (f * 1e-6) / peak,
+                     "inv_frac": bf / (i * 1e-6) / peak})
+    return {"metric": "batched NTT, N=2^16: time per launch sequence and fraction of the butterfly peak",
+            "butterfly_peak_per_s": peak, "shapes": ctx.ntt_tuning(), "rows": rows}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (the paper has no runnable code) on the same workload,
     metric and unit. Each step is one whole membership query of the oracle on the host cores;
@@ -628,7 +708,7 @@ def run_reference(args):
     t_all = time.perf_counter()
     secs, cores, _ = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq, budget_s=100.0,
                                     max_queries=max(1, args.steps), sum_radix=args.sum_radix,
-                                    hoist=bool(args.hoist_giants))
+                                    hoist=bool(args.hoist_giants), babies_pq=bool(args.hoist_babies))
     wall = time.perf_counter() - t_all
     per = float(np.mean(secs))
     value = len(T) / per
@@ -713,12 +793,15 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     cfg = args.config
-    c = W.CONFIGS[cfg]
+    if args.ell:   # a smaller template dimension (profiling cases); the headline is ell = 512
+        cfg = dict(W.CONFIGS[cfg], ell=args.ell)
+    c = W.CONFIGS[cfg] if isinstance(cfg, str) else cfg
     mode = c["mode"]
     T, q, planted = W.workload(cfg)
     K = len(T)
     t0 = time.perf_counter()
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
     rots = ctx.required_rotations(mode)
     keys = ctx.keygen(rots, W.key_seed(cfg))
     t_keygen = time.perf_counter() - t0
@@ -847,7 +930,8 @@ def run_ours(args):
     # the same query on the whole modulus chain (no level drop), for comparison
     full = None
     if args.level_mode == 1 and not args.no_full_chain and lq < len(c["q_bits"]) - 1:
-        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
         ctx_f.load_keys(keys)
         db_f = ctx_f.load_db(T)
         dq_f = ctx_f.encrypt(keys, q, W.enc_seed(cfg)).upload()
@@ -873,7 +957,8 @@ def run_ours(args):
     table = None
     if not args.no_table:
         ctx_t = fr.Context(device=local, cuda_stream=stream.cuda_stream, schedule=1,
-                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
         ctx_t.load_keys(keys)
         db_t = ctx_t.load_db(T)
         dq_t = ctx_t.encrypt(keys, q, W.enc_seed(cfg)).upload()
@@ -903,7 +988,8 @@ def run_ours(args):
     if not args.no_hybrid:
         ctx_h = fr.Context(device=local, cuda_stream=stream.cuda_stream, comparator=1,
                            **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix,
-                           hoist_giants=args.hoist_giants)
+                           hoist_giants=args.hoist_giants,
+                     hoist_babies=args.hoist_babies)
         ctx_h.load_keys(keys)
         db_h = ctx_h.load_db(T)
         dq_h = ctx_h.encrypt(keys, q, W.enc_seed(cfg)).upload()
@@ -951,7 +1037,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         secs, cores, (o_ct, o_lvl) = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq,
-                                                    sum_radix=args.sum_radix, hoist=bool(args.hoist_giants))
+                                                    sum_radix=args.sum_radix, hoist=bool(args.hoist_giants),
+                                                    babies_pq=bool(args.hoist_babies))
         cpu = {"value": K / float(np.mean(secs)), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "one whole membership query of the oracle, K=%d at working level %d: %.1f s" % (K, lq, secs[0]),
                "seconds_per_query": float(np.mean(secs)),
@@ -964,10 +1051,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded Gaussian L2-normalised templates, 32 planted duplicates at cosine 0.8)",
-            "config": {"workload": "membership N=2^16 K=2^15 ell=512 n1=32 deg59", "K": K, "log_n": c["log_n"],
+            "config": {"workload": "membership N=2^16 K=2^15 ell=%d n1=32 deg59" % c["ell"], "K": K, "log_n": c["log_n"],
                        "q_limbs": len(c["q_bits"]), "p_limbs": len(c["p_bits"]), "dnum": c["dnum"],
                        "work_level": lq, "level_mode": args.level_mode, "sum_radix": args.sum_radix,
-                       "hoist_giants": args.hoist_giants,
+                       "hoist_giants": args.hoist_giants, "hoist_babies": args.hoist_babies,
                        "parallelism": f"replicas x{ws}",
                        "l2": "working set (diagonals + evaluation keys, several GB) exceeds the 129 MB L2; no flush"},
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99)),
@@ -1012,6 +1099,8 @@ def main():
     ap.add_argument("--no-full-chain", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the table-schedule comparison")
     ap.add_argument("--level-mode", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--hoist-babies", type=int, default=1, choices=[0, 1],
+                    help="baby steps kept in Q_l u P with one ModDown per giant step (fr_params.hoist_babies)")
     ap.add_argument("--hoist-giants", type=int, default=1, choices=[0, 1],
                     help="giant steps of a (query, group) share one ModDown (0: one per rotation)")
     ap.add_argument("--sum-radix", type=int, default=4, choices=[2, 4, 8, 16, 32],
@@ -1031,6 +1120,12 @@ def main():
                     help="run the encrypted-database membership workload instead")
     ap.add_argument("--db-ell", type=int, default=512, help="template dimension of --encrypted-db (512: the workload)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-comparator comparison")
+    ap.add_argument("--ntt-sweep", action="store_true", help="time the batched NTT alone per batch size instead")
+    ap.add_argument("--ntt-sizes", type=int, nargs="+", default=[1, 4, 16, 30, 64, 128, 248, 512, 1024])
+    ap.add_argument("--ell", type=int, default=0,
+                    help="template dimension of the membership workload (0: 512); smaller cases for profiling")
+    ap.add_argument("--tensor-probe", action="store_true",
+                    help="measure the INT8 / bf16 tensor rates against the CUDA-core NTT instead")
     ap.add_argument("--shard", action="store_true",
                     help="run the block-sharded K=2^20 membership across the ranks instead (strong scaling)")
     ap.add_argument("--no-secondary", action="store_true",
@@ -1048,6 +1143,10 @@ def main():
         print(json.dumps(run_encrypted(args)), flush=True)
     elif args.shard:
         run_sharded(args)
+    elif args.tensor_probe:
+        print(json.dumps(run_tensor_probe(args)), flush=True)
+    elif args.ntt_sweep:
+        print(json.dumps(run_ntt_sweep(args)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

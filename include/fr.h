@@ -126,6 +126,15 @@ typedef struct {
                                   35 y^9) / 128, depth d2 + 4. Its slot values are 0 or 1 to within about
                                   1e-2 outside |x - tau| <= 0.02, so a membership sum counts the matches.
                                   level_mode 1 adds the 4 levels to the working level. */
+    uint32_t hoist_babies;     /* on-demand schedule, plaintext databases: 0 every baby step B_i = Rot_i(q)
+                                  ends with its own ModDown (Algorithm 1's hoisting, the paper's GPU
+                                  path); 1 the baby steps stay in Q_l u P before any ModDown (double
+                                  hoisting of the baby steps, Section "Hoisting and double hoisting"):
+                                  B_i = (P sigma_i(q.b) + IP0_i, IP1_i), the diagonals are kept over
+                                  every limb of Q_l u P, and each giant step takes one ModDown of its
+                                  sum, fused with its rescale. Same values, other noise; fewer NTTs,
+                                  (l + 1 + n_p) / (l + 1) more diagonal words. Encrypted databases
+                                  (fr_load_db_encrypted) need 0. */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.
@@ -353,13 +362,15 @@ fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t*
 /* NTT autotuner (run by fr_setup on device contexts unless the environment sets
  * FR_NTT_TUNE=0): for N >= 2^15 it times each shape of a forward + inverse transform on this
  * GPU for one batch size per bucket (<= 4, <= 16, <= 64, > 64 limb-polynomials; best of 3
- * runs after a warm-up) and keeps the fastest. Shapes 0..3: two-pass kernels, bit 0 = 8
- * columns per column-pass CTA (else 4), bit 1 = 256-thread row-pass CTAs (else 128); shape 4
- * (N = 2^16 only): one launch per transform, a cluster of 8 CTAs per polynomial exchanging
- * through distributed shared memory. shapes[4] receives the chosen shape per bucket, us[20]
- * (may be NULL) the measured microseconds, bucket-major (-1: shape not available). */
+ * runs after a warm-up) and keeps the fastest. Shapes 0..3: radix-8 two-pass kernels (8
+ * residues per thread), bit 0 = 8 columns per column-pass CTA (else 4), bit 1 = 256-thread
+ * row-pass CTAs (else 128); shape 4 (N = 2^16 only): one launch per transform, a cluster of 8
+ * CTAs per polynomial exchanging through distributed shared memory; shape 5 (N = 2^16 only):
+ * radix-16 two-pass kernels (16 residues per thread, one exchange per pass). shapes[4]
+ * receives the chosen shape per bucket, us[24] (may be NULL) the measured microseconds,
+ * bucket-major, 6 per bucket (-1: shape not available). */
 fr_status fr_ntt_tuning(const fr_ctx* ctx, uint32_t* shapes, double* us);
-/* Override the shape per bucket (shapes[4], each 0..4); drops the captured match graphs.
+/* Override the shape per bucket (shapes[4], each 0..5); drops the captured match graphs.
  * Every shape computes the same transform, bit for bit. */
 fr_status fr_ntt_set_shapes(fr_ctx* ctx, const uint32_t* shapes);
 

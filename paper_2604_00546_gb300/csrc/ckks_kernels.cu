@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, 
 // ---------------------------------------------------------------------------
 template <int BETA>
 __device__ __forceinline__ void ip_job(const IPJob& J, const u64 (&k0)[BETA], const u64 (&k1)[BETA], int npos, int pos,
-                                       int k, u64 q, u64 qinv, int logN, int N) {
+                                       int k, u64 q, u64 qinv, int logN, int N, int level, const u64* pmod,
+                                       const u64* pmod_s) {
     const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
     Acc128 a0{0, 0}, a1{0, 0};
 #pragma unroll
@@ -96,13 +97,16 @@ __device__ __forceinline__ void ip_job(const IPJob& J, const u64 (&k0)[BETA], co
     }
     fold(a0, q);
     fold(a1, q);
-    J.out[(long long)pos * N + k] = redc(a0.hi, a0.lo, q, qinv);
+    u64 r0 = redc(a0.hi, a0.lo, q, qinv);
+    if (J.addb && pos <= level)  // a rotation kept in Q_l u P: + P sigma(b) on the Q positions
+        r0 = add_mod(r0, mul_shoup(J.addb[(long long)pos * N + src], pmod[pos], pmod_s[pos], q), q);
+    J.out[(long long)pos * N + k] = r0;
     J.out[((long long)npos + pos) * N + k] = redc(a1.hi, a1.lo, q, qinv);
 }
 
 template <int BETA>
 __device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, int klimb, int T, int k, u64 q,
-                                        u64 qinv, int logN, int N) {
+                                        u64 qinv, int logN, int N, int level, const u64* pmod, const u64* pmod_s) {
     // one key group per blockIdx.z: its key words are read once and applied to every job of the group
     const int g = blockIdx.z;
     const u64* key = jobs.gkey[g];
@@ -112,14 +116,16 @@ __device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, i
         k0[d] = key[(((long long)d * 2 + 0) * T + klimb) * N + k];
         k1[d] = key[(((long long)d * 2 + 1) * T + klimb) * N + k];
     }
-    for (int j = jobs.gstart[g]; j < jobs.gstart[g + 1]; ++j) ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N);
+    for (int j = jobs.gstart[g]; j < jobs.gstart[g + 1]; ++j)
+        ip_job<BETA>(jobs.j[j], k0, k1, npos, pos, k, q, qinv, logN, N, level, pmod, pmod_s);
 }
 
 // key layout [digit][2][T][N]: Q limbs at positions 0.., P limbs from position kp. One
 // instantiation per digit count, so the registers a launch needs follow its beta.
 template <int BETA>
-__global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int npos, int level, int kp, int T,
-                                                 const DevPrime* __restrict__ primes, int pbase, int logN) {
+__global__ void __launch_bounds__(kThreads) k_ip(const __grid_constant__ IPJobs jobs, int npos, int level, int kp,
+                                                 int T, const DevPrime* __restrict__ primes, int pbase, int logN,
+                                                 const u64* __restrict__ pmod, const u64* __restrict__ pmod_s) {
     pdl_wait();
     pdl_trigger();
     const int N = 1 << logN;
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_ip(const IPJobs jobs, int npos, in
     const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
     const u64 q = primes[pi].q, qinv = primes[pi].qinv;
     const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
-    ip_body<BETA>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N);
+    ip_body<BETA>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N, level, pmod, pmod_s);
 }
 
 // ---------------------------------------------------------------------------
@@ -220,6 +226,74 @@ __global__ void __launch_bounds__(kThreads) k_rescale_lift(const u64* __restrict
         u64 r = mul_shoup(x, 1, tab->one_s[i], q);  // x mod q
         if (neg) r = sub_mod(r, tab->ql_mod[i], q);
         o[(long long)i * N + k] = r;
+    }
+}
+
+// Baby steps kept in Q_l u P (double hoisting of the baby steps): baby 0 of query b is P q_b on
+// the Q positions and zero on the P positions (babies 1..n1-1 come from the inner-product
+// kernel, which adds P sigma_i(q_b.b) itself). babies [B][n1][2][npos][N] (query b at babies +
+// b baby_q); q_b at q + b q_bs, [2][q_cap][N], evaluation form. Grid (N / 256, npos, 2 B).
+__global__ void __launch_bounds__(kThreads) k_baby0_pq(u64* __restrict__ babies, long long baby_q,
+                                                       const u64* __restrict__ q, long long q_bs, int q_cap, int npos,
+                                                       int level, const DevPrime* __restrict__ primes,
+                                                       const u64* __restrict__ pmod, const u64* __restrict__ pmod_s,
+                                                       int N) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y;
+    const int t = blockIdx.z & 1, b = blockIdx.z >> 1;
+    if (k >= N) return;
+    u64* o = babies + (long long)b * baby_q + ((long long)t * npos + pos) * N + k;
+    if (pos > level) {
+        *o = 0;
+        return;
+    }
+    const u64 qp = primes[pos].q;
+    *o = mul_shoup(q[(long long)b * q_bs + ((long long)t * q_cap + pos) * N + k], pmod[pos], pmod_s[pos], qp);
+}
+
+// Relinearisation + rescale, last limb: z = acc_l P^-1 + d_l (evaluation form), the last limb
+// of the relinearised product before the rescale. acc [J][2][npos][N], d [J][3][l+1][N] or
+// null (a ModDown with no addend), z [J][2][N].
+__global__ void __launch_bounds__(kThreads) k_rs_last(const u64* __restrict__ acc, const u64* __restrict__ d,
+                                                      u64* __restrict__ z, const u64* __restrict__ pinv,
+                                                      const u64* __restrict__ pinv_s, int npos, int l,
+                                                      const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jt = blockIdx.y, j = jt >> 1, t = jt & 1;
+    if (k >= N) return;
+    const u64 q = primes[l].q;
+    const u64 a = acc[((long long)jt * npos + l) * N + k];
+    const u64 dd = d ? d[(((long long)j * 3 + t) * (l + 1) + l) * N + k] : 0;
+    z[(long long)jt * N + k] = add_mod(mul_shoup(a, pinv[l], pinv_s[l], q), dd, q);
+}
+
+// Relinearisation + rescale, lift: with zc = z in coefficient form and conv the P -> Q
+// conversion (coefficient form, [J][2][l+1][N]), the relinearised product's last limb is
+// m = zc - conv_l P^-1 (mod q_l); y_i = conv_i P^-1 + [centered m]_{q_i} for i < l, [J][2][l][N].
+__global__ void __launch_bounds__(kThreads) k_rs_lift(const u64* __restrict__ zc, const u64* __restrict__ conv,
+                                                      u64* __restrict__ y, const u64* __restrict__ pinv,
+                                                      const u64* __restrict__ pinv_s,
+                                                      const RescaleTab* __restrict__ tab,
+                                                      const DevPrime* __restrict__ primes, int l, int N) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jt = blockIdx.y;
+    if (k >= N) return;
+    const u64 ql = primes[l].q;
+    const u64* cv = conv + (long long)jt * (l + 1) * N;
+    const u64 m = sub_mod(zc[(long long)jt * N + k], mul_shoup(cv[(long long)l * N + k], pinv[l], pinv_s[l], ql), ql);
+    const bool neg = m > tab->half;
+    u64* o = y + (long long)jt * l * N;
+    for (int i = 0; i < l; ++i) {
+        const u64 q = tab->q[i];
+        u64 r = mul_shoup(m, 1, tab->one_s[i], q);
+        if (neg) r = sub_mod(r, tab->ql_mod[i], q);
+        o[(long long)i * N + k] = add_mod(mul_shoup(cv[(long long)i * N + k], pinv[i], pinv_s[i], q), r, q);
     }
 }
 
@@ -361,6 +435,117 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
         j = jn;
         i0 = in;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal MAC with the diagonals streamed through shared memory (the on-demand schedule's S4
+// for B = 1..4 queries against one database, when n1 is a multiple of SD = 8 and n2 of JG): the
+// sums of k_mac, P_{b,j}[t][i][k] = sum_{i'} B_{b,i'}[t][i][k] * D'_{j n1 + i'}[i][k], every
+// diagonal word read once for all B queries. A CTA owns TP points of one limb and JG giant-step
+// rows: thread (jg, point) accumulates giant steps jb JG + jg for its point. The babies of the
+// CTA's points are staged once (30-bit halves, every query); the diagonals flow through a ring of
+// kMpNS stages, stage (jb, i0) holding diagonals (jb JG + jg) n1 + i0 + u for jg < JG, u < SD,
+// filled by 16-byte asynchronous copies (cp.async, one commit group per stage, kMpNS - 1 stages
+// in flight while one is multiplied). A warp reads TP consecutive words of one row: no bank
+// conflicts, and no exchange between threads until a giant step's sums are complete.
+// ---------------------------------------------------------------------------
+constexpr int kMpNS = 4;  // ring stages
+constexpr int kMpSD = 8;  // diagonals of one giant step per stage (8 products between carries)
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
+
+template <int B, int TP, int JG>
+__global__ void __launch_bounds__(TP * JG) k_mac_pipe(const u64* __restrict__ babies, long long baby_q, int cap_b,
+                                                      const u64* __restrict__ diags, u64* __restrict__ out,
+                                                      long long out_q, int cap_o, int nl, int n1, int n2,
+                                                      const DevPrime* __restrict__ primes, int N) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int SD = kMpSD;
+    constexpr int NT = TP * JG;                       // threads
+    constexpr int ROWS = JG * SD;                     // diagonal rows per stage
+    constexpr int CHUNKS = ROWS * TP / 2;             // 16-byte chunks per stage
+    static_assert(CHUNKS % NT == 0, "whole chunks per thread");
+    extern __shared__ __align__(16) u64 smp[];
+    u64* sb = smp;                                    // babies [B][n1][2][TP], split
+    u64* sd = sb + (size_t)B * n1 * 2 * TP;           // ring [NS][JG][SD][TP]
+    const int i = blockIdx.y;
+    const int k0 = blockIdx.x * TP;
+    const int pl = threadIdx.x % TP, jg = threadIdx.x / TP;
+    const u64 q = primes[i].q, qinv = primes[i].qinv;
+    const int spb = n1 / SD;                          // stages per giant-step block
+    const int nst = (n2 / JG) * spb;
+    const int per_q = n1 * 2 * TP;
+    auto issue = [&](int s) {
+        if (s < nst) {
+            const int jb = s / spb, i0 = (s % spb) * SD;
+            u64* dst = sd + (size_t)(s % kMpNS) * ROWS * TP;
+#pragma unroll
+            for (int r = 0; r < CHUNKS / NT; ++r) {
+                const int ch = threadIdx.x + r * NT;
+                const int row = ch / (TP / 2), w = (ch % (TP / 2)) * 2;
+                const int g = row / SD, u = row % SD;
+                const long long d = (long long)(jb * JG + g) * n1 + i0 + u;
+                cp_async16(dst + (size_t)row * TP + w, diags + (d * nl + i) * N + k0 + w);
+            }
+        }
+        cp_async_commit();  // an empty group past the last stage keeps the group count uniform
+    };
+#pragma unroll
+    for (int s = 0; s < kMpNS - 1; ++s) issue(s);
+    for (int e = threadIdx.x; e < B * per_q; e += NT) {
+        const int qb = e / per_q, r = e % per_q;
+        const int ib = r / (2 * TP), t = (r / TP) & 1, pp = r % TP;
+        sb[e] = split30(babies[(long long)qb * baby_q + ((long long)ib * 2 + t) * cap_b * N + (long long)i * N + k0 + pp]);
+    }
+    Acc128 acc[B][2];
+#pragma unroll
+    for (int qb = 0; qb < B; ++qb) acc[qb][0] = acc[qb][1] = Acc128{0, 0};
+    for (int s = 0; s < nst; ++s) {
+        cp_async_wait<kMpNS - 2>();  // this thread's copies of stage s have landed
+        __syncthreads();             // every thread's have; slot (s - 1) % NS is free again
+        issue(s + kMpNS - 1);
+        const int jb = s / spb, i0 = (s % spb) * SD;
+        const u64* st = sd + (size_t)(s % kMpNS) * ROWS * TP + (size_t)jg * SD * TP + pl;
+        Acc3 p[B][2];
+#pragma unroll
+        for (int qb = 0; qb < B; ++qb) p[qb][0] = p[qb][1] = Acc3{0, 0, 0};
+#pragma unroll
+        for (int u = 0; u < SD; ++u) {
+            const u64 ds = split30(st[(size_t)u * TP]);
+#pragma unroll
+            for (int qb = 0; qb < B; ++qb) {
+                const u64* sq = sb + (size_t)qb * per_q + ((size_t)(i0 + u) * 2) * TP + pl;
+                mac30(p[qb][0], sq[0], ds);
+                mac30(p[qb][1], sq[TP], ds);
+            }
+        }
+#pragma unroll
+        for (int qb = 0; qb < B; ++qb) {
+            flush30(acc[qb][0], p[qb][0]);
+            flush30(acc[qb][1], p[qb][1]);
+            fold(acc[qb][0], q);
+            fold(acc[qb][1], q);
+        }
+        if (i0 + SD == n1) {
+            // giant step jb JG + jg complete for this point: reduce and store
+            const int j = jb * JG + jg;
+#pragma unroll
+            for (int qb = 0; qb < B; ++qb) {
+                u64* O = out + (long long)qb * out_q + (long long)j * 2 * cap_o * N;
+                O[(long long)i * N + k0 + pl] = redc(acc[qb][0].hi, acc[qb][0].lo, q, qinv);
+                O[((long long)cap_o + i) * N + k0 + pl] = redc(acc[qb][1].hi, acc[qb][1].lo, q, qinv);
+                acc[qb][0] = acc[qb][1] = Acc128{0, 0};
+            }
+        }
+    }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -781,15 +966,17 @@ void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext,
 }
 
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
-               const PrimeMap& pos_prime, int logN, cudaStream_t s) {
+               const PrimeMap& pos_prime, int logN, cudaStream_t s, const u64* pmod, const u64* pmod_s) {
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, npos, jobs.ngroups);
     const int pbase = npos > level + 1 ? pos_prime.idx[level + 1] : 0;
     switch (beta) {
 #define FR_IP_CASE(B) \
-    case B: launch_k(k_ip<B>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN); break;
+    case B: launch_k(k_ip<B>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN, pmod, pmod_s); \
+        break;
         FR_IP_CASE(1) FR_IP_CASE(2) FR_IP_CASE(3) FR_IP_CASE(4) FR_IP_CASE(5) FR_IP_CASE(6) FR_IP_CASE(7)
-        default: launch_k(k_ip<8>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN); break;
+        default: launch_k(k_ip<8>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN, pmod, pmod_s);
+            break;
 #undef FR_IP_CASE
     }
 }
@@ -805,6 +992,24 @@ void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, cons
     const int N = 1 << logN;
     dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), J);
     launch_k(k_moddown_combine, dim3(g), dim3(kThreads), 0, s, jobs, npos, level, pinv, pinv_s, primes, logN);
+}
+
+void launch_baby0_pq(u64* babies, long long baby_q, const u64* q, long long q_bs, int q_cap, int B, int npos,
+                     int level, const DevPrime* primes, const u64* pmod, const u64* pmod_s, int N, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, npos, 2 * B);
+    launch_k(k_baby0_pq, g, dim3(kThreads), 0, s, babies, baby_q, q, q_bs, q_cap, npos, level, primes, pmod, pmod_s, N);
+}
+
+void launch_rs_last(const u64* acc, const u64* d, u64* z, const u64* pinv, const u64* pinv_s, int npos, int l,
+                    const DevPrime* primes, int N, int J, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * J);
+    launch_k(k_rs_last, g, dim3(kThreads), 0, s, acc, d, z, pinv, pinv_s, npos, l, primes, N);
+}
+
+void launch_rs_lift(const u64* zc, const u64* conv, u64* y, const u64* pinv, const u64* pinv_s, const RescaleTab* tab,
+                    const DevPrime* primes, int l, int N, int J, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * J);
+    launch_k(k_rs_lift, g, dim3(kThreads), 0, s, zc, conv, y, pinv, pinv_s, tab, primes, l, N);
 }
 
 void launch_rescale_lift(const u64* last, u64* lifted, const RescaleTab* tab, int l, int N, int BT, cudaStream_t s) {
@@ -837,6 +1042,39 @@ static void launch_mac_t(const u64* babies, long long baby_q, int cap_b, const u
     smem_limit_once(k_mac<B>, 200 * 1024, attr);
     dim3 g(N / TP, nl);
     launch_k(k_mac<B>, dim3(g), dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
+}
+
+bool mac_pipe_fits(int n1, int ell, int N) {
+    const int n2 = n1 > 0 ? ell / n1 : 0;
+    return n1 % kMpSD == 0 && n1 <= 64 && ell % n1 == 0 && n2 % 4 == 0 && N % 64 == 0;
+}
+
+// TP points x JG = 4 giant-step rows per CTA: 64 points for one query, 32 for 2..4 (the staged
+// babies of B queries stay within 64 KiB at n1 = 32)
+template <int B>
+static void launch_mac_pipe_t(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out,
+                              long long out_q, int cap_o, int nl, int n1, int n2, const DevPrime* primes, int N,
+                              cudaStream_t s) {
+    constexpr int TP = B == 1 ? 64 : 32, JG = 4;
+    const size_t sm = ((size_t)B * n1 * 2 * TP + (size_t)kMpNS * JG * kMpSD * TP) * sizeof(u64);
+    // the limit is raised once per device, so to the most any n1 <= 64 needs (200 KiB)
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(k_mac_pipe<B, TP, JG>, 200 * 1024, attr);
+    dim3 g(N / TP, nl);
+    launch_k(k_mac_pipe<B, TP, JG>, g, dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1,
+             n2, primes, N);
+}
+
+void launch_mac_pipe(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                     int cap_o, int nl, int n1, int ell, int B, const DevPrime* primes, int N, cudaStream_t s) {
+    const int n2 = ell / n1;
+    switch (B) {
+        case 1: launch_mac_pipe_t<1>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 2: launch_mac_pipe_t<2>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 3: launch_mac_pipe_t<3>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 4: launch_mac_pipe_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        default: break;  // the engine splits larger batches
+    }
 }
 
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,

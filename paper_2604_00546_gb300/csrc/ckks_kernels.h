@@ -43,6 +43,8 @@ struct IPJob {
     u64* out;        // [2][npos][N]
     u32 galois;      // 1: no automorphism
     u32 pad;
+    const u64* addb = nullptr;  // non-null: add P sigma_galois(addb) to component 0 on the Q positions
+                                // (addb: limbs 0..level, stride N, evaluation form)
 };
 
 struct MDJob {
@@ -98,10 +100,27 @@ void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs
 void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
                         const RescaleTab* tab, int l, int mode, const u64* add, int add_cap, long long add_bs,
                         const u64* cres, cudaStream_t s);
+// Baby steps kept in Q_l u P: baby 0 = P q (zero on the P positions) of each of B queries,
+// babies [B][n1][2][npos][N]; babies 1..n1-1 are inner products with IPJob::addb set.
+void launch_baby0_pq(u64* babies, long long baby_q, const u64* q, long long q_bs, int q_cap, int B, int npos,
+                     int level, const DevPrime* primes, const u64* pmod, const u64* pmod_s, int N, cudaStream_t s);
+// Relinearisation fused with the rescale after it (J products at level l): launch_rs_last forms
+// z = acc_l P^-1 + d_l [J][2][N]; after its inverse NTT, launch_rs_lift forms y = conv P^-1 +
+// centered lift [J][2][l][N]; the forward NTT of y with launch_ntt_relin_rescale writes
+// out_j = (acc P^-1 + d - NTT(y)) q_l^-1 (+ the EpiRescale modes) at level l - 1.
+void launch_rs_last(const u64* acc, const u64* d, u64* z, const u64* pinv, const u64* pinv_s, int npos, int l,
+                    const DevPrime* primes, int N, int J, cudaStream_t s);
+void launch_rs_lift(const u64* zc, const u64* conv, u64* y, const u64* pinv, const u64* pinv_s, const RescaleTab* tab,
+                    const DevPrime* primes, int l, int N, int J, cudaStream_t s);
+void launch_ntt_relin_rescale(const RingDev& R, const PolyBatch& b, const u64* acc, const u64* d, int npos, int l,
+                              const u64* pinv, const u64* pinv_s, const RescaleTab* tab, u64* out, int out_cap,
+                              long long out_bs, int mode, const u64* add, int add_cap, long long add_bs,
+                              const u64* cres, cudaStream_t s);
 void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
                   int npos, int N, int J, cudaStream_t s);
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
-               const PrimeMap& pos_prime, int logN, cudaStream_t s);
+               const PrimeMap& pos_prime, int logN, cudaStream_t s, const u64* pmod = nullptr,
+               const u64* pmod_s = nullptr);
 void launch_p2q(const u64* acc, long long acc_job, int npos, int level, u64* conv, const P2QTab* tab, int N, int J,
                 cudaStream_t s);
 void launch_moddown_combine(const MDJobs& jobs, int J, int npos, int level, const u64* pinv, const u64* pinv_s,
@@ -119,6 +138,13 @@ void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const
 // babies [n1][2][cap_b][N]; diags [ell][2][nl][N] (evaluation form, Montgomery); out [n2][3][cap_o][N].
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
                    const DevPrime* primes, int N, cudaStream_t s);
+// The diagonal MAC of B = 1..4 queries against one database with the diagonals streamed
+// through a shared-memory ring of asynchronous copies, every diagonal word read once for all B
+// queries (the sums of launch_mac: babies of query b at babies + b baby_q, [n1][2][cap_b][N];
+// outputs at out + b out_q, [n2][2][cap_o][N]); usable when mac_pipe_fits.
+bool mac_pipe_fits(int n1, int ell, int N);
+void launch_mac_pipe(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                     int cap_o, int nl, int n1, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
                 int cap_o, int nl, int n1, int n2, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 // Table schedule (Algorithm 1): out_g = sum_{m < ell} table[m] (.) D_{g,m} for g < G (evaluation form,

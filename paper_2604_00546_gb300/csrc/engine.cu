@@ -129,6 +129,8 @@ struct fr_ctx {
     uint32_t db_tier = 0;                // 0 auto, 1 stored diagonals, 2 encoded per query, 3 stored coefficients
     int sum_radix = 2;                   // RotateAndSum radix (2: one rotation per step)
     bool hoist_giants = false;           // giant steps of a group share one ModDown
+    bool hoist_babies = false;           // baby steps stay in Q_l u P; one ModDown per giant step
+    std::map<int, DevPrime*> d_primes_ext;  // per level: the primes of the positions of Q_l u P
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::set<fr_db*> dbs;                // databases loaded and not yet freed
     std::recursive_mutex mu;             // serialises device work of API calls and the serving loop
@@ -168,6 +170,7 @@ struct fr_db {
                              // 3 (B): rounded integer coefficients stored, residues + NTT per query;
                              // 4 (E): encrypted pre-rotated diagonals (ciphertexts, evaluation form)
     int schedule = 0;        // 0: on-demand BSGS (diagonals pre-rotated by j n1); 1: rotated-query table (plain diagonals)
+    int nl = 0;              // limbs per plaintext diagonal: level + 1, or level + 1 + n_p over Q_l u P (hoist_babies)
     u64* diags = nullptr;    // tier 1: [G][ell][level+1][N]; tier 4: [G][ell][2][level+1][N] (Montgomery form)
     float* templates = nullptr;  // tier 2: [K][ell] FP32
     long long* coeffs = nullptr; // tier 3: [G][ell][N] integer coefficients of the diagonals
@@ -598,6 +601,106 @@ void mul_relin(fr_ctx* c, int level, const std::vector<const u64*>& A, int a_cap
     }
 }
 
+// One ModDown of nj accumulators acc [nj][2][npos][N] (evaluation form over Q_l u P; their P
+// limbs are transformed in place), each plus the addend (d0, d1) of d [nj][3][l+1][N] when d is
+// not null, then the rescale by q_l: out_j at level l - 1 (job j at out + j out_bs, cap out_cap),
+// then the rescale's epilogue modes. The ModDown's conversion and the rescale's lift share one
+// forward NTT; the bits equal ModDown, addition and rescale one after the other.
+void moddown_rescale(fr_ctx* c, int l, u64* acc, const u64* d, int nj, u64* out, int out_cap, long long out_bs,
+                     const RescaleEpi& ep) {
+    const int N = c->R.N, np = c->R.np, nq = c->R.nq;
+    const int npos = l + 1 + np;
+    const size_t aw = (size_t)2 * npos * N;
+    PrimeMap pmP{};
+    pmP.period = np;
+    for (int j = 0; j < np; ++j) pmP.idx[j] = (unsigned char)(nq + j);
+    PrimeMap pmL{};
+    pmL.period = 1;
+    pmL.idx[0] = (unsigned char)l;
+    // P limbs to coefficients, P -> Q conversion
+    ntt(c, acc + (size_t)(l + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, true);
+    Tmp conv(c, (size_t)nj * 2 * (l + 1) * N);
+    {
+        Prof p(c, "moddown", 8.0 * N * nj * 2.0 * (np + l + 1));
+        launch_p2q(acc, (long long)aw, npos, l, conv.p, c->d_p2q, N, nj, c->cur);
+        c->launches++;
+    }
+    // the last limb of the result before the rescale, to coefficients; the lift; one forward
+    // NTT with the combine as its epilogue
+    Tmp z(c, (size_t)nj * 2 * N);
+    {
+        Prof p(c, "rescale", 8.0 * N * nj * 2.0 * (d ? 3.0 : 2.0));
+        launch_rs_last(acc, d, z.p, c->d_pinv, c->d_pinv_s, npos, l, c->d_primes, N, nj, c->cur);
+        c->launches++;
+    }
+    ntt(c, z.p, N, 1, 2 * nj, pmL, true);
+    Tmp y(c, (size_t)nj * 2 * l * N);
+    {
+        Prof p(c, "rescale", 8.0 * N * nj * 2.0 * (2.0 + 2.0 * l));
+        launch_rs_lift(z.p, conv.p, y.p, c->d_pinv, c->d_pinv_s, c->d_rescale[l], c->d_primes, l, N, nj, c->cur);
+        c->launches++;
+    }
+    Prof p(c, "ntt", 16.0 * nj * 2 * l * N);
+    PolyBatch pb{y.p, (long long)l * N, l, nj * 2 * l, pm_level(l - 1)};
+    launch_ntt_relin_rescale(c->rd, pb, acc, d, npos, l, c->d_pinv, c->d_pinv_s, c->d_rescale[l], out, out_cap, out_bs,
+                             ep.mode, ep.add, ep.add_cap, ep.add_bs, ep.cres, c->cur);
+    c->launches += 2;
+}
+
+// Products of ciphertext pairs at level l, relinearised and rescaled, with the relinearisation's
+// ModDown and the rescale sharing one forward NTT: out_j = Rescale(Relin(A_j (x) B_j)) at level
+// l - 1, job j at out + j out_bs (cap out_cap), then the epilogue modes of the rescale. Bit-identical
+// to mul_relin followed by rescale (every step is exact modular arithmetic and the NTT is
+// linear), with 2(l + 1) fewer limb transforms per product.
+void mul_relin_rescale(fr_ctx* c, int l, const std::vector<const u64*>& A, int a_cap, const std::vector<const u64*>& Bv,
+                       int b_cap, u64* out, int out_cap, long long out_bs, const RescaleEpi& ep = RescaleEpi()) {
+    if (l < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
+    if (l > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
+    const int N = c->R.N, np = c->R.np;
+    const int npos = l + 1 + np;
+    const size_t J = A.size();
+    const size_t dw = (size_t)3 * (l + 1) * N, aw = (size_t)2 * npos * N;
+    const size_t chunk = 16;
+    for (size_t j0 = 0; j0 < J; j0 += chunk) {
+        const int nj = (int)std::min(chunk, J - j0);
+        Tmp d(c, nj * dw);
+        TensorJobs tj;
+        for (int j = 0; j < nj; ++j) tj.j[j] = TensorJob{A[j0 + j], Bv[j0 + j], d.p + j * dw, a_cap, b_cap};
+        {
+            Prof p(c, "tensor", 8.0 * N * nj * 7.0 * (l + 1));
+            launch_tensor(tj, nj, l, c->d_primes, N, c->cur);
+            c->launches++;
+        }
+        // ModUp of every d2 and the inner products with the relinearisation key -> acc [nj][2][npos][N]
+        Tmp acc(c, (size_t)nj * aw);
+        std::vector<KSReq> reqs;
+        for (int j = 0; j < nj; ++j)
+            reqs.push_back(KSReq{d.p + j * dw + (size_t)2 * (l + 1) * N, relin_key(c), 1u, 2, d.p + j * dw, l + 1,
+                                 nullptr, 0});
+        int done = 0;
+        modup_chunks(c, l, reqs, [&](const std::vector<const KSReq*>& rq, const std::vector<const u64*>& ex) {
+            IPJobs ij;
+            ij.ngroups = 1;
+            ij.gkey[0] = rq[0]->key;
+            ij.gstart[0] = 0;
+            ij.gstart[1] = (int)rq.size();
+            for (size_t t = 0; t < rq.size(); ++t) {
+                const int j = (int)(rq[t]->c - (d.p + 2 * (size_t)(l + 1) * N)) / (int)dw;  // job of this request
+                ij.j[t] = IPJob{ex[t], rq[t]->key, acc.p + (size_t)j * aw, 1u, 0};
+            }
+            Prof p(c, "ip", 8.0 * N * npos * (2.0 * c->R.digits_at(l) + (double)rq.size() * (c->R.digits_at(l) + 2.0)));
+            launch_ip(ij, c->R.digits_at(l), npos, l, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, l),
+                      c->R.logN, c->cur);
+            c->launches++;
+            done += (int)rq.size();
+        });
+        if (done != nj) raise(FR_ERR_INTERNAL, "relinearisation jobs lost");
+        RescaleEpi ej = ep;
+        if (ej.add) ej.add += (size_t)j0 * ej.add_bs;
+        moddown_rescale(c, l, acc.p, d.p, nj, out + (size_t)j0 * out_bs, out_cap, out_bs, ej);
+    }
+}
+
 void add_cts(fr_ctx* c, const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap, long long b_bs, u64* out,
              int o_cap, long long o_bs, int level, int B) {
     Prof p(c, "misc", 8.0 * c->R.N * B * 6.0 * (level + 1));
@@ -697,20 +800,14 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     int prev_cap = x_cap;
     for (int m = 1; m < d2; ++m) {
         const int lv = ls - (m - 1);
-        Tmp sq(c, (size_t)B * ctw(c, lv + 1));
         std::vector<const u64*> A;
-        std::vector<u64*> O;
-        for (int b = 0; b < B; ++b) {
-            A.push_back(prev + (size_t)b * ctw(c, prev_cap));
-            O.push_back(sq.p + (size_t)b * ctw(c, lv + 1));
-        }
-        mul_relin(c, lv, A, prev_cap, A, prev_cap, O, lv + 1);
+        for (int b = 0; b < B; ++b) A.push_back(prev + (size_t)b * ctw(c, prev_cap));
         pw[m].reset(new Tmp(c, (size_t)B * ctw(c, lv)));
         pw_cap[m] = lv;
         RescaleEpi dsub;  // T_2k = 2 T_k^2 - 1: doubling and the constant in the rescale's epilogue
         dsub.mode = 2;
         dsub.cres = c->d_delta;
-        rescale(c, sq.p, B, lv, lv + 1, pw[m]->p, lv, dsub);
+        mul_relin_rescale(c, lv, A, prev_cap, A, prev_cap, pw[m]->p, lv, ctw(c, lv), dsub);
         CU(cudaEventRecord(c->evs[m], main));
         prev = pw[m]->p;
         prev_cap = lv;
@@ -737,23 +834,19 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
         CU(cudaStreamWaitEvent(side, c->evs[s], 0));
         const int P = nleaves >> s;
         const int lc = ls - s;
-        Tmp prod(c, (size_t)B * P * ctw(c, lc + 1));
         std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
         for (int b = 0; b < B; ++b)
             for (int i = 0; i < P; ++i) {
                 A.push_back(v->p + ((size_t)b * 2 * P + 2 * i) * ctw(c, vcap));
                 Bv.push_back(pw[s]->p + (size_t)b * ctw(c, pw_cap[s]));
-                O.push_back(prod.p + ((size_t)b * P + i) * ctw(c, lc + 1));
             }
-        mul_relin(c, lc, A, vcap, Bv, pw_cap[s], O, lc + 1);
         std::unique_ptr<Tmp> w(new Tmp(c, (size_t)B * P * ctw(c, lc)));
         RescaleEpi addc;  // + child(2i+1), the odd children, in the rescale's epilogue
         addc.mode = 1;
         addc.add = v->p + ctw(c, vcap);
         addc.add_cap = vcap;
         addc.add_bs = 2 * ctw(c, vcap);
-        rescale(c, prod.p, B * P, lc, lc + 1, w->p, lc, addc);
+        mul_relin_rescale(c, lc, A, vcap, Bv, pw_cap[s], w->p, lc, ctw(c, lc), addc);
         v = std::move(w);
         vcap = lc;
     }
@@ -771,7 +864,8 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
 //   y2 = y y, y4 = y2 y2, y8 = y4 y4; u_k = Rescale(y round(a_k Delta)) (u_1 with the constant
 //   round(Delta / 2) Delta); t3 = u3 y2, v7 = u7 y2, t5 = u5 y4, t7 = v7 y4, t9 = u9 y8 (every
 //   product relinearised and rescaled); out = t9 + t7 + t5 + t3 + u1 at level l - 4.
-// Products of one level share one key-switch batch: 1, 3, 3 and 1 products per ct.
+// Products of one level share one key-switch batch (1, 3, 3 and 1 products per ct), each
+// relinearised and rescaled through one shared forward NTT (mul_relin_rescale).
 void comparator_f4(fr_ctx* c, const u64* y, int B, int l, int y_cap, u64* out, int out_cap) {
     if (l < 4) raise(FR_ERR_LEVEL, "not enough levels for the hybrid comparator");
     const int cap = l + 1;  // every intermediate is stored with l + 1 limb slots
@@ -781,15 +875,9 @@ void comparator_f4(fr_ctx* c, const u64* y, int B, int l, int y_cap, u64* out, i
     // level l: y2 = y^2, and the five scaled copies u_k
     Tmp Y2(c, (size_t)B * cw);
     {
-        Tmp sq(c, (size_t)B * cw);
         std::vector<const u64*> A;
-        std::vector<u64*> O;
-        for (int b = 0; b < B; ++b) {
-            A.push_back(y + (size_t)b * ctw(c, y_cap));
-            O.push_back(sq.p + (size_t)b * cw);
-        }
-        mul_relin(c, l, A, y_cap, A, y_cap, O, cap);
-        rescale(c, sq.p, B, l, cap, Y2.p, cap);
+        for (int b = 0; b < B; ++b) A.push_back(y + (size_t)b * ctw(c, y_cap));
+        mul_relin_rescale(c, l, A, y_cap, A, y_cap, Y2.p, cap, (long long)cw);
     }
     Tmp U(c, (size_t)B * 5 * cw);  // [B][5]: y, y^3, y^5, y^7, y^9 scalars (u1 with the constant 1/2)
     {
@@ -806,54 +894,42 @@ void comparator_f4(fr_ctx* c, const u64* y, int B, int l, int y_cap, u64* out, i
     // level l - 1: y4 = y2 y2, t3 = u3 y2, v7 = u7 y2 -> R1 [B][3] at level l - 2
     Tmp R1(c, (size_t)B * 3 * cw);
     {
-        Tmp pr(c, (size_t)B * 3 * cw);
         std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
         for (int b = 0; b < B; ++b) {
             const u64* y2 = Y2.p + (size_t)b * cw;
             const u64* a3[3] = {y2, u(b, 1), u(b, 3)};
             for (int t = 0; t < 3; ++t) {
                 A.push_back(a3[t]);
                 Bv.push_back(y2);
-                O.push_back(pr.p + ((size_t)b * 3 + t) * cw);
             }
         }
-        mul_relin(c, l - 1, A, cap, Bv, cap, O, cap);
-        rescale(c, pr.p, B * 3, l - 1, cap, R1.p, cap);
+        mul_relin_rescale(c, l - 1, A, cap, Bv, cap, R1.p, cap, (long long)cw);
     }
     auto r1 = [&](int b, int t) { return R1.p + ((size_t)b * 3 + t) * cw; };  // y4, t3, v7
     // level l - 2: y8 = y4 y4, t5 = u5 y4, t7 = v7 y4 -> R2 [B][3] at level l - 3
     Tmp R2(c, (size_t)B * 3 * cw);
     {
-        Tmp pr(c, (size_t)B * 3 * cw);
         std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
         for (int b = 0; b < B; ++b) {
             const u64* y4 = r1(b, 0);
             const u64* a3[3] = {y4, u(b, 2), r1(b, 2)};
             for (int t = 0; t < 3; ++t) {
                 A.push_back(a3[t]);
                 Bv.push_back(y4);
-                O.push_back(pr.p + ((size_t)b * 3 + t) * cw);
             }
         }
-        mul_relin(c, l - 2, A, cap, Bv, cap, O, cap);
-        rescale(c, pr.p, B * 3, l - 2, cap, R2.p, cap);
+        mul_relin_rescale(c, l - 2, A, cap, Bv, cap, R2.p, cap, (long long)cw);
     }
     auto r2 = [&](int b, int t) { return R2.p + ((size_t)b * 3 + t) * cw; };  // y8, t5, t7
     // level l - 3: t9 = u9 y8 -> level l - 4
     Tmp R3(c, (size_t)B * cw);
     {
-        Tmp pr(c, (size_t)B * cw);
         std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
         for (int b = 0; b < B; ++b) {
             A.push_back(u(b, 4));
             Bv.push_back(r2(b, 0));
-            O.push_back(pr.p + (size_t)b * cw);
         }
-        mul_relin(c, l - 3, A, cap, Bv, cap, O, cap);
-        rescale(c, pr.p, B, l - 3, cap, R3.p, cap);
+        mul_relin_rescale(c, l - 3, A, cap, Bv, cap, R3.p, cap, (long long)cw);
     }
     // out = t9 + t7 + t5 + t3 + u1 on limbs 0..l-4
     const int lo = l - 4;
@@ -894,20 +970,44 @@ int choose_schedule(const fr_ctx* c, long long G) {
 // Eq. eq:prerotation), ell (no shift) for the table schedule.
 int db_n1_enc(const fr_ctx* c, const fr_db* db) { return db->schedule == 1 ? (int)c->ell : (int)c->n1; }
 
-// Encode the diagonals of template group g at the working level into dst
-// [ell][level+1][N] (evaluation + Montgomery form), diagonal d pre-rotated by
-// (d / n1_enc) n1_enc slots (n1_enc = ell: plain diagonals).
-void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst, int n1_enc) {
-    const int N = c->R.N, n = N / 2, nl = c->work_level + 1, ell = (int)c->ell;
+// The primes of the positions of Q_l u P in order (Q limbs 0..l, then the P limbs), on the
+// device; made once per level, outside stream capture (fr_setup, fr_load_db).
+const DevPrime* primes_ext(fr_ctx* c, int level) {
+    auto it = c->d_primes_ext.find(level);
+    if (it != c->d_primes_ext.end()) return it->second;
+    const PrimeMap m = pm_ext(c, level);
+    DevPrime* d = nullptr;
+    CU(cudaMalloc(&d, sizeof(DevPrime) * m.period));
+    c->owned.push_back(d);
+    for (int pos = 0; pos < m.period; ++pos)
+        CU(cudaMemcpy(d + pos, c->d_primes + m.idx[pos], sizeof(DevPrime), cudaMemcpyDeviceToDevice));
+    c->d_primes_ext[level] = d;
+    return d;
+}
+
+// Limbs of a plaintext diagonal at the working level: level + 1, or every limb of Q_l u P when
+// the baby steps stay in the extended basis (on-demand schedule).
+int diag_limbs(const fr_ctx* c, int schedule) {
+    return c->work_level + 1 + (c->hoist_babies && schedule == 0 ? c->R.np : 0);
+}
+
+// Encode the diagonals of template group g at the working level into dst [ell][nl][N]
+// (evaluation + Montgomery form; nl = level + 1, or the positions of Q_l u P when
+// nl > level + 1), diagonal d pre-rotated by (d / n1_enc) n1_enc slots (n1_enc = ell: plain
+// diagonals).
+void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst, int n1_enc, int nl) {
+    const int N = c->R.N, n = N / 2, L = c->work_level, ell = (int)c->ell;
     const int chunk = 64;
     Tmp z(c, (size_t)chunk * n * 2);
-    const PrimeMap pm = pm_level(nl - 1);
+    const bool ext = nl > L + 1;
+    const PrimeMap pm = ext ? pm_ext(c, L) : pm_level(L);
+    const DevPrime* primes = ext ? primes_ext(c, L) : c->d_primes;
     for (int d0 = 0; d0 < ell; d0 += chunk) {
         const int nd = std::min(chunk, ell - d0);
         u64* o = dst + (size_t)d0 * nl * N;
         {
             Prof p(c, "encode", 8.0 * N * nd * nl);
-            launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, n1_enc, z.p, o, nl, c->d_primes,
+            launch_encode_diags(dT, K, ell, c->R.logN - 1, g, d0, nd, n1_enc, z.p, o, nl, primes,
                                 c->R.scale_bits, c->d_rot, c->d_zr, c->d_zi, c->cur);
             c->launches += 4;
         }
@@ -1005,17 +1105,19 @@ void encode_group_int(fr_ctx* c, const float* dT, long long K, long long g, long
 }
 
 // Storage tier B, per query: residues of the stored coefficients at the working level, then
-// the forward NTT with the Montgomery conversion: dst [ell][level+1][N] as encode_group writes.
-void expand_group(fr_ctx* c, const long long* src, u64* dst) {
-    const int N = c->R.N, nl = c->work_level + 1, ell = (int)c->ell;
+// the forward NTT with the Montgomery conversion: dst [ell][nl][N] as encode_group writes.
+void expand_group(fr_ctx* c, const long long* src, u64* dst, int nl) {
+    const int N = c->R.N, L = c->work_level, ell = (int)c->ell;
     const int chunk = 64;
-    const PrimeMap pm = pm_level(nl - 1);
+    const bool ext = nl > L + 1;
+    const PrimeMap pm = ext ? pm_ext(c, L) : pm_level(L);
+    const DevPrime* primes = ext ? primes_ext(c, L) : c->d_primes;
     for (int d0 = 0; d0 < ell; d0 += chunk) {
         const int nd = std::min(chunk, ell - d0);
         u64* o = dst + (size_t)d0 * nl * N;
         {
             Prof p(c, "encode", 8.0 * N * nd * (1.0 + nl));
-            launch_coef_residues(src + (size_t)d0 * N, nd, o, nl, c->d_primes, N, c->cur);
+            launch_coef_residues(src + (size_t)d0 * N, nd, o, nl, primes, N, c->cur);
             c->launches++;
         }
         Prof p(c, "ntt", 16.0 * nd * nl * N);
@@ -1289,6 +1391,8 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         c->sum_radix = prm->sum_radix ? (int)prm->sum_radix : 2;
         if (prm->hoist_giants > 1) raise(FR_ERR_INVALID_ARG, "hoist_giants must be 0 or 1");
         c->hoist_giants = prm->hoist_giants == 1;
+        if (prm->hoist_babies > 1) raise(FR_ERR_INVALID_ARG, "hoist_babies must be 0 or 1");
+        c->hoist_babies = prm->hoist_babies == 1;
         if (c->sum_radix < 2 || c->sum_radix > 64 || (c->sum_radix & (c->sum_radix - 1)))
             raise(FR_ERR_INVALID_ARG, "sum_radix must be 0 or a power of two in [2, 64]");
         c->work_level = c->R.nq - 1;
@@ -1320,6 +1424,7 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         uint64_t thr = ~0ull;
         CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         build_tables(c.get());
+        if (c->hoist_babies) primes_ext(c.get(), c->work_level);  // before any capture uses it
         CU(cudaStreamSynchronize(c->cur));
         // NTT tile shapes per batch-size bucket, timed on this GPU (FR_NTT_TUNE=0: defaults)
         const char* tune = std::getenv("FR_NTT_TUNE");
@@ -1469,13 +1574,15 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
         if (!c || !templates || !out || K == 0) raise(FR_ERR_INVALID_ARG, "null argument or empty database");
         if (ell != c->ell) raise(FR_ERR_INVALID_ARG, "template dimension differs from the context's ell");
         CU(cudaSetDevice(c->device));
-        const int N = c->R.N, n = N / 2, nl = c->work_level + 1;
+        const int N = c->R.N, n = N / 2;
         std::unique_ptr<fr_db> db(new fr_db());
         db->ctx = c;
         db->K = (long long)K;
         db->ell = (int)ell;
         db->G = ((long long)K + n - 1) / n;
         db->schedule = choose_schedule(c, db->G);
+        const int nl = diag_limbs(c, db->schedule);
+        db->nl = nl;
         const size_t tbytes = K * ell * sizeof(float);
         const size_t dbytes = (size_t)db->G * ell * nl * N * 8;
         // storage tier: the stored diagonals when they fit (budget, or free HBM minus a working
@@ -1509,7 +1616,8 @@ fr_status fr_load_db(fr_ctx* c, const float* templates, size_t K, size_t ell, fr
             for (long long g = 0; g < db->G; ++g) {
                 if (tier == 1) {
                     db->diags = (u64*)p;
-                    encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N, db_n1_enc(c, db.get()));
+                    encode_group(c, dT, (long long)K, g, db->diags + (size_t)g * ell * nl * N, db_n1_enc(c, db.get()),
+                                 nl);
                 } else {
                     db->coeffs = (long long*)p;
                     encode_group_int(c, dT, (long long)K, g, db->coeffs + (size_t)g * ell * N, db_n1_enc(c, db.get()));
@@ -1992,20 +2100,77 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
     const int L1 = L + 1;
     const int B = (int)qs.size();
     const size_t cw1 = (size_t)ctw(c, L1), cw = (size_t)ctw(c, L);
+    // baby steps in Q_l u P (double hoisting): babies and diagonals span every position of Q_l u P
+    const bool pq = c->hoist_babies;
+    const int npos = L1 + c->R.np;
+    const int nlx = pq ? npos : L1;                       // limbs of a baby ct and of a diagonal
+    const size_t bw = (size_t)2 * nlx * N;                // words of one baby
+    const DevPrime* mprimes = pq ? primes_ext(c, L) : c->d_primes;
+    if (pq)
+        for (int b = 0; b < B; ++b)
+            if (P.dbs[qs[b]]->tier == 4)
+                raise(FR_ERR_UNSUPPORTED, "encrypted databases need hoist_babies = 0");
     // S2: baby steps B_{b,i} = Rot_i(q_b), hoisted per query
     std::unique_ptr<Prof> stage(new Prof(c, "stage:babies"));
-    Tmp babies(c, (size_t)B * n1 * cw1);  // [B][n1][2][L1][N]
-    for (int b = 0; b < B; ++b) copy_d2d(c, babies.p + (size_t)b * n1 * cw1, q + (size_t)qs[b] * cw1, cw1);
-    if (n1 > 1) {
-        std::vector<KSReq> reqs;
-        for (int b = 0; b < B; ++b) {
-            u64* q0 = babies.p + (size_t)b * n1 * cw1;
-            for (int i = 1; i < n1; ++i) {
-                const u64 g = frh::galois_of_rotation(c->R, i);
-                reqs.push_back(KSReq{q0 + (size_t)L1 * N, rot_key(c, g), (u32)g, 1, q0, L1, q0 + (size_t)i * cw1, L1});
+    Tmp babies(c, (size_t)B * n1 * bw);  // [B][n1][2][nlx][N]
+    if (!pq) {
+        for (int b = 0; b < B; ++b) copy_d2d(c, babies.p + (size_t)b * n1 * cw1, q + (size_t)qs[b] * cw1, cw1);
+        if (n1 > 1) {
+            std::vector<KSReq> reqs;
+            for (int b = 0; b < B; ++b) {
+                u64* q0 = babies.p + (size_t)b * n1 * cw1;
+                for (int i = 1; i < n1; ++i) {
+                    const u64 g = frh::galois_of_rotation(c->R, i);
+                    reqs.push_back(KSReq{q0 + (size_t)L1 * N, rot_key(c, g), (u32)g, 1, q0, L1, q0 + (size_t)i * cw1, L1});
+                }
             }
+            keyswitch(c, L, reqs);
         }
-        keyswitch(c, L, reqs);
+    } else {
+        // one ModUp per query; the inner products of babies 1..n1-1 land in the babies buffer;
+        // then P sigma_i(q.b) on their Q positions and baby 0 = P q
+        if (n1 > 1) {
+            std::vector<KSReq> reqs;
+            for (int b = 0; b < B; ++b) {
+                const u64* qb = q + (size_t)qs[b] * cw1;
+                for (int i = 1; i < n1; ++i) {
+                    const u64 g = frh::galois_of_rotation(c->R, i);
+                    reqs.push_back(KSReq{qb + (size_t)L1 * N, rot_key(c, g), (u32)g, 1, qb, L1,
+                                         babies.p + ((size_t)b * n1 + i) * bw, npos});
+                }
+            }
+            const int beta = c->R.digits_at(L);
+            modup_chunks(c, L, reqs, [&](const std::vector<const KSReq*>& rq, const std::vector<const u64*>& ex) {
+                IPJobs ij;
+                ij.ngroups = 0;
+                const int nj = (int)rq.size();
+                for (int j = 0; j < nj; ++j) {
+                    ij.j[j] = IPJob{ex[j], rq[j]->key, rq[j]->out, rq[j]->galois, 0, rq[j]->add};  // + P sigma(b)
+                    if (j == 0 || rq[j]->key != rq[j - 1]->key) {
+                        ij.gkey[ij.ngroups] = rq[j]->key;
+                        ij.gstart[ij.ngroups] = j;
+                        ij.ngroups++;
+                    }
+                }
+                ij.gstart[ij.ngroups] = nj;
+                Prof p(c, "ip", 8.0 * N * npos * (ij.ngroups * 2.0 * beta + nj * (double)beta + nj * 2.0) +
+                                    8.0 * N * nj * L1);
+                launch_ip(ij, beta, npos, L, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, L), c->R.logN,
+                          c->cur, c->d_pmod, c->d_pmod_s);
+                c->launches++;
+            });
+        }
+        // baby 0 = P q; queries are gathered in qs order and their inputs sit at q + qs[b] cw1:
+        // one launch per run of consecutive indices
+        for (int b0 = 0; b0 < B;) {
+            int b1 = b0 + 1;
+            while (b1 < B && qs[b1] == qs[b1 - 1] + 1) ++b1;
+            Prof p(c, "misc", 8.0 * N * (b1 - b0) * 2.0 * (npos + L1));
+            launch_baby0_pq(babies.p + (size_t)b0 * n1 * bw, (long long)n1 * bw, q + (size_t)qs[b0] * cw1, (long long)cw1,
+                            L1, b1 - b0, npos, L, mprimes, c->d_pmod, c->d_pmod_s, N, c->cur);
+            c->launches++;
+            b0 = b1;
+        }
     }
     // S3-S5 group by group: (tiers B, C: encode the group's diagonals), MAC, rescale, giant
     // rotations, sum; at most 8 databases encoded per query in flight
@@ -2029,23 +2194,21 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             std::unique_ptr<Tmp> dg;
             if (!enc.empty()) {
                 stage.reset(new Prof(c, "stage:encode"));
-                dg.reset(new Tmp(c, enc.size() * (size_t)ell * L1 * N));
+                dg.reset(new Tmp(c, enc.size() * (size_t)ell * nlx * N));
                 for (size_t e = 0; e < enc.size(); ++e) {
-                    u64* dst = dg->p + e * (size_t)ell * L1 * N;
-                    if (enc[e]->tier == 2) encode_group(c, enc[e]->templates, enc[e]->K, g, dst, (int)c->n1);
-                    else expand_group(c, enc[e]->coeffs + (size_t)g * ell * N, dst);
+                    u64* dst = dg->p + e * (size_t)ell * nlx * N;
+                    if (enc[e]->tier == 2) encode_group(c, enc[e]->templates, enc[e]->K, g, dst, (int)c->n1, nlx);
+                    else expand_group(c, enc[e]->coeffs + (size_t)g * ell * N, dst, nlx);
                 }
             }
             auto diag_of = [&](const fr_db* d) -> const u64* {
-                if (d->tier == 1) return d->diags + (size_t)g * ell * L1 * N;
+                if (d->tier == 1) return d->diags + (size_t)g * ell * d->nl * N;
                 if (d->tier == 4) return d->diags + (size_t)g * ell * 2 * L1 * N;
                 const size_t e = std::find(enc.begin(), enc.end(), d) - enc.begin();
-                return dg->p + e * (size_t)ell * L1 * N;
+                return dg->p + e * (size_t)ell * nlx * N;
             };
             stage.reset(new Prof(c, "stage:mac"));
-            Tmp Pj(c, (size_t)nb * n2 * cw1);  // [nb][n2][2][L1][N]
-            // one query per launch: the products dominate the diagonal reads, and a launch over
-            // 2-4 queries measured slower per query (1.73 ms for 2 vs 0.75 ms for 1 at level 8)
+            Tmp Pj(c, (size_t)nb * n2 * bw);  // [nb][n2][2][nlx][N]
             int nenc = 0;  // queries of the chunk against encrypted databases
             for (int t = 0; t < nb; ++t) nenc += P.dbs[qs[sel[s0 + t]]]->tier == 4;
             std::unique_ptr<Tmp> D3;  // their unrelinearised products, [nenc][n2][3][L1][N]
@@ -2054,6 +2217,23 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             for (int t = 0, e = 0; t < nb; ++t) {
                 const int b = sel[s0 + t];
                 const fr_db* d = P.dbs[qs[b]];
+                // up to 4 queries against the same diagonals (consecutive babies) share one ring
+                // launch that reads each diagonal word once for all of them; a single query runs
+                // k_mac below (its register pipeline measured faster for one query)
+                int cnt = 1;
+                if (d->tier != 4 && mac_pipe_fits(n1, ell, N))
+                    while (cnt < 4 && t + cnt < nb && sel[s0 + t + cnt] == b + cnt &&
+                           diag_of(P.dbs[qs[b + cnt]]) == diag_of(d))
+                        ++cnt;
+                if (cnt > 1) {
+                    Prof p(c, "mac", 8.0 * N * nlx * ((double)ell + cnt * (2.0 * n1 + 2.0 * n2)));
+                    launch_mac_pipe(babies.p + (size_t)b * n1 * bw, (long long)n1 * bw, nlx, diag_of(d),
+                                    Pj.p + (size_t)t * n2 * bw, (long long)n2 * bw, nlx, nlx, n1, ell, cnt, mprimes, N,
+                                    c->cur);
+                    c->launches++;
+                    t += cnt - 1;
+                    continue;
+                }
                 if (d->tier == 4) {
                     // ct x ct products summed per giant step; one relinearisation each (below)
                     u64* o = D3->p + (size_t)e++ * n2 * 3 * L1 * N;
@@ -2068,10 +2248,9 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
                     }
                     continue;
                 }
-                Prof p(c, "mac", 8.0 * N * L1 * ((double)ell + 2.0 * n1 + 2.0 * n2));
-                launch_mac(babies.p + (size_t)b * n1 * cw1, (long long)n1 * cw1, L1, diag_of(d),
-                           Pj.p + (size_t)t * n2 * cw1, (long long)n2 * cw1, L1, L1, n1, n2, ell, 1, c->d_primes, N,
-                           c->cur);
+                Prof p(c, "mac", 8.0 * N * nlx * ((double)ell + 2.0 * n1 + 2.0 * n2));
+                launch_mac(babies.p + (size_t)b * n1 * bw, (long long)n1 * bw, nlx, diag_of(d),
+                           Pj.p + (size_t)t * n2 * bw, (long long)n2 * bw, nlx, nlx, n1, n2, ell, 1, mprimes, N, c->cur);
                 c->launches++;
             }
             if (!relin.empty()) {
@@ -2079,7 +2258,10 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
                 keyswitch(c, L, relin);
             }
             Tmp Gs(c, (size_t)nb * n2 * cw);  // [nb][n2][2][L][N]
-            rescale(c, Pj.p, nb * n2, L, L1, Gs.p, L);
+            if (pq)
+                moddown_rescale(c, L, Pj.p, nullptr, nb * n2, Gs.p, L, (long long)cw, RescaleEpi());
+            else
+                rescale(c, Pj.p, nb * n2, L, L1, Gs.p, L);
             stage.reset(new Prof(c, "stage:giants"));
             if (n2 > 1 && c->hoist_giants) {
                 // S = P_0 + sum_j Rot_{j n1}(P_j) with one ModDown per (query, group)
@@ -2174,12 +2356,12 @@ void table_scores(fr_ctx* c, const fr_db* db, const u64* q, u64* S) {
         if (db->tier == 2) {
             stage.reset(new Prof(c, "stage:encode"));
             for (int t = 0; t < gc; ++t)
-                encode_group(c, db->templates, db->K, g0 + t, dg->p + (size_t)t * ell * L1 * N, ell);
+                encode_group(c, db->templates, db->K, g0 + t, dg->p + (size_t)t * ell * L1 * N, ell, L1);
             D = dg->p;
         } else if (db->tier == 3) {
             stage.reset(new Prof(c, "stage:encode"));
             for (int t = 0; t < gc; ++t)
-                expand_group(c, db->coeffs + (size_t)(g0 + t) * ell * N, dg->p + (size_t)t * ell * L1 * N);
+                expand_group(c, db->coeffs + (size_t)(g0 + t) * ell * N, dg->p + (size_t)t * ell * L1 * N, L1);
             D = dg->p;
         }
         stage.reset(new Prof(c, "stage:mac"));
@@ -2215,13 +2397,17 @@ void match_pipeline(fr_ctx* c, const std::vector<const fr_db*>& dbs, const u64* 
     }
     if (!od.empty()) ondemand_scores(c, P, q, od, S);
     std::unique_ptr<Prof> stage;
-    if (scores_only) return;
+    if (scores_only) {
+        CU(cudaGetLastError());  // a launch the device refused (configuration, resources) fails the match
+        return;
+    }
     // S6: threshold on every (query, group) score ciphertext (batched)
     const int lo = L - 1 - c->cmp_depth;
     const size_t cwo = (size_t)ctw(c, lo + 1);
     if (mode == FR_MODE_IDENTIFY) {
         stage.reset(new Prof(c, "stage:cheb"));
         threshold(c, S, (int)total, L - 1, L, out, lo + 1);
+        CU(cudaGetLastError());  // a launch the device refused (configuration, resources) fails the match
         return;
     }
     Tmp cbuf(c, (size_t)total * cwo);
@@ -2236,6 +2422,7 @@ void match_pipeline(fr_ctx* c, const std::vector<const fr_db*>& dbs, const u64* 
         c->launches++;
     }
     rotate_sum(c, out, lo + 1, lo, B);
+    CU(cudaGetLastError());  // a launch the device refused (configuration, resources) fails the match
 }
 
 // Number of output ciphertexts of a batch and the offset of each query's first output.
@@ -2499,12 +2686,13 @@ void match_workspace(const fr_ctx* c, const fr_db* db, fr_mode mode, uint64_t* b
     int nout, lo;
     match_shape(c, db, mode, &nout, &lo);
     double per = cw1 + nout * 2.0 * (lo + 1) * N + G * cw;
-    if (db->schedule != 1) per += (n1 + n2) * cw1 + 2.0 * n2 * cw;
+    const double bwq = db->schedule != 1 && c->hoist_babies ? 2.0 * npos * N : cw1;  // one baby / giant-step sum
+    if (db->schedule != 1) per += (n1 + n2) * bwq + 2.0 * n2 * cw;
     if (mode != FR_MODE_SCORES) per += G * 54.0 * cw;  // threshold: powers, leaves, tree temporaries
     double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N;  // key-switch scratch
     if (db->schedule == 1) b += ell * cw1 + G * cw1;
     if (db->tier == 4) per += 3.0 * n2 * L1 * N;  // unrelinearised products of the giant steps
-    if (db->tier != 1 && db->tier != 4) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * L1 * N;
+    if (db->tier != 1 && db->tier != 4) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * db->nl * N;
     *base = (uint64_t)(b * 8.0 * 1.25);
     *per_query = (uint64_t)(per * 8.0 * 1.25);
 }
@@ -2964,7 +3152,7 @@ fr_status fr_ntt_set_shapes(fr_ctx* c, const uint32_t* shapes) {
         std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
         if (!shapes) raise(FR_ERR_INVALID_ARG, "null argument");
         for (int b = 0; b < FR_NTT_BUCKETS; ++b)
-            if (shapes[b] >= FR_NTT_SHAPES) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..4");
+            if (shapes[b] >= FR_NTT_SHAPES) raise(FR_ERR_INVALID_ARG, "NTT tile shape must be 0..5");
         for (int b = 0; b < FR_NTT_BUCKETS; ++b) c->rd.ntt_shape[b] = (unsigned char)shapes[b];
         drop_graphs(c, nullptr);  // captured graphs hold the previous launch shapes
     });

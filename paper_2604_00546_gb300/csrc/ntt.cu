@@ -283,6 +283,42 @@ struct EpiRescale {
     }
 };
 
+// Relinearisation ModDown fused with the rescale after it (the product of two ciphertexts at
+// level l, relinearised, then divided by q_l): poly p = (job j, component t, limb i < l) of
+// y = conv P^-1 + lift, where conv is the ModDown's P -> Q conversion and lift the centered last
+// limb of the ModDown's output. out = (acc_i P^-1 + d_i - v) q_l^-1 with acc the job's key-switch
+// inner product [2][npos][N] and d its tensor product [3][l+1][N] (d0, d1 the addend; null: no
+// addend, a plain ModDown then rescale); then the modes of EpiRescale. Each step is exact modular arithmetic and the NTT is linear, so this equals
+// ModDown, the addition of (d0, d1) and the rescale one after the other, bit for bit.
+struct EpiRelinRescale {
+    const u64* acc;
+    const u64* d;
+    u64* out;          // job j at out + j out_bs, component t at + t out_cap N
+    const RescaleTab* tab;
+    const u64* pinv;
+    const u64* pinv_s;
+    int npos, l, N, out_cap, mode;
+    long long out_bs;
+    const u64* add;    // mode 1: job j's addend at add + j add_bs, component t at + t add_cap N
+    int add_cap;
+    long long add_bs;
+    const u64* cres;   // mode 2: [l] constants
+    __device__ __forceinline__ void put(int p, int k, u64 v, u64 q) const {
+        const int jt = p / l, i = p % l, j = jt >> 1, t = jt & 1;
+        const u64 a = acc[((long long)jt * npos + i) * N + k];
+        const u64 dd = d ? d[(((long long)j * 3 + t) * (l + 1) + i) * N + k] : 0;
+        const u64 m = add_mod(mul_shoup(a, pinv[i], pinv_s[i], q), dd, q);
+        u64 r = mul_shoup(sub_mod(m, v, q), tab->qlinv[i], tab->qlinv_s[i], q);
+        if (mode == 1) {
+            r = add_mod(r, add[(long long)j * add_bs + ((long long)t * add_cap + i) * N + k], q);
+        } else if (mode == 2) {
+            r = add_mod(r, r, q);
+            if (t == 0) r = sub_mod(r, cres[i], q);
+        }
+        out[(long long)j * out_bs + ((long long)t * out_cap + i) * N + k] = r;
+    }
+};
+
 // row pass: one CTA = RPC rows of S contiguous elements (RT threads), S/8 threads per row
 template <int LOG, int LOGR, bool INV, class E, int RT>
 __global__ void __launch_bounds__(RT, RT == 128 ? 9 : 4) k_ntt_row(const __grid_constant__ RingDev R, const __grid_constant__ PolyBatch b,
@@ -834,6 +870,14 @@ void launch_ntt_tomont(const RingDev& R, const PolyBatch& b, cudaStream_t s) {
 void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs, int npos, int level,
                         const u64* pinv, const u64* pinv_s, cudaStream_t s) {
     EpiModDown e{jobs, npos, level, R.logN, pinv, pinv_s};
+    launch_ntt_e(R, b, false, s, e);
+}
+
+void launch_ntt_relin_rescale(const RingDev& R, const PolyBatch& b, const u64* acc, const u64* d, int npos, int l,
+                              const u64* pinv, const u64* pinv_s, const RescaleTab* tab, u64* out, int out_cap,
+                              long long out_bs, int mode, const u64* add, int add_cap, long long add_bs,
+                              const u64* cres, cudaStream_t s) {
+    EpiRelinRescale e{acc, d, out, tab, pinv, pinv_s, npos, l, R.N, out_cap, mode, out_bs, add, add_cap, add_bs, cres};
     launch_ntt_e(R, b, false, s, e);
 }
 

@@ -55,7 +55,7 @@ class Params(C.Structure):
         ("n1", C.c_uint32), ("schedule", C.c_uint32), ("cheb_degree", C.c_uint32), ("threshold", C.c_double),
         ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("db_tier", C.c_uint32), ("level_mode", C.c_uint32), ("sum_radix", C.c_uint32),
-        ("hoist_giants", C.c_uint32), ("comparator", C.c_uint32),
+        ("hoist_giants", C.c_uint32), ("comparator", C.c_uint32), ("hoist_babies", C.c_uint32),
     ]
 
 
@@ -227,14 +227,14 @@ class Context:
 
     def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
                  hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0, db_tier=0, sum_radix=0,
-                 hoist_giants=0, comparator=0):
+                 hoist_giants=0, comparator=0, hoist_babies=0):
         L = load()
         self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
         self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
                              C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode, sum_radix,
-                             int(hoist_giants), int(comparator))
+                             int(hoist_giants), int(comparator), int(hoist_babies))
         h = C.c_void_p()
         self._live = 0          # library objects of this context still alive
         self._closing = False
