@@ -126,7 +126,7 @@ def _declare(L):
     L.or_diag_scores.argtypes = [vp, vp, u64p, f32p, C.c_long, C.c_int, u64p]
     L.or_match.restype = C.c_int
     L.or_match.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                           C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+                           C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_bsgs_scores_pq.restype = C.c_int
     L.or_bsgs_scores_pq.argtypes = [vp, vp, u64p, C.c_int, f32p, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int, u64p]
     L.or_bsgs_scores_hoisted.restype = C.c_int
@@ -142,9 +142,11 @@ def _declare(L):
                                      u64p]
     L.or_match_enc.restype = C.c_int
     L.or_match_enc.argtypes = [vp, vp, u64p, C.c_int, u64p, C.c_int, C.c_long, C.c_int, C.c_int, C.c_int, C.c_int,
-                               C.c_double, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
+                               C.c_double, C.c_int, C.c_int, C.c_int, u64p, C.POINTER(C.c_int)]
     L.or_rotate_sum_radix.restype = C.c_int
     L.or_rotate_sum_radix.argtypes = [vp, vp, u64p, C.c_int, C.c_int, C.c_int]
+    L.or_rotate_sum_hoisted.restype = C.c_int
+    L.or_rotate_sum_hoisted.argtypes = [vp, vp, u64p, C.c_int, C.c_int, C.c_int]
     L.or_set_threads.argtypes = [C.c_int]
     L.or_get_threads.restype = C.c_int
 
@@ -357,10 +359,14 @@ class Keys:
             raise ValueError("unsupported comparator / level")
         return out
 
-    def rotate_sum(self, ct, level, steps, radix=2):
-        """RotateAndSum over 2^steps slots, in radix `radix` (2: one rotation per step)."""
+    def rotate_sum(self, ct, level, steps, radix=2, hoist=False):
+        """RotateAndSum over 2^steps slots, in radix `radix` (2: one rotation per step); hoist: the
+        rotations of each step are summed before one ModDown."""
         x = np.ascontiguousarray(ct, dtype=np.uint64).copy()
-        if radix == 2:
+        if hoist:
+            if self.L.or_rotate_sum_hoisted(self.ctx.h, self.h, x, level, int(steps), int(radix)) < 0:
+                raise ValueError("radix must be a power of two")
+        elif radix == 2:
             self.L.or_rotate_sum(self.ctx.h, self.h, x, level, int(steps))
         elif self.L.or_rotate_sum_radix(self.ctx.h, self.h, x, level, int(steps), int(radix)) < 0:
             raise ValueError("radix must be a power of two")
@@ -448,11 +454,12 @@ class Keys:
         return out
 
     def match(self, qct, T, ell, n1, mode, cheb_n=59, tau=0.5, level=None, schedule=0, sum_radix=2, hoist=False,
-              comparator=0, babies_pq=False):
+              comparator=0, babies_pq=False, hoist_sum=False):
         """Full match of a top-level query ct, computed at working level `level` (default: top);
         schedule 0: on-demand BSGS with pre-rotated diagonals, 1: rotated-query table;
         comparator 0: the step interpolant (the paper's GPU path), 1: the hybrid comparator;
-        babies_pq: the baby steps stay in Q_l u P (one ModDown per giant step)."""
+        babies_pq: the baby steps stay in Q_l u P (one ModDown per giant step); hoist_sum: the
+        rotations of each RotateAndSum step share one ModDown."""
         c = self.ctx
         lq = c.top if level is None else int(level)
         T = np.ascontiguousarray(T, dtype=np.float32)
@@ -463,7 +470,7 @@ class Keys:
         lvl = C.c_int(0)
         r = self.L.or_match(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, T, K, ell, n1, mode,
                             int(cheb_n), float(tau), int(comparator), int(schedule), int(sum_radix),
-                            1 if hoist else 0, 1 if babies_pq else 0, out, C.byref(lvl))
+                            1 if hoist else 0, 1 if babies_pq else 0, 1 if hoist_sum else 0, out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value
@@ -505,7 +512,8 @@ class Keys:
             raise ValueError("bad arguments")
         return out
 
-    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None, sum_radix=2, hoist=False):
+    def match_enc(self, qct, E, K, n1, mode, cheb_n=59, tau=0.5, level=None, sum_radix=2, hoist=False,
+                  hoist_sum=False):
         """Full match of a top-level query ct against encrypted diagonals E, at working level
         `level` (default: top); returns (outputs, their level)."""
         c = self.ctx
@@ -516,8 +524,8 @@ class Keys:
         out = np.zeros(cnt * 2 * c.top * c.N, dtype=np.uint64)
         lvl = C.c_int(0)
         r = self.L.or_match_enc(c.h, self.h, np.ascontiguousarray(qct, dtype=np.uint64), lq, E, el, int(K), ell,
-                                n1, mode, int(cheb_n), float(tau), int(sum_radix), 1 if hoist else 0, out,
-                                C.byref(lvl))
+                                n1, mode, int(cheb_n), float(tau), int(sum_radix), 1 if hoist else 0,
+                                1 if hoist_sum else 0, out, C.byref(lvl))
         if r < 0:
             raise ValueError("match failed")
         level = lvl.value

@@ -1342,6 +1342,59 @@ int or_rotate_sum_radix(const or_ctx* c, const or_keys* k, u64* ct, int l, int s
     return 0;
 }
 
+/* RotateAndSum in radix r with the rotations of each step summed before one ModDown (double
+ * hoisting after Bossuat et al., Section "Hoisting and double hoisting", applied to the
+ * aggregation of Algorithm 5): with s = 1, r, r^2, ... below 2^steps and rr = min(r, 2^steps / s),
+ *   x <- x + (sum_t sigma_t(x.b) + ModDown(sum_t IP0_t), ModDown(sum_t IP1_t)),  t = 1 .. rr-1,
+ * IP0_t, IP1_t the inner products of the one ModUp of x.a under the automorphism sigma_t of
+ * Rot_{t s} with its key (Q_l u P, evaluation form). It differs from or_rotate_sum_radix only in
+ * the rounding of the ModDowns; with rr = 2 (r = 2) every step is one rotation and one addition,
+ * bit for bit the radix-2 form. */
+int or_rotate_sum_hoisted(const or_ctx* c, const or_keys* k, u64* ct, int l, int steps, int r) {
+    if (r < 2 || (r & (r - 1))) return -1;
+    int N = c->n, npos = l + 1 + c->np, beta = beta_at(c, l);
+    long n = 1L << steps;
+    size_t cw = ct_words(c, l), ew = (size_t)npos * N;
+    u64* x = (u64*)malloc(sizeof(u64) * cw);
+    u64* ext = (u64*)malloc(sizeof(u64) * (size_t)beta * ew);
+    u64* evk = (u64*)malloc(sizeof(u64) * evk_words(c));
+    u64* a0 = (u64*)malloc(sizeof(u64) * ew);
+    u64* a1 = (u64*)malloc(sizeof(u64) * ew);
+    u64* s0 = (u64*)malloc(sizeof(u64) * ew);
+    u64* s1 = (u64*)malloc(sizeof(u64) * ew);
+    u64* t = (u64*)malloc(sizeof(u64) * N);
+    u64* md = (u64*)malloc(sizeof(u64) * cw);
+    for (long s_ = 1; s_ < n; s_ *= r) {
+        long rr = n / s_ < r ? n / s_ : r;
+        memcpy(x, ct, sizeof(u64) * cw);
+        modup(c, x + (size_t)(l + 1) * N, l, ext);
+        memset(s0, 0, sizeof(u64) * ew);
+        memset(s1, 0, sizeof(u64) * ew);
+        for (long j = 1; j < rr; j++) {
+            u64 g = or_galois(c, j * s_);
+            or_make_evk(c, k, 0, g, evk);
+            keyswitch_ip(c, ext, l, evk, g, a0, a1);
+            for (int pos = 0; pos < npos; pos++) {
+                u64 q = c->p[ext_limb(c, l, pos)];
+                for (int i = 0; i < N; i++) {
+                    s0[(size_t)pos * N + i] = madd(s0[(size_t)pos * N + i], a0[(size_t)pos * N + i], q);
+                    s1[(size_t)pos * N + i] = madd(s1[(size_t)pos * N + i], a1[(size_t)pos * N + i], q);
+                }
+            }
+            for (int i = 0; i <= l; i++) {   /* sigma_t(x.b), coefficient form */
+                u64 q = c->p[i];
+                automorph_coef(c, g, q, x + (size_t)i * N, t);
+                for (int m = 0; m < N; m++) ct[(size_t)i * N + m] = madd(ct[(size_t)i * N + m], t[m], q);
+            }
+        }
+        moddown(c, s0, l, md);
+        moddown(c, s1, l, md + (size_t)(l + 1) * N);
+        or_add(c, ct, md, l, ct);
+    }
+    free(x); free(ext); free(evk); free(a0); free(a1); free(s0); free(s1); free(t); free(md);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* HyDia packing (Section "Diagonal method for rectangular matrices", Fig. 1) */
 /* and the pre-rotated diagonal of Eq. eq:prerotation.                       */
@@ -1756,7 +1809,7 @@ static int comparator_depth(int cheb_n, int comparator) {
 }
 
 static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq, int mode, int cheb_n, double tau,
-                      int comparator, int sum_radix, u64* out, int* out_level) {
+                      int comparator, int sum_radix, int hoist_sum, u64* out, int* out_level) {
     int n = c->n / 2;
     int dep = comparator_depth(cheb_n, comparator);
     if (dep < 0 || lq - 1 - dep < 0) return -1;
@@ -1777,7 +1830,9 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
     }
     int steps = 0;
     while ((1 << steps) < n) steps++;
-    if (or_rotate_sum_radix(c, k, out, lo, steps, sum_radix) < 0) { free(t); return -1; }
+    int rs = hoist_sum ? or_rotate_sum_hoisted(c, k, out, lo, steps, sum_radix)
+                       : or_rotate_sum_radix(c, k, out, lo, steps, sum_radix);
+    if (rs < 0) { free(t); return -1; }
     *out_level = lo;
     free(t);
     return 1;
@@ -1789,11 +1844,12 @@ static int match_tail(const or_ctx* c, or_keys* k, const u64* S, long G, int lq,
  * baby steps stay in Q_l u P, one ModDown per giant step); schedule 1: the
  * rotated-query table of Algorithm 1. mode 0: scores (G cts, level
  * lq-1); mode 1: identification (G cts of p(S_k), level lq-1-d2); mode 2:
- * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix).
+ * membership (1 ct: sum_k p(S_k), then RotateAndSum over all slots in radix sum_radix; hoist_sum:
+ * the rotations of each step share one ModDown).
  * Returns the number of output cts; *out_level receives their level. */
 int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T, long K, int ell, int n1, int mode,
-             int cheb_n, double tau, int comparator, int schedule, int sum_radix, int hoist, int babies_pq, u64* out,
-             int* out_level) {
+             int cheb_n, double tau, int comparator, int schedule, int sum_radix, int hoist, int babies_pq,
+             int hoist_sum, u64* out, int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top) return -1;
     long G = (K + n - 1) / n;
@@ -1813,7 +1869,7 @@ int or_match(const or_ctx* c, or_keys* k, const u64* qct, int lq, const float* T
                            : or_bsgs_scores_pq(c, k, q, lq, T, K, ell, n1, babies_pq, hoist, S);
     if (rs < 0) { free(S); free(q); return -1; }
     free(q);
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, comparator, sum_radix, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, comparator, sum_radix, hoist_sum, out, out_level);
     free(S);
     return r;
 }
@@ -2002,7 +2058,8 @@ int or_enc_bsgs_scores(const or_ctx* c, or_keys* k, const u64* qct, int L, const
 
 /* Full match against an encrypted database at level el (>= lq); modes as in or_match. */
 int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64* E, int el, long K, int ell, int n1,
-                 int mode, int cheb_n, double tau, int sum_radix, int hoist, u64* out, int* out_level) {
+                 int mode, int cheb_n, double tau, int sum_radix, int hoist, int hoist_sum, u64* out,
+                 int* out_level) {
     int top = c->nq - 1, n = c->n / 2;
     if (lq < 1 || lq > top || el < lq) return -1;
     long G = (K + n - 1) / n;
@@ -2018,7 +2075,7 @@ int or_match_enc(const or_ctx* c, or_keys* k, const u64* qct, int lq, const u64*
     int rs = or_enc_bsgs_scores(c, k, q, lq, E, el, G, ell, n1, hoist, S);
     free(q);
     if (rs < 0) { free(S); return -1; }
-    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, 0, sum_radix, out, out_level);
+    int r = match_tail(c, k, S, G, lq, mode, cheb_n, tau, 0, sum_radix, hoist_sum, out, out_level);
     free(S);
     return r;
 }

@@ -352,6 +352,27 @@ def test_rotate_sum_gives_total_in_every_slot(c1, k1):
     assert np.array_equal(k1.rotate_sum(ct, 2, 3, radix=4), y)
 
 
+def test_rotate_sum_hoisted_one_moddown_per_step(c1, k1):
+    """RotateAndSum with the rotations of each step summed before one ModDown: the total in
+    every slot; with one rotation per step (radix 2) the radix-2 form bit for bit; the steps
+    are those of the radix form (a radix-4 step over 4 slots, then a plain rotation by 4)."""
+    rng = np.random.default_rng(12)
+    z = rng.uniform(-1, 1, c1.n) / c1.n
+    ct = k1.encrypt(z, 5)
+    steps = int(np.log2(c1.n))
+    assert np.array_equal(k1.rotate_sum(ct, 2, steps, radix=2, hoist=True), k1.rotate_sum(ct, 2, steps))
+    for radix in (4, 8, 32):
+        h = k1.rotate_sum(ct, 2, steps, radix=radix, hoist=True)
+        plain = k1.rotate_sum(ct, 2, steps, radix=radix)
+        assert np.abs(k1.decrypt(h, 2) - z.sum()).max() < 1e-5
+        assert not np.array_equal(h, plain)
+        # the ModDown of a sum and the sum of the ModDowns differ by key-switch rounding only
+        assert np.abs(k1.decrypt(h, 2) - k1.decrypt(plain, 2)).max() < 1e-5
+    y = k1.rotate_sum(ct, 2, 2, radix=4, hoist=True)
+    y = c1.add(y, k1.rotate(y, 2, 4), 2)
+    assert np.array_equal(k1.rotate_sum(ct, 2, 3, radix=4, hoist=True), y)
+
+
 # ---------------------------------------------------------------------------
 # Matrix-vector product: diagonal method and BSGS (Eq. equ:diag, Eq. equ:diagbsgs-grouped,
 # Eq. eq:prerotation), checked against the FP64 matvec and against each other
@@ -710,6 +731,10 @@ def test_match_modes_small():
     memq, lvl6 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, hoist=True, babies_pq=True)
     assert lvl6 == lvl2 and not np.array_equal(memq, memh)
     assert np.abs(k.decrypt(memq[0], lvl6) - p.sum()).max() < 1e-2
+    # RotateAndSum steps sharing one ModDown: the same sum
+    mems, lvl7 = k.match(qct, T, ell, 4, oracle.MODE_MEMBERSHIP, 59, 0.5, sum_radix=8, hoist_sum=True)
+    assert lvl7 == lvl2 and not np.array_equal(mems, memr)
+    assert np.abs(k.decrypt(mems[0], lvl7) - p.sum()).max() < 1e-2
 
 
 def test_match_hybrid_comparator_small():
