@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "templates matched/sec and p50/p99 encrypted query latency at N=2^16, K=2^15; HBM GB/s"
 UNIT = "templates/s"
+# the library's profiling regions (fr_profile_read) and the stages of a membership match
+REGIONS = ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac", "misc", "copy")
+STAGES = ("babies", "mac", "giants", "cheb", "sum")
 
 
 def dist_env():
@@ -103,11 +106,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle: whole membership queries, timed
 # ---------------------------------------------------------------------------
-def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_queries=1, sum_radix=4, hoist=True,
-                   babies_pq=False):
+def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_queries=1, sum_radix=8, hoist=True,
+                   babies_pq=False, hoist_sum=False):
     """Time whole membership queries of the CPU oracle (the same match the library computes,
-    bit for bit: on-demand BSGS at working level lq, by default with giant steps sharing one
-    ModDown and RotateAndSum in radix 4). Key generation and encryption happen before the timed region;
+    bit for bit: on-demand BSGS at working level lq, with the bench's choices of hoisting and
+    RotateAndSum radix passed in). Key generation and encryption happen before the timed region;
     the oracle derives each rotation key inside the query, as it stands. Runs one query, then
     more while the time spent stays under budget_s, at most max_queries.
     Returns (seconds per query list, threads used, membership ciphertext of the first query)."""
@@ -121,7 +124,7 @@ def oracle_queries(cfgname, T, q, seed_key, seed_enc, lq, budget_s=0.0, max_quer
     while True:
         t0 = time.perf_counter()
         ref, lvl = ok.match(oq, T, c["ell"], c["n1"], 2, c["cheb_degree"], c["threshold"], level=lq,
-                            sum_radix=sum_radix, hoist=hoist, babies_pq=babies_pq)
+                            sum_radix=sum_radix, hoist=hoist, babies_pq=babies_pq, hoist_sum=hoist_sum)
         secs.append(time.perf_counter() - t0)
         if first is None:
             first = (ref[0], lvl)
@@ -170,7 +173,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+    ctx = fr.Context(device=local, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
@@ -265,7 +268,7 @@ def run_identify(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, db_tier=args.identify_tier,
-                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_IDENTIFY), W.key_seed(cfg))
     ctx.load_keys(keys)
@@ -357,7 +360,7 @@ def run_multi(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cfg = "membership"
     c = W.CONFIGS[cfg]
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
     ctx.load_keys(keys)
@@ -448,7 +451,7 @@ def run_encrypted(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cfg = dict(W.CONFIGS["membership"], ell=args.db_ell)   # --db-ell: a smaller case for profiling
     c = cfg
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants)
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants)
     # with the negative giant-step keys of the server-side pre-rotation variant
     rots = set(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP))
     rots |= set(fr.rotation_set(c["ell"], c["n1"], ctx.n, fr.FR_KEYS_TBS_TOTAL, True))
@@ -562,7 +565,7 @@ def run_sharded(args):
     slots = 1 << (c["log_n"] - 1)
     Ts, (g0, g1) = shard.template_shard(T, slots, ws, rank)
     ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, db_tier=args.identify_tier,
-                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix,
+                     **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum,
                      hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
     keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
@@ -707,7 +710,7 @@ def run_reference(args):
     lq = W.work_level(cfg, args.level_mode)
     t_all = time.perf_counter()
     secs, cores, _ = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq, budget_s=100.0,
-                                    max_queries=max(1, args.steps), sum_radix=args.sum_radix,
+                                    max_queries=max(1, args.steps), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum,
                                     hoist=bool(args.hoist_giants), babies_pq=bool(args.hoist_babies))
     wall = time.perf_counter() - t_all
     per = float(np.mean(secs))
@@ -729,16 +732,36 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM traffic of the NTT passes from one ncu capture: bytes read + written per byte of
-# algorithmic traffic (summed over the column and row pass), valid only for the NTT source
-# whose SHA-256 is listed; null is reported once the source differs.
-NTT_TRAFFIC = {"sha256": [], "dram_per_alg_byte": None}
+# Kernel-time share of each region class in one headline membership match, and the NTT passes'
+# DRAM bytes (read + written) per algorithmic byte, from the committed one-pass launch list of
+# that match (ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+# --cache-control none; see profiles/launches_membership_N65536_K32768_level8.md). Valid only for
+# the CUDA sources whose combined SHA-256 (csrc_sha256) is listed: then the regions of the bench
+# line are these shares of the timed step; otherwise they come from the profiled replays and the
+# NTT traffic is null.
+LAUNCH_LIST = {"sha256": [], "share": {}, "ntt_dram_per_alg_byte": None}
+
+# kernel name prefix -> region class, for reading a launch list
+KERNEL_CLASS = (("k_ntt", "ntt"), ("k_modup", "modup"), ("k_ip", "ip"), ("k_baby0_pq", "ip"), ("k_p2q", "moddown"),
+                ("k_moddown", "moddown"), ("k_rs_", "rescale"), ("k_rescale", "rescale"), ("k_leaf_lift", "rescale"),
+                ("k_tensor", "tensor"), ("k_mac", "mac"))
 
 
-def _sha256(path):
+def csrc_sha256():
+    """SHA-256 over the package's CUDA sources (names and contents, in name order)."""
     import hashlib
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    d = os.path.join(ROOT, "paper_2604_00546_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def launch_list_valid():
+    return bool(LAUNCH_LIST["share"]) and csrc_sha256() in LAUNCH_LIST["sha256"]
 
 
 def roofline(regions, log_n, device, fr):
@@ -762,9 +785,8 @@ def roofline(regions, log_n, device, fr):
         peak = fr.butterfly_peak(device) / 1e9
         achieved = bfly / secs / 1e9 if secs > 0 else 0.0
         traffic = None
-        ntt_src = os.path.join(ROOT, "paper_2604_00546_gb300", "csrc", "ntt.cu")
-        if NTT_TRAFFIC["dram_per_alg_byte"] and _sha256(ntt_src) in NTT_TRAFFIC["sha256"]:
-            traffic = NTT_TRAFFIC["dram_per_alg_byte"] * d["bytes"] / nl
+        if LAUNCH_LIST["ntt_dram_per_alg_byte"] and launch_list_valid():
+            traffic = LAUNCH_LIST["ntt_dram_per_alg_byte"] * d["bytes"] / nl
         roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
                      "frac": achieved / peak if peak > 0 else None,
                      "peak_kind": "measured: register-only butterfly loop on this GPU (fr_butterfly_peak)",
@@ -800,7 +822,7 @@ def run_ours(args):
     T, q, planted = W.workload(cfg)
     K = len(T)
     t0 = time.perf_counter()
-    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+    ctx = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
     rots = ctx.required_rotations(mode)
     keys = ctx.keygen(rots, W.key_seed(cfg))
@@ -856,23 +878,36 @@ def run_ours(args):
     value = whole_job_value(ws, K * args.steps, tmax)
 
     # per-region device time: the same steps again as profiled graph replays (the match
-    # captured with CUDA events around every region as graph nodes, replayed once per step),
-    # so the regions are timed back to back on the same time base as the timed steps
+    # captured with CUDA events around the timed regions as graph nodes, replayed once per
+    # step). One region class per replay (fr_profile_only), so only that class's launches carry
+    # event records and every other launch runs as in the timed steps.
     nprof = max(3, min(args.steps, 10))
-    ctx.profile(True)
-    for i in range(nprof):
-        outs = step(ctx, db, dev_q)
-    torch.cuda.synchronize()
-    regions = {}
-    for r in ("ntt", "modup", "ip", "moddown", "rescale", "tensor", "mac", "misc"):
-        ms, nl, by = ctx.profile_read(r)
-        regions[r] = {"ms": ms / nprof, "launches": nl / nprof, "bytes": by / nprof}
-    stages = {}
-    for st in ("babies", "mac", "giants", "cheb", "sum"):
-        stages[st] = ctx.profile_read("stage:" + st)[0] / nprof
-    prof_match_ms = ctx.profile_read("match")[0] / nprof
-    ctx.profile(False)
-    del outs
+    regions, prof_match = {}, {}
+    for r in REGIONS + ("stage:",):
+        ctx.profile_only(r)
+        ctx.profile(True)
+        for i in range(nprof):
+            outs = step(ctx, db, dev_q)
+        torch.cuda.synchronize()
+        if r == "stage:":
+            stages = {st: ctx.profile_read("stage:" + st)[0] / nprof for st in STAGES}
+        else:
+            ms, nl, by = ctx.profile_read(r)
+            regions[r] = {"ms": ms / nprof, "launches": nl / nprof, "bytes": by / nprof}
+        prof_match[r] = ctx.profile_read("match")[0] / nprof
+        ctx.profile(False)
+        del outs
+    ctx.profile_only("")
+    # each class's replay carries event records around that class's launches only, and each
+    # record adds latency to its region: these times are upper bounds. When the committed launch
+    # list matches the sources, the regions are its kernel-time shares of the timed step.
+    replayed = {r: dict(v) for r, v in regions.items()}
+    regions_source = "profiled replays, one region class each (upper bounds: event latency inside)"
+    if launch_list_valid():
+        for r in regions:
+            regions[r]["ms"] = LAUNCH_LIST["share"].get(r, 0.0) * (tmax / args.steps)
+        regions_source = ("kernel-time shares of the committed one-pass launch list (ncu, current sources) x the "
+                          "timed step")
 
     # end to end through the C ABI: host query -> H2D (the working-level limbs) -> match -> D2H
     h2d = 2 * (lq + 1) * (1 << c["log_n"]) * 8
@@ -924,13 +959,31 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_b = e0.elapsed_time(e1) / nb
         del outs
+        # profiled replays of the batch, one for the stages and one for every region: where
+        # its time goes
+        b_replay = {}
+        for only in ("stage:", ""):
+            ctx.profile_only(only)
+            ctx.profile(True)
+            outs = ctx.match_batch(db, qs, mode)
+            torch.cuda.synchronize()
+            if only:
+                b_stages = {st: ctx.profile_read("stage:" + st)[0] for st in STAGES}
+            else:
+                b_regions = {r: ctx.profile_read(r)[0] for r in REGIONS}
+            b_replay[only or "all regions"] = ctx.profile_read("match")[0]
+            ctx.profile(False)
+            del outs
+        ctx.profile_only("")
         batched = {"queries": args.batch, "ms_per_batch": ms_b, "value": args.batch * K / (ms_b / 1000.0),
-                   "unit": UNIT, "max_abs_err": max(abs(v - pref) for v in got_b)}
+                   "unit": UNIT, "max_abs_err": max(abs(v - pref) for v in got_b),
+                   "vs_plain_per_query": ms_p / (ms_b / args.batch),
+                   "profiled_replay_ms": b_replay, "stages_ms": b_stages, "regions_ms": b_regions}
 
     # the same query on the whole modulus chain (no level drop), for comparison
     full = None
     if args.level_mode == 1 and not args.no_full_chain and lq < len(c["q_bits"]) - 1:
-        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+        ctx_f = fr.Context(device=local, cuda_stream=stream.cuda_stream, **W.ctx_params(cfg, level_mode=0), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
         ctx_f.load_keys(keys)
         db_f = ctx_f.load_db(T)
@@ -957,7 +1010,7 @@ def run_ours(args):
     table = None
     if not args.no_table:
         ctx_t = fr.Context(device=local, cuda_stream=stream.cuda_stream, schedule=1,
-                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_giants=args.hoist_giants,
+                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
         ctx_t.load_keys(keys)
         db_t = ctx_t.load_db(T)
@@ -987,7 +1040,7 @@ def run_ours(args):
     hybrid = None
     if not args.no_hybrid:
         ctx_h = fr.Context(device=local, cuda_stream=stream.cuda_stream, comparator=1,
-                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix,
+                           **W.ctx_params(cfg, level_mode=args.level_mode), sum_radix=args.sum_radix, hoist_sum=args.hoist_sum,
                            hoist_giants=args.hoist_giants,
                      hoist_babies=args.hoist_babies)
         ctx_h.load_keys(keys)
@@ -1037,7 +1090,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         secs, cores, (o_ct, o_lvl) = oracle_queries(cfg, T, q, W.key_seed(cfg), W.enc_seed(cfg), lq,
-                                                    sum_radix=args.sum_radix, hoist=bool(args.hoist_giants),
+                                                    sum_radix=args.sum_radix, hoist_sum=args.hoist_sum, hoist=bool(args.hoist_giants),
                                                     babies_pq=bool(args.hoist_babies))
         cpu = {"value": K / float(np.mean(secs)), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "one whole membership query of the oracle, K=%d at working level %d: %.1f s" % (K, lq, secs[0]),
@@ -1055,6 +1108,7 @@ def run_ours(args):
                        "q_limbs": len(c["q_bits"]), "p_limbs": len(c["p_bits"]), "dnum": c["dnum"],
                        "work_level": lq, "level_mode": args.level_mode, "sum_radix": args.sum_radix,
                        "hoist_giants": args.hoist_giants, "hoist_babies": args.hoist_babies,
+                       "hoist_sum": args.hoist_sum,
                        "parallelism": f"replicas x{ws}",
                        "l2": "working set (diagonals + evaluation keys, several GB) exceeds the 129 MB L2; no flush"},
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99)),
@@ -1063,8 +1117,12 @@ def run_ours(args):
             "roofline": roof,
             "regions_ms_per_step": {r: regions[r]["ms"] for r in regions},
             "regions_sum_ms": sum(regions[r]["ms"] for r in regions),
-            "profiled_replay_ms": prof_match_ms,
-            "profiling": "one profiled graph replay per step (region events as graph nodes), %d steps" % nprof,
+            "regions_source": regions_source,
+            "regions_replayed_ms": {r: replayed[r]["ms"] for r in replayed},
+            "profiled_replay_ms": prof_match,
+            "profiling": ("graph replays with CUDA events as graph nodes around one region class per replay "
+                          "(fr_profile_only), %d replays per class; the Chebyshev branches run on one stream "
+                          "when profiled" % nprof),
             "regions_hbm_gbs": {r: (regions[r]["bytes"] / (regions[r]["ms"] / 1000.0) / 1e9 if regions[r]["ms"] > 0
                                     else 0.0) for r in regions},
             "stages_ms_per_step": stages,
@@ -1103,8 +1161,10 @@ def main():
                     help="baby steps kept in Q_l u P with one ModDown per giant step (fr_params.hoist_babies)")
     ap.add_argument("--hoist-giants", type=int, default=1, choices=[0, 1],
                     help="giant steps of a (query, group) share one ModDown (0: one per rotation)")
-    ap.add_argument("--sum-radix", type=int, default=4, choices=[2, 4, 8, 16, 32],
+    ap.add_argument("--sum-radix", type=int, default=8, choices=[2, 4, 8, 16, 32],
                     help="RotateAndSum radix of the membership result (2: one rotation per step)")
+    ap.add_argument("--hoist-sum", type=int, default=1, choices=[0, 1],
+                    help="the rotations of a RotateAndSum step share one ModDown (fr_params.hoist_sum)")
     ap.add_argument("--batch", type=int, default=8, help="queries per pass for the batched measurement (1: skip)")
     ap.add_argument("--serving", action="store_true", help="run the serving-loop workload instead")
     ap.add_argument("--serve-seconds", type=float, default=60.0)

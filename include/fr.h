@@ -135,6 +135,13 @@ typedef struct {
                                   sum, fused with its rescale. Same values, other noise; fewer NTTs,
                                   (l + 1 + n_p) / (l + 1) more diagonal words. Encrypted databases
                                   (fr_load_db_encrypted) need 0. */
+    uint32_t hoist_sum;        /* RotateAndSum (membership, fr_rotate_sum): 0 every rotation of a step
+                                  ends with its own ModDown; 1 the rotations of a step share one ModDown:
+                                  their inner products are summed in Q_l u P and x <- x + sum_t
+                                  sigma_t(x.b) + ModDown(sum_t IP_t) (double hoisting, Section "Hoisting
+                                  and double hoisting", applied to Algorithm 5's aggregation). With
+                                  sum_radix 2 it is the radix-2 form bit for bit; with r > 2 the same
+                                  total, other noise, one ModDown per step instead of r - 1. */
 } fr_params;
 
 /* Set up primes, NTT / base-conversion tables and device state.
@@ -349,16 +356,21 @@ fr_status fr_sync(fr_ctx* ctx);
  * starts accumulating, 0 clears and stops; fr_profile_read returns the summed
  * milliseconds, the number of timed launches and their algorithmic bytes (the
  * minimum DRAM reads + writes the launches must make) for a region: "ntt", "modup",
- * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc", the stages
- * "stage:babies", "stage:mac", "stage:giants", "stage:cheb", "stage:sum" and "match".
- * With graphs on (fr_use_graphs, the default) a profiled fr_match / fr_match_batch
- * captures the match with the region events as event-record nodes of a graph and replays
- * it once: regions are timed back to back as in a graph replay, and "match" times the
- * whole replay. With graphs off the events are recorded around each launch as it is
- * enqueued (host launch gaps fall inside the regions). Regions on the second stream of
- * the Chebyshev stage overlap those of the first, so their sum can exceed "match". */
+ * "ip", "moddown", "rescale", "tensor", "mac", "encode", "misc", "copy" (device-to-device
+ * copies and memsets), the stages "stage:babies", "stage:mac", "stage:giants", "stage:cheb",
+ * "stage:sum" and "match". With graphs on (fr_use_graphs, the default) a profiled fr_match /
+ * fr_match_batch captures the match with the region events as event-record nodes of a graph
+ * and replays it once: regions are timed back to back as in a graph replay, and "match" times
+ * the whole replay. With graphs off the events are recorded around each launch as it is
+ * enqueued (host launch gaps fall inside the regions). A profiled match runs the two branches
+ * of the Chebyshev stage on one stream, so no two regions overlap; the event records add to
+ * "match", which therefore exceeds an unprofiled match. */
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
+/* Restrict profiling to the regions whose name starts with `prefix` (NULL or "": every
+ * region); "match" is always timed. Fewer regions mean fewer event records in a profiled
+ * replay, so the timed regions run as they do unprofiled. Stays set until changed. */
+fr_status fr_profile_only(fr_ctx* ctx, const char* prefix);
 /* NTT autotuner (run by fr_setup on device contexts unless the environment sets
  * FR_NTT_TUNE=0): for N >= 2^15 it times each shape of a forward + inverse transform on this
  * GPU for one batch size per bucket (<= 4, <= 16, <= 64, > 64 limb-polynomials; best of 3

@@ -2,6 +2,7 @@
 // product with the slot automorphism fused into its gather, rescale, tensor
 // product, the diagonal plaintext x ciphertext multiply-accumulate, Chebyshev
 // scalar steps and the on-device slot encoder for template diagonals.
+#include <algorithm>
 #include <cstdio>
 
 #include "ckks_kernels.h"
@@ -18,7 +19,7 @@ __device__ __forceinline__ void fold(Acc128& a, u64 q) {
 // ModUp: per digit, fast-convert the digit's limbs to every other position of
 // Q_l u P (coefficient form); the digit's own positions are copied from the
 // evaluation-form input so they need no forward NTT afterwards.
-// in: coefficient form, job j at in + j * in_job; in_eval: evaluation form (same layout)
+// in: coefficient form, job j at in + j * in_job; in_eval: evaluation form, job j at in_eval + j * eval_job
 // ext: [J][beta][npos][N]
 // ---------------------------------------------------------------------------
 // sum_i ys_i [B/b_i]_t mod t from split residues: 30-bit multiply-accumulate, the high word
@@ -26,11 +27,11 @@ __device__ __forceinline__ void fold(Acc128& a, u64 q) {
 template <int NS>
 __device__ __forceinline__ u64 bconv_sum(const u64 (&ys)[NS], const u64 (&hat_m)[FR_MAX_DIGIT_LIMBS][FR_MAX_PRIMES],
                                          int pos, u64 t, u64 tinv, u64 t_one_s) {
-    Acc3 a{0, 0, 0};
+    AccK a{0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < NS; ++i) mac30(a, ys[i], hat_m[i][pos]);
+    for (int i = 0; i < NS; ++i) mack(a, ys[i], sum30(ys[i]), hat_m[i][pos]);
     Acc128 acc{0, 0};
-    flush30(acc, a);
+    flushk(acc, a);
     return redc(mul_shoup(acc.hi, 1, t_one_s, t), acc.lo, t, tinv);
 }
 
@@ -50,9 +51,10 @@ __device__ __forceinline__ void modup_body(const ModUpTab& T, const u64* __restr
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, const u64* __restrict__ in_eval,
-                                                    long long in_job, u64* __restrict__ ext,
-                                                    const ModUpTab* __restrict__ tabs, int beta, int npos, int N) {
+__global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, long long in_job,
+                                                    const u64* __restrict__ in_eval, long long eval_job,
+                                                    u64* __restrict__ ext, const ModUpTab* __restrict__ tabs, int beta,
+                                                    int npos, int N) {
     pdl_wait();
     pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_modup(const u64* __restrict__ in, 
     if (k >= N) return;
     const ModUpTab& T = tabs[d];
     const u64* x = in + (long long)j * in_job;
-    const u64* xe = in_eval + (long long)j * in_job;
+    const u64* xe = in_eval + (long long)j * eval_job;
     u64* out = ext + (((long long)j * beta + d) * npos) * N;
     switch (T.ns) {
         case 1: modup_body<1>(T, x, xe, out, npos, N, k); break;
@@ -107,8 +109,8 @@ __device__ __forceinline__ void ip_job(const IPJob& J, const u64 (&k0)[BETA], co
 template <int BETA>
 __device__ __forceinline__ void ip_body(const IPJobs& jobs, int npos, int pos, int klimb, int T, int k, u64 q,
                                         u64 qinv, int logN, int N, int level, const u64* pmod, const u64* pmod_s) {
-    // one key group per blockIdx.z: its key words are read once and applied to every job of the group
-    const int g = blockIdx.z;
+    // one key group per blockIdx.y: its key words are read once and applied to every job of the group
+    const int g = blockIdx.y;
     const u64* key = jobs.gkey[g];
     u64 k0[BETA], k1[BETA];
 #pragma unroll
@@ -130,13 +132,61 @@ __global__ void __launch_bounds__(kThreads) k_ip(const __grid_constant__ IPJobs 
     pdl_trigger();
     const int N = 1 << logN;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pos = blockIdx.y;
+    // position-major grid: the key groups of one position run back to back, so a ModUp
+    // extension that several groups gather from (hoisted rotations) is read from L2
+    const int pos = blockIdx.z;
     if (k >= N) return;
     // positions 0..level are Q limbs 0..level; the P limbs follow (prime indices from pbase)
     const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
     const u64 q = primes[pi].q, qinv = primes[pi].qinv;
     const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
     ip_body<BETA>(jobs, npos, pos, klimb, T, k, q, qinv, logN, N, level, pmod, pmod_s);
+}
+
+// Inner products summed into their accumulator (double-hoisted sums of rotations): thread
+// (point k, group g, position pos) runs the jobs of group g, each a key-switch inner product
+// of its ext under its automorphism (the same products as ip_job), in one 128-bit sum per
+// component, folded after every job: a product of two residues below q < 2^61 adds less than
+// q/8 to the high word, so a job's beta <= 8 products leave it below 2q before the fold. Then
+// it adds P sigma_j(addb_j) on the Q positions of component 0 and the value already in the
+// accumulator. The grid is (points, groups, positions), groups fastest after the points:
+// the key words of one position, which every group's job with that key reads, are L2 hits
+// after the first group.
+template <int BETA>
+__global__ void __launch_bounds__(kThreads) k_ip_sum(const __grid_constant__ IPSumJobs jobs, int npos, int level,
+                                                     int kp, int T, const DevPrime* __restrict__ primes, int pbase,
+                                                     int logN, const u64* __restrict__ pmod,
+                                                     const u64* __restrict__ pmod_s) {
+    pdl_wait();
+    pdl_trigger();
+    const int N = 1 << logN;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    const int pos = blockIdx.z;
+    if (k >= N) return;
+    const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
+    const u64 q = primes[pi].q, qinv = primes[pi].qinv;
+    const int klimb = pos <= level ? pos : kp + (pos - (level + 1));
+    Acc128 a0{0, 0}, a1{0, 0};
+    u64 badd = 0;
+    for (int jj = jobs.gstart[g]; jj < jobs.gstart[g + 1]; ++jj) {
+        const IPJob& J = jobs.j[jj];
+        const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
+#pragma unroll
+        for (int d = 0; d < BETA; ++d) {
+            const u64 e = J.ext[((long long)d * npos + pos) * N + src];
+            mac128(a0, e, J.key[(((long long)d * 2 + 0) * T + klimb) * N + k]);
+            mac128(a1, e, J.key[(((long long)d * 2 + 1) * T + klimb) * N + k]);
+        }
+        fold(a0, q);
+        fold(a1, q);
+        if (J.addb && pos <= level)
+            badd = add_mod(badd, mul_shoup(J.addb[(long long)pos * N + src], pmod[pos], pmod_s[pos], q), q);
+    }
+    u64* O = jobs.j[jobs.gstart[g]].out;
+    const long long o0 = (long long)pos * N + k, o1 = ((long long)npos + pos) * N + k;
+    O[o0] = add_mod(O[o0], add_mod(redc(a0.hi, a0.lo, q, qinv), badd, q), q);
+    O[o1] = add_mod(O[o1], redc(a1.hi, a1.lo, q, qinv), q);
 }
 
 // ---------------------------------------------------------------------------
@@ -377,9 +427,9 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
         const int cnt = min(n1, ell - j * n1);
         const u64* D = diags + ((long long)j * n1 + i0) * dstride + (long long)i * N + k;
         const u64* s0 = sbase + i0 * TP2;
-        Acc3 p[B][2];
+        AccK p[B][2];
 #pragma unroll
-        for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = Acc3{0, 0, 0};
+        for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = AccK{0, 0, 0};
         if (i0 + 8 <= cnt) {
             // full batch: no bounds checks
             u64 d[8];
@@ -391,28 +441,30 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const u64 ds = split30(d[u]);
+                const u32 dsum = sum30(ds);
                 const u64* sq = s0 + u * TP2;
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
-                    mac30(p[b][0], sq[b * per_q], ds);
-                    mac30(p[b][1], sq[b * per_q + TP], ds);
+                    mack(p[b][0], ds, dsum, sq[b * per_q]);
+                    mack(p[b][1], ds, dsum, sq[b * per_q + TP]);
                 }
             }
         } else {
             for (int u = 0; i0 + u < cnt; ++u) {
                 const u64 ds = split30(__ldcs(D + (long long)u * dstride));
+                const u32 dsum = sum30(ds);
                 const u64* sq = s0 + u * TP2;
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
-                    mac30(p[b][0], sq[b * per_q], ds);
-                    mac30(p[b][1], sq[b * per_q + TP], ds);
+                    mack(p[b][0], ds, dsum, sq[b * per_q]);
+                    mack(p[b][1], ds, dsum, sq[b * per_q + TP]);
                 }
             }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            flush30(acc[b][0], p[b][0]);
-            flush30(acc[b][1], p[b][1]);
+            flushk(acc[b][0], p[b][0]);
+            flushk(acc[b][1], p[b][1]);
             fold(acc[b][0], q);
             fold(acc[b][1], q);
         }
@@ -513,23 +565,24 @@ __global__ void __launch_bounds__(TP * JG) k_mac_pipe(const u64* __restrict__ ba
         issue(s + kMpNS - 1);
         const int jb = s / spb, i0 = (s % spb) * SD;
         const u64* st = sd + (size_t)(s % kMpNS) * ROWS * TP + (size_t)jg * SD * TP + pl;
-        Acc3 p[B][2];
+        AccK p[B][2];
 #pragma unroll
-        for (int qb = 0; qb < B; ++qb) p[qb][0] = p[qb][1] = Acc3{0, 0, 0};
+        for (int qb = 0; qb < B; ++qb) p[qb][0] = p[qb][1] = AccK{0, 0, 0};
 #pragma unroll
         for (int u = 0; u < SD; ++u) {
             const u64 ds = split30(st[(size_t)u * TP]);
+            const u32 dsum = sum30(ds);
 #pragma unroll
             for (int qb = 0; qb < B; ++qb) {
                 const u64* sq = sb + (size_t)qb * per_q + ((size_t)(i0 + u) * 2) * TP + pl;
-                mac30(p[qb][0], sq[0], ds);
-                mac30(p[qb][1], sq[TP], ds);
+                mack(p[qb][0], ds, dsum, sq[0]);
+                mack(p[qb][1], ds, dsum, sq[TP]);
             }
         }
 #pragma unroll
         for (int qb = 0; qb < B; ++qb) {
-            flush30(acc[qb][0], p[qb][0]);
-            flush30(acc[qb][1], p[qb][1]);
+            flushk(acc[qb][0], p[qb][0]);
+            flushk(acc[qb][1], p[qb][1]);
             fold(acc[qb][0], q);
             fold(acc[qb][1], q);
         }
@@ -549,39 +602,152 @@ __global__ void __launch_bounds__(TP * JG) k_mac_pipe(const u64* __restrict__ ba
 }
 
 // ---------------------------------------------------------------------------
-// Sums of rotations sharing one ModDown (double hoisting after Bossuat et al.): the inner
-// products IP_j of the rotations summed into one accumulator per sum, in Q_l u P, together
-// with P sigma_j(b_j) on the Q positions of component 0. ModDown then returns
-// sum_j sigma_j(b_j) + ModDown(sum_j IP_j): (x + P y - conv(x_P)) P^-1 = ModDown(x) + y
-// exactly, since the P positions of P y are zero.
-// One thread per (component, position, point); the jobs of one sum are applied in order, so
-// accumulators are never written by two threads.
+// Diagonal MAC as a persistent pipeline (the on-demand schedule's S4 for B = 1..4 queries against
+// one database): the sums of k_mac, P_{b,j}[t][i][k] = sum_{i'} B_{b,i'}[t][i][k] D'_{j n1 + i'}[i][k].
+// A tile is TP = 16 points of one limb; each CTA runs the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... with 256 threads, thread (giant-step row jg, point) accumulating giant steps jb 16 + jg. One
+// ring of kMrNS stages of 16-byte asynchronous copies carries everything: stage (tile, jb, i0)
+// holds diagonals (jb 16 + g) n1 + i0 + u, g < 16, u < 8, and the last stage of a tile also
+// carries the next tile's babies (every query, raw residues) into the other of two baby buffers.
+// So the copies of the next tile overlap the products of this one, and a CTA never waits for a
+// tile's start. The babies of a tile are split into 30-bit halves in shared memory once, after
+// they land. Every diagonal word is read once for all B queries. Needs n1 % 8 == 0, n2 % 16 == 0
+// and at least kMrNS stages per tile (checked by mac_ring_fits).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_giant_acc(const AccJobs jobs, u64* __restrict__ outs, int npos,
-                                                        int level, const DevPrime* __restrict__ primes, int pbase,
-                                                        const u64* __restrict__ pmod, const u64* __restrict__ pmod_s,
-                                                        int logN) {
+constexpr int kMrNS = 3;   // ring stages
+constexpr int kMrTP = 16;  // points per tile
+constexpr int kMrJG = 16;  // giant-step rows per CTA
+
+// Cursor over a CTA's stages (tile m, stage sl of the tile), advanced without divisions.
+struct MrCursor {
+    int m, sl, slot, tile, i, k0;
+};
+
+template <int B>
+__global__ void __launch_bounds__(kMrTP * kMrJG) k_mac_ring(const u64* __restrict__ babies, long long baby_q,
+                                                            int cap_b, const u64* __restrict__ diags,
+                                                            u64* __restrict__ out, long long out_q, int cap_o, int nl,
+                                                            int n1, int n2, const DevPrime* __restrict__ primes,
+                                                            int N) {
     pdl_wait();
     pdl_trigger();
-    const int N = 1 << logN;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pos = blockIdx.y, t = blockIdx.z;
-    if (k >= N) return;
-    const int pi = pos <= level ? pos : pbase + (pos - (level + 1));
-    const u64 q = primes[pi].q;
-    const long long off = ((long long)t * npos + pos) * N + k;
-    const bool addb = t == 0 && pos <= level;
-    const u64 pm = addb ? pmod[pos] : 0, pms = addb ? pmod_s[pos] : 0;
-    for (int j = 0; j < jobs.n; ++j) {
-        const AccJob& J = jobs.j[j];
-        u64* o = outs + (long long)J.dst * 2 * npos * N + off;
-        u64 v = add_mod(*o, J.acc[off], q);
-        if (addb) {
-            const u32 src = J.galois != 1u ? galois_src_index((u32)k, J.galois, logN) : (u32)k;
-            v = add_mod(v, mul_shoup(J.b[(long long)pos * N + src], pm, pms, q), q);
+    constexpr int TP = kMrTP, JG = kMrJG, SD = kMpSD, NT = TP * JG, NS = kMrNS;
+    constexpr int ROWS = JG * SD;          // diagonal rows per stage
+    constexpr int CHUNKS = ROWS * TP / 2;  // 16-byte chunks per stage
+    static_assert(CHUNKS % NT == 0, "whole chunks per thread");
+    extern __shared__ __align__(16) u64 smr[];
+    const int qw = n1 * 2 * TP;            // words of one query's babies in a tile
+    const int bw = B * qw;                 // words of one tile's babies
+    u64* bb = smr;                         // [2][B][n1][2][TP]
+    u64* sd = bb + 2 * (size_t)bw;         // ring [NS][JG][SD][TP]
+    const int pl = threadIdx.x % TP, jg = threadIdx.x / TP;
+    const int tpl = N / TP;                // tiles per limb
+    const int ntile = nl * tpl;
+    const int mt = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int spb = n1 / SD;               // stages per giant-step block
+    const int nst = (n2 / JG) * spb;       // stages per tile
+    const long long dstep = (long long)nl * N;  // one diagonal
+    auto at_tile = [&](MrCursor& c) {
+        c.tile = (int)blockIdx.x + c.m * (int)gridDim.x;
+        c.i = c.tile / tpl;
+        c.k0 = (c.tile - c.i * tpl) * TP;
+    };
+    auto advance = [&](MrCursor& c) {
+        c.slot = c.slot + 1 == NS ? 0 : c.slot + 1;
+        if (++c.sl == nst) {
+            c.sl = 0;
+            ++c.m;
+            at_tile(c);
         }
-        *o = v;
+    };
+    auto issue = [&](const MrCursor& c) {
+        if (c.m < mt) {
+            const int jb = c.sl / spb, i0 = (c.sl - jb * spb) * SD;
+            u64* dst = sd + (size_t)c.slot * ROWS * TP;
+            const u64* src = diags + ((long long)jb * JG * n1 + i0) * dstep + (long long)c.i * N + c.k0;
+#pragma unroll
+            for (int r = 0; r < CHUNKS / NT; ++r) {
+                const int ch = threadIdx.x + r * NT;
+                const int row = ch / (TP / 2), w = (ch % (TP / 2)) * 2;
+                const int gg = row / SD, u = row % SD;
+                cp_async16(dst + (size_t)row * TP + w, src + ((long long)gg * n1 + u) * dstep + w);
+            }
+            // the babies of tile 0 ride on its first stage, those of tile m + 1 on tile m's last
+            const int mb = (c.m == 0 && c.sl == 0) ? 0 : (c.sl == nst - 1 ? c.m + 1 : -1);
+            if (mb >= 0 && mb < mt) {
+                const int tb = (int)blockIdx.x + mb * (int)gridDim.x, il = tb / tpl, kb = (tb - il * tpl) * TP;
+                u64* bd = bb + (size_t)(mb & 1) * bw;
+                const u64* bs = babies + (long long)il * N + kb;
+                for (int ch = threadIdx.x; ch < bw / 2; ch += NT) {
+                    const int e = ch * 2;
+                    const int qb = e / qw, r = e - qb * qw;
+                    const int row = r / TP, pp = r - row * TP;  // row = 2 ib + t
+                    cp_async16(bd + e, bs + (long long)qb * baby_q + (long long)row * cap_b * N + pp);
+                }
+            }
+        }
+        cp_async_commit();  // empty groups past the end keep the group count uniform
+    };
+    MrCursor ic{0, 0, 0, 0, 0, 0};  // issue cursor, NS - 1 stages ahead
+    at_tile(ic);
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+        issue(ic);
+        advance(ic);
     }
+    MrCursor cc{0, 0, 0, 0, 0, 0};  // compute cursor
+    at_tile(cc);
+    Acc128 acc[B][2];
+#pragma unroll
+    for (int qb = 0; qb < B; ++qb) acc[qb][0] = acc[qb][1] = Acc128{0, 0};
+    for (; cc.m < mt; advance(cc)) {
+        cp_async_wait<NS - 2>();  // this thread's copies of this stage (and earlier) have landed
+        __syncthreads();          // everyone's have; the ring slot before this one is free again
+        issue(ic);
+        advance(ic);
+        u64* bm = bb + (size_t)(cc.m & 1) * bw;
+        if (cc.sl == 0) {
+            // a new tile: its babies have landed; split them into 30-bit halves in place
+            for (int e = threadIdx.x; e < bw; e += NT) bm[e] = split30(bm[e]);
+            __syncthreads();
+        }
+        const int jb = cc.sl / spb, i0 = (cc.sl - jb * spb) * SD;
+        const u64* st = sd + (size_t)cc.slot * ROWS * TP + jg * SD * TP + pl;
+        const u64* sq = bm + i0 * 2 * TP + pl;
+        AccK p[B][2];
+#pragma unroll
+        for (int qb = 0; qb < B; ++qb) p[qb][0] = p[qb][1] = AccK{0, 0, 0};
+#pragma unroll
+        for (int u = 0; u < SD; ++u) {
+            const u64 ds = split30(st[u * TP]);
+            const u32 dsum = sum30(ds);
+#pragma unroll
+            for (int qb = 0; qb < B; ++qb) {
+                mack(p[qb][0], ds, dsum, sq[qb * qw + u * 2 * TP]);
+                mack(p[qb][1], ds, dsum, sq[qb * qw + u * 2 * TP + TP]);
+            }
+        }
+        // no fold here: a flush adds less than 2^60 to the high word, and a giant step has at
+        // most 8 flushes (n1 <= 64), so the high word is reduced once, before the REDC
+#pragma unroll
+        for (int qb = 0; qb < B; ++qb) {
+            flushk(acc[qb][0], p[qb][0]);
+            flushk(acc[qb][1], p[qb][1]);
+        }
+        if (i0 + SD == n1) {
+            // giant step jb JG + jg complete for this point: reduce and store
+            const DevPrime P = primes[cc.i];
+            const int j = jb * JG + jg;
+#pragma unroll
+            for (int qb = 0; qb < B; ++qb) {
+                u64* O = out + (long long)qb * out_q + (long long)j * 2 * cap_o * N + (long long)cc.i * N + cc.k0 + pl;
+                O[0] = redc(mul_shoup(acc[qb][0].hi, 1, P.one_s, P.q), acc[qb][0].lo, P.q, P.qinv);
+                O[(long long)cap_o * N] = redc(mul_shoup(acc[qb][1].hi, 1, P.one_s, P.q), acc[qb][1].lo, P.q, P.qinv);
+                acc[qb][0] = acc[qb][1] = Acc128{0, 0};
+            }
+        }
+    }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -626,7 +792,7 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
         const u64* D = diags + (long long)j * n1 * dstride + (long long)i * N + k;
         Acc128 a0{0, 0}, am{0, 0}, a2{0, 0};
         for (int i0 = 0; i0 < cnt; i0 += 4) {
-            Acc3 p0{0, 0, 0}, pm{0, 0, 0}, p2{0, 0, 0};
+            AccK p0{0, 0, 0}, pm{0, 0, 0}, p2{0, 0, 0};
             const u64* sq = sb + (size_t)i0 * 3 * TP + pl;
             if (i0 + 4 <= cnt) {
                 u64 e0[4], e1[4];
@@ -638,22 +804,24 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const u64* bq = sq + u * 3 * TP;
-                    mac30(p0, bq[0], split30(e0[u]));
-                    mac30(p2, bq[TP], split30(e1[u]));
-                    mac30(pm, bq[2 * TP], split30(add_mod(e0[u], e1[u], q)));
+                    const u64 x0 = split30(e0[u]), x2 = split30(e1[u]), xm = split30(add_mod(e0[u], e1[u], q));
+                    mack(p0, x0, sum30(x0), bq[0]);
+                    mack(p2, x2, sum30(x2), bq[TP]);
+                    mack(pm, xm, sum30(xm), bq[2 * TP]);
                 }
             } else {
                 for (int u = 0; i0 + u < cnt; ++u) {
                     const u64 f0 = __ldcs(D + u * dstride), f1 = __ldcs(D + u * dstride + cstride);
                     const u64* bq = sq + u * 3 * TP;
-                    mac30(p0, bq[0], split30(f0));
-                    mac30(p2, bq[TP], split30(f1));
-                    mac30(pm, bq[2 * TP], split30(add_mod(f0, f1, q)));
+                    const u64 x0 = split30(f0), x2 = split30(f1), xm = split30(add_mod(f0, f1, q));
+                    mack(p0, x0, sum30(x0), bq[0]);
+                    mack(p2, x2, sum30(x2), bq[TP]);
+                    mack(pm, xm, sum30(xm), bq[2 * TP]);
                 }
             }
-            flush30(a0, p0);
-            flush30(am, pm);
-            flush30(a2, p2);
+            flushk(a0, p0);
+            flushk(am, pm);
+            flushk(a2, p2);
             fold(a0, q);
             fold(am, q);
             fold(a2, q);
@@ -706,15 +874,16 @@ __global__ void __launch_bounds__(256) k_mac_table(const u64* __restrict__ table
 #pragma unroll
         for (int gg = 0; gg < GG; ++gg) {
             if (g0 + gg < G) {
-                Acc3 p0{0, 0, 0}, p1{0, 0, 0};
+                AccK p0{0, 0, 0}, p1{0, 0, 0};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const u64 d = split30(m0 + u < ell ? __ldcs(d0 + gg * dgrp + (long long)(m0 + u) * ds) : 0ull);
-                    mac30(p0, a[u], d);
-                    mac30(p1, b[u], d);
+                    const u32 dsum = sum30(d);
+                    mack(p0, d, dsum, a[u]);
+                    mack(p1, d, dsum, b[u]);
                 }
-                flush30(acc[gg][0], p0);
-                flush30(acc[gg][1], p1);
+                flushk(acc[gg][0], p0);
+                flushk(acc[gg][1], p1);
                 fold(acc[gg][0], q);
                 fold(acc[gg][1], q);
             }
@@ -764,21 +933,29 @@ __global__ void k_sum(const u64* a, int cap, long long js, int J, u64* out, int 
     out[((long long)t * o_cap + i) * N + k] = v;
 }
 
-// Chebyshev leaves: out[leaf] = x * cb[leaf] + (c0 += ca[leaf])   (before rescale)
-__global__ void k_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, const u64* cb,
-                              const u64* cb_s, const u64* ca, const DevPrime* primes, int N) {
+// Lifted last limbs of the Chebyshev leaves, T1 cb_j + ca_j at limb l, from u, the coefficient
+// form of T1's last limb ([B][2][N]): the INTT is linear and the constant ca_j is the constant
+// polynomial, so the leaf's last limb in coefficient form is cb_{j,l} u + ca_{j,l} at coefficient 0
+// of component 0; centered and reduced to q_i for i < l as in k_rescale_lift.
+// lifted [B nl][2][l][N]; grid (N / 256, 2 nl, B).
+__global__ void k_leaf_lift(const u64* __restrict__ u, const u64* __restrict__ cb, const u64* __restrict__ cb_s,
+                            const u64* __restrict__ ca, int nl, int L1, u64* __restrict__ lifted,
+                            const RescaleTab* __restrict__ tab, u64 ql, int l, int N) {
     pdl_wait();
     pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y % (level + 1);
-    const int t = blockIdx.y / (level + 1);
-    const int leaf = blockIdx.z;
+    const int j = blockIdx.y >> 1, t = blockIdx.y & 1, b = blockIdx.z;
     if (k >= N) return;
-    const u64 q = primes[i].q;
-    const int L1 = level + 1;
-    u64 v = mul_shoup(x[((long long)t * x_cap + i) * N + k], cb[leaf * L1 + i], cb_s[leaf * L1 + i], q);
-    if (t == 0) v = add_mod(v, ca[leaf * L1 + i], q);
-    out[(long long)leaf * 2 * o_cap * N + ((long long)t * o_cap + i) * N + k] = v;
+    u64 r = mul_shoup(u[((long long)b * 2 + t) * N + k], cb[j * L1 + l], cb_s[j * L1 + l], ql);
+    if (t == 0 && k == 0) r = add_mod(r, ca[j * L1 + l], ql);
+    const bool neg = r > tab->half;
+    u64* o = lifted + ((((long long)b * nl + j) * 2 + t) * l) * N + k;
+    for (int i = 0; i < l; ++i) {
+        const u64 q = tab->q[i];
+        u64 w = mul_shoup(r, 1, tab->one_s[i], q);
+        if (neg) w = sub_mod(w, tab->ql_mod[i], q);
+        o[(long long)i * N] = w;
+    }
 }
 
 // x <- 2 x - c (c added to the constant term: every evaluation point of c0)
@@ -959,16 +1136,16 @@ __global__ void k_coef_residues(const long long* __restrict__ m, int nd, u64* __
 // launchers
 // ===========================================================================
 
-void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
-                  int npos, int N, int J, cudaStream_t s) {
+void launch_modup(const u64* in, long long in_job, const u64* in_eval, long long eval_job, u64* ext,
+                  const ModUpTab* tabs, int beta, int npos, int N, int J, cudaStream_t s) {
     dim3 g((N + kThreads - 1) / kThreads, beta, J);
-    launch_k(k_modup, dim3(g), dim3(kThreads), 0, s, in, in_eval, in_job, ext, tabs, beta, npos, N);
+    launch_k(k_modup, dim3(g), dim3(kThreads), 0, s, in, in_job, in_eval, eval_job, ext, tabs, beta, npos, N);
 }
 
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
                const PrimeMap& pos_prime, int logN, cudaStream_t s, const u64* pmod, const u64* pmod_s) {
     const int N = 1 << logN;
-    dim3 g((N + kThreads - 1) / kThreads, npos, jobs.ngroups);
+    dim3 g((N + kThreads - 1) / kThreads, jobs.ngroups, npos);
     const int pbase = npos > level + 1 ? pos_prime.idx[level + 1] : 0;
     switch (beta) {
 #define FR_IP_CASE(B) \
@@ -978,6 +1155,23 @@ void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T,
         default: launch_k(k_ip<8>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN, pmod, pmod_s);
             break;
 #undef FR_IP_CASE
+    }
+}
+
+void launch_ip_sum(const IPSumJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
+                   const PrimeMap& pos_prime, int logN, const u64* pmod, const u64* pmod_s, cudaStream_t s) {
+    const int N = 1 << logN;
+    dim3 g((N + kThreads - 1) / kThreads, jobs.ngroups, npos);
+    const int pbase = npos > level + 1 ? pos_prime.idx[level + 1] : 0;
+    switch (beta) {
+#define FR_IPS_CASE(B) \
+    case B: launch_k(k_ip_sum<B>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN, pmod, pmod_s); \
+        break;
+        FR_IPS_CASE(1) FR_IPS_CASE(2) FR_IPS_CASE(3) FR_IPS_CASE(4) FR_IPS_CASE(5) FR_IPS_CASE(6) FR_IPS_CASE(7)
+        default: launch_k(k_ip_sum<8>, g, dim3(kThreads), 0, s, jobs, npos, level, kp, T, primes, pbase, logN, pmod,
+                          pmod_s);
+            break;
+#undef FR_IPS_CASE
     }
 }
 
@@ -1044,18 +1238,59 @@ static void launch_mac_t(const u64* babies, long long baby_q, int cap_b, const u
     launch_k(k_mac<B>, dim3(g), dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, TP, JG, primes, N);
 }
 
+static size_t mac_ring_smem(int B, int n1) {
+    return ((size_t)2 * B * n1 * 2 * kMrTP + (size_t)kMrNS * kMrJG * kMpSD * kMrTP) * sizeof(u64);
+}
+
+bool mac_ring_fits(int n1, int ell, int N, int B) {
+    if (n1 <= 0 || n1 % kMpSD != 0 || ell % n1 != 0 || N % kMrTP != 0 || B < 1 || B > 4) return false;
+    const int n2 = ell / n1;
+    if (n1 > 64 || n2 % kMrJG != 0 || (n2 / kMrJG) * (n1 / kMpSD) < kMrNS) return false;
+    return mac_ring_smem(B, n1) <= 200u * 1024;
+}
+
+template <int B>
+static void launch_mac_ring_t(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out,
+                              long long out_q, int cap_o, int nl, int n1, int n2, const DevPrime* primes, int N,
+                              cudaStream_t s) {
+    const size_t sm = mac_ring_smem(B, n1);
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit_once(k_mac_ring<B>, 200 * 1024, attr);
+    // persistent grid: as many CTAs as fit on the GPU at once, capped by the tile count
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_ring<B>, kMrTP * kMrJG, sm);
+    const long long ntile = (long long)nl * (N / kMrTP);
+    const int grid = (int)std::min<long long>(ntile, (long long)std::max(1, per) * std::max(1, sms));
+    launch_k(k_mac_ring<B>, dim3(grid), dim3(kMrTP * kMrJG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o,
+             nl, n1, n2, primes, N);
+}
+
+void launch_mac_ring(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                     int cap_o, int nl, int n1, int ell, int B, const DevPrime* primes, int N, cudaStream_t s) {
+    const int n2 = ell / n1;
+    switch (B) {
+        case 1: launch_mac_ring_t<1>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 2: launch_mac_ring_t<2>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 3: launch_mac_ring_t<3>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        case 4: launch_mac_ring_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s); break;
+        default: break;  // the engine splits larger batches
+    }
+}
+
 bool mac_pipe_fits(int n1, int ell, int N) {
     const int n2 = n1 > 0 ? ell / n1 : 0;
     return n1 % kMpSD == 0 && n1 <= 64 && ell % n1 == 0 && n2 % 4 == 0 && N % 64 == 0;
 }
 
-// TP points x JG = 4 giant-step rows per CTA: 64 points for one query, 32 for 2..4 (the staged
-// babies of B queries stay within 64 KiB at n1 = 32)
-template <int B>
-static void launch_mac_pipe_t(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out,
+// TP points x JG giant-step rows per CTA. One query: 64 points x 4 rows. Two to four queries:
+// 16 points x 16 rows when the giant steps come in blocks of 16 (256 threads; 8 B KiB of staged
+// babies and a 64 KiB ring, so two CTAs, 16 warps, share an SM), else 32 points x 4 rows.
+template <int B, int TP, int JG>
+static void launch_mac_pipe_s(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out,
                               long long out_q, int cap_o, int nl, int n1, int n2, const DevPrime* primes, int N,
                               cudaStream_t s) {
-    constexpr int TP = B == 1 ? 64 : 32, JG = 4;
     const size_t sm = ((size_t)B * n1 * 2 * TP + (size_t)kMpNS * JG * kMpSD * TP) * sizeof(u64);
     // the limit is raised once per device, so to the most any n1 <= 64 needs (200 KiB)
     static std::atomic<unsigned long long> attr{0};
@@ -1063,6 +1298,20 @@ static void launch_mac_pipe_t(const u64* babies, long long baby_q, int cap_b, co
     dim3 g(N / TP, nl);
     launch_k(k_mac_pipe<B, TP, JG>, g, dim3(TP * JG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1,
              n2, primes, N);
+}
+
+template <int B>
+static void launch_mac_pipe_t(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out,
+                              long long out_q, int cap_o, int nl, int n1, int n2, const DevPrime* primes, int N,
+                              cudaStream_t s) {
+    if constexpr (B == 1) {
+        launch_mac_pipe_s<1, 64, 4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s);
+    } else {
+        if (n2 % 16 == 0 && N % 16 == 0)
+            launch_mac_pipe_s<B, 16, 16>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s);
+        else
+            launch_mac_pipe_s<B, 32, 4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, primes, N, s);
+    }
 }
 
 void launch_mac_pipe(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
@@ -1086,13 +1335,6 @@ void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags
         case 4: launch_mac_t<4>(babies, baby_q, cap_b, diags, out, out_q, cap_o, nl, n1, n2, ell, primes, N, s); break;
         default: break;  // the engine splits larger batches
     }
-}
-
-void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const DevPrime* primes, int pbase,
-                      const u64* pmod, const u64* pmod_s, int logN, cudaStream_t s) {
-    const int N = 1 << logN;
-    dim3 g((N + kThreads - 1) / kThreads, npos, 2);
-    launch_k(k_giant_acc, g, dim3(kThreads), 0, s, jobs, outs, npos, level, primes, pbase, pmod, pmod_s, logN);
 }
 
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
@@ -1134,10 +1376,10 @@ void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap,
     launch_k(k_sum, dim3(g), dim3(kThreads), 0, s, a, cap, js, J, out, o_cap, level, primes, N);
 }
 
-void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
-                        const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s) {
-    dim3 g((N + kThreads - 1) / kThreads, 2 * (level + 1), nleaves);
-    launch_k(k_cheb_leaves, dim3(g), dim3(kThreads), 0, s, x, x_cap, out, o_cap, level, cb, cb_s, ca, primes, N);
+void launch_leaf_lift(const u64* u, const u64* cb, const u64* cb_s, const u64* ca, int nl, int L1, u64* lifted,
+                      const RescaleTab* tab, u64 ql, int l, int N, int B, cudaStream_t s) {
+    dim3 g((N + kThreads - 1) / kThreads, 2 * nl, B);
+    launch_k(k_leaf_lift, dim3(g), dim3(kThreads), 0, s, u, cb, cb_s, ca, nl, L1, lifted, tab, ql, l, N);
 }
 
 void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,

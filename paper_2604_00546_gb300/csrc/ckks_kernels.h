@@ -76,14 +76,14 @@ struct IPJobs {
     int ngroups;
 };
 struct MDJobs { MDJob j[FR_MAX_JOBS]; };
-// One inner product folded into the accumulator of its sum of rotations (double hoisting).
-struct AccJob {
-    const u64* acc;  // [2][npos][N] inner product (evaluation form)
-    const u64* b;    // c0 of the rotated ciphertext, limbs 0..level (stride N)
-    u32 galois;
-    int dst;         // accumulator index
+// Inner products summed straight into the accumulators of their sums of rotations: group g
+// (jobs gstart[g] .. gstart[g+1]-1) adds into j[gstart[g]].out. Each job's ext, key, galois and
+// addb (its rotated ciphertext's c0) are used as in IPJobs.
+struct IPSumJobs {
+    IPJob j[FR_MAX_JOBS];
+    int gstart[FR_MAX_JOBS + 1];
+    int ngroups;
 };
-struct AccJobs { AccJob j[FR_MAX_JOBS]; int n; };
 struct TensorJobs { TensorJob j[FR_MAX_JOBS]; };
 
 // Forward NTT that stores its values in Montgomery form (x 2^64 mod q), in place.
@@ -97,6 +97,16 @@ void launch_ntt_moddown(const RingDev& R, const PolyBatch& b, const MDJobs& jobs
 // (ct component p / l, limb p % l); writes out = (x - NTT(lifted)) q_l^-1, then mode 1 adds
 // the matching component of the ct at add + (p / l / 2) add_bs (cap add_cap), mode 2 doubles
 // and subtracts cres[i] from component 0.
+// Chebyshev leaves Rescale(T1 cb_j + ca_j) in two launches and one transform, without the
+// leaves in memory: launch_leaf_lift forms the lifted last limbs [B nl][2][l][N] from u, the
+// coefficient form of T1's last limb ([B][2][N]); launch_ntt_leaf_rescale transforms them
+// (b: poly ((b nl + j) 2 + t) l + i) and writes leaf (b, j) at out + (b nl + j) 2 out_cap N.
+// T1 of query b at x + b x_bs (cap x_cap); constants [nl][L1] each.
+void launch_leaf_lift(const u64* u, const u64* cb, const u64* cb_s, const u64* ca, int nl, int L1, u64* lifted,
+                      const RescaleTab* tab, u64 ql, int l, int N, int B, cudaStream_t s);
+void launch_ntt_leaf_rescale(const RingDev& R, const PolyBatch& b, const u64* x, long long x_bs, int x_cap,
+                             const u64* cb, const u64* cb_s, const u64* ca, int nl, int L1, u64* out, int out_cap,
+                             const RescaleTab* tab, int l, cudaStream_t s);
 void launch_ntt_rescale(const RingDev& R, const PolyBatch& b, const u64* x, int x_cap, u64* out, int out_cap,
                         const RescaleTab* tab, int l, int mode, const u64* add, int add_cap, long long add_bs,
                         const u64* cres, cudaStream_t s);
@@ -116,8 +126,10 @@ void launch_ntt_relin_rescale(const RingDev& R, const PolyBatch& b, const u64* a
                               const u64* pinv, const u64* pinv_s, const RescaleTab* tab, u64* out, int out_cap,
                               long long out_bs, int mode, const u64* add, int add_cap, long long add_bs,
                               const u64* cres, cudaStream_t s);
-void launch_modup(const u64* in, const u64* in_eval, long long in_job, u64* ext, const ModUpTab* tabs, int beta,
-                  int npos, int N, int J, cudaStream_t s);
+// ModUp of J inputs: coefficient form of input j at in + j in_job, evaluation form (for the
+// digits' own positions) at in_eval + j eval_job
+void launch_modup(const u64* in, long long in_job, const u64* in_eval, long long eval_job, u64* ext,
+                  const ModUpTab* tabs, int beta, int npos, int N, int J, cudaStream_t s);
 void launch_ip(const IPJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
                const PrimeMap& pos_prime, int logN, cudaStream_t s, const u64* pmod = nullptr,
                const u64* pmod_s = nullptr);
@@ -130,10 +142,12 @@ void launch_rescale_combine(const u64* x, int x_cap, const u64* lifted, u64* out
                             int l, int N, int BT, cudaStream_t s);
 void launch_tensor(const TensorJobs& jobs, int J, int level, const DevPrime* primes, int N, cudaStream_t s);
 // B <= 4 queries: babies of query b at babies + b * baby_q, outputs at out + b * out_q
-// Sums of rotations with one ModDown (double hoisting): for each job, outs[dst] += acc and,
-// on the Q positions of component 0, += P sigma_g(b). outs: [ndst][2][npos][N].
-void launch_giant_acc(const AccJobs& jobs, u64* outs, int npos, int level, const DevPrime* primes, int pbase,
-                      const u64* pmod, const u64* pmod_s, int logN, cudaStream_t s);
+// Sums of rotations with one ModDown (double hoisting), without the per-job inner products in
+// memory: for each group g and position,
+// out_g += sum_{jobs of g} (IP_j + P sigma_j(addb_j) on the Q positions of component 0), the
+// inner products as launch_ip computes them. out_g: [2][npos][N], read and written.
+void launch_ip_sum(const IPSumJobs& jobs, int beta, int npos, int level, int kp, int T, const DevPrime* primes,
+                   const PrimeMap& pos_prime, int logN, const u64* pmod, const u64* pmod_s, cudaStream_t s);
 // Encrypted-database MAC: (d0, d1, d2)_j = sum_i B_i (x) E_{j n1 + i} for every giant step j.
 // babies [n1][2][cap_b][N]; diags [ell][2][nl][N] (evaluation form, Montgomery); out [n2][3][cap_o][N].
 void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int cap_o, int nl, int n1, int n2, int ell,
@@ -143,6 +157,12 @@ void launch_mac_ct(const u64* babies, int cap_b, const u64* diags, u64* out, int
 // queries (the sums of launch_mac: babies of query b at babies + b baby_q, [n1][2][cap_b][N];
 // outputs at out + b out_q, [n2][2][cap_o][N]); usable when mac_pipe_fits.
 bool mac_pipe_fits(int n1, int ell, int N);
+// The same sums as a persistent pipeline (k_mac_ring): one CTA per GPU slot runs point tiles in
+// turn, the next tile's diagonals and babies in flight while this one is multiplied; B = 1..4
+// queries, each diagonal word read once for all of them. Usable when mac_ring_fits.
+bool mac_ring_fits(int n1, int ell, int N, int B);
+void launch_mac_ring(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
+                     int cap_o, int nl, int n1, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_mac_pipe(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
                      int cap_o, int nl, int n1, int ell, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_mac(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
@@ -155,8 +175,6 @@ void launch_add(const u64* a, int a_cap, long long a_bs, const u64* b, int b_cap
                 long long o_bs, int level, int B, const DevPrime* primes, int N, cudaStream_t s);
 void launch_sum(const u64* a, int cap, long long js, int J, u64* out, int o_cap, int level, const DevPrime* primes,
                 int N, cudaStream_t s);
-void launch_cheb_leaves(const u64* x, int x_cap, u64* out, int o_cap, int level, int nleaves, const u64* cb,
-                        const u64* cb_s, const u64* ca, const DevPrime* primes, int N, cudaStream_t s);
 void launch_to_mont(u64* x, long long n_per_poly, const PrimeMap& pm, const DevPrime* primes, long long total,
                     cudaStream_t s);
 void launch_encode_diags(const float* T, long long K, int ell, int logn, long long grp, int d0, int nd, int n1,

@@ -53,19 +53,12 @@ __device__ __forceinline__ void mac128(Acc128& a, u64 x, u64 y) {
 
 // Products of residues below 2^60 from 30-bit halves: x = xh 2^30 + xl, y = yh 2^30 + yl,
 // x y = xl yl + (xl yh + xh yl) 2^30 + xh yh 2^60. Each partial product is below 2^60, so up
-// to 8 products sum in three 64-bit words (a1 takes two per product) with no carries; each
-// term is one 32 x 32 -> 64-bit multiply-add.
+// to 8 products sum in three 64-bit words, a1 holding the middle terms (below 2^64), with no
+// carries. split30 packs (xl, xh) into the low and high 32-bit words.
 struct Acc3 {
     u64 a0, a1, a2;
 };
 __device__ __forceinline__ u64 split30(u64 x) { return (x & 0x3fffffffull) | ((x >> 30) << 32); }
-__device__ __forceinline__ void mac30(Acc3& a, u64 xs, u64 ys) {
-    const u32 xl = (u32)xs, xh = (u32)(xs >> 32), yl = (u32)ys, yh = (u32)(ys >> 32);
-    a.a0 += (u64)xl * yl;
-    a.a1 += (u64)xl * yh;
-    a.a1 += (u64)xh * yl;
-    a.a2 += (u64)xh * yh;
-}
 // acc += a0 + a1 2^30 + a2 2^60, then a = 0
 __device__ __forceinline__ void flush30(Acc128& acc, Acc3& a) {
     u64 lo = a.a0, hi = 0;
@@ -78,6 +71,28 @@ __device__ __forceinline__ void flush30(Acc128& acc, Acc3& a) {
     acc.lo += lo;
     acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
     a.a0 = a.a1 = a.a2 = 0;
+}
+
+// Karatsuba form of the same sums, three multiply-adds per product:
+//   x y = xl yl + ((xl + xh)(yl + yh) - xl yl - xh yh) 2^30 + xh yh 2^60.
+// am = sum (xl + xh)(yl + yh) may wrap modulo 2^64, but the middle term sum (xl yh + xh yl) is
+// below 8 * 2 * 2^60 = 2^64 for up to 8 products, so am - a0 - a2 modulo 2^64 is exact.
+// xsum = xl + xh is passed in (it is shared by every product with the same x).
+struct AccK {
+    u64 a0, am, a2;
+};
+__device__ __forceinline__ u32 sum30(u64 xs) { return (u32)xs + (u32)(xs >> 32); }
+__device__ __forceinline__ void mack(AccK& a, u64 xs, u32 xsum, u64 ys) {
+    const u32 xl = (u32)xs, xh = (u32)(xs >> 32), yl = (u32)ys, yh = (u32)(ys >> 32);
+    a.a0 += (u64)xl * yl;
+    a.am += (u64)xsum * (yl + yh);
+    a.a2 += (u64)xh * yh;
+}
+// acc += the products summed in a, then a = 0
+__device__ __forceinline__ void flushk(Acc128& acc, AccK& a) {
+    Acc3 t{a.a0, a.am - a.a0 - a.a2, a.a2};
+    flush30(acc, t);
+    a.a0 = a.am = a.a2 = 0;
 }
 
 // a * b mod q for two variable residues: REDC(REDC(a b) * R^2)

@@ -122,6 +122,7 @@ struct fr_ctx {
     long long fail_alloc_after = -1;     // failure injection: the device allocation that fails (-1 none)
     std::vector<void*>* defer_free = nullptr;  // frees held back while a two-stream section unwinds
     bool prof = false;
+    std::string prof_only;               // profile only the regions whose name starts with this
     std::map<std::string, Region> regions;
     uint64_t launches = 0;
     int host_threads = 1;
@@ -130,6 +131,7 @@ struct fr_ctx {
     int sum_radix = 2;                   // RotateAndSum radix (2: one rotation per step)
     bool hoist_giants = false;           // giant steps of a group share one ModDown
     bool hoist_babies = false;           // baby steps stay in Q_l u P; one ModDown per giant step
+    bool hoist_sum = false;              // the rotations of a RotateAndSum step share one ModDown
     std::map<int, DevPrime*> d_primes_ext;  // per level: the primes of the positions of Q_l u P
     double ntt_tune_us[FR_NTT_BUCKETS * FR_NTT_SHAPES] = {};  // tuner times: bucket x shape (forward + inverse)
     std::set<fr_db*> dbs;                // databases loaded and not yet freed
@@ -231,6 +233,7 @@ struct Prof {
     cudaEvent_t a = nullptr, b = nullptr;
     Prof(fr_ctx* cc, const char* name, double bytes = 0) : c(cc) {
         if (!c->prof) return;
+        if (!c->prof_only.empty() && std::strncmp(name, c->prof_only.c_str(), c->prof_only.size()) != 0) return;
         r = &c->regions[name];
         r->bytes += (uint64_t)bytes;
         cudaEventCreate(&a);
@@ -265,6 +268,17 @@ void ntt(fr_ctx* c, u64* base, long long outer, int inner, int npolys, const Pri
     launch_ntt(c->rd, b, inv, c->cur);
     c->launches += 2;
 }
+// the same transform out of place: poly p read from src + (p / inner) src_outer + (p % inner) N
+// (npolys a multiple of inner), written to its place in base
+void ntt_from(fr_ctx* c, const u64* src, long long src_outer, u64* base, long long outer, int inner, int npolys,
+              const PrimeMap& pm, bool inv) {
+    Prof p(c, "ntt", 16.0 * npolys * c->R.N);
+    PolyBatch b{base, outer, inner, npolys, pm};
+    b.src = src;
+    b.src_outer = src_outer;
+    launch_ntt(c->rd, b, inv, c->cur);
+    c->launches += 2;
+}
 // forward NTT of the non-own positions of nj ModUp outputs [nj][beta][npos][N]
 void ntt_modup(fr_ctx* c, u64* ext, int nj, int level) {
     const int beta = c->R.digits_at(level), npos = level + 1 + c->R.np;
@@ -282,11 +296,13 @@ void ntt_cts(fr_ctx* c, u64* p, int B, int level, int cap, bool inv) {
 long long ctw(const fr_ctx* c, int cap) { return 2ll * cap * c->R.N; }
 
 void copy_d2d(fr_ctx* c, u64* dst, const u64* src, size_t words) {
+    Prof p(c, "copy", 16.0 * words);
     CU(cudaMemcpyAsync(dst, src, words * sizeof(u64), cudaMemcpyDeviceToDevice, c->cur));
 }
 // copy limbs 0..level of B cts from cap_s to cap_d layout
 void copy_cts(fr_ctx* c, u64* dst, int cap_d, const u64* src, int cap_s, int B, int level) {
     const size_t N = c->R.N;
+    Prof p(c, "copy", 16.0 * 2 * B * (level + 1) * N);
     CU(cudaMemcpy2DAsync(dst, cap_d * N * 8, src, cap_s * N * 8, (level + 1) * N * 8, 2 * (size_t)B,
                          cudaMemcpyDeviceToDevice, c->cur));
 }
@@ -397,15 +413,27 @@ void modup_chunks(fr_ctx* c, int level, const std::vector<KSReq>& reqs, F finish
     const int UCH = 16;
     for (size_t u0 = 0; u0 < ins.size(); u0 += UCH) {
         const int nu = (int)std::min<size_t>(UCH, ins.size() - u0);
-        Tmp in(c, (size_t)2 * nu * L1N);  // [nu] coefficient-form copies, then [nu] evaluation-form copies
-        u64* in_e = in.p + (size_t)nu * L1N;
-        for (int u = 0; u < nu; ++u) copy_d2d(c, in_e + (size_t)u * L1N, ins[u0 + u], L1N);
-        copy_d2d(c, in.p, in_e, (size_t)nu * L1N);
-        ntt(c, in.p, (long long)L1N, level + 1, nu * (level + 1), pm_level(level), true);
+        // inputs at one stride (the d2 parts of a batch of products, the ciphertexts of a batch)
+        // are read in place: the inverse NTT writes their coefficient form straight into `in`,
+        // and the ModUp takes the digits' own positions from the inputs themselves. Others are
+        // first gathered into a second half of `in`.
+        const long long st = nu > 1 ? (long long)(ins[u0 + 1] - ins[u0]) : (long long)L1N;
+        bool strided = st > 0;
+        for (int u = 1; u < nu && strided; ++u) strided = ins[u0 + u] == ins[u0] + (long long)u * st;
+        Tmp in(c, (size_t)(strided ? 1 : 2) * nu * L1N);  // coefficient form [nu], then gathered inputs
+        const u64* in_e = ins[u0];
+        long long e_job = st;
+        if (!strided) {
+            u64* g = in.p + (size_t)nu * L1N;
+            for (int u = 0; u < nu; ++u) copy_d2d(c, g + (size_t)u * L1N, ins[u0 + u], L1N);
+            in_e = g;
+            e_job = (long long)L1N;
+        }
+        ntt_from(c, in_e, e_job, in.p, (long long)L1N, level + 1, nu * (level + 1), pm_level(level), true);
         Tmp ext(c, (size_t)nu * beta * npos * N);
         {
             Prof p(c, "modup", 8.0 * N * nu * (2.0 * (level + 1) + (double)beta * npos));
-            launch_modup(in.p, in_e, (long long)L1N, ext.p, c->d_modup[level], beta, npos, N, nu, c->cur);
+            launch_modup(in.p, (long long)L1N, in_e, e_job, ext.p, c->d_modup[level], beta, npos, N, nu, c->cur);
             c->launches++;
         }
         ntt_modup(c, ext.p, nu, level);
@@ -436,9 +464,9 @@ void keyswitch(fr_ctx* c, int level, const std::vector<KSReq>& reqs) {
 // Sums of rotations that share one ModDown per sum (double hoisting after Bossuat et al.):
 // out[o] = base[o] + sum over the requests r with r.sum_dst = o of Rot(r), where a request is
 // a rotation (mode 1: r.c the a part, r.add its b part, r.galois, r.key). Every request gets
-// its own ModUp (hoisted where inputs repeat) and inner product; the inner products of a sum
-// and P sigma(b) are folded into one accumulator in Q_l u P (k_giant_acc), and one ModDown
-// with base[o] as its addend ends the sum: base + sum_r sigma_r(b_r) + ModDown(sum_r IP_r).
+// its own ModUp (hoisted where inputs repeat); the inner products of a sum and P sigma(b) are
+// summed straight into one accumulator in Q_l u P (k_ip_sum), and one ModDown with base[o] as
+// its addend ends the sum: base + sum_r sigma_r(b_r) + ModDown(sum_r IP_r).
 void keyswitch_sums(fr_ctx* c, int level, const std::vector<KSReq>& reqs, const std::vector<const u64*>& base,
                     int base_cap, const std::vector<u64*>& out, int out_cap) {
     if (level > c->key_level) raise(FR_ERR_LEVEL, "key switching above the context's working level");
@@ -447,36 +475,38 @@ void keyswitch_sums(fr_ctx* c, int level, const std::vector<KSReq>& reqs, const 
     const int ndst = (int)out.size();
     const size_t aw = (size_t)2 * npos * N;
     Tmp accs(c, (size_t)ndst * aw);
-    CU(cudaMemsetAsync(accs.p, 0, (size_t)ndst * aw * 8, c->cur));
+    {
+        Prof p(c, "copy", 8.0 * ndst * aw);
+        CU(cudaMemsetAsync(accs.p, 0, (size_t)ndst * aw * 8, c->cur));
+    }
     const int pbase = nq;
+    (void)pbase;
     modup_chunks(c, level, reqs, [&](const std::vector<const KSReq*>& rq, const std::vector<const u64*>& ex) {
+        // the jobs of one sum form one group of the summing inner product
         const int nj = (int)rq.size();
-        Tmp acc(c, (size_t)nj * aw);
-        IPJobs ij;
-        ij.ngroups = 0;
-        for (int j = 0; j < nj; ++j) {
-            ij.j[j] = IPJob{ex[j], rq[j]->key, acc.p + (size_t)j * aw, rq[j]->galois, 0};
-            if (j == 0 || rq[j]->key != rq[j - 1]->key) {
-                ij.gkey[ij.ngroups] = rq[j]->key;
-                ij.gstart[ij.ngroups] = j;
-                ij.ngroups++;
-            }
-        }
-        ij.gstart[ij.ngroups] = nj;
-        {
-            Prof p(c, "ip", 8.0 * N * npos * (ij.ngroups * 2.0 * beta + nj * (double)beta + nj * 2.0));
-            launch_ip(ij, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, level), c->R.logN,
-                      c->cur);
-            c->launches++;
-        }
-        AccJobs aj;
-        aj.n = nj;
+        std::vector<int> ord(nj);
         for (int j = 0; j < nj; ++j) {
             if (rq[j]->sum_dst < 0 || rq[j]->sum_dst >= ndst) raise(FR_ERR_INTERNAL, "sum index out of range");
-            aj.j[j] = AccJob{acc.p + (size_t)j * aw, rq[j]->add, rq[j]->galois, rq[j]->sum_dst};
+            ord[j] = j;
         }
-        Prof p(c, "misc", 8.0 * N * (nj * (aw / N + (double)(level + 1)) + 2.0 * ndst * (aw / N)));
-        launch_giant_acc(aj, accs.p, npos, level, c->d_primes, pbase, c->d_pmod, c->d_pmod_s, c->R.logN, c->cur);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return rq[a]->sum_dst < rq[b]->sum_dst; });
+        IPSumJobs ij;
+        ij.ngroups = 0;
+        std::vector<const u64*> keys, exts;
+        for (int t = 0; t < nj; ++t) {
+            const KSReq* r = rq[ord[t]];
+            ij.j[t] = IPJob{ex[ord[t]], r->key, accs.p + (size_t)r->sum_dst * aw, r->galois, 0, r->add};
+            if (t == 0 || r->sum_dst != rq[ord[t - 1]]->sum_dst) ij.gstart[ij.ngroups++] = t;
+            if (std::find(keys.begin(), keys.end(), r->key) == keys.end()) keys.push_back(r->key);
+            if (std::find(exts.begin(), exts.end(), ex[ord[t]]) == exts.end()) exts.push_back(ex[ord[t]]);
+        }
+        ij.gstart[ij.ngroups] = nj;
+        // key words once per distinct key, ext once per distinct input, c0 gathers on the Q
+        // positions, accumulators read and written
+        Prof p(c, "ip", 8.0 * N * (npos * (keys.size() * 2.0 * beta + exts.size() * (double)beta + 4.0 * ij.ngroups) +
+                                   (double)nj * (level + 1)));
+        launch_ip_sum(ij, beta, npos, level, c->key_level + 1, c->key_limbs, c->d_primes, pm_ext(c, level), c->R.logN,
+                      c->d_pmod, c->d_pmod_s, c->cur);
         c->launches++;
     });
     // one ModDown per sum: P limbs to coefficients, P -> Q conversion, forward NTT + combine
@@ -554,12 +584,11 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     if (level < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
     const int N = c->R.N, l = level;
     Tmp last(c, (size_t)2 * B * N);
-    CU(cudaMemcpy2DAsync(last.p, (size_t)N * 8, in + (size_t)l * N, (size_t)in_cap * N * 8, (size_t)N * 8,
-                         2 * (size_t)B, cudaMemcpyDeviceToDevice, c->cur));
     PrimeMap one{};
     one.period = 1;
     one.idx[0] = (unsigned char)l;
-    ntt(c, last.p, N, 1, 2 * B, one, true);
+    // the last limb of every component, to coefficients (read in place)
+    ntt_from(c, in + (size_t)l * N, (long long)in_cap * N, last.p, N, 1, 2 * B, one, true);
     Tmp lifted(c, (size_t)2 * B * l * N);
     {
         Prof p(c, "rescale", 8.0 * N * 2 * B * (1.0 + l));
@@ -571,6 +600,34 @@ void rescale(fr_ctx* c, const u64* in, int B, int level, int in_cap, u64* out, i
     PolyBatch pb{lifted.p, (long long)l * N, l, 2 * B * l, pm_level(l - 1)};
     launch_ntt_rescale(c->rd, pb, in, in_cap, out, out_cap, c->d_rescale[l], l, ep.mode, ep.add, ep.add_cap, ep.add_bs,
                        ep.cres, c->cur);
+    c->launches += 2;
+}
+
+// Rescale(T1 round(c1 Delta) + round(c0 Delta) Delta) for nl leaves of each of B cts T1 at level
+// l (x: [B][2][x_cap][N]; constants cc [3][nl][l + 1] as cheb_consts lays them out) -> out
+// [B nl][2][out_cap][N] at level l - 1, without the leaves in memory: the inverse NTT of T1's last
+// limb, the leaves' lifted last limbs from it, and one forward NTT whose epilogue forms each leaf
+// limb from T1 and rescales it. Bit for bit the leaves stored, then rescaled.
+void leaves_rescaled(fr_ctx* c, const u64* x, int B, int x_cap, int l, int nl, const u64* cc, u64* out,
+                     int out_cap) {
+    if (l < 1) raise(FR_ERR_LEVEL, "rescale needs level >= 1");
+    const int N = c->R.N, L1 = l + 1;
+    const u64 *cb = cc, *cb_s = cc + (size_t)nl * L1, *ca = cc + (size_t)2 * nl * L1;
+    PrimeMap one{};
+    one.period = 1;
+    one.idx[0] = (unsigned char)l;
+    Tmp u(c, (size_t)2 * B * N);
+    ntt_from(c, x + (size_t)l * N, (long long)x_cap * N, u.p, N, 1, 2 * B, one, true);
+    Tmp lifted(c, (size_t)B * nl * 2 * l * N);
+    {
+        Prof p(c, "rescale", 8.0 * N * B * 2.0 * (1.0 + (double)nl * l));
+        launch_leaf_lift(u.p, cb, cb_s, ca, nl, L1, lifted.p, c->d_rescale[l], c->R.primes[l], l, N, B, c->cur);
+        c->launches++;
+    }
+    Prof p(c, "ntt", 16.0 * B * nl * 2 * l * N);
+    PolyBatch pb{lifted.p, (long long)l * N, l, B * nl * 2 * l, pm_level(l - 1)};
+    launch_ntt_leaf_rescale(c->rd, pb, x, ctw(c, x_cap), x_cap, cb, cb_s, ca, nl, L1, out, out_cap, c->d_rescale[l], l,
+                            c->cur);
     c->launches += 2;
 }
 
@@ -735,7 +792,7 @@ const u64* cheb_consts(fr_ctx* c, int ls) {
 }
 
 // Constants of the hybrid comparator's scaled copies at input level l, laid out for
-// launch_cheb_leaves: [3][5][l+1] (round(a_k Delta) residues, their Shoup quotients, and the
+// leaves_rescaled: [3][5][l+1] (round(a_k Delta) residues, their Shoup quotients, and the
 // constant round(Delta / 2) Delta in copy 0), a_k = 315, -420, 378, -180, 35 over 256.
 const u64* f4_consts(fr_ctx* c, int l) {
     auto it = c->d_f4.find(l);
@@ -814,20 +871,8 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     }
     c->cur = side;
     // leaves: Rescale(T_1 round(c1 Delta) + round(c0 Delta) Delta)
-    const u64* cc = cheb_consts(c, ls);
-    const int L1 = ls + 1;
     std::unique_ptr<Tmp> v(new Tmp(c, (size_t)B * nleaves * ctw(c, ls)));
-    {
-        Tmp pre(c, (size_t)B * nleaves * ctw(c, ls + 1));
-        for (int b = 0; b < B; ++b) {
-            Prof p(c, "misc");
-            launch_cheb_leaves(x + (size_t)b * ctw(c, x_cap), x_cap, pre.p + (size_t)b * nleaves * ctw(c, ls + 1),
-                               ls + 1, ls, nleaves, cc, cc + (size_t)nleaves * L1, cc + (size_t)2 * nleaves * L1,
-                               c->d_primes, N, c->cur);
-            c->launches++;
-        }
-        rescale(c, pre.p, B * nleaves, ls, ls + 1, v->p, ls);
-    }
+    leaves_rescaled(c, x, B, x_cap, ls, nleaves, cheb_consts(c, ls), v->p, ls);
     int vcap = ls;
     // tree: parents i = child(2i) * T_{2^s} + child(2i+1)
     for (int s = 1; s < d2; ++s) {
@@ -880,16 +925,7 @@ void comparator_f4(fr_ctx* c, const u64* y, int B, int l, int y_cap, u64* out, i
         mul_relin_rescale(c, l, A, y_cap, A, y_cap, Y2.p, cap, (long long)cw);
     }
     Tmp U(c, (size_t)B * 5 * cw);  // [B][5]: y, y^3, y^5, y^7, y^9 scalars (u1 with the constant 1/2)
-    {
-        Tmp pre(c, (size_t)B * 5 * cw);
-        for (int b = 0; b < B; ++b) {
-            Prof p(c, "misc");
-            launch_cheb_leaves(y + (size_t)b * ctw(c, y_cap), y_cap, pre.p + (size_t)b * 5 * cw, cap, l, 5, cc,
-                               cc + (size_t)5 * L1, cc + (size_t)10 * L1, c->d_primes, c->R.N, c->cur);
-            c->launches++;
-        }
-        rescale(c, pre.p, B * 5, l, cap, U.p, cap);
-    }
+    leaves_rescaled(c, y, B, y_cap, l, 5, cc, U.p, cap);
     auto u = [&](int b, int k) { return U.p + ((size_t)b * 5 + k) * cw; };
     // level l - 1: y4 = y2 y2, t3 = u3 y2, v7 = u7 y2 -> R1 [B][3] at level l - 2
     Tmp R1(c, (size_t)B * 3 * cw);
@@ -1025,6 +1061,32 @@ void encode_group(fr_ctx* c, const float* dT, long long K, long long g, u64* dst
 void rotate_sum(fr_ctx* c, u64* ct, int cap, int level, int B = 1) {
     const int n = c->R.N / 2, N = c->R.N;
     const size_t cw = (size_t)ctw(c, cap);
+    if (c->hoist_sum) {
+        // x <- x + sum_{t=1}^{rr-1} Rot_{t s}(x) with one ModDown per step and ciphertext: the
+        // rr-1 rotations share the ModUp of x.a, their inner products and P sigma_t(x.b) are summed
+        // in Q_l u P, and the ModDown's combine adds x (in place: each word of x is read and
+        // written by the same thread of the last launch)
+        const int r = std::max(2, c->sum_radix);
+        for (long st = 1; st < n; st *= r) {
+            const int rr = (int)std::min<long>(r, n / st);
+            std::vector<KSReq> reqs;
+            std::vector<const u64*> base;
+            std::vector<u64*> outs;
+            for (int b = 0; b < B; ++b) {
+                u64* x = ct + (size_t)b * cw;
+                base.push_back(x);
+                outs.push_back(x);
+                for (int t = 1; t < rr; ++t) {
+                    const u64 g = frh::galois_of_rotation(c->R, (long)t * st);
+                    KSReq rq{x + (size_t)cap * N, rot_key(c, g), (u32)g, 1, x, cap, nullptr, 0};
+                    rq.sum_dst = b;
+                    reqs.push_back(rq);
+                }
+            }
+            keyswitch_sums(c, level, reqs, base, cap, outs, cap);
+        }
+        return;
+    }
     if (c->sum_radix > 2) {
         // radix r: x <- x + sum_{t=1}^{rr-1} Rot_{t s}(x), s = 1, r, r^2, ..., rr = min(r, n / s).
         // The rr-1 rotations of a ciphertext share one ModUp (hoisting); each lands in its slot
@@ -1393,6 +1455,8 @@ fr_status fr_setup(const fr_params* prm, fr_ctx** out) {
         c->hoist_giants = prm->hoist_giants == 1;
         if (prm->hoist_babies > 1) raise(FR_ERR_INVALID_ARG, "hoist_babies must be 0 or 1");
         c->hoist_babies = prm->hoist_babies == 1;
+        if (prm->hoist_sum > 1) raise(FR_ERR_INVALID_ARG, "hoist_sum must be 0 or 1");
+        c->hoist_sum = prm->hoist_sum == 1;
         if (c->sum_radix < 2 || c->sum_radix > 64 || (c->sum_radix & (c->sum_radix - 1)))
             raise(FR_ERR_INVALID_ARG, "sum_radix must be 0 or a power of two in [2, 64]");
         c->work_level = c->R.nq - 1;
@@ -2217,15 +2281,25 @@ void ondemand_scores(fr_ctx* c, const BatchPlan& P, const u64* q, const std::vec
             for (int t = 0, e = 0; t < nb; ++t) {
                 const int b = sel[s0 + t];
                 const fr_db* d = P.dbs[qs[b]];
-                // up to 4 queries against the same diagonals (consecutive babies) share one ring
-                // launch that reads each diagonal word once for all of them; a single query runs
-                // k_mac below (its register pipeline measured faster for one query)
+                // up to 4 queries against the same diagonals (consecutive babies) share one launch
+                // that reads each diagonal word once for all of them: the persistent pipeline
+                // k_mac_ring where its tiling fits, else k_mac_pipe. A single query runs k_mac
+                // below (measured faster for one query: 0.98 ms against 1.13 ms at the headline)
                 int cnt = 1;
-                if (d->tier != 4 && mac_pipe_fits(n1, ell, N))
+                if (d->tier != 4 && (mac_ring_fits(n1, ell, N, 2) || mac_pipe_fits(n1, ell, N)))
                     while (cnt < 4 && t + cnt < nb && sel[s0 + t + cnt] == b + cnt &&
                            diag_of(P.dbs[qs[b + cnt]]) == diag_of(d))
                         ++cnt;
-                if (cnt > 1) {
+                if (d->tier != 4 && cnt > 1 && mac_ring_fits(n1, ell, N, cnt)) {
+                    Prof p(c, "mac", 8.0 * N * nlx * ((double)ell + cnt * (2.0 * n1 + 2.0 * n2)));
+                    launch_mac_ring(babies.p + (size_t)b * n1 * bw, (long long)n1 * bw, nlx, diag_of(d),
+                                    Pj.p + (size_t)t * n2 * bw, (long long)n2 * bw, nlx, nlx, n1, ell, cnt, mprimes, N,
+                                    c->cur);
+                    c->launches++;
+                    t += cnt - 1;
+                    continue;
+                }
+                if (cnt > 1 && mac_pipe_fits(n1, ell, N)) {
                     Prof p(c, "mac", 8.0 * N * nlx * ((double)ell + cnt * (2.0 * n1 + 2.0 * n2)));
                     launch_mac_pipe(babies.p + (size_t)b * n1 * bw, (long long)n1 * bw, nlx, diag_of(d),
                                     Pj.p + (size_t)t * n2 * bw, (long long)n2 * bw, nlx, nlx, n1, ell, cnt, mprimes, N,
@@ -3095,6 +3169,13 @@ fr_status fr_profile(fr_ctx* c, int enable) {
     });
 }
 
+fr_status fr_profile_only(fr_ctx* c, const char* prefix) {
+    return guard([&] {
+        if (!c) raise(FR_ERR_INVALID_ARG, "null argument");
+        c->prof_only = prefix ? prefix : "";
+    });
+}
+
 fr_status fr_profile_read(fr_ctx* c, const char* region, double* ms, uint64_t* launches, uint64_t* bytes) {
     return guard([&] {
         if (!c || !region) raise(FR_ERR_INVALID_ARG, "null argument");
@@ -3325,7 +3406,7 @@ extern "C" fr_status fr_rotate_noalloc(fr_ctx* c, const uint64_t* d_in, uint32_t
         CU(cudaMemcpyAsync(a, d_in + L1N, L1N * 8, cudaMemcpyDeviceToDevice, st));
         const PrimeMap pl = pm_level(l);
         launch_ntt(c->rd, PolyBatch{e, (long long)N, 2 * (l + 1), 2 * (l + 1), pl}, false, st);
-        launch_modup(a, e + L1N, 0, ext, c->d_modup[l], beta, npos, N, 1, st);
+        launch_modup(a, 0, e + L1N, 0, ext, c->d_modup[l], beta, npos, N, 1, st);
         launch_ntt(c->rd, PolyBatch{ext, (long long)beta * npos * N, 1, c->modup_ntt_n[l], PrimeMap{},
                                     c->d_modup_ntt[l], c->modup_ntt_n[l]},
                    false, st);

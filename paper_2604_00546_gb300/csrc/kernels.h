@@ -80,6 +80,10 @@ struct PolyBatch {
     PrimeMap pm;
     const int* tab = nullptr;
     int tab_n = 0;
+    // optional source of the first pass (out of place): poly p read from
+    // src + (p / inner) src_outer + (p % inner) N and written to its place in base
+    const u64* src = nullptr;
+    long long src_outer = 0;
 };
 
 // NTT batch-size buckets for the tuned tile shapes: <= 4, <= 16, <= 64, larger.

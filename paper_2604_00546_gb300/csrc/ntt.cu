@@ -37,6 +37,11 @@ __device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* p
     return b.base + (long long)(p / b.inner) * b.outer + (long long)(p % b.inner) * N;
 }
 
+// where the first pass reads poly p: its source when the batch has one, else its place
+__device__ __forceinline__ const u64* poly_in(const PolyBatch& b, int p, int N, const u64* x) {
+    return b.src ? b.src + (long long)(p / b.inner) * b.src_outer + (long long)(p % b.inner) * N : x;
+}
+
 __device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 ws, u64 q) {
     return x * w - __umul64hi(x, ws) * q;  // in [0, 2q)
 }
@@ -206,9 +211,10 @@ __global__ void __launch_bounds__(KTC * (1 << LOG) / 8, 5) k_ntt_col(const __gri
     const int gcol = blockIdx.x * KTC + col;
     constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
     constexpr int LL = LastLo<LOG, INV>::v;
+    const u64* xin = INV ? x : poly_in(b, p, N, x);  // the column pass is the forward transform's first
     u64 v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = x[(long long)phase_x<L0>(tau, e) * C + gcol];
+    for (int e = 0; e < 8; ++e) v[e] = xin[(long long)phase_x<L0>(tau, e) * C + gcol];
     __syncthreads();
     Ctx<false> c{0, S, sw, q, q < (1ull << 57)};
     ColEx<KTC> ex{sm, col};
@@ -283,6 +289,31 @@ struct EpiRescale {
     }
 };
 
+// Rescale of the Chebyshev leaves Rescale(T1 cb_j + ca_j) without the leaves in memory: poly
+// p = ((b nl + j) 2 + t) l + i of the lifted last limbs; the leaf's limb i,
+// x_i cb_{j,i} (+ ca_{j,i} on component 0), is formed from T1 (query b at x + b x_bs) with the
+// same operations as the leaf kernel that stores it, then out = (leaf_i - v) q_l^-1, leaf (b, j)
+// at out + (b nl + j) 2 out_cap N. Bit for bit the leaves stored, then rescaled.
+struct EpiLeafRescale {
+    const u64* x;
+    long long x_bs;
+    int x_cap;
+    const u64* cb;      // [nl][L1] residues of round(c1 Delta)
+    const u64* cb_s;    // their Shoup quotients
+    const u64* ca;      // [nl][L1] residues of round(c0 Delta) Delta
+    int nl, L1;
+    u64* out;
+    int out_cap;
+    const RescaleTab* tab;
+    int l, N;
+    __device__ __forceinline__ void put(int p, int k, u64 v, u64 q) const {
+        const int bjt = p / l, i = p % l, t = bjt & 1, bj = bjt >> 1, j = bj % nl, b = bj / nl;
+        u64 a = mul_shoup(x[(long long)b * x_bs + ((long long)t * x_cap + i) * N + k], cb[j * L1 + i], cb_s[j * L1 + i], q);
+        if (t == 0) a = add_mod(a, ca[j * L1 + i], q);
+        out[((long long)bjt * out_cap + i) * N + k] = mul_shoup(sub_mod(a, v, q), tab->qlinv[i], tab->qlinv_s[i], q);
+    }
+};
+
 // Relinearisation ModDown fused with the rescale after it (the product of two ciphertexts at
 // level l, relinearised, then divided by q_l): poly p = (job j, component t, limb i < l) of
 // y = conv P^-1 + lift, where conv is the ModDown's P -> Q conversion and lift the centered last
@@ -341,11 +372,12 @@ __global__ void __launch_bounds__(RT, RT == 128 ? 9 : 4) k_ntt_row(const __grid_
     const int rho = blockIdx.x * RPC + rloc;
     const int Jbase = rho * S;
     u64* xr = x + Jbase;
+    const u64* xin = (INV ? poly_in(b, p, N, x) : x) + Jbase;  // the row pass is the inverse's first
     constexpr int L0 = PhaseInfo<LOG, INV, 0>::LO;
     constexpr int LL = LastLo<LOG, INV>::v;
     u64 v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = xr[phase_x<L0>(tau, e)];
+    for (int e = 0; e < 8; ++e) v[e] = xin[phase_x<L0>(tau, e)];
     const bool grow = q < (1ull << 57);
     Ctx<true> c{Jbase, N, tw, q, grow};
     RowEx ex{sm + rloc * SP};
@@ -793,6 +825,19 @@ double measure_butterfly_peak(int device) {
 template <class E>
 void launch_ntt_e(const RingDev& R, const PolyBatch& b, bool inverse, cudaStream_t s, const E& epi) {
     if (b.npolys <= 0) return;
+    if (b.src) {
+        // the radix-8 two-pass kernels read a source themselves; for the cluster and radix-16
+        // shapes (and a table-mapped batch) the source is copied into place first
+        const int shape = R.logN >= 15 ? R.ntt_shape[ntt_bucket(b.npolys)] : 0;
+        if (b.tab || shape == 4 || shape == 5) {
+            cudaMemcpy2DAsync(b.base, (size_t)b.outer * 8, b.src, (size_t)b.src_outer * 8, (size_t)b.inner * R.N * 8,
+                              (size_t)(b.npolys / b.inner), cudaMemcpyDeviceToDevice, s);
+            PolyBatch c = b;
+            c.src = nullptr;
+            launch_ntt_e(R, c, inverse, s, epi);
+            return;
+        }
+    }
     switch (R.logN) {
         case 10: launch_ntt_t<5, 5, E, 4, 128>(R, b, inverse, s, epi); break;
         case 11: launch_ntt_t<5, 6, E, 4, 128>(R, b, inverse, s, epi); break;
@@ -878,6 +923,13 @@ void launch_ntt_relin_rescale(const RingDev& R, const PolyBatch& b, const u64* a
                               long long out_bs, int mode, const u64* add, int add_cap, long long add_bs,
                               const u64* cres, cudaStream_t s) {
     EpiRelinRescale e{acc, d, out, tab, pinv, pinv_s, npos, l, R.N, out_cap, mode, out_bs, add, add_cap, add_bs, cres};
+    launch_ntt_e(R, b, false, s, e);
+}
+
+void launch_ntt_leaf_rescale(const RingDev& R, const PolyBatch& b, const u64* x, long long x_bs, int x_cap,
+                             const u64* cb, const u64* cb_s, const u64* ca, int nl, int L1, u64* out, int out_cap,
+                             const RescaleTab* tab, int l, cudaStream_t s) {
+    EpiLeafRescale e{x, x_bs, x_cap, cb, cb_s, ca, nl, L1, out, out_cap, tab, l, R.N};
     launch_ntt_e(R, b, false, s, e);
 }
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "fr_setup", "fr_required_rotations", "fr_rotation_set", "fr_rotation_count", "fr_keygen", "fr_load_keys",
     "fr_load_db", "fr_encrypt_db", "fr_load_db_encrypted", "fr_db_info", "fr_encrypt", "fr_encrypt_slots", "fr_match", "fr_match_batch", "fr_match_multi", "fr_set_db_tier", "fr_decrypt", "fr_ct_export", "fr_ct_import",
     "fr_ct_info", "fr_ct_upload", "fr_rotate", "fr_rotate_hoisted", "fr_rotate_noalloc", "fr_rescale", "fr_mul_relin", "fr_add",
-    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_launch_count", "fr_butterfly_peak", "fr_fp64_peak", "fr_ntt_time", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
+    "fr_chebyshev", "fr_rotate_sum", "fr_membership_reduce", "fr_sync", "fr_profile", "fr_profile_read", "fr_profile_only", "fr_launch_count", "fr_butterfly_peak", "fr_fp64_peak", "fr_ntt_time", "fr_use_graphs", "fr_inject_alloc_failure", "fr_ntt_tuning", "fr_ntt_set_shapes",
     "fr_ctx_primes", "fr_ctx_info", "fr_work_level", "fr_cheb_coeffs", "fr_cheb_coeffs_lo", "fr_free_ct", "fr_free_cts", "fr_free_keys", "fr_free_db",
     "fr_free", "fr_last_error", "fr_serve_start", "fr_serve_stop", "fr_match_submit", "fr_match_poll",
     "fr_serve_stats", "fr_serve_plan",
@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("hbm_budget_bytes", C.c_uint64), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("db_tier", C.c_uint32), ("level_mode", C.c_uint32), ("sum_radix", C.c_uint32),
         ("hoist_giants", C.c_uint32), ("comparator", C.c_uint32), ("hoist_babies", C.c_uint32),
+        ("hoist_sum", C.c_uint32),
     ]
 
 
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
         "fr_membership_reduce": (st, [vp, C.POINTER(vp), C.c_size_t, C.POINTER(vp)]),
         "fr_sync": (st, [vp]),
         "fr_profile": (st, [vp, C.c_int]),
+        "fr_profile_only": (st, [vp, C.c_char_p]),
         "fr_profile_read": (st, [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_uint64)]),
         "fr_launch_count": (C.c_uint64, [vp]),
@@ -227,14 +229,14 @@ class Context:
 
     def __init__(self, log_n, q_bits, p_bits, dnum, scale_bits, ell, n1, cheb_degree=0, threshold=0.5,
                  hbm_budget_bytes=0, device=0, cuda_stream=None, schedule=0, level_mode=0, db_tier=0, sum_radix=0,
-                 hoist_giants=0, comparator=0, hoist_babies=0):
+                 hoist_giants=0, comparator=0, hoist_babies=0, hoist_sum=0):
         L = load()
         self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
         self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
         self.params = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, dnum, scale_bits, ell, n1,
                              schedule, cheb_degree, threshold, hbm_budget_bytes, device,
                              C.c_void_p(cuda_stream) if cuda_stream else None, db_tier, level_mode, sum_radix,
-                             int(hoist_giants), int(comparator), int(hoist_babies))
+                             int(hoist_giants), int(comparator), int(hoist_babies), int(hoist_sum))
         h = C.c_void_p()
         self._live = 0          # library objects of this context still alive
         self._closing = False
@@ -498,6 +500,9 @@ class Context:
 
     def profile(self, enable):
         _check(_lib.fr_profile(self.h, 1 if enable else 0))
+
+    def profile_only(self, prefix=""):
+        _check(_lib.fr_profile_only(self.h, (prefix or "").encode()))
 
     def profile_read(self, region):
         ms, n, b = C.c_double(), C.c_uint64(), C.c_uint64()

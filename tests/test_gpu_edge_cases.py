@@ -102,3 +102,27 @@ def test_refusals():
     with pytest.raises(fr.FrError) as e:
         ctx.match(db, q, fr.FR_MODE_MEMBERSHIP)
     assert e.value.status == fr.FR_ERR_INVALID_ARG
+
+
+def test_profile_only_times_one_region_class(orc):
+    # a profiled match with a region filter times that class only (and the whole replay); the
+    # outputs are the same bits as unprofiled
+    ctx, keys = make()
+    T = W.templates(300, C["ell"], 15)
+    db = ctx.load_db(T)
+    q = ctx.encrypt(keys, query(6), 6)
+    ref = [o.export() for o in ctx.match(db, q, fr.FR_MODE_SCORES)]
+    for only in ("ntt", "ip", ""):
+        ctx.profile_only(only)
+        ctx.profile(True)
+        out = ctx.match(db, q, fr.FR_MODE_SCORES)
+        ms_ntt, n_ntt, _ = ctx.profile_read("ntt")
+        ms_ip, n_ip, _ = ctx.profile_read("ip")
+        ms_match, n_match, _ = ctx.profile_read("match")
+        ctx.profile(False)
+        assert len(out) == len(ref) and all(np.array_equal(o.export(), r) for o, r in zip(out, ref))
+        assert n_match == 1 and ms_match > 0
+        assert (n_ntt > 0) == (only in ("ntt", ""))
+        assert (n_ip > 0) == (only in ("ip", ""))
+        assert ms_ntt + ms_ip <= ms_match
+    ctx.profile_only("")
