@@ -674,6 +674,38 @@ def run_tensor_probe(args):
     return line
 
 
+def run_mac_small(args):
+    """The batched diagonal MAC on a small case, for profiling: N = 2^13, Q = 60 + 4 x 45, P = 3 x 60,
+    ell = 512, n1 = 32 (the headline's BSGS split), baby steps in Q_l u P, 4096 seeded templates,
+    4 queries per fr_match_batch (scores). About 2 GB on the device; the diagonals (268 MB) are
+    twice the L2. Returns the batch time."""
+    import torch
+
+    from paper_2604_00546_gb300 import fr
+    from paper_2604_00546_gb300 import workloads as W
+    cfg = dict(log_n=13, q_bits=[60] + [45] * 4, p_bits=[60, 60, 60], dnum=2, scale_bits=45, ell=512, n1=32,
+               cheb_degree=0, threshold=0.5)
+    ctx = fr.Context(device=0, hoist_babies=1, **cfg)
+    keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_SCORES), 0x5EED0A11)
+    ctx.load_keys(keys)
+    db = ctx.load_db(W.templates(4096, cfg["ell"], 21))
+    rng = np.random.default_rng(1)
+    qs = []
+    for i in range(4):
+        q = rng.standard_normal(cfg["ell"])
+        qs.append(ctx.encrypt(keys, q / np.linalg.norm(q), 900 + i))
+    ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = ctx.match_batch(db, qs, fr.FR_MODE_SCORES)
+        ctx.sync()
+        ms.append(1000.0 * (time.perf_counter() - t0))
+    free, total = torch.cuda.mem_get_info(0)
+    return {"mode": "mac-small", "queries": len(qs), "outputs": len(outs), "batch_ms": ms,
+            "device_gb": (total - free) / 1e9}
+
+
 def run_ntt_sweep(args):
     """The batched NTT alone (fr_ntt_time) at the headline ring (N = 2^16, working level 8,
     shapes picked by the tuner): microseconds per forward and inverse launch sequence and
@@ -739,7 +771,13 @@ def run_reference(args):
 # the CUDA sources whose combined SHA-256 (csrc_sha256) is listed: then the regions of the bench
 # line are these shares of the timed step; otherwise they come from the profiled replays and the
 # NTT traffic is null.
-LAUNCH_LIST = {"sha256": [], "share": {}, "ntt_dram_per_alg_byte": None}
+LAUNCH_LIST = {
+    "sha256": ["e6eca046581744169865270da076e9d026c2d88995e4ae21bf5f68a8090fb86f"],
+    "share": {"ntt": 0.5488, "mac": 0.1411, "ip": 0.1203, "modup": 0.0549, "moddown": 0.0519, "rescale": 0.0498,
+              "tensor": 0.0327, "misc": 0.0007, "copy": 0.0},
+    "ntt_dram_per_alg_byte": 1.685,
+    "keyswitch_dram_gbs": 2920.8,
+}
 
 # kernel name prefix -> region class, for reading a launch list
 KERNEL_CLASS = (("k_ntt", "ntt"), ("k_modup", "modup"), ("k_ip", "ip"), ("k_baby0_pq", "ip"), ("k_p2q", "moddown"),
@@ -762,6 +800,25 @@ def csrc_sha256():
 
 def launch_list_valid():
     return bool(LAUNCH_LIST["share"]) and csrc_sha256() in LAUNCH_LIST["sha256"]
+
+
+def keyswitch_entry(regions, hbm_peak, hbm_kind):
+    """Aggregate rate of the key switches' memory-bound kernels (ModUp base conversion, inner
+    products, ModDown base conversion): their algorithmic bytes over their time in the step, and,
+    from the committed launch list when it matches the sources, the DRAM bytes those kernels
+    moved over their durations. Their NTTs are arithmetic-bound and counted with the NTT."""
+    parts = ("modup", "ip", "moddown")
+    ms = sum(regions[r]["ms"] for r in parts)
+    by = sum(regions[r]["bytes"] for r in parts)
+    gbs = by / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+    e = {"kernels": "k_modup, k_ip, k_ip_sum, k_baby0_pq, k_p2q", "ms_per_step": ms, "algorithmic_bytes": by,
+         "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": hbm_kind,
+         "dram_view": None}
+    if launch_list_valid() and LAUNCH_LIST.get("keyswitch_dram_gbs"):
+        g = LAUNCH_LIST["keyswitch_dram_gbs"]
+        e["dram_view"] = {"achieved": g, "frac": g / hbm_peak,
+                          "source": "DRAM bytes / durations of those launches in the committed launch list"}
+    return e
 
 
 def roofline(regions, log_n, device, fr):
@@ -1126,6 +1183,7 @@ def run_ours(args):
             "regions_hbm_gbs": {r: (regions[r]["bytes"] / (regions[r]["ms"] / 1000.0) / 1e9 if regions[r]["ms"] > 0
                                     else 0.0) for r in regions},
             "stages_ms_per_step": stages,
+            "keyswitch": keyswitch_entry(regions, *load_peaks()),
             "gpu_launches": int(n_launch),
             "ntt_autotune": ctx.ntt_tuning(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -1182,6 +1240,8 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-comparator comparison")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the batched NTT alone per batch size instead")
     ap.add_argument("--ntt-sizes", type=int, nargs="+", default=[1, 4, 16, 30, 64, 128, 248, 512, 1024])
+    ap.add_argument("--mac-small", action="store_true",
+                    help="run the batched MAC on a small case (N = 2^13, 4 queries) instead, for profiling")
     ap.add_argument("--ell", type=int, default=0,
                     help="template dimension of the membership workload (0: 512); smaller cases for profiling")
     ap.add_argument("--tensor-probe", action="store_true",
@@ -1207,6 +1267,8 @@ def main():
         print(json.dumps(run_tensor_probe(args)), flush=True)
     elif args.ntt_sweep:
         print(json.dumps(run_ntt_sweep(args)), flush=True)
+    elif args.mac_small:
+        print(json.dumps(run_mac_small(args)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -623,11 +623,11 @@ struct MrCursor {
     int m, sl, slot, tile, i, k0;
 };
 
-template <int B>
+template <int B, int N1>
 __global__ void __launch_bounds__(kMrTP * kMrJG) k_mac_ring(const u64* __restrict__ babies, long long baby_q,
                                                             int cap_b, const u64* __restrict__ diags,
                                                             u64* __restrict__ out, long long out_q, int cap_o, int nl,
-                                                            int n1, int n2, const DevPrime* __restrict__ primes,
+                                                            int n2, const DevPrime* __restrict__ primes,
                                                             int N) {
     pdl_wait();
     pdl_trigger();
@@ -636,15 +636,15 @@ __global__ void __launch_bounds__(kMrTP * kMrJG) k_mac_ring(const u64* __restric
     constexpr int CHUNKS = ROWS * TP / 2;  // 16-byte chunks per stage
     static_assert(CHUNKS % NT == 0, "whole chunks per thread");
     extern __shared__ __align__(16) u64 smr[];
-    const int qw = n1 * 2 * TP;            // words of one query's babies in a tile
-    const int bw = B * qw;                 // words of one tile's babies
-    u64* bb = smr;                         // [2][B][n1][2][TP]
+    constexpr int qw = N1 * 2 * TP;        // words of one query's babies in a tile
+    constexpr int bw = B * qw;             // words of one tile's babies
+    u64* bb = smr;                         // [2][B][N1][2][TP]
     u64* sd = bb + 2 * (size_t)bw;         // ring [NS][JG][SD][TP]
     const int pl = threadIdx.x % TP, jg = threadIdx.x / TP;
     const int tpl = N / TP;                // tiles per limb
     const int ntile = nl * tpl;
     const int mt = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int spb = n1 / SD;               // stages per giant-step block
+    constexpr int spb = N1 / SD;           // stages per giant-step block
     const int nst = (n2 / JG) * spb;       // stages per tile
     const long long dstep = (long long)nl * N;  // one diagonal
     auto at_tile = [&](MrCursor& c) {
@@ -664,13 +664,13 @@ __global__ void __launch_bounds__(kMrTP * kMrJG) k_mac_ring(const u64* __restric
         if (c.m < mt) {
             const int jb = c.sl / spb, i0 = (c.sl - jb * spb) * SD;
             u64* dst = sd + (size_t)c.slot * ROWS * TP;
-            const u64* src = diags + ((long long)jb * JG * n1 + i0) * dstep + (long long)c.i * N + c.k0;
+            const u64* src = diags + ((long long)jb * JG * N1 + i0) * dstep + (long long)c.i * N + c.k0;
 #pragma unroll
             for (int r = 0; r < CHUNKS / NT; ++r) {
                 const int ch = threadIdx.x + r * NT;
                 const int row = ch / (TP / 2), w = (ch % (TP / 2)) * 2;
                 const int gg = row / SD, u = row % SD;
-                cp_async16(dst + (size_t)row * TP + w, src + ((long long)gg * n1 + u) * dstep + w);
+                cp_async16(dst + (size_t)row * TP + w, src + ((long long)gg * N1 + u) * dstep + w);
             }
             // the babies of tile 0 ride on its first stage, those of tile m + 1 on tile m's last
             const int mb = (c.m == 0 && c.sl == 0) ? 0 : (c.sl == nst - 1 ? c.m + 1 : -1);
@@ -728,13 +728,13 @@ __global__ void __launch_bounds__(kMrTP * kMrJG) k_mac_ring(const u64* __restric
             }
         }
         // no fold here: a flush adds less than 2^60 to the high word, and a giant step has at
-        // most 8 flushes (n1 <= 64), so the high word is reduced once, before the REDC
+        // most 8 flushes (N1 <= 64), so the high word is reduced once, before the REDC
 #pragma unroll
         for (int qb = 0; qb < B; ++qb) {
             flushk(acc[qb][0], p[qb][0]);
             flushk(acc[qb][1], p[qb][1]);
         }
-        if (i0 + SD == n1) {
+        if (i0 + SD == N1) {
             // giant step jb JG + jg complete for this point: reduce and store
             const DevPrime P = primes[cc.i];
             const int j = jb * JG + jg;
@@ -1243,7 +1243,8 @@ static size_t mac_ring_smem(int B, int n1) {
 }
 
 bool mac_ring_fits(int n1, int ell, int N, int B) {
-    if (n1 <= 0 || n1 % kMpSD != 0 || ell % n1 != 0 || N % kMrTP != 0 || B < 1 || B > 4) return false;
+    // instantiated for n1 = 32 (the headline BSGS split); other splits take k_mac_pipe or k_mac
+    if (n1 != 32 || ell % n1 != 0 || N % kMrTP != 0 || B < 1 || B > 4) return false;
     const int n2 = ell / n1;
     if (n1 > 64 || n2 % kMrJG != 0 || (n2 / kMrJG) * (n1 / kMpSD) < kMrNS) return false;
     return mac_ring_smem(B, n1) <= 200u * 1024;
@@ -1255,16 +1256,16 @@ static void launch_mac_ring_t(const u64* babies, long long baby_q, int cap_b, co
                               cudaStream_t s) {
     const size_t sm = mac_ring_smem(B, n1);
     static std::atomic<unsigned long long> attr{0};
-    smem_limit_once(k_mac_ring<B>, 200 * 1024, attr);
+    smem_limit_once(k_mac_ring<B, 32>, 200 * 1024, attr);
     // persistent grid: as many CTAs as fit on the GPU at once, capped by the tile count
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_ring<B>, kMrTP * kMrJG, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_ring<B, 32>, kMrTP * kMrJG, sm);
     const long long ntile = (long long)nl * (N / kMrTP);
     const int grid = (int)std::min<long long>(ntile, (long long)std::max(1, per) * std::max(1, sms));
-    launch_k(k_mac_ring<B>, dim3(grid), dim3(kMrTP * kMrJG), sm, s, babies, baby_q, cap_b, diags, out, out_q, cap_o,
-             nl, n1, n2, primes, N);
+    launch_k(k_mac_ring<B, 32>, dim3(grid), dim3(kMrTP * kMrJG), sm, s, babies, baby_q, cap_b, diags, out, out_q,
+             cap_o, nl, n2, primes, N);
 }
 
 void launch_mac_ring(const u64* babies, long long baby_q, int cap_b, const u64* diags, u64* out, long long out_q,
