@@ -279,6 +279,20 @@ void ntt_from(fr_ctx* c, const u64* src, long long src_outer, u64* base, long lo
     launch_ntt(c->rd, b, inv, c->cur);
     c->launches += 2;
 }
+// two transforms of the same direction in one launch: n polys of (base, outer, inner, pm), then
+// n2 polys of (base2, outer2, inner2, pm2)
+void ntt_pair(fr_ctx* c, u64* base, long long outer, int inner, int n, const PrimeMap& pm, u64* base2,
+              long long outer2, int inner2, int n2, const PrimeMap& pm2, bool inv) {
+    Prof p(c, "ntt", 16.0 * (n + n2) * c->R.N);
+    PolyBatch b{base, outer, inner, n + n2, pm};
+    b.split = n;
+    b.base2 = base2;
+    b.outer2 = outer2;
+    b.inner2 = inner2;
+    b.pm2 = pm2;
+    launch_ntt(c->rd, b, inv, c->cur);
+    c->launches += 2;
+}
 // forward NTT of the non-own positions of nj ModUp outputs [nj][beta][npos][N]
 void ntt_modup(fr_ctx* c, u64* ext, int nj, int level) {
     const int beta = c->R.digits_at(level), npos = level + 1 + c->R.np;
@@ -674,23 +688,23 @@ void moddown_rescale(fr_ctx* c, int l, u64* acc, const u64* d, int nj, u64* out,
     PrimeMap pmL{};
     pmL.period = 1;
     pmL.idx[0] = (unsigned char)l;
-    // P limbs to coefficients, P -> Q conversion
-    ntt(c, acc + (size_t)(l + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, true);
-    Tmp conv(c, (size_t)nj * 2 * (l + 1) * N);
-    {
-        Prof p(c, "moddown", 8.0 * N * nj * 2.0 * (np + l + 1));
-        launch_p2q(acc, (long long)aw, npos, l, conv.p, c->d_p2q, N, nj, c->cur);
-        c->launches++;
-    }
-    // the last limb of the result before the rescale, to coefficients; the lift; one forward
-    // NTT with the combine as its epilogue
+    // the last limb of the result before the rescale, in evaluation form (it reads only limb l of
+    // acc and d, not the P limbs)
     Tmp z(c, (size_t)nj * 2 * N);
     {
         Prof p(c, "rescale", 8.0 * N * nj * 2.0 * (d ? 3.0 : 2.0));
         launch_rs_last(acc, d, z.p, c->d_pinv, c->d_pinv_s, npos, l, c->d_primes, N, nj, c->cur);
         c->launches++;
     }
-    ntt(c, z.p, N, 1, 2 * nj, pmL, true);
+    // the P limbs and that last limb to coefficients, in one launch; the P -> Q conversion
+    ntt_pair(c, acc + (size_t)(l + 1) * N, (long long)npos * N, np, nj * 2 * np, pmP, z.p, N, 1, 2 * nj, pmL, true);
+    Tmp conv(c, (size_t)nj * 2 * (l + 1) * N);
+    {
+        Prof p(c, "moddown", 8.0 * N * nj * 2.0 * (np + l + 1));
+        launch_p2q(acc, (long long)aw, npos, l, conv.p, c->d_p2q, N, nj, c->cur);
+        c->launches++;
+    }
+    // the lift; one forward NTT with the combine as its epilogue
     Tmp y(c, (size_t)nj * 2 * l * N);
     {
         Prof p(c, "rescale", 8.0 * N * nj * 2.0 * (2.0 + 2.0 * l));
@@ -1526,6 +1540,13 @@ void fr_free(fr_ctx* c) {
     for (auto& e : c->evs) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    // workspaces come from the device's default pool, which keeps what it has reserved while
+    // contexts run (its release threshold is unbounded); a context that goes hands the unused
+    // part back, with the memory its graphs reserved
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaDeviceGraphMemTrim(c->device);
+    cudaGetLastError();
     delete c;
 }
 
@@ -2597,6 +2618,9 @@ void match_queries(fr_ctx* c, const std::vector<const fr_db*>& dbs, const fr_ct*
         CU(cudaEventRecord(pb, c->cur));
         CU(cudaStreamSynchronize(c->cur));
         cudaGraphExecDestroy(exec);
+        // a profiled graph is replayed once: hand the memory its allocations reserved back to
+        // the device, so that repeated profiled matches do not accumulate graph memory
+        cudaDeviceGraphMemTrim(c->device);
         CU(le);
         Region& whole = c->regions["match"];
         whole.pending.emplace_back(pa, pb);

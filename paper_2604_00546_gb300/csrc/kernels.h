@@ -84,6 +84,14 @@ struct PolyBatch {
     // src + (p / inner) src_outer + (p % inner) N and written to its place in base
     const u64* src = nullptr;
     long long src_outer = 0;
+    // optional second segment (no source, no table): polys split .. npolys - 1 live at
+    // base2 + (q / inner2) outer2 + (q % inner2) N, q = p - split, with primes pm2, so the
+    // transforms of two buffers share one launch
+    int split = 0;
+    u64* base2 = nullptr;
+    long long outer2 = 0;
+    int inner2 = 1;
+    PrimeMap pm2{};
 };
 
 // NTT batch-size buckets for the tuned tile shapes: <= 4, <= 16, <= 64, larger.

@@ -28,6 +28,11 @@ namespace {
 
 
 __device__ __forceinline__ u64* poly_at(const PolyBatch& b, int p, int N, int* prime) {
+    if (b.split && p >= b.split) {
+        const int q = p - b.split;
+        *prime = b.pm2.idx[q % b.pm2.period];
+        return b.base2 + (long long)(q / b.inner2) * b.outer2 + (long long)(q % b.inner2) * N;
+    }
     if (b.tab) {
         const int e = p % b.tab_n;
         *prime = __ldg(b.tab + 2 * e + 1);
