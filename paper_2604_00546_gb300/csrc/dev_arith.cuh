@@ -59,17 +59,15 @@ struct Acc3 {
     u64 a0, a1, a2;
 };
 __device__ __forceinline__ u64 split30(u64 x) { return (x & 0x3fffffffull) | ((x >> 30) << 32); }
+// acc += hi 2^64 + lo, one add-with-carry chain
+__device__ __forceinline__ void add128(Acc128& acc, u64 lo, u64 hi) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(acc.lo), "+l"(acc.hi) : "l"(lo), "l"(hi));
+}
 // acc += a0 + a1 2^30 + a2 2^60, then a = 0
 __device__ __forceinline__ void flush30(Acc128& acc, Acc3& a) {
-    u64 lo = a.a0, hi = 0;
-    u64 t = a.a1 << 30;
-    lo += t;
-    hi += (a.a1 >> 34) + (lo < t ? 1ull : 0ull);
-    t = a.a2 << 60;
-    lo += t;
-    hi += (a.a2 >> 4) + (lo < t ? 1ull : 0ull);
-    acc.lo += lo;
-    acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+    add128(acc, a.a0, 0);
+    add128(acc, a.a1 << 30, a.a1 >> 34);
+    add128(acc, a.a2 << 60, a.a2 >> 4);
     a.a0 = a.a1 = a.a2 = 0;
 }
 
