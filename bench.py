@@ -772,11 +772,11 @@ def run_reference(args):
 # line are these shares of the timed step; otherwise they come from the profiled replays and the
 # NTT traffic is null.
 LAUNCH_LIST = {
-    "sha256": ["e6eca046581744169865270da076e9d026c2d88995e4ae21bf5f68a8090fb86f"],
-    "share": {"ntt": 0.5488, "mac": 0.1411, "ip": 0.1203, "modup": 0.0549, "moddown": 0.0519, "rescale": 0.0498,
-              "tensor": 0.0327, "misc": 0.0007, "copy": 0.0},
-    "ntt_dram_per_alg_byte": 1.685,
-    "keyswitch_dram_gbs": 2920.8,
+    "sha256": ["e83981eb595d765bed90a9139d3449d824caba515d54af419ca32f67fcbe0530"],
+    "share": {"ntt": 0.5462, "mac": 0.1369, "ip": 0.1228, "modup": 0.0550, "moddown": 0.0539, "rescale": 0.0513,
+              "tensor": 0.0333, "misc": 0.0007, "copy": 0.0},
+    "ntt_dram_per_alg_byte": 1.760,
+    "keyswitch_dram_gbs": 2946.1,
 }
 
 # kernel name prefix -> region class, for reading a launch list
