@@ -798,8 +798,17 @@ def csrc_sha256():
     return h.hexdigest()
 
 
+# the configuration the launch list was taken on: the headline membership match with the bench's
+# defaults (set by run_ours from its arguments)
+LAUNCH_LIST_CONFIG = {"ell": 512, "level_mode": 1, "sum_radix": 8, "hoist_giants": 1, "hoist_babies": 1, "hoist_sum": 1}
+_RUN_CONFIG = {}
+
+
 def launch_list_valid():
-    return bool(LAUNCH_LIST["share"]) and csrc_sha256() in LAUNCH_LIST["sha256"]
+    """True when the committed launch list describes this run: the same CUDA sources and the
+    headline configuration."""
+    return (bool(LAUNCH_LIST["share"]) and csrc_sha256() in LAUNCH_LIST["sha256"]
+            and _RUN_CONFIG == LAUNCH_LIST_CONFIG)
 
 
 def keyswitch_entry(regions, hbm_peak, hbm_kind):
@@ -876,6 +885,11 @@ def run_ours(args):
         cfg = dict(W.CONFIGS[cfg], ell=args.ell)
     c = W.CONFIGS[cfg] if isinstance(cfg, str) else cfg
     mode = c["mode"]
+    _RUN_CONFIG.clear()
+    if args.config == "membership":
+        _RUN_CONFIG.update({"ell": c["ell"], "level_mode": args.level_mode, "sum_radix": args.sum_radix,
+                            "hoist_giants": args.hoist_giants, "hoist_babies": args.hoist_babies,
+                            "hoist_sum": args.hoist_sum})
     T, q, planted = W.workload(cfg)
     K = len(T)
     t0 = time.perf_counter()
