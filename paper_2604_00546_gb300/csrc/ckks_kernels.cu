@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
     const int jg = threadIdx.x / TP;
     const int k = blockIdx.x * TP + pl;
     const int i = blockIdx.y;
-    const u64 q = primes[i].q, qinv = primes[i].qinv;
+    const u64 q = primes[i].q, qinv = primes[i].qinv, one_s = primes[i].one_s;
+    const bool fold_each = n1 > 64;
     const int per_q = n1 * 2 * TP;
     for (int e = threadIdx.x; e < B * per_q; e += TP * JG) {
         const int b = e / per_q, r = e % per_q;
@@ -461,12 +462,16 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
                 }
             }
         }
+        // a flush adds less than 2^60 to the high word: up to 64 products per giant step (8
+        // flushes) need no fold, and the high word is reduced once before the REDC
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             flushk(acc[b][0], p[b][0]);
             flushk(acc[b][1], p[b][1]);
-            fold(acc[b][0], q);
-            fold(acc[b][1], q);
+            if (fold_each) {
+                fold(acc[b][0], q);
+                fold(acc[b][1], q);
+            }
         }
         // next batch
         int jn = j, in = i0 + 8;
@@ -478,8 +483,8 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 u64* O = out + (long long)b * out_q + (long long)j * 2 * cap_o * N;
-                O[(long long)i * N + k] = redc(acc[b][0].hi, acc[b][0].lo, q, qinv);
-                O[((long long)cap_o + i) * N + k] = redc(acc[b][1].hi, acc[b][1].lo, q, qinv);
+                O[(long long)i * N + k] = redc(mul_shoup(acc[b][0].hi, 1, one_s, q), acc[b][0].lo, q, qinv);
+                O[((long long)cap_o + i) * N + k] = redc(mul_shoup(acc[b][1].hi, 1, one_s, q), acc[b][1].lo, q, qinv);
                 acc[b][0] = acc[b][1] = Acc128{0, 0};
             }
         }

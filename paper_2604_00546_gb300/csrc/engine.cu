@@ -731,7 +731,7 @@ void mul_relin_rescale(fr_ctx* c, int l, const std::vector<const u64*>& A, int a
     const int npos = l + 1 + np;
     const size_t J = A.size();
     const size_t dw = (size_t)3 * (l + 1) * N, aw = (size_t)2 * npos * N;
-    const size_t chunk = 16;
+    const size_t chunk = 32;  // products per key-switch batch (two ModUp chunks of 16 inputs)
     for (size_t j0 = 0; j0 < J; j0 += chunk) {
         const int nj = (int)std::min(chunk, J - j0);
         Tmp d(c, nj * dw);
@@ -2787,7 +2787,8 @@ void match_workspace(const fr_ctx* c, const fr_db* db, fr_mode mode, uint64_t* b
     const double bwq = db->schedule != 1 && c->hoist_babies ? 2.0 * npos * N : cw1;  // one baby / giant-step sum
     if (db->schedule != 1) per += (n1 + n2) * bwq + 2.0 * n2 * cw;
     if (mode != FR_MODE_SCORES) per += G * 54.0 * cw;  // threshold: powers, leaves, tree temporaries
-    double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N;  // key-switch scratch
+    // key-switch scratch: ModUp of 16 inputs, 32 accumulators, 32 tensor products
+    double b = 16.0 * (2.0 * L1 + beta * npos) * N + 32.0 * 2.0 * npos * N + 32.0 * 3.0 * L1 * N;
     if (db->schedule == 1) b += ell * cw1 + G * cw1;
     if (db->tier == 4) per += 3.0 * n2 * L1 * N;  // unrelinearised products of the giant steps
     if (db->tier != 1 && db->tier != 4) b += (db->schedule == 1 ? std::min(G, 8.0) : 1.0) * ell * db->nl * N;
