@@ -391,7 +391,9 @@ __global__ void __launch_bounds__(kThreads) k_tensor(const TensorJobs jobs, int 
 // A CTA owns TP evaluation points of one limb. The n1 baby words (both polys)
 // of its points are staged in shared memory for every query; JG thread groups
 // split the n2 giant steps. Every plaintext diagonal word is read once for all
-// B queries, eight at a time per thread to keep loads in flight.
+// B queries, eight at a time per thread; when every batch of eight is full (n1 a
+// multiple of 8 dividing ell), a word's register is refilled with the next batch's
+// word as soon as it has been multiplied, so the loads stay in flight.
 // ---------------------------------------------------------------------------
 template <int B>
 __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __restrict__ babies, long long baby_q, int cap_b,
@@ -408,11 +410,17 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
     const u64 q = primes[i].q, qinv = primes[i].qinv, one_s = primes[i].one_s;
     const bool fold_each = n1 > 64;
     const int per_q = n1 * 2 * TP;
-    for (int e = threadIdx.x; e < B * per_q; e += TP * JG) {
-        const int b = e / per_q, r = e % per_q;
-        const int ib = r / (2 * TP), t = (r / TP) & 1, pp = r % TP;
-        sb[e] = split30(babies[(long long)b * baby_q + ((long long)ib * 2 + t) * cap_b * N + (long long)i * N +
-                               (long long)blockIdx.x * TP + pp]);
+    // staging: thread (pl, jg) takes point pl of the rows r = 2 i' + t = jg, jg + JG, ... of
+    // every query (no index divisions)
+    {
+        const long long rstep = (long long)cap_b * N;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const u64* src = babies + (long long)b * baby_q + (long long)i * N + k;
+            u64* dst = sb + b * per_q + pl;
+#pragma unroll 8
+            for (int r = jg; r < 2 * n1; r += JG) dst[r * TP] = split30(src[r * rstep]);
+        }
     }
     __syncthreads();
     const long long dstride = (long long)nl * N;
@@ -424,46 +432,20 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
     Acc128 acc[B][2];
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b][0] = acc[b][1] = Acc128{0, 0};
-    for (;;) {
-        const int cnt = min(n1, ell - j * n1);
-        const u64* D = diags + ((long long)j * n1 + i0) * dstride + (long long)i * N + k;
-        const u64* s0 = sbase + i0 * TP2;
-        AccK p[B][2];
+    // the products of one diagonal word d (both polys of every query's baby) into p
+    auto mul_word = [&](AccK (&p)[B][2], u64 d, const u64* sq) {
+        const u64 ds = split30(d);
+        const u32 dsum = sum30(ds);
 #pragma unroll
-        for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = AccK{0, 0, 0};
-        if (i0 + 8 <= cnt) {
-            // full batch: no bounds checks
-            u64 d[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                d[u] = __ldcs(D);
-                D += dstride;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const u64 ds = split30(d[u]);
-                const u32 dsum = sum30(ds);
-                const u64* sq = s0 + u * TP2;
-#pragma unroll
-                for (int b = 0; b < B; ++b) {
-                    mack(p[b][0], ds, dsum, sq[b * per_q]);
-                    mack(p[b][1], ds, dsum, sq[b * per_q + TP]);
-                }
-            }
-        } else {
-            for (int u = 0; i0 + u < cnt; ++u) {
-                const u64 ds = split30(__ldcs(D + (long long)u * dstride));
-                const u32 dsum = sum30(ds);
-                const u64* sq = s0 + u * TP2;
-#pragma unroll
-                for (int b = 0; b < B; ++b) {
-                    mack(p[b][0], ds, dsum, sq[b * per_q]);
-                    mack(p[b][1], ds, dsum, sq[b * per_q + TP]);
-                }
-            }
+        for (int b = 0; b < B; ++b) {
+            mack(p[b][0], ds, dsum, sq[b * per_q]);
+            mack(p[b][1], ds, dsum, sq[b * per_q + TP]);
         }
-        // a flush adds less than 2^60 to the high word: up to 64 products per giant step (8
-        // flushes) need no fold, and the high word is reduced once before the REDC
+    };
+    // after a batch of giant step j: add its sums (a flush adds less than 2^60 to the high word,
+    // so up to 64 products per giant step, 8 flushes, need no fold and the high word is reduced
+    // once before the REDC); when the giant step ends, store it
+    auto close_batch = [&](AccK (&p)[B][2], int jc, bool last) {
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             flushk(acc[b][0], p[b][0]);
@@ -473,21 +455,75 @@ __global__ void __launch_bounds__(512, (B == 1 ? 2 : 1)) k_mac(const u64* __rest
                 fold(acc[b][1], q);
             }
         }
+        if (last) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                u64* O = out + (long long)b * out_q + (long long)jc * 2 * cap_o * N;
+                O[(long long)i * N + k] = redc(mul_shoup(acc[b][0].hi, 1, one_s, q), acc[b][0].lo, q, qinv);
+                O[((long long)cap_o + i) * N + k] = redc(mul_shoup(acc[b][1].hi, 1, one_s, q), acc[b][1].lo, q, qinv);
+                acc[b][0] = acc[b][1] = Acc128{0, 0};
+            }
+        }
+    };
+    const u64* dbase = diags + (long long)i * N + k;
+    if (ell % n1 == 0 && n1 % 8 == 0) {
+        // every batch is full: while a batch is multiplied, each word's register is refilled with
+        // the same word of the next batch, so eight loads per thread stay in flight throughout
+        u64 d[8];
+        {
+            const u64* D = dbase + (long long)j * n1 * dstride;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = __ldcs(D + u * dstride);
+        }
+        for (;;) {
+            int jn = j, in = i0 + 8;
+            if (in == n1) {
+                jn = j + JG;
+                in = 0;
+            }
+            const bool more = jn < n2;
+            const u64* Dn = dbase + ((long long)(more ? jn : j) * n1 + (more ? in : i0)) * dstride;
+            const u64* s0 = sbase + i0 * TP2;
+            AccK p[B][2];
+#pragma unroll
+            for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = AccK{0, 0, 0};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const u64 w = d[u];
+                if (more) d[u] = __ldcs(Dn + u * dstride);
+                mul_word(p, w, s0 + u * TP2);
+            }
+            close_batch(p, j, jn != j);
+            if (!more) break;
+            j = jn;
+            i0 = in;
+        }
+        return;
+    }
+    for (;;) {
+        const int cnt = min(n1, ell - j * n1);
+        const u64* D = dbase + ((long long)j * n1 + i0) * dstride;
+        const u64* s0 = sbase + i0 * TP2;
+        AccK p[B][2];
+#pragma unroll
+        for (int b = 0; b < B; ++b) p[b][0] = p[b][1] = AccK{0, 0, 0};
+        if (i0 + 8 <= cnt) {
+            // full batch: no bounds checks
+            u64 d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = __ldcs(D + u * dstride);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mul_word(p, d[u], s0 + u * TP2);
+        } else {
+            for (int u = 0; i0 + u < cnt; ++u) mul_word(p, __ldcs(D + (long long)u * dstride), s0 + u * TP2);
+        }
         // next batch
         int jn = j, in = i0 + 8;
         if (in >= cnt) {
             jn = j + JG;
             in = 0;
         }
-        if (jn != j) {
-#pragma unroll
-            for (int b = 0; b < B; ++b) {
-                u64* O = out + (long long)b * out_q + (long long)j * 2 * cap_o * N;
-                O[(long long)i * N + k] = redc(mul_shoup(acc[b][0].hi, 1, one_s, q), acc[b][0].lo, q, qinv);
-                O[((long long)cap_o + i) * N + k] = redc(mul_shoup(acc[b][1].hi, 1, one_s, q), acc[b][1].lo, q, qinv);
-                acc[b][0] = acc[b][1] = Acc128{0, 0};
-            }
-        }
+        close_batch(p, j, jn != j);
         if (jn >= n2) break;
         j = jn;
         i0 = in;
@@ -780,11 +816,12 @@ __global__ void __launch_bounds__(512, 2) k_mac_ct(const u64* __restrict__ babie
     const int k = blockIdx.x * TP + pl;
     const int i = blockIdx.y;
     const u64 q = primes[i].q, qinv = primes[i].qinv;
-    for (int e = threadIdx.x; e < n1 * TP; e += TP * JG) {
-        const int ib = e / TP, pp = e % TP;
-        const u64* src = babies + (long long)ib * 2 * cap_b * N + (long long)i * N + (long long)blockIdx.x * TP + pp;
+    // staging: thread (pl, jg) takes point pl of babies jg, jg + JG, ... (no index divisions)
+#pragma unroll 4
+    for (int ib = jg; ib < n1; ib += JG) {
+        const u64* src = babies + (long long)ib * 2 * cap_b * N + (long long)i * N + k;
         const u64 b0 = src[0], b1 = src[(long long)cap_b * N];
-        u64* dst = sb + (size_t)ib * 3 * TP + pp;
+        u64* dst = sb + (size_t)ib * 3 * TP + pl;
         dst[0] = split30(b0);
         dst[TP] = split30(b1);
         dst[2 * TP] = split30(add_mod(b0, b1, q));
