@@ -362,9 +362,11 @@ fr_status fr_sync(fr_ctx* ctx);
  * fr_match_batch captures the match with the region events as event-record nodes of a graph
  * and replays it once: regions are timed back to back as in a graph replay, and "match" times
  * the whole replay. With graphs off the events are recorded around each launch as it is
- * enqueued (host launch gaps fall inside the regions). A profiled match runs the two branches
- * of the Chebyshev stage on one stream, so no two regions overlap; the event records add to
- * "match", which therefore exceeds an unprofiled match. */
+ * enqueued (host launch gaps fall inside the regions). A match profiled by region class runs
+ * the two branches of the Chebyshev stage on one stream, so no two regions overlap; one
+ * restricted to the stages (fr_profile_only "stage:") keeps the two streams, so "stage:cheb"
+ * times the stage as an unprofiled match runs it. The event records add to "match", which
+ * therefore exceeds an unprofiled match. */
 fr_status fr_profile(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, const char* region, double* ms, uint64_t* launches, uint64_t* bytes);
 /* Restrict profiling to the regions whose name starts with `prefix` (NULL or "": every

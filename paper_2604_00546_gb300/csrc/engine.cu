@@ -838,9 +838,11 @@ void chebyshev(fr_ctx* c, const u64* x, int B, int ls, int x_cap, u64* out, int 
     if (d2 + 2 > (int)c->evs.size()) raise(FR_ERR_UNSUPPORTED, "Chebyshev degree too large");
     const int nleaves = (int)c->leaves.size();
     // Two concurrent branches: the giant powers T_{2^m} on the current stream, the
-    // leaves and the tree on the side stream; tree level s waits for T_{2^s} only. A profiled
-    // match runs both branches on one stream, so that no two timed regions overlap.
-    cudaStream_t main = c->cur, side = c->prof ? c->cur : c->side;
+    // leaves and the tree on the side stream; tree level s waits for T_{2^s} only. A match
+    // profiled by region class runs both branches on one stream, so that no two timed regions
+    // overlap; one that times stages only (filter "stage:") keeps both streams, as unprofiled.
+    const bool one_stream = c->prof && c->prof_only.compare(0, 6, "stage:") != 0;
+    cudaStream_t main = c->cur, side = one_stream ? c->cur : c->side;
     // Declared first, destroyed last. If an exception unwinds this function, the buffers its
     // locals free are held back (dfree) until both branches have finished, so no kernel still
     // queued on either stream can touch memory the pool has taken back.

@@ -126,3 +126,28 @@ def test_profile_only_times_one_region_class(orc):
         assert (n_ip > 0) == (only in ("ip", ""))
         assert ms_ntt + ms_ip <= ms_match
     ctx.profile_only("")
+
+
+def test_stage_profile_keeps_both_chebyshev_streams():
+    # a membership match profiled by stages only runs the Chebyshev branches on their two
+    # streams, one profiled by region class on one stream; every form gives the unprofiled bits
+    cfg = "mid"
+    ctx = fr.Context(device=0, **W.ctx_params(cfg))
+    keys = ctx.keygen(ctx.required_rotations(fr.FR_MODE_MEMBERSHIP), W.key_seed(cfg))
+    ctx.load_keys(keys)
+    T, q, _ = W.workload(cfg)
+    db = ctx.load_db(T)
+    qct = ctx.encrypt(keys, q, W.enc_seed(cfg))
+    ref = ctx.match(db, qct, fr.FR_MODE_MEMBERSHIP)[0].export()
+    for only in ("stage:", ""):
+        ctx.profile_only(only)
+        ctx.profile(True)
+        out = ctx.match(db, qct, fr.FR_MODE_MEMBERSHIP)[0].export()
+        ms_cheb, n_cheb, _ = ctx.profile_read("stage:cheb")
+        ms_match, n_match, _ = ctx.profile_read("match")
+        n_ntt = ctx.profile_read("ntt")[1]
+        ctx.profile(False)
+        assert np.array_equal(out, ref)
+        assert n_cheb == 1 and 0 < ms_cheb <= ms_match
+        assert (n_ntt > 0) == (only == "")
+    ctx.profile_only("")
